@@ -1,0 +1,156 @@
+"""CPU oracle (test infrastructure only).
+
+The plain C statement of the extended POP metrics lives in talp_oracle.c; this
+module compiles it with gcc (no FMA contraction) and wraps it with ctypes.
+Only the tests, the smoke check and the benchmark's CPU-baseline leg may use
+it; the product library never imports it.
+
+Inputs are numpy arrays in the record layout of the trace generator:
+host_se int64[N,2], host_state uint8[N], host_off uint64[n+1],
+dev_se int64[N,2], dev_tag uint8[N], dev_off uint64[m+1],
+devices_per_rank uint32[n], region_window int64[R,n,2].
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+SOURCE = os.path.join(_HERE, "talp_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+INT_FIELDS = ("elapsed_ns", "sum_useful", "sum_offload", "sum_mpi", "max_useful_offload",
+              "sum_kernel", "max_kernel", "max_busy", "sum_mem", "sum_idle", "sum_hidden_mem")
+RATIO_FIELDS = ("host_pe", "host_mpi_pe", "host_mpi_lb", "host_mpi_ce", "host_oe",
+                "dev_pe", "dev_lb", "dev_ce", "dev_oe")
+FLAG_EMPTY, FLAG_HOST_NOT_TILED, FLAG_NO_DEVICES = 1, 2, 4
+
+
+def compile_c(src: str, out: str) -> str:
+    """gcc -O2, FP contraction off, so every product and quotient rounds once."""
+    tmp = out + f".{os.getpid()}.tmp"
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
+                           "-fno-fast-math", "-o", tmp, src])
+    os.replace(tmp, out)
+    return out
+
+
+def build(force=False) -> str:
+    """Compile the oracle shared library next to its source."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(SOURCE):
+        compile_c(SOURCE, _LIB)
+    return _LIB
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+class Oracle:
+    """ctypes view of one build of talp_oracle.c."""
+
+    def __init__(self, lib_path: str):
+        lib = ctypes.CDLL(lib_path)
+        P = ctypes.c_void_p
+        lib.oracle_validate.argtypes = [ctypes.c_uint64, P, P, ctypes.c_uint64, P, P]
+        lib.oracle_validate.restype = ctypes.c_int
+        lib.oracle_host_sums.argtypes = [ctypes.c_uint32, P, P, P, P, P]
+        lib.oracle_host_sums.restype = None
+        lib.oracle_device_unions.argtypes = [ctypes.c_uint32, P, P, P, P, P, P]
+        lib.oracle_device_unions.restype = ctypes.c_int
+        lib.oracle_metrics.argtypes = [ctypes.c_uint32, P, P, P, P, P, P, P]
+        lib.oracle_metrics.restype = None
+        self.lib = lib
+
+    def validate(self, t) -> int:
+        hse, hst = _c(t.host_se, np.int64), _c(t.host_state, np.uint8)
+        dse, dtg = _c(t.dev_se, np.int64), _c(t.dev_tag, np.uint8)
+        return int(self.lib.oracle_validate(hse.shape[0], _p(hse), _p(hst), dse.shape[0], _p(dse), _p(dtg)))
+
+    def host_sums(self, t, region: int) -> np.ndarray:
+        """int64[n,3]: per rank (useful, offload, MPI) time inside the region."""
+        n = int(t.n_ranks)
+        out = np.zeros((n, 3), np.int64)
+        hse, hst, hoff = _c(t.host_se, np.int64), _c(t.host_state, np.uint8), _c(t.host_off, np.uint64)
+        win = _c(t.region_window[region], np.int64)
+        self.lib.oracle_host_sums(n, _p(hse), _p(hst), _p(hoff), _p(win), _p(out))
+        return out
+
+    def device_unions(self, t, region: int) -> np.ndarray:
+        """int64[m,3]: per device |U kernels|, |U memory ops|, |U all| inside the region."""
+        n = int(t.n_ranks)
+        dpr = _c(t.devices_per_rank, np.uint32)
+        m = int(dpr.sum())
+        out = np.zeros((m, 3), np.int64)
+        dse, dtg, doff = _c(t.dev_se, np.int64), _c(t.dev_tag, np.uint8), _c(t.dev_off, np.uint64)
+        win = _c(t.region_window[region], np.int64)
+        rc = self.lib.oracle_device_unions(n, _p(dpr), _p(dse), _p(dtg), _p(doff), _p(win), _p(out))
+        if rc != 0:
+            raise MemoryError("oracle_device_unions")
+        return out
+
+    def metrics_from_sums(self, n_ranks, devices_per_rank, hs, du, win) -> dict:
+        dpr = _c(devices_per_rank, np.uint32)
+        hs = _c(hs, np.int64)
+        du = _c(du, np.int64)
+        win = _c(win, np.int64)
+        iout = np.zeros(11, np.int64)
+        dout = np.zeros(9, np.float64)
+        flags = np.zeros(1, np.uint32)
+        self.lib.oracle_metrics(int(n_ranks), _p(dpr), _p(hs), _p(du), _p(win), _p(iout), _p(dout), _p(flags))
+        res = {k: int(v) for k, v in zip(INT_FIELDS, iout)}
+        res.update({k: float(v) for k, v in zip(RATIO_FIELDS, dout)})
+        res["flags"] = int(flags[0])
+        res["n_ranks"] = int(n_ranks)
+        res["m_devices"] = int(dpr.sum())
+        return res
+
+    def region_metrics(self, t, region: int) -> dict:
+        """All sums and the nine ratios of one region (Eqs. 1, 6-12)."""
+        hs = self.host_sums(t, region)
+        du = self.device_unions(t, region)
+        return self.metrics_from_sums(t.n_ranks, t.devices_per_rank, hs, du, t.region_window[region])
+
+    def trace_metrics(self, t) -> list:
+        return [self.region_metrics(t, r) for r in range(int(t.region_window.shape[0]))]
+
+
+_default = None
+
+
+def default() -> Oracle:
+    global _default
+    if _default is None:
+        _default = Oracle(build())
+    return _default
+
+
+def validate(t):
+    return default().validate(t)
+
+
+def host_sums(t, region):
+    return default().host_sums(t, region)
+
+
+def device_unions(t, region):
+    return default().device_unions(t, region)
+
+
+def metrics_from_sums(*a):
+    return default().metrics_from_sums(*a)
+
+
+def region_metrics(t, region):
+    return default().region_metrics(t, region)
+
+
+def trace_metrics(t):
+    return default().trace_metrics(t)

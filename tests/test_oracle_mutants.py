@@ -1,0 +1,56 @@
+"""The pins must catch plausible mistakes in the oracle.
+
+Each mutant is a copy of talp_oracle.c with one planted error (a dropped
+term, a wrong sign, a wrong index, a transposed operand, a missing clip),
+compiled on the CPU into a temporary library; at least one pin of
+test_oracle_pins must fail against it.
+"""
+import os
+
+import pytest
+
+import oracle
+from test_oracle_pins import ALL_PINS
+
+MUTANTS = [
+    ("mpi_pe drops offload (Eq. 7)", "dout[1] = ratio_k(sU + sW, E,", "dout[1] = ratio_k(sU, E,"),
+    ("host LB/CE use useful only", "maxUW = max64(maxUW, U + W);", "maxUW = max64(maxUW, U);"),
+    ("elapsed drops MPI (Eq. 1)", "E = max64(E, U + W + P);", "E = max64(E, U + W);"),
+    ("OE_host counts MPI (Eq. 8)", "dout[4] = ratio(sU, sU + sW);", "dout[4] = ratio(sU, sU + sW + sMPI);"),
+    ("transfers not reduced by kernels", "int64_t DM = B - K;", "int64_t DM = UM;"),
+    ("transfer sign flipped", "int64_t DM = B - K;", "int64_t DM = K - B;"),
+    ("device OE uses device span (Eq. 12)", "dout[8] = ratio(maxB, E);", "dout[8] = ratio(maxB, maxB);"),
+    ("CE_dev transposed (Eq. 11)", "dout[7] = ratio(maxK, maxB);", "dout[7] = ratio(maxB, maxK);"),
+    ("LB_dev divides by n (Eq. 10)", "dout[6] = ratio_k(sK, (int64_t)m, maxK);",
+     "dout[6] = ratio_k(sK, (int64_t)n_ranks, maxK);"),
+    ("PE_dev divides by n (Eq. 9)", "dout[5] = ratio_k(sK, E, (int64_t)m);", "dout[5] = ratio_k(sK, E, (int64_t)n_ranks);"),
+    ("max busy is max kernel + max transfer", "maxB = max64(maxB, K + DM);", "maxB = max64(maxB, K) + 0 * DM;"),
+    ("device start not clipped", "int64_t s = max64(dev_se[2 * j], a);", "int64_t s = dev_se[2 * j];"),
+    ("host end not clipped", "int64_t hi = min64(host_se[2 * j + 1], b);", "int64_t hi = host_se[2 * j + 1];"),
+    ("kind read from the stream bits", "if ((dev_tag[j] >> 5) == 0) kv", "if ((dev_tag[j] & 31) == 0) kv"),
+    ("nested interval shrinks the run", "} else if (v[j].e > ce) {   /* overlapping or touching: extend */",
+     "} else {   /* overlapping or touching: extend */"),
+    ("union drops the last run", "    total += ce - cs;\n    return total;", "    return total;"),
+    ("host state collapsed", "if (hi > lo) acc[host_state[j]] += hi - lo;", "if (hi > lo) acc[0] += hi - lo;"),
+    ("idle uses window start", "sIdle += len - B;", "sIdle += win[2 * i] - B;"),
+    ("hidden transfer sign", "sHidden += K + UM - B;", "sHidden += K - UM + B;"),
+    ("0/0 reads as 0", "if (k == 0 || den == 0) return 1.0;", "if (k == 0 || den == 0) return 0.0;"),
+    ("validation ignores kind", "if ((dev_tag[j] >> 5) > 4) bad |= 8;", "if ((dev_tag[j] >> 5) > 7) bad |= 8;"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(name, old, new, tmp_path):
+    src = open(oracle.SOURCE).read()
+    assert src.count(old) == 1, f"mutation site not unique/present: {old!r}"
+    mut = os.path.join(tmp_path, "mutant.c")
+    open(mut, "w").write(src.replace(old, new))
+    lib = oracle.compile_c(mut, os.path.join(tmp_path, "libmutant.so"))
+    O = oracle.Oracle(lib)
+    caught = []
+    for pin in ALL_PINS:
+        try:
+            pin(O)
+        except AssertionError:
+            caught.append(pin.__name__)
+    assert caught, f"no pin catches mutant: {name}"
