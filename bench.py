@@ -1,0 +1,366 @@
+#!/usr/bin/env python3
+"""Benchmark of the efficiency-metric reducer on synthetic traces.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
+                  [--workload plain|small] [--scale S]
+
+One step = one pass of the whole hot path over one trace resident in HBM:
+record validation, the device flattening (kernel / transfer / busy unions per
+device and region), the host-state sums, and the final reduction into the
+nine efficiency ratios of every region (launched through the C ABI).
+
+Default workload ("plain"): one trace of 64 ranks x 4 GPUs x 4 streams,
+2M device events per GPU and 1M host intervals per rank, 4 nested regions
+(576M records, 9.8 GB), generated seeded on the host.  Its inputs are far
+larger than the 126 MB L2, so no flush is needed between steps.
+
+value   : records (events) per second with the inputs already in HBM;
+e2e     : the same metric through the C ABI from pinned HOST buffers, the
+          host->device copy of every step's records and the device->host
+          copy of its metrics inside the timed region;
+roofline: the sweep kernel (the dominant kernel) against the measured HBM
+          copy bandwidth: 17 algorithmic bytes per record / its CUDA-event
+          duration;
+cpu_baseline: the CPU oracle on a bounded one-rank sample of the workload.
+
+--impl reference times the CPU oracle itself (the slow, plain statement of
+the method) on a bounded sample per step; it is the reference arm.
+
+With N > 1 (torchrun, one rank per GPU) every rank reduces its own trace of
+the same shape (weak scaling, no collective on the data path); the timing is
+the max over ranks.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import tracegen as tg  # noqa: E402
+
+METRIC = "events/s and HBM GB/s for host+device efficiency metrics; p99 runtime-query ms"
+UNIT = "events/s"
+BYTES_PER_RECORD = 17
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--workload", default="plain", choices=["plain", "small"])
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name, scale, rank):
+    if name == "plain":
+        t = tg.plain_large(seed=0x7A1F + 1 + 1000 * rank, scale=scale, trace_id=1 + rank)
+        desc = "plain large single trace: 64 ranks x 4 GPUs x 4 streams, 2M device events/GPU, " \
+               "1M host intervals/rank, 4 nested regions"
+    else:
+        t = tg.single_trace_small(seed=0x7A1F + 1000 * rank, scale=scale, trace_id=rank)
+        desc = "single trace: 4 ranks x 1 GPU x 1 stream, 10k host + 10k device intervals/rank, 1 region"
+    return t, desc
+
+
+def oracle_sample(name, scale):
+    """A bounded sample of the workload for the CPU oracle: one rank of it."""
+    if name == "plain":
+        return tg.plain_large(seed=0x7A1F + 1, scale=scale, trace_id=1, n_ranks=1)
+    return tg.single_trace_small(scale=scale)
+
+
+def time_oracle(t):
+    import oracle
+    t0 = time.perf_counter()
+    for r in range(t.n_regions):
+        oracle.host_sums(t, r)
+        oracle.device_unions(t, r)
+    return time.perf_counter() - t0
+
+
+class Clocks:
+    """nvidia-smi sampler for the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def sweep_traffic_per_record():
+    """dram bytes per record of the sweep kernel from the committed ncu
+    summary, valid only while the kernel source is unchanged."""
+    src = os.path.join(ROOT, "paper_2603_26576_b300", "csrc", "sweep.cu")
+    prof = os.path.join(ROOT, "profiles", "sweep_plain_large.txt")
+    if not os.path.exists(prof):
+        return None
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    kv = {}
+    for ln in open(prof):
+        if ":" in ln:
+            k, v = ln.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("sweep_source_sha256_16") != h:
+        return None
+    try:
+        return float(kv["dram_bytes_per_record"])
+    except (KeyError, ValueError):
+        return None
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(a):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    t = oracle_sample(a.workload, a.scale if a.workload == "small" else min(a.scale, 1.0))
+    n = t.n_records
+    for _ in range(a.warmup):
+        time_oracle(t)
+    dts = [time_oracle(t) for _ in range(a.steps)]
+    total = sum(dts)
+    value = n * a.steps / total
+    _, desc = (None, "")
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": 1000 * total / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64", "data": "synthetic (seeded generator)", "impl": "reference",
+        "config": {"workload": workload_name(a), "sample": f"one rank of the workload: {n} records per step",
+                   "l2": "inputs in host memory (CPU oracle)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"one rank ({t.m_devices} devices, {n} records) x {t.n_regions} regions"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_name(a):
+    if a.workload == "plain":
+        base = "plain large single trace: 64 ranks x 4 GPUs x 4 streams, 2M device events/GPU, 1M host intervals/rank, 4 nested regions"
+    else:
+        base = "single trace: 4 ranks x 1 GPU x 1 stream, 10k host + 10k device intervals/rank, 1 region"
+    return base if a.scale == 1.0 else f"{base} (scale {a.scale})"
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    import torch
+    import paper_2603_26576_b300 as P
+
+    ws, rank, local = dist_setup()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", local)
+
+    t, _ = workload(a.workload, a.scale, rank)
+    N = t.n_records
+    R = t.n_regions
+
+    # device-resident copies of the records
+    d_arrays = dict(host_se=torch.from_numpy(t.host_se).to(dev), host_state=torch.from_numpy(t.host_state).to(dev),
+                    dev_se=torch.from_numpy(t.dev_se).to(dev), dev_tag=torch.from_numpy(t.dev_tag).to(dev))
+    torch.cuda.synchronize()
+    ctx = P.Context(local)
+    stream = torch.cuda.Stream(device=dev)
+    flags = P.TALP_GPU_SORTED_BY_START
+    batch_d, keep_d = P.batch_from_arrays(t.trace_id, t.devices_per_rank, t.region_window, d_arrays["host_se"],
+                                          d_arrays["host_state"], t.host_off, d_arrays["dev_se"],
+                                          d_arrays["dev_tag"], t.dev_off, flags)
+    out_dev = torch.empty(R * 200, dtype=torch.uint8, device=dev)
+
+    def step_device():
+        P.talp_gpu_ingest_events(ctx.ctx, [batch_d], stream)
+        P.talp_gpu_region_metrics_device(ctx.ctx, [t.trace_id], P.TALP_GPU_ALL_REGIONS, out_dev.data_ptr(), stream)
+
+    for _ in range(max(a.warmup, 3) if a.warmup >= 3 else 3):
+        step_device()
+    torch.cuda.synchronize()
+    # the results of the warm-up are checked once through the host API
+    res = P.talp_gpu_region_metrics(ctx.ctx, t.trace_id, P.TALP_GPU_ALL_REGIONS, stream, n_regions=R)
+    P.talp_gpu_profile(ctx.ctx, True)
+    P.talp_gpu_profile_read(ctx.ctx)
+    launches0 = P.talp_gpu_profile_read(ctx.ctx)["kernel_launches"]
+
+    clocks = Clocks(torch.cuda.current_device() if ws == 1 else local)
+    clocks.start()
+    time.sleep(0.3)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        step_device()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    prof = P.talp_gpu_profile_read(ctx.ctx)
+    P.talp_gpu_profile(ctx.ctx, False)
+    launches = prof["kernel_launches"] - launches0
+    if ws > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = N * a.steps * ws / (ms / 1000.0)
+
+    # ---- end to end through the C ABI from pinned host buffers
+    e2e = None
+    if not a.no_e2e:
+        h_arrays = dict(host_se=torch.from_numpy(t.host_se).pin_memory(),
+                        host_state=torch.from_numpy(t.host_state).pin_memory(),
+                        dev_se=torch.from_numpy(t.dev_se).pin_memory(),
+                        dev_tag=torch.from_numpy(t.dev_tag).pin_memory())
+        batch_h, keep_h = P.batch_from_arrays(t.trace_id, t.devices_per_rank, t.region_window, h_arrays["host_se"],
+                                              h_arrays["host_state"], t.host_off, h_arrays["dev_se"],
+                                              h_arrays["dev_tag"], t.dev_off, flags)
+
+        def step_e2e():
+            P.talp_gpu_ingest_events(ctx.ctx, [batch_h], stream)
+            return P.talp_gpu_region_metrics(ctx.ctx, t.trace_id, P.TALP_GPU_ALL_REGIONS, stream, n_regions=R)
+
+        step_e2e()
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        k = max(1, a.e2e_steps)
+        w0 = time.perf_counter()
+        for _ in range(k):
+            step_e2e()
+        w1 = time.perf_counter()
+        el = w1 - w0
+        if ws > 1:
+            tt = torch.tensor([el], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            el = float(tt.item())
+        h2d = (t.host_se.nbytes + t.host_state.nbytes + t.dev_se.nbytes + t.dev_tag.nbytes)
+        meta = t.devices_per_rank.nbytes + t.region_window.nbytes + t.host_off.nbytes + t.dev_off.nbytes
+        e2e = {"value": N * k * ws / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d + meta),
+               "d2h_bytes_per_step": int(R * 200), "steps": k}
+
+    # ---- roofline of the sweep kernel
+    peak, peak_kind = measured_peaks()
+    sweep_ms = prof["sweep_ms"] / max(1, prof["sweep_launches"])
+    achieved = BYTES_PER_RECORD * N / (sweep_ms / 1000.0) / 1e9
+    tpr = sweep_traffic_per_record()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": (tpr * N) if tpr is not None else None, "kernel": "talp::sweep_kernel",
+            "kernel_ms": sweep_ms, "peak_source": f"{peak_kind} hbm_gbs"}
+
+    # ---- CPU oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and ws == 1 and not a.no_cpu_baseline:
+        s = oracle_sample(a.workload, a.scale)
+        dt = time_oracle(s)
+        cpu = {"value": s.n_records / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one rank of the workload ({s.m_devices} devices, {s.n_records} records) x "
+                         f"{s.n_regions} regions, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64", "data": "synthetic (seeded generator; the paper's traces are not available)",
+            "config": {"workload": workload_name(a), "records_per_step": N, "bytes_per_step": BYTES_PER_RECORD * N,
+                       "regions": R, "l2": "inputs (%.1f GB) larger than L2; no flush" % (BYTES_PER_RECORD * N / 1e9),
+                       "input_order": "device records in start order (caller asserts SORTED_BY_START)",
+                       "hbm_gb_per_s": BYTES_PER_RECORD * N * a.steps / (ms / 1000.0) / 1e9},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": ck,
+            "check": {"elapsed_ns_region0": res[0].elapsed_ns, "dev_pe_region0": res[0].dev_pe},
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

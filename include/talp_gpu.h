@@ -1,0 +1,260 @@
+/*
+ * talp_gpu.h -- C ABI of the B300 efficiency-metric reducer.
+ *
+ * The library turns per-rank host-state intervals and per-device activity
+ * records into the extended POP efficiency hierarchy of "Hardware-Agnostic
+ * and Insightful Efficiency Metrics for Accelerated Systems" (arXiv
+ * 2603.26576), per monitoring region:
+ *   host tree   (Sec. 4.1, Eqs. 6-8): Host Hybrid Parallel Efficiency =
+ *               MPI Parallel Efficiency (= load balance x communication
+ *               efficiency, offloading counted as useful) x Device Offload
+ *               Efficiency;
+ *   device tree (Sec. 4.1, Eqs. 9-12): Device Parallel Efficiency = load
+ *               balance x communication efficiency x orchestration efficiency,
+ *               over the kernel / memory-operation / idle occupancy of every
+ *               device obtained by the flattening of Sec. 4.2.
+ * All interval arithmetic is exact int64 nanoseconds on the GPU; the nine
+ * ratios are formed in FP64 with a fixed expression order.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Intervals are half open [start, end) in int64 ns; end == start adds 0;
+ *    end < start is invalid input.
+ *  - A record is 16 bytes {int64 start, int64 end} in an array `*_se`
+ *    (row j at se[2j], se[2j+1]) plus one byte in a parallel array:
+ *      host:   state, one of TALP_HOST_* (Sec. 4.1 host states);
+ *      device: tag = kind << 5 | stream, kind one of TALP_DEV_* (kernel or a
+ *              memory operation, Sec. 4.1 / 4.2), stream 0..31.
+ *  - Records are grouped by CSR offsets: host records by rank
+ *    (host_off[n_ranks + 1]); device records by device, devices numbered
+ *    rank-major (rank 0's devices first), dev_off[m + 1] with
+ *    m = sum(devices_per_rank).  A device owns no records of other ranks.
+ *  - A region is one window [begin, end) per rank; every host interval of a
+ *    rank and every record of its devices is clipped to it (regions are
+ *    independent; nesting is allowed).
+ *  - A ratio whose denominator is 0 reads 1 (no loss attributable to that
+ *    factor); E == 0 sets TALP_GPU_M_EMPTY and every ratio to 1.
+ *  - Errors are returned as talp_gpu_status; nothing throws across the ABI.
+ *    talp_gpu_last_error() gives a message for the calling thread.
+ *  - `stream` is a cudaStream_t (0 = legacy default stream).  Calls that
+ *    return results to the host synchronise that stream; the others are
+ *    stream ordered and return once the work is enqueued.
+ *  - Every call is safe from one host thread per context; a context must
+ *    not be used by two threads at once.
+ */
+#ifndef TALP_GPU_H
+#define TALP_GPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TALP_GPU_ABI_VERSION 1
+#define TALP_GPU_MAX_REGIONS 8
+#define TALP_GPU_ALL ((uint64_t)-1)             /* talp_gpu_reset: every trace */
+#define TALP_GPU_ALL_REGIONS ((uint32_t)-1)     /* region selector: all regions */
+
+typedef struct talp_gpu_ctx talp_gpu_ctx;       /* opaque; owns all device state */
+
+typedef enum {
+    TALP_GPU_OK = 0,
+    TALP_GPU_EINVAL = -1,      /* bad argument or invalid record detected */
+    TALP_GPU_ENOMEM = -2,      /* HBM budget or device allocation exhausted */
+    TALP_GPU_ECUDA = -3,       /* a CUDA runtime call failed */
+    TALP_GPU_ETIMEDOUT = -4,   /* a bounded device-side wait ran out */
+    TALP_GPU_ENOTFOUND = -5,   /* unknown trace id or job id */
+    TALP_GPU_EBUSY = -6        /* resource in use (serving slot, pending work) */
+} talp_gpu_status;
+
+/* host states (Sec. 4.1): useful, device offloading, MPI calls */
+enum { TALP_HOST_USEFUL = 0, TALP_HOST_OFFLOAD = 1, TALP_HOST_MPI = 2 };
+/* device record kinds: kernel = useful; the rest are memory operations
+ * (GPU-GPU and CPU-GPU transfers and memsets, Sec. 4.1 / 4.2) */
+enum { TALP_DEV_KERNEL = 0, TALP_DEV_H2D = 1, TALP_DEV_D2H = 2, TALP_DEV_D2D = 3, TALP_DEV_MEMSET = 4 };
+#define TALP_DEV_TAG(kind, stream) ((uint8_t)((((unsigned)(kind)) << 5) | (((unsigned)(stream)) & 31u)))
+
+/* talp_gpu_trace_batch.flags */
+#define TALP_GPU_DEVICE_PTRS     0x1u  /* host_se/host_state/dev_se/dev_tag are device pointers */
+#define TALP_GPU_SORTED_BY_START 0x2u  /* caller asserts each device's records are in start order */
+#define TALP_GPU_APPEND          0x4u  /* fold into the trace's running state (later time slice) */
+
+/*
+ * One trace (or one later time slice of it with TALP_GPU_APPEND).
+ *
+ * Pointers marked "host" are always host memory and are read during the
+ * call.  The four record arrays are host memory, or device memory of the
+ * context's GPU when TALP_GPU_DEVICE_PTRS is set; device record arrays must
+ * start on a 16-byte boundary and stay valid and unmodified until `stream`
+ * has passed the ingest call.  Host record arrays are copied during the call
+ * (pinned memory makes the copy faster; pageable memory works).
+ *
+ * Without TALP_GPU_SORTED_BY_START the library checks the order of every
+ * device's records on the GPU and sorts the devices that need it.  With the
+ * flag, a device found out of order makes the next result call return
+ * TALP_GPU_EINVAL.
+ *
+ * TALP_GPU_APPEND continues an existing trace: the shape (n_ranks,
+ * devices_per_rank, n_regions) must match, every device's new records must
+ * start no earlier than its last ingested record, and the windows given here
+ * replace the stored ones.  Without APPEND an existing trace of the same id is
+ * replaced.
+ */
+typedef struct {
+    uint64_t trace_id;
+    uint32_t n_ranks;                  /* n >= 1 */
+    uint32_t n_regions;                /* 1 .. TALP_GPU_MAX_REGIONS */
+    uint32_t flags;
+    uint32_t reserved;                 /* must be 0 */
+    const uint32_t *devices_per_rank;  /* host [n_ranks] */
+    const int64_t *region_window;      /* host [n_regions][n_ranks][2] = [begin, end) */
+    const int64_t *host_se;            /* [N_host][2] */
+    const uint8_t *host_state;         /* [N_host] */
+    const uint64_t *host_off;          /* host [n_ranks + 1], host_off[0] == 0 */
+    const int64_t *dev_se;             /* [N_dev][2] */
+    const uint8_t *dev_tag;            /* [N_dev] */
+    const uint64_t *dev_off;           /* host [m + 1], dev_off[0] == 0 */
+} talp_gpu_trace_batch;
+
+/* talp_gpu_metrics.flags */
+#define TALP_GPU_M_EMPTY          0x1u  /* E == 0: every ratio reported as 1 */
+#define TALP_GPU_M_HOST_NOT_TILED 0x2u  /* some rank's host intervals do not sum to its window */
+#define TALP_GPU_M_NO_DEVICES     0x4u  /* m == 0: device ratios reported as 1 */
+#define TALP_GPU_M_INVALID        0x100u /* invalid record seen (end < start, bad kind/state) */
+#define TALP_GPU_M_UNSORTED       0x200u /* out-of-order device records under SORTED_BY_START/APPEND */
+#define TALP_GPU_M_TIMEOUT        0x400u /* a bounded device-side wait ran out while ingesting */
+
+/*
+ * Metrics of one region of one trace.  Sums are over ranks (host) or devices
+ * (device) of the region-clipped times; every time is int64 ns.
+ */
+typedef struct {
+    uint64_t trace_id;
+    uint32_t region;
+    uint32_t flags;                    /* TALP_GPU_M_* */
+    uint32_t n_ranks;                  /* n */
+    uint32_t m_devices;                /* m */
+    int64_t elapsed_ns;                /* E = max_i (U_i + W_i + MPI_i), Eq. 1 */
+    int64_t sum_useful;                /* sum_i U_i (Eq. 2) */
+    int64_t sum_offload;               /* sum_i W_i */
+    int64_t sum_mpi;                   /* sum_i MPI_i */
+    int64_t max_useful_offload;        /* max_i (U_i + W_i) */
+    int64_t sum_kernel;                /* sum_g D_K,g  (kernel union per device) */
+    int64_t max_kernel;                /* max_g D_K,g */
+    int64_t max_busy;                  /* max_g (D_K,g + D_M,g) */
+    int64_t sum_mem;                   /* sum_g D_M,g  (transfers not under kernels) */
+    int64_t sum_idle;                  /* sum_g (window_g - D_K,g - D_M,g) */
+    int64_t sum_hidden_mem;            /* sum_g |transfers under kernels| */
+    double host_pe;                    /* Eq. 6  sum U / (E n) */
+    double host_mpi_pe;                /* Eq. 7  sum (U+W) / (E n) */
+    double host_mpi_lb;                /* sum (U+W) / (n max (U+W)) */
+    double host_mpi_ce;                /* max (U+W) / E */
+    double host_oe;                    /* Eq. 8  sum U / sum (U+W) */
+    double dev_pe;                     /* Eq. 9  sum D_K / (E m) */
+    double dev_lb;                     /* Eq. 10 sum D_K / (m max D_K) */
+    double dev_ce;                     /* Eq. 11 max D_K / max (D_K + D_M) */
+    double dev_oe;                     /* Eq. 12 max (D_K + D_M) / E */
+} talp_gpu_metrics;
+
+/* ---------------------------------------------------------------- context */
+
+/*
+ * Create a context on CUDA device `device`.  hbm_budget_bytes caps the device
+ * memory the context may hold (traces, staging, workspace); 0 means 90% of
+ * the device's free memory at creation.  *out receives the context.
+ * Errors: EINVAL (null out, bad device), ECUDA.
+ */
+talp_gpu_status talp_gpu_create(talp_gpu_ctx **out, int device, size_t hbm_budget_bytes);
+
+/* Free every device buffer and the context.  NULL is accepted. */
+talp_gpu_status talp_gpu_destroy(talp_gpu_ctx *ctx);
+
+/* ------------------------------------------------------------------ ingest */
+
+/*
+ * Ingest n_batches traces (the plain form is n_batches == 1; larger n is the
+ * batched form: every trace is reduced by the same persistent launch
+ * sequence).  Validation of the headers happens on the host before anything
+ * is enqueued (EINVAL, nothing changed); validation of the records happens on
+ * the GPU and surfaces as EINVAL from the next result call for that trace.
+ * Admission: ENOMEM is returned before any allocation when the traces would
+ * exceed the context's HBM budget.  The call is stream ordered.
+ * The trace's per-rank and per-device partial sums stay on the device
+ * (Sec. 4.2 flattening and the host-state sums of Sec. 4.1).
+ */
+talp_gpu_status talp_gpu_ingest_events(talp_gpu_ctx *ctx, const talp_gpu_trace_batch *batches,
+                                       size_t n_batches, void *stream);
+
+/* ----------------------------------------------------------------- results */
+
+/*
+ * Metrics of `region` (or every region with TALP_GPU_ALL_REGIONS, written to
+ * out_host[0 .. n_regions-1]) of trace `trace_id`: the Eqs. 1 and 6-12 ratios
+ * formed on the GPU from its sums.  Synchronises `stream`.
+ * Errors: ENOTFOUND (unknown trace), EINVAL (bad region, or invalid records
+ * were ingested: out_host is still written and its flags say why),
+ * ETIMEDOUT (a device-side bounded wait ran out during ingest), ECUDA.
+ */
+talp_gpu_status talp_gpu_region_metrics(talp_gpu_ctx *ctx, uint64_t trace_id, uint32_t region,
+                                        talp_gpu_metrics *out_host, void *stream);
+
+/*
+ * Metrics of one region for n traces with one launch and one copy:
+ * out_host[k] belongs to trace_ids[k].  Same errors as above (the first
+ * failing trace decides the status; every entry is written).
+ */
+talp_gpu_status talp_gpu_region_metrics_batch(talp_gpu_ctx *ctx, const uint64_t *trace_ids, size_t n,
+                                              uint32_t region, talp_gpu_metrics *out_host, void *stream);
+
+/*
+ * Stream-ordered variant: writes the n metrics structs to device memory
+ * out_device (n entries, 8-byte aligned) without synchronising.  Record
+ * problems are reported only through the flags of the written structs.
+ */
+talp_gpu_status talp_gpu_region_metrics_device(talp_gpu_ctx *ctx, const uint64_t *trace_ids, size_t n,
+                                               uint32_t region, talp_gpu_metrics *out_device,
+                                               void *stream);
+
+/*
+ * Raw per-unit times of one region (TALP also reports raw times so users can
+ * form their own indicators): host_out [n_ranks][3] = useful, offload, MPI
+ * per rank; dev_out [m][3] = kernel union D_K, memory-operation union, busy
+ * union B per device (D_M = B - D_K).  Either pointer may be NULL.  Host
+ * memory; synchronises `stream`.
+ */
+talp_gpu_status talp_gpu_unit_sums(talp_gpu_ctx *ctx, uint64_t trace_id, uint32_t region,
+                                   int64_t *host_out, int64_t *dev_out, void *stream);
+
+/* Drop trace_id's state and return its HBM (TALP_GPU_ALL: every trace). */
+talp_gpu_status talp_gpu_reset(talp_gpu_ctx *ctx, uint64_t trace_id);
+
+/* Device bytes the context currently holds, and its budget. */
+talp_gpu_status talp_gpu_memory(talp_gpu_ctx *ctx, size_t *held_bytes, size_t *budget_bytes);
+
+/*
+ * Kernel timing for benchmarks and tracing.  While enabled, every sweep
+ * launch (the pass over the records: flattening, host sums, validation) is
+ * bracketed by CUDA events on the ingest stream.  talp_gpu_profile_read
+ * synchronises those events, returns the totals since the last read and
+ * clears them.  kernel_launches counts every kernel the context launched
+ * (enabled or not).
+ */
+typedef struct {
+    uint64_t sweep_launches;
+    uint64_t sweep_records;            /* records covered by those launches */
+    double sweep_ms;                   /* summed event time of those launches */
+    uint64_t kernel_launches;
+} talp_gpu_profile_stats;
+
+talp_gpu_status talp_gpu_profile(talp_gpu_ctx *ctx, int enable);
+talp_gpu_status talp_gpu_profile_read(talp_gpu_ctx *ctx, talp_gpu_profile_stats *out);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *talp_gpu_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TALP_GPU_H */

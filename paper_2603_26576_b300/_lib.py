@@ -1,0 +1,331 @@
+"""ctypes binding of include/talp_gpu.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtalp_gpu.so")
+
+TALP_GPU_MAX_REGIONS = 8
+TALP_GPU_ALL = (1 << 64) - 1
+TALP_GPU_ALL_REGIONS = (1 << 32) - 1
+TALP_GPU_DEVICE_PTRS = 0x1
+TALP_GPU_SORTED_BY_START = 0x2
+TALP_GPU_APPEND = 0x4
+
+STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEDOUT", -5: "ENOTFOUND", -6: "EBUSY"}
+
+# every function the header declares
+EXPORTED_SYMBOLS = (
+    "talp_gpu_create", "talp_gpu_destroy", "talp_gpu_ingest_events", "talp_gpu_region_metrics",
+    "talp_gpu_region_metrics_batch", "talp_gpu_region_metrics_device", "talp_gpu_unit_sums",
+    "talp_gpu_reset", "talp_gpu_memory", "talp_gpu_profile", "talp_gpu_profile_read", "talp_gpu_last_error",
+)
+
+
+class TalpGpuError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class talp_gpu_trace_batch(ctypes.Structure):
+    _fields_ = [
+        ("trace_id", ctypes.c_uint64),
+        ("n_ranks", ctypes.c_uint32),
+        ("n_regions", ctypes.c_uint32),
+        ("flags", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
+        ("devices_per_rank", ctypes.c_void_p),
+        ("region_window", ctypes.c_void_p),
+        ("host_se", ctypes.c_void_p),
+        ("host_state", ctypes.c_void_p),
+        ("host_off", ctypes.c_void_p),
+        ("dev_se", ctypes.c_void_p),
+        ("dev_tag", ctypes.c_void_p),
+        ("dev_off", ctypes.c_void_p),
+    ]
+
+
+INT_FIELDS = ("elapsed_ns", "sum_useful", "sum_offload", "sum_mpi", "max_useful_offload",
+              "sum_kernel", "max_kernel", "max_busy", "sum_mem", "sum_idle", "sum_hidden_mem")
+RATIO_FIELDS = ("host_pe", "host_mpi_pe", "host_mpi_lb", "host_mpi_ce", "host_oe",
+                "dev_pe", "dev_lb", "dev_ce", "dev_oe")
+
+
+class talp_gpu_profile_stats(ctypes.Structure):
+    _fields_ = [("sweep_launches", ctypes.c_uint64), ("sweep_records", ctypes.c_uint64),
+                ("sweep_ms", ctypes.c_double), ("kernel_launches", ctypes.c_uint64)]
+
+
+class talp_gpu_metrics(ctypes.Structure):
+    _fields_ = ([("trace_id", ctypes.c_uint64), ("region", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                 ("n_ranks", ctypes.c_uint32), ("m_devices", ctypes.c_uint32)]
+                + [(f, ctypes.c_int64) for f in INT_FIELDS]
+                + [(f, ctypes.c_double) for f in RATIO_FIELDS])
+
+
+def metrics_to_dict(m: talp_gpu_metrics) -> dict:
+    d = {f: int(getattr(m, f)) for f in INT_FIELDS}
+    d.update({f: float(getattr(m, f)) for f in RATIO_FIELDS})
+    d.update(trace_id=int(m.trace_id), region=int(m.region), flags=int(m.flags), n_ranks=int(m.n_ranks),
+             m_devices=int(m.m_devices))
+    return d
+
+
+_lib = None
+
+
+def load_library():
+    """Load libtalp_gpu.so; raises if the CUDA library has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library missing: {LIB_PATH} (build it with `python -m paper_2603_26576_b300.build`)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, S = ctypes.c_void_p, ctypes.c_size_t
+    I32, U32, U64 = ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64
+    sig = {
+        "talp_gpu_create": ([ctypes.POINTER(ctypes.c_void_p), I32, S], I32),
+        "talp_gpu_destroy": ([P], I32),
+        "talp_gpu_ingest_events": ([P, ctypes.POINTER(talp_gpu_trace_batch), S, P], I32),
+        "talp_gpu_region_metrics": ([P, U64, U32, ctypes.POINTER(talp_gpu_metrics), P], I32),
+        "talp_gpu_region_metrics_batch": ([P, P, S, U32, ctypes.POINTER(talp_gpu_metrics), P], I32),
+        "talp_gpu_region_metrics_device": ([P, P, S, U32, P, P], I32),
+        "talp_gpu_unit_sums": ([P, U64, U32, P, P, P], I32),
+        "talp_gpu_reset": ([P, U64], I32),
+        "talp_gpu_memory": ([P, ctypes.POINTER(S), ctypes.POINTER(S)], I32),
+        "talp_gpu_profile": ([P, I32], I32),
+        "talp_gpu_profile_read": ([P, ctypes.POINTER(talp_gpu_profile_stats)], I32),
+        "talp_gpu_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def talp_gpu_last_error() -> str:
+    return load_library().talp_gpu_last_error().decode()
+
+
+def _check(st):
+    if st != 0:
+        raise TalpGpuError(st, talp_gpu_last_error())
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def talp_gpu_create(device: int = 0, hbm_budget_bytes: int = 0):
+    ctx = ctypes.c_void_p()
+    _check(load_library().talp_gpu_create(ctypes.byref(ctx), device, hbm_budget_bytes))
+    return ctx
+
+
+def talp_gpu_destroy(ctx):
+    _check(load_library().talp_gpu_destroy(ctx))
+
+
+def talp_gpu_ingest_events(ctx, batches, stream=None):
+    arr = (talp_gpu_trace_batch * len(batches))(*batches)
+    _check(load_library().talp_gpu_ingest_events(ctx, arr, len(batches), _stream(stream)))
+
+
+def talp_gpu_region_metrics(ctx, trace_id, region, stream=None, n_regions=None, check=True):
+    """Metrics of one region (a talp_gpu_metrics) or, with
+    region=TALP_GPU_ALL_REGIONS, a list over the n_regions regions."""
+    k = n_regions if region == TALP_GPU_ALL_REGIONS else 1
+    if k is None:
+        raise ValueError("n_regions is needed with TALP_GPU_ALL_REGIONS")
+    out = (talp_gpu_metrics * k)()
+    st = load_library().talp_gpu_region_metrics(ctx, trace_id, region, out, _stream(stream))
+    res = list(out) if region == TALP_GPU_ALL_REGIONS else out[0]
+    if check:
+        _check(st)
+        return res
+    return st, res
+
+
+def talp_gpu_region_metrics_batch(ctx, trace_ids, region, stream=None, check=True):
+    ids = np.ascontiguousarray(trace_ids, dtype=np.uint64)
+    out = (talp_gpu_metrics * len(ids))()
+    st = load_library().talp_gpu_region_metrics_batch(ctx, ids.ctypes.data_as(ctypes.c_void_p), len(ids), region,
+                                                      out, _stream(stream))
+    if check:
+        _check(st)
+        return list(out)
+    return st, list(out)
+
+
+def talp_gpu_region_metrics_device(ctx, trace_ids, region, out_device_ptr, stream=None):
+    ids = np.ascontiguousarray(trace_ids, dtype=np.uint64)
+    _check(load_library().talp_gpu_region_metrics_device(ctx, ids.ctypes.data_as(ctypes.c_void_p), len(ids),
+                                                         region, ctypes.c_void_p(out_device_ptr), _stream(stream)))
+
+
+def talp_gpu_unit_sums(ctx, trace_id, region, n_ranks, m_devices, stream=None):
+    h = np.zeros((n_ranks, 3), np.int64)
+    d = np.zeros((m_devices, 3), np.int64)
+    _check(load_library().talp_gpu_unit_sums(ctx, trace_id, region, h.ctypes.data_as(ctypes.c_void_p),
+                                             d.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+    return h, d
+
+
+def talp_gpu_reset(ctx, trace_id=TALP_GPU_ALL):
+    _check(load_library().talp_gpu_reset(ctx, trace_id))
+
+
+def talp_gpu_memory(ctx):
+    held, budget = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(load_library().talp_gpu_memory(ctx, ctypes.byref(held), ctypes.byref(budget)))
+    return held.value, budget.value
+
+
+def talp_gpu_profile(ctx, enable=True):
+    _check(load_library().talp_gpu_profile(ctx, 1 if enable else 0))
+
+
+def talp_gpu_profile_read(ctx) -> dict:
+    st = talp_gpu_profile_stats()
+    _check(load_library().talp_gpu_profile_read(ctx, ctypes.byref(st)))
+    return dict(sweep_launches=int(st.sweep_launches), sweep_records=int(st.sweep_records),
+                sweep_ms=float(st.sweep_ms), kernel_launches=int(st.kernel_launches))
+
+
+# ----------------------------------------------------------------- marshalling
+
+
+def _ptr(a):
+    """(address, is_device) of a numpy array or a torch tensor."""
+    if a is None:
+        return None, False
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr(), bool(a.is_cuda)
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("arrays must be C-contiguous")
+    return a.ctypes.data, False
+
+
+def batch_from_arrays(trace_id, devices_per_rank, region_window, host_se, host_state, host_off,
+                      dev_se, dev_tag, dev_off, flags=0):
+    """Build a talp_gpu_trace_batch.  Header arrays (devices_per_rank,
+    region_window, offsets) are host numpy arrays; record arrays are numpy
+    arrays (host) or CUDA tensors (device; TALP_GPU_DEVICE_PTRS is then set).
+    Returns (batch, keepalive): keep `keepalive` referenced until the ingest
+    call's stream has passed it."""
+    dpr = np.ascontiguousarray(devices_per_rank, dtype=np.uint32)
+    win = np.ascontiguousarray(region_window, dtype=np.int64)
+    hoff = np.ascontiguousarray(host_off, dtype=np.uint64)
+    doff = np.ascontiguousarray(dev_off, dtype=np.uint64)
+    keep = [dpr, win, hoff, doff]
+    ptrs = []
+    dev_flags = set()
+    for a, dt in ((host_se, np.int64), (host_state, np.uint8), (dev_se, np.int64), (dev_tag, np.uint8)):
+        if not hasattr(a, "data_ptr"):
+            a = np.ascontiguousarray(a, dtype=dt)
+        keep.append(a)
+        p, is_dev = _ptr(a)
+        ptrs.append(p)
+        dev_flags.add(is_dev)
+    if len(dev_flags) != 1:
+        raise ValueError("record arrays must be all host or all device")
+    if dev_flags.pop():
+        flags |= TALP_GPU_DEVICE_PTRS
+    b = talp_gpu_trace_batch()
+    b.trace_id = int(trace_id)
+    b.n_ranks = int(dpr.shape[0])
+    b.n_regions = int(win.shape[0])
+    b.flags = int(flags)
+    b.reserved = 0
+    b.devices_per_rank = dpr.ctypes.data
+    b.region_window = win.ctypes.data
+    b.host_se, b.host_state, b.dev_se, b.dev_tag = ptrs
+    b.host_off = hoff.ctypes.data
+    b.dev_off = doff.ctypes.data
+    return b, keep
+
+
+class Context:
+    """Owning wrapper of a talp_gpu_ctx."""
+
+    def __init__(self, device=0, hbm_budget_bytes=0):
+        self.ctx = talp_gpu_create(device, hbm_budget_bytes)
+        self._keep = []
+        self._shapes = {}
+
+    def close(self):
+        if self.ctx is not None:
+            talp_gpu_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def ingest(self, traces, flags=0, stream=None, arrays=None):
+        """Ingest trace objects (attributes as produced by tracegen).  With
+        `arrays`, a parallel list of dicts overriding the record arrays (e.g.
+        CUDA tensors) is used."""
+        batches, keep = [], []
+        for k, t in enumerate(traces):
+            rec = dict(host_se=t.host_se, host_state=t.host_state, dev_se=t.dev_se, dev_tag=t.dev_tag)
+            if arrays is not None:
+                rec.update(arrays[k])
+            b, kp = batch_from_arrays(t.trace_id, t.devices_per_rank, t.region_window, rec["host_se"],
+                                      rec["host_state"], t.host_off, rec["dev_se"], rec["dev_tag"], t.dev_off,
+                                      flags)
+            batches.append(b)
+            keep.append(kp)
+            self._shapes[int(t.trace_id)] = (int(t.n_ranks), int(np.asarray(t.devices_per_rank).sum()),
+                                             int(np.asarray(t.region_window).shape[0]))
+        talp_gpu_ingest_events(self.ctx, batches, stream)
+        self._keep = keep
+        return batches
+
+    def metrics(self, trace_id, region=TALP_GPU_ALL_REGIONS, stream=None, check=True):
+        R = self._shapes[int(trace_id)][2]
+        r = talp_gpu_region_metrics(self.ctx, trace_id, region, stream, n_regions=R, check=check)
+        if not check:
+            st, r = r
+            conv = [metrics_to_dict(x) for x in r] if isinstance(r, list) else metrics_to_dict(r)
+            return st, conv
+        return [metrics_to_dict(x) for x in r] if isinstance(r, list) else metrics_to_dict(r)
+
+    def metrics_batch(self, trace_ids, region, stream=None):
+        return [metrics_to_dict(x) for x in talp_gpu_region_metrics_batch(self.ctx, trace_ids, region, stream)]
+
+    def unit_sums(self, trace_id, region, stream=None):
+        n, m, _ = self._shapes[int(trace_id)]
+        return talp_gpu_unit_sums(self.ctx, trace_id, region, n, m, stream)
+
+    def reset(self, trace_id=TALP_GPU_ALL):
+        talp_gpu_reset(self.ctx, trace_id)
+        if trace_id == TALP_GPU_ALL:
+            self._shapes.clear()
+        else:
+            self._shapes.pop(int(trace_id), None)
+
+    def memory(self):
+        return talp_gpu_memory(self.ctx)

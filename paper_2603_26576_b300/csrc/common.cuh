@@ -1,0 +1,184 @@
+// Device-side building blocks shared by the kernels of the reducer:
+// descriptors of the work, PTX wrappers for mbarriers and 1-D bulk TMA,
+// warp scans/reductions of int64 values.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace talp {
+
+constexpr int64_t NEG_INF = INT64_MIN;   // running max end before any record
+constexpr uint32_t NONE = 0xFFFFFFFFu;
+
+// validation / status bits (per segment and per trace)
+constexpr uint32_t ST_BAD_END = 0x1u;      // end < start
+constexpr uint32_t ST_BAD_KIND = 0x2u;     // device kind > 4 or host state > 2
+constexpr uint32_t ST_UNSORTED = 0x4u;     // device starts out of order
+constexpr uint32_t ST_TIMEOUT = 0x8u;      // a bounded device wait ran out
+
+// One unit of independent work: the records of one device (a sweep with
+// three running-max chains) or of one rank's host (plain clipped sums).
+struct SegDesc {
+    const int64_t* se;         // record 0 of the segment: {start, end}
+    const uint8_t* tag;        // tag (device) or state (host) of record 0
+    const uint8_t* tag_limit;  // 16-byte floor of the end of the tag array;
+                               // tag bytes at or past it are read directly
+    int64_t* sums;             // [R][3] accumulators of this unit
+    const int64_t* win;        // [R][2] windows of the owning rank
+    uint32_t* status;          // per-trace status word
+    const int64_t* carry_in;   // device: {max kernel end, max memory end, last start}
+                               // of earlier ingests (read only during the pass)
+    int64_t* carry_out;        // device: the same after this ingest (atomic max)
+    uint64_t n;                // records
+    uint16_t R;                // regions
+    uint8_t is_host;
+    uint8_t pad[5];
+};
+
+// What one warp of the sweep publishes for the fix-up pass.
+struct WarpRec {
+    uint64_t head_pos;   // first virtual record index of the warp's range
+    uint64_t head_end;   // end of its first portion (same segment)
+    uint32_t head_seg;   // segment of head_pos (NONE: the warp had no records)
+    uint32_t tail_seg;   // segment of its last portion
+    int64_t head_K, head_M;  // max kernel / memory end over the first portion
+    int64_t tail_K, tail_M;  // same over the last portion
+};
+
+// Device-resident descriptor of one trace, read by the finalize kernel.
+struct TraceDev {
+    uint64_t trace_id;
+    uint32_t n, m, R;
+    uint32_t pad;
+    const int64_t* hsum;     // [n][R][3]  useful, offload, MPI
+    const int64_t* dsum;     // [m][R][3]  kernel union, memory union, busy union
+    const int64_t* hwin;     // [n][R][2]
+    const int64_t* dev_rank; // [m]
+    const uint32_t* status;  // trace status word
+};
+
+// Metrics record written by the finalize kernel; mirrors talp_gpu_metrics.
+struct MetricsOut {
+    uint64_t trace_id;
+    uint32_t region, flags, n_ranks, m_devices;
+    int64_t elapsed_ns, sum_useful, sum_offload, sum_mpi, max_useful_offload;
+    int64_t sum_kernel, max_kernel, max_busy, sum_mem, sum_idle, sum_hidden_mem;
+    double host_pe, host_mpi_pe, host_mpi_lb, host_mpi_ce, host_oe;
+    double dev_pe, dev_lb, dev_ce, dev_oe;
+};
+
+struct FinalizeJob {
+    const TraceDev* t;
+    MetricsOut* out;
+    uint32_t region;
+    uint32_t pad;
+};
+
+// (ptr, count, value) fill job for the prep kernel
+struct FillJob {
+    int64_t* ptr;
+    uint64_t count;
+    int64_t value;
+    const int64_t* src;   // when non-null: copy count values from src instead
+};
+
+// ---------------------------------------------------------------- helpers
+
+__device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
+__device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: returns false when `limit` clock cycles pass first.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int64_t limit) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const int64_t t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > limit) return false;
+    }
+    return true;
+}
+
+// 1-D bulk copy global -> shared through the TMA unit, completing on `bar`.
+// dst and src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ int64_t shfl_up64(int64_t v, int d) {
+    return static_cast<int64_t>(__shfl_up_sync(0xFFFFFFFFu, static_cast<long long>(v), d));
+}
+__device__ __forceinline__ int64_t shfl64(int64_t v, int src) {
+    return static_cast<int64_t>(__shfl_sync(0xFFFFFFFFu, static_cast<long long>(v), src));
+}
+__device__ __forceinline__ int64_t shfl_xor64(int64_t v, int m) {
+    return static_cast<int64_t>(__shfl_xor_sync(0xFFFFFFFFu, static_cast<long long>(v), m));
+}
+
+__device__ __forceinline__ int64_t warp_sum64(int64_t v) {
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) v += shfl_xor64(v, m);
+    return v;
+}
+__device__ __forceinline__ int64_t warp_max64(int64_t v) {
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) v = max64(v, shfl_xor64(v, m));
+    return v;
+}
+
+// Inclusive max-scan of two values across the warp.
+__device__ __forceinline__ void warp_incl_max2(int64_t& a, int64_t& b, int lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int64_t ta = shfl_up64(a, d);
+        const int64_t tb = shfl_up64(b, d);
+        if (lane >= d) {
+            a = max64(a, ta);
+            b = max64(b, tb);
+        }
+    }
+}
+
+__device__ __forceinline__ void atomic_add64(int64_t* p, int64_t v) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(v));
+}
+__device__ __forceinline__ void atomic_max64(int64_t* p, int64_t v) {
+    atomicMax(reinterpret_cast<long long*>(p), static_cast<long long>(v));
+}
+
+}  // namespace talp

@@ -1,0 +1,37 @@
+// Launchers of the reducer's kernels (host-callable; used by the engine).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace talp {
+
+// Shape of the sweep kernel: records per lane per tile (odd, so that the
+// blocked shared-memory reads are free of bank conflicts), warps per CTA and
+// TMA pipeline stages per warp.
+struct SweepShape {
+    int items;
+    int warps;
+    int stages;
+};
+
+constexpr int kNumSweepShapes = 4;
+extern const SweepShape kSweepShapes[kNumSweepShapes];
+
+// Largest number of co-resident CTAs per SM for a shape, 0 if it cannot run.
+int sweep_ctas_per_sm(int shape, int rmax);
+int sweep_tile(int shape);
+
+cudaError_t launch_sweep(int shape, int rmax, int grid, const SegDesc* segs, const uint64_t* seg_start,
+                         uint32_t n_segs, WarpRec* wrec, uint32_t* seg_flags, uint32_t* gstatus, int64_t wait_limit,
+                         cudaStream_t stream);
+
+cudaError_t launch_fixup(const SegDesc* segs, const uint64_t* seg_start, const WarpRec* wrec, uint32_t n_wrec,
+                         uint32_t* seg_flags, cudaStream_t stream);
+
+cudaError_t launch_prep(const FillJob* jobs, uint32_t n_jobs, cudaStream_t stream);
+
+cudaError_t launch_finalize(const FinalizeJob* jobs, uint32_t n_jobs, cudaStream_t stream);
+
+}  // namespace talp

@@ -1,0 +1,286 @@
+// Fix-up of slice boundaries, state preparation, and the final reduction
+// into the Eq. 1 / Eqs. 6-12 metrics.
+#include "kernels.h"
+
+namespace talp {
+
+// ------------------------------------------------------------------ fix-up
+//
+// A sweep warp whose slice starts inside a device segment ran its three
+// chains from an empty carry.  Its new pieces are then too long exactly by
+// their part below the true carry C (the largest end before the slice), so
+// the fix-up subtracts |piece ∩ (-inf, C) ∩ [a, b)| for each chain and region.
+// Only records starting below C have such a part; with the records in start
+// order they form a prefix of the slice, usually a handful of records.
+// C comes from the running state of earlier ingests and from the portions of
+// the same segment owned by the preceding warps (a warp-parallel walk back).
+// One warp per sweep warp; nothing waits on anything.
+__global__ void __launch_bounds__(256) fixup_kernel(const SegDesc* __restrict__ segs,
+                                                    const uint64_t* __restrict__ seg_start,
+                                                    const WarpRec* __restrict__ wrec, uint32_t n_wrec,
+                                                    uint32_t* __restrict__ seg_flags) {
+    constexpr int RM = 8;
+    const int lane = threadIdx.x & 31;
+    const uint32_t w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (w >= n_wrec) return;
+    const WarpRec rec = wrec[w];
+    if (rec.head_seg == NONE) return;
+    const uint32_t seg = rec.head_seg;
+    const SegDesc d = segs[seg];
+    if (d.is_host) return;
+    const uint64_t sbase = seg_start[seg];
+    if (rec.head_pos <= sbase) return;
+
+    const uint64_t off0 = rec.head_pos - sbase;
+    if (lane == 0 && d.se[2 * off0] < d.se[2 * (off0 - 1)]) {
+        atomicOr(d.status, ST_UNSORTED);
+        atomicOr(&seg_flags[seg], ST_UNSORTED);
+    }
+
+    // carry: running state + tails of the preceding warps inside this segment
+    int64_t CK = d.carry_in[0];
+    int64_t CM = d.carry_in[1];
+    for (int64_t b = static_cast<int64_t>(w) - 1; b >= 0; b -= 32) {
+        const int64_t idx = b - lane;
+        bool stop = true;
+        int64_t tk = NEG_INF, tm = NEG_INF;
+        if (idx >= 0) {
+            const WarpRec p = wrec[idx];
+            if (p.tail_seg == seg) {
+                tk = p.tail_K;
+                tm = p.tail_M;
+            }
+            stop = (p.head_seg != NONE) && !(p.head_seg == seg && p.head_pos > sbase);
+        }
+        const uint32_t sm = __ballot_sync(0xFFFFFFFFu, stop);
+        const int first = sm ? (__ffs(sm) - 1) : 31;
+        if (lane > first) {
+            tk = NEG_INF;
+            tm = NEG_INF;
+        }
+        CK = max64(CK, warp_max64(tk));
+        CM = max64(CM, warp_max64(tm));
+        if (sm) break;
+    }
+    const int64_t CA = max64(CK, CM);
+    if (CA == NEG_INF) return;
+
+    int64_t sub[RM][3];
+#pragma unroll
+    for (int r = 0; r < RM; ++r) sub[r][0] = sub[r][1] = sub[r][2] = 0;
+    int64_t Kl = NEG_INF, Ml = NEG_INF;
+    for (uint64_t p = rec.head_pos; p < rec.head_end; p += 32) {
+        const uint64_t j = p + lane;
+        const bool valid = j < rec.head_end;
+        int64_t s = 0, e = 0;
+        uint32_t kind = 0;
+        if (valid) {
+            const uint64_t o = j - sbase;
+            s = d.se[2 * o];
+            e = d.se[2 * o + 1];
+            kind = d.tag[o] >> 5;
+        }
+        const bool isK = kind == 0u;
+        int64_t iK = (valid && isK) ? e : NEG_INF;
+        int64_t iM = (valid && !isK) ? e : NEG_INF;
+        warp_incl_max2(iK, iM, lane);
+        int64_t xK = shfl_up64(iK, 1), xM = shfl_up64(iM, 1);
+        if (lane == 0) {
+            xK = NEG_INF;
+            xM = NEG_INF;
+        }
+        xK = max64(xK, Kl);
+        xM = max64(xM, Ml);
+        Kl = max64(Kl, shfl64(iK, 31));
+        Ml = max64(Ml, shfl64(iM, 31));
+        if (valid && s < CA) {
+            // a chain's over-count exists only below its own carry; a chain
+            // without carry (NEG_INF) has none (and must not enter the
+            // subtraction, which would overflow)
+            const int64_t CO = isK ? CK : CM;
+            const bool own = s < CO;
+            const int64_t pA = max64(s, max64(xK, xM));
+            const int64_t pO = max64(s, isK ? xK : xM);
+            const int64_t eA = min64(e, CA);
+            const int64_t eO = own ? min64(e, CO) : s;
+#pragma unroll
+            for (int r = 0; r < RM; ++r) {
+                if (r < d.R) {
+                    const int64_t a = d.win[2 * r], b = d.win[2 * r + 1];
+                    sub[r][2] += max64(min64(eA, b) - max64(pA, a), 0);
+                    if (own) sub[r][isK ? 0 : 1] += max64(min64(eO, b) - max64(pO, a), 0);
+                }
+            }
+        }
+        if (__any_sync(0xFFFFFFFFu, valid && s >= CA)) break;
+    }
+#pragma unroll
+    for (int r = 0; r < RM; ++r) {
+        if (r < d.R) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int64_t v = warp_sum64(sub[r][c]);
+                if (lane == 0 && v != 0) atomic_add64(&d.sums[3 * r + c], -v);
+            }
+        }
+    }
+}
+
+cudaError_t launch_fixup(const SegDesc* segs, const uint64_t* seg_start, const WarpRec* wrec, uint32_t n_wrec,
+                         uint32_t* seg_flags, cudaStream_t stream) {
+    if (n_wrec == 0) return cudaSuccess;
+    const int wpb = 8;
+    const int grid = static_cast<int>((n_wrec + wpb - 1) / wpb);
+    fixup_kernel<<<grid, wpb * 32, 0, stream>>>(segs, seg_start, wrec, n_wrec, seg_flags);
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------------------------- prep
+// Zero the sums of freshly ingested traces, reset or copy running state.
+__global__ void __launch_bounds__(256) prep_kernel(const FillJob* __restrict__ jobs, uint32_t n_jobs) {
+    for (uint32_t j = blockIdx.y; j < n_jobs; j += gridDim.y) {
+        const FillJob job = jobs[j];
+        for (uint64_t i = blockIdx.x * 256ull + threadIdx.x; i < job.count; i += 256ull * gridDim.x)
+            job.ptr[i] = job.src ? job.src[i] : job.value;
+    }
+}
+
+cudaError_t launch_prep(const FillJob* jobs, uint32_t n_jobs, cudaStream_t stream) {
+    if (n_jobs == 0) return cudaSuccess;
+    dim3 grid(8, n_jobs < 65535 ? n_jobs : 65535);
+    prep_kernel<<<grid, 256, 0, stream>>>(jobs, n_jobs);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- finalize
+//
+// One CTA per (trace, region): reduce the per-rank host sums and per-device
+// unions into E and the sums/maxima, then form the nine ratios in FP64 with
+// the fixed order num / (k * den) (forms with n or m) or num / den, round to
+// nearest, no contraction: Eqs. 6-8 (host tree) and 9-12 (device tree).
+__device__ __forceinline__ double ratio_k(int64_t num, int64_t k, int64_t den) {
+    if (k == 0 || den == 0) return 1.0;
+    return __ddiv_rn(__ll2double_rn(num), __dmul_rn(__ll2double_rn(k), __ll2double_rn(den)));
+}
+__device__ __forceinline__ double ratio(int64_t num, int64_t den) {
+    if (den == 0) return 1.0;
+    return __ddiv_rn(__ll2double_rn(num), __ll2double_rn(den));
+}
+
+template <typename T, typename Op>
+__device__ __forceinline__ T block_reduce(T v, Op op, T* sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) v = op(v, static_cast<T>(__shfl_xor_sync(0xFFFFFFFFu, v, m)));
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    T r = sh[0];
+    for (int i = 1; i < static_cast<int>(blockDim.x >> 5); ++i) r = op(r, sh[i]);
+    return r;
+}
+
+__global__ void __launch_bounds__(256) finalize_kernel(const FinalizeJob* __restrict__ jobs) {
+    __shared__ long long sh[32];
+    const FinalizeJob job = jobs[blockIdx.x];
+    const TraceDev t = *job.t;
+    const uint32_t r = job.region;
+    const uint32_t R = t.R;
+    auto add = [](long long a, long long b) { return a + b; };
+    auto mx = [](long long a, long long b) { return a > b ? a : b; };
+    auto bor = [](long long a, long long b) { return a | b; };
+
+    long long E = 0, sU = 0, sW = 0, sP = 0, maxUW = 0, not_tiled = 0;
+    for (uint32_t i = threadIdx.x; i < t.n; i += blockDim.x) {
+        const int64_t* h = t.hsum + (static_cast<uint64_t>(i) * R + r) * 3;
+        const int64_t U = h[0], W = h[1], P = h[2];
+        const int64_t* wv = t.hwin + (static_cast<uint64_t>(i) * R + r) * 2;
+        E = mx(E, U + W + P);
+        sU += U;
+        sW += W;
+        sP += P;
+        maxUW = mx(maxUW, U + W);
+        if (U + W + P != wv[1] - wv[0]) not_tiled = 1;
+    }
+    long long sK = 0, maxK = 0, maxB = 0, sM = 0, sIdle = 0, sHid = 0;
+    for (uint32_t g = threadIdx.x; g < t.m; g += blockDim.x) {
+        const int64_t* u = t.dsum + (static_cast<uint64_t>(g) * R + r) * 3;
+        const int64_t K = u[0], UM = u[1], B = u[2];
+        const int64_t DM = B - K;
+        const int64_t* wv = t.hwin + (static_cast<uint64_t>(t.dev_rank[g]) * R + r) * 2;
+        sK += K;
+        maxK = mx(maxK, K);
+        maxB = mx(maxB, K + DM);
+        sM += DM;
+        sIdle += (wv[1] - wv[0]) - B;
+        sHid += K + UM - B;
+    }
+    E = block_reduce<long long>(E, mx, sh);
+    sU = block_reduce<long long>(sU, add, sh);
+    sW = block_reduce<long long>(sW, add, sh);
+    sP = block_reduce<long long>(sP, add, sh);
+    maxUW = block_reduce<long long>(maxUW, mx, sh);
+    not_tiled = block_reduce<long long>(not_tiled, bor, sh);
+    sK = block_reduce<long long>(sK, add, sh);
+    maxK = block_reduce<long long>(maxK, mx, sh);
+    maxB = block_reduce<long long>(maxB, mx, sh);
+    sM = block_reduce<long long>(sM, add, sh);
+    sIdle = block_reduce<long long>(sIdle, add, sh);
+    sHid = block_reduce<long long>(sHid, add, sh);
+    if (threadIdx.x != 0) return;
+
+    MetricsOut o;
+    o.trace_id = t.trace_id;
+    o.region = r;
+    o.n_ranks = t.n;
+    o.m_devices = t.m;
+    uint32_t fl = 0;
+    if (not_tiled) fl |= 0x2u;
+    const uint32_t st = *t.status;
+    if (st & (ST_BAD_END | ST_BAD_KIND)) fl |= 0x100u;
+    if (st & ST_UNSORTED) fl |= 0x200u;
+    if (st & ST_TIMEOUT) fl |= 0x400u;
+    o.elapsed_ns = E;
+    o.sum_useful = sU;
+    o.sum_offload = sW;
+    o.sum_mpi = sP;
+    o.max_useful_offload = maxUW;
+    o.sum_kernel = sK;
+    o.max_kernel = maxK;
+    o.max_busy = maxB;
+    o.sum_mem = sM;
+    o.sum_idle = sIdle;
+    o.sum_hidden_mem = sHid;
+    if (E == 0) {
+        fl |= 0x1u;
+        if (t.m == 0) fl |= 0x4u;
+        o.host_pe = o.host_mpi_pe = o.host_mpi_lb = o.host_mpi_ce = o.host_oe = 1.0;
+        o.dev_pe = o.dev_lb = o.dev_ce = o.dev_oe = 1.0;
+    } else {
+        const int64_t n = t.n, m = t.m;
+        o.host_pe = ratio_k(sU, E, n);          // Eq. 6
+        o.host_mpi_pe = ratio_k(sU + sW, E, n); // Eq. 7
+        o.host_mpi_lb = ratio_k(sU + sW, n, maxUW);
+        o.host_mpi_ce = ratio(maxUW, E);
+        o.host_oe = ratio(sU, sU + sW);         // Eq. 8
+        if (m == 0) {
+            fl |= 0x4u;
+            o.dev_pe = o.dev_lb = o.dev_ce = o.dev_oe = 1.0;
+        } else {
+            o.dev_pe = ratio_k(sK, E, m);       // Eq. 9
+            o.dev_lb = ratio_k(sK, m, maxK);    // Eq. 10
+            o.dev_ce = ratio(maxK, maxB);       // Eq. 11
+            o.dev_oe = ratio(maxB, E);          // Eq. 12
+        }
+    }
+    o.flags = fl;
+    *job.out = o;
+}
+
+cudaError_t launch_finalize(const FinalizeJob* jobs, uint32_t n_jobs, cudaStream_t stream) {
+    if (n_jobs == 0) return cudaSuccess;
+    finalize_kernel<<<n_jobs, 256, 0, stream>>>(jobs);
+    return cudaGetLastError();
+}
+
+}  // namespace talp
