@@ -356,7 +356,7 @@ talp_gpu_status talp_gpu_ingest_events(talp_gpu_ctx* c, const talp_gpu_trace_bat
     size_t payload_words = 0;
     for (size_t k = 0; k < nb; ++k)
         payload_words += 2ull * batches[k].n_ranks * batches[k].n_regions + mm[k] + sizeof(TraceDev) / 8;
-    const size_t n_jobs_max = 8 * nb;
+    const size_t n_jobs_max = 8 * nb + 2;   // <= 8 per trace + seg flags + status
     size_t off_segs = 0;
     size_t off_start = align_up(off_segs + sizeof(SegDesc) * n_segs, 256);
     size_t off_jobs = align_up(off_start + sizeof(uint64_t) * (n_segs + 1), 256);
@@ -550,6 +550,8 @@ talp_gpu_status talp_gpu_ingest_events(talp_gpu_ctx* c, const talp_gpu_trace_bat
     sstart[si] = pos;
     jobs[nj++] = FillJob{reinterpret_cast<int64_t*>(seg_flags), (n_segs + 2) / 2, 0, nullptr};
     jobs[nj++] = FillJob{reinterpret_cast<int64_t*>(gstatus), 1, 0, nullptr};
+    if (nj > n_jobs_max || pw > payload_words || si != n_segs)
+        return fail(TALP_GPU_ECUDA, "internal: upload table overflow");
 
     TALP_CUDA(cudaMemcpyAsync(wsd, up, up_bytes, cudaMemcpyHostToDevice, stream));
     TALP_CUDA(cudaEventRecord(c->ev_up, stream));
