@@ -251,6 +251,37 @@ typedef struct {
 talp_gpu_status talp_gpu_profile(talp_gpu_ctx *ctx, int enable);
 talp_gpu_status talp_gpu_profile_read(talp_gpu_ctx *ctx, talp_gpu_profile_stats *out);
 
+/*
+ * Reduction of one trace with no device allocation at all.  (The paper has
+ * no counterpart: this is a service of the library, not a step of the
+ * method.)
+ *
+ * For callers that must not call cudaMalloc or cudaFree, such as a
+ * monitoring hook running inside the measured application: the application
+ * or its framework's caching allocator owns the device memory (possibly all
+ * of it), and an allocation or free from the hook could fail or synchronise
+ * the device and stall the application's streams.  No context is needed.
+ * The scratch lives in one fixed-size __device__ array of the library
+ * (under 6 MiB, held on every GPU that loads the library until the process
+ * exits); the device used is the calling thread's current device.
+ *
+ * b:        one trace with TALP_GPU_DEVICE_PTRS and TALP_GPU_SORTED_BY_START
+ *           set and TALP_GPU_APPEND clear (records in device memory, each
+ *           device's records in start order); n_ranks + m must not exceed
+ *           TALP_GPU_NOALLOC_MAX_UNITS, n_regions <= 8, else EINVAL.
+ * out_host: n_regions metrics, one per region, in host memory.
+ * The call synchronises `stream`.  The first call on a device looks up the
+ * scratch's device address (make that first call before any stream capture).
+ * Every call shares the one scratch array, which keeps the last call's
+ * contents; each call clears what must start at zero.  Calls that overlap on
+ * the GPU (two streams, or two host threads with different streams) race and
+ * corrupt each other's results.
+ * Errors: EINVAL (limits, flags, invalid or out-of-order records; out_host is
+ * written and its flags say why), ETIMEDOUT, ECUDA.
+ */
+#define TALP_GPU_NOALLOC_MAX_UNITS 8192u
+talp_gpu_status talp_gpu_reduce_noalloc(const talp_gpu_trace_batch *b, talp_gpu_metrics *out_host, void *stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *talp_gpu_last_error(void);
 

@@ -10,5 +10,6 @@ from ._lib import (  # noqa: F401
     TALP_GPU_SORTED_BY_START, TalpGpuError, LIB_PATH, Context, batch_from_arrays, load_library,
     metrics_to_dict, talp_gpu_create, talp_gpu_destroy, talp_gpu_ingest_events, talp_gpu_last_error,
     talp_gpu_memory, talp_gpu_region_metrics, talp_gpu_region_metrics_batch, talp_gpu_region_metrics_device,
-    talp_gpu_reset, talp_gpu_unit_sums, talp_gpu_profile, talp_gpu_profile_read, talp_gpu_metrics, talp_gpu_trace_batch, EXPORTED_SYMBOLS,
+    talp_gpu_reset, talp_gpu_unit_sums, talp_gpu_profile, talp_gpu_profile_read, talp_gpu_reduce_noalloc,
+    TALP_GPU_NOALLOC_MAX_UNITS, talp_gpu_metrics, talp_gpu_trace_batch, EXPORTED_SYMBOLS,
 )

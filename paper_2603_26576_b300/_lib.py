@@ -22,8 +22,10 @@ STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEDOUT
 EXPORTED_SYMBOLS = (
     "talp_gpu_create", "talp_gpu_destroy", "talp_gpu_ingest_events", "talp_gpu_region_metrics",
     "talp_gpu_region_metrics_batch", "talp_gpu_region_metrics_device", "talp_gpu_unit_sums",
-    "talp_gpu_reset", "talp_gpu_memory", "talp_gpu_profile", "talp_gpu_profile_read", "talp_gpu_last_error",
+    "talp_gpu_reset", "talp_gpu_memory", "talp_gpu_profile", "talp_gpu_profile_read", "talp_gpu_reduce_noalloc",
+    "talp_gpu_last_error",
 )
+TALP_GPU_NOALLOC_MAX_UNITS = 8192
 
 
 class TalpGpuError(RuntimeError):
@@ -101,6 +103,7 @@ def load_library():
         "talp_gpu_memory": ([P, ctypes.POINTER(S), ctypes.POINTER(S)], I32),
         "talp_gpu_profile": ([P, I32], I32),
         "talp_gpu_profile_read": ([P, ctypes.POINTER(talp_gpu_profile_stats)], I32),
+        "talp_gpu_reduce_noalloc": ([ctypes.POINTER(talp_gpu_trace_batch), ctypes.POINTER(talp_gpu_metrics), P], I32),
         "talp_gpu_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -202,6 +205,19 @@ def talp_gpu_profile_read(ctx) -> dict:
     _check(load_library().talp_gpu_profile_read(ctx, ctypes.byref(st)))
     return dict(sweep_launches=int(st.sweep_launches), sweep_records=int(st.sweep_records),
                 sweep_ms=float(st.sweep_ms), kernel_launches=int(st.kernel_launches))
+
+
+def talp_gpu_reduce_noalloc(batch, stream=None, check=True):
+    """Metrics of every region of one trace with no device allocation (the
+    records must be device memory in start order).  Returns a list of
+    talp_gpu_metrics, one per region."""
+    out = (talp_gpu_metrics * max(1, batch.n_regions))()
+    st = load_library().talp_gpu_reduce_noalloc(ctypes.byref(batch), out, _stream(stream))
+    res = list(out)[: batch.n_regions]
+    if check:
+        _check(st)
+        return res
+    return st, res
 
 
 # ----------------------------------------------------------------- marshalling

@@ -86,6 +86,8 @@ struct PinBuf {
 
 }  // namespace
 
+void talp::set_last_error(const std::string& msg) { g_last_error = msg; }
+
 struct talp_gpu_ctx {
     int device = 0;
     int num_sms = 0;

@@ -1,6 +1,7 @@
 // Launchers of the reducer's kernels (host-callable; used by the engine).
 #pragma once
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -33,5 +34,8 @@ cudaError_t launch_fixup(const SegDesc* segs, const uint64_t* seg_start, const W
 cudaError_t launch_prep(const FillJob* jobs, uint32_t n_jobs, cudaStream_t stream);
 
 cudaError_t launch_finalize(const FinalizeJob* jobs, uint32_t n_jobs, cudaStream_t stream);
+
+// Message returned by talp_gpu_last_error() on this thread.
+void set_last_error(const std::string& msg);
 
 }  // namespace talp
