@@ -100,7 +100,7 @@ struct talp_gpu_ctx {
     cudaEvent_t ev_up = nullptr;      // upload scratch free again
     cudaEvent_t ev_ws = nullptr;      // workspace/staging free again
     bool ws_used = false;
-    int shape = 0;
+    int shape = kDefaultSweepShape;
     int min_tiles_per_warp = 4;
     // profiling
     bool profiling = false;

@@ -18,6 +18,7 @@ struct SweepShape {
 };
 
 constexpr int kNumSweepShapes = 4;
+constexpr int kDefaultSweepShape = 3;   // fastest on the large single-trace workload
 extern const SweepShape kSweepShapes[kNumSweepShapes];
 
 // Largest number of co-resident CTAs per SM for a shape, 0 if it cannot run.

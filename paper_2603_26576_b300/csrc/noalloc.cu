@@ -218,7 +218,7 @@ extern "C" talp_gpu_status talp_gpu_reduce_noalloc(const talp_gpu_trace_batch* b
     for (uint32_t r = 0; r < R; ++r) fin[r] = FinalizeJob{tdev, mout + r, r, 0};
 
     // sweep grid, capped by the warp records the scratch holds
-    const int shape = 0;
+    const int shape = kDefaultSweepShape;
     const int tile = sweep_tile(shape);
     const int warps = kSweepShapes[shape].warps;
     const int cps = sweep_ctas_per_sm(shape, static_cast<int>(R));

@@ -20,39 +20,46 @@
 // shared-memory buffers filled by 1-D bulk TMA copies (cp.async.bulk) that
 // complete on per-stage mbarriers.  No CTA-wide barrier exists: warps are
 // independent.  Lane l holds records [l*ITEMS, (l+1)*ITEMS) of a tile
-// (blocked), so each lane scans its records serially and the warp combines
-// lane aggregates with one shuffle max-scan per tile.
+// (blocked, ITEMS odd so the 16-byte shared loads are conflict free), scans
+// them serially, and the warp combines lane aggregates with one shuffle
+// max-scan per tile.
+//
+// Arithmetic: a tile is rebased on its first start s0.  When every start and
+// end of the tile, and the carries entering it, lie within 2^32 ns of s0
+// (any tile whose span is below 4.29 s), the whole tile runs in 32-bit
+// unsigned offsets, where max, min and subtraction are single instructions
+// and offset 0 stands for "no earlier record".  Otherwise the warp takes the
+// exact int64 path.  Both give identical integers.
+//
+// Regions: the three chain sums of a tile are reduced over the warp once;
+// lanes 0 .. 3R-1 each own the accumulator of one (region, chain) and add
+// the tile total when the tile's span [s0, max end] lies inside their
+// region's window.  Tiles straddling a window boundary recompute their
+// pieces clipped to that window.
 //
 // A warp whose slice starts inside a device segment does not know the
-// running max end of the records before its slice; it starts that chain
+// running max end of the records before its slice; it starts its chains
 // empty and the fix-up kernel later subtracts the over-count (the part of the
-// slice's new pieces that lies below the true carry), which only touches the
-// few records whose start lies below the carry.  No warp ever waits on
-// another.
-//
-// Each lane classifies its records of a tile against each region window by
-// their span [first start, max end]: fully inside adds the unclipped piece
-// sums, fully outside adds nothing, and only a straddling lane recomputes its
-// pieces clipped.
+// slice's new pieces below the true carry), which only touches the records
+// whose start lies below the carry.  No warp ever waits on another.
 #include "kernels.h"
 
 namespace talp {
 
 const SweepShape kSweepShapes[kNumSweepShapes] = {
-    {7, 8, 4},   // 224-record tiles, 8 warps, 4 stages
-    {9, 8, 3},   // 288-record tiles, 8 warps, 3 stages
-    {7, 4, 6},   // 224-record tiles, 4 warps, 6 stages
-    {5, 8, 4},   // 160-record tiles, 8 warps, 4 stages
+    {9, 8, 2},   // 288-record tiles, 8 warps, 2 stages, 2 CTAs/SM
+    {7, 8, 3},   // 224-record tiles, 8 warps, 3 stages, 2 CTAs/SM
+    {11, 8, 2},  // 352-record tiles, 8 warps, 2 stages, 2 CTAs/SM
+    {13, 8, 2},  // 416-record tiles, 8 warps, 2 stages, 2 CTAs/SM
 };
 
-template <int ITEMS, int WARPS, int STAGES, int RMAX>
+template <int ITEMS, int WARPS, int STAGES>
 struct SweepCfg {
     static constexpr int TILE = 32 * ITEMS;
     static constexpr int SE_BYTES = TILE * 16;
     static constexpr int TAG_BYTES = TILE + 32;                 // 16-byte aligned superset of a tile's tags
     static constexpr int STAGE_BYTES = SE_BYTES + TAG_BYTES;    // multiple of 16
-    static constexpr int WIN_BYTES = RMAX * 16;
-    static constexpr int RAW = STAGES * STAGE_BYTES + STAGES * 8 + WIN_BYTES;
+    static constexpr int RAW = STAGES * STAGE_BYTES + STAGES * 8;
     static constexpr int WARP_BYTES = (RAW + 127) / 128 * 128;
     static constexpr int SMEM = WARPS * WARP_BYTES;
 };
@@ -83,19 +90,135 @@ __device__ __forceinline__ bool walk_advance(Walk& w, uint32_t len, const uint64
     return false;
 }
 
-template <int ITEMS, int WARPS, int STAGES, int RMAX>
-__global__ void __launch_bounds__(WARPS * 32)
+__device__ __forceinline__ uint32_t umax(uint32_t a, uint32_t b) { return a > b ? a : b; }
+__device__ __forceinline__ uint32_t umin(uint32_t a, uint32_t b) { return a < b ? a : b; }
+
+// Warp sum of per-lane values below 2^51 with two hardware 32-bit reductions.
+__device__ __forceinline__ int64_t warp_sum_u64_small(uint64_t v) {
+    const uint32_t lo = __reduce_add_sync(0xFFFFFFFFu, static_cast<uint32_t>(v & 0xFFFFFull));
+    const uint32_t hi = __reduce_add_sync(0xFFFFFFFFu, static_cast<uint32_t>(v >> 20));
+    return static_cast<int64_t>((static_cast<uint64_t>(hi) << 20) + lo);
+}
+
+// a window bound relative to s0, saturated to [0, 2^32 - 1]
+__device__ __forceinline__ uint32_t rel_sat(int64_t x, int64_t s0) {
+    if (x <= s0) return 0u;
+    const uint64_t d = static_cast<uint64_t>(x - s0);
+    return d > 0xFFFFFFFFull ? 0xFFFFFFFFu : static_cast<uint32_t>(d);
+}
+
+// Validation and lane aggregates of a device tile (32-bit offsets): all ends
+// >= starts, kinds <= 4 (tag < 160), starts non-decreasing; largest kernel
+// and memory end of the lane (0 = none).  A tag below 32 is a kernel.
+template <int ITEMS, bool FULL>
+__device__ __forceinline__ void dev_pass1(const uint32_t (&sr)[ITEMS], const uint32_t (&er)[ITEMS],
+                                          const uint32_t (&tg)[ITEMS], int cnt, uint32_t& aK, uint32_t& aM,
+                                          bool& okE, bool& okS, bool& okK) {
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        if (FULL || i < cnt) {
+            const uint32_t t = tg[i];
+            okE = okE & (er[i] >= sr[i]);
+            okK = okK & (t < 160u);
+            if (i > 0) okS = okS & (sr[i] >= sr[i - 1]);
+            const bool isK = t < 32u;
+            aK = isK ? umax(aK, er[i]) : aK;
+            aM = isK ? aM : umax(aM, er[i]);
+        }
+    }
+}
+
+// New pieces of one lane's records (32-bit offsets), clipped to [a, b)
+// (a = 0, b = 2^32 - 1: unclipped).  Kp/Mp: largest kernel / memory end
+// before the lane's first record.  sK, sM, sA must enter as 0.
+template <int ITEMS, bool FULL>
+__device__ __forceinline__ void pieces32(const uint32_t (&sr)[ITEMS], const uint32_t (&er)[ITEMS],
+                                         const uint32_t (&tg)[ITEMS], int cnt, uint32_t Kp, uint32_t Mp,
+                                         uint32_t a, uint32_t b, uint32_t& sK, uint32_t& sM, uint32_t& sA) {
+    uint32_t Ap = umax(Kp, Mp), sO = 0;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        if (FULL || i < cnt) {
+            const bool isK = tg[i] < 32u;
+            const uint32_t own = isK ? Kp : Mp;
+            const uint32_t pA = umax(umax(sr[i], Ap), a);
+            const uint32_t pO = umax(umax(sr[i], own), a);
+            const uint32_t e = umin(er[i], b);
+            sA += umax(e, pA) - pA;
+            const uint32_t lO = umax(e, pO) - pO;
+            sO += lO;
+            sK += isK ? lO : 0u;
+            const uint32_t nw = umax(own, er[i]);
+            Kp = isK ? nw : Kp;
+            Mp = isK ? Mp : nw;
+            Ap = umax(Ap, er[i]);
+        }
+    }
+    sM += sO - sK;
+}
+
+// Host tile (32-bit offsets): per-state sums of lengths clipped to [a, b),
+// the lane's smallest start and largest end, and validation.
+template <int ITEMS, bool FULL>
+__device__ __forceinline__ void host_pass(const uint32_t (&sr)[ITEMS], const uint32_t (&er)[ITEMS],
+                                          const uint32_t (&tg)[ITEMS], int cnt, uint32_t a, uint32_t b,
+                                          uint64_t& h0, uint64_t& h1, uint64_t& h2, uint32_t& lo, uint32_t& hi,
+                                          bool& okE, bool& okK) {
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        if (FULL || i < cnt) {
+            const uint32_t q = tg[i];
+            okE = okE & (er[i] >= sr[i]);
+            okK = okK & (q < 3u);
+            const uint32_t p = umax(sr[i], a);
+            const uint64_t l = umax(umin(er[i], b), p) - p;
+            h0 += q == 0u ? l : 0ull;
+            h1 += q == 1u ? l : 0ull;
+            h2 += q == 2u ? l : 0ull;
+            lo = umin(lo, sr[i]);
+            hi = umax(hi, er[i]);
+        }
+    }
+}
+
+// Same in absolute int64 from the shared-memory tile (the exact path).
+template <int ITEMS>
+__device__ __forceinline__ void pieces64(const longlong2* sse, int base, const uint32_t (&tg)[ITEMS], int cnt,
+                                         int64_t Kp, int64_t Mp, int64_t a, int64_t b, int64_t& sK, int64_t& sM,
+                                         int64_t& sA) {
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        if (i < cnt) {
+            const longlong2 v = sse[base + i];
+            const bool isK = (tg[i] >> 5) == 0u;
+            const int64_t pA = max64(max64(v.x, max64(Kp, Mp)), a);
+            const int64_t pO = max64(max64(v.x, isK ? Kp : Mp), a);
+            const int64_t e = min64(v.y, b);
+            sA += max64(e - pA, 0);
+            const int64_t lO = max64(e - pO, 0);
+            if (isK) {
+                sK += lO;
+                Kp = max64(Kp, v.y);
+            } else {
+                sM += lO;
+                Mp = max64(Mp, v.y);
+            }
+        }
+    }
+}
+
+template <int ITEMS, int WARPS, int STAGES, int RMAX, int MINB>
+__global__ void __launch_bounds__(WARPS * 32, MINB)
     sweep_kernel(const SegDesc* __restrict__ segs, const uint64_t* __restrict__ seg_start, uint32_t n_segs,
                  WarpRec* __restrict__ wrec, uint32_t* __restrict__ seg_flags, uint32_t* __restrict__ gstatus,
                  int64_t wait_limit) {
-    using C = SweepCfg<ITEMS, WARPS, STAGES, RMAX>;
+    using C = SweepCfg<ITEMS, WARPS, STAGES>;
     constexpr int TILE = C::TILE;
     extern __shared__ __align__(128) uint8_t smem[];
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     uint8_t* wsm = smem + wid * C::WARP_BYTES;
     uint64_t* bars = reinterpret_cast<uint64_t*>(wsm + STAGES * C::STAGE_BYTES);
-    int64_t* swin = reinterpret_cast<int64_t*>(wsm + STAGES * C::STAGE_BYTES + STAGES * 8);
 
     const uint64_t GW = static_cast<uint64_t>(gridDim.x) * WARPS;
     const uint64_t gw = static_cast<uint64_t>(blockIdx.x) * WARPS + wid;
@@ -137,21 +260,30 @@ __global__ void __launch_bounds__(WARPS * 32)
     walk_enter(iw, seg_start, r1);
     uint32_t n_issued = 0;
     bool iw_done = false;
+    uint32_t iw_cached = NONE;
+    const int64_t* iw_se = nullptr;
+    const uint8_t* iw_tag = nullptr;
+    uintptr_t iw_lim = 0;
 
     auto issue = [&](int st) {
-        const SegDesc& d = segs[iw.seg];
+        if (iw_cached != iw.seg) {
+            const SegDesc& d = segs[iw.seg];
+            iw_se = d.se;
+            iw_tag = d.tag;
+            iw_lim = reinterpret_cast<uintptr_t>(d.tag_limit);
+            iw_cached = iw.seg;
+        }
         const uint64_t off = iw.pos - iw.seg_base;
         const uint64_t rem = iw.seg_end - iw.pos;
         const uint32_t len = rem < static_cast<uint64_t>(TILE) ? static_cast<uint32_t>(rem) : TILE;
         uint8_t* stage = wsm + st * C::STAGE_BYTES;
-        const uintptr_t A = reinterpret_cast<uintptr_t>(d.tag + off);
+        const uintptr_t A = reinterpret_cast<uintptr_t>(iw_tag + off);
         const uintptr_t tlo = A & ~static_cast<uintptr_t>(15);
         uintptr_t thi = (A + len + 15) & ~static_cast<uintptr_t>(15);
-        const uintptr_t lim = reinterpret_cast<uintptr_t>(d.tag_limit);
-        if (thi > lim) thi = lim;
+        if (thi > iw_lim) thi = iw_lim;
         const uint32_t tag_bytes = thi > tlo ? static_cast<uint32_t>(thi - tlo) : 0u;
         mbar_arrive_expect_tx(&bars[st], len * 16u + tag_bytes);
-        tma_load_1d(stage, d.se + 2 * off, len * 16u, &bars[st]);
+        tma_load_1d(stage, iw_se + 2 * off, len * 16u, &bars[st]);
         if (tag_bytes) tma_load_1d(stage + C::SE_BYTES, reinterpret_cast<const void*>(tlo), tag_bytes, &bars[st]);
         ++n_issued;
         if (iw.pos + len >= r1) {
@@ -170,39 +302,61 @@ __global__ void __launch_bounds__(WARPS * 32)
     cw.pos = r0;
     cw.seg = lo;
     walk_enter(cw, seg_start, r1);
-
-    WarpRec rec;
-    rec.head_pos = r0;
-    rec.head_seg = cw.seg;
-    rec.head_end = cw.seg_end;
-    rec.head_K = rec.head_M = NEG_INF;
-    rec.tail_seg = NONE;
-    rec.tail_K = rec.tail_M = NEG_INF;
+    if (lane == 0) {
+        wrec[gw].head_pos = r0;
+        wrec[gw].head_seg = cw.seg;
+        wrec[gw].head_end = cw.seg_end;
+    }
     bool first_portion = true;
 
-    int64_t acc[RMAX][3];
+    // per portion
+    const uint8_t* d_tag = nullptr;
+    uintptr_t d_lim = 0;
+    int64_t* d_sums = nullptr;
+    uint32_t* d_status = nullptr;
+    int64_t* d_cout = nullptr;
+    int d_R = 0;
+    bool d_host = false;
+    int64_t wa = 0, wb = 0;   // lane j < 3R: window of region j / 3
+    int64_t acc = 0;          // lane j < 3R: sum of chain j % 3 in region j / 3
     int64_t carryK = NEG_INF, carryM = NEG_INF, last_s = NEG_INF;
     uint32_t pbad = 0;
-    SegDesc d;
     bool portion_open = false;
     uint32_t n_consumed = 0;
     bool timed_out = false;
+    const int lchain = lane % 3;
+
+    auto release = [&](int st) {
+        __syncwarp();
+        if (lane == 0) {
+            fence_proxy_async_smem();
+            if (!iw_done) issue(st);
+        }
+    };
 
     while (true) {
         if (!portion_open) {
-            d = segs[cw.seg];
-#pragma unroll
-            for (int r = 0; r < RMAX; ++r) acc[r][0] = acc[r][1] = acc[r][2] = 0;
+            const SegDesc& d = segs[cw.seg];
+            d_tag = d.tag;
+            d_lim = reinterpret_cast<uintptr_t>(d.tag_limit);
+            d_sums = d.sums;
+            d_status = d.status;
+            d_cout = d.carry_out;
+            d_R = d.R;
+            d_host = d.is_host != 0;
+            if (lane < 3 * d_R) {
+                wa = d.win[2 * (lane / 3)];
+                wb = d.win[2 * (lane / 3) + 1];
+            }
+            acc = 0;
             pbad = 0;
-            if (!d.is_host && cw.pos == cw.seg_base) {
+            if (!d_host && cw.pos == cw.seg_base) {
                 carryK = d.carry_in[0];
                 carryM = d.carry_in[1];
                 last_s = d.carry_in[2];
             } else {
                 carryK = carryM = last_s = NEG_INF;
             }
-            if (lane < 2 * RMAX && lane < 2 * d.R) swin[lane] = d.win[lane];
-            __syncwarp();
             portion_open = true;
         }
         const int st = static_cast<int>(n_consumed % STAGES);
@@ -212,181 +366,227 @@ __global__ void __launch_bounds__(WARPS * 32)
             timed_out = true;
             break;
         }
-        const uint8_t* stage = wsm + st * C::STAGE_BYTES;
+        uint8_t* stage = wsm + st * C::STAGE_BYTES;
         const longlong2* sse = reinterpret_cast<const longlong2*>(stage);
         const uint64_t off = cw.pos - cw.seg_base;
         const uint64_t rem = cw.seg_end - cw.pos;
         const int len = rem < static_cast<uint64_t>(TILE) ? static_cast<int>(rem) : TILE;
-        const uintptr_t A = reinterpret_cast<uintptr_t>(d.tag + off);
-        const int toff = static_cast<int>(A & 15u);
-        const uintptr_t lim = reinterpret_cast<uintptr_t>(d.tag_limit);
-        const int direct_from = lim > A ? static_cast<int>(min(static_cast<uint64_t>(lim - A), static_cast<uint64_t>(len))) : 0;
-        const uint8_t* stag = stage + C::SE_BYTES + toff;
-        const uint8_t* gtag = d.tag + off;
+        const uintptr_t A = reinterpret_cast<uintptr_t>(d_tag + off);
+        uint8_t* stag = stage + C::SE_BYTES + static_cast<int>(A & 15u);
+        const int direct_from =
+            d_lim > A ? static_cast<int>(min(static_cast<uint64_t>(d_lim - A), static_cast<uint64_t>(len))) : 0;
+        if (direct_from < len) {
+            // the last bytes of the tag array lie past the last 16-byte
+            // boundary the bulk copy may touch: fetch them directly
+            for (int k = direct_from + lane; k < len; k += 32) stag[k] = d_tag[off + k];
+            __syncwarp();
+        }
 
         const int base = lane * ITEMS;
         const int cnt = max(0, min(ITEMS, len - base));
-        int64_t s_[ITEMS], e_[ITEMS];
-        uint32_t t_[ITEMS];
+        const int64_t s0 = sse[0].x;
+        const int64_t tile_last_s = sse[len - 1].x;
+        uint32_t sr[ITEMS], er[ITEMS], tg[ITEMS];
+        uint32_t hib = 0;
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             if (i < cnt) {
                 const longlong2 v = sse[base + i];
-                s_[i] = v.x;
-                e_[i] = v.y;
-                const int k = base + i;
-                t_[i] = k < direct_from ? stag[k] : __ldg(gtag + k);
+                const int64_t ds = v.x - s0, de = v.y - s0;
+                sr[i] = static_cast<uint32_t>(ds);
+                er[i] = static_cast<uint32_t>(de);
+                hib |= static_cast<uint32_t>(ds >> 32) | static_cast<uint32_t>(de >> 32);
+                tg[i] = stag[base + i];
             } else {
-                s_[i] = 0;
-                e_[i] = 0;
-                t_[i] = 0;
+                sr[i] = er[i] = tg[i] = 0;
             }
         }
-        const int64_t prev_s = (cnt > 0) ? (lane == 0 ? last_s : sse[base - 1].x) : 0;
-        const int64_t tile_last_s = sse[len - 1].x;
-        __syncwarp();
-        if (lane == 0) {
-            fence_proxy_async_smem();
-            if (!iw_done) issue(st);
-        }
-        ++n_consumed;
-
         uint32_t bad = 0;
-        if (!d.is_host) {
-            // pass 1: validation and lane aggregates of the kernel / memory ends
-            int64_t aK = NEG_INF, aM = NEG_INF;
-            int64_t ps = prev_s;
+        if (!d_host && cnt > 0) {
+            const int64_t prev = lane == 0 ? last_s : sse[base - 1].x;
+            bad |= (sse[base].x < prev) ? ST_UNSORTED : 0u;
+        }
+        const bool carry_ok = (carryK <= s0 || ((carryK - s0) >> 32) == 0) &&
+                              (carryM <= s0 || ((carryM - s0) >> 32) == 0);
+        const bool fast = __all_sync(0xFFFFFFFFu, hib == 0) && carry_ok;
+        if (fast) release(st);
+
+        // tile totals of the three sums (warp-uniform) and the tile span
+        int64_t tot0 = 0, tot1 = 0, tot2 = 0;
+        int64_t span_lo = s0, span_hi = s0;
+        if (fast) {
+            uint32_t s1 = 0, s2 = 0, s3 = 0;   // device: K, M, all chain sums of the lane
+            uint32_t lo32 = 0, hi32 = 0;
+            uint64_t h0 = 0, h1 = 0, h2 = 0;   // host: U, W, MPI sums of the lane
+            uint32_t xK = 0, xM = 0;
+            const bool full = len == TILE;     // warp-uniform: no per-record guards
+            if (!d_host) {
+                const uint32_t cK = carryK <= s0 ? 0u : static_cast<uint32_t>(carryK - s0);
+                const uint32_t cM = carryM <= s0 ? 0u : static_cast<uint32_t>(carryM - s0);
+                uint32_t aK = 0, aM = 0;
+                bool okE = true, okS = true, okK = true;
+                if (full) dev_pass1<ITEMS, true>(sr, er, tg, cnt, aK, aM, okE, okS, okK);
+                else dev_pass1<ITEMS, false>(sr, er, tg, cnt, aK, aM, okE, okS, okK);
+                bad |= (okE ? 0u : ST_BAD_END) | (okK ? 0u : ST_BAD_KIND) | (okS ? 0u : ST_UNSORTED);
+                uint32_t iK = aK, iM = aM;
 #pragma unroll
-            for (int i = 0; i < ITEMS; ++i) {
-                if (i < cnt) {
-                    const uint32_t kind = t_[i] >> 5;
-                    bad |= (e_[i] < s_[i]) ? ST_BAD_END : 0u;
-                    bad |= (kind > 4u) ? ST_BAD_KIND : 0u;
-                    bad |= (s_[i] < ps) ? ST_UNSORTED : 0u;
-                    ps = s_[i];
-                    if (kind == 0u) aK = max64(aK, e_[i]); else aM = max64(aM, e_[i]);
+                for (int dd = 1; dd < 32; dd <<= 1) {
+                    const uint32_t tk = __shfl_up_sync(0xFFFFFFFFu, iK, dd);
+                    const uint32_t tm = __shfl_up_sync(0xFFFFFFFFu, iM, dd);
+                    if (lane >= dd) {
+                        iK = umax(iK, tk);
+                        iM = umax(iM, tm);
+                    }
+                }
+                xK = __shfl_up_sync(0xFFFFFFFFu, iK, 1);
+                xM = __shfl_up_sync(0xFFFFFFFFu, iM, 1);
+                if (lane == 0) xK = xM = 0u;
+                xK = umax(xK, cK);
+                xM = umax(xM, cM);
+                const uint32_t tK = __shfl_sync(0xFFFFFFFFu, iK, 31);
+                const uint32_t tM = __shfl_sync(0xFFFFFFFFu, iM, 31);
+                if (tK) carryK = max64(carryK, s0 + tK);
+                if (tM) carryM = max64(carryM, s0 + tM);
+                hi32 = umax(tK, tM);
+                if (full) pieces32<ITEMS, true>(sr, er, tg, cnt, xK, xM, 0u, 0xFFFFFFFFu, s1, s2, s3);
+                else pieces32<ITEMS, false>(sr, er, tg, cnt, xK, xM, 0u, 0xFFFFFFFFu, s1, s2, s3);
+                tot0 = __reduce_add_sync(0xFFFFFFFFu, s1);
+                tot1 = __reduce_add_sync(0xFFFFFFFFu, s2);
+                tot2 = __reduce_add_sync(0xFFFFFFFFu, s3);
+            } else {
+                lo32 = 0xFFFFFFFFu;
+                bool okE = true, okK = true;
+                if (full) host_pass<ITEMS, true>(sr, er, tg, cnt, 0u, 0xFFFFFFFFu, h0, h1, h2, lo32, hi32, okE, okK);
+                else host_pass<ITEMS, false>(sr, er, tg, cnt, 0u, 0xFFFFFFFFu, h0, h1, h2, lo32, hi32, okE, okK);
+                bad |= (okE ? 0u : ST_BAD_END) | (okK ? 0u : ST_BAD_KIND);
+                tot0 = warp_sum_u64_small(h0);
+                tot1 = warp_sum_u64_small(h1);
+                tot2 = warp_sum_u64_small(h2);
+                lo32 = __reduce_min_sync(0xFFFFFFFFu, lo32);
+                hi32 = __reduce_max_sync(0xFFFFFFFFu, hi32);
+                span_lo = s0 + lo32;
+            }
+            span_hi = s0 + hi32;
+            // classification of the tile span against the lane's region
+            const bool mine = lane < 3 * d_R;
+            const bool inside = mine && wa <= span_lo && span_hi <= wb;
+            const bool outside = mine && (span_hi <= wa || span_lo >= wb);
+            if (inside) acc += lchain == 0 ? tot0 : (lchain == 1 ? tot1 : tot2);
+            uint32_t sb = __ballot_sync(0xFFFFFFFFu, mine && lchain == 0 && !inside && !outside);
+            while (sb) {
+                const int src = __ffs(sb) - 1;
+                sb &= sb - 1;
+                const int64_t a64 = shfl64(wa, src), b64 = shfl64(wb, src);
+                const uint32_t a = rel_sat(a64, s0), b = rel_sat(b64, s0);
+                int64_t c0, c1, c2;
+                if (!d_host) {
+                    uint32_t k1 = 0, k2 = 0, k3 = 0;
+                    pieces32<ITEMS, false>(sr, er, tg, cnt, xK, xM, a, b, k1, k2, k3);
+                    c0 = __reduce_add_sync(0xFFFFFFFFu, k1);
+                    c1 = __reduce_add_sync(0xFFFFFFFFu, k2);
+                    c2 = __reduce_add_sync(0xFFFFFFFFu, k3);
+                } else {
+                    uint64_t g0 = 0, g1 = 0, g2 = 0;
+                    uint32_t l2 = 0, h2x = 0;
+                    bool e2 = true, k2x = true;
+                    host_pass<ITEMS, false>(sr, er, tg, cnt, a, b, g0, g1, g2, l2, h2x, e2, k2x);
+                    c0 = warp_sum_u64_small(g0);
+                    c1 = warp_sum_u64_small(g1);
+                    c2 = warp_sum_u64_small(g2);
+                }
+                if (lane / 3 == src / 3 && mine) acc += lchain == 0 ? c0 : (lchain == 1 ? c1 : c2);
+            }
+        } else {
+            // exact int64 path (a tile spanning 2^32 ns or more)
+            int64_t k0 = 0, k1 = 0, k2 = 0;
+            int64_t xK = NEG_INF, xM = NEG_INF;
+            int64_t lo64 = INT64_MAX, hi64 = NEG_INF;
+            if (!d_host) {
+                int64_t aK = NEG_INF, aM = NEG_INF;
+#pragma unroll
+                for (int i = 0; i < ITEMS; ++i) {
+                    if (i < cnt) {
+                        const longlong2 v = sse[base + i];
+                        const uint32_t kind = tg[i] >> 5;
+                        bad |= (v.y < v.x) ? ST_BAD_END : 0u;
+                        bad |= (kind > 4u) ? ST_BAD_KIND : 0u;
+                        if (i > 0) bad |= (v.x < sse[base + i - 1].x) ? ST_UNSORTED : 0u;
+                        if (kind == 0u) aK = max64(aK, v.y); else aM = max64(aM, v.y);
+                    }
+                }
+                int64_t iK = aK, iM = aM;
+                warp_incl_max2(iK, iM, lane);
+                xK = shfl_up64(iK, 1);
+                xM = shfl_up64(iM, 1);
+                if (lane == 0) xK = xM = NEG_INF;
+                xK = max64(xK, carryK);
+                xM = max64(xM, carryM);
+                const int64_t tK = shfl64(iK, 31), tM = shfl64(iM, 31);
+                carryK = max64(carryK, tK);
+                carryM = max64(carryM, tM);
+                lo64 = s0;
+                hi64 = max64(tK, tM);
+                pieces64<ITEMS>(sse, base, tg, cnt, xK, xM, NEG_INF, INT64_MAX, k0, k1, k2);
+            } else {
+#pragma unroll
+                for (int i = 0; i < ITEMS; ++i) {
+                    if (i < cnt) {
+                        const longlong2 v = sse[base + i];
+                        const uint32_t q = tg[i];
+                        bad |= (v.y < v.x) ? ST_BAD_END : 0u;
+                        bad |= (q > 2u) ? ST_BAD_KIND : 0u;
+                        const int64_t l = max64(v.y - v.x, 0);
+                        k0 += q == 0u ? l : 0;
+                        k1 += q == 1u ? l : 0;
+                        k2 += q == 2u ? l : 0;
+                        lo64 = min64(lo64, v.x);
+                        hi64 = max64(hi64, v.y);
+                    }
+                }
+#pragma unroll
+                for (int m = 16; m > 0; m >>= 1) {
+                    lo64 = min64(lo64, shfl_xor64(lo64, m));
+                    hi64 = max64(hi64, shfl_xor64(hi64, m));
                 }
             }
-            // warp exclusive max-scan of the lane aggregates, seeded by the carry
-            int64_t iK = aK, iM = aM;
-            warp_incl_max2(iK, iM, lane);
-            int64_t xK = shfl_up64(iK, 1), xM = shfl_up64(iM, 1);
-            if (lane == 0) {
-                xK = NEG_INF;
-                xM = NEG_INF;
-            }
-            xK = max64(xK, carryK);
-            xM = max64(xM, carryM);
-            carryK = max64(carryK, shfl64(iK, 31));
-            carryM = max64(carryM, shfl64(iM, 31));
-
-            if (cnt > 0) {
-                // pass 2: unclipped new pieces of the three chains
-                int64_t sK = 0, sM = 0, sA = 0;
-                {
-                    int64_t Kp = xK, Mp = xM;
+            tot0 = warp_sum64(k0);
+            tot1 = warp_sum64(k1);
+            tot2 = warp_sum64(k2);
+            span_lo = lo64;
+            span_hi = hi64;
+            const bool mine = lane < 3 * d_R;
+            const bool inside = mine && wa <= span_lo && span_hi <= wb;
+            const bool outside = mine && (span_hi <= wa || span_lo >= wb);
+            if (inside) acc += lchain == 0 ? tot0 : (lchain == 1 ? tot1 : tot2);
+            uint32_t sb = __ballot_sync(0xFFFFFFFFu, mine && lchain == 0 && !inside && !outside);
+            while (sb) {
+                const int src = __ffs(sb) - 1;
+                sb &= sb - 1;
+                const int64_t a = shfl64(wa, src), b = shfl64(wb, src);
+                int64_t c0 = 0, c1 = 0, c2 = 0;
+                if (!d_host) {
+                    pieces64<ITEMS>(sse, base, tg, cnt, xK, xM, a, b, c0, c1, c2);
+                } else {
 #pragma unroll
                     for (int i = 0; i < ITEMS; ++i) {
                         if (i < cnt) {
-                            const bool isK = (t_[i] >> 5) == 0u;
-                            const int64_t pA = max64(s_[i], max64(Kp, Mp));
-                            const int64_t pO = max64(s_[i], isK ? Kp : Mp);
-                            sA += max64(e_[i] - pA, 0);
-                            const int64_t lO = max64(e_[i] - pO, 0);
-                            if (isK) {
-                                sK += lO;
-                                Kp = max64(Kp, e_[i]);
-                            } else {
-                                sM += lO;
-                                Mp = max64(Mp, e_[i]);
-                            }
+                            const longlong2 v = sse[base + i];
+                            const uint32_t q = tg[i];
+                            const int64_t l = max64(min64(v.y, b) - max64(v.x, a), 0);
+                            c0 += q == 0u ? l : 0;
+                            c1 += q == 1u ? l : 0;
+                            c2 += q == 2u ? l : 0;
                         }
                     }
                 }
-                const int64_t lo_t = s_[0];
-                const int64_t hi_t = max64(aK, aM);
-#pragma unroll
-                for (int r = 0; r < RMAX; ++r) {
-                    if (r < d.R) {
-                        const int64_t a = swin[2 * r], b = swin[2 * r + 1];
-                        if (lo_t >= a && hi_t <= b) {
-                            acc[r][0] += sK;
-                            acc[r][1] += sM;
-                            acc[r][2] += sA;
-                        } else if (!(hi_t <= a || lo_t >= b)) {
-                            int64_t Kp = xK, Mp = xM, cK = 0, cM = 0, cA = 0;
-#pragma unroll
-                            for (int i = 0; i < ITEMS; ++i) {
-                                if (i < cnt) {
-                                    const bool isK = (t_[i] >> 5) == 0u;
-                                    const int64_t pA = max64(s_[i], max64(Kp, Mp));
-                                    const int64_t pO = max64(s_[i], isK ? Kp : Mp);
-                                    const int64_t eb = min64(e_[i], b);
-                                    cA += max64(eb - max64(pA, a), 0);
-                                    const int64_t lO = max64(eb - max64(pO, a), 0);
-                                    if (isK) {
-                                        cK += lO;
-                                        Kp = max64(Kp, e_[i]);
-                                    } else {
-                                        cM += lO;
-                                        Mp = max64(Mp, e_[i]);
-                                    }
-                                }
-                            }
-                            acc[r][0] += cK;
-                            acc[r][1] += cM;
-                            acc[r][2] += cA;
-                        }
-                    }
-                }
+                c0 = warp_sum64(c0);
+                c1 = warp_sum64(c1);
+                c2 = warp_sum64(c2);
+                if (lane / 3 == src / 3 && mine) acc += lchain == 0 ? c0 : (lchain == 1 ? c1 : c2);
             }
-        } else {
-            // host: per-state sums of clipped lengths
-            int64_t u = 0, w = 0, p = 0;
-            int64_t lo_t = INT64_MAX, hi_t = NEG_INF;
-#pragma unroll
-            for (int i = 0; i < ITEMS; ++i) {
-                if (i < cnt) {
-                    const uint32_t q = t_[i];
-                    bad |= (e_[i] < s_[i]) ? ST_BAD_END : 0u;
-                    bad |= (q > 2u) ? ST_BAD_KIND : 0u;
-                    const int64_t l = max64(e_[i] - s_[i], 0);
-                    u += (q == 0u) ? l : 0;
-                    w += (q == 1u) ? l : 0;
-                    p += (q == 2u) ? l : 0;
-                    lo_t = min64(lo_t, s_[i]);
-                    hi_t = max64(hi_t, e_[i]);
-                }
-            }
-            if (cnt > 0) {
-#pragma unroll
-                for (int r = 0; r < RMAX; ++r) {
-                    if (r < d.R) {
-                        const int64_t a = swin[2 * r], b = swin[2 * r + 1];
-                        if (lo_t >= a && hi_t <= b) {
-                            acc[r][0] += u;
-                            acc[r][1] += w;
-                            acc[r][2] += p;
-                        } else if (!(hi_t <= a || lo_t >= b)) {
-                            int64_t cu = 0, cw2 = 0, cp = 0;
-#pragma unroll
-                            for (int i = 0; i < ITEMS; ++i) {
-                                if (i < cnt) {
-                                    const uint32_t q = t_[i];
-                                    const int64_t l = max64(min64(e_[i], b) - max64(s_[i], a), 0);
-                                    cu += (q == 0u) ? l : 0;
-                                    cw2 += (q == 1u) ? l : 0;
-                                    cp += (q == 2u) ? l : 0;
-                                }
-                            }
-                            acc[r][0] += cu;
-                            acc[r][1] += cw2;
-                            acc[r][2] += cp;
-                        }
-                    }
-                }
-            }
+            release(st);
         }
+        ++n_consumed;
         pbad |= bad;
         last_s = tile_last_s;
 
@@ -394,36 +594,29 @@ __global__ void __launch_bounds__(WARPS * 32)
         const bool slice_done = cw.pos + static_cast<uint64_t>(len) >= r1;
         const bool seg_done = slice_done || (cw.pos + static_cast<uint64_t>(len) == cw.seg_end);
         if (seg_done) {
-#pragma unroll
-            for (int r = 0; r < RMAX; ++r) {
-                if (r < d.R) {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const int64_t v = warp_sum64(acc[r][c]);
-                        if (lane == 0 && v != 0) atomic_add64(&d.sums[3 * r + c], v);
-                    }
-                }
-            }
+            if (lane < 3 * d_R && acc != 0) atomic_add64(&d_sums[lane], acc);
             const uint32_t bits = __reduce_or_sync(0xFFFFFFFFu, pbad);
             if (lane == 0) {
                 if (bits) {
-                    atomicOr(d.status, bits);
+                    atomicOr(d_status, bits);
                     atomicOr(&seg_flags[cw.seg], bits);
                 }
-                if (!d.is_host) {
-                    atomic_max64(&d.carry_out[0], carryK);
-                    atomic_max64(&d.carry_out[1], carryM);
-                    atomic_max64(&d.carry_out[2], last_s);
+                if (!d_host) {
+                    atomic_max64(&d_cout[0], carryK);
+                    atomic_max64(&d_cout[1], carryM);
+                    atomic_max64(&d_cout[2], last_s);
+                }
+                if (first_portion) {
+                    wrec[gw].head_K = carryK;
+                    wrec[gw].head_M = carryM;
+                }
+                if (slice_done) {
+                    wrec[gw].tail_seg = cw.seg;
+                    wrec[gw].tail_K = carryK;
+                    wrec[gw].tail_M = carryM;
                 }
             }
-            if (first_portion) {
-                rec.head_K = carryK;
-                rec.head_M = carryM;
-                first_portion = false;
-            }
-            rec.tail_seg = cw.seg;
-            rec.tail_K = carryK;
-            rec.tail_M = carryM;
+            first_portion = false;
             portion_open = false;
         }
         if (slice_done) break;
@@ -433,27 +626,25 @@ __global__ void __launch_bounds__(WARPS * 32)
     if (timed_out) {
         if (lane == 0) {
             atomicOr(gstatus, ST_TIMEOUT);
-            atomicOr(d.status, ST_TIMEOUT);
+            if (d_status) atomicOr(d_status, ST_TIMEOUT);
             // let the copies still in flight land before the CTA's shared memory goes away
             for (uint32_t t = n_consumed; t < n_issued; ++t)
                 (void)mbar_wait_bounded(&bars[t % STAGES], (t / STAGES) & 1u, wait_limit);
-            rec.head_seg = NONE;
-            rec.tail_seg = NONE;
-            wrec[gw] = rec;
+            wrec[gw].head_seg = NONE;
+            wrec[gw].tail_seg = NONE;
         }
-        return;
     }
-    if (lane == 0) wrec[gw] = rec;
 }
 
 // ---------------------------------------------------------------- dispatch
 
 template <int ITEMS, int WARPS, int STAGES, int RMAX>
 static cudaError_t launch_t(int grid, const SegDesc* segs, const uint64_t* seg_start, uint32_t n_segs,
-                            WarpRec* wrec, uint32_t* seg_flags,
-                            uint32_t* gstatus, int64_t wait_limit, cudaStream_t stream) {
-    using C = SweepCfg<ITEMS, WARPS, STAGES, RMAX>;
-    auto k = sweep_kernel<ITEMS, WARPS, STAGES, RMAX>;
+                            WarpRec* wrec, uint32_t* seg_flags, uint32_t* gstatus, int64_t wait_limit,
+                            cudaStream_t stream) {
+    using C = SweepCfg<ITEMS, WARPS, STAGES>;
+    constexpr int MINB = WARPS == 8 ? 2 : 3;
+    auto k = sweep_kernel<ITEMS, WARPS, STAGES, RMAX, MINB>;
     static bool attr_set = false;   // per-instantiation, set once per process
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
@@ -466,8 +657,9 @@ static cudaError_t launch_t(int grid, const SegDesc* segs, const uint64_t* seg_s
 
 template <int ITEMS, int WARPS, int STAGES, int RMAX>
 static int occupancy_t() {
-    using C = SweepCfg<ITEMS, WARPS, STAGES, RMAX>;
-    auto k = sweep_kernel<ITEMS, WARPS, STAGES, RMAX>;
+    using C = SweepCfg<ITEMS, WARPS, STAGES>;
+    constexpr int MINB = WARPS == 8 ? 2 : 3;
+    auto k = sweep_kernel<ITEMS, WARPS, STAGES, RMAX, MINB>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) != cudaSuccess) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, WARPS * 32, C::SMEM) != cudaSuccess) return 0;
@@ -476,10 +668,10 @@ static int occupancy_t() {
 
 #define TALP_SHAPE_SWITCH(shape, RM, CALL)                \
     switch (shape) {                                      \
-        case 0: return CALL(7, 8, 4, RM);                 \
-        case 1: return CALL(9, 8, 3, RM);                 \
-        case 2: return CALL(7, 4, 6, RM);                 \
-        case 3: return CALL(5, 8, 4, RM);                 \
+        case 0: return CALL(9, 8, 2, RM);                 \
+        case 1: return CALL(7, 8, 3, RM);                 \
+        case 2: return CALL(11, 8, 2, RM);                \
+        case 3: return CALL(13, 8, 2, RM);                \
         default: break;                                   \
     }
 
@@ -487,21 +679,20 @@ static int occupancy_t() {
     launch_t<I, W, S, RM>(grid, segs, seg_start, n_segs, wrec, seg_flags, gstatus, wait_limit, stream)
 #define TALP_OCC(I, W, S, RM) occupancy_t<I, W, S, RM>()
 
+// The region count no longer shapes the kernel's registers (each lane owns
+// one (region, chain) accumulator), so one instantiation per shape serves
+// every R <= 8.
 cudaError_t launch_sweep(int shape, int rmax, int grid, const SegDesc* segs, const uint64_t* seg_start,
                          uint32_t n_segs, WarpRec* wrec, uint32_t* seg_flags, uint32_t* gstatus, int64_t wait_limit,
                          cudaStream_t stream) {
-    if (rmax <= 1) { TALP_SHAPE_SWITCH(shape, 1, TALP_LAUNCH) }
-    else if (rmax <= 2) { TALP_SHAPE_SWITCH(shape, 2, TALP_LAUNCH) }
-    else if (rmax <= 4) { TALP_SHAPE_SWITCH(shape, 4, TALP_LAUNCH) }
-    else { TALP_SHAPE_SWITCH(shape, 8, TALP_LAUNCH) }
+    (void)rmax;
+    TALP_SHAPE_SWITCH(shape, 8, TALP_LAUNCH)
     return cudaErrorInvalidValue;
 }
 
 int sweep_ctas_per_sm(int shape, int rmax) {
-    if (rmax <= 1) { TALP_SHAPE_SWITCH(shape, 1, TALP_OCC) }
-    else if (rmax <= 2) { TALP_SHAPE_SWITCH(shape, 2, TALP_OCC) }
-    else if (rmax <= 4) { TALP_SHAPE_SWITCH(shape, 4, TALP_OCC) }
-    else { TALP_SHAPE_SWITCH(shape, 8, TALP_OCC) }
+    (void)rmax;
+    TALP_SHAPE_SWITCH(shape, 8, TALP_OCC)
     return 0;
 }
 

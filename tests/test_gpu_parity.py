@@ -107,6 +107,26 @@ def test_covering_intervals_cross_slices(tpw):
         c.close()
 
 
+@pytest.mark.parametrize("scale,offset", [(1 << 20, 0), (1 << 28, 0), (3, (1 << 61) + 12345),
+                                          (1 << 21, -(1 << 58))])
+def test_wide_timestamps_take_the_exact_path(scale, offset):
+    """Spans of 2^32 ns and more (the int64 path of the sweep), values near
+    2^61 and negative times; mixed with tiles that fit 32-bit offsets."""
+    c = make_ctx(tiles_per_warp=1)
+    try:
+        ts = [tg.rescale_time(tg.tiny_trace(seed, trace_id=seed, max_events=300), scale, offset)
+              for seed in range(40)]
+        c.ingest(ts)
+        for t in ts:
+            assert_trace_equal(c, t, ("wide", scale, offset), sums=(t.trace_id % 5 == 0))
+        for seed in range(2):
+            t = tg.rescale_time(_covering_trace(seed, n=6000), scale, offset)
+            c.ingest([t])
+            assert_trace_equal(c, t, ("wide-covering", scale, offset, seed))
+    finally:
+        c.close()
+
+
 def test_device_pointers_match_host_pointers(ctx):
     import torch
     t = tg.random_trace(5, trace_id=77, n_ranks=4, devices_per_rank=2, dev_events=3000, host_events=2000,

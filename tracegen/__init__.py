@@ -379,6 +379,17 @@ def batched_trace(k, ranks, gpus, ev, seed=0x7A1F + 2, n_regions=8, threads=1):
 # small adversarial traces for exact checks
 
 
+def rescale_time(t: Trace, scale: int, offset: int = 0) -> Trace:
+    """The same trace with every timestamp (records and windows) mapped to
+    t * scale + offset: spans of 2^32 ns and more, or values near 2^62."""
+    def f(a):
+        return (a.astype(np.int64) * np.int64(scale) + np.int64(offset)).astype(np.int64)
+    return Trace(trace_id=t.trace_id, n_ranks=t.n_ranks, devices_per_rank=t.devices_per_rank,
+                 region_window=f(t.region_window), host_se=f(t.host_se), host_state=t.host_state,
+                 host_off=t.host_off, dev_se=f(t.dev_se), dev_tag=t.dev_tag, dev_off=t.dev_off,
+                 sorted_by_start=t.sorted_by_start, meta=dict(t.meta, scale=scale, offset=offset))
+
+
 def tiny_trace(seed, trace_id=0, max_ranks=3, max_devs=2, max_events=64, horizon=4096,
                n_regions=None, tiled_host=None, allow_empty=True, kinds=(0, 1, 2, 3, 4), streams=4):
     """Random small trace: arbitrary overlaps, zero-length intervals, empty
