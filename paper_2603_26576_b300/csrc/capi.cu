@@ -96,6 +96,7 @@ struct talp_gpu_ctx {
     std::unordered_map<uint64_t, TraceState*> traces;
     DevBuf ws;          // segment table, starts, fill jobs, payload, warp records, flags
     DevBuf stage;       // host-pointer record staging
+    DevBuf sortbuf;     // ping-pong copies of the device segments being sorted
     PinBuf up, down;    // pinned upload / download scratch
     cudaEvent_t ev_up = nullptr;      // upload scratch free again
     cudaEvent_t ev_ws = nullptr;      // workspace/staging free again
@@ -285,6 +286,7 @@ talp_gpu_status talp_gpu_destroy(talp_gpu_ctx* c) {
     c->traces.clear();
     dev_free(c, c->ws.p, c->ws.cap);
     dev_free(c, c->stage.p, c->stage.cap);
+    dev_free(c, c->sortbuf.p, c->sortbuf.cap);
     if (c->up.p) cudaFreeHost(c->up.p);
     if (c->down.p) cudaFreeHost(c->down.p);
     if (c->ev_up) cudaEventDestroy(c->ev_up);
@@ -340,6 +342,22 @@ talp_gpu_status talp_gpu_ingest_events(talp_gpu_ctx* c, const talp_gpu_trace_bat
     }
     if (n_segs > 0xFFFFFFF0ull) return fail(TALP_GPU_EINVAL, "too many segments in one call");
 
+    // sort stage sizes: device segments of batches that do not assert start order
+    uint64_t sort_slots = 0, sort_recs = 0, sort_tiles = 0, n_dev_segs = 0;
+    size_t n_backup_words = 0;
+    for (size_t k = 0; k < nb; ++k) {
+        const talp_gpu_trace_batch& b = batches[k];
+        n_dev_segs += mm[k];
+        if (b.flags & TALP_GPU_SORTED_BY_START) continue;
+        sort_slots += mm[k];
+        sort_recs += nd[k];
+        for (uint32_t g = 0; g < mm[k]; ++g)
+            sort_tiles += (b.dev_off[g + 1] - b.dev_off[g] + sort_tile_records() - 1) / sort_tile_records();
+        if ((b.flags & TALP_GPU_APPEND) && mm[k]) n_backup_words += 3ull * b.n_regions * mm[k];
+    }
+    const bool sorting = sort_slots > 0;
+    const size_t sortbuf_bytes = sorting ? 2 * (align_up(16 * sort_recs, 256) + align_up(sort_recs + 64, 256)) : 0;
+
     // workspace layout (device): [segs][seg_start][fill jobs][payload][wrec][seg_flags][gstatus]
     const int shape = c->shape;
     const int tile = sweep_tile(shape);
@@ -352,7 +370,9 @@ talp_gpu_status talp_gpu_ingest_events(talp_gpu_ctx* c, const talp_gpu_trace_bat
     if (want_warps > max_warps) want_warps = max_warps;
     if (want_warps < 1) want_warps = 1;
     const int grid = static_cast<int>((want_warps + warps - 1) / warps);
+    const int full_grid = static_cast<int>(max_warps / warps);   // re-sweep: size unknown on the host
     const uint32_t n_wrec = static_cast<uint32_t>(grid) * warps;
+    const uint32_t n_wrec_cap = static_cast<uint32_t>(sorting ? std::max(grid, full_grid) : grid) * warps;
 
     // payload per trace: hwin [n][R][2], dev_rank [m] (only at creation), TraceDev
     size_t payload_words = 0;
@@ -362,16 +382,31 @@ talp_gpu_status talp_gpu_ingest_events(talp_gpu_ctx* c, const talp_gpu_trace_bat
     size_t off_segs = 0;
     size_t off_start = align_up(off_segs + sizeof(SegDesc) * n_segs, 256);
     size_t off_jobs = align_up(off_start + sizeof(uint64_t) * (n_segs + 1), 256);
-    size_t off_pay = align_up(off_jobs + sizeof(FillJob) * n_jobs_max, 256);
+    size_t off_rest = align_up(off_jobs + sizeof(FillJob) * n_jobs_max, 256);
+    size_t off_sctl = align_up(off_rest + sizeof(int64_t*) * (sorting ? n_segs : 0), 256);
+    size_t off_pay = align_up(off_sctl + sizeof(SortCtl), 256);
     size_t up_bytes = align_up(off_pay + 8 * payload_words, 256);
+    // device-only part
     size_t off_wrec = up_bytes;
-    size_t off_flags = align_up(off_wrec + sizeof(WarpRec) * n_wrec, 256);
+    size_t off_flags = align_up(off_wrec + sizeof(WarpRec) * n_wrec_cap, 256);
     size_t off_gst = align_up(off_flags + sizeof(uint32_t) * (n_segs + 1), 256);
-    size_t ws_bytes = off_gst + 256;
+    size_t off_bk = align_up(off_gst + 256, 256);
+    size_t off_slist = align_up(off_bk + 8 * n_backup_words, 256);
+    size_t off_srb = align_up(off_slist + 4 * sort_slots, 256);
+    size_t off_stb = align_up(off_srb + 8 * sort_slots, 256);
+    size_t off_smn = align_up(off_stb + 8 * (sort_slots + 1), 256);
+    size_t off_smx = align_up(off_smn + 8 * sort_slots, 256);
+    size_t off_hist = align_up(off_smx + 8 * sort_slots, 256);
+    size_t off_offs = align_up(off_hist + 4 * 256 * sort_tiles, 256);
+    size_t off_rsegs = align_up(off_offs + 8 * 256 * sort_tiles, 256);
+    size_t off_rstart = align_up(off_rsegs + sizeof(SegDesc) * (sorting ? n_dev_segs : 0), 256);
+    size_t ws_bytes = align_up(off_rstart + 8 * (sorting ? n_dev_segs + 1 : 0), 256);
 
     size_t extra = new_bytes;
     if (c->ws.cap < ws_bytes) extra += align_up(ws_bytes + ws_bytes / 4, 1 << 20) - c->ws.cap;
     if (c->stage.cap < stage_bytes) extra += align_up(stage_bytes + stage_bytes / 4, 1 << 20) - c->stage.cap;
+    if (c->sortbuf.cap < sortbuf_bytes)
+        extra += align_up(sortbuf_bytes + sortbuf_bytes / 4, 1 << 20) - c->sortbuf.cap;
     if (c->held + extra > c->budget)
         return fail(TALP_GPU_ENOMEM, "admission: the ingest needs " + std::to_string(extra) +
                                          " more device bytes than the budget leaves");
@@ -382,6 +417,10 @@ talp_gpu_status talp_gpu_ingest_events(talp_gpu_ctx* c, const talp_gpu_trace_bat
     if (st != TALP_GPU_OK) return st;
     if (stage_bytes) {
         st = grow(c, c->stage, stage_bytes);
+        if (st != TALP_GPU_OK) return st;
+    }
+    if (sortbuf_bytes) {
+        st = grow(c, c->sortbuf, sortbuf_bytes);
         if (st != TALP_GPU_OK) return st;
     }
     TALP_CUDA(cudaEventSynchronize(c->ev_up));   // upload scratch no longer read by a pending copy
@@ -459,7 +498,8 @@ talp_gpu_status talp_gpu_ingest_events(talp_gpu_ctx* c, const talp_gpu_trace_bat
     int64_t* pay_dev = reinterpret_cast<int64_t*>(wsd + off_pay);
     uint32_t* seg_flags = reinterpret_cast<uint32_t*>(wsd + off_flags);
     uint32_t* gstatus = reinterpret_cast<uint32_t*>(wsd + off_gst);
-    size_t pw = 0;
+    const int64_t** restore = reinterpret_cast<const int64_t**>(up + off_rest);
+    size_t pw = 0, bk_used = 0;
     uint32_t nj = 0;
     uint64_t si = 0, pos = 0;
     for (size_t k = 0; k < nb; ++k) {
@@ -467,6 +507,7 @@ talp_gpu_status talp_gpu_ingest_events(talp_gpu_ctx* c, const talp_gpu_trace_bat
         TraceState* t = ts[k];
         const bool append = (b.flags & TALP_GPU_APPEND) != 0;
         const uint32_t n = t->n, m = t->m, R = t->R;
+        int64_t* bkd = nullptr;   // pre-ingest device sums (APPEND + sorting)
         int64_t* cin = t->carry[t->cur];
         int64_t* cout = t->carry[t->cur ^ 1];
         // windows: transpose [R][n][2] -> [n][R][2]
@@ -507,7 +548,15 @@ talp_gpu_status talp_gpu_ingest_events(talp_gpu_ctx* c, const talp_gpu_trace_bat
             jobs[nj++] = FillJob{reinterpret_cast<int64_t*>(t->status), 1, 0, nullptr};
         } else {
             if (m) jobs[nj++] = FillJob{cout, 3ull * m, 0, cin};
+            if (!(b.flags & TALP_GPU_SORTED_BY_START) && m) {
+                // a device segment that gets sorted is re-swept from its sums
+                // before this slice: keep a copy of them
+                bkd = reinterpret_cast<int64_t*>(wsd + off_bk) + bk_used;
+                bk_used += 3ull * R * m;
+                jobs[nj++] = FillJob{bkd, 3ull * m * R, 0, t->dsum};
+            }
         }
+        const uint8_t seg_flags0 = (b.flags & TALP_GPU_SORTED_BY_START) ? 0 : kSegSortable;
         // device segments, then host segments
         for (uint32_t g = 0; g < m; ++g) {
             SegDesc& s = sd[si];
@@ -525,6 +574,8 @@ talp_gpu_status talp_gpu_ingest_events(talp_gpu_ctx* c, const talp_gpu_trace_bat
             s.R = static_cast<uint16_t>(R);
             s.is_host = 0;
             memset(s.pad, 0, sizeof(s.pad));
+            s.pad[0] = seg_flags0;
+            if (sorting) restore[si] = bkd ? bkd + static_cast<size_t>(g) * R * 3 : nullptr;
             sstart[si] = pos;
             pos += s.n;
             ++si;
@@ -552,8 +603,29 @@ talp_gpu_status talp_gpu_ingest_events(talp_gpu_ctx* c, const talp_gpu_trace_bat
     sstart[si] = pos;
     jobs[nj++] = FillJob{reinterpret_cast<int64_t*>(seg_flags), (n_segs + 2) / 2, 0, nullptr};
     jobs[nj++] = FillJob{reinterpret_cast<int64_t*>(gstatus), 1, 0, nullptr};
-    if (nj > n_jobs_max || pw > payload_words || si != n_segs)
+    if (nj > n_jobs_max || pw > payload_words || si != n_segs || bk_used > n_backup_words)
         return fail(TALP_GPU_ECUDA, "internal: upload table overflow");
+    if (sorting) {
+        SortCtl sc{};
+        sc.list = reinterpret_cast<uint32_t*>(wsd + off_slist);
+        sc.rec_base = reinterpret_cast<uint64_t*>(wsd + off_srb);
+        sc.tile_base = reinterpret_cast<uint64_t*>(wsd + off_stb);
+        sc.mn = reinterpret_cast<int64_t*>(wsd + off_smn);
+        sc.mx = reinterpret_cast<int64_t*>(wsd + off_smx);
+        sc.hist = reinterpret_cast<uint32_t*>(wsd + off_hist);
+        sc.offs = reinterpret_cast<uint64_t*>(wsd + off_offs);
+        char* sb = static_cast<char*>(c->sortbuf.p);
+        const size_t se_b = align_up(16 * sort_recs, 256), tg_b = align_up(sort_recs + 64, 256);
+        for (int q = 0; q < 2; ++q) {
+            char* base = sb + q * (se_b + tg_b);
+            sc.buf_se[q] = reinterpret_cast<int64_t*>(base);
+            sc.buf_tag[q] = reinterpret_cast<uint8_t*>(base + se_b);
+            sc.buf_tag_limit[q] = reinterpret_cast<const uint8_t*>(
+                reinterpret_cast<uintptr_t>(base + se_b + tg_b) & ~static_cast<uintptr_t>(15));
+        }
+        sc.restore = reinterpret_cast<const int64_t* const*>(wsd + off_rest);
+        memcpy(up + off_sctl, &sc, sizeof(SortCtl));
+    }
 
     TALP_CUDA(cudaMemcpyAsync(wsd, up, up_bytes, cudaMemcpyHostToDevice, stream));
     TALP_CUDA(cudaEventRecord(c->ev_up, stream));
@@ -580,6 +652,21 @@ talp_gpu_status talp_gpu_ingest_events(talp_gpu_ctx* c, const talp_gpu_trace_bat
         }
         TALP_CUDA(launch_fixup(dsegs, dstart, wrec, n_wrec, seg_flags, stream));
         c->kernel_launches += 2;
+        if (sorting) {
+            // a2: sort the device segments found out of order, re-sweep them
+            SortCtl* sctl = reinterpret_cast<SortCtl*>(wsd + off_sctl);
+            SegDesc* rsegs = reinterpret_cast<SegDesc*>(wsd + off_rsegs);
+            uint64_t* rstart = reinterpret_cast<uint64_t*>(wsd + off_rstart);
+            const uint64_t gt = std::min<uint64_t>(sort_tiles, static_cast<uint64_t>(c->num_sms) * 8);
+            const uint64_t gs = std::min<uint64_t>(sort_slots, static_cast<uint64_t>(c->num_sms) * 4);
+            TALP_CUDA(launch_sort_stage(dsegs, static_cast<uint32_t>(n_segs), static_cast<uint32_t>(n_dev_segs),
+                                        seg_flags, sctl, rsegs, rstart, static_cast<int>(std::max<uint64_t>(gt, 1)),
+                                        static_cast<int>(std::max<uint64_t>(gs, 1)), stream));
+            TALP_CUDA(launch_sweep(shape, static_cast<int>(rmax), full_grid, rsegs, rstart,
+                                   static_cast<uint32_t>(n_dev_segs), wrec, seg_flags, gstatus, c->wait_limit, stream));
+            TALP_CUDA(launch_fixup(rsegs, rstart, wrec, static_cast<uint32_t>(full_grid) * warps, seg_flags, stream));
+            c->kernel_launches += 2 + 24 + 1 + 2;
+        }
     }
     TALP_CUDA(cudaEventRecord(c->ev_ws, stream));
     c->ws_used = true;

@@ -78,8 +78,30 @@ struct FinalizeJob {
 struct FillJob {
     int64_t* ptr;
     uint64_t count;
-    int64_t value;
-    const int64_t* src;   // when non-null: copy count values from src instead
+    int64_t value;        // fill value; with src: 0 = copy src, 1 = add src
+    const int64_t* src;
+};
+
+// SegDesc.pad[0] bits
+constexpr uint8_t kSegSortable = 1;   // device segment may be sorted when found out of order
+
+// Control block of the sort stage (device memory; pointers into scratch).
+struct SortCtl {
+    uint32_t nflag;            // flagged segments
+    uint32_t pad;
+    uint64_t nrec;             // their records
+    uint64_t ntile;            // their sort tiles
+    uint32_t* list;            // [slots] segment index of flagged segment k
+    uint64_t* rec_base;        // [slots] first record of k in the sort buffers
+    uint64_t* tile_base;       // [slots + 1] first tile of k
+    int64_t* mn;               // [slots] smallest start of k
+    int64_t* mx;               // [slots] largest start of k
+    uint32_t* hist;            // [tiles][256] digit counts
+    uint64_t* offs;            // [tiles][256] output offsets
+    int64_t* buf_se[2];        // ping-pong record buffers
+    uint8_t* buf_tag[2];
+    const uint8_t* buf_tag_limit[2];
+    const int64_t* const* restore;  // [segments] sums a flagged segment restarts from (null: zero)
 };
 
 // ---------------------------------------------------------------- helpers

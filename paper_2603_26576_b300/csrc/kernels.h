@@ -36,6 +36,14 @@ cudaError_t launch_prep(const FillJob* jobs, uint32_t n_jobs, cudaStream_t strea
 
 cudaError_t launch_finalize(const FinalizeJob* jobs, uint32_t n_jobs, cudaStream_t stream);
 
+// Sort stage over the device segments flagged out of order (sortable ones),
+// then the segment table of their sorted copies for the re-sweep.
+// n_segs: entries of `segs`; n_slots: device segments (upper bound of flagged).
+cudaError_t launch_sort_stage(const SegDesc* segs, uint32_t n_segs, uint32_t n_slots, const uint32_t* seg_flags,
+                              SortCtl* ctl, SegDesc* resweep_segs, uint64_t* resweep_start, int grid_tiles,
+                              int grid_segs, cudaStream_t stream);
+int sort_tile_records();
+
 // Message returned by talp_gpu_last_error() on this thread.
 void set_last_error(const std::string& msg);
 

@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(256) prep_kernel(const FillJob* __restrict__ j
     for (uint32_t j = blockIdx.y; j < n_jobs; j += gridDim.y) {
         const FillJob job = jobs[j];
         for (uint64_t i = blockIdx.x * 256ull + threadIdx.x; i < job.count; i += 256ull * gridDim.x)
-            job.ptr[i] = job.src ? job.src[i] : job.value;
+            job.ptr[i] = job.src ? (job.value ? job.ptr[i] + job.src[i] : job.src[i]) : job.value;
     }
 }
 

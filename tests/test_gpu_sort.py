@@ -1,0 +1,116 @@
+"""The sort stage: device records out of start order (no SORTED_BY_START
+flag) are sorted on the GPU and the results equal the oracle bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+import tracegen as tg
+from gpu_common import assert_metrics_equal, assert_trace_equal, make_ctx
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = make_ctx()
+    yield c
+    c.close()
+
+
+def test_shuffled_tiny_traces_batched(ctx):
+    ts = [tg.shuffle_segments(tg.tiny_trace(seed, trace_id=seed, max_events=200), seed=seed, frac=0.7)
+          for seed in range(120)]
+    ctx.ingest(ts)
+    for t in ts:
+        assert_trace_equal(ctx, t, "shuffled-tiny", sums=(t.trace_id % 4 == 0))
+    ctx.reset()
+
+
+@pytest.mark.parametrize("mode", ["lanes", "shuffle"])
+def test_unsorted_mid_size(ctx, mode):
+    for seed in range(3):
+        base = tg.random_trace(seed, trace_id=seed, n_ranks=3, devices_per_rank=[2, 1, 3],
+                               dev_events=[9000, 1, 0, 20000, 5000, 4097], host_events=[3000, 10, 7], n_regions=4)
+        t = tg.interleave_lanes(base) if mode == "lanes" else tg.shuffle_segments(base, seed=seed)
+        ctx.ingest([t])
+        assert_trace_equal(ctx, t, (mode, seed))
+    ctx.reset()
+
+
+def test_unsorted_wide_timestamps(ctx):
+    """Keys spanning many radix digits (up to 8 passes)."""
+    for scale, offset in [(1 << 30, 0), (1 << 45, -(1 << 61)), (7, (1 << 61))]:
+        ts = [tg.shuffle_segments(tg.rescale_time(tg.tiny_trace(s, trace_id=s, max_events=300), scale, offset), seed=s)
+              for s in range(20)]
+        ctx.ingest(ts)
+        for t in ts:
+            assert_trace_equal(ctx, t, ("wide-unsorted", scale), sums=(t.trace_id % 5 == 0))
+    ctx.reset()
+
+
+def test_mixed_sorted_and_unsorted_batches(ctx):
+    """One ingest call with traces that assert start order and traces that
+    do not; a trace that asserts order but lies is still reported."""
+    good = [tg.tiny_trace(s, trace_id=100 + s) for s in range(10)]
+    uns = [tg.shuffle_segments(tg.tiny_trace(s, trace_id=200 + s), seed=s) for s in range(10)]
+    import paper_2603_26576_b300 as P
+    batches, keep = [], []
+    for t in good:
+        b, k = P.batch_from_arrays(t.trace_id, t.devices_per_rank, t.region_window, t.host_se, t.host_state,
+                                   t.host_off, t.dev_se, t.dev_tag, t.dev_off, P.TALP_GPU_SORTED_BY_START)
+        batches.append(b)
+        keep.append(k)
+    for t in uns:
+        b, k = P.batch_from_arrays(t.trace_id, t.devices_per_rank, t.region_window, t.host_se, t.host_state,
+                                   t.host_off, t.dev_se, t.dev_tag, t.dev_off, 0)
+        batches.append(b)
+        keep.append(k)
+    liar = tg.shuffle_segments(tg.tiny_trace(3, trace_id=300, allow_empty=False, max_events=60), seed=9)
+    b, k = P.batch_from_arrays(liar.trace_id, liar.devices_per_rank, liar.region_window, liar.host_se,
+                               liar.host_state, liar.host_off, liar.dev_se, liar.dev_tag, liar.dev_off,
+                               P.TALP_GPU_SORTED_BY_START)
+    batches.append(b)
+    keep.append(k)
+    P.talp_gpu_ingest_events(ctx.ctx, batches)
+    for t in good + uns:
+        ctx._shapes[int(t.trace_id)] = (t.n_ranks, t.m_devices, t.n_regions)
+        assert_trace_equal(ctx, t, "mixed", sums=False)
+    ctx._shapes[300] = (liar.n_ranks, liar.m_devices, liar.n_regions)
+    st, res = ctx.metrics(300, check=False)
+    unsorted_somewhere = any(np.any(np.diff(liar.dev_segment(g)[0][:, 0]) < 0) for g in range(liar.m_devices))
+    if unsorted_somewhere:
+        assert st == -1 and res[0]["flags"] & 0x200
+    ctx.reset()
+
+
+def test_append_with_unsorted_slices():
+    """Each later slice arrives out of order inside itself (sorted on the GPU);
+    the earlier slices' sums are kept."""
+    from test_gpu_parity import _split_by_time
+    c = make_ctx(tiles_per_warp=1)
+    try:
+        t = tg.random_trace(12, trace_id=7, n_ranks=2, devices_per_rank=2, dev_events=5000, host_events=2000,
+                            n_regions=3)
+        a, b = _split_by_time(t, 0.5)
+        c.ingest([tg.interleave_lanes(a)])
+        c.ingest([tg.shuffle_segments(b, seed=4)], flags=4)
+        assert_trace_equal(c, t, "append-unsorted")
+        # a slice that starts before the previous one ended is still refused
+        c.ingest([tg.interleave_lanes(b)])
+        c.ingest([tg.shuffle_segments(a, seed=5)], flags=4)
+        st, _ = c.metrics(7, check=False)
+        assert st == -1
+    finally:
+        c.close()
+
+
+def test_unsorted_with_many_warps_per_segment():
+    c = make_ctx(tiles_per_warp=1)
+    try:
+        base = tg.random_trace(31, trace_id=1, n_ranks=1, devices_per_rank=1, dev_events=300_000,
+                               host_events=1000, n_regions=2)
+        t = tg.interleave_lanes(base)
+        c.ingest([t])
+        assert_trace_equal(c, t, "unsorted-big")
+    finally:
+        c.close()
