@@ -227,6 +227,62 @@ talp_gpu_status talp_gpu_region_metrics_device(talp_gpu_ctx *ctx, const uint64_t
 talp_gpu_status talp_gpu_unit_sums(talp_gpu_ctx *ctx, uint64_t trace_id, uint32_t region,
                                    int64_t *host_out, int64_t *dev_out, void *stream);
 
+/* ------------------------------------------------------------ batched plans */
+
+/*
+ * A plan is the batched form: the whole reduction of many traces (of uneven
+ * rank, device and record counts) -- prep, sweep, fix-up, the sort stage when
+ * records may be out of order, and the finalize of every region of every
+ * trace -- recorded once as a CUDA graph and replayed by talp_gpu_plan_launch
+ * as one graph launch; its segment tables are uploaded once, when the plan
+ * is created.  Each trace's
+ * sums are the same as after talp_gpu_ingest_events of that trace alone
+ * (Sec. 4.1, 4.2, Eqs. 1-12 per trace and region); the traces also stay in
+ * the context (talp_gpu_region_metrics etc. work on them after a launch).
+ *
+ * batches:    n traces; every one with TALP_GPU_DEVICE_PTRS and without
+ *             TALP_GPU_APPEND.  The record arrays must stay at the same
+ *             device addresses for the plan's lifetime; their contents may
+ *             change between launches (shapes and offsets may not).
+ * plan_flags: TALP_GPU_PLAN_AUTOTUNE times every sweep shape (records per
+ *             lane, warps, pipeline stages) and tiles-per-warp setting on
+ *             these traces and keeps the fastest; the choice is also
+ *             remembered by the context for later ingests of the same size
+ *             class.
+ * Errors: EINVAL, ENOMEM (admission: plan workspace + new traces), EBUSY
+ * (a trace id in use by a plan with another shape), ECUDA.
+ * A trace used by a plan cannot be reset or re-shaped (EBUSY) until the plan
+ * is destroyed.
+ */
+#define TALP_GPU_PLAN_AUTOTUNE 0x1u
+
+typedef struct talp_gpu_plan talp_gpu_plan;
+
+typedef struct {
+    uint64_t n_metrics;                /* sum of n_regions over the plan's traces */
+    uint64_t records;                  /* records reduced per launch */
+    uint64_t segments;                 /* device + host segments */
+    uint32_t kernels_per_launch;       /* kernels in the graph */
+    uint32_t sweep_items;              /* chosen sweep shape: records per lane per tile */
+    uint32_t sweep_warps;              /*   warps per CTA */
+    uint32_t sweep_stages;             /*   TMA pipeline stages per warp */
+    uint32_t tiles_per_warp;           /*   minimum tiles per warp (grid sizing) */
+    uint32_t sweep_grid;               /*   CTAs of the sweep launch */
+    uint32_t reserved;
+} talp_gpu_plan_stats;
+
+talp_gpu_status talp_gpu_plan_create(talp_gpu_ctx *ctx, const talp_gpu_trace_batch *batches, size_t n,
+                                     uint32_t plan_flags, talp_gpu_plan **out);
+/* Enqueue one replay of the plan's graph on `stream` (stream ordered). */
+talp_gpu_status talp_gpu_plan_launch(talp_gpu_plan *plan, void *stream);
+/* Copy the metrics of the last launch to out_host[n_metrics] (traces in plan
+ * order, regions 0..R-1 each) and synchronise `stream`; EINVAL/ETIMEDOUT
+ * as for talp_gpu_region_metrics (out_host is written either way). */
+talp_gpu_status talp_gpu_plan_metrics(talp_gpu_plan *plan, talp_gpu_metrics *out_host, void *stream);
+talp_gpu_status talp_gpu_plan_info(talp_gpu_plan *plan, talp_gpu_plan_stats *out);
+/* Synchronise the device and free the plan (the traces stay). NULL is accepted. */
+talp_gpu_status talp_gpu_plan_destroy(talp_gpu_plan *plan);
+
 /* Drop trace_id's state and return its HBM (TALP_GPU_ALL: every trace). */
 talp_gpu_status talp_gpu_reset(talp_gpu_ctx *ctx, uint64_t trace_id);
 

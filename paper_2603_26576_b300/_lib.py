@@ -23,8 +23,10 @@ EXPORTED_SYMBOLS = (
     "talp_gpu_create", "talp_gpu_destroy", "talp_gpu_ingest_events", "talp_gpu_region_metrics",
     "talp_gpu_region_metrics_batch", "talp_gpu_region_metrics_device", "talp_gpu_unit_sums",
     "talp_gpu_reset", "talp_gpu_memory", "talp_gpu_profile", "talp_gpu_profile_read", "talp_gpu_reduce_noalloc",
-    "talp_gpu_last_error",
+    "talp_gpu_plan_create", "talp_gpu_plan_launch", "talp_gpu_plan_metrics", "talp_gpu_plan_info",
+    "talp_gpu_plan_destroy", "talp_gpu_last_error",
 )
+TALP_GPU_PLAN_AUTOTUNE = 0x1
 TALP_GPU_NOALLOC_MAX_UNITS = 8192
 
 
@@ -61,6 +63,13 @@ RATIO_FIELDS = ("host_pe", "host_mpi_pe", "host_mpi_lb", "host_mpi_ce", "host_oe
 class talp_gpu_profile_stats(ctypes.Structure):
     _fields_ = [("sweep_launches", ctypes.c_uint64), ("sweep_records", ctypes.c_uint64),
                 ("sweep_ms", ctypes.c_double), ("kernel_launches", ctypes.c_uint64)]
+
+
+class talp_gpu_plan_stats(ctypes.Structure):
+    _fields_ = [("n_metrics", ctypes.c_uint64), ("records", ctypes.c_uint64), ("segments", ctypes.c_uint64),
+                ("kernels_per_launch", ctypes.c_uint32), ("sweep_items", ctypes.c_uint32),
+                ("sweep_warps", ctypes.c_uint32), ("sweep_stages", ctypes.c_uint32),
+                ("tiles_per_warp", ctypes.c_uint32), ("sweep_grid", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class talp_gpu_metrics(ctypes.Structure):
@@ -104,6 +113,12 @@ def load_library():
         "talp_gpu_profile": ([P, I32], I32),
         "talp_gpu_profile_read": ([P, ctypes.POINTER(talp_gpu_profile_stats)], I32),
         "talp_gpu_reduce_noalloc": ([ctypes.POINTER(talp_gpu_trace_batch), ctypes.POINTER(talp_gpu_metrics), P], I32),
+        "talp_gpu_plan_create": ([P, ctypes.POINTER(talp_gpu_trace_batch), S, U32, ctypes.POINTER(ctypes.c_void_p)],
+                                 I32),
+        "talp_gpu_plan_launch": ([P, P], I32),
+        "talp_gpu_plan_metrics": ([P, ctypes.POINTER(talp_gpu_metrics), P], I32),
+        "talp_gpu_plan_info": ([P, ctypes.POINTER(talp_gpu_plan_stats)], I32),
+        "talp_gpu_plan_destroy": ([P], I32),
         "talp_gpu_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -205,6 +220,38 @@ def talp_gpu_profile_read(ctx) -> dict:
     _check(load_library().talp_gpu_profile_read(ctx, ctypes.byref(st)))
     return dict(sweep_launches=int(st.sweep_launches), sweep_records=int(st.sweep_records),
                 sweep_ms=float(st.sweep_ms), kernel_launches=int(st.kernel_launches))
+
+
+def talp_gpu_plan_create(ctx, batches, plan_flags=0):
+    arr = (talp_gpu_trace_batch * len(batches))(*batches)
+    plan = ctypes.c_void_p()
+    _check(load_library().talp_gpu_plan_create(ctx, arr, len(batches), plan_flags, ctypes.byref(plan)))
+    return plan
+
+
+def talp_gpu_plan_launch(plan, stream=None):
+    _check(load_library().talp_gpu_plan_launch(plan, _stream(stream)))
+
+
+def talp_gpu_plan_info(plan) -> dict:
+    st = talp_gpu_plan_stats()
+    _check(load_library().talp_gpu_plan_info(plan, ctypes.byref(st)))
+    return {f: int(getattr(st, f)) for f, _ in talp_gpu_plan_stats._fields_}
+
+
+def talp_gpu_plan_metrics(plan, stream=None, check=True):
+    n = talp_gpu_plan_info(plan)["n_metrics"]
+    out = (talp_gpu_metrics * max(1, n))()
+    st = load_library().talp_gpu_plan_metrics(plan, out, _stream(stream))
+    res = list(out)[:n]
+    if check:
+        _check(st)
+        return res
+    return st, res
+
+
+def talp_gpu_plan_destroy(plan):
+    _check(load_library().talp_gpu_plan_destroy(plan))
 
 
 def talp_gpu_reduce_noalloc(batch, stream=None, check=True):
@@ -345,3 +392,48 @@ class Context:
 
     def memory(self):
         return talp_gpu_memory(self.ctx)
+
+    def plan(self, traces, arrays, flags=TALP_GPU_SORTED_BY_START, plan_flags=0):
+        """A batched plan over traces whose records are the CUDA tensors in
+        `arrays` (one dict per trace: host_se, host_state, dev_se, dev_tag)."""
+        batches, keep = [], []
+        for t, a in zip(traces, arrays):
+            b, kp = batch_from_arrays(t.trace_id, t.devices_per_rank, t.region_window, a["host_se"],
+                                      a["host_state"], t.host_off, a["dev_se"], a["dev_tag"], t.dev_off, flags)
+            batches.append(b)
+            keep.append(kp)
+            self._shapes[int(t.trace_id)] = (int(t.n_ranks), int(np.asarray(t.devices_per_rank).sum()),
+                                             int(np.asarray(t.region_window).shape[0]))
+        return Plan(talp_gpu_plan_create(self.ctx, batches, plan_flags), keep)
+
+
+class Plan:
+    """Owning wrapper of a talp_gpu_plan (the batched form)."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def launch(self, stream=None):
+        talp_gpu_plan_launch(self.handle, stream)
+
+    def metrics(self, stream=None, check=True):
+        r = talp_gpu_plan_metrics(self.handle, stream, check)
+        if check:
+            return [metrics_to_dict(x) for x in r]
+        st, r = r
+        return st, [metrics_to_dict(x) for x in r]
+
+    def info(self):
+        return talp_gpu_plan_info(self.handle)
+
+    def close(self):
+        if self.handle is not None:
+            talp_gpu_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

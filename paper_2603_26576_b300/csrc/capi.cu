@@ -1,6 +1,8 @@
 // Host engine behind the C ABI: trace table, HBM admission, host-pointer
-// staging, segment tables, launch sequence (prep -> sweep -> fix-up) and
-// the result calls (finalize -> copy back).
+// staging, segment tables, the launch sequence (prep -> sweep -> fix-up ->
+// [sort -> re-sweep -> fix-up] -> [finalize]), the result calls, and
+// reusable plans captured as CUDA graphs with an autotuned sweep shape.
+#include <algorithm>
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
@@ -34,15 +36,21 @@ talp_gpu_status cuda_fail(cudaError_t e, const char* what) {
     return TALP_GPU_ECUDA;
 }
 
-#define TALP_CUDA(call)                                   \
-    do {                                                  \
-        cudaError_t e_ = (call);                          \
+#define TALP_CUDA(call)                                     \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
         if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+#define TALP_TRY(call)                                      \
+    do {                                                    \
+        talp_gpu_status s_ = (call);                        \
+        if (s_ != TALP_GPU_OK) return s_;                   \
     } while (0)
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Per-trace device state: partial sums, windows, running carries, metrics.
+// Per-trace device state: partial sums, windows, running carries.
 struct TraceState {
     uint64_t id = 0;
     uint32_t n = 0, m = 0, R = 0;
@@ -56,8 +64,8 @@ struct TraceState {
     int64_t* carry[2] = {nullptr, nullptr};  // [m][3] each
     uint32_t* status = nullptr;    // one word (+ padding)
     TraceDev* tdev = nullptr;
-    MetricsOut* metrics = nullptr; // [R]
     int cur = 0;
+    int plan_refs = 0;             // plans whose graphs point at this state
 };
 
 size_t trace_bytes(uint32_t n, uint32_t m, uint32_t R) {
@@ -69,11 +77,9 @@ size_t trace_bytes(uint32_t n, uint32_t m, uint32_t R) {
     b += 2 * align_up(sizeof(int64_t) * 3 * (m ? m : 1), 256);
     b += 256;                                         // status
     b += align_up(sizeof(TraceDev), 256);
-    b += align_up(sizeof(MetricsOut) * R, 256);
     return b;
 }
 
-// grow-only device buffer
 struct DevBuf {
     void* p = nullptr;
     size_t cap = 0;
@@ -82,6 +88,34 @@ struct DevBuf {
 struct PinBuf {
     void* p = nullptr;
     size_t cap = 0;
+};
+
+// Everything an ingest needs to know before touching memory: sizes, grid,
+// and the byte layout of its workspace (upload part first).
+struct Tuning {
+    int shape = kDefaultSweepShape;
+    int tpw = 4;              // minimum tiles per warp (grid sizing of small ingests)
+    uint64_t seg_cost = 0;    // phantom records per segment (balances segment switches)
+};
+
+struct Layout {
+    int shape = 0, warps = 0, tile = 0, grid = 0, full_grid = 0, tpw = 4;
+    uint64_t seg_cost = 0;
+    uint32_t rmax = 1, n_wrec = 0, n_wrec_cap = 0;
+    uint64_t n_segs = 0, n_records = 0, n_dev_segs = 0;
+    uint64_t sort_slots = 0, sort_recs = 0, sort_tiles = 0;
+    size_t n_backup_words = 0, payload_words = 0, n_jobs_max = 0, n_fin = 0;
+    bool sorting = false;
+    size_t off_segs = 0, off_start = 0, off_send = 0, off_jobs = 0, off_rest = 0, off_sctl = 0, off_fin = 0,
+           off_pay = 0, off_rrend = 0;
+    uint64_t virt = 0;        // virtual positions (records + phantoms)
+    size_t up_bytes = 0;
+    size_t off_wrec = 0, off_flags = 0, off_gst = 0, off_bk = 0, off_slist = 0, off_srb = 0, off_stb = 0;
+    size_t off_smn = 0, off_smx = 0, off_hist = 0, off_offs = 0, off_rsegs = 0, off_rstart = 0, off_mout = 0;
+    size_t ws_bytes = 0, stage_bytes = 0, sortbuf_bytes = 0, new_bytes = 0;
+    uint32_t nj = 0;
+    std::vector<uint64_t> nh, nd;
+    std::vector<uint32_t> mm;
 };
 
 }  // namespace
@@ -94,15 +128,17 @@ struct talp_gpu_ctx {
     size_t budget = 0;
     size_t held = 0;
     std::unordered_map<uint64_t, TraceState*> traces;
-    DevBuf ws;          // segment table, starts, fill jobs, payload, warp records, flags
+    DevBuf ws;          // segment table, starts, jobs, payload, warp records, flags, sort control
     DevBuf stage;       // host-pointer record staging
     DevBuf sortbuf;     // ping-pong copies of the device segments being sorted
     PinBuf up, down;    // pinned upload / download scratch
     cudaEvent_t ev_up = nullptr;      // upload scratch free again
     cudaEvent_t ev_ws = nullptr;      // workspace/staging free again
     bool ws_used = false;
-    int shape = kDefaultSweepShape;
-    int min_tiles_per_warp = 4;
+    Tuning defaults;
+    bool shape_forced = false;
+    std::unordered_map<uint64_t, Tuning> tune;   // size class -> tuning picked by a plan's autotuner
+    cudaStream_t cap_stream = nullptr;                         // stream used for graph capture
     // profiling
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -110,6 +146,18 @@ struct talp_gpu_ctx {
     std::vector<uint64_t> ev_records;
     uint64_t kernel_launches = 0;
     int64_t wait_limit = 4000000000LL;   // cycles (~2 s at 2 GHz)
+};
+
+struct talp_gpu_plan {
+    talp_gpu_ctx* c = nullptr;
+    DevBuf ws, sortbuf;
+    PinBuf up;
+    Layout L;
+    std::vector<TraceState*> ts;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    size_t n_metrics = 0;
+    uint64_t launches_per_run = 0;
 };
 
 namespace {
@@ -133,9 +181,11 @@ void dev_free(talp_gpu_ctx* c, void* p, size_t bytes) {
     c->held -= bytes;
 }
 
+size_t grow_size(size_t need) { return align_up(need + need / 4, 1 << 20); }
+
 talp_gpu_status grow(talp_gpu_ctx* c, DevBuf& b, size_t need) {
     if (b.cap >= need) return TALP_GPU_OK;
-    size_t cap = align_up(need + need / 4, 1 << 20);
+    size_t cap = grow_size(need);
     if (b.p) {
         cudaDeviceSynchronize();
         dev_free(c, b.p, b.cap);
@@ -207,15 +257,18 @@ talp_gpu_status alloc_trace(talp_gpu_ctx* c, uint64_t id, uint32_t n, const uint
     t->carry[1] = reinterpret_cast<int64_t*>(take(sizeof(int64_t) * 3 * (t->m ? t->m : 1)));
     t->status = reinterpret_cast<uint32_t*>(take(256));
     t->tdev = reinterpret_cast<TraceDev*>(take(sizeof(TraceDev)));
-    t->metrics = reinterpret_cast<MetricsOut*>(take(sizeof(MetricsOut) * R));
     *out = t;
     return TALP_GPU_OK;
 }
 
+bool same_shape(const TraceState* t, const talp_gpu_trace_batch& b) {
+    return t->n == b.n_ranks && t->R == b.n_regions &&
+           memcmp(t->dpr.data(), b.devices_per_rank, sizeof(uint32_t) * b.n_ranks) == 0;
+}
+
 // Host-side checks of one batch header (the records themselves are checked
 // on the GPU).
-talp_gpu_status check_batch(talp_gpu_ctx* c, const talp_gpu_trace_batch& b, uint64_t* n_host, uint64_t* n_dev,
-                            uint32_t* m_out) {
+talp_gpu_status check_batch(const talp_gpu_trace_batch& b, uint64_t* n_host, uint64_t* n_dev, uint32_t* m_out) {
     if (b.n_ranks == 0) return fail(TALP_GPU_EINVAL, "n_ranks must be >= 1");
     if (b.n_regions == 0 || b.n_regions > TALP_GPU_MAX_REGIONS)
         return fail(TALP_GPU_EINVAL, "n_regions must be in 1..8");
@@ -244,196 +297,118 @@ talp_gpu_status check_batch(talp_gpu_ctx* c, const talp_gpu_trace_batch& b, uint
         if ((*n_host && (mis(b.host_se) || mis(b.host_state))) || (*n_dev && (mis(b.dev_se) || mis(b.dev_tag))))
             return fail(TALP_GPU_EINVAL, "device record arrays must be 16-byte aligned");
     }
-    (void)c;
     return TALP_GPU_OK;
 }
 
-}  // namespace
-
-// ===================================================================== ABI
-
-extern "C" {
-
-const char* talp_gpu_last_error(void) { return g_last_error.c_str(); }
-
-talp_gpu_status talp_gpu_create(talp_gpu_ctx** out, int device, size_t hbm_budget_bytes) {
-    if (!out) return fail(TALP_GPU_EINVAL, "null out");
-    *out = nullptr;
-    int ndev = 0;
-    cudaError_t e = cudaGetDeviceCount(&ndev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
-    if (device < 0 || device >= ndev) return fail(TALP_GPU_EINVAL, "bad device index");
-    TALP_CUDA(cudaSetDevice(device));
-    talp_gpu_ctx* c = new talp_gpu_ctx();
-    c->device = device;
-    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
-    size_t fr = 0, tot = 0;
-    cudaMemGetInfo(&fr, &tot);
-    c->budget = hbm_budget_bytes ? hbm_budget_bytes : static_cast<size_t>(fr * 0.9);
-    cudaEventCreateWithFlags(&c->ev_up, cudaEventDisableTiming);
-    cudaEventCreateWithFlags(&c->ev_ws, cudaEventDisableTiming);
-    if (const char* s = getenv("TALP_GPU_SWEEP_SHAPE")) c->shape = atoi(s) % kNumSweepShapes;
-    if (const char* s = getenv("TALP_GPU_TILES_PER_WARP")) c->min_tiles_per_warp = atoi(s) > 0 ? atoi(s) : 4;
-    *out = c;
-    return TALP_GPU_OK;
+int ceil_log2(uint64_t x) {
+    int b = 0;
+    while ((1ull << b) < x && b < 63) ++b;
+    return b;
 }
 
-talp_gpu_status talp_gpu_destroy(talp_gpu_ctx* c) {
-    if (!c) return TALP_GPU_OK;
-    cudaSetDevice(c->device);
-    cudaDeviceSynchronize();
-    for (auto& kv : c->traces) free_trace(c, kv.second);
-    c->traces.clear();
-    dev_free(c, c->ws.p, c->ws.cap);
-    dev_free(c, c->stage.p, c->stage.cap);
-    dev_free(c, c->sortbuf.p, c->sortbuf.cap);
-    if (c->up.p) cudaFreeHost(c->up.p);
-    if (c->down.p) cudaFreeHost(c->down.p);
-    if (c->ev_up) cudaEventDestroy(c->ev_up);
-    if (c->ev_ws) cudaEventDestroy(c->ev_ws);
-    for (auto& pr : c->ev_pending) {
-        cudaEventDestroy(pr.first);
-        cudaEventDestroy(pr.second);
-    }
-    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
-    delete c;
-    return TALP_GPU_OK;
+// size class of an ingest for the tuning cache
+uint64_t size_class(uint64_t records, uint64_t segs, bool sorting) {
+    return (static_cast<uint64_t>(ceil_log2(records + 1)) << 16) | (static_cast<uint64_t>(ceil_log2(segs + 1)) << 1) |
+           (sorting ? 1u : 0u);
 }
 
-talp_gpu_status talp_gpu_ingest_events(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches, size_t nb,
-                                       void* stream_) {
-    if (!c) return fail(TALP_GPU_EINVAL, "null context");
-    if (nb == 0) return TALP_GPU_OK;
-    if (!batches) return fail(TALP_GPU_EINVAL, "null batches");
-    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
-    TALP_CUDA(cudaSetDevice(c->device));
-
-    // ---- host-side validation and admission (nothing changes on failure)
-    std::vector<uint64_t> nh(nb), nd(nb);
-    std::vector<uint32_t> mm(nb);
+// Validation, sizes and workspace layout of an ingest (no side effects).
+talp_gpu_status size_ingest(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches, size_t nb, const Tuning& tu,
+                            bool with_finalize, Layout& L) {
+    const int shape = tu.shape, tpw = tu.tpw;
+    L = Layout();
+    L.nh.resize(nb);
+    L.nd.resize(nb);
+    L.mm.resize(nb);
     std::unordered_set<uint64_t> seen;
-    size_t new_bytes = 0, stage_bytes = 0;
-    uint64_t n_segs = 0, n_records = 0;
-    uint32_t rmax = 1;
     for (size_t k = 0; k < nb; ++k) {
         const talp_gpu_trace_batch& b = batches[k];
-        talp_gpu_status st = check_batch(c, b, &nh[k], &nd[k], &mm[k]);
-        if (st != TALP_GPU_OK) return st;
+        TALP_TRY(check_batch(b, &L.nh[k], &L.nd[k], &L.mm[k]));
         if (!seen.insert(b.trace_id).second) return fail(TALP_GPU_EINVAL, "trace id repeated in one call");
         auto it = c->traces.find(b.trace_id);
         if (b.flags & TALP_GPU_APPEND) {
             if (it == c->traces.end()) return fail(TALP_GPU_ENOTFOUND, "APPEND to an unknown trace");
-            TraceState* t = it->second;
-            if (t->n != b.n_ranks || t->R != b.n_regions ||
-                memcmp(t->dpr.data(), b.devices_per_rank, sizeof(uint32_t) * b.n_ranks) != 0)
-                return fail(TALP_GPU_EINVAL, "APPEND with a different trace shape");
-        } else {
-            bool reuse = it != c->traces.end() && it->second->n == b.n_ranks && it->second->R == b.n_regions &&
-                         memcmp(it->second->dpr.data(), b.devices_per_rank, sizeof(uint32_t) * b.n_ranks) == 0;
-            if (!reuse) {
-                new_bytes += trace_bytes(b.n_ranks, mm[k], b.n_regions);
-                if (it != c->traces.end()) new_bytes -= std::min(new_bytes, it->second->dbytes);
-            }
+            if (!same_shape(it->second, b)) return fail(TALP_GPU_EINVAL, "APPEND with a different trace shape");
+        } else if (it == c->traces.end() || !same_shape(it->second, b)) {
+            if (it != c->traces.end() && it->second->plan_refs)
+                return fail(TALP_GPU_EBUSY, "a plan uses this trace id with another shape");
+            L.new_bytes += trace_bytes(b.n_ranks, L.mm[k], b.n_regions);
         }
-        if (!(b.flags & TALP_GPU_DEVICE_PTRS)) stage_bytes += nh[k] * 16 + nd[k] * 16 + align_up(nh[k], 16) + align_up(nd[k], 16) + 64;
-        n_segs += mm[k] + b.n_ranks;
-        n_records += nh[k] + nd[k];
-        rmax = std::max(rmax, b.n_regions);
+        if (!(b.flags & TALP_GPU_DEVICE_PTRS))
+            L.stage_bytes += L.nh[k] * 16 + L.nd[k] * 16 + align_up(L.nh[k], 16) + align_up(L.nd[k], 16) + 64;
+        L.n_segs += L.mm[k] + b.n_ranks;
+        L.n_records += L.nh[k] + L.nd[k];
+        L.n_dev_segs += L.mm[k];
+        L.rmax = std::max(L.rmax, b.n_regions);
+        if (with_finalize) L.n_fin += b.n_regions;
+        if (!(b.flags & TALP_GPU_SORTED_BY_START)) {
+            L.sort_slots += L.mm[k];
+            L.sort_recs += L.nd[k];
+            for (uint32_t g = 0; g < L.mm[k]; ++g)
+                L.sort_tiles += (b.dev_off[g + 1] - b.dev_off[g] + sort_tile_records() - 1) / sort_tile_records();
+            if ((b.flags & TALP_GPU_APPEND) && L.mm[k]) L.n_backup_words += 3ull * b.n_regions * L.mm[k];
+        }
     }
-    if (n_segs > 0xFFFFFFF0ull) return fail(TALP_GPU_EINVAL, "too many segments in one call");
+    if (L.n_segs > 0xFFFFFFF0ull) return fail(TALP_GPU_EINVAL, "too many segments in one call");
+    L.sorting = L.sort_slots > 0;
+    L.sortbuf_bytes = L.sorting ? 2 * (align_up(16 * L.sort_recs, 256) + align_up(L.sort_recs + 64, 256)) : 0;
 
-    // sort stage sizes: device segments of batches that do not assert start order
-    uint64_t sort_slots = 0, sort_recs = 0, sort_tiles = 0, n_dev_segs = 0;
-    size_t n_backup_words = 0;
-    for (size_t k = 0; k < nb; ++k) {
-        const talp_gpu_trace_batch& b = batches[k];
-        n_dev_segs += mm[k];
-        if (b.flags & TALP_GPU_SORTED_BY_START) continue;
-        sort_slots += mm[k];
-        sort_recs += nd[k];
-        for (uint32_t g = 0; g < mm[k]; ++g)
-            sort_tiles += (b.dev_off[g + 1] - b.dev_off[g] + sort_tile_records() - 1) / sort_tile_records();
-        if ((b.flags & TALP_GPU_APPEND) && mm[k]) n_backup_words += 3ull * b.n_regions * mm[k];
-    }
-    const bool sorting = sort_slots > 0;
-    const size_t sortbuf_bytes = sorting ? 2 * (align_up(16 * sort_recs, 256) + align_up(sort_recs + 64, 256)) : 0;
-
-    // workspace layout (device): [segs][seg_start][fill jobs][payload][wrec][seg_flags][gstatus]
-    const int shape = c->shape;
-    const int tile = sweep_tile(shape);
-    const int warps = kSweepShapes[shape].warps;
-    int cps = sweep_ctas_per_sm(shape, static_cast<int>(rmax));
+    L.shape = shape;
+    L.tpw = tpw;
+    L.seg_cost = tu.seg_cost;
+    L.virt = L.n_records + L.seg_cost * L.n_segs;
+    L.tile = sweep_tile(shape);
+    L.warps = kSweepShapes[shape].warps;
+    const int cps = sweep_ctas_per_sm(shape, static_cast<int>(L.rmax));
     if (cps <= 0) return fail(TALP_GPU_ECUDA, "sweep kernel cannot be resident");
-    const uint64_t tiles = (n_records + tile - 1) / tile;
-    uint64_t want_warps = (tiles + c->min_tiles_per_warp - 1) / c->min_tiles_per_warp;
-    const uint64_t max_warps = static_cast<uint64_t>(c->num_sms) * cps * warps;
-    if (want_warps > max_warps) want_warps = max_warps;
-    if (want_warps < 1) want_warps = 1;
-    const int grid = static_cast<int>((want_warps + warps - 1) / warps);
-    const int full_grid = static_cast<int>(max_warps / warps);   // re-sweep: size unknown on the host
-    const uint32_t n_wrec = static_cast<uint32_t>(grid) * warps;
-    const uint32_t n_wrec_cap = static_cast<uint32_t>(sorting ? std::max(grid, full_grid) : grid) * warps;
+    const uint64_t tiles = (L.virt + L.tile - 1) / L.tile;
+    uint64_t want = (tiles + tpw - 1) / tpw;
+    const uint64_t max_warps = static_cast<uint64_t>(c->num_sms) * cps * L.warps;
+    want = std::min(std::max<uint64_t>(want, 1), max_warps);
+    L.grid = static_cast<int>((want + L.warps - 1) / L.warps);
+    L.full_grid = static_cast<int>(max_warps / L.warps);
+    L.n_wrec = static_cast<uint32_t>(L.grid) * L.warps;
+    L.n_wrec_cap = static_cast<uint32_t>(L.sorting ? std::max(L.grid, L.full_grid) : L.grid) * L.warps;
 
-    // payload per trace: hwin [n][R][2], dev_rank [m] (only at creation), TraceDev
-    size_t payload_words = 0;
     for (size_t k = 0; k < nb; ++k)
-        payload_words += 2ull * batches[k].n_ranks * batches[k].n_regions + mm[k] + sizeof(TraceDev) / 8;
-    const size_t n_jobs_max = 8 * nb + 2;   // <= 8 per trace + seg flags + status
-    size_t off_segs = 0;
-    size_t off_start = align_up(off_segs + sizeof(SegDesc) * n_segs, 256);
-    size_t off_jobs = align_up(off_start + sizeof(uint64_t) * (n_segs + 1), 256);
-    size_t off_rest = align_up(off_jobs + sizeof(FillJob) * n_jobs_max, 256);
-    size_t off_sctl = align_up(off_rest + sizeof(int64_t*) * (sorting ? n_segs : 0), 256);
-    size_t off_pay = align_up(off_sctl + sizeof(SortCtl), 256);
-    size_t up_bytes = align_up(off_pay + 8 * payload_words, 256);
-    // device-only part
-    size_t off_wrec = up_bytes;
-    size_t off_flags = align_up(off_wrec + sizeof(WarpRec) * n_wrec_cap, 256);
-    size_t off_gst = align_up(off_flags + sizeof(uint32_t) * (n_segs + 1), 256);
-    size_t off_bk = align_up(off_gst + 256, 256);
-    size_t off_slist = align_up(off_bk + 8 * n_backup_words, 256);
-    size_t off_srb = align_up(off_slist + 4 * sort_slots, 256);
-    size_t off_stb = align_up(off_srb + 8 * sort_slots, 256);
-    size_t off_smn = align_up(off_stb + 8 * (sort_slots + 1), 256);
-    size_t off_smx = align_up(off_smn + 8 * sort_slots, 256);
-    size_t off_hist = align_up(off_smx + 8 * sort_slots, 256);
-    size_t off_offs = align_up(off_hist + 4 * 256 * sort_tiles, 256);
-    size_t off_rsegs = align_up(off_offs + 8 * 256 * sort_tiles, 256);
-    size_t off_rstart = align_up(off_rsegs + sizeof(SegDesc) * (sorting ? n_dev_segs : 0), 256);
-    size_t ws_bytes = align_up(off_rstart + 8 * (sorting ? n_dev_segs + 1 : 0), 256);
+        L.payload_words += 2ull * batches[k].n_ranks * batches[k].n_regions + L.mm[k] + sizeof(TraceDev) / 8;
+    L.n_jobs_max = 8 * nb + 2;   // <= 8 per trace + seg flags + status
+    L.off_segs = 0;
+    L.off_start = align_up(L.off_segs + sizeof(SegDesc) * L.n_segs, 256);
+    L.off_send = align_up(L.off_start + sizeof(uint64_t) * (L.n_segs + 1), 256);
+    L.off_jobs = align_up(L.off_send + sizeof(uint64_t) * (L.n_segs + 1), 256);
+    L.off_rest = align_up(L.off_jobs + sizeof(FillJob) * L.n_jobs_max, 256);
+    L.off_sctl = align_up(L.off_rest + sizeof(int64_t*) * (L.sorting ? L.n_segs : 0), 256);
+    L.off_fin = align_up(L.off_sctl + sizeof(SortCtl), 256);
+    L.off_pay = align_up(L.off_fin + sizeof(FinalizeJob) * L.n_fin, 256);
+    L.up_bytes = align_up(L.off_pay + 8 * L.payload_words, 256);
+    L.off_wrec = L.up_bytes;
+    L.off_flags = align_up(L.off_wrec + sizeof(WarpRec) * L.n_wrec_cap, 256);
+    L.off_gst = align_up(L.off_flags + sizeof(uint32_t) * (L.n_segs + 2), 256);
+    L.off_bk = align_up(L.off_gst + 256, 256);
+    L.off_slist = align_up(L.off_bk + 8 * L.n_backup_words, 256);
+    L.off_srb = align_up(L.off_slist + 4 * L.sort_slots, 256);
+    L.off_stb = align_up(L.off_srb + 8 * L.sort_slots, 256);
+    L.off_smn = align_up(L.off_stb + 8 * (L.sort_slots + 1), 256);
+    L.off_smx = align_up(L.off_smn + 8 * L.sort_slots, 256);
+    L.off_hist = align_up(L.off_smx + 8 * L.sort_slots, 256);
+    L.off_offs = align_up(L.off_hist + 4 * 256 * L.sort_tiles, 256);
+    L.off_rsegs = align_up(L.off_offs + 8 * 256 * L.sort_tiles, 256);
+    L.off_rstart = align_up(L.off_rsegs + sizeof(SegDesc) * (L.sorting ? L.n_dev_segs : 0), 256);
+    L.off_rrend = align_up(L.off_rstart + 8 * (L.sorting ? L.n_dev_segs + 1 : 0), 256);
+    L.off_mout = align_up(L.off_rrend + 8 * (L.sorting ? L.n_dev_segs + 1 : 0), 256);
+    L.ws_bytes = align_up(L.off_mout + sizeof(MetricsOut) * L.n_fin, 256);
+    return TALP_GPU_OK;
+}
 
-    size_t extra = new_bytes;
-    if (c->ws.cap < ws_bytes) extra += align_up(ws_bytes + ws_bytes / 4, 1 << 20) - c->ws.cap;
-    if (c->stage.cap < stage_bytes) extra += align_up(stage_bytes + stage_bytes / 4, 1 << 20) - c->stage.cap;
-    if (c->sortbuf.cap < sortbuf_bytes)
-        extra += align_up(sortbuf_bytes + sortbuf_bytes / 4, 1 << 20) - c->sortbuf.cap;
-    if (c->held + extra > c->budget)
-        return fail(TALP_GPU_ENOMEM, "admission: the ingest needs " + std::to_string(extra) +
-                                         " more device bytes than the budget leaves");
-
-    // previous ingest must be done with the workspace/staging before reuse
-    if (c->ws_used) TALP_CUDA(cudaStreamWaitEvent(stream, c->ev_ws, 0));
-    talp_gpu_status st = grow(c, c->ws, ws_bytes);
-    if (st != TALP_GPU_OK) return st;
-    if (stage_bytes) {
-        st = grow(c, c->stage, stage_bytes);
-        if (st != TALP_GPU_OK) return st;
-    }
-    if (sortbuf_bytes) {
-        st = grow(c, c->sortbuf, sortbuf_bytes);
-        if (st != TALP_GPU_OK) return st;
-    }
-    TALP_CUDA(cudaEventSynchronize(c->ev_up));   // upload scratch no longer read by a pending copy
-    st = grow_pinned(c->up, up_bytes);
-    if (st != TALP_GPU_OK) return st;
-
-    // ---- trace states
-    std::vector<TraceState*> ts(nb);
+// Find, reuse or create the trace states of an ingest.
+talp_gpu_status get_traces(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches, size_t nb, cudaStream_t stream,
+                           std::vector<TraceState*>& ts) {
+    ts.assign(nb, nullptr);
     for (size_t k = 0; k < nb; ++k) {
         const talp_gpu_trace_batch& b = batches[k];
         auto it = c->traces.find(b.trace_id);
-        if (it != c->traces.end() && it->second->n == b.n_ranks && it->second->R == b.n_regions &&
-            memcmp(it->second->dpr.data(), b.devices_per_rank, sizeof(uint32_t) * b.n_ranks) == 0) {
+        if (it != c->traces.end() && same_shape(it->second, b)) {
             ts[k] = it->second;
             continue;
         }
@@ -443,19 +418,27 @@ talp_gpu_status talp_gpu_ingest_events(talp_gpu_ctx* c, const talp_gpu_trace_bat
             c->traces.erase(it);
         }
         TraceState* t = nullptr;
-        st = alloc_trace(c, b.trace_id, b.n_ranks, b.devices_per_rank, b.n_regions, &t);
-        if (st != TALP_GPU_OK) return st;
+        TALP_TRY(alloc_trace(c, b.trace_id, b.n_ranks, b.devices_per_rank, b.n_regions, &t));
         c->traces[b.trace_id] = t;
         ts[k] = t;
     }
+    return TALP_GPU_OK;
+}
 
-    // ---- host-pointer records: copy into staging
-    char* up = static_cast<char*>(c->up.p);
-    char* wsd = static_cast<char*>(c->ws.p);
+const uint8_t* floor16(const uint8_t* p) {
+    return reinterpret_cast<const uint8_t*>(reinterpret_cast<uintptr_t>(p) & ~static_cast<uintptr_t>(15));
+}
+
+// Write the upload part of the workspace (segment table, starts, jobs,
+// payload, sort control, finalize jobs) into `up`, with device addresses in
+// the workspace `wsd`.  Host-pointer records are copied into `stg` on
+// `stream`.  `mout_user`: where finalize writes (null: the workspace).
+talp_gpu_status fill_ingest(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches, size_t nb, Layout& L,
+                            const std::vector<TraceState*>& ts, char* up, char* wsd, char* stg, char* sortbuf,
+                            cudaStream_t stream) {
     std::vector<const int64_t*> hse(nb), dse(nb);
     std::vector<const uint8_t*> hst(nb), dtg(nb), hst_end(nb), dtg_end(nb);
     size_t so = 0;
-    char* stg = static_cast<char*>(c->stage.p);
     for (size_t k = 0; k < nb; ++k) {
         const talp_gpu_trace_batch& b = batches[k];
         if (b.flags & TALP_GPU_DEVICE_PTRS) {
@@ -473,33 +456,32 @@ talp_gpu_status talp_gpu_ingest_events(talp_gpu_ctx* c, const talp_gpu_trace_bat
                 so = align_up(so + bytes, 16);
                 return d;
             };
-            char* a = put(b.host_se, nh[k] * 16);
-            char* bb = put(b.dev_se, nd[k] * 16);
-            char* cc = put(b.host_state, nh[k]);
-            char* dd = put(b.dev_tag, nd[k]);
+            char* a = put(b.host_se, L.nh[k] * 16);
+            char* bb = put(b.dev_se, L.nd[k] * 16);
+            char* cc = put(b.host_state, L.nh[k]);
+            char* dd = put(b.dev_tag, L.nd[k]);
             if (!a || !bb || !cc || !dd) return cuda_fail(cudaGetLastError(), "cudaMemcpyAsync (records)");
             hse[k] = reinterpret_cast<const int64_t*>(a);
             dse[k] = reinterpret_cast<const int64_t*>(bb);
             hst[k] = reinterpret_cast<const uint8_t*>(cc);
             dtg[k] = reinterpret_cast<const uint8_t*>(dd);
         }
-        auto floor16 = [](const uint8_t* p) {
-            return reinterpret_cast<const uint8_t*>(reinterpret_cast<uintptr_t>(p) & ~static_cast<uintptr_t>(15));
-        };
-        hst_end[k] = floor16(hst[k] + nh[k]);
-        dtg_end[k] = floor16(dtg[k] + nd[k]);
+        hst_end[k] = floor16(hst[k] + L.nh[k]);
+        dtg_end[k] = floor16(dtg[k] + L.nd[k]);
     }
 
-    // ---- segment table, fill jobs, payload (one upload)
-    SegDesc* sd = reinterpret_cast<SegDesc*>(up + off_segs);
-    uint64_t* sstart = reinterpret_cast<uint64_t*>(up + off_start);
-    FillJob* jobs = reinterpret_cast<FillJob*>(up + off_jobs);
-    int64_t* pay = reinterpret_cast<int64_t*>(up + off_pay);
-    int64_t* pay_dev = reinterpret_cast<int64_t*>(wsd + off_pay);
-    uint32_t* seg_flags = reinterpret_cast<uint32_t*>(wsd + off_flags);
-    uint32_t* gstatus = reinterpret_cast<uint32_t*>(wsd + off_gst);
-    const int64_t** restore = reinterpret_cast<const int64_t**>(up + off_rest);
-    size_t pw = 0, bk_used = 0;
+    SegDesc* sd = reinterpret_cast<SegDesc*>(up + L.off_segs);
+    uint64_t* sstart = reinterpret_cast<uint64_t*>(up + L.off_start);
+    uint64_t* send = reinterpret_cast<uint64_t*>(up + L.off_send);
+    FillJob* jobs = reinterpret_cast<FillJob*>(up + L.off_jobs);
+    const int64_t** restore = reinterpret_cast<const int64_t**>(up + L.off_rest);
+    FinalizeJob* fin = reinterpret_cast<FinalizeJob*>(up + L.off_fin);
+    int64_t* pay = reinterpret_cast<int64_t*>(up + L.off_pay);
+    int64_t* pay_dev = reinterpret_cast<int64_t*>(wsd + L.off_pay);
+    uint32_t* seg_flags = reinterpret_cast<uint32_t*>(wsd + L.off_flags);
+    uint32_t* gstatus = reinterpret_cast<uint32_t*>(wsd + L.off_gst);
+    MetricsOut* mout = reinterpret_cast<MetricsOut*>(wsd + L.off_mout);
+    size_t pw = 0, bk_used = 0, nf = 0;
     uint32_t nj = 0;
     uint64_t si = 0, pos = 0;
     for (size_t k = 0; k < nb; ++k) {
@@ -507,9 +489,9 @@ talp_gpu_status talp_gpu_ingest_events(talp_gpu_ctx* c, const talp_gpu_trace_bat
         TraceState* t = ts[k];
         const bool append = (b.flags & TALP_GPU_APPEND) != 0;
         const uint32_t n = t->n, m = t->m, R = t->R;
-        int64_t* bkd = nullptr;   // pre-ingest device sums (APPEND + sorting)
         int64_t* cin = t->carry[t->cur];
         int64_t* cout = t->carry[t->cur ^ 1];
+        int64_t* bkd = nullptr;   // pre-ingest device sums (APPEND + sorting)
         // windows: transpose [R][n][2] -> [n][R][2]
         int64_t* hw = pay + pw;
         for (uint32_t i = 0; i < n; ++i)
@@ -551,37 +533,42 @@ talp_gpu_status talp_gpu_ingest_events(talp_gpu_ctx* c, const talp_gpu_trace_bat
             if (!(b.flags & TALP_GPU_SORTED_BY_START) && m) {
                 // a device segment that gets sorted is re-swept from its sums
                 // before this slice: keep a copy of them
-                bkd = reinterpret_cast<int64_t*>(wsd + off_bk) + bk_used;
+                bkd = reinterpret_cast<int64_t*>(wsd + L.off_bk) + bk_used;
                 bk_used += 3ull * R * m;
                 jobs[nj++] = FillJob{bkd, 3ull * m * R, 0, t->dsum};
             }
         }
-        const uint8_t seg_flags0 = (b.flags & TALP_GPU_SORTED_BY_START) ? 0 : kSegSortable;
+        for (uint32_t r = 0; r < R && L.n_fin; ++r) {
+            fin[nf] = FinalizeJob{t->tdev, mout + nf, r, 0};
+            ++nf;
+        }
+        const uint8_t sflag = (b.flags & TALP_GPU_SORTED_BY_START) ? 0 : kSegSortable;
         // device segments, then host segments
         for (uint32_t g = 0; g < m; ++g) {
             SegDesc& s = sd[si];
+            memset(&s, 0, sizeof(SegDesc));
             const uint64_t o = b.dev_off[g];
             s.se = dse[k] + 2 * o;
             s.tag = dtg[k] + o;
             s.tag_limit = dtg_end[k];
             s.sums = t->dsum + static_cast<size_t>(g) * R * 3;
-            uint32_t rank = static_cast<uint32_t>(dr[g]);
-            s.win = t->hwin + static_cast<size_t>(rank) * R * 2;
+            s.win = t->hwin + static_cast<size_t>(dr[g]) * R * 2;
             s.status = t->status;
             s.carry_in = cin + 3ull * g;
             s.carry_out = cout + 3ull * g;
             s.n = b.dev_off[g + 1] - o;
             s.R = static_cast<uint16_t>(R);
             s.is_host = 0;
-            memset(s.pad, 0, sizeof(s.pad));
-            s.pad[0] = seg_flags0;
-            if (sorting) restore[si] = bkd ? bkd + static_cast<size_t>(g) * R * 3 : nullptr;
+            s.pad[0] = sflag;
+            if (L.sorting) restore[si] = bkd ? bkd + static_cast<size_t>(g) * R * 3 : nullptr;
             sstart[si] = pos;
-            pos += s.n;
+            send[si] = pos + s.n;
+            pos += s.n + L.seg_cost;
             ++si;
         }
         for (uint32_t i = 0; i < n; ++i) {
             SegDesc& s = sd[si];
+            memset(&s, 0, sizeof(SegDesc));
             const uint64_t o = b.host_off[i];
             s.se = hse[k] + 2 * o;
             s.tag = hst[k] + o;
@@ -589,85 +576,244 @@ talp_gpu_status talp_gpu_ingest_events(talp_gpu_ctx* c, const talp_gpu_trace_bat
             s.sums = t->hsum + static_cast<size_t>(i) * R * 3;
             s.win = t->hwin + static_cast<size_t>(i) * R * 2;
             s.status = t->status;
-            s.carry_in = nullptr;
-            s.carry_out = nullptr;
             s.n = b.host_off[i + 1] - o;
             s.R = static_cast<uint16_t>(R);
             s.is_host = 1;
-            memset(s.pad, 0, sizeof(s.pad));
+            if (L.sorting) restore[si] = nullptr;
             sstart[si] = pos;
-            pos += s.n;
+            send[si] = pos + s.n;
+            pos += s.n + L.seg_cost;
             ++si;
         }
     }
     sstart[si] = pos;
-    jobs[nj++] = FillJob{reinterpret_cast<int64_t*>(seg_flags), (n_segs + 2) / 2, 0, nullptr};
+    send[si] = pos;
+    jobs[nj++] = FillJob{reinterpret_cast<int64_t*>(seg_flags), (L.n_segs + 2) / 2, 0, nullptr};
     jobs[nj++] = FillJob{reinterpret_cast<int64_t*>(gstatus), 1, 0, nullptr};
-    if (nj > n_jobs_max || pw > payload_words || si != n_segs || bk_used > n_backup_words)
+    if (nj > L.n_jobs_max || pw > L.payload_words || si != L.n_segs || bk_used > L.n_backup_words || nf != L.n_fin)
         return fail(TALP_GPU_ECUDA, "internal: upload table overflow");
-    if (sorting) {
+    L.nj = nj;
+    if (L.sorting) {
         SortCtl sc{};
-        sc.list = reinterpret_cast<uint32_t*>(wsd + off_slist);
-        sc.rec_base = reinterpret_cast<uint64_t*>(wsd + off_srb);
-        sc.tile_base = reinterpret_cast<uint64_t*>(wsd + off_stb);
-        sc.mn = reinterpret_cast<int64_t*>(wsd + off_smn);
-        sc.mx = reinterpret_cast<int64_t*>(wsd + off_smx);
-        sc.hist = reinterpret_cast<uint32_t*>(wsd + off_hist);
-        sc.offs = reinterpret_cast<uint64_t*>(wsd + off_offs);
-        char* sb = static_cast<char*>(c->sortbuf.p);
-        const size_t se_b = align_up(16 * sort_recs, 256), tg_b = align_up(sort_recs + 64, 256);
+        sc.list = reinterpret_cast<uint32_t*>(wsd + L.off_slist);
+        sc.rec_base = reinterpret_cast<uint64_t*>(wsd + L.off_srb);
+        sc.tile_base = reinterpret_cast<uint64_t*>(wsd + L.off_stb);
+        sc.mn = reinterpret_cast<int64_t*>(wsd + L.off_smn);
+        sc.mx = reinterpret_cast<int64_t*>(wsd + L.off_smx);
+        sc.hist = reinterpret_cast<uint32_t*>(wsd + L.off_hist);
+        sc.offs = reinterpret_cast<uint64_t*>(wsd + L.off_offs);
+        const size_t se_b = align_up(16 * L.sort_recs, 256), tg_b = align_up(L.sort_recs + 64, 256);
         for (int q = 0; q < 2; ++q) {
-            char* base = sb + q * (se_b + tg_b);
+            char* base = sortbuf + q * (se_b + tg_b);
             sc.buf_se[q] = reinterpret_cast<int64_t*>(base);
             sc.buf_tag[q] = reinterpret_cast<uint8_t*>(base + se_b);
-            sc.buf_tag_limit[q] = reinterpret_cast<const uint8_t*>(
-                reinterpret_cast<uintptr_t>(base + se_b + tg_b) & ~static_cast<uintptr_t>(15));
+            sc.buf_tag_limit[q] = floor16(reinterpret_cast<const uint8_t*>(base + se_b + tg_b));
         }
-        sc.restore = reinterpret_cast<const int64_t* const*>(wsd + off_rest);
-        memcpy(up + off_sctl, &sc, sizeof(SortCtl));
+        sc.restore = reinterpret_cast<const int64_t* const*>(wsd + L.off_rest);
+        memcpy(up + L.off_sctl, &sc, sizeof(SortCtl));
     }
+    (void)c;
+    return TALP_GPU_OK;
+}
 
-    TALP_CUDA(cudaMemcpyAsync(wsd, up, up_bytes, cudaMemcpyHostToDevice, stream));
-    TALP_CUDA(cudaEventRecord(c->ev_up, stream));
-
-    // ---- launches
-    TALP_CUDA(launch_prep(reinterpret_cast<const FillJob*>(wsd + off_jobs), nj, stream));
-    ++c->kernel_launches;
-    const SegDesc* dsegs = reinterpret_cast<const SegDesc*>(wsd + off_segs);
-    const uint64_t* dstart = reinterpret_cast<const uint64_t*>(wsd + off_start);
-    WarpRec* wrec = reinterpret_cast<WarpRec*>(wsd + off_wrec);
-    if (n_records > 0) {
+// Upload and the launch sequence of an ingest (capturable).
+talp_gpu_status enqueue_ingest(talp_gpu_ctx* c, const Layout& L, const char* up, char* wsd, cudaStream_t stream,
+                               bool profile, uint64_t* launches, bool upload = true) {
+    uint64_t nl = 0;
+    if (upload) TALP_CUDA(cudaMemcpyAsync(wsd, up, L.up_bytes, cudaMemcpyHostToDevice, stream));
+    TALP_CUDA(launch_prep(reinterpret_cast<const FillJob*>(wsd + L.off_jobs), L.nj, stream));
+    ++nl;
+    const SegDesc* dsegs = reinterpret_cast<const SegDesc*>(wsd + L.off_segs);
+    const uint64_t* dstart = reinterpret_cast<const uint64_t*>(wsd + L.off_start);
+    const uint64_t* dsend = reinterpret_cast<const uint64_t*>(wsd + L.off_send);
+    WarpRec* wrec = reinterpret_cast<WarpRec*>(wsd + L.off_wrec);
+    uint32_t* seg_flags = reinterpret_cast<uint32_t*>(wsd + L.off_flags);
+    uint32_t* gstatus = reinterpret_cast<uint32_t*>(wsd + L.off_gst);
+    if (L.n_records > 0) {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (c->profiling) {
+        if (profile) {
             e0 = take_event(c);
             e1 = take_event(c);
             TALP_CUDA(cudaEventRecord(e0, stream));
         }
-        TALP_CUDA(launch_sweep(shape, static_cast<int>(rmax), grid, dsegs, dstart, static_cast<uint32_t>(n_segs), wrec,
-                               seg_flags, gstatus, c->wait_limit, stream));
-        if (c->profiling) {
+        TALP_CUDA(launch_sweep(L.shape, static_cast<int>(L.rmax), L.grid, dsegs, dstart, dsend,
+                               static_cast<uint32_t>(L.n_segs), wrec, seg_flags, gstatus, c->wait_limit, stream));
+        if (profile) {
             TALP_CUDA(cudaEventRecord(e1, stream));
             c->ev_pending.emplace_back(e0, e1);
-            c->ev_records.push_back(n_records);
+            c->ev_records.push_back(L.n_records);
         }
-        TALP_CUDA(launch_fixup(dsegs, dstart, wrec, n_wrec, seg_flags, stream));
-        c->kernel_launches += 2;
-        if (sorting) {
+        TALP_CUDA(launch_fixup(dsegs, dstart, wrec, L.n_wrec, seg_flags, stream));
+        nl += 2;
+        if (L.sorting) {
             // a2: sort the device segments found out of order, re-sweep them
-            SortCtl* sctl = reinterpret_cast<SortCtl*>(wsd + off_sctl);
-            SegDesc* rsegs = reinterpret_cast<SegDesc*>(wsd + off_rsegs);
-            uint64_t* rstart = reinterpret_cast<uint64_t*>(wsd + off_rstart);
-            const uint64_t gt = std::min<uint64_t>(sort_tiles, static_cast<uint64_t>(c->num_sms) * 8);
-            const uint64_t gs = std::min<uint64_t>(sort_slots, static_cast<uint64_t>(c->num_sms) * 4);
-            TALP_CUDA(launch_sort_stage(dsegs, static_cast<uint32_t>(n_segs), static_cast<uint32_t>(n_dev_segs),
-                                        seg_flags, sctl, rsegs, rstart, static_cast<int>(std::max<uint64_t>(gt, 1)),
+            SortCtl* sctl = reinterpret_cast<SortCtl*>(wsd + L.off_sctl);
+            SegDesc* rsegs = reinterpret_cast<SegDesc*>(wsd + L.off_rsegs);
+            uint64_t* rstart = reinterpret_cast<uint64_t*>(wsd + L.off_rstart);
+            uint64_t* rrend = reinterpret_cast<uint64_t*>(wsd + L.off_rrend);
+            const uint64_t gt = std::min<uint64_t>(L.sort_tiles, static_cast<uint64_t>(c->num_sms) * 8);
+            const uint64_t gs = std::min<uint64_t>(L.sort_slots, static_cast<uint64_t>(c->num_sms) * 4);
+            TALP_CUDA(launch_sort_stage(dsegs, static_cast<uint32_t>(L.n_segs), static_cast<uint32_t>(L.n_dev_segs),
+                                        seg_flags, sctl, rsegs, rstart, rrend,
+                                        static_cast<int>(std::max<uint64_t>(gt, 1)),
                                         static_cast<int>(std::max<uint64_t>(gs, 1)), stream));
-            TALP_CUDA(launch_sweep(shape, static_cast<int>(rmax), full_grid, rsegs, rstart,
-                                   static_cast<uint32_t>(n_dev_segs), wrec, seg_flags, gstatus, c->wait_limit, stream));
-            TALP_CUDA(launch_fixup(rsegs, rstart, wrec, static_cast<uint32_t>(full_grid) * warps, seg_flags, stream));
-            c->kernel_launches += 2 + 24 + 1 + 2;
+            TALP_CUDA(launch_sweep(L.shape, static_cast<int>(L.rmax), L.full_grid, rsegs, rstart, rrend,
+                                   static_cast<uint32_t>(L.n_dev_segs), wrec, seg_flags, gstatus, c->wait_limit,
+                                   stream));
+            TALP_CUDA(launch_fixup(rsegs, rstart, wrec, static_cast<uint32_t>(L.full_grid) * L.warps, seg_flags,
+                                   stream));
+            nl += 2 + 24 + 1 + 2;
         }
     }
+    if (L.n_fin) {
+        TALP_CUDA(launch_finalize(reinterpret_cast<const FinalizeJob*>(wsd + L.off_fin),
+                                  static_cast<uint32_t>(L.n_fin), stream));
+        ++nl;
+    }
+    if (launches) *launches = nl;
+    return TALP_GPU_OK;
+}
+
+talp_gpu_status check_metrics_flags(const talp_gpu_metrics* out, size_t n) {
+    for (size_t k = 0; k < n; ++k) {
+        const uint32_t f = out[k].flags;
+        if (f & TALP_GPU_M_TIMEOUT) return fail(TALP_GPU_ETIMEDOUT, "a device-side wait ran out during ingest");
+        if (f & (TALP_GPU_M_INVALID | TALP_GPU_M_UNSORTED))
+            return fail(TALP_GPU_EINVAL, (f & TALP_GPU_M_INVALID) ? "invalid record (end < start or bad kind/state)"
+                                                                 : "device records out of start order");
+    }
+    return TALP_GPU_OK;
+}
+
+// Default segment cost in records: a segment switch costs about two tiles
+// of streaming, more with more regions (tiles of short segments straddle
+// most region boundaries).
+uint64_t default_seg_cost(uint32_t rmax) { return 512 + 64ull * rmax; }
+
+Tuning pick_tuning(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches, size_t nb) {
+    Tuning tu = c->defaults;
+    uint32_t rmax = 1;
+    for (size_t k = 0; k < nb; ++k) rmax = std::max(rmax, batches[k].n_regions);
+    if (!tu.seg_cost) tu.seg_cost = default_seg_cost(rmax);
+    if (c->shape_forced || c->tune.empty()) return tu;
+    uint64_t recs = 0, segs = 0;
+    bool sorting = false;
+    for (size_t k = 0; k < nb; ++k) {
+        const talp_gpu_trace_batch& b = batches[k];
+        uint64_t m = 0;
+        for (uint32_t i = 0; i < b.n_ranks; ++i) m += b.devices_per_rank[i];
+        recs += b.host_off[b.n_ranks] + b.dev_off[m];
+        segs += m + b.n_ranks;
+        sorting |= !(b.flags & TALP_GPU_SORTED_BY_START);
+    }
+    auto it = c->tune.find(size_class(recs, segs, sorting));
+    if (it != c->tune.end()) tu = it->second;
+    return tu;
+}
+
+}  // namespace
+
+// ===================================================================== ABI
+
+extern "C" {
+
+const char* talp_gpu_last_error(void) { return g_last_error.c_str(); }
+
+talp_gpu_status talp_gpu_create(talp_gpu_ctx** out, int device, size_t hbm_budget_bytes) {
+    if (!out) return fail(TALP_GPU_EINVAL, "null out");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(TALP_GPU_EINVAL, "bad device index");
+    TALP_CUDA(cudaSetDevice(device));
+    talp_gpu_ctx* c = new talp_gpu_ctx();
+    c->device = device;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    c->budget = hbm_budget_bytes ? hbm_budget_bytes : static_cast<size_t>(fr * 0.9);
+    cudaEventCreateWithFlags(&c->ev_up, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&c->ev_ws, cudaEventDisableTiming);
+    cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    // overrides of the sweep tuning (benchmarks and tests)
+    if (const char* s = getenv("TALP_GPU_SWEEP_SHAPE")) {
+        c->defaults.shape = atoi(s) % kNumSweepShapes;
+        c->shape_forced = true;
+    }
+    if (const char* s = getenv("TALP_GPU_TILES_PER_WARP")) {
+        c->defaults.tpw = atoi(s) > 0 ? atoi(s) : 4;
+        c->shape_forced = true;
+    }
+    if (const char* s = getenv("TALP_GPU_SEG_COST")) {
+        c->defaults.seg_cost = strtoull(s, nullptr, 10);
+        c->shape_forced = true;
+    }
+    *out = c;
+    return TALP_GPU_OK;
+}
+
+talp_gpu_status talp_gpu_destroy(talp_gpu_ctx* c) {
+    if (!c) return TALP_GPU_OK;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    for (auto& kv : c->traces) free_trace(c, kv.second);
+    c->traces.clear();
+    dev_free(c, c->ws.p, c->ws.cap);
+    dev_free(c, c->stage.p, c->stage.cap);
+    dev_free(c, c->sortbuf.p, c->sortbuf.cap);
+    if (c->up.p) cudaFreeHost(c->up.p);
+    if (c->down.p) cudaFreeHost(c->down.p);
+    if (c->ev_up) cudaEventDestroy(c->ev_up);
+    if (c->ev_ws) cudaEventDestroy(c->ev_ws);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    for (auto& pr : c->ev_pending) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    delete c;
+    return TALP_GPU_OK;
+}
+
+talp_gpu_status talp_gpu_ingest_events(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches, size_t nb,
+                                       void* stream_) {
+    if (!c) return fail(TALP_GPU_EINVAL, "null context");
+    if (nb == 0) return TALP_GPU_OK;
+    if (!batches) return fail(TALP_GPU_EINVAL, "null batches");
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    TALP_CUDA(cudaSetDevice(c->device));
+
+    Layout L;
+    TALP_TRY(size_ingest(c, batches, nb, pick_tuning(c, batches, nb), false, L));
+
+    // admission: everything this ingest would add, before any allocation
+    size_t extra = L.new_bytes;
+    if (c->ws.cap < L.ws_bytes) extra += grow_size(L.ws_bytes) - c->ws.cap;
+    if (c->stage.cap < L.stage_bytes) extra += grow_size(L.stage_bytes) - c->stage.cap;
+    if (c->sortbuf.cap < L.sortbuf_bytes) extra += grow_size(L.sortbuf_bytes) - c->sortbuf.cap;
+    if (c->held + extra > c->budget)
+        return fail(TALP_GPU_ENOMEM, "admission: the ingest needs " + std::to_string(extra) +
+                                         " more device bytes than the budget leaves");
+
+    // the previous ingest must be done with the workspace/staging before reuse
+    if (c->ws_used) TALP_CUDA(cudaStreamWaitEvent(stream, c->ev_ws, 0));
+    TALP_TRY(grow(c, c->ws, L.ws_bytes));
+    if (L.stage_bytes) TALP_TRY(grow(c, c->stage, L.stage_bytes));
+    if (L.sortbuf_bytes) TALP_TRY(grow(c, c->sortbuf, L.sortbuf_bytes));
+    TALP_CUDA(cudaEventSynchronize(c->ev_up));   // upload scratch no longer read by a pending copy
+    TALP_TRY(grow_pinned(c->up, L.up_bytes));
+
+    std::vector<TraceState*> ts;
+    TALP_TRY(get_traces(c, batches, nb, stream, ts));
+    char* up = static_cast<char*>(c->up.p);
+    char* wsd = static_cast<char*>(c->ws.p);
+    TALP_TRY(fill_ingest(c, batches, nb, L, ts, up, wsd, static_cast<char*>(c->stage.p),
+                         static_cast<char*>(c->sortbuf.p), stream));
+    uint64_t nl = 0;
+    TALP_TRY(enqueue_ingest(c, L, up, wsd, stream, c->profiling, &nl));
+    c->kernel_launches += nl;
+    TALP_CUDA(cudaEventRecord(c->ev_up, stream));
     TALP_CUDA(cudaEventRecord(c->ev_ws, stream));
     c->ws_used = true;
     for (size_t k = 0; k < nb; ++k) ts[k]->cur ^= 1;
@@ -681,57 +827,43 @@ static talp_gpu_status finalize_common(talp_gpu_ctx* c, const uint64_t* ids, siz
     if (n == 0) return TALP_GPU_OK;
     TALP_CUDA(cudaSetDevice(c->device));
     std::vector<FinalizeJob> jobs;
-    std::vector<TraceState*> ts;
     for (size_t k = 0; k < n; ++k) {
         auto it = c->traces.find(ids[k]);
         if (it == c->traces.end()) return fail(TALP_GPU_ENOTFOUND, "unknown trace id " + std::to_string(ids[k]));
         TraceState* t = it->second;
         if (region == TALP_GPU_ALL_REGIONS) {
             if (n != 1) return fail(TALP_GPU_EINVAL, "TALP_GPU_ALL_REGIONS takes one trace");
-            for (uint32_t r = 0; r < t->R; ++r) {
-                jobs.push_back(FinalizeJob{t->tdev, out_dev_user ? out_dev_user + r : t->metrics + r, r, 0});
-                ts.push_back(t);
-            }
+            for (uint32_t r = 0; r < t->R; ++r) jobs.push_back(FinalizeJob{t->tdev, nullptr, r, 0});
         } else {
             if (region >= t->R) return fail(TALP_GPU_EINVAL, "region out of range");
-            jobs.push_back(FinalizeJob{t->tdev, out_dev_user ? out_dev_user + k : t->metrics + region, region, 0});
-            ts.push_back(t);
+            jobs.push_back(FinalizeJob{t->tdev, nullptr, region, 0});
         }
     }
-    const size_t jb = sizeof(FinalizeJob) * jobs.size();
-    TALP_CUDA(cudaEventSynchronize(c->ev_up));
-    talp_gpu_status st = grow_pinned(c->up, jb);
-    if (st != TALP_GPU_OK) return st;
+    const size_t nj = jobs.size();
+    const size_t jb = align_up(sizeof(FinalizeJob) * nj, 256);
     if (c->ws_used) TALP_CUDA(cudaStreamWaitEvent(stream, c->ev_ws, 0));
-    st = grow(c, c->ws, jb + 256);
-    if (st != TALP_GPU_OK) return st;
-    memcpy(c->up.p, jobs.data(), jb);
-    TALP_CUDA(cudaMemcpyAsync(c->ws.p, c->up.p, jb, cudaMemcpyHostToDevice, stream));
+    TALP_TRY(grow(c, c->ws, jb + sizeof(MetricsOut) * nj));
+    MetricsOut* res = reinterpret_cast<MetricsOut*>(static_cast<char*>(c->ws.p) + jb);
+    for (size_t k = 0; k < nj; ++k) jobs[k].out = out_dev_user ? out_dev_user + k : res + k;
+    TALP_CUDA(cudaEventSynchronize(c->ev_up));
+    TALP_TRY(grow_pinned(c->up, jb));
+    memcpy(c->up.p, jobs.data(), sizeof(FinalizeJob) * nj);
+    TALP_CUDA(cudaMemcpyAsync(c->ws.p, c->up.p, sizeof(FinalizeJob) * nj, cudaMemcpyHostToDevice, stream));
     TALP_CUDA(cudaEventRecord(c->ev_up, stream));
-    TALP_CUDA(launch_finalize(static_cast<const FinalizeJob*>(c->ws.p), static_cast<uint32_t>(jobs.size()), stream));
+    TALP_CUDA(launch_finalize(static_cast<const FinalizeJob*>(c->ws.p), static_cast<uint32_t>(nj), stream));
     ++c->kernel_launches;
+    if (!sync) {
+        TALP_CUDA(cudaEventRecord(c->ev_ws, stream));
+        c->ws_used = true;
+        return TALP_GPU_OK;
+    }
+    TALP_TRY(grow_pinned(c->down, sizeof(MetricsOut) * nj));
+    TALP_CUDA(cudaMemcpyAsync(c->down.p, res, sizeof(MetricsOut) * nj, cudaMemcpyDeviceToHost, stream));
     TALP_CUDA(cudaEventRecord(c->ev_ws, stream));
     c->ws_used = true;
-    if (!sync) return TALP_GPU_OK;
-    st = grow_pinned(c->down, sizeof(MetricsOut) * jobs.size());
-    if (st != TALP_GPU_OK) return st;
-    MetricsOut* dn = static_cast<MetricsOut*>(c->down.p);
-    for (size_t k = 0; k < jobs.size(); ++k)
-        TALP_CUDA(cudaMemcpyAsync(dn + k, jobs[k].out, sizeof(MetricsOut), cudaMemcpyDeviceToHost, stream));
     TALP_CUDA(cudaStreamSynchronize(stream));
-    memcpy(out_host, dn, sizeof(MetricsOut) * jobs.size());
-    talp_gpu_status res = TALP_GPU_OK;
-    for (size_t k = 0; k < jobs.size(); ++k) {
-        const uint32_t f = out_host[k].flags;
-        if (f & TALP_GPU_M_TIMEOUT) {
-            if (res == TALP_GPU_OK) res = fail(TALP_GPU_ETIMEDOUT, "a device-side wait ran out during ingest");
-        } else if (f & (TALP_GPU_M_INVALID | TALP_GPU_M_UNSORTED)) {
-            if (res == TALP_GPU_OK)
-                res = fail(TALP_GPU_EINVAL, (f & TALP_GPU_M_INVALID) ? "invalid record (end < start or bad kind/state)"
-                                                                     : "device records out of start order");
-        }
-    }
-    return res;
+    memcpy(out_host, c->down.p, sizeof(MetricsOut) * nj);
+    return check_metrics_flags(out_host, nj);
 }
 
 talp_gpu_status talp_gpu_region_metrics(talp_gpu_ctx* c, uint64_t trace_id, uint32_t region,
@@ -780,12 +912,15 @@ talp_gpu_status talp_gpu_reset(talp_gpu_ctx* c, uint64_t trace_id) {
     TALP_CUDA(cudaSetDevice(c->device));
     TALP_CUDA(cudaDeviceSynchronize());
     if (trace_id == TALP_GPU_ALL) {
+        for (auto& kv : c->traces)
+            if (kv.second->plan_refs) return fail(TALP_GPU_EBUSY, "a plan uses one of the traces");
         for (auto& kv : c->traces) free_trace(c, kv.second);
         c->traces.clear();
         return TALP_GPU_OK;
     }
     auto it = c->traces.find(trace_id);
     if (it == c->traces.end()) return fail(TALP_GPU_ENOTFOUND, "unknown trace id");
+    if (it->second->plan_refs) return fail(TALP_GPU_EBUSY, "a plan uses this trace");
     free_trace(c, it->second);
     c->traces.erase(it);
     return TALP_GPU_OK;
@@ -823,6 +958,190 @@ talp_gpu_status talp_gpu_memory(talp_gpu_ctx* c, size_t* held, size_t* budget) {
     if (!c) return fail(TALP_GPU_EINVAL, "null context");
     if (held) *held = c->held;
     if (budget) *budget = c->budget;
+    return TALP_GPU_OK;
+}
+
+// ------------------------------------------------------------------- plans
+
+static void plan_release(talp_gpu_plan* p) {
+    if (!p) return;
+    talp_gpu_ctx* c = p->c;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    for (TraceState* t : p->ts)
+        if (t) --t->plan_refs;
+    dev_free(c, p->ws.p, p->ws.cap);
+    dev_free(c, p->sortbuf.p, p->sortbuf.cap);
+    if (p->up.p) cudaFreeHost(p->up.p);
+    delete p;
+}
+
+talp_gpu_status talp_gpu_plan_create(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches, size_t nb,
+                                     uint32_t plan_flags, talp_gpu_plan** out) {
+    if (!c || !out || (nb && !batches)) return fail(TALP_GPU_EINVAL, "null argument");
+    *out = nullptr;
+    if (nb == 0) return fail(TALP_GPU_EINVAL, "a plan needs at least one trace");
+    if (plan_flags & ~TALP_GPU_PLAN_AUTOTUNE) return fail(TALP_GPU_EINVAL, "unknown plan flag bits");
+    for (size_t k = 0; k < nb; ++k) {
+        if (!(batches[k].flags & TALP_GPU_DEVICE_PTRS) || (batches[k].flags & TALP_GPU_APPEND))
+            return fail(TALP_GPU_EINVAL, "a plan takes device-resident records and no APPEND");
+    }
+    TALP_CUDA(cudaSetDevice(c->device));
+    cudaStream_t s = c->cap_stream;
+
+    // candidate tunings (all sized first, so admission sees the largest):
+    // every sweep shape x segment costs {1/4, 1, 4} of the default
+    std::vector<Tuning> cand;
+    const Tuning base = pick_tuning(c, batches, nb);
+    if ((plan_flags & TALP_GPU_PLAN_AUTOTUNE) && !c->shape_forced) {
+        for (int sh = 0; sh < kNumSweepShapes; ++sh)
+            for (uint64_t mul : {1ull, 4ull, 16ull}) {
+                Tuning t = base;
+                t.shape = sh;
+                t.seg_cost = base.seg_cost * mul / 4;
+                cand.push_back(t);
+            }
+    } else {
+        cand.push_back(base);
+    }
+    std::vector<Layout> Ls(cand.size());
+    size_t ws_max = 0, up_max = 0, sb_max = 0;
+    for (size_t q = 0; q < cand.size(); ++q) {
+        TALP_TRY(size_ingest(c, batches, nb, cand[q], true, Ls[q]));
+        ws_max = std::max(ws_max, Ls[q].ws_bytes);
+        up_max = std::max(up_max, Ls[q].up_bytes);
+        sb_max = std::max(sb_max, Ls[q].sortbuf_bytes);
+    }
+    const size_t extra = Ls[0].new_bytes + grow_size(ws_max) + (sb_max ? grow_size(sb_max) : 0);
+    if (c->held + extra > c->budget)
+        return fail(TALP_GPU_ENOMEM, "admission: the plan needs " + std::to_string(extra) +
+                                         " more device bytes than the budget leaves");
+    if (c->ws_used) TALP_CUDA(cudaStreamWaitEvent(s, c->ev_ws, 0));
+
+    talp_gpu_plan* p = new talp_gpu_plan();
+    p->c = c;
+    talp_gpu_status st = get_traces(c, batches, nb, s, p->ts);
+    if (st == TALP_GPU_OK) st = grow(c, p->ws, ws_max);
+    if (st == TALP_GPU_OK && sb_max) st = grow(c, p->sortbuf, sb_max);
+    if (st == TALP_GPU_OK) st = grow_pinned(p->up, up_max);
+    if (st != TALP_GPU_OK) {
+        plan_release(p);
+        return st;
+    }
+    for (TraceState* t : p->ts) ++t->plan_refs;
+    char* up = static_cast<char*>(p->up.p);
+    char* wsd = static_cast<char*>(p->ws.p);
+
+    // autotune: time each candidate's launch sequence
+    size_t best = 0;
+    if (cand.size() > 1) {
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best_ms = 1e30f;
+        for (size_t q = 0; q < cand.size() && st == TALP_GPU_OK; ++q) {
+            st = fill_ingest(c, batches, nb, Ls[q], p->ts, up, wsd, nullptr, static_cast<char*>(p->sortbuf.p), s);
+            for (int it = 0; it < 4 && st == TALP_GPU_OK; ++it) {   // 1 warm-up (with upload), 3 timed
+                if (it == 1) cudaEventRecord(e0, s);
+                st = enqueue_ingest(c, Ls[q], up, wsd, s, false, nullptr, it == 0);
+            }
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = q;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (st != TALP_GPU_OK) {
+            plan_release(p);
+            return st;
+        }
+        const Layout& B = Ls[best];
+        c->tune[size_class(B.n_records, B.n_segs, B.sorting)] = cand[best];
+    }
+    p->L = Ls[best];
+    p->n_metrics = p->L.n_fin;
+
+    // The tables do not change between launches: upload them once, then
+    // capture the kernels (every launch re-initialises what they write).
+    st = fill_ingest(c, batches, nb, p->L, p->ts, up, wsd, nullptr, static_cast<char*>(p->sortbuf.p), s);
+    if (st == TALP_GPU_OK) {
+        cudaError_t e = cudaMemcpyAsync(wsd, up, p->L.up_bytes, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamBeginCapture");
+    }
+    if (st == TALP_GPU_OK) {
+        talp_gpu_status st2 = enqueue_ingest(c, p->L, up, wsd, s, false, &p->launches_per_run, false);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(s, &g);
+        if (st2 != TALP_GPU_OK) {
+            if (g) cudaGraphDestroy(g);
+            st = st2;
+        } else if (e != cudaSuccess) {
+            st = cuda_fail(e, "cudaStreamEndCapture");
+        } else {
+            p->graph = g;
+            e = cudaGraphInstantiate(&p->exec, g, 0);
+            if (e != cudaSuccess) st = cuda_fail(e, "cudaGraphInstantiate");
+        }
+    }
+    if (st != TALP_GPU_OK) {
+        plan_release(p);
+        return st;
+    }
+    // after a launch the carries of these traces are in carry[cur ^ 1]
+    for (TraceState* t : p->ts) t->cur ^= 1;
+    *out = p;
+    return TALP_GPU_OK;
+}
+
+talp_gpu_status talp_gpu_plan_launch(talp_gpu_plan* p, void* stream) {
+    if (!p) return fail(TALP_GPU_EINVAL, "null plan");
+    TALP_CUDA(cudaSetDevice(p->c->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (p->c->ws_used) TALP_CUDA(cudaStreamWaitEvent(s, p->c->ev_ws, 0));
+    TALP_CUDA(cudaGraphLaunch(p->exec, s));
+    p->c->kernel_launches += p->launches_per_run;
+    TALP_CUDA(cudaEventRecord(p->c->ev_ws, s));
+    p->c->ws_used = true;
+    return TALP_GPU_OK;
+}
+
+talp_gpu_status talp_gpu_plan_metrics(talp_gpu_plan* p, talp_gpu_metrics* out_host, void* stream) {
+    if (!p || !out_host) return fail(TALP_GPU_EINVAL, "null argument");
+    TALP_CUDA(cudaSetDevice(p->c->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const MetricsOut* mout = reinterpret_cast<const MetricsOut*>(static_cast<char*>(p->ws.p) + p->L.off_mout);
+    TALP_CUDA(cudaMemcpyAsync(out_host, mout, sizeof(MetricsOut) * p->n_metrics, cudaMemcpyDeviceToHost, s));
+    TALP_CUDA(cudaStreamSynchronize(s));
+    return check_metrics_flags(out_host, p->n_metrics);
+}
+
+talp_gpu_status talp_gpu_plan_info(talp_gpu_plan* p, talp_gpu_plan_stats* out) {
+    if (!p || !out) return fail(TALP_GPU_EINVAL, "null argument");
+    out->n_metrics = p->n_metrics;
+    out->records = p->L.n_records;
+    out->segments = p->L.n_segs;
+    out->kernels_per_launch = static_cast<uint32_t>(p->launches_per_run);
+    out->sweep_items = kSweepShapes[p->L.shape].items;
+    out->sweep_warps = kSweepShapes[p->L.shape].warps;
+    out->sweep_stages = kSweepShapes[p->L.shape].stages;
+    out->tiles_per_warp = static_cast<uint32_t>(p->L.tpw);
+    out->sweep_grid = static_cast<uint32_t>(p->L.grid);
+    out->reserved = 0;
+    return TALP_GPU_OK;
+}
+
+talp_gpu_status talp_gpu_plan_destroy(talp_gpu_plan* p) {
+    if (!p) return TALP_GPU_OK;
+    cudaSetDevice(p->c->device);
+    cudaDeviceSynchronize();
+    plan_release(p);
     return TALP_GPU_OK;
 }
 

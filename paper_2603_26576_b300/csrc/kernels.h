@@ -25,9 +25,12 @@ extern const SweepShape kSweepShapes[kNumSweepShapes];
 int sweep_ctas_per_sm(int shape, int rmax);
 int sweep_tile(int shape);
 
+// seg_start[s]: virtual start of segment s (n_segs + 1 entries, the last the
+// total); seg_rend[s]: virtual end of its records (start + records).  The
+// gap up to seg_start[s + 1] is the segment's share of fixed cost.
 cudaError_t launch_sweep(int shape, int rmax, int grid, const SegDesc* segs, const uint64_t* seg_start,
-                         uint32_t n_segs, WarpRec* wrec, uint32_t* seg_flags, uint32_t* gstatus, int64_t wait_limit,
-                         cudaStream_t stream);
+                         const uint64_t* seg_rend, uint32_t n_segs, WarpRec* wrec, uint32_t* seg_flags,
+                         uint32_t* gstatus, int64_t wait_limit, cudaStream_t stream);
 
 cudaError_t launch_fixup(const SegDesc* segs, const uint64_t* seg_start, const WarpRec* wrec, uint32_t n_wrec,
                          uint32_t* seg_flags, cudaStream_t stream);
@@ -40,8 +43,8 @@ cudaError_t launch_finalize(const FinalizeJob* jobs, uint32_t n_jobs, cudaStream
 // then the segment table of their sorted copies for the re-sweep.
 // n_segs: entries of `segs`; n_slots: device segments (upper bound of flagged).
 cudaError_t launch_sort_stage(const SegDesc* segs, uint32_t n_segs, uint32_t n_slots, const uint32_t* seg_flags,
-                              SortCtl* ctl, SegDesc* resweep_segs, uint64_t* resweep_start, int grid_tiles,
-                              int grid_segs, cudaStream_t stream);
+                              SortCtl* ctl, SegDesc* resweep_segs, uint64_t* resweep_start, uint64_t* resweep_rend,
+                              int grid_tiles, int grid_segs, cudaStream_t stream);
 int sort_tile_records();
 
 // Message returned by talp_gpu_last_error() on this thread.

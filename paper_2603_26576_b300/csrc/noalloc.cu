@@ -38,7 +38,8 @@ constexpr size_t al(size_t x) { return (x + 255) / 256 * 256; }
 // scratch layout (byte offsets); the first part is uploaded from the host
 constexpr size_t kOffSegs = 0;
 constexpr size_t kOffStart = al(kOffSegs + sizeof(SegDesc) * kMaxUnits);
-constexpr size_t kOffJobs = al(kOffStart + sizeof(uint64_t) * (kMaxUnits + 1));
+constexpr size_t kOffEnd = al(kOffStart + sizeof(uint64_t) * (kMaxUnits + 1));
+constexpr size_t kOffJobs = al(kOffEnd + sizeof(uint64_t) * (kMaxUnits + 1));
 constexpr size_t kOffFin = al(kOffJobs + sizeof(FillJob) * kMaxJobs);
 constexpr size_t kOffWin = al(kOffFin + sizeof(FinalizeJob) * kMaxR);
 constexpr size_t kOffRank = al(kOffWin + sizeof(int64_t) * 2 * kMaxR * kMaxUnits);
@@ -125,6 +126,7 @@ extern "C" talp_gpu_status talp_gpu_reduce_noalloc(const talp_gpu_trace_batch* b
 
     SegDesc* sd = reinterpret_cast<SegDesc*>(H + kOffSegs);
     uint64_t* sstart = reinterpret_cast<uint64_t*>(H + kOffStart);
+    uint64_t* send = reinterpret_cast<uint64_t*>(H + kOffEnd);
     FillJob* jobs = reinterpret_cast<FillJob*>(H + kOffJobs);
     FinalizeJob* fin = reinterpret_cast<FinalizeJob*>(H + kOffFin);
     int64_t* hwin_h = reinterpret_cast<int64_t*>(H + kOffWin);
@@ -167,7 +169,10 @@ extern "C" talp_gpu_status talp_gpu_reduce_noalloc(const talp_gpu_trace_batch* b
         reinterpret_cast<uintptr_t>(b->host_state + nh) & ~static_cast<uintptr_t>(15));
     const uint8_t* dlim = reinterpret_cast<const uint8_t*>(
         reinterpret_cast<uintptr_t>(b->dev_tag + nd) & ~static_cast<uintptr_t>(15));
-    uint64_t pos = 0;
+    // virtual positions: records plus a fixed cost per segment (balances
+    // segment switches across warps)
+    const uint64_t seg_cost = 512 + 64ull * R;
+    uint64_t pos = 0, nrec = 0;
     uint32_t si = 0;
     for (uint32_t g = 0; g < m; ++g, ++si) {
         SegDesc& s = sd[si];
@@ -185,7 +190,9 @@ extern "C" talp_gpu_status talp_gpu_reduce_noalloc(const talp_gpu_trace_batch* b
         s.R = static_cast<uint16_t>(R);
         s.is_host = 0;
         sstart[si] = pos;
-        pos += s.n;
+        send[si] = pos + s.n;
+        pos += s.n + seg_cost;
+        nrec += s.n;
     }
     for (uint32_t i = 0; i < n; ++i, ++si) {
         SegDesc& s = sd[si];
@@ -201,9 +208,12 @@ extern "C" talp_gpu_status talp_gpu_reduce_noalloc(const talp_gpu_trace_batch* b
         s.R = static_cast<uint16_t>(R);
         s.is_host = 1;
         sstart[si] = pos;
-        pos += s.n;
+        send[si] = pos + s.n;
+        pos += s.n + seg_cost;
+        nrec += s.n;
     }
     sstart[si] = pos;
+    send[si] = pos;
     const uint32_t n_segs = si;
 
     // what must start at zero (the array keeps the previous call's contents)
@@ -235,11 +245,12 @@ extern "C" talp_gpu_status talp_gpu_reduce_noalloc(const talp_gpu_trace_batch* b
 
     cudaError_t e = cudaMemcpyAsync(S, H, kUploadBytes, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = launch_prep(reinterpret_cast<const FillJob*>(S + kOffJobs), nj, stream);
-    if (e == cudaSuccess && pos > 0)
+    if (e == cudaSuccess && nrec > 0)
         e = launch_sweep(shape, static_cast<int>(R), grid, reinterpret_cast<const SegDesc*>(S + kOffSegs),
-                         reinterpret_cast<const uint64_t*>(S + kOffStart), n_segs, wrec, flags, gstatus,
+                         reinterpret_cast<const uint64_t*>(S + kOffStart),
+                         reinterpret_cast<const uint64_t*>(S + kOffEnd), n_segs, wrec, flags, gstatus,
                          4000000000LL, stream);
-    if (e == cudaSuccess && pos > 0)
+    if (e == cudaSuccess && nrec > 0)
         e = launch_fixup(reinterpret_cast<const SegDesc*>(S + kOffSegs),
                          reinterpret_cast<const uint64_t*>(S + kOffStart), wrec, n_wrec, flags, stream);
     if (e == cudaSuccess) e = launch_finalize(reinterpret_cast<const FinalizeJob*>(S + kOffFin), R, stream);

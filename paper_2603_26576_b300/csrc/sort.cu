@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(const SegDes
 // sorted copy; slots nflag .. n_slots-1 are empty segments.
 __global__ void __launch_bounds__(256) sort_resweep_plan_kernel(const SegDesc* __restrict__ segs, SortCtl* ctl,
                                                                 SegDesc* out, uint64_t* out_start,
-                                                                uint32_t n_slots) {
+                                                                uint64_t* out_rend, uint32_t n_slots) {
     const uint32_t nflag = ctl->nflag;
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k <= n_slots; k += gridDim.x * blockDim.x) {
         if (k == n_slots) {
@@ -313,6 +313,7 @@ __global__ void __launch_bounds__(256) sort_resweep_plan_kernel(const SegDesc* _
             s.tag_limit = ctl->buf_tag_limit[b];
             out[k] = s;
             out_start[k] = ctl->rec_base[k];
+            out_rend[k] = ctl->rec_base[k] + s.n;
         } else {
             SegDesc s = segs[0];
             s.n = 0;
@@ -320,6 +321,7 @@ __global__ void __launch_bounds__(256) sort_resweep_plan_kernel(const SegDesc* _
             s.R = 0;
             out[k] = s;
             out_start[k] = ctl->nrec;
+            out_rend[k] = ctl->nrec;
         }
     }
 }
@@ -327,8 +329,8 @@ __global__ void __launch_bounds__(256) sort_resweep_plan_kernel(const SegDesc* _
 }  // namespace
 
 cudaError_t launch_sort_stage(const SegDesc* segs, uint32_t n_segs, uint32_t n_slots, const uint32_t* seg_flags,
-                              SortCtl* ctl, SegDesc* resweep_segs, uint64_t* resweep_start, int grid_tiles,
-                              int grid_segs, cudaStream_t stream) {
+                              SortCtl* ctl, SegDesc* resweep_segs, uint64_t* resweep_start, uint64_t* resweep_rend,
+                              int grid_tiles, int grid_segs, cudaStream_t stream) {
     if (n_slots == 0) return cudaSuccess;
     sort_plan_kernel<<<1, 1024, 0, stream>>>(segs, n_segs, seg_flags, ctl);
     sort_minmax_kernel<<<grid_tiles, kSortThreads, 0, stream>>>(segs, ctl);
@@ -339,7 +341,7 @@ cudaError_t launch_sort_stage(const SegDesc* segs, uint32_t n_segs, uint32_t n_s
     }
     const int g = static_cast<int>((n_slots + 1 + 255) / 256);
     sort_resweep_plan_kernel<<<g < 1024 ? g : 1024, 256, 0, stream>>>(segs, ctl, resweep_segs, resweep_start,
-                                                                       n_slots);
+                                                                       resweep_rend, n_slots);
     return cudaGetLastError();
 }
 

@@ -64,30 +64,46 @@ struct SweepCfg {
     static constexpr int SMEM = WARPS * WARP_BYTES;
 };
 
+// The ingest's segments occupy one virtual index space: segment s owns
+// [seg_start[s], seg_start[s+1]); its records sit at [seg_start[s],
+// seg_rend[s]) and the positions after them are phantoms that only carry the
+// segment's fixed cost (descriptor, windows, carries, flush), so that equal
+// slices balance records and segment switches alike.
+//
 // Position of a warp inside its slice: current tile start, current segment,
-// end of the current portion (segment end or slice end).
+// end of the current portion (the segment's last record or the slice end).
 struct Walk {
     uint64_t pos, seg_end, seg_base;
     uint32_t seg;
 };
 
-__device__ __forceinline__ void walk_enter(Walk& w, const uint64_t* __restrict__ seg_start, uint64_t r1) {
-    while (seg_start[w.seg + 1] <= w.pos) ++w.seg;   // skip empty segments
-    w.seg_base = seg_start[w.seg];
-    const uint64_t e = seg_start[w.seg + 1];
-    w.seg_end = e < r1 ? e : r1;
-}
-
-// Returns true when the walk moved into a new segment.
-__device__ __forceinline__ bool walk_advance(Walk& w, uint32_t len, const uint64_t* __restrict__ seg_start,
-                                             uint64_t r1) {
-    w.pos += len;
-    if (w.pos < r1 && w.pos == w.seg_end) {
+// Move to the first record at or after w.pos (skipping phantoms and empty
+// segments); false when the slice [.., r1) holds no further record.
+__device__ __forceinline__ bool walk_enter(Walk& w, const uint64_t* __restrict__ seg_start,
+                                           const uint64_t* __restrict__ seg_rend, uint32_t n_segs, uint64_t r1) {
+    while (w.seg < n_segs) {
+        const uint64_t vs = seg_start[w.seg];
+        if (w.pos < vs) w.pos = vs;
+        if (w.pos >= r1) return false;
+        const uint64_t ve = seg_rend[w.seg];
+        if (w.pos < ve) {
+            w.seg_base = vs;
+            w.seg_end = ve < r1 ? ve : r1;
+            return true;
+        }
         ++w.seg;
-        walk_enter(w, seg_start, r1);
-        return true;
     }
     return false;
+}
+
+// Advance past a tile of len records; false when the slice is done.
+__device__ __forceinline__ bool walk_advance(Walk& w, uint32_t len, const uint64_t* __restrict__ seg_start,
+                                             const uint64_t* __restrict__ seg_rend, uint32_t n_segs, uint64_t r1) {
+    w.pos += len;
+    if (w.pos < w.seg_end) return true;
+    if (w.pos >= r1) return false;
+    ++w.seg;
+    return walk_enter(w, seg_start, seg_rend, n_segs, r1);
 }
 
 __device__ __forceinline__ uint32_t umax(uint32_t a, uint32_t b) { return a > b ? a : b; }
@@ -209,7 +225,8 @@ __device__ __forceinline__ void pieces64(const longlong2* sse, int base, const u
 
 template <int ITEMS, int WARPS, int STAGES, int RMAX, int MINB>
 __global__ void __launch_bounds__(WARPS * 32, MINB)
-    sweep_kernel(const SegDesc* __restrict__ segs, const uint64_t* __restrict__ seg_start, uint32_t n_segs,
+    sweep_kernel(const SegDesc* __restrict__ segs, const uint64_t* __restrict__ seg_start,
+                 const uint64_t* __restrict__ seg_rend, uint32_t n_segs,
                  WarpRec* __restrict__ wrec, uint32_t* __restrict__ seg_flags, uint32_t* __restrict__ gstatus,
                  int64_t wait_limit) {
     using C = SweepCfg<ITEMS, WARPS, STAGES>;
@@ -226,7 +243,17 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     const uint64_t r0 = (N * gw) / GW;
     const uint64_t r1 = (N * (gw + 1)) / GW;
 
-    if (r0 >= r1) {
+    // segment containing r0: the last index whose start is <= r0
+    uint32_t lo = 0, hi = n_segs;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (seg_start[mid] <= r0) lo = mid; else hi = mid;
+    }
+    Walk cw;
+    cw.pos = r0;
+    cw.seg = lo;
+    if (r0 >= r1 || !walk_enter(cw, seg_start, seg_rend, n_segs, r1)) {
+        // the slice holds no record (empty or phantom positions only)
         if (lane == 0) {
             WarpRec rec;
             rec.head_pos = r0;
@@ -239,13 +266,6 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
         return;
     }
 
-    // segment containing r0: the last index whose start is <= r0
-    uint32_t lo = 0, hi = n_segs;
-    while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (seg_start[mid] <= r0) lo = mid; else hi = mid;
-    }
-
     if (lane == 0) {
 #pragma unroll
         for (int st = 0; st < STAGES; ++st) mbar_init(&bars[st], 1);
@@ -254,10 +274,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     __syncwarp();
 
     // ---- producer (lane 0): its own walk over the same tile sequence
-    Walk iw;
-    iw.pos = r0;
-    iw.seg = lo;
-    walk_enter(iw, seg_start, r1);
+    Walk iw = cw;
     uint32_t n_issued = 0;
     bool iw_done = false;
     uint32_t iw_cached = NONE;
@@ -286,11 +303,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
         tma_load_1d(stage, iw_se + 2 * off, len * 16u, &bars[st]);
         if (tag_bytes) tma_load_1d(stage + C::SE_BYTES, reinterpret_cast<const void*>(tlo), tag_bytes, &bars[st]);
         ++n_issued;
-        if (iw.pos + len >= r1) {
-            iw_done = true;
-        } else {
-            walk_advance(iw, len, seg_start, r1);
-        }
+        if (!walk_advance(iw, len, seg_start, seg_rend, n_segs, r1)) iw_done = true;
     };
 
     if (lane == 0) {
@@ -298,12 +311,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     }
 
     // ---- consumers (all lanes): the same walk
-    Walk cw;
-    cw.pos = r0;
-    cw.seg = lo;
-    walk_enter(cw, seg_start, r1);
     if (lane == 0) {
-        wrec[gw].head_pos = r0;
+        wrec[gw].head_pos = cw.pos;
         wrec[gw].head_seg = cw.seg;
         wrec[gw].head_end = cw.seg_end;
     }
@@ -590,16 +599,18 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
         pbad |= bad;
         last_s = tile_last_s;
 
-        // advance; close the portion when the segment (or the slice) ends
-        const bool slice_done = cw.pos + static_cast<uint64_t>(len) >= r1;
-        const bool seg_done = slice_done || (cw.pos + static_cast<uint64_t>(len) == cw.seg_end);
+        // close the portion when the segment's records (or the slice) end
+        const bool seg_done = cw.pos + static_cast<uint64_t>(len) == cw.seg_end;
+        const uint32_t seg_now = cw.seg;
+        const bool more = walk_advance(cw, static_cast<uint32_t>(len), seg_start, seg_rend, n_segs, r1);
+        const bool slice_done = !more;
         if (seg_done) {
             if (lane < 3 * d_R && acc != 0) atomic_add64(&d_sums[lane], acc);
             const uint32_t bits = __reduce_or_sync(0xFFFFFFFFu, pbad);
             if (lane == 0) {
                 if (bits) {
                     atomicOr(d_status, bits);
-                    atomicOr(&seg_flags[cw.seg], bits);
+                    atomicOr(&seg_flags[seg_now], bits);
                 }
                 if (!d_host) {
                     atomic_max64(&d_cout[0], carryK);
@@ -611,7 +622,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
                     wrec[gw].head_M = carryM;
                 }
                 if (slice_done) {
-                    wrec[gw].tail_seg = cw.seg;
+                    wrec[gw].tail_seg = seg_now;
                     wrec[gw].tail_K = carryK;
                     wrec[gw].tail_M = carryM;
                 }
@@ -620,7 +631,6 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
             portion_open = false;
         }
         if (slice_done) break;
-        walk_advance(cw, static_cast<uint32_t>(len), seg_start, r1);
     }
 
     if (timed_out) {
@@ -638,20 +648,35 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
 
 // ---------------------------------------------------------------- dispatch
 
+// The dynamic shared-memory opt-in of one instantiation, set once per
+// process (sizing an ingest does it, so no attribute call happens while a
+// launch sequence is being captured into a graph).
 template <int ITEMS, int WARPS, int STAGES, int RMAX>
-static cudaError_t launch_t(int grid, const SegDesc* segs, const uint64_t* seg_start, uint32_t n_segs,
+static cudaError_t ensure_smem_attr() {
+    using C = SweepCfg<ITEMS, WARPS, STAGES>;
+    constexpr int MINB = WARPS == 8 ? 2 : 3;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<ITEMS, WARPS, STAGES, RMAX, MINB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    return cudaSuccess;
+}
+
+template <int ITEMS, int WARPS, int STAGES, int RMAX>
+static cudaError_t launch_t(int grid, const SegDesc* segs, const uint64_t* seg_start, const uint64_t* seg_rend,
+                            uint32_t n_segs,
                             WarpRec* wrec, uint32_t* seg_flags, uint32_t* gstatus, int64_t wait_limit,
                             cudaStream_t stream) {
     using C = SweepCfg<ITEMS, WARPS, STAGES>;
     constexpr int MINB = WARPS == 8 ? 2 : 3;
     auto k = sweep_kernel<ITEMS, WARPS, STAGES, RMAX, MINB>;
-    static bool attr_set = false;   // per-instantiation, set once per process
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    k<<<grid, WARPS * 32, C::SMEM, stream>>>(segs, seg_start, n_segs, wrec, seg_flags, gstatus, wait_limit);
+    cudaError_t e = ensure_smem_attr<ITEMS, WARPS, STAGES, RMAX>();
+    if (e != cudaSuccess) return e;
+    k<<<grid, WARPS * 32, C::SMEM, stream>>>(segs, seg_start, seg_rend, n_segs, wrec, seg_flags, gstatus,
+                                              wait_limit);
     return cudaGetLastError();
 }
 
@@ -660,7 +685,7 @@ static int occupancy_t() {
     using C = SweepCfg<ITEMS, WARPS, STAGES>;
     constexpr int MINB = WARPS == 8 ? 2 : 3;
     auto k = sweep_kernel<ITEMS, WARPS, STAGES, RMAX, MINB>;
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) != cudaSuccess) return 0;
+    if (ensure_smem_attr<ITEMS, WARPS, STAGES, RMAX>() != cudaSuccess) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, WARPS * 32, C::SMEM) != cudaSuccess) return 0;
     return n;
@@ -676,15 +701,15 @@ static int occupancy_t() {
     }
 
 #define TALP_LAUNCH(I, W, S, RM) \
-    launch_t<I, W, S, RM>(grid, segs, seg_start, n_segs, wrec, seg_flags, gstatus, wait_limit, stream)
+    launch_t<I, W, S, RM>(grid, segs, seg_start, seg_rend, n_segs, wrec, seg_flags, gstatus, wait_limit, stream)
 #define TALP_OCC(I, W, S, RM) occupancy_t<I, W, S, RM>()
 
 // The region count no longer shapes the kernel's registers (each lane owns
 // one (region, chain) accumulator), so one instantiation per shape serves
 // every R <= 8.
 cudaError_t launch_sweep(int shape, int rmax, int grid, const SegDesc* segs, const uint64_t* seg_start,
-                         uint32_t n_segs, WarpRec* wrec, uint32_t* seg_flags, uint32_t* gstatus, int64_t wait_limit,
-                         cudaStream_t stream) {
+                         const uint64_t* seg_rend, uint32_t n_segs, WarpRec* wrec, uint32_t* seg_flags,
+                         uint32_t* gstatus, int64_t wait_limit, cudaStream_t stream) {
     (void)rmax;
     TALP_SHAPE_SWITCH(shape, 8, TALP_LAUNCH)
     return cudaErrorInvalidValue;

@@ -375,6 +375,89 @@ def batched_trace(k, ranks, gpus, ev, seed=0x7A1F + 2, n_regions=8, threads=1):
     return t
 
 
+def batched_trace_fast(k, ranks, gpus, ev, seed=0x7A1F + 2, n_regions=8, ev_scale=1.0):
+    """One member of the batched workload, generated with whole-trace array
+    operations (one Philox stream per trace, so a trace, not a segment, is
+    the unit that can be regenerated alone).  Same laws as the small single
+    trace: one kernel stream at occupancy 0.7 with lognormal kernels times
+    the rank work factor, 30% copies (30% inside a kernel), back-to-back host
+    intervals padded with one offload interval to the rank window end."""
+    n = int(ranks[k])
+    g = int(gpus[k])
+    E = max(1, int(round(int(ev[k]) * ev_scale)))
+    m = n * g
+    rng = _rng(seed, k, D_TRACE, 3)
+    work = 0.7 + 0.3 * _rng(seed, k, D_SHAPE, 2).random(n)
+    wdev = np.repeat(work, g)[:, None]
+    n_k = max(1, int(round(0.7 * E)))
+    n_c = E - n_k
+    kd = np.maximum(np.rint(np.exp(rng.normal(math.log(20 * US), 1.0, (m, n_k))) * wdev), 1).astype(np.int64)
+    mean_k = 20 * US * math.exp(0.5) * wdev
+    gaps = np.rint(rng.exponential(1.0, (m, n_k)) * (mean_k * (1 - 0.7) / 0.7)).astype(np.int64)
+    ks = np.cumsum(gaps + kd, axis=1) - kd
+    ke = ks + kd
+    gap_next = np.empty_like(gaps)
+    gap_next[:, :-1] = gaps[:, 1:]
+    gap_next[:, -1] = np.rint(mean_k[:, 0] * (1 - 0.7) / 0.7).astype(np.int64)
+    if n_c > 0:
+        which = rng.integers(0, n_k, (m, n_c))
+        inside = rng.random((m, n_c)) < 0.3
+        u = rng.random((m, n_c))
+        rows = np.arange(m)[:, None]
+        cs = np.where(inside, ks[rows, which] + np.floor(u * kd[rows, which]).astype(np.int64),
+                      ke[rows, which] + np.floor(u * gap_next[rows, which]).astype(np.int64))
+        cd = np.maximum(np.rint(np.exp(rng.normal(math.log(8 * US), 0.7, (m, n_c)))), 1).astype(np.int64)
+        ckind = np.where(rng.random((m, n_c)) < 0.5, KIND_H2D, KIND_D2H).astype(np.uint8)
+        starts = np.concatenate([ks, cs], axis=1)
+        ends = np.concatenate([ke, cs + cd], axis=1)
+        tags = np.concatenate([np.zeros((m, n_k), np.uint8), (ckind << 5)], axis=1)
+    else:
+        starts, ends, tags = ks, ke, np.zeros((m, n_k), np.uint8)
+    order = np.argsort(starts, axis=1, kind="stable")
+    starts = np.take_along_axis(starts, order, 1)
+    ends = np.take_along_axis(ends, order, 1)
+    tags = np.take_along_axis(tags, order, 1)
+    dev_se = np.empty((m * E, 2), np.int64)
+    dev_se[:, 0] = starts.reshape(-1)
+    dev_se[:, 1] = ends.reshape(-1)
+    dev_end = ends.max(axis=1).reshape(n, g).max(axis=1)
+    # host: E intervals per rank + one padding interval
+    state = rng.integers(0, 3, (n, E)).astype(np.uint8)
+    means = np.array([HOST_MEANS_NS[0], HOST_MEANS_NS[1], HOST_MEANS_NS[2]], np.float64)[state]
+    dur = np.rint(rng.exponential(1.0, (n, E)) * means).astype(np.int64)
+    hend = np.cumsum(dur, axis=1)
+    T = np.maximum(np.maximum(hend[:, -1], dev_end), 1)
+    hs = np.empty((n, E + 1), np.int64)
+    he = np.empty((n, E + 1), np.int64)
+    hs[:, :E] = hend - dur
+    he[:, :E] = hend
+    hs[:, E] = hend[:, -1]
+    he[:, E] = T
+    hst = np.empty((n, E + 1), np.uint8)
+    hst[:, :E] = state
+    hst[:, E] = STATE_OFFLOAD
+    host_se = np.empty((n * (E + 1), 2), np.int64)
+    host_se[:, 0] = hs.reshape(-1)
+    host_se[:, 1] = he.reshape(-1)
+    return Trace(trace_id=k, n_ranks=n, devices_per_rank=np.full(n, g, np.uint32),
+                 region_window=nested_regions(T, n_regions), host_se=host_se, host_state=hst.reshape(-1),
+                 host_off=(np.arange(n + 1, dtype=np.uint64) * np.uint64(E + 1)),
+                 dev_se=dev_se, dev_tag=tags.reshape(-1).astype(np.uint8),
+                 dev_off=(np.arange(m + 1, dtype=np.uint64) * np.uint64(E)),
+                 sorted_by_start=True, meta=dict(workload="batched member", index=k, events_per_gpu=E))
+
+
+def batched_workload(n_traces=4096, ev_lo=5, ev_hi=5000, seed=0x7A1F + 2, n_regions=8, threads=None):
+    """The batched workload: n_traces traces with ranks log-uniform in
+    [1, 512], GPUs per rank uniform in [1, 8], events per GPU (= host
+    intervals per rank) log-uniform in [ev_lo, ev_hi]."""
+    ranks, gpus, ev = batched_shapes(seed=seed, n_traces=n_traces, ev_lo=ev_lo, ev_hi=ev_hi)
+    if threads is None:
+        threads = min(32, os.cpu_count() or 1)
+    return _pool_map(lambda k: batched_trace_fast(k, ranks, gpus, ev, seed=seed, n_regions=n_regions),
+                     list(range(n_traces)), threads)
+
+
 # ----------------------------------------------------------------------------
 # small adversarial traces for exact checks
 
