@@ -283,6 +283,71 @@ talp_gpu_status talp_gpu_plan_info(talp_gpu_plan *plan, talp_gpu_plan_stats *out
 /* Synchronise the device and free the plan (the traces stay). NULL is accepted. */
 talp_gpu_status talp_gpu_plan_destroy(talp_gpu_plan *plan);
 
+/* ----------------------------------------------------------------- serving */
+
+/*
+ * The served form: at-runtime monitoring of many jobs (TALP answers queries
+ * while the application runs, Sec. 3.2).  Each job is a trace whose
+ * per-rank/per-device running state (sums and carries of Sec. 4.1/4.2)
+ * stays on the device.  Client threads submit the job's records as time
+ * slices (talp_gpu_server_submit) and ask for metrics (talp_gpu_server_query)
+ * concurrently.  A server thread batches continuously: every job's pending
+ * slice joins the next fold wave (one APPEND ingest of all of them), waves
+ * are enqueued back to back while earlier ones run, and pending queries are
+ * batched into one finalize launch on a separate stream, ordered after the
+ * wave that holds their data.  A query returns the metrics of the job with
+ * at least every slice submitted before it folded in; the result does not
+ * depend on what else is in flight.
+ *
+ * Admission: talp_gpu_server_open_job fails with EBUSY when all job slots
+ * are taken and with ENOMEM when the job's state would exceed the context's
+ * HBM budget; closing a job frees its slot and memory.
+ *
+ * Slices: host memory, copied during the call; flags may only hold
+ * TALP_GPU_SORTED_BY_START (APPEND is implied after the first slice); a
+ * job's slices must come in time order per device (a slice may be out of
+ * order inside itself: it is sorted on the device).  Records per slice are
+ * limited by max_slice_records.
+ */
+typedef struct talp_gpu_server talp_gpu_server;
+
+typedef struct {
+    uint32_t max_jobs;                 /* job slots (admission) */
+    uint32_t max_slice_records;        /* host + device records per submitted slice */
+    uint32_t staging_slices;           /* pinned staging buffers (slices in flight) */
+    uint32_t reserved;
+} talp_gpu_server_config;
+
+typedef struct {
+    uint64_t slices_submitted, slices_folded;
+    uint64_t records_folded;
+    uint64_t waves;                    /* fold waves launched */
+    uint64_t queries, query_batches;   /* answered queries, finalize launches for them */
+    double query_p50_ms, query_p99_ms, query_max_ms;   /* submit-to-answer latency of queries */
+    uint32_t jobs_open, reserved;
+} talp_gpu_server_stats;
+
+talp_gpu_status talp_gpu_server_create(talp_gpu_ctx *ctx, const talp_gpu_server_config *cfg,
+                                       talp_gpu_server **out);
+/* Admit a job: n_ranks, devices_per_rank[n_ranks], n_regions and the region
+ * windows [n_regions][n_ranks][2] as in talp_gpu_trace_batch. */
+talp_gpu_status talp_gpu_server_open_job(talp_gpu_server *srv, uint64_t job_id, uint32_t n_ranks,
+                                         const uint32_t *devices_per_rank, uint32_t n_regions,
+                                         const int64_t *region_window);
+/* Queue one time slice of a job (the batch's trace_id, n_ranks, n_regions,
+ * devices_per_rank and region_window are ignored: the job's are used). */
+talp_gpu_status talp_gpu_server_submit(talp_gpu_server *srv, uint64_t job_id, const talp_gpu_trace_batch *slice);
+/* Metrics of one region (or TALP_GPU_ALL_REGIONS: out_host[n_regions]);
+ * blocks until answered.  EINVAL when the job's records were invalid. */
+talp_gpu_status talp_gpu_server_query(talp_gpu_server *srv, uint64_t job_id, uint32_t region,
+                                      talp_gpu_metrics *out_host);
+/* Wait until everything submitted so far is folded. */
+talp_gpu_status talp_gpu_server_drain(talp_gpu_server *srv);
+talp_gpu_status talp_gpu_server_close_job(talp_gpu_server *srv, uint64_t job_id);
+talp_gpu_status talp_gpu_server_info(talp_gpu_server *srv, talp_gpu_server_stats *out);
+/* Stop the server threads, close every job, free the server. NULL is accepted. */
+talp_gpu_status talp_gpu_server_destroy(talp_gpu_server *srv);
+
 /* Drop trace_id's state and return its HBM (TALP_GPU_ALL: every trace). */
 talp_gpu_status talp_gpu_reset(talp_gpu_ctx *ctx, uint64_t trace_id);
 

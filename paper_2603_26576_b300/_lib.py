@@ -24,7 +24,9 @@ EXPORTED_SYMBOLS = (
     "talp_gpu_region_metrics_batch", "talp_gpu_region_metrics_device", "talp_gpu_unit_sums",
     "talp_gpu_reset", "talp_gpu_memory", "talp_gpu_profile", "talp_gpu_profile_read", "talp_gpu_reduce_noalloc",
     "talp_gpu_plan_create", "talp_gpu_plan_launch", "talp_gpu_plan_metrics", "talp_gpu_plan_info",
-    "talp_gpu_plan_destroy", "talp_gpu_last_error",
+    "talp_gpu_plan_destroy", "talp_gpu_server_create", "talp_gpu_server_open_job", "talp_gpu_server_submit",
+    "talp_gpu_server_query", "talp_gpu_server_drain", "talp_gpu_server_close_job", "talp_gpu_server_info",
+    "talp_gpu_server_destroy", "talp_gpu_last_error",
 )
 TALP_GPU_PLAN_AUTOTUNE = 0x1
 TALP_GPU_NOALLOC_MAX_UNITS = 8192
@@ -70,6 +72,19 @@ class talp_gpu_plan_stats(ctypes.Structure):
                 ("kernels_per_launch", ctypes.c_uint32), ("sweep_items", ctypes.c_uint32),
                 ("sweep_warps", ctypes.c_uint32), ("sweep_stages", ctypes.c_uint32),
                 ("tiles_per_warp", ctypes.c_uint32), ("sweep_grid", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class talp_gpu_server_config(ctypes.Structure):
+    _fields_ = [("max_jobs", ctypes.c_uint32), ("max_slice_records", ctypes.c_uint32),
+                ("staging_slices", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class talp_gpu_server_stats(ctypes.Structure):
+    _fields_ = [("slices_submitted", ctypes.c_uint64), ("slices_folded", ctypes.c_uint64),
+                ("records_folded", ctypes.c_uint64), ("waves", ctypes.c_uint64), ("queries", ctypes.c_uint64),
+                ("query_batches", ctypes.c_uint64), ("query_p50_ms", ctypes.c_double),
+                ("query_p99_ms", ctypes.c_double), ("query_max_ms", ctypes.c_double),
+                ("jobs_open", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class talp_gpu_metrics(ctypes.Structure):
@@ -119,6 +134,15 @@ def load_library():
         "talp_gpu_plan_metrics": ([P, ctypes.POINTER(talp_gpu_metrics), P], I32),
         "talp_gpu_plan_info": ([P, ctypes.POINTER(talp_gpu_plan_stats)], I32),
         "talp_gpu_plan_destroy": ([P], I32),
+        "talp_gpu_server_create": ([P, ctypes.POINTER(talp_gpu_server_config), ctypes.POINTER(ctypes.c_void_p)],
+                                   I32),
+        "talp_gpu_server_open_job": ([P, U64, U32, P, U32, P], I32),
+        "talp_gpu_server_submit": ([P, U64, ctypes.POINTER(talp_gpu_trace_batch)], I32),
+        "talp_gpu_server_query": ([P, U64, U32, ctypes.POINTER(talp_gpu_metrics)], I32),
+        "talp_gpu_server_drain": ([P], I32),
+        "talp_gpu_server_close_job": ([P, U64], I32),
+        "talp_gpu_server_info": ([P, ctypes.POINTER(talp_gpu_server_stats)], I32),
+        "talp_gpu_server_destroy": ([P], I32),
         "talp_gpu_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -265,6 +289,63 @@ def talp_gpu_reduce_noalloc(batch, stream=None, check=True):
         _check(st)
         return res
     return st, res
+
+
+def talp_gpu_server_create(ctx, max_jobs=0, max_slice_records=0, staging_slices=0):
+    cfg = talp_gpu_server_config(max_jobs, max_slice_records, staging_slices, 0)
+    srv = ctypes.c_void_p()
+    _check(load_library().talp_gpu_server_create(ctx, ctypes.byref(cfg), ctypes.byref(srv)))
+    return srv
+
+
+def talp_gpu_server_open_job(srv, job_id, devices_per_rank, region_window, check=True):
+    dpr = np.ascontiguousarray(devices_per_rank, dtype=np.uint32)
+    win = np.ascontiguousarray(region_window, dtype=np.int64)
+    st = load_library().talp_gpu_server_open_job(srv, int(job_id), int(dpr.shape[0]),
+                                                 dpr.ctypes.data_as(ctypes.c_void_p), int(win.shape[0]),
+                                                 win.ctypes.data_as(ctypes.c_void_p))
+    if check:
+        _check(st)
+    return st
+
+
+def talp_gpu_server_submit(srv, job_id, batch, check=True):
+    st = load_library().talp_gpu_server_submit(srv, int(job_id), ctypes.byref(batch))
+    if check:
+        _check(st)
+    return st
+
+
+def talp_gpu_server_query(srv, job_id, region, n_regions=None, check=True):
+    k = n_regions if region == TALP_GPU_ALL_REGIONS else 1
+    if k is None:
+        raise ValueError("n_regions is needed with TALP_GPU_ALL_REGIONS")
+    out = (talp_gpu_metrics * k)()
+    st = load_library().talp_gpu_server_query(srv, int(job_id), region, out)
+    res = list(out) if region == TALP_GPU_ALL_REGIONS else out[0]
+    if check:
+        _check(st)
+        return res
+    return st, res
+
+
+def talp_gpu_server_drain(srv):
+    _check(load_library().talp_gpu_server_drain(srv))
+
+
+def talp_gpu_server_close_job(srv, job_id):
+    _check(load_library().talp_gpu_server_close_job(srv, int(job_id)))
+
+
+def talp_gpu_server_info(srv) -> dict:
+    st = talp_gpu_server_stats()
+    _check(load_library().talp_gpu_server_info(srv, ctypes.byref(st)))
+    return {f: (float(getattr(st, f)) if t is ctypes.c_double else int(getattr(st, f)))
+            for f, t in talp_gpu_server_stats._fields_ if f != "reserved"}
+
+
+def talp_gpu_server_destroy(srv):
+    _check(load_library().talp_gpu_server_destroy(srv))
 
 
 # ----------------------------------------------------------------- marshalling
@@ -431,6 +512,67 @@ class Plan:
         if self.handle is not None:
             talp_gpu_plan_destroy(self.handle)
             self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Owning wrapper of a talp_gpu_server (the served form) on a Context.
+    submit/query release the GIL inside the library, so client threads run
+    concurrently."""
+
+    def __init__(self, context, max_jobs=0, max_slice_records=0, staging_slices=0):
+        self.context = context
+        self.handle = talp_gpu_server_create(context.ctx, max_jobs, max_slice_records, staging_slices)
+        self._R = {}
+
+    def open_job(self, job_id, devices_per_rank, region_window, check=True):
+        st = talp_gpu_server_open_job(self.handle, job_id, devices_per_rank, region_window, check)
+        if st == 0:
+            self._R[int(job_id)] = int(np.asarray(region_window).shape[0])
+        return st
+
+    def submit(self, job_id, host_se, host_state, host_off, dev_se, dev_tag, dev_off, sorted_by_start=True,
+               check=True):
+        """Queue one time slice (host numpy arrays, copied during the call)."""
+        b, keep = batch_from_arrays(job_id, np.zeros(0, np.uint32), np.zeros((0, 0, 2), np.int64), host_se,
+                                    host_state, host_off, dev_se, dev_tag, dev_off,
+                                    TALP_GPU_SORTED_BY_START if sorted_by_start else 0)
+        st = talp_gpu_server_submit(self.handle, job_id, b, check)
+        del keep
+        return st
+
+    def query(self, job_id, region=TALP_GPU_ALL_REGIONS, check=True):
+        r = talp_gpu_server_query(self.handle, job_id, region, self._R[int(job_id)], check)
+        if not check:
+            st, r = r
+            return st, ([metrics_to_dict(x) for x in r] if isinstance(r, list) else metrics_to_dict(r))
+        return [metrics_to_dict(x) for x in r] if isinstance(r, list) else metrics_to_dict(r)
+
+    def drain(self):
+        talp_gpu_server_drain(self.handle)
+
+    def close_job(self, job_id):
+        talp_gpu_server_close_job(self.handle, job_id)
+        self._R.pop(int(job_id), None)
+
+    def stats(self):
+        return talp_gpu_server_info(self.handle)
+
+    def close(self):
+        if self.handle is not None:
+            talp_gpu_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
     def __del__(self):
         try:

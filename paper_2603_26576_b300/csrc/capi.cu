@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/talp_gpu.h"
+#include "engine.h"
 #include "kernels.h"
 
 using namespace talp;
@@ -122,6 +123,8 @@ struct Layout {
 
 void talp::set_last_error(const std::string& msg) { g_last_error = msg; }
 
+// (definitions of the engine.h hooks follow the context struct)
+
 struct talp_gpu_ctx {
     int device = 0;
     int num_sms = 0;
@@ -147,6 +150,15 @@ struct talp_gpu_ctx {
     uint64_t kernel_launches = 0;
     int64_t wait_limit = 4000000000LL;   // cycles (~2 s at 2 GHz)
 };
+
+const TraceDev* talp::trace_device_desc(talp_gpu_ctx* c, uint64_t trace_id, uint32_t* n_regions) {
+    auto it = c->traces.find(trace_id);
+    if (it == c->traces.end()) return nullptr;
+    if (n_regions) *n_regions = it->second->R;
+    return it->second->tdev;
+}
+
+int talp::ctx_device(talp_gpu_ctx* c) { return c->device; }
 
 struct talp_gpu_plan {
     talp_gpu_ctx* c = nullptr;

@@ -1,0 +1,185 @@
+"""The served form: jobs stream time slices into device-resident running
+state while clients query it.  Every answer must equal the oracle on the
+records submitted so far (bit-exact), whatever else the server is doing."""
+import threading
+
+import numpy as np
+import pytest
+
+import oracle
+import tracegen as tg
+from gpu_common import assert_metrics_equal, make_ctx
+
+pytestmark = pytest.mark.gpu
+
+EINVAL, ENOMEM, ENOTFOUND, EBUSY = -1, -2, -5, -6
+
+
+def _jobs(seed0=0):
+    ts = [tg.tiny_trace(s, trace_id=100 + s, max_events=200) for s in range(seed0, seed0 + 6)]
+    ts += [tg.random_trace(seed0 + 7, trace_id=200, n_ranks=3, devices_per_rank=2, dev_events=4000,
+                           host_events=2500)]
+    ranks, gpus, ev = tg.batched_shapes(n_traces=12, max_ranks=40, max_gpus=4, ev_lo=20, ev_hi=3000)
+    for k in range(12):
+        t = tg.batched_trace_fast(k, ranks, gpus, ev, n_regions=4)
+        t.trace_id = 300 + k
+        ts.append(t)
+    return ts
+
+
+def _submit(srv, t, sl):
+    return srv.submit(t.trace_id, sl.host_se, sl.host_state, sl.host_off, sl.dev_se, sl.dev_tag, sl.dev_off,
+                      sorted_by_start=sl.sorted_by_start)
+
+
+def _client(srv, t, slices, results, errors):
+    try:
+        results.append(srv.query(t.trace_id))          # nothing folded yet
+        for sl in slices:
+            _submit(srv, t, sl)
+            results.append(srv.query(t.trace_id))
+    except Exception as e:  # pragma: no cover - reported by the test
+        errors.append((t.trace_id, repr(e)))
+
+
+def _check_prefixes(t, cuts, results, tag):
+    assert len(results) == cuts.shape[0] + 2
+    for k, res in enumerate(results):
+        p = tg.prefix_trace(t, cuts, k - 1)
+        for r in range(t.n_regions):
+            assert_metrics_equal(res[r], oracle.region_metrics(p, r), (tag, t.trace_id, "slices", k, r))
+
+
+def test_serving_prefix_parity_concurrent_clients():
+    from paper_2603_26576_b300 import Server
+    c = make_ctx()
+    ts = _jobs()
+    with Server(c, max_jobs=64, max_slice_records=1 << 18, staging_slices=16) as srv:
+        plan = []
+        for i, t in enumerate(ts):
+            cuts = tg.random_cuts(t, 3 + i % 4, seed=11)
+            slices = tg.time_slices(t, cuts, shuffle_seed=(7 if i % 3 == 0 else None))
+            srv.open_job(t.trace_id, t.devices_per_rank, t.region_window)
+            plan.append((t, cuts, slices, []))
+        errors = []
+        th = [threading.Thread(target=_client, args=(srv, t, sl, res, errors)) for t, _, sl, res in plan]
+        for x in th:
+            x.start()
+        for x in th:
+            x.join()
+        assert not errors, errors
+        srv.drain()
+        st = srv.stats()
+        assert st["slices_submitted"] == st["slices_folded"] == sum(len(p[2]) for p in plan)
+        assert st["records_folded"] == sum(t.n_records for t in ts)
+        assert st["queries"] == sum(len(p[3]) for p in plan)
+        assert st["jobs_open"] == len(ts)
+        assert 0 < st["query_p50_ms"] <= st["query_p99_ms"] <= st["query_max_ms"]
+    for t, cuts, _, res in plan:
+        _check_prefixes(t, cuts, res, "served")
+    c.close()
+
+
+def test_serving_alone_equals_mixed_equals_plain():
+    from paper_2603_26576_b300 import Server
+    c = make_ctx()
+    ts = _jobs(seed0=40)
+    x = ts[6]
+    cuts = tg.random_cuts(x, 5, seed=3)
+    slices = tg.time_slices(x, cuts, shuffle_seed=2)
+    # alone
+    with Server(c, max_jobs=64, max_slice_records=1 << 18) as srv:
+        srv.open_job(x.trace_id, x.devices_per_rank, x.region_window)
+        for sl in slices:
+            _submit(srv, x, sl)
+        alone = srv.query(x.trace_id)
+    # in a mix of concurrently streaming jobs
+    with Server(c, max_jobs=64, max_slice_records=1 << 18) as srv:
+        plan = []
+        for t in ts:
+            ct = tg.random_cuts(t, 4, seed=9) if t is not x else cuts
+            sl = tg.time_slices(t, ct, shuffle_seed=4) if t is not x else slices
+            srv.open_job(t.trace_id, t.devices_per_rank, t.region_window)
+            plan.append((t, sl, []))
+        errors = []
+        th = [threading.Thread(target=_client, args=(srv, t, sl, res, errors)) for t, sl, res in plan]
+        for h in th:
+            h.start()
+        for h in th:
+            h.join()
+        assert not errors, errors
+        mixed = [p for p in plan if p[0] is x][0][2][-1]
+    # one plain ingest of the whole trace
+    c.ingest([x], flags=0)
+    plain = c.metrics(x.trace_id)
+    c.reset()
+    for r in range(x.n_regions):
+        assert alone[r] == mixed[r], ("alone-vs-mixed", r)
+        assert alone[r] == plain[r], ("alone-vs-plain", r)
+        assert_metrics_equal(alone[r], oracle.region_metrics(x, r), ("served-full", r))
+    c.close()
+
+
+def test_serving_admission_slots_and_budget():
+    from paper_2603_26576_b300 import Server
+    small = tg.tiny_trace(3, trace_id=1, max_events=50)
+    c = make_ctx(budget=8 << 20)
+    with Server(c, max_jobs=2, max_slice_records=4096, staging_slices=4) as srv:
+        assert srv.open_job(1, small.devices_per_rank, small.region_window) == 0
+        assert srv.open_job(2, small.devices_per_rank, small.region_window) == 0
+        assert srv.open_job(3, small.devices_per_rank, small.region_window, check=False) == EBUSY
+        assert srv.open_job(2, small.devices_per_rank, small.region_window, check=False) == EBUSY
+        srv.close_job(2)
+        # a job whose running state alone exceeds what the budget leaves
+        n = 20000
+        win = np.zeros((8, n, 2), np.int64)
+        win[:, :, 1] = 1000
+        assert srv.open_job(4, np.ones(n, np.uint32), win, check=False) == ENOMEM
+        assert srv.stats()["jobs_open"] == 1
+        # the server is still serving the admitted job
+        cuts = tg.random_cuts(small, 2, seed=1)
+        for sl in tg.time_slices(small, cuts):
+            srv.submit(1, sl.host_se, sl.host_state, sl.host_off, sl.dev_se, sl.dev_tag, sl.dev_off)
+        res = srv.query(1)
+        for r in range(small.n_regions):
+            assert_metrics_equal(res[r], oracle.region_metrics(small, r), ("after-admission", r))
+        assert srv.open_job(5, small.devices_per_rank, small.region_window) == 0
+    c.close()
+
+
+def test_serving_errors_stay_with_their_job():
+    from paper_2603_26576_b300 import Server, talp_gpu_server_query
+    c = make_ctx()
+    good = tg.tiny_trace(11, trace_id=21, max_events=120)
+    bad = tg.random_trace(12, trace_id=22, n_ranks=2, devices_per_rank=1, dev_events=300, host_events=200)
+    with Server(c, max_jobs=8, max_slice_records=4096) as srv:
+        for t in (good, bad):
+            srv.open_job(t.trace_id, t.devices_per_rank, t.region_window)
+        # argument errors are refused at submit
+        hoff = bad.host_off.copy()
+        hoff[1] = hoff[2] + 1
+        assert srv.submit(bad.trace_id, bad.host_se, bad.host_state, hoff, bad.dev_se, bad.dev_tag,
+                          bad.dev_off, check=False) == EINVAL
+        assert srv.submit(999, good.host_se, good.host_state, good.host_off, good.dev_se, good.dev_tag,
+                          good.dev_off, check=False) == ENOTFOUND
+        n = 5000
+        off = np.zeros(good.n_ranks + 1, np.uint64)
+        off[1:] = n
+        assert srv.submit(good.trace_id, np.zeros((n, 2), np.int64), np.zeros(n, np.uint8), off, good.dev_se,
+                          good.dev_tag, good.dev_off, check=False) == EINVAL
+        # a record with end < start makes its own job's metrics invalid only
+        dse = bad.dev_se.copy()
+        dse[0, 1] = dse[0, 0] - 1
+        srv.submit(good.trace_id, good.host_se, good.host_state, good.host_off, good.dev_se, good.dev_tag,
+                   good.dev_off)
+        srv.submit(bad.trace_id, bad.host_se, bad.host_state, bad.host_off, dse, bad.dev_tag, bad.dev_off)
+        st, _ = srv.query(bad.trace_id, check=False)
+        assert st == EINVAL
+        res = srv.query(good.trace_id)
+        for r in range(good.n_regions):
+            assert_metrics_equal(res[r], oracle.region_metrics(good, r), ("good-beside-bad", r))
+        st, _ = talp_gpu_server_query(srv.handle, 999, 0, check=False)
+        assert st == ENOTFOUND
+        st, _ = talp_gpu_server_query(srv.handle, good.trace_id, good.n_regions, check=False)
+        assert st == EINVAL
+    c.close()

@@ -603,3 +603,78 @@ def _with_dev(trace, se, tag):
                  region_window=trace.region_window, host_se=trace.host_se, host_state=trace.host_state,
                  host_off=trace.host_off, dev_se=se, dev_tag=tag, dev_off=trace.dev_off,
                  sorted_by_start=False, meta=dict(trace.meta))
+
+
+# ----------------------------------------------------------------------------
+# streamed delivery: a trace cut into time slices (activity buffers handed
+# over while the application runs)
+
+
+@dataclass
+class Slice:
+    host_se: np.ndarray
+    host_state: np.ndarray
+    host_off: np.ndarray
+    dev_se: np.ndarray
+    dev_tag: np.ndarray
+    dev_off: np.ndarray
+    sorted_by_start: bool = True
+
+    @property
+    def n_records(self) -> int:
+        return int(self.host_se.shape[0] + self.dev_se.shape[0])
+
+
+def random_cuts(trace: Trace, n_slices: int, seed=5) -> np.ndarray:
+    """n_slices - 1 increasing cut times drawn uniformly over the trace's span
+    of start times."""
+    starts = np.concatenate([trace.host_se[:, 0], trace.dev_se[:, 0]])
+    if starts.size == 0 or n_slices < 2:
+        return np.zeros(0, np.int64)
+    lo, hi = int(starts.min()), int(starts.max()) + 1
+    c = _rng(seed, trace.trace_id, D_TRACE, 21).integers(lo, hi, size=n_slices - 1)
+    return np.sort(c).astype(np.int64)
+
+
+def _keep(se, tag, off, mask):
+    seg = np.repeat(np.arange(off.shape[0] - 1), np.diff(off.astype(np.int64)))
+    counts = np.bincount(seg[mask], minlength=off.shape[0] - 1)
+    new_off = np.zeros(off.shape[0], np.uint64)
+    new_off[1:] = np.cumsum(counts)
+    return np.ascontiguousarray(se[mask]), np.ascontiguousarray(tag[mask]), new_off
+
+
+def time_slices(trace: Trace, cuts: np.ndarray, shuffle_seed=None) -> list:
+    """Slice k holds, per rank and device, the records whose start lies in
+    [cuts[k-1], cuts[k]) (open at both ends of the list), in the trace's own
+    order.  With shuffle_seed, odd slices have their device segments
+    permuted (the served form must sort them) and are flagged unsorted."""
+    hk = np.searchsorted(cuts, trace.host_se[:, 0], side="right")
+    dk = np.searchsorted(cuts, trace.dev_se[:, 0], side="right")
+    out = []
+    for k in range(cuts.shape[0] + 1):
+        hse, hst, hoff = _keep(trace.host_se, trace.host_state, trace.host_off, hk == k)
+        dse, dtg, doff = _keep(trace.dev_se, trace.dev_tag, trace.dev_off, dk == k)
+        sl = Slice(hse, hst, hoff, dse, dtg, doff, sorted_by_start=trace.sorted_by_start)
+        if shuffle_seed is not None and k % 2 == 1:
+            rng = _rng(shuffle_seed, trace.trace_id, D_TRACE, 100 + k)
+            for g in range(doff.shape[0] - 1):
+                a, b = int(doff[g]), int(doff[g + 1])
+                if b - a > 1:
+                    p = rng.permutation(b - a)
+                    dse[a:b] = dse[a:b][p]
+                    dtg[a:b] = dtg[a:b][p]
+            sl.sorted_by_start = False
+        out.append(sl)
+    return out
+
+
+def prefix_trace(trace: Trace, cuts: np.ndarray, k: int) -> Trace:
+    """The trace restricted to slices 0..k of time_slices(trace, cuts)."""
+    hk = np.searchsorted(cuts, trace.host_se[:, 0], side="right")
+    dk = np.searchsorted(cuts, trace.dev_se[:, 0], side="right")
+    hse, hst, hoff = _keep(trace.host_se, trace.host_state, trace.host_off, hk <= k)
+    dse, dtg, doff = _keep(trace.dev_se, trace.dev_tag, trace.dev_off, dk <= k)
+    return Trace(trace_id=trace.trace_id, n_ranks=trace.n_ranks, devices_per_rank=trace.devices_per_rank,
+                 region_window=trace.region_window, host_se=hse, host_state=hst, host_off=hoff, dev_se=dse,
+                 dev_tag=dtg, dev_off=doff, sorted_by_start=trace.sorted_by_start, meta=dict(trace.meta))
