@@ -2,7 +2,7 @@
 """Benchmark of the efficiency-metric reducer on synthetic traces.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
-                  [--workload plain|small] [--scale S]
+                  [--workload plain|small|batched|serving] [--scale S]
 
 One step = one pass of the whole hot path over one trace resident in HBM:
 record validation, the device flattening (kernel / transfer / busy unions per
@@ -58,10 +58,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
-    ap.add_argument("--workload", default="plain", choices=["plain", "small", "batched"])
+    ap.add_argument("--workload", default="plain", choices=["plain", "small", "batched", "serving"])
     ap.add_argument("--traces", type=int, default=4096, help="batched: number of traces")
     ap.add_argument("--ev-hi", type=int, default=5000, help="batched: largest events per GPU")
     ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--jobs", type=int, default=256, help="serving: monitored jobs")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serving: batch arrivals per second (all jobs)")
+    ap.add_argument("--query-ms", type=float, default=10.0, help="serving: query period per job")
+    ap.add_argument("--step-s", type=float, default=1.0, help="serving: seconds of served load per step")
+    ap.add_argument("--sat-s", type=float, default=3.0, help="serving: seconds of the saturation phase")
+    ap.add_argument("--plain-s", type=float, default=3.0, help="serving: seconds of the plain-form phase")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -326,12 +332,269 @@ def run_batched(a):
     return 0 if agree else 1
 
 
+# ----------------------------------------------------------------- serving
+
+
+class ServeLoad:
+    """Client load of the serving workload: submitter threads with Poisson
+    arrivals (or closed loop), and query threads asking every job for all
+    its regions once per query period.  `api` is the served form or the
+    plain form behind the same two calls."""
+
+    def __init__(self, jobs, submit, query, rate, query_s, n_sub=8, n_q=16, seed=7):
+        self.jobs, self.submit, self.query = jobs, submit, query
+        self.rate, self.query_s = rate, query_s
+        self.n_sub, self.n_q, self.seed = n_sub, n_q, seed
+        self.next_q = [0] * len(jobs)
+        self.sub_records = 0
+        self.lat = []
+        self.errors = []
+
+    def run(self, seconds, closed_loop=False):
+        stop = threading.Event()
+        self.lat = []
+        t_start = time.perf_counter()
+
+        def submitter(tid):
+            rng = np.random.default_rng([self.seed, tid, len(self.lat), int(t_start * 1e3) & 0xFFFF])
+            mine = list(range(tid, len(self.jobs), self.n_sub))
+            t_next = time.perf_counter()
+            k = 0
+            try:
+                while not stop.is_set():
+                    if closed_loop:
+                        j = mine[k % len(mine)]
+                        k += 1
+                    else:
+                        t_next += rng.exponential(self.n_sub / self.rate)
+                        d = t_next - time.perf_counter()
+                        if d > 0:
+                            time.sleep(d)
+                        j = mine[int(rng.integers(0, len(mine)))]
+                    b = self.jobs[j].batch(self.next_q[j])
+                    self.submit(j, b)
+                    self.next_q[j] += 1
+                    self.sub_records += b.n_records
+            except Exception as e:  # reported in the result line
+                self.errors.append(repr(e))
+
+        def querier(tid):
+            mine = list(range(tid, len(self.jobs), self.n_q))
+            t_tick = time.perf_counter()
+            lat = []
+            try:
+                while not stop.is_set():
+                    for j in mine:
+                        q0 = time.perf_counter()
+                        self.query(j)
+                        lat.append(time.perf_counter() - q0)
+                    t_tick += self.query_s
+                    d = t_tick - time.perf_counter()
+                    if d > 0:
+                        time.sleep(d)
+                    else:
+                        t_tick = time.perf_counter()
+            except Exception as e:
+                self.errors.append(repr(e))
+            self.lat.extend(lat)
+
+        th = [threading.Thread(target=submitter, args=(i,)) for i in range(self.n_sub)]
+        th += [threading.Thread(target=querier, args=(i,)) for i in range(self.n_q)]
+        for x in th:
+            x.start()
+        time.sleep(seconds)
+        stop.set()
+        for x in th:
+            x.join()
+        return time.perf_counter() - t_start
+
+
+def _pct(v, p):
+    if not v:
+        return None
+    v = sorted(v)
+    return v[min(len(v), max(1, int(np.ceil(p * len(v))))) - 1]
+
+
+def run_serving(a):
+    """Served form: many jobs stream batches into device-resident state while
+    clients query it; against the plain form (one ingest per batch, one
+    synchronous metrics call per query) at the same load."""
+    import torch
+    import oracle
+    import paper_2603_26576_b300 as P
+    sys.setswitchinterval(0.0002)
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    jobs = tg.serving_jobs(n_jobs=a.jobs)
+    gen_s = time.time() - t0
+    R = jobs[0].n_regions
+    step_s = a.step_s
+    paced_s = (a.warmup + a.steps) * step_s
+    # region windows cover what the paced phases deliver (later batches are clipped)
+    horizon = int(a.rate / a.jobs * (paced_s + a.plain_s) * 2 + 64)
+    wins = [j.windows(horizon) for j in jobs]
+    max_rec = max(b.n_records for j in jobs for b in j.batches)
+
+    ctx = P.Context(0)
+    srv = P.Server(ctx, max_jobs=a.jobs, max_slice_records=max_rec, staging_slices=128)
+    for j, w in zip(jobs, wins):
+        srv.open_job(j.job_id, j.trace.devices_per_rank, w)
+
+    def s_submit(k, b):
+        srv.submit(k, b.host_se, b.host_state, b.host_off, b.dev_se, b.dev_tag, b.dev_off)
+
+    lib = P.load_library()
+
+    def s_query(k):
+        o = (P.talp_gpu_metrics * R)()
+        st = lib.talp_gpu_server_query(srv.handle, k, P.TALP_GPU_ALL_REGIONS, o)
+        if st != 0:
+            raise P.TalpGpuError(st, P.talp_gpu_last_error())
+
+    load = ServeLoad(jobs, s_submit, s_query, a.rate, a.query_ms / 1000.0)
+    # warm-up phase, then the timed phase (paced arrivals)
+    load.run(a.warmup * step_s)
+    srv.drain()
+    P.talp_gpu_profile(ctx.ctx, True)
+    P.talp_gpu_profile_read(ctx.ctx)
+    l0 = P.talp_gpu_profile_read(ctx.ctx)["kernel_launches"]
+    s0 = srv.stats()
+    clocks = Clocks(0)
+    clocks.start()
+    time.sleep(0.2)
+    s0 = srv.stats()
+    wall = load.run(a.steps * step_s)
+    s1 = srv.stats()
+    ck = clocks.stop()
+    lat_paced = list(load.lat)
+    srv.drain()
+    prof = P.talp_gpu_profile_read(ctx.ctx)
+    P.talp_gpu_profile(ctx.ctx, False)
+    s2 = srv.stats()
+    folded = s1["records_folded"] - s0["records_folded"]
+    value = folded / wall
+    launches = (prof["kernel_launches"] - l0) + (s2["query_batches"] - s0["query_batches"])
+    waves = s2["waves"] - s0["waves"]
+    n_queries = s2["queries"] - s0["queries"]
+    sub_slices = s2["slices_submitted"] - s0["slices_submitted"]
+    # saturation: closed-loop submitters, queries still every period
+    sa0 = srv.stats()
+    sat_wall = load.run(a.sat_s, closed_loop=True)
+    sa1 = srv.stats()
+    lat_sat = list(load.lat)
+    srv.drain()
+    # bit-exact check of sampled jobs against the oracle on what they received
+    order = sorted(range(len(jobs)), key=lambda k: sum(jobs[k].batch(q).n_records for q in range(load.next_q[k])))
+    sample = order[:3]
+    exact = True
+    cpu_records, cpu_s = 0, 0.0
+    for k in sample:
+        got = srv.query(k)
+        pt = jobs[k].prefix(load.next_q[k], wins[k])
+        c0 = time.perf_counter()
+        ref = [oracle.region_metrics(pt, r) for r in range(R)]
+        cpu_s += time.perf_counter() - c0
+        cpu_records += pt.n_records
+        for r in range(R):
+            for f in P._lib.INT_FIELDS + P._lib.RATIO_FIELDS:
+                if got[r][f] != ref[r][f]:
+                    exact = False
+    st_native = srv.stats()
+    srv.close()
+    ctx.close()
+
+    # ---- plain form at the same load: one ingest per batch, one synchronous
+    # metrics call per query, serialised on one context
+    ctx2 = P.Context(0)
+    lock = threading.Lock()
+    stream = torch.cuda.Stream()
+    for j, w in zip(jobs, wins):
+        t = j.trace
+        e = tg.Slice(np.zeros((0, 2), np.int64), np.zeros(0, np.uint8), np.zeros(t.n_ranks + 1, np.uint64),
+                     np.zeros((0, 2), np.int64), np.zeros(0, np.uint8), np.zeros(t.m_devices + 1, np.uint64))
+        b, keep = P.batch_from_arrays(j.job_id, t.devices_per_rank, w, e.host_se, e.host_state, e.host_off,
+                                      e.dev_se, e.dev_tag, e.dev_off, P.TALP_GPU_SORTED_BY_START)
+        P.talp_gpu_ingest_events(ctx2.ctx, [b], stream)
+
+    def p_submit(k, b):
+        t = jobs[k].trace
+        bb, keep = P.batch_from_arrays(k, t.devices_per_rank, wins[k], b.host_se, b.host_state, b.host_off,
+                                       b.dev_se, b.dev_tag, b.dev_off,
+                                       P.TALP_GPU_SORTED_BY_START | P.TALP_GPU_APPEND)
+        with lock:
+            P.talp_gpu_ingest_events(ctx2.ctx, [bb], stream)
+        del keep
+
+    def p_query(k):
+        with lock:
+            P.talp_gpu_region_metrics(ctx2.ctx, k, P.TALP_GPU_ALL_REGIONS, stream, n_regions=R)
+
+    pload = ServeLoad(jobs, p_submit, p_query, a.rate, a.query_ms / 1000.0)
+    pload.next_q = [0] * len(jobs)
+    pr0 = pload.sub_records
+    p_wall = pload.run(a.plain_s)
+    torch.cuda.synchronize()
+    p_rec = pload.sub_records - pr0
+    lat_plain = list(pload.lat)
+    ctx2.close()
+
+    peak, peak_kind = measured_peaks()
+    sweep_ms = prof["sweep_ms"] / max(1, prof["sweep_launches"])
+    rec_per_sweep = prof["sweep_records"] / max(1, prof["sweep_launches"])
+    achieved = BYTES_PER_RECORD * rec_per_sweep / (sweep_ms / 1000.0) / 1e9 if sweep_ms > 0 else 0.0
+    ms = lambda x: None if x is None else 1000.0 * x  # noqa: E731
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": 1000.0 * wall / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64", "data": "synthetic (seeded generator; the paper's traces are not available)",
+        "config": {"workload": f"serving: {a.jobs} jobs (8-256 ranks x 1-4 GPUs), batches of 1k-100k events "
+                               f"log-uniform, Poisson {a.rate:g} batches/s, a query per job every "
+                               f"{a.query_ms:g} ms (all {R} nested regions)",
+                   "step": f"{step_s:g} s of served load (wall clock)", "generate_s": gen_s,
+                   "l2": "each batch crosses PCIe once; device state is small and stays resident"},
+        "latency_ms": {"p50": ms(_pct(lat_paced, 0.5)), "p99": ms(_pct(lat_paced, 0.99)),
+                       "max": ms(max(lat_paced) if lat_paced else None), "queries": len(lat_paced),
+                       "measured": "client side, around each query call"},
+        "server_latency_ms": {"p50": st_native["query_p50_ms"], "p99": st_native["query_p99_ms"],
+                              "max": st_native["query_max_ms"],
+                              "measured": "inside the library, whole run"},
+        "served": {"queries_per_s": n_queries / wall, "batches_per_s": sub_slices / wall,
+                   "waves_per_s": waves / wall, "query_batches": s2["query_batches"] - s0["query_batches"]},
+        "saturation": {"events_per_s": (sa1["records_folded"] - sa0["records_folded"]) / sat_wall,
+                       "batches_per_s": (sa1["slices_folded"] - sa0["slices_folded"]) / sat_wall,
+                       "p50_ms": ms(_pct(lat_sat, 0.5)), "p99_ms": ms(_pct(lat_sat, 0.99)),
+                       "queries": len(lat_sat)},
+        "plain_same_load": {"events_per_s": p_rec / p_wall, "queries_per_s": len(lat_plain) / p_wall,
+                            "p50_ms": ms(_pct(lat_plain, 0.5)), "p99_ms": ms(_pct(lat_plain, 0.99)),
+                            "form": "one APPEND ingest per batch + one synchronous metrics call per query"},
+        "bit_exact_sampled_jobs": {"jobs": sample, "exact": exact},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if peak else None, "traffic": None, "kernel": "talp::sweep_kernel",
+                     "kernel_ms": sweep_ms, "records_per_launch": rec_per_sweep,
+                     "peak_source": f"{peak_kind} hbm_gbs",
+                     "note": "small waves: the sweep is latency-bound, not bandwidth-bound"},
+        "cpu_baseline": {"value": cpu_records / cpu_s if cpu_s else None, "unit": UNIT, "cores": 1,
+                         "kind": "oracle", "sample": f"{len(sample)} smallest jobs' received streams "
+                                                     f"({cpu_records} records), {cpu_s:.1f} s"},
+        "e2e": {"value": value, "unit": UNIT,
+                "h2d_bytes_per_step": int(BYTES_PER_RECORD * folded / a.steps),
+                "d2h_bytes_per_step": int(n_queries * R * 184 / a.steps),
+                "note": "the served form takes host buffers: value is already end to end"},
+        "gpu_launches": launches, "clocks": ck, "errors": load.errors + pload.errors,
+    }
+    print(json.dumps(line), flush=True)
+    return 0 if exact and not line["errors"] else 1
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
     if a.workload == "batched":
         return run_batched(a)
+    if a.workload == "serving":
+        return run_serving(a)
     import torch
     import paper_2603_26576_b300 as P
 

@@ -678,3 +678,76 @@ def prefix_trace(trace: Trace, cuts: np.ndarray, k: int) -> Trace:
     return Trace(trace_id=trace.trace_id, n_ranks=trace.n_ranks, devices_per_rank=trace.devices_per_rank,
                  region_window=trace.region_window, host_se=hse, host_state=hst, host_off=hoff, dev_se=dse,
                  dev_tag=dtg, dev_off=doff, sorted_by_start=trace.sorted_by_start, meta=dict(trace.meta))
+
+
+@dataclass
+class ServingJob:
+    """One monitored job of the serving workload: a base trace cut into
+    period batches by record count; batch q of the stream is base batch
+    q mod P with every timestamp shifted by (q // P) * span."""
+    job_id: int
+    trace: Trace
+    batches: list            # [Slice] * P
+    span: int                # > every timestamp of the base trace
+    n_regions: int
+
+    def batch(self, q: int) -> Slice:
+        b = self.batches[q % len(self.batches)]
+        shift = np.int64((q // len(self.batches)) * self.span)
+        if shift == 0:
+            return b
+        return Slice(b.host_se + shift, b.host_state, b.host_off, b.dev_se + shift, b.dev_tag, b.dev_off,
+                     b.sorted_by_start)
+
+    def windows(self, n_batches: int) -> np.ndarray:
+        """Nested region windows over the time the first n_batches cover."""
+        cycles = (max(1, n_batches) + len(self.batches) - 1) // len(self.batches)
+        return nested_regions(np.full(self.trace.n_ranks, cycles * self.span, np.int64), self.n_regions)
+
+    def prefix(self, n_batches: int, windows: np.ndarray) -> Trace:
+        """The trace made of the first n_batches batches of the stream."""
+        parts = [self.batch(q) for q in range(n_batches)]
+        def cat(attr_se, attr_tag, attr_off, n_seg):
+            if not parts:
+                return np.zeros((0, 2), np.int64), np.zeros(0, np.uint8), np.zeros(n_seg + 1, np.uint64)
+            se = np.concatenate([getattr(p, attr_se) for p in parts])
+            tag = np.concatenate([getattr(p, attr_tag) for p in parts])
+            seg = np.concatenate([np.repeat(np.arange(n_seg), np.diff(getattr(p, attr_off).astype(np.int64)))
+                                  for p in parts])
+            order = np.argsort(seg, kind="stable")
+            off = np.zeros(n_seg + 1, np.uint64)
+            off[1:] = np.cumsum(np.bincount(seg, minlength=n_seg))
+            return se[order], tag[order], off
+        t = self.trace
+        hse, hst, hoff = cat("host_se", "host_state", "host_off", t.n_ranks)
+        dse, dtg, doff = cat("dev_se", "dev_tag", "dev_off", t.m_devices)
+        return Trace(trace_id=self.job_id, n_ranks=t.n_ranks, devices_per_rank=t.devices_per_rank,
+                     region_window=windows, host_se=hse, host_state=hst, host_off=hoff, dev_se=dse, dev_tag=dtg,
+                     dev_off=doff, sorted_by_start=True, meta=dict(workload="serving prefix", batches=n_batches))
+
+
+def serving_jobs(n_jobs=256, seed=0x7A1F + 4, period=8, rank_lo=8, rank_hi=256, gpus_hi=4, batch_lo=1_000,
+                 batch_hi=100_000, n_regions=4, threads=None):
+    """The serving workload: n_jobs jobs of ranks log-uniform in [rank_lo,
+    rank_hi] x GPUs per rank uniform in [1, gpus_hi]; each job's stream is
+    made of batches whose record counts are log-uniform in [batch_lo,
+    batch_hi] (one period of `period` batches, repeated shifted in time)."""
+    rng = _rng(seed, 0, D_SHAPE, 7)
+    ranks = np.clip(np.floor(np.exp(rng.uniform(math.log(rank_lo), math.log(rank_hi + 1), n_jobs))),
+                    rank_lo, rank_hi).astype(np.int64)
+    gpus = rng.integers(1, gpus_hi + 1, n_jobs)
+    sizes = np.rint(np.exp(rng.uniform(math.log(batch_lo), math.log(batch_hi), (n_jobs, period)))).astype(np.int64)
+    # events per GPU (and host intervals per rank) so one period holds the drawn records
+    ev = np.maximum(1, np.ceil(sizes.sum(1) / (ranks * gpus + ranks)).astype(np.int64))
+
+    def one(k):
+        t = batched_trace_fast(k, ranks, gpus, ev, seed=seed, n_regions=n_regions)
+        t.trace_id = k
+        starts = np.sort(np.concatenate([t.host_se[:, 0], t.dev_se[:, 0]]))
+        cum = np.cumsum(sizes[k])[:-1]
+        cuts = starts[np.minimum(cum, starts.shape[0] - 1)]
+        span = int(max(t.host_se[:, 1].max(), t.dev_se[:, 1].max() if t.n_dev else 0)) + 1
+        return ServingJob(k, t, time_slices(t, cuts), span, n_regions)
+    if threads is None:
+        threads = min(32, os.cpu_count() or 1)
+    return _pool_map(one, list(range(n_jobs)), threads)
