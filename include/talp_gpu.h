@@ -218,6 +218,22 @@ talp_gpu_status talp_gpu_region_metrics_device(talp_gpu_ctx *ctx, const uint64_t
                                                void *stream);
 
 /*
+ * Sharded reduction (one trace split over several GPUs or contexts by whole
+ * ranks, each rank with all of its devices): parts[0 .. n_parts-1] are the
+ * talp_gpu_metrics of one region computed on each shard (host memory, same
+ * trace_id and region).  Their integer aggregates combine exactly -- E
+ * (Eq. 1, a maximum over ranks) and the maxima of Eqs. 7-12 by max, the
+ * sums and the rank/device counts by addition, the status flags by or --
+ * and one kernel forms the nine ratios from the combined aggregates, so
+ * out_host equals the metrics of the whole trace bit for bit.  The shards'
+ * own ratios are ignored.  Synchronises `stream`.
+ * Errors: EINVAL (no parts, more than 2^20, mixed traces or regions, or a
+ * part carrying the flag of invalid records), ETIMEDOUT, ECUDA.
+ */
+talp_gpu_status talp_gpu_metrics_combine(talp_gpu_ctx *ctx, const talp_gpu_metrics *parts, size_t n_parts,
+                                         talp_gpu_metrics *out_host, void *stream);
+
+/*
  * Raw per-unit times of one region (TALP also reports raw times so users can
  * form their own indicators): host_out [n_ranks][3] = useful, offload, MPI
  * per rank; dev_out [m][3] = kernel union D_K, memory-operation union, busy

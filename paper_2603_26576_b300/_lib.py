@@ -21,7 +21,8 @@ STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEDOUT
 # every function the header declares
 EXPORTED_SYMBOLS = (
     "talp_gpu_create", "talp_gpu_destroy", "talp_gpu_ingest_events", "talp_gpu_region_metrics",
-    "talp_gpu_region_metrics_batch", "talp_gpu_region_metrics_device", "talp_gpu_unit_sums",
+    "talp_gpu_region_metrics_batch", "talp_gpu_region_metrics_device", "talp_gpu_metrics_combine",
+    "talp_gpu_unit_sums",
     "talp_gpu_reset", "talp_gpu_memory", "talp_gpu_profile", "talp_gpu_profile_read", "talp_gpu_reduce_noalloc",
     "talp_gpu_plan_create", "talp_gpu_plan_launch", "talp_gpu_plan_metrics", "talp_gpu_plan_info",
     "talp_gpu_plan_destroy", "talp_gpu_server_create", "talp_gpu_server_open_job", "talp_gpu_server_submit",
@@ -102,6 +103,13 @@ def metrics_to_dict(m: talp_gpu_metrics) -> dict:
     return d
 
 
+def metrics_from_dict(d: dict) -> talp_gpu_metrics:
+    m = talp_gpu_metrics()
+    for f, _ in talp_gpu_metrics._fields_:
+        setattr(m, f, d[f])
+    return m
+
+
 _lib = None
 
 
@@ -122,6 +130,8 @@ def load_library():
         "talp_gpu_region_metrics": ([P, U64, U32, ctypes.POINTER(talp_gpu_metrics), P], I32),
         "talp_gpu_region_metrics_batch": ([P, P, S, U32, ctypes.POINTER(talp_gpu_metrics), P], I32),
         "talp_gpu_region_metrics_device": ([P, P, S, U32, P, P], I32),
+        "talp_gpu_metrics_combine": ([P, ctypes.POINTER(talp_gpu_metrics), S, ctypes.POINTER(talp_gpu_metrics), P],
+                                     I32),
         "talp_gpu_unit_sums": ([P, U64, U32, P, P, P], I32),
         "talp_gpu_reset": ([P, U64], I32),
         "talp_gpu_memory": ([P, ctypes.POINTER(S), ctypes.POINTER(S)], I32),
@@ -215,6 +225,20 @@ def talp_gpu_region_metrics_device(ctx, trace_ids, region, out_device_ptr, strea
     ids = np.ascontiguousarray(trace_ids, dtype=np.uint64)
     _check(load_library().talp_gpu_region_metrics_device(ctx, ids.ctypes.data_as(ctypes.c_void_p), len(ids),
                                                          region, ctypes.c_void_p(out_device_ptr), _stream(stream)))
+
+
+def talp_gpu_metrics_combine(ctx, parts, stream=None, check=True):
+    """Metrics of a region of a trace from its shards' metrics (a list of
+    talp_gpu_metrics or of dicts as metrics_to_dict returns)."""
+    arr = (talp_gpu_metrics * len(parts))()
+    for k, p in enumerate(parts):
+        arr[k] = p if isinstance(p, talp_gpu_metrics) else metrics_from_dict(p)
+    out = talp_gpu_metrics()
+    st = load_library().talp_gpu_metrics_combine(ctx, arr, len(parts), ctypes.byref(out), _stream(stream))
+    if check:
+        _check(st)
+        return out
+    return st, out
 
 
 def talp_gpu_unit_sums(ctx, trace_id, region, n_ranks, m_devices, stream=None):

@@ -899,6 +899,37 @@ talp_gpu_status talp_gpu_region_metrics_device(talp_gpu_ctx* c, const uint64_t* 
                            static_cast<cudaStream_t>(stream), false);
 }
 
+talp_gpu_status talp_gpu_metrics_combine(talp_gpu_ctx* c, const talp_gpu_metrics* parts, size_t n_parts,
+                                         talp_gpu_metrics* out_host, void* stream_) {
+    if (!c) return fail(TALP_GPU_EINVAL, "null context");
+    if (!parts || !out_host || n_parts == 0) return fail(TALP_GPU_EINVAL, "null argument or no parts");
+    if (n_parts > (1u << 20)) return fail(TALP_GPU_EINVAL, "more than 2^20 parts");
+    for (size_t k = 1; k < n_parts; ++k)
+        if (parts[k].trace_id != parts[0].trace_id || parts[k].region != parts[0].region)
+            return fail(TALP_GPU_EINVAL, "parts of different traces or regions");
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    TALP_CUDA(cudaSetDevice(c->device));
+    const size_t pb = align_up(sizeof(MetricsOut) * n_parts, 256);
+    if (c->ws_used) TALP_CUDA(cudaStreamWaitEvent(stream, c->ev_ws, 0));
+    TALP_TRY(grow(c, c->ws, pb + sizeof(MetricsOut)));
+    MetricsOut* dparts = static_cast<MetricsOut*>(c->ws.p);
+    MetricsOut* dres = reinterpret_cast<MetricsOut*>(static_cast<char*>(c->ws.p) + pb);
+    TALP_CUDA(cudaEventSynchronize(c->ev_up));
+    TALP_TRY(grow_pinned(c->up, pb));
+    memcpy(c->up.p, parts, sizeof(MetricsOut) * n_parts);
+    TALP_CUDA(cudaMemcpyAsync(dparts, c->up.p, sizeof(MetricsOut) * n_parts, cudaMemcpyHostToDevice, stream));
+    TALP_CUDA(cudaEventRecord(c->ev_up, stream));
+    TALP_CUDA(launch_combine(dparts, static_cast<uint32_t>(n_parts), dres, stream));
+    ++c->kernel_launches;
+    TALP_TRY(grow_pinned(c->down, sizeof(MetricsOut)));
+    TALP_CUDA(cudaMemcpyAsync(c->down.p, dres, sizeof(MetricsOut), cudaMemcpyDeviceToHost, stream));
+    TALP_CUDA(cudaEventRecord(c->ev_ws, stream));
+    c->ws_used = true;
+    TALP_CUDA(cudaStreamSynchronize(stream));
+    memcpy(out_host, c->down.p, sizeof(MetricsOut));
+    return check_metrics_flags(out_host, 1);
+}
+
 talp_gpu_status talp_gpu_unit_sums(talp_gpu_ctx* c, uint64_t trace_id, uint32_t region, int64_t* host_out,
                                    int64_t* dev_out, void* stream_) {
     if (!c) return fail(TALP_GPU_EINVAL, "null context");

@@ -38,6 +38,7 @@ cudaError_t launch_fixup(const SegDesc* segs, const uint64_t* seg_start, const W
 cudaError_t launch_prep(const FillJob* jobs, uint32_t n_jobs, cudaStream_t stream);
 
 cudaError_t launch_finalize(const FinalizeJob* jobs, uint32_t n_jobs, cudaStream_t stream);
+cudaError_t launch_combine(const MetricsOut* parts, uint32_t n_parts, MetricsOut* out, cudaStream_t stream);
 
 // Sort stage over the device segments flagged out of order (sortable ones),
 // then the segment table of their sorted copies for the re-sweep.

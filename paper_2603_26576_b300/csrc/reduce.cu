@@ -167,6 +167,36 @@ __device__ __forceinline__ double ratio(int64_t num, int64_t den) {
     return __ddiv_rn(__ll2double_rn(num), __ll2double_rn(den));
 }
 
+// The nine ratios from the region's integer aggregates (o.flags holds the
+// status bits on entry; EMPTY and NO_DEVICES are set here).  E = 0 gives
+// EMPTY with every ratio 1; 0/0 := 1 for the factors.
+__device__ __forceinline__ void form_ratios(MetricsOut& o) {
+    const int64_t E = o.elapsed_ns, n = o.n_ranks, m = o.m_devices;
+    const int64_t sU = o.sum_useful, sW = o.sum_offload, maxUW = o.max_useful_offload;
+    const int64_t sK = o.sum_kernel, maxK = o.max_kernel, maxB = o.max_busy;
+    if (E == 0) {
+        o.flags |= 0x1u;
+        if (m == 0) o.flags |= 0x4u;
+        o.host_pe = o.host_mpi_pe = o.host_mpi_lb = o.host_mpi_ce = o.host_oe = 1.0;
+        o.dev_pe = o.dev_lb = o.dev_ce = o.dev_oe = 1.0;
+        return;
+    }
+    o.host_pe = ratio_k(sU, E, n);          // Eq. 6
+    o.host_mpi_pe = ratio_k(sU + sW, E, n); // Eq. 7
+    o.host_mpi_lb = ratio_k(sU + sW, n, maxUW);
+    o.host_mpi_ce = ratio(maxUW, E);
+    o.host_oe = ratio(sU, sU + sW);         // Eq. 8
+    if (m == 0) {
+        o.flags |= 0x4u;
+        o.dev_pe = o.dev_lb = o.dev_ce = o.dev_oe = 1.0;
+        return;
+    }
+    o.dev_pe = ratio_k(sK, E, m);           // Eq. 9
+    o.dev_lb = ratio_k(sK, m, maxK);        // Eq. 10
+    o.dev_ce = ratio(maxK, maxB);           // Eq. 11
+    o.dev_oe = ratio(maxB, E);              // Eq. 12
+}
+
 template <typename T, typename Op>
 __device__ __forceinline__ T block_reduce(T v, Op op, T* sh) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -229,17 +259,17 @@ __global__ void __launch_bounds__(256) finalize_kernel(const FinalizeJob* __rest
     sHid = block_reduce<long long>(sHid, add, sh);
     if (threadIdx.x != 0) return;
 
-    MetricsOut o;
-    o.trace_id = t.trace_id;
-    o.region = r;
-    o.n_ranks = t.n;
-    o.m_devices = t.m;
     uint32_t fl = 0;
     if (not_tiled) fl |= 0x2u;
     const uint32_t st = *t.status;
     if (st & (ST_BAD_END | ST_BAD_KIND)) fl |= 0x100u;
     if (st & ST_UNSORTED) fl |= 0x200u;
     if (st & ST_TIMEOUT) fl |= 0x400u;
+    MetricsOut o;
+    o.trace_id = t.trace_id;
+    o.region = r;
+    o.n_ranks = t.n;
+    o.m_devices = t.m;
     o.elapsed_ns = E;
     o.sum_useful = sU;
     o.sum_offload = sW;
@@ -251,30 +281,83 @@ __global__ void __launch_bounds__(256) finalize_kernel(const FinalizeJob* __rest
     o.sum_mem = sM;
     o.sum_idle = sIdle;
     o.sum_hidden_mem = sHid;
-    if (E == 0) {
-        fl |= 0x1u;
-        if (t.m == 0) fl |= 0x4u;
-        o.host_pe = o.host_mpi_pe = o.host_mpi_lb = o.host_mpi_ce = o.host_oe = 1.0;
-        o.dev_pe = o.dev_lb = o.dev_ce = o.dev_oe = 1.0;
-    } else {
-        const int64_t n = t.n, m = t.m;
-        o.host_pe = ratio_k(sU, E, n);          // Eq. 6
-        o.host_mpi_pe = ratio_k(sU + sW, E, n); // Eq. 7
-        o.host_mpi_lb = ratio_k(sU + sW, n, maxUW);
-        o.host_mpi_ce = ratio(maxUW, E);
-        o.host_oe = ratio(sU, sU + sW);         // Eq. 8
-        if (m == 0) {
-            fl |= 0x4u;
-            o.dev_pe = o.dev_lb = o.dev_ce = o.dev_oe = 1.0;
-        } else {
-            o.dev_pe = ratio_k(sK, E, m);       // Eq. 9
-            o.dev_lb = ratio_k(sK, m, maxK);    // Eq. 10
-            o.dev_ce = ratio(maxK, maxB);       // Eq. 11
-            o.dev_oe = ratio(maxB, E);          // Eq. 12
-        }
-    }
     o.flags = fl;
+    form_ratios(o);
     *job.out = o;
+}
+
+// ---------------------------------------------------------------- combine
+//
+// Aggregates of one region computed on disjoint shards of a trace (whole
+// ranks with their devices) combine exactly: E and the maxima by max, the
+// sums and the unit counts by addition, the status bits by or.  One CTA
+// reduces the shard records and forms the ratios with the same code as the
+// single-shard finalize.
+__global__ void __launch_bounds__(256) combine_kernel(const MetricsOut* __restrict__ parts, uint32_t n_parts,
+                                                      MetricsOut* __restrict__ out) {
+    __shared__ long long sh[32];
+    auto add = [](long long a, long long b) { return a + b; };
+    auto mx = [](long long a, long long b) { return a > b ? a : b; };
+    auto bor = [](long long a, long long b) { return a | b; };
+    long long E = 0, sU = 0, sW = 0, sP = 0, maxUW = 0, sK = 0, maxK = 0, maxB = 0, sM = 0, sIdle = 0, sHid = 0;
+    long long n = 0, m = 0, fl = 0;
+    for (uint32_t k = threadIdx.x; k < n_parts; k += blockDim.x) {
+        const MetricsOut& p = parts[k];
+        E = mx(E, p.elapsed_ns);
+        sU += p.sum_useful;
+        sW += p.sum_offload;
+        sP += p.sum_mpi;
+        maxUW = mx(maxUW, p.max_useful_offload);
+        sK += p.sum_kernel;
+        maxK = mx(maxK, p.max_kernel);
+        maxB = mx(maxB, p.max_busy);
+        sM += p.sum_mem;
+        sIdle += p.sum_idle;
+        sHid += p.sum_hidden_mem;
+        n += p.n_ranks;
+        m += p.m_devices;
+        fl |= p.flags & 0x702u;   // status bits and HOST_NOT_TILED; EMPTY / NO_DEVICES are recomputed
+    }
+    E = block_reduce<long long>(E, mx, sh);
+    sU = block_reduce<long long>(sU, add, sh);
+    sW = block_reduce<long long>(sW, add, sh);
+    sP = block_reduce<long long>(sP, add, sh);
+    maxUW = block_reduce<long long>(maxUW, mx, sh);
+    sK = block_reduce<long long>(sK, add, sh);
+    maxK = block_reduce<long long>(maxK, mx, sh);
+    maxB = block_reduce<long long>(maxB, mx, sh);
+    sM = block_reduce<long long>(sM, add, sh);
+    sIdle = block_reduce<long long>(sIdle, add, sh);
+    sHid = block_reduce<long long>(sHid, add, sh);
+    n = block_reduce<long long>(n, add, sh);
+    m = block_reduce<long long>(m, add, sh);
+    fl = block_reduce<long long>(fl, bor, sh);
+    if (threadIdx.x != 0) return;
+    MetricsOut o;
+    o.trace_id = parts[0].trace_id;
+    o.region = parts[0].region;
+    o.n_ranks = static_cast<uint32_t>(n);
+    o.m_devices = static_cast<uint32_t>(m);
+    o.elapsed_ns = E;
+    o.sum_useful = sU;
+    o.sum_offload = sW;
+    o.sum_mpi = sP;
+    o.max_useful_offload = maxUW;
+    o.sum_kernel = sK;
+    o.max_kernel = maxK;
+    o.max_busy = maxB;
+    o.sum_mem = sM;
+    o.sum_idle = sIdle;
+    o.sum_hidden_mem = sHid;
+    o.flags = static_cast<uint32_t>(fl);
+    form_ratios(o);
+    *out = o;
+}
+
+cudaError_t launch_combine(const MetricsOut* parts, uint32_t n_parts, MetricsOut* out, cudaStream_t stream) {
+    if (n_parts == 0) return cudaSuccess;
+    combine_kernel<<<1, 256, 0, stream>>>(parts, n_parts, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(const FinalizeJob* jobs, uint32_t n_jobs, cudaStream_t stream) {
