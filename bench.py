@@ -58,9 +58,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
-    ap.add_argument("--workload", default="plain", choices=["plain", "small", "batched", "serving"])
+    ap.add_argument("--workload", default="plain",
+                    choices=["plain", "small", "scale", "batched", "batched-full", "serving"])
+    ap.add_argument("--wave-records", type=float, default=3e9, help="batched-full: records per wave")
     ap.add_argument("--traces", type=int, default=4096, help="batched: number of traces")
-    ap.add_argument("--ev-hi", type=int, default=5000, help="batched: largest events per GPU")
+    ap.add_argument("--ev-hi", type=int, default=None,
+                    help="batched: largest events per GPU (default 5000; batched-full 1e6)")
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--jobs", type=int, default=256, help="serving: monitored jobs")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: batch arrivals per second (all jobs)")
@@ -75,6 +78,12 @@ def parse():
 
 
 def workload(name, scale, rank):
+    if name == "scale":
+        from tracegen import igen
+        spec = igen.scale_spec(seed=0x7A1F + 3 + 1000 * rank, scale=scale, trace_id=3 + rank)
+        desc = "scale trace: 1024 ranks x 4 GPUs x 8 streams, bimodal kernels, 20% of ranks with 1.5x events, " \
+               "222k device events/GPU, 100k host intervals/rank, 4 nested regions (generated in HBM)"
+        return spec, desc
     if name == "plain":
         t = tg.plain_large(seed=0x7A1F + 1 + 1000 * rank, scale=scale, trace_id=1 + rank)
         desc = "plain large single trace: 64 ranks x 4 GPUs x 4 streams, 2M device events/GPU, " \
@@ -87,6 +96,12 @@ def workload(name, scale, rank):
 
 def oracle_sample(name, scale):
     """A bounded sample of the workload for the CPU oracle: one rank of it."""
+    if name == "scale":
+        from tracegen import igen
+        spec = igen.scale_spec(scale=scale)
+        T = igen.rank_ends(spec)
+        heavy = int(np.argmax(spec.dev_events[::4]))
+        return igen.host_trace(spec, T, ranks=[heavy])
     if name == "plain":
         return tg.plain_large(seed=0x7A1F + 1, scale=scale, trace_id=1, n_ranks=1)
     return tg.single_trace_small(scale=scale)
@@ -223,6 +238,9 @@ def run_reference(a):
 def workload_name(a):
     if a.workload == "plain":
         base = "plain large single trace: 64 ranks x 4 GPUs x 4 streams, 2M device events/GPU, 1M host intervals/rank, 4 nested regions"
+    elif a.workload == "scale":
+        base = ("scale trace: 1024 ranks x 4 GPUs x 8 streams, bimodal kernels (1 us / 500 us, 80/20), 20% of ranks "
+                "with 1.5x events, 222k device events/GPU, 100k host intervals/rank, 4 nested regions")
     else:
         base = "single trace: 4 ranks x 1 GPU x 1 stream, 10k host + 10k device intervals/rank, 1 region"
     return base if a.scale == 1.0 else f"{base} (scale {a.scale})"
@@ -236,7 +254,8 @@ def run_batched(a):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     t0 = time.time()
-    ts = tg.batched_workload(n_traces=a.traces, ev_lo=5, ev_hi=a.ev_hi)
+    ev_hi = a.ev_hi or 5000
+    ts = tg.batched_workload(n_traces=a.traces, ev_lo=5, ev_hi=ev_hi)
     gen_s = time.time() - t0
     N = sum(t.n_records for t in ts)
     # one device buffer per record array; each trace a 16-byte aligned view
@@ -314,7 +333,7 @@ def run_batched(a):
         "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int64", "data": "synthetic (seeded generator; the paper's traces are not available)",
         "config": {"workload": f"batched: {len(ts)} traces, ranks log-uniform 1-512, 1-8 GPUs per rank, "
-                               f"5-{a.ev_hi} device events per GPU log-uniform, 8 nested regions each",
+                               f"5-{ev_hi} device events per GPU log-uniform, 8 nested regions each",
                    "form": "one CUDA-graph launch of an autotuned plan per step", "records_per_step": N,
                    "plan": info, "plan_build_s": plan_s, "generate_s": gen_s,
                    "plain_one_trace_per_launch_events_per_s": N / plain_s,
@@ -330,6 +349,122 @@ def run_batched(a):
     plan.close()
     ctx.close()
     return 0 if agree else 1
+
+
+def run_batched_full(a):
+    """The batched workload at its full laws (4096 traces, 1e3-1e6 device
+    events per GPU: 2.6e11 records, 4.3 TB), far beyond HBM: consecutive
+    waves of whole traces are generated in HBM by the generator's device
+    twin (untimed), each wave is reduced by one CUDA-graph launch of a plan
+    (timed with CUDA events) and, for comparison, by one ingest + finalize
+    per trace.  The smallest trace of every wave is checked against the
+    oracle on the host twin's copy of it."""
+    import torch
+    import oracle
+    import paper_2603_26576_b300 as P
+    from tracegen import igen
+    torch.cuda.set_device(0)
+    ev_hi = a.ev_hi or 1_000_000
+    specs = igen.batched_specs(n_traces=a.traces, ev_hi=ev_hi)
+    wv = igen.waves(specs, int(a.wave_records))
+    stream = torch.cuda.Stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    tot_rec = tot_seg = 0
+    plan_ms = plain_ms = gen_s = build_s = 0.0
+    launches = 0
+    exact = True
+    checked = []
+    cpu_rec, cpu_s = 0, 0.0
+    ctx = P.Context(0)
+    clocks = Clocks(0)
+    clocks.start()
+    out_dev = torch.empty(8 * 200, dtype=torch.uint8, device="cuda")
+    for wi, w in enumerate(wv):
+        g0 = time.perf_counter()
+        dts = igen.generate_device(w, stream=stream)
+        torch.cuda.synchronize()
+        gen_s += time.perf_counter() - g0
+        arrays = [dict(host_se=d.host_se, host_state=d.host_state, dev_se=d.dev_se, dev_tag=d.dev_tag) for d in dts]
+        b0 = time.perf_counter()
+        plan = ctx.plan(dts, arrays, flags=P.TALP_GPU_SORTED_BY_START)
+        build_s += time.perf_counter() - b0
+        info = plan.info()
+        plan.launch(stream)                       # warm-up (and first result)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        plan.launch(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plan_ms += e0.elapsed_time(e1)
+        launches += info["kernels_per_launch"]
+        res = plan.metrics(stream)
+        # plain form on the same wave: one ingest + one finalize per trace
+        batches = []
+        for d, arr in zip(dts, arrays):
+            b, keep = P.batch_from_arrays(d.trace_id + (1 << 40), d.devices_per_rank, d.region_window,
+                                          arr["host_se"], arr["host_state"], d.host_off, arr["dev_se"],
+                                          arr["dev_tag"], d.dev_off, P.TALP_GPU_SORTED_BY_START)
+            batches.append((b, keep, d))
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for b, _, d in batches:
+            P.talp_gpu_ingest_events(ctx.ctx, [b], stream)
+            P.talp_gpu_region_metrics_device(ctx.ctx, [d.trace_id + (1 << 40)], P.TALP_GPU_ALL_REGIONS,
+                                             out_dev.data_ptr(), stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms += e0.elapsed_time(e1)
+        # the smallest trace of the wave against the oracle (when it is small
+        # enough for the host: waves of a few huge traces are not sampled)
+        k = int(np.argmin([sp.n_records for sp in w]))
+        if w[k].n_records <= 4_000_000:
+            ht = igen.host_trace(w[k], igen.rank_ends(w[k]))
+            q = sum(sp.n_regions for sp in w[:k])
+            c0 = time.perf_counter()
+            ref = [oracle.region_metrics(ht, r) for r in range(ht.n_regions)]
+            cpu_s += time.perf_counter() - c0
+            cpu_rec += ht.n_records
+            for r in range(ht.n_regions):
+                got = res[q + r]
+                for f in oracle.INT_FIELDS + oracle.RATIO_FIELDS:
+                    exact &= got[f] == ref[r][f]
+            checked.append(int(w[k].trace_id))
+        print(f"wave {wi + 1}/{len(wv)}: {info['records']} records, plan {plan_ms:.1f} ms, "
+              f"plain {plain_ms:.1f} ms, {time.perf_counter() - g0:.1f} s", file=sys.stderr, flush=True)
+        tot_rec += info["records"]
+        tot_seg += info["segments"]
+        plan.close()
+        ctx.reset()
+        del dts, arrays, batches
+        torch.cuda.empty_cache()
+    ck = clocks.stop()
+    ctx.close()
+    peak, peak_kind = measured_peaks()
+    value = tot_rec / (plan_ms / 1000.0)
+    achieved = BYTES_PER_RECORD * tot_rec / (plan_ms / 1000.0) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": len(wv), "warmup": len(wv),
+        "ms_per_step": plan_ms / len(wv), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64", "data": "synthetic (counter-based generator, made in HBM; the paper's traces are not available)",
+        "config": {"workload": f"batched at full laws: {a.traces} traces, ranks log-uniform 1-512, 1-8 GPUs per rank, "
+                               f"1e3-{ev_hi:g} device events per GPU log-uniform, 8 nested regions each",
+                   "form": "per wave of whole traces: one CUDA-graph launch of a plan (a step = one wave)",
+                   "waves": len(wv), "records": tot_rec, "bytes": BYTES_PER_RECORD * tot_rec, "segments": tot_seg,
+                   "wave_records_max": int(a.wave_records), "generate_s": gen_s, "plan_build_s": build_s,
+                   "plain_one_trace_per_launch_events_per_s": tot_rec / (plain_ms / 1000.0),
+                   "batched_over_plain": plain_ms / plan_ms,
+                   "oracle_checked_traces": checked, "bit_exact_sampled_vs_oracle": bool(exact),
+                   "l2": "every wave far larger than L2; no flush"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "whole graph (prep, sweep, fixup, finalize), summed over waves",
+                     "kernel_ms": plan_ms, "peak_source": f"{peak_kind} hbm_gbs"},
+        "cpu_baseline": {"value": cpu_rec / cpu_s if cpu_s else None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"the smallest trace of every wave ({cpu_rec} records), {cpu_s:.2f} s"},
+        "e2e": None, "gpu_launches": launches, "clocks": ck,
+    }
+    print(json.dumps(line), flush=True)
+    return 0 if exact else 1
 
 
 # ----------------------------------------------------------------- serving
@@ -593,6 +728,8 @@ def main():
         return run_reference(a)
     if a.workload == "batched":
         return run_batched(a)
+    if a.workload == "batched-full":
+        return run_batched_full(a)
     if a.workload == "serving":
         return run_serving(a)
     import torch
@@ -608,12 +745,18 @@ def main():
     dev = torch.device("cuda", local)
 
     t, _ = workload(a.workload, a.scale, rank)
+    if a.workload == "scale":
+        # generated straight into HBM by the generator's device twin
+        from tracegen import igen
+        (t,) = igen.generate_device([t], device=local)
+        d_arrays = dict(host_se=t.host_se, host_state=t.host_state, dev_se=t.dev_se, dev_tag=t.dev_tag)
+    else:
+        # device-resident copies of the records
+        d_arrays = dict(host_se=torch.from_numpy(t.host_se).to(dev),
+                        host_state=torch.from_numpy(t.host_state).to(dev),
+                        dev_se=torch.from_numpy(t.dev_se).to(dev), dev_tag=torch.from_numpy(t.dev_tag).to(dev))
     N = t.n_records
     R = t.n_regions
-
-    # device-resident copies of the records
-    d_arrays = dict(host_se=torch.from_numpy(t.host_se).to(dev), host_state=torch.from_numpy(t.host_state).to(dev),
-                    dev_se=torch.from_numpy(t.dev_se).to(dev), dev_tag=torch.from_numpy(t.dev_tag).to(dev))
     torch.cuda.synchronize()
     ctx = P.Context(local)
     stream = torch.cuda.Stream(device=dev)
@@ -665,10 +808,13 @@ def main():
     # ---- end to end through the C ABI from pinned host buffers
     e2e = None
     if not a.no_e2e:
-        h_arrays = dict(host_se=torch.from_numpy(t.host_se).pin_memory(),
-                        host_state=torch.from_numpy(t.host_state).pin_memory(),
-                        dev_se=torch.from_numpy(t.dev_se).pin_memory(),
-                        dev_tag=torch.from_numpy(t.dev_tag).pin_memory())
+        def pinned(x):
+            if hasattr(x, "is_cuda"):
+                h = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
+                h.copy_(x)
+                return h
+            return torch.from_numpy(x).pin_memory()
+        h_arrays = {k: pinned(getattr(t, k)) for k in ("host_se", "host_state", "dev_se", "dev_tag")}
         batch_h, keep_h = P.batch_from_arrays(t.trace_id, t.devices_per_rank, t.region_window, h_arrays["host_se"],
                                               h_arrays["host_state"], t.host_off, h_arrays["dev_se"],
                                               h_arrays["dev_tag"], t.dev_off, flags)
@@ -691,7 +837,7 @@ def main():
             tt = torch.tensor([el], device=dev)
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             el = float(tt.item())
-        h2d = (t.host_se.nbytes + t.host_state.nbytes + t.dev_se.nbytes + t.dev_tag.nbytes)
+        h2d = sum(int(v.numel() * v.element_size()) for v in h_arrays.values())
         meta = t.devices_per_rank.nbytes + t.region_window.nbytes + t.host_off.nbytes + t.dev_off.nbytes
         e2e = {"value": N * k * ws / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d + meta),
                "d2h_bytes_per_step": int(R * 200), "steps": k}
@@ -700,7 +846,7 @@ def main():
     peak, peak_kind = measured_peaks()
     sweep_ms = prof["sweep_ms"] / max(1, prof["sweep_launches"])
     achieved = BYTES_PER_RECORD * N / (sweep_ms / 1000.0) / 1e9
-    tpr = sweep_traffic_per_record()
+    tpr = sweep_traffic_per_record() if a.workload == "plain" else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": (tpr * N) if tpr is not None else None, "kernel": "talp::sweep_kernel",
             "kernel_ms": sweep_ms, "peak_source": f"{peak_kind} hbm_gbs"}
