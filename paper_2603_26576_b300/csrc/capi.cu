@@ -149,6 +149,7 @@ struct talp_gpu_ctx {
     std::vector<uint64_t> ev_records;
     uint64_t kernel_launches = 0;
     int64_t wait_limit = 4000000000LL;   // cycles (~2 s at 2 GHz)
+    int dependents = 0;                  // live plans and servers on this context
 };
 
 const TraceDev* talp::trace_device_desc(talp_gpu_ctx* c, uint64_t trace_id, uint32_t* n_regions) {
@@ -159,6 +160,8 @@ const TraceDev* talp::trace_device_desc(talp_gpu_ctx* c, uint64_t trace_id, uint
 }
 
 int talp::ctx_device(talp_gpu_ctx* c) { return c->device; }
+
+void talp::ctx_hold(talp_gpu_ctx* c, int delta) { c->dependents += delta; }
 
 struct talp_gpu_plan {
     talp_gpu_ctx* c = nullptr;
@@ -698,15 +701,20 @@ talp_gpu_status check_metrics_flags(const talp_gpu_metrics* out, size_t n) {
 }
 
 // Default segment cost in records: a segment switch costs about two tiles
-// of streaming, more with more regions (tiles of short segments straddle
-// most region boundaries).
-uint64_t default_seg_cost(uint32_t rmax) { return 512 + 64ull * rmax; }
+// of streaming, and every window boundary (2 per region beyond the first)
+// that falls inside the segment's time range costs one clipped re-pass of
+// the tile holding it.  Short segments are mostly such tiles; without this
+// term the slices of warps full of short segments run several times longer
+// than the others.
+uint64_t default_seg_cost(uint32_t rmax, uint32_t tile) {
+    return 512 + 64ull * rmax + 2ull * (rmax - 1) * tile;
+}
 
 Tuning pick_tuning(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches, size_t nb) {
     Tuning tu = c->defaults;
     uint32_t rmax = 1;
     for (size_t k = 0; k < nb; ++k) rmax = std::max(rmax, batches[k].n_regions);
-    if (!tu.seg_cost) tu.seg_cost = default_seg_cost(rmax);
+    if (!tu.seg_cost) tu.seg_cost = default_seg_cost(rmax, static_cast<uint32_t>(sweep_tile(tu.shape)));
     if (c->shape_forced || c->tune.empty()) return tu;
     uint64_t recs = 0, segs = 0;
     bool sorting = false;
@@ -767,6 +775,7 @@ talp_gpu_status talp_gpu_create(talp_gpu_ctx** out, int device, size_t hbm_budge
 
 talp_gpu_status talp_gpu_destroy(talp_gpu_ctx* c) {
     if (!c) return TALP_GPU_OK;
+    if (c->dependents > 0) return fail(TALP_GPU_EBUSY, "plans or servers still use this context");
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
     for (auto& kv : c->traces) free_trace(c, kv.second);
@@ -1016,6 +1025,7 @@ static void plan_release(talp_gpu_plan* p) {
     dev_free(c, p->ws.p, p->ws.cap);
     dev_free(c, p->sortbuf.p, p->sortbuf.cap);
     if (p->up.p) cudaFreeHost(p->up.p);
+    --c->dependents;
     delete p;
 }
 
@@ -1063,6 +1073,7 @@ talp_gpu_status talp_gpu_plan_create(talp_gpu_ctx* c, const talp_gpu_trace_batch
 
     talp_gpu_plan* p = new talp_gpu_plan();
     p->c = c;
+    ++c->dependents;
     talp_gpu_status st = get_traces(c, batches, nb, s, p->ts);
     if (st == TALP_GPU_OK) st = grow(c, p->ws, ws_max);
     if (st == TALP_GPU_OK && sb_max) st = grow(c, p->sortbuf, sb_max);

@@ -171,7 +171,7 @@ extern "C" talp_gpu_status talp_gpu_reduce_noalloc(const talp_gpu_trace_batch* b
         reinterpret_cast<uintptr_t>(b->dev_tag + nd) & ~static_cast<uintptr_t>(15));
     // virtual positions: records plus a fixed cost per segment (balances
     // segment switches across warps)
-    const uint64_t seg_cost = 512 + 64ull * R;
+    const uint64_t seg_cost = 512 + 64ull * R + 2ull * (R - 1) * static_cast<uint64_t>(sweep_tile(kDefaultSweepShape));
     uint64_t pos = 0, nrec = 0;
     uint32_t si = 0;
     for (uint32_t g = 0; g < m; ++g, ++si) {
