@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--plain-s", type=float, default=3.0, help="serving: seconds of the plain-form phase")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--unsorted", action="store_true",
+                    help="plain/small: device records grouped by stream (each stream in start order, as per-stream "
+                         "activity buffers deliver them); the library sorts them")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
@@ -243,6 +246,8 @@ def workload_name(a):
                 "with 1.5x events, 222k device events/GPU, 100k host intervals/rank, 4 nested regions")
     else:
         base = "single trace: 4 ranks x 1 GPU x 1 stream, 10k host + 10k device intervals/rank, 1 region"
+    if a.unsorted:
+        base += ", device records grouped by stream (sorted by the library)"
     return base if a.scale == 1.0 else f"{base} (scale {a.scale})"
 
 
@@ -754,6 +759,8 @@ def main():
         (t,) = igen.generate_device([t], device=local)
         d_arrays = dict(host_se=t.host_se, host_state=t.host_state, dev_se=t.dev_se, dev_tag=t.dev_tag)
     else:
+        if a.unsorted:
+            t = tg.interleave_lanes(t)
         # device-resident copies of the records
         d_arrays = dict(host_se=torch.from_numpy(t.host_se).to(dev),
                         host_state=torch.from_numpy(t.host_state).to(dev),
@@ -763,7 +770,7 @@ def main():
     torch.cuda.synchronize()
     ctx = P.Context(local)
     stream = torch.cuda.Stream(device=dev)
-    flags = P.TALP_GPU_SORTED_BY_START
+    flags = 0 if a.unsorted else P.TALP_GPU_SORTED_BY_START
     batch_d, keep_d = P.batch_from_arrays(t.trace_id, t.devices_per_rank, t.region_window, d_arrays["host_se"],
                                           d_arrays["host_state"], t.host_off, d_arrays["dev_se"],
                                           d_arrays["dev_tag"], t.dev_off, flags)
@@ -849,7 +856,7 @@ def main():
     peak, peak_kind = measured_peaks()
     sweep_ms = prof["sweep_ms"] / max(1, prof["sweep_launches"])
     achieved = BYTES_PER_RECORD * N / (sweep_ms / 1000.0) / 1e9
-    tpr = sweep_traffic_per_record() if a.workload == "plain" else None
+    tpr = sweep_traffic_per_record() if a.workload == "plain" and not a.unsorted else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": (tpr * N) if tpr is not None else None, "kernel": "talp::sweep_kernel",
             "kernel_ms": sweep_ms, "peak_source": f"{peak_kind} hbm_gbs"}
@@ -870,7 +877,9 @@ def main():
             "dtype": "int64", "data": "synthetic (seeded generator; the paper's traces are not available)",
             "config": {"workload": workload_name(a), "records_per_step": N, "bytes_per_step": BYTES_PER_RECORD * N,
                        "regions": R, "l2": "inputs (%.1f GB) larger than L2; no flush" % (BYTES_PER_RECORD * N / 1e9),
-                       "input_order": "device records in start order (caller asserts SORTED_BY_START)",
+                       "input_order": ("device records grouped by stream, each stream in start order; the "
+                                       "library finds the out-of-order devices and sorts them (sort stage)")
+                       if a.unsorted else "device records in start order (caller asserts SORTED_BY_START)",
                        "hbm_gb_per_s": BYTES_PER_RECORD * N * a.steps / (ms / 1000.0) / 1e9},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": ck,
             "check": {"elapsed_ns_region0": res[0].elapsed_ns, "dev_pe_region0": res[0].dev_pe},

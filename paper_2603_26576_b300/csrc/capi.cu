@@ -658,7 +658,7 @@ talp_gpu_status enqueue_ingest(talp_gpu_ctx* c, const Layout& L, const char* up,
             c->ev_pending.emplace_back(e0, e1);
             c->ev_records.push_back(L.n_records);
         }
-        TALP_CUDA(launch_fixup(dsegs, dstart, wrec, L.n_wrec, seg_flags, stream));
+        TALP_CUDA(launch_fixup(dsegs, dstart, wrec, L.n_wrec, seg_flags, L.sorting, stream));
         nl += 2;
         if (L.sorting) {
             // a2: sort the device segments found out of order, re-sweep them
@@ -676,7 +676,7 @@ talp_gpu_status enqueue_ingest(talp_gpu_ctx* c, const Layout& L, const char* up,
                                    static_cast<uint32_t>(L.n_dev_segs), wrec, seg_flags, gstatus, c->wait_limit,
                                    stream));
             TALP_CUDA(launch_fixup(rsegs, rstart, wrec, static_cast<uint32_t>(L.full_grid) * L.warps, seg_flags,
-                                   stream));
+                                   false, stream));
             nl += 2 + 24 + 1 + 2;
         }
     }

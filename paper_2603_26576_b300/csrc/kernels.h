@@ -33,7 +33,7 @@ cudaError_t launch_sweep(int shape, int rmax, int grid, const SegDesc* segs, con
                          uint32_t* gstatus, int64_t wait_limit, cudaStream_t stream);
 
 cudaError_t launch_fixup(const SegDesc* segs, const uint64_t* seg_start, const WarpRec* wrec, uint32_t n_wrec,
-                         uint32_t* seg_flags, cudaStream_t stream);
+                         uint32_t* seg_flags, bool skip_resorted, cudaStream_t stream);
 
 cudaError_t launch_prep(const FillJob* jobs, uint32_t n_jobs, cudaStream_t stream);
 

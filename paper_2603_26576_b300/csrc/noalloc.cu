@@ -252,7 +252,7 @@ extern "C" talp_gpu_status talp_gpu_reduce_noalloc(const talp_gpu_trace_batch* b
                          4000000000LL, stream);
     if (e == cudaSuccess && nrec > 0)
         e = launch_fixup(reinterpret_cast<const SegDesc*>(S + kOffSegs),
-                         reinterpret_cast<const uint64_t*>(S + kOffStart), wrec, n_wrec, flags, stream);
+                         reinterpret_cast<const uint64_t*>(S + kOffStart), wrec, n_wrec, flags, false, stream);
     if (e == cudaSuccess) e = launch_finalize(reinterpret_cast<const FinalizeJob*>(S + kOffFin), R, stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out_host, mout, sizeof(MetricsOut) * R, cudaMemcpyDeviceToHost, stream);

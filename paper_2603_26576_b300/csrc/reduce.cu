@@ -18,7 +18,7 @@ namespace talp {
 __global__ void __launch_bounds__(256) fixup_kernel(const SegDesc* __restrict__ segs,
                                                     const uint64_t* __restrict__ seg_start,
                                                     const WarpRec* __restrict__ wrec, uint32_t n_wrec,
-                                                    uint32_t* __restrict__ seg_flags) {
+                                                    uint32_t* __restrict__ seg_flags, bool skip_resorted) {
     constexpr int RM = 8;
     const int lane = threadIdx.x & 31;
     const uint32_t w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -36,6 +36,10 @@ __global__ void __launch_bounds__(256) fixup_kernel(const SegDesc* __restrict__ 
         atomicOr(d.status, ST_UNSORTED);
         atomicOr(&seg_flags[seg], ST_UNSORTED);
     }
+    // a segment already found out of order and allowed to sort is sorted and
+    // swept again from its saved sums: correcting this pass is wasted work
+    // (and, its records not being in order, not a short prefix)
+    if (skip_resorted && (d.pad[0] & kSegSortable) && (seg_flags[seg] & ST_UNSORTED)) return;
 
     // carry: running state + tails of the preceding warps inside this segment
     int64_t CK = d.carry_in[0];
@@ -127,11 +131,11 @@ __global__ void __launch_bounds__(256) fixup_kernel(const SegDesc* __restrict__ 
 }
 
 cudaError_t launch_fixup(const SegDesc* segs, const uint64_t* seg_start, const WarpRec* wrec, uint32_t n_wrec,
-                         uint32_t* seg_flags, cudaStream_t stream) {
+                         uint32_t* seg_flags, bool skip_resorted, cudaStream_t stream) {
     if (n_wrec == 0) return cudaSuccess;
     const int wpb = 8;
     const int grid = static_cast<int>((n_wrec + wpb - 1) / wpb);
-    fixup_kernel<<<grid, wpb * 32, 0, stream>>>(segs, seg_start, wrec, n_wrec, seg_flags);
+    fixup_kernel<<<grid, wpb * 32, 0, stream>>>(segs, seg_start, wrec, n_wrec, seg_flags, skip_resorted);
     return cudaGetLastError();
 }
 
