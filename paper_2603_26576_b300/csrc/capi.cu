@@ -113,6 +113,7 @@ struct Layout {
     size_t up_bytes = 0;
     size_t off_wrec = 0, off_flags = 0, off_gst = 0, off_bk = 0, off_slist = 0, off_srb = 0, off_stb = 0;
     size_t off_smn = 0, off_smx = 0, off_hist = 0, off_offs = 0, off_rsegs = 0, off_rstart = 0, off_mout = 0;
+    size_t off_nruns = 0, off_runs = 0, off_rounds = 0;
     size_t ws_bytes = 0, stage_bytes = 0, sortbuf_bytes = 0, new_bytes = 0;
     uint32_t nj = 0;
     std::vector<uint64_t> nh, nd;
@@ -408,7 +409,10 @@ talp_gpu_status size_ingest(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches
     L.off_smx = align_up(L.off_smn + 8 * L.sort_slots, 256);
     L.off_hist = align_up(L.off_smx + 8 * L.sort_slots, 256);
     L.off_offs = align_up(L.off_hist + 4 * 256 * L.sort_tiles, 256);
-    L.off_rsegs = align_up(L.off_offs + 8 * 256 * L.sort_tiles, 256);
+    L.off_nruns = align_up(L.off_offs + 8 * 256 * L.sort_tiles, 256);
+    L.off_runs = align_up(L.off_nruns + 4 * L.sort_slots, 256);
+    L.off_rounds = align_up(L.off_runs + 8 * (kMaxRuns + 1) * L.sort_slots, 256);
+    L.off_rsegs = align_up(L.off_rounds + 4 * L.sort_slots, 256);
     L.off_rstart = align_up(L.off_rsegs + sizeof(SegDesc) * (L.sorting ? L.n_dev_segs : 0), 256);
     L.off_rrend = align_up(L.off_rstart + 8 * (L.sorting ? L.n_dev_segs + 1 : 0), 256);
     L.off_mout = align_up(L.off_rrend + 8 * (L.sorting ? L.n_dev_segs + 1 : 0), 256);
@@ -617,6 +621,9 @@ talp_gpu_status fill_ingest(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches
         sc.mx = reinterpret_cast<int64_t*>(wsd + L.off_smx);
         sc.hist = reinterpret_cast<uint32_t*>(wsd + L.off_hist);
         sc.offs = reinterpret_cast<uint64_t*>(wsd + L.off_offs);
+        sc.nruns = reinterpret_cast<uint32_t*>(wsd + L.off_nruns);
+        sc.runs = reinterpret_cast<uint64_t*>(wsd + L.off_runs);
+        sc.rounds = reinterpret_cast<uint32_t*>(wsd + L.off_rounds);
         const size_t se_b = align_up(16 * L.sort_recs, 256), tg_b = align_up(L.sort_recs + 64, 256);
         for (int q = 0; q < 2; ++q) {
             char* base = sortbuf + q * (se_b + tg_b);
@@ -677,7 +684,7 @@ talp_gpu_status enqueue_ingest(talp_gpu_ctx* c, const Layout& L, const char* up,
                                    stream));
             TALP_CUDA(launch_fixup(rsegs, rstart, wrec, static_cast<uint32_t>(L.full_grid) * L.warps, seg_flags,
                                    false, stream));
-            nl += 2 + 24 + 1 + 2;
+            nl += 2 + 1 + kMergeRounds + 24 + 1 + 2;
         }
     }
     if (L.n_fin) {

@@ -88,7 +88,7 @@ constexpr uint8_t kSegSortable = 1;   // device segment may be sorted when found
 // Control block of the sort stage (device memory; pointers into scratch).
 struct SortCtl {
     uint32_t nflag;            // flagged segments
-    uint32_t pad;
+    uint32_t max_passes;       // most radix passes any flagged segment needs
     uint64_t nrec;             // their records
     uint64_t ntile;            // their sort tiles
     uint32_t* list;            // [slots] segment index of flagged segment k
@@ -102,7 +102,17 @@ struct SortCtl {
     uint8_t* buf_tag[2];
     const uint8_t* buf_tag_limit[2];
     const int64_t* const* restore;  // [segments] sums a flagged segment restarts from (null: zero)
+    uint32_t* nruns;           // [slots] descents found in k (runs - 1)
+    uint64_t* runs;            // [slots][kMaxRuns + 1] run boundaries of k (sorted by the merge plan)
+    uint32_t* rounds;          // [slots] pairwise merge rounds for k; 0: radix sort
+    uint32_t max_rounds;       // most merge rounds any flagged segment needs
+    uint32_t pad2;
 };
+
+// A flagged segment made of at most this many sorted runs (records grouped
+// by stream, each stream in start order) is merged instead of radix sorted.
+constexpr int kMaxRuns = 16;
+constexpr int kMergeRounds = 4;   // ceil(log2(kMaxRuns))
 
 // ---------------------------------------------------------------- helpers
 

@@ -16,6 +16,14 @@
 // the kernels of a pass skip segments that are done.  The re-sweep then
 // runs the ordinary sweep kernel over a segment table that points into the
 // sorted copies.
+//
+// A flagged segment that is only a few sorted runs laid end to end (records
+// grouped by stream, each stream in start order: the order per-stream
+// activity buffers deliver) is merged instead: the min/max kernel also
+// records where the start order descends, and when a segment has at most
+// kMaxRuns runs, ceil(log2(runs)) rounds of pairwise merge-path merges move
+// each record once per round, against once per 8-bit digit for the radix
+// sort, with coalesced reads and writes.
 #include "kernels.h"
 
 namespace talp {
@@ -32,6 +40,11 @@ __device__ __forceinline__ int passes_for(int64_t mn, int64_t mx) {
     return (bits + 7) / 8;
 }
 
+// radix passes of flagged segment k (0 when it is merged instead)
+__device__ __forceinline__ int radix_passes(const SortCtl* ctl, uint32_t k) {
+    return ctl->rounds[k] ? 0 : passes_for(ctl->mn[k], ctl->mx[k]);
+}
+
 // segment k of the flagged list owning tile t
 __device__ __forceinline__ uint32_t seg_of_tile(const SortCtl* ctl, uint32_t t) {
     uint32_t lo = 0, hi = ctl->nflag;
@@ -40,6 +53,15 @@ __device__ __forceinline__ uint32_t seg_of_tile(const SortCtl* ctl, uint32_t t) 
         if (ctl->tile_base[mid] <= t) lo = mid; else hi = mid;
     }
     return lo;
+}
+
+// In a grid-stride loop over tiles, the last tile before the first one of
+// this CTA's stride class past segment k (the loop's increment lands there):
+// skips the rest of a segment that has nothing to do in this launch.
+__device__ __forceinline__ uint32_t skip_segment(const SortCtl* ctl, uint32_t k, uint32_t t) {
+    const uint64_t end = ctl->tile_base[k + 1];
+    const uint64_t steps = (end - t + gridDim.x - 1) / gridDim.x;
+    return static_cast<uint32_t>(t + (steps - 1) * gridDim.x);
 }
 
 // ---------------------------------------------------------------- plan
@@ -98,6 +120,8 @@ __global__ void __launch_bounds__(1024) sort_plan_kernel(const SegDesc* __restri
             ctl->tile_base[k] = s_tbase + pt + wt - tiles;
             ctl->mn[k] = INT64_MAX;
             ctl->mx[k] = INT64_MIN;
+            ctl->nruns[k] = 0;
+            ctl->rounds[k] = 0;
             // the re-sweep recomputes this ingest's part of the segment: its
             // sums restart from their value before the ingest
             const SegDesc& d = segs[s];
@@ -117,6 +141,8 @@ __global__ void __launch_bounds__(1024) sort_plan_kernel(const SegDesc* __restri
         __syncthreads();
     }
     if (tid == 0) {
+        ctl->max_passes = 0;
+        ctl->max_rounds = 0;
         ctl->nflag = s_base;
         ctl->nrec = s_rbase;
         ctl->ntile = s_tbase;
@@ -133,10 +159,32 @@ __global__ void __launch_bounds__(kSortThreads) sort_minmax_kernel(const SegDesc
         const SegDesc& d = segs[ctl->list[k]];
         const uint64_t r0 = static_cast<uint64_t>(t - ctl->tile_base[k]) * kSortTile;
         int64_t mn = INT64_MAX, mx = INT64_MIN;
-        for (uint64_t j = r0 + threadIdx.x; j < d.n && j < r0 + kSortTile; j += kSortThreads) {
-            const int64_t s = d.se[2 * j];
-            mn = min64(mn, s);
-            mx = max64(mx, s);
+        uint64_t* runs = ctl->runs + static_cast<uint64_t>(k) * (kMaxRuns + 1);
+        for (uint64_t j0 = r0; j0 < d.n && j0 < r0 + kSortTile; j0 += kSortThreads) {
+            const uint64_t j = j0 + threadIdx.x;
+            bool desc = false;
+            if (j < d.n && j < r0 + kSortTile) {
+                const int64_t s = d.se[2 * j];
+                mn = min64(mn, s);
+                mx = max64(mx, s);
+                desc = j > 0 && s < d.se[2 * (j - 1)];
+            }
+            // positions where the start order descends (run starts); the
+            // count goes on past kMaxRuns only to tell the segment is not a
+            // few runs, so stop counting once it is far beyond
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, desc);
+            uint32_t seen = 0;
+            if (bal && (threadIdx.x & 31) == 0) seen = *static_cast<volatile uint32_t*>(&ctl->nruns[k]);
+            seen = __shfl_sync(0xFFFFFFFFu, seen, 0);   // warp-uniform decision below
+            if (bal && seen <= static_cast<uint32_t>(kMaxRuns)) {
+                uint32_t base = 0;
+                if ((threadIdx.x & 31) == 0) base = atomicAdd(&ctl->nruns[k], static_cast<uint32_t>(__popc(bal)));
+                base = __shfl_sync(0xFFFFFFFFu, base, 0);
+                if (desc) {
+                    const uint32_t slot = base + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u));
+                    if (slot < static_cast<uint32_t>(kMaxRuns)) runs[1 + slot] = j;
+                }
+            }
         }
 #pragma unroll
         for (int m = 16; m > 0; m >>= 1) {
@@ -178,10 +226,14 @@ __device__ __forceinline__ void pass_src(const SegDesc& d, const SortCtl* ctl, u
 __global__ void __launch_bounds__(kSortThreads) sort_hist_kernel(const SegDesc* __restrict__ segs, SortCtl* ctl,
                                                                  int p) {
     __shared__ uint32_t h[256];
+    if (static_cast<uint32_t>(p) >= ctl->max_passes) return;
     const uint32_t ntile = static_cast<uint32_t>(ctl->ntile);
     for (uint32_t t = blockIdx.x; t < ntile; t += gridDim.x) {
         const uint32_t k = seg_of_tile(ctl, t);
-        if (p >= passes_for(ctl->mn[k], ctl->mx[k])) continue;   // block-uniform
+        if (p >= radix_passes(ctl, k)) {   // block-uniform
+            t = skip_segment(ctl, k, t);
+            continue;
+        }
         const SegDesc& d = segs[ctl->list[k]];
         const int64_t* se;
         const uint8_t* tag;
@@ -204,9 +256,10 @@ __global__ void __launch_bounds__(kSortThreads) sort_hist_kernel(const SegDesc* 
 // hist[t][d] -> absolute output offset of tile t's first record of digit d
 __global__ void __launch_bounds__(256) sort_scan_kernel(SortCtl* ctl, int p) {
     __shared__ uint32_t s_tot[256];
+    if (static_cast<uint32_t>(p) >= ctl->max_passes) return;
     const uint32_t d = threadIdx.x;
     for (uint32_t k = blockIdx.x; k < ctl->nflag; k += gridDim.x) {
-        if (p >= passes_for(ctl->mn[k], ctl->mx[k])) continue;
+        if (p >= radix_passes(ctl, k)) continue;
         const uint64_t t0 = ctl->tile_base[k], t1 = ctl->tile_base[k + 1];
         uint64_t tot = 0;
         for (uint64_t t = t0; t < t1; ++t) tot += ctl->hist[t * 256 + d];
@@ -230,11 +283,15 @@ __global__ void __launch_bounds__(256) sort_scan_kernel(SortCtl* ctl, int p) {
 __global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(const SegDesc* __restrict__ segs, SortCtl* ctl,
                                                                     int p) {
     __shared__ uint32_t cnt[kSortThreads / 32][256];
+    if (static_cast<uint32_t>(p) >= ctl->max_passes) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t ntile = static_cast<uint32_t>(ctl->ntile);
     for (uint32_t t = blockIdx.x; t < ntile; t += gridDim.x) {
         const uint32_t k = seg_of_tile(ctl, t);
-        if (p >= passes_for(ctl->mn[k], ctl->mx[k])) continue;
+        if (p >= radix_passes(ctl, k)) {
+            t = skip_segment(ctl, k, t);
+            continue;
+        }
         const SegDesc& d = segs[ctl->list[k]];
         const int64_t* se;
         const uint8_t* tag;
@@ -292,6 +349,184 @@ __global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(const SegDes
     }
 }
 
+
+// --------------------------------------------------------------- merge plan
+// One thread per flagged segment: a segment of at most kMaxRuns sorted runs
+// gets its run starts in order and its number of merge rounds.
+__global__ void sort_merge_plan_kernel(const SegDesc* __restrict__ segs, SortCtl* ctl) {
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < ctl->nflag; k += gridDim.x * blockDim.x) {
+        const uint32_t c = ctl->nruns[k];
+        if (c == 0 || c + 1 > static_cast<uint32_t>(kMaxRuns)) {
+            ctl->rounds[k] = 0;
+            atomicMax(&ctl->max_passes, static_cast<uint32_t>(passes_for(ctl->mn[k], ctl->mx[k])));
+            continue;
+        }
+        uint64_t* runs = ctl->runs + static_cast<uint64_t>(k) * (kMaxRuns + 1);
+        for (uint32_t i = 2; i <= c; ++i) {   // insertion sort of runs[1 .. c]
+            const uint64_t v = runs[i];
+            uint32_t q = i;
+            while (q > 1 && runs[q - 1] > v) {
+                runs[q] = runs[q - 1];
+                --q;
+            }
+            runs[q] = v;
+        }
+        runs[0] = 0;
+        runs[c + 1] = segs[ctl->list[k]].n;
+        uint32_t r = 0;
+        while ((1u << r) < c + 1) ++r;
+        ctl->rounds[k] = r;
+        atomicMax(&ctl->max_rounds, r);
+    }
+}
+
+// ------------------------------------------------------------------ merge
+// Round r merges, in every merged segment, the pairs of adjacent groups of
+// 2^r runs.  A CTA takes the outputs of one sort tile, 1024 at a time; for
+// each pair those outputs overlap it finds the merge-path split at both
+// ends (ties taken from the earlier group, so the merge is stable), stages
+// the two input ranges in shared memory, merges 4 outputs per thread and
+// writes the rows back coalesced.
+constexpr int kMergeChunk = 1024;
+
+__device__ __forceinline__ uint64_t merge_split(const int64_t* A, uint64_t nA, const int64_t* B, uint64_t nB,
+                                                uint64_t q) {
+    uint64_t lo = q > nB ? q - nB : 0, hi = q < nA ? q : nA;
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (A[2 * mid] <= B[2 * (q - 1 - mid)]) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// merge input of round r for segment k (the original records, or the
+// buffer written by the previous round)
+__device__ __forceinline__ void merge_src(const SegDesc& d, const SortCtl* ctl, uint32_t k, int r,
+                                          const int64_t*& se, const uint8_t*& tag) {
+    if (r == 0) {
+        se = d.se;
+        tag = d.tag;
+    } else {
+        se = ctl->buf_se[(r - 1) & 1] + 2 * ctl->rec_base[k];
+        tag = ctl->buf_tag[(r - 1) & 1] + ctl->rec_base[k];
+    }
+}
+
+// Merge-path split at the start of every output chunk of round r, one
+// thread per chunk (the dependent binary searches of all chunks overlap):
+// the number of the chunk's pair's first-group records among the pair's
+// outputs before the chunk.  Stored in offs[tile * 256 + half] (the radix
+// offsets of a merged segment's tiles are not used).
+__global__ void __launch_bounds__(256) sort_merge_split_kernel(const SegDesc* __restrict__ segs, SortCtl* ctl,
+                                                               int r) {
+    if (static_cast<uint32_t>(r) >= ctl->max_rounds) return;
+    const uint64_t nb = ctl->ntile * (kSortTile / kMergeChunk);
+    for (uint64_t b = blockIdx.x * 256ull + threadIdx.x; b < nb; b += gridDim.x * 256ull) {
+        const uint32_t t = static_cast<uint32_t>(b / (kSortTile / kMergeChunk));
+        const uint32_t half = static_cast<uint32_t>(b % (kSortTile / kMergeChunk));
+        const uint32_t k = seg_of_tile(ctl, t);
+        const uint32_t R = ctl->rounds[k];
+        if (R == 0 || static_cast<uint32_t>(r) >= R) continue;
+        const SegDesc& d = segs[ctl->list[k]];
+        const uint64_t h = static_cast<uint64_t>(t - ctl->tile_base[k]) * kSortTile + half * kMergeChunk;
+        if (h >= d.n) continue;
+        const int64_t* se;
+        const uint8_t* tag;
+        merge_src(d, ctl, k, r, se, tag);
+        const uint64_t* runs = ctl->runs + static_cast<uint64_t>(k) * (kMaxRuns + 1);
+        const uint32_t nr = ctl->nruns[k] + 1;
+        const uint32_t w = 1u << r;
+        for (uint32_t g = 0; g < nr; g += 2 * w) {
+            const uint64_t pa = runs[g], pm = runs[min(g + w, nr)], pb = runs[min(g + 2 * w, nr)];
+            if (h >= pa && h < pb) {
+                ctl->offs[static_cast<uint64_t>(t) * 256 + half] =
+                    merge_split(se + 2 * pa, pm - pa, se + 2 * pm, pb - pm, h - pa);
+                break;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) sort_merge_kernel(const SegDesc* __restrict__ segs, SortCtl* ctl, int r) {
+    __shared__ longlong2 s_in[kMergeChunk];
+    __shared__ longlong2 s_out[kMergeChunk];
+    __shared__ uint8_t s_tin[kMergeChunk];
+    __shared__ uint8_t s_tout[kMergeChunk];
+    if (static_cast<uint32_t>(r) >= ctl->max_rounds) return;
+    const uint32_t ntile = static_cast<uint32_t>(ctl->ntile);
+    for (uint32_t t = blockIdx.x; t < ntile; t += gridDim.x) {
+        const uint32_t k = seg_of_tile(ctl, t);
+        const uint32_t R = ctl->rounds[k];
+        if (R == 0 || static_cast<uint32_t>(r) >= R) {   // block-uniform
+            t = skip_segment(ctl, k, t);
+            continue;
+        }
+        const SegDesc& d = segs[ctl->list[k]];
+        const int64_t* se;
+        const uint8_t* tag;
+        merge_src(d, ctl, k, r, se, tag);
+        int64_t* dse = ctl->buf_se[r & 1] + 2 * ctl->rec_base[k];
+        uint8_t* dtag = ctl->buf_tag[r & 1] + ctl->rec_base[k];
+        const uint64_t* runs = ctl->runs + static_cast<uint64_t>(k) * (kMaxRuns + 1);
+        const uint32_t nr = ctl->nruns[k] + 1;
+        const uint32_t w = 1u << r;
+        const uint64_t tb = ctl->tile_base[k];
+        const uint64_t t0 = static_cast<uint64_t>(t - tb) * kSortTile;
+        const uint64_t t1 = min(t0 + static_cast<uint64_t>(kSortTile), d.n);
+        for (uint64_t h0 = t0; h0 < t1; h0 += kMergeChunk) {
+            const uint64_t h1 = min(h0 + static_cast<uint64_t>(kMergeChunk), t1);
+            for (uint32_t g = 0; g < nr; g += 2 * w) {
+                const uint64_t pa = runs[g];
+                const uint64_t pm = runs[min(g + w, nr)];
+                const uint64_t pb = runs[min(g + 2 * w, nr)];
+                if (pb <= h0 || pa >= h1) continue;
+                const uint64_t lo = max(h0, pa), hi = min(h1, pb);
+                const uint64_t nA = pm - pa;
+                // splits at the chunk's ends (stored by the split kernel),
+                // or the pair's own ends when the pair starts or ends inside
+                const uint64_t i0 = pa >= h0 ? 0
+                                             : ctl->offs[(tb + h0 / kSortTile) * 256 + (h0 % kSortTile) / kMergeChunk];
+                const uint64_t i1 = pb <= h1 ? nA
+                                             : ctl->offs[(tb + h1 / kSortTile) * 256 + (h1 % kSortTile) / kMergeChunk];
+                const uint64_t j0 = (lo - pa) - i0, j1 = (hi - pa) - i1;
+                const int ca = static_cast<int>(i1 - i0), cb = static_cast<int>(j1 - j0);
+                for (int q = threadIdx.x; q < ca + cb; q += blockDim.x) {
+                    const uint64_t src = q < ca ? pa + i0 + q : pm + j0 + (q - ca);
+                    s_in[q] = *reinterpret_cast<const longlong2*>(se + 2 * src);
+                    s_tin[q] = tag[src];
+                }
+                __syncthreads();
+                // 4 outputs per thread: merge path inside the staged ranges
+                const int n = ca + cb;
+                const int o0 = min(static_cast<int>(threadIdx.x) * 4, n);
+                const int o1 = min(o0 + 4, n);
+                if (o0 < o1) {
+                    int a = max(0, o0 - cb), b = min(o0, ca);
+                    while (a < b) {
+                        const int mid = (a + b) >> 1;
+                        if (s_in[mid].x <= s_in[ca + o0 - 1 - mid].x) a = mid + 1;
+                        else b = mid;
+                    }
+                    int ia = a, ib = o0 - a;
+                    for (int o = o0; o < o1; ++o) {
+                        const bool takeA = ib >= cb || (ia < ca && s_in[ia].x <= s_in[ca + ib].x);
+                        const int src = takeA ? ia++ : ca + ib++;
+                        s_out[o] = s_in[src];
+                        s_tout[o] = s_tin[src];
+                    }
+                }
+                __syncthreads();
+                for (int q = threadIdx.x; q < n; q += blockDim.x) {
+                    *reinterpret_cast<longlong2*>(dse + 2 * (lo + q)) = s_out[q];
+                    dtag[lo + q] = s_tout[q];
+                }
+                __syncthreads();
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------- re-sweep table
 // Flagged segment k becomes segment k of a new table whose records are the
 // sorted copy; slots nflag .. n_slots-1 are empty segments.
@@ -306,7 +541,7 @@ __global__ void __launch_bounds__(256) sort_resweep_plan_kernel(const SegDesc* _
         }
         if (k < nflag) {
             SegDesc s = segs[ctl->list[k]];
-            const int P = passes_for(ctl->mn[k], ctl->mx[k]);
+            const int P = ctl->rounds[k] ? static_cast<int>(ctl->rounds[k]) : passes_for(ctl->mn[k], ctl->mx[k]);
             const int b = (P - 1) & 1;
             s.se = ctl->buf_se[b] + 2 * ctl->rec_base[k];
             s.tag = ctl->buf_tag[b] + ctl->rec_base[k];
@@ -334,6 +569,11 @@ cudaError_t launch_sort_stage(const SegDesc* segs, uint32_t n_segs, uint32_t n_s
     if (n_slots == 0) return cudaSuccess;
     sort_plan_kernel<<<1, 1024, 0, stream>>>(segs, n_segs, seg_flags, ctl);
     sort_minmax_kernel<<<grid_tiles, kSortThreads, 0, stream>>>(segs, ctl);
+    sort_merge_plan_kernel<<<grid_segs, 32, 0, stream>>>(segs, ctl);
+    for (int r = 0; r < kMergeRounds; ++r) {
+        sort_merge_split_kernel<<<grid_tiles, 256, 0, stream>>>(segs, ctl, r);
+        sort_merge_kernel<<<grid_tiles, 256, 0, stream>>>(segs, ctl, r);
+    }
     for (int p = 0; p < 8; ++p) {
         sort_hist_kernel<<<grid_tiles, kSortThreads, 0, stream>>>(segs, ctl, p);
         sort_scan_kernel<<<grid_segs, 256, 0, stream>>>(ctl, p);

@@ -37,6 +37,24 @@ def test_unsorted_mid_size(ctx, mode):
     ctx.reset()
 
 
+@pytest.mark.parametrize("k", [2, 3, 5, 16, 17, 40])
+def test_few_sorted_runs(ctx, k):
+    """Segments made of k sorted runs: up to 16 runs take the merge path,
+    more the radix path; ties across runs, one-record runs and segments
+    shorter and longer than a sort tile included."""
+    for seed in range(2):
+        base = tg.random_trace(seed + 10 * k, trace_id=seed, n_ranks=3, devices_per_rank=[2, 1, 3],
+                               dev_events=[9000, 2, 1, 20000, 5000, 4097], host_events=[300, 10, 7], n_regions=3)
+        t = tg.split_runs(base, k, seed=seed)
+        ctx.ingest([t])
+        assert_trace_equal(ctx, t, ("runs", k, seed))
+    ts = [tg.split_runs(tg.tiny_trace(s, trace_id=s, max_events=300, horizon=512), k, seed=s) for s in range(40)]
+    ctx.ingest(ts)
+    for t in ts:
+        assert_trace_equal(ctx, t, ("runs-tiny", k), sums=(t.trace_id % 3 == 0))
+    ctx.reset()
+
+
 def test_unsorted_wide_timestamps(ctx):
     """Keys spanning many radix digits (up to 8 passes)."""
     for scale, offset in [(1 << 30, 0), (1 << 45, -(1 << 61)), (7, (1 << 61))]:

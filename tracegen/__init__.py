@@ -598,6 +598,24 @@ def shuffle_segments(trace: Trace, seed=1, frac=1.0) -> Trace:
     return _with_dev(trace, se, tag)
 
 
+def split_runs(trace: Trace, k: int, seed=3) -> Trace:
+    """Deal each device's records (in start order) into k groups at random
+    and lay the groups end to end: every segment becomes at most k sorted
+    runs, as records grouped by stream are."""
+    rng = _rng(seed, trace.trace_id, D_TRACE, 31)
+    se = trace.dev_se.copy()
+    tag = trace.dev_tag.copy()
+    for g in range(trace.m_devices):
+        a, b = int(trace.dev_off[g]), int(trace.dev_off[g + 1])
+        if b - a < 2:
+            continue
+        grp = rng.integers(0, k, b - a)
+        order = np.argsort(grp, kind="stable")
+        se[a:b] = se[a:b][order]
+        tag[a:b] = tag[a:b][order]
+    return _with_dev(trace, se, tag)
+
+
 def _with_dev(trace, se, tag):
     return Trace(trace_id=trace.trace_id, n_ranks=trace.n_ranks, devices_per_rank=trace.devices_per_rank,
                  region_window=trace.region_window, host_se=trace.host_se, host_state=trace.host_state,
