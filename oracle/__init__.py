@@ -67,6 +67,8 @@ class Oracle:
         lib.oracle_device_unions.restype = ctypes.c_int
         lib.oracle_metrics.argtypes = [ctypes.c_uint32, P, P, P, P, P, P, P]
         lib.oracle_metrics.restype = None
+        lib.oracle_concurrency.argtypes = [ctypes.c_uint32, P, P, P, P, P, ctypes.c_uint32, P]
+        lib.oracle_concurrency.restype = ctypes.c_int
         self.lib = lib
 
     def validate(self, t) -> int:
@@ -94,6 +96,19 @@ class Oracle:
         rc = self.lib.oracle_device_unions(n, _p(dpr), _p(dse), _p(dtg), _p(doff), _p(win), _p(out))
         if rc != 0:
             raise MemoryError("oracle_device_unions")
+        return out
+
+    def concurrency(self, t, region: int, K: int = 8) -> np.ndarray:
+        """int64[m, 2, K]: per device, time with at least k active records
+        (all records, then kernels only), k = 1 .. K, inside the region."""
+        n = int(t.n_ranks)
+        dpr = _c(t.devices_per_rank, np.uint32)
+        m = int(dpr.sum())
+        out = np.zeros((m, 2, K), np.int64)
+        dse, dtg, doff = _c(t.dev_se, np.int64), _c(t.dev_tag, np.uint8), _c(t.dev_off, np.uint64)
+        win = _c(t.region_window[region], np.int64)
+        if self.lib.oracle_concurrency(n, _p(dpr), _p(dse), _p(dtg), _p(doff), _p(win), K, _p(out)) != 0:
+            raise MemoryError("oracle_concurrency")
         return out
 
     def metrics_from_sums(self, n_ranks, devices_per_rank, hs, du, win) -> dict:
@@ -146,6 +161,10 @@ def device_unions(t, region):
 
 def metrics_from_sums(*a):
     return default().metrics_from_sums(*a)
+
+
+def concurrency(t, region, K=8):
+    return default().concurrency(t, region, K)
 
 
 def region_metrics(t, region):

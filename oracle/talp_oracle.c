@@ -161,6 +161,78 @@ int oracle_device_unions(uint32_t n_ranks, const uint32_t *devices_per_rank, con
     return 0;
 }
 
+/*
+ * Concurrency profile of one region (the per-device occupancy the paper
+ * leaves to future work on streams, Sec. 4.1): for device g of rank i, with
+ * its records clipped to [a_i, b_i) and c(t) the number of them active at
+ * time t (a record [s, e) is active for s <= t < e),
+ *   out[g][0][k-1] = |{t : c(t) >= k}|                 for k = 1 .. K,
+ *   out[g][1][k-1] = the same over kernel records only.
+ * Level 1 is the busy union B (resp. the kernel union D_K).  Computed the
+ * plain way: +1 / -1 events at every clipped start / end, sorted by time,
+ * and the time between consecutive events added to every level up to the
+ * count of active records.
+ * Returns 0, or -1 when memory for the events cannot be had.
+ */
+typedef struct {
+    int64_t t;
+    int d;
+} ev_t;
+
+static int cmp_ev(const void *pa, const void *pb) {
+    const ev_t *a = (const ev_t *)pa, *b = (const ev_t *)pb;
+    if (a->t < b->t) return -1;
+    if (a->t > b->t) return 1;
+    return 0;
+}
+
+static void level_times(ev_t *ev, size_t n, uint32_t K, int64_t *out) {
+    for (uint32_t k = 0; k < K; ++k) out[k] = 0;
+    if (n == 0) return;
+    qsort(ev, n, sizeof(ev_t), cmp_ev);
+    int64_t c = 0;
+    for (size_t j = 0; j + 1 < n; ++j) {
+        c += ev[j].d;
+        const int64_t dt = ev[j + 1].t - ev[j].t;
+        for (int64_t k = 1; k <= c && k <= (int64_t)K; ++k) out[k - 1] += dt;
+    }
+}
+
+int oracle_concurrency(uint32_t n_ranks, const uint32_t *devices_per_rank, const int64_t *dev_se,
+                       const uint8_t *dev_tag, const uint64_t *dev_off, const int64_t *win, uint32_t K,
+                       int64_t *out) {
+    uint32_t g = 0;
+    for (uint32_t i = 0; i < n_ranks; ++i) {
+        int64_t a = win[2 * i], b = win[2 * i + 1];
+        for (uint32_t d = 0; d < devices_per_rank[i]; ++d, ++g) {
+            uint64_t lo_idx = dev_off[g], hi_idx = dev_off[g + 1];
+            size_t n = (size_t)(hi_idx - lo_idx);
+            ev_t *ea = (ev_t *)malloc((2 * n + 1) * sizeof(ev_t));
+            ev_t *ek = (ev_t *)malloc((2 * n + 1) * sizeof(ev_t));
+            if (!ea || !ek) {
+                free(ea); free(ek);
+                return -1;
+            }
+            size_t na = 0, nk = 0;
+            for (uint64_t j = lo_idx; j < hi_idx; ++j) {
+                int64_t s = max64(dev_se[2 * j], a);
+                int64_t e = min64(dev_se[2 * j + 1], b);
+                if (e <= s) continue;
+                ea[na].t = s; ea[na++].d = 1;
+                ea[na].t = e; ea[na++].d = -1;
+                if ((dev_tag[j] >> 5) == 0) {
+                    ek[nk].t = s; ek[nk++].d = 1;
+                    ek[nk].t = e; ek[nk++].d = -1;
+                }
+            }
+            level_times(ea, na, K, out + (size_t)g * 2 * K);
+            level_times(ek, nk, K, out + (size_t)g * 2 * K + K);
+            free(ea); free(ek);
+        }
+    }
+    return 0;
+}
+
 /* num / (k * den) with the 0/0 := 1 reading. */
 static double ratio_k(int64_t num, int64_t k, int64_t den) {
     if (k == 0 || den == 0) return 1.0;

@@ -73,6 +73,32 @@ def tick_device(trace, region):
     return np.asarray(out, np.int64).reshape(-1, 3)
 
 
+def tick_concurrency(trace, region, K):
+    """Per device, count the nanoseconds with at least k active records
+    (all kinds, then kernels only), k = 1 .. K, inside the rank window: one
+    counter per ns."""
+    win = trace.region_window[region]
+    m = int(np.asarray(trace.devices_per_rank).sum())
+    out = np.zeros((m, 2, K), np.int64)
+    g = 0
+    for i in range(trace.n_ranks):
+        a, b = int(win[i, 0]), int(win[i, 1])
+        for _ in range(int(trace.devices_per_rank[i])):
+            lo, hi = int(trace.dev_off[g]), int(trace.dev_off[g + 1])
+            if b > a:
+                cnt = np.zeros((2, b - a), np.int64)
+                for j in range(lo, hi):
+                    s, e = max(int(trace.dev_se[j, 0]), a), min(int(trace.dev_se[j, 1]), b)
+                    if e > s:
+                        cnt[0, s - a:e - a] += 1
+                        if (int(trace.dev_tag[j]) >> 5) == 0:
+                            cnt[1, s - a:e - a] += 1
+                for k in range(1, K + 1):
+                    out[g, :, k - 1] = (cnt >= k).sum(axis=1)
+            g += 1
+    return out
+
+
 def tick_host(trace, region):
     """Per rank and state, the number of nanosecond ticks of each host
     interval that fall inside the window, summed over intervals."""

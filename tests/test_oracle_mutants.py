@@ -25,7 +25,10 @@ MUTANTS = [
      "dout[6] = ratio_k(sK, (int64_t)n_ranks, maxK);"),
     ("PE_dev divides by n (Eq. 9)", "dout[5] = ratio_k(sK, E, (int64_t)m);", "dout[5] = ratio_k(sK, E, (int64_t)n_ranks);"),
     ("max busy is max kernel + max transfer", "maxB = max64(maxB, K + DM);", "maxB = max64(maxB, K) + 0 * DM;"),
-    ("device start not clipped", "int64_t s = max64(dev_se[2 * j], a);", "int64_t s = dev_se[2 * j];"),
+    ("device start not clipped", "int64_t s = max64(dev_se[2 * j], a);\n                int64_t e = min64(dev_se[2 * j + 1], b);\n                if (e <= s) continue;\n                ivl_t x",
+     "int64_t s = dev_se[2 * j];\n                int64_t e = min64(dev_se[2 * j + 1], b);\n                if (e <= s) continue;\n                ivl_t x"),
+    ("concurrency start not clipped", "int64_t s = max64(dev_se[2 * j], a);\n                int64_t e = min64(dev_se[2 * j + 1], b);\n                if (e <= s) continue;\n                ea[na]",
+     "int64_t s = dev_se[2 * j];\n                int64_t e = min64(dev_se[2 * j + 1], b);\n                if (e <= s) continue;\n                ea[na]"),
     ("host end not clipped", "int64_t hi = min64(host_se[2 * j + 1], b);", "int64_t hi = host_se[2 * j + 1];"),
     ("kind read from the stream bits", "if ((dev_tag[j] >> 5) == 0) kv", "if ((dev_tag[j] & 31) == 0) kv"),
     ("nested interval shrinks the run", "} else if (v[j].e > ce) {   /* overlapping or touching: extend */",
@@ -36,6 +39,12 @@ MUTANTS = [
     ("hidden transfer sign", "sHidden += K + UM - B;", "sHidden += K - UM + B;"),
     ("0/0 reads as 0", "if (k == 0 || den == 0) return 1.0;", "if (k == 0 || den == 0) return 0.0;"),
     ("validation ignores kind", "if ((dev_tag[j] >> 5) > 4) bad |= 8;", "if ((dev_tag[j] >> 5) > 7) bad |= 8;"),
+    ("concurrency levels off by one", "for (int64_t k = 1; k <= c && k <= (int64_t)K; ++k)",
+     "for (int64_t k = 1; k < c && k <= (int64_t)K; ++k)"),
+    ("concurrency end not clipped", "                int64_t e = min64(dev_se[2 * j + 1], b);\n                if (e <= s) continue;\n                ea[na]",
+     "                int64_t e = dev_se[2 * j + 1];\n                if (e <= s) continue;\n                ea[na]"),
+    ("concurrency kernels read from stream bits", "if ((dev_tag[j] >> 5) == 0) {\n                    ek[nk]",
+     "if ((dev_tag[j] & 31) == 0) {\n                    ek[nk]"),
 ]
 
 

@@ -30,7 +30,7 @@ import pytest
 import oracle
 import tracegen as tg
 from helpers import (GOLDEN, fixture_trace, host_tiles_windows, load_fixture, pils_cases, tick_device,
-                     tick_host)
+                     tick_host, tick_concurrency)
 
 pytestmark = pytest.mark.filterwarnings("ignore")
 
@@ -236,14 +236,62 @@ def pin_validation(O):
     assert O.validate(bad) & 8
 
 
+def pin_concurrency_brute_force(O, seeds=range(40)):
+    """Concurrency profile = per-ns counts of active records, on tiny traces."""
+    for seed in seeds:
+        t = tg.tiny_trace(seed, trace_id=seed, max_events=80, horizon=600)
+        for r in range(t.n_regions):
+            np.testing.assert_array_equal(O.concurrency(t, r, 6), tick_concurrency(t, r, 6), err_msg=str((seed, r)))
+
+
+def pin_concurrency_closed_forms(O):
+    """Level 1 is the busy (kernel) union; the levels add up to the summed
+    record time; k identical records give k levels of their length; nested
+    records give level 2 = the inner one; back-to-back records never reach 2."""
+    for seed in range(10):
+        t = tg.random_trace(seed, trace_id=seed, n_ranks=2, devices_per_rank=2, dev_events=700, host_events=50,
+                            n_regions=3)
+        for r in range(t.n_regions):
+            c = O.concurrency(t, r, 64)
+            u = O.device_unions(t, r)
+            np.testing.assert_array_equal(c[:, 0, 0], u[:, 2])
+            np.testing.assert_array_equal(c[:, 1, 0], u[:, 0])
+            win = t.region_window[r]
+            dr = np.repeat(np.arange(t.n_ranks), t.devices_per_rank)
+            for g in range(t.m_devices):
+                a, b = int(t.dev_off[g]), int(t.dev_off[g + 1])
+                lo, hi = win[dr[g], 0], win[dr[g], 1]
+                se = t.dev_se[a:b]
+                ln = np.maximum(np.minimum(se[:, 1], hi) - np.maximum(se[:, 0], lo), 0)
+                assert c[g, 0].sum() == ln.sum() and c[g, 0, -1] == 0
+                assert c[g, 1].sum() == ln[(t.dev_tag[a:b] >> 5) == 0].sum()
+    base = dict(trace_id=1, n_ranks=1, devices_per_rank=np.array([1], np.uint32),
+                region_window=np.array([[[0, 1000]]], np.int64), host_se=np.zeros((0, 2), np.int64),
+                host_state=np.zeros(0, np.uint8), host_off=np.array([0, 0], np.uint64))
+    same = tg.Trace(dev_se=np.array([[100, 400]] * 5, np.int64), dev_tag=np.array([0, 0, 0, 32, 64], np.uint8),
+                    dev_off=np.array([0, 5], np.uint64), **base)
+    c = O.concurrency(same, 0, 8)
+    assert c[0, 0].tolist() == [300] * 5 + [0] * 3 and c[0, 1].tolist() == [300] * 3 + [0] * 5
+    nest = tg.Trace(dev_se=np.array([[100, 900], [200, 300], [250, 260]], np.int64),
+                    dev_tag=np.array([0, 0, 0], np.uint8), dev_off=np.array([0, 3], np.uint64), **base)
+    assert O.concurrency(nest, 0, 4)[0, 0].tolist() == [800, 100, 10, 0]
+    chain = tg.Trace(dev_se=np.array([[0, 100], [100, 250], [250, 251], [300, 2000]], np.int64),
+                     dev_tag=np.array([0, 32, 0, 64], np.uint8), dev_off=np.array([0, 4], np.uint64), **base)
+    assert O.concurrency(chain, 0, 3)[0, 0].tolist() == [951, 0, 0]      # clipped at 1000
+
+
 ALL_PINS = [pin_brute_force, pin_balanced_devices_lb_one, pin_single_unit_lb_one,
             pin_disjoint_transfers_not_hidden, pin_transfers_inside_kernels_cost_nothing, pin_covering_kernel,
             pin_union_at_most_sum, pin_tiled_host_elapsed_and_ce, pin_invariants, pin_pils_tables,
-            pin_empty_and_degenerate, pin_validation]
+            pin_empty_and_degenerate, pin_validation, pin_concurrency_brute_force, pin_concurrency_closed_forms]
 
 
 # ----------------------------------------------------------------------------
 # the tests (default oracle build)
+
+
+def test_concurrency_brute_force_many_seeds():
+    pin_concurrency_brute_force(oracle.default(), seeds=range(40, 200))
 
 
 @pytest.mark.parametrize("pin", ALL_PINS, ids=lambda p: p.__name__)
