@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--workload", default="plain",
-                    choices=["plain", "small", "scale", "batched", "batched-full", "serving"])
+                    choices=["plain", "small", "scale", "batched", "batched-full", "serving", "concurrency"])
     ap.add_argument("--wave-records", type=float, default=3e9, help="batched-full: records per wave")
     ap.add_argument("--traces", type=int, default=4096, help="batched: number of traces")
     ap.add_argument("--ev-hi", type=int, default=None,
@@ -475,6 +475,74 @@ def run_batched_full(a):
     return 0 if exact else 1
 
 
+def run_concurrency(a):
+    """Concurrency profile (time with >= k active records per device, k =
+    1..8, all kinds and kernels only) of the plain large trace's devices, one
+    call per step through the C ABI with the records resident in HBM."""
+    import torch
+    import oracle
+    import paper_2603_26576_b300 as P
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    t = tg.plain_large(scale=a.scale)
+    arr = dict(host_se=torch.from_numpy(t.host_se).to(dev), host_state=torch.from_numpy(t.host_state).to(dev),
+               dev_se=torch.from_numpy(t.dev_se).to(dev), dev_tag=torch.from_numpy(t.dev_tag).to(dev))
+    b, keep = P.batch_from_arrays(t.trace_id, t.devices_per_rank, t.region_window, arr["host_se"],
+                                  arr["host_state"], t.host_off, arr["dev_se"], arr["dev_tag"], t.dev_off)
+    ctx = P.Context(0)
+    stream = torch.cuda.Stream()
+    region = 0
+    for _ in range(max(a.warmup, 3)):
+        res = P.talp_gpu_concurrency(ctx.ctx, b, region, stream)
+    P.talp_gpu_profile_read(ctx.ctx)
+    l0 = P.talp_gpu_profile_read(ctx.ctx)["kernel_launches"]
+    clocks = Clocks(0)
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(a.steps):
+        P.talp_gpu_concurrency(ctx.ctx, b, region, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1) / a.steps
+    launches = P.talp_gpu_profile_read(ctx.ctx)["kernel_launches"] - l0
+    N = t.n_dev
+    # parity on one rank's devices against the oracle
+    from paper_2603_26576_b300 import shard
+    s0 = shard.shard_of(t, [0])
+    c0 = time.perf_counter()
+    want = oracle.concurrency(s0, region, P.TALP_GPU_CONC_LEVELS)
+    cpu_s = time.perf_counter() - c0
+    exact = bool(np.array_equal(res[: int(s0.devices_per_rank.sum())], want))
+    peak, peak_kind = measured_peaks()
+    achieved = BYTES_PER_RECORD * N / (ms / 1000.0) / 1e9
+    line = {
+        "metric": METRIC, "value": N / (ms / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64", "data": "synthetic (seeded generator; the paper's traces are not available)",
+        "config": {"workload": "concurrency profile of the plain large trace's 256 devices (2M events each, "
+                               "4 streams), levels 1-8, all records and kernels only, region 0"
+                               + ("" if a.scale == 1.0 else f" (scale {a.scale})"),
+                   "records_per_step": N, "form": "talp_gpu_concurrency, one synchronous call per step",
+                   "l2": "records (%.1f GB) larger than L2; no flush" % (BYTES_PER_RECORD * N / 1e9),
+                   "bit_exact_rank0_vs_oracle": exact},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "chunk top-K + per-device scan + levels (the records are read twice)",
+                     "kernel_ms": ms, "peak_source": f"{peak_kind} hbm_gbs"},
+        "cpu_baseline": {"value": s0.n_records / cpu_s if cpu_s else None, "unit": UNIT, "cores": 1,
+                         "kind": "oracle", "sample": f"rank 0's 4 devices ({int(s0.dev_se.shape[0])} records), "
+                                                     f"{cpu_s:.2f} s"},
+        "e2e": None, "gpu_launches": launches, "clocks": ck,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0 if exact else 1
+
+
 # ----------------------------------------------------------------- serving
 
 
@@ -738,6 +806,8 @@ def main():
         return run_batched(a)
     if a.workload == "batched-full":
         return run_batched_full(a)
+    if a.workload == "concurrency":
+        return run_concurrency(a)
     if a.workload == "serving":
         return run_serving(a)
     import torch

@@ -168,7 +168,9 @@ typedef struct {
  */
 talp_gpu_status talp_gpu_create(talp_gpu_ctx **out, int device, size_t hbm_budget_bytes);
 
-/* Free every device buffer and the context.  NULL is accepted. */
+/* Free every device buffer and the context.  NULL is accepted.
+ * Errors: EBUSY (nothing freed) while a plan or a server created on the
+ * context still exists: destroy those first. */
 talp_gpu_status talp_gpu_destroy(talp_gpu_ctx *ctx);
 
 /* ------------------------------------------------------------------ ingest */
@@ -242,6 +244,26 @@ talp_gpu_status talp_gpu_metrics_combine(talp_gpu_ctx *ctx, const talp_gpu_metri
  */
 talp_gpu_status talp_gpu_unit_sums(talp_gpu_ctx *ctx, uint64_t trace_id, uint32_t region,
                                    int64_t *host_out, int64_t *dev_out, void *stream);
+
+/*
+ * Concurrency profile of every device of one trace in one region: the
+ * per-stream occupancy the paper leaves to future work (Sec. 4.1, device
+ * states; the streams are merged here).  With a device's records clipped to
+ * its rank's window and c(t) the number of them active at time t,
+ *   out_host[g][0][k-1] = |{t : c(t) >= k}|            k = 1 .. TALP_GPU_CONC_LEVELS,
+ *   out_host[g][1][k-1] = the same over kernel records,
+ * int64 ns, host memory [m][2][TALP_GPU_CONC_LEVELS].  Level 1 equals the
+ * busy union (resp. the kernel union) of the flattening (Sec. 4.2).
+ * `b` is read as for talp_gpu_ingest_events (host records are ignored, the
+ * device records must be in start order per device; TALP_GPU_APPEND is not
+ * used); nothing is stored.  Synchronises `stream`.
+ * Errors: EINVAL (bad header or region; a record with end < start or a bad
+ * kind; device records out of start order: out_host is still written),
+ * ENOMEM, ECUDA.
+ */
+#define TALP_GPU_CONC_LEVELS 8
+talp_gpu_status talp_gpu_concurrency(talp_gpu_ctx *ctx, const talp_gpu_trace_batch *b, uint32_t region,
+                                     int64_t *out_host, void *stream);
 
 /* ------------------------------------------------------------ batched plans */
 

@@ -22,6 +22,7 @@ STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEDOUT
 EXPORTED_SYMBOLS = (
     "talp_gpu_create", "talp_gpu_destroy", "talp_gpu_ingest_events", "talp_gpu_region_metrics",
     "talp_gpu_region_metrics_batch", "talp_gpu_region_metrics_device", "talp_gpu_metrics_combine",
+    "talp_gpu_concurrency",
     "talp_gpu_unit_sums",
     "talp_gpu_reset", "talp_gpu_memory", "talp_gpu_profile", "talp_gpu_profile_read", "talp_gpu_reduce_noalloc",
     "talp_gpu_plan_create", "talp_gpu_plan_launch", "talp_gpu_plan_metrics", "talp_gpu_plan_info",
@@ -31,6 +32,7 @@ EXPORTED_SYMBOLS = (
 )
 TALP_GPU_PLAN_AUTOTUNE = 0x1
 TALP_GPU_NOALLOC_MAX_UNITS = 8192
+TALP_GPU_CONC_LEVELS = 8
 
 
 class TalpGpuError(RuntimeError):
@@ -133,6 +135,7 @@ def load_library():
         "talp_gpu_metrics_combine": ([P, ctypes.POINTER(talp_gpu_metrics), S, ctypes.POINTER(talp_gpu_metrics), P],
                                      I32),
         "talp_gpu_unit_sums": ([P, U64, U32, P, P, P], I32),
+        "talp_gpu_concurrency": ([P, ctypes.POINTER(talp_gpu_trace_batch), U32, P, P], I32),
         "talp_gpu_reset": ([P, U64], I32),
         "talp_gpu_memory": ([P, ctypes.POINTER(S), ctypes.POINTER(S)], I32),
         "talp_gpu_profile": ([P, I32], I32),
@@ -235,6 +238,20 @@ def talp_gpu_metrics_combine(ctx, parts, stream=None, check=True):
         arr[k] = p if isinstance(p, talp_gpu_metrics) else metrics_from_dict(p)
     out = talp_gpu_metrics()
     st = load_library().talp_gpu_metrics_combine(ctx, arr, len(parts), ctypes.byref(out), _stream(stream))
+    if check:
+        _check(st)
+        return out
+    return st, out
+
+
+def talp_gpu_concurrency(ctx, batch, region, stream=None, check=True):
+    """int64[m, 2, TALP_GPU_CONC_LEVELS]: per device, time with at least k
+    active records (all, then kernels only) in the region."""
+    m = int(np.ctypeslib.as_array(ctypes.cast(batch.devices_per_rank, ctypes.POINTER(ctypes.c_uint32)),
+                                  shape=(batch.n_ranks,)).sum())
+    out = np.zeros((m, 2, TALP_GPU_CONC_LEVELS), np.int64)
+    st = load_library().talp_gpu_concurrency(ctx, ctypes.byref(batch), region,
+                                             out.ctypes.data_as(ctypes.c_void_p), _stream(stream))
     if check:
         _check(st)
         return out
@@ -498,6 +515,16 @@ class Context:
     def memory(self):
         return talp_gpu_memory(self.ctx)
 
+    def concurrency(self, t, region, arrays=None, stream=None, check=True):
+        """Concurrency profile of trace `t` (records in start order) in one
+        region; `arrays` may hold CUDA tensors for dev_se / dev_tag."""
+        rec = dict(host_se=t.host_se, host_state=t.host_state, dev_se=t.dev_se, dev_tag=t.dev_tag)
+        if arrays is not None:
+            rec.update(arrays)
+        b, keep = batch_from_arrays(t.trace_id, t.devices_per_rank, t.region_window, rec["host_se"],
+                                    rec["host_state"], t.host_off, rec["dev_se"], rec["dev_tag"], t.dev_off)
+        return talp_gpu_concurrency(self.ctx, b, region, stream, check)
+
     def plan(self, traces, arrays, flags=TALP_GPU_SORTED_BY_START, plan_flags=0):
         """A batched plan over traces whose records are the CUDA tensors in
         `arrays` (one dict per trace: host_se, host_state, dev_se, dev_tag)."""
@@ -509,15 +536,16 @@ class Context:
             keep.append(kp)
             self._shapes[int(t.trace_id)] = (int(t.n_ranks), int(np.asarray(t.devices_per_rank).sum()),
                                              int(np.asarray(t.region_window).shape[0]))
-        return Plan(talp_gpu_plan_create(self.ctx, batches, plan_flags), keep)
+        return Plan(talp_gpu_plan_create(self.ctx, batches, plan_flags), keep, self)
 
 
 class Plan:
     """Owning wrapper of a talp_gpu_plan (the batched form)."""
 
-    def __init__(self, handle, keep):
+    def __init__(self, handle, keep, context=None):
         self.handle = handle
         self._keep = keep
+        self.context = context   # destroyed after the plan
 
     def launch(self, stream=None):
         talp_gpu_plan_launch(self.handle, stream)

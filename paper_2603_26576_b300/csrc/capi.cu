@@ -946,6 +946,101 @@ talp_gpu_status talp_gpu_metrics_combine(talp_gpu_ctx* c, const talp_gpu_metrics
     return check_metrics_flags(out_host, 1);
 }
 
+talp_gpu_status talp_gpu_concurrency(talp_gpu_ctx* c, const talp_gpu_trace_batch* b, uint32_t region,
+                                     int64_t* out_host, void* stream_) {
+    if (!c) return fail(TALP_GPU_EINVAL, "null context");
+    if (!b || !out_host) return fail(TALP_GPU_EINVAL, "null argument");
+    if (b->n_ranks == 0 || !b->devices_per_rank || !b->region_window || !b->dev_off)
+        return fail(TALP_GPU_EINVAL, "concurrency: bad header");
+    if (region >= b->n_regions || b->n_regions > TALP_GPU_MAX_REGIONS)
+        return fail(TALP_GPU_EINVAL, "concurrency: region out of range");
+    uint64_t m = 0;
+    for (uint32_t i = 0; i < b->n_ranks; ++i) m += b->devices_per_rank[i];
+    if (m == 0) return TALP_GPU_OK;
+    if (m > (1u << 24)) return fail(TALP_GPU_EINVAL, "concurrency: too many devices");
+    if (b->dev_off[0] != 0) return fail(TALP_GPU_EINVAL, "concurrency: dev_off[0] != 0");
+    for (uint64_t g = 0; g < m; ++g)
+        if (b->dev_off[g + 1] < b->dev_off[g]) return fail(TALP_GPU_EINVAL, "concurrency: dev_off decreases");
+    const uint64_t N = b->dev_off[m];
+    const bool dev_ptrs = (b->flags & TALP_GPU_DEVICE_PTRS) != 0;
+    if (N && (!b->dev_se || !b->dev_tag)) return fail(TALP_GPU_EINVAL, "concurrency: null record arrays");
+    if (N && dev_ptrs && (reinterpret_cast<uintptr_t>(b->dev_se) & 15u))
+        return fail(TALP_GPU_EINVAL, "concurrency: dev_se not 16-byte aligned");
+
+    // device and chunk tables (chunks of at most kChunk records)
+    constexpr uint64_t kChunk = 16384;
+    std::vector<ConcDev> devs(m);
+    std::vector<ConcChunk> chunks;
+    uint64_t g = 0;
+    for (uint32_t i = 0; i < b->n_ranks; ++i) {
+        const int64_t* w = b->region_window + (static_cast<uint64_t>(region) * b->n_ranks + i) * 2;
+        for (uint32_t d = 0; d < b->devices_per_rank[i]; ++d, ++g) {
+            ConcDev& v = devs[g];
+            v.a = w[0];
+            v.b = w[1];
+            v.rec0 = b->dev_off[g];
+            v.n = b->dev_off[g + 1] - b->dev_off[g];
+            v.chunk0 = static_cast<uint32_t>(chunks.size());
+            for (uint64_t o = 0; o < v.n; o += kChunk)
+                chunks.push_back(ConcChunk{v.rec0 + o, static_cast<uint32_t>(std::min(kChunk, v.n - o)),
+                                           static_cast<uint32_t>(g)});
+            v.nchunk = static_cast<uint32_t>(chunks.size()) - v.chunk0;
+        }
+    }
+    const size_t nc = chunks.size();
+    const size_t o_dev = 0;
+    const size_t o_chunk = align_up(o_dev + sizeof(ConcDev) * m, 256);
+    const size_t o_top = align_up(o_chunk + sizeof(ConcChunk) * nc, 256);
+    const size_t o_in = align_up(o_top + sizeof(int64_t) * 2 * kConcLevels * nc, 256);
+    const size_t o_out = align_up(o_in + sizeof(int64_t) * 2 * kConcLevels * nc, 256);
+    const size_t o_st = align_up(o_out + sizeof(int64_t) * 2 * kConcLevels * m, 256);
+    const size_t ws_bytes = o_st + 256;
+    const size_t up_bytes = o_top;
+    const size_t down_bytes = o_st + 16 - o_out;
+    const size_t stage_bytes = dev_ptrs ? 0 : align_up(16 * N, 256) + align_up(N + 16, 256);
+
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    TALP_CUDA(cudaSetDevice(c->device));
+    if (c->ws_used) TALP_CUDA(cudaStreamWaitEvent(stream, c->ev_ws, 0));
+    TALP_TRY(grow(c, c->ws, ws_bytes));
+    if (stage_bytes) TALP_TRY(grow(c, c->stage, stage_bytes));
+    TALP_CUDA(cudaEventSynchronize(c->ev_up));
+    TALP_TRY(grow_pinned(c->up, up_bytes));
+    TALP_TRY(grow_pinned(c->down, down_bytes));
+    char* up = static_cast<char*>(c->up.p);
+    memcpy(up + o_dev, devs.data(), sizeof(ConcDev) * m);
+    if (nc) memcpy(up + o_chunk, chunks.data(), sizeof(ConcChunk) * nc);
+    char* ws = static_cast<char*>(c->ws.p);
+    TALP_CUDA(cudaMemcpyAsync(ws, up, up_bytes, cudaMemcpyHostToDevice, stream));
+    TALP_CUDA(cudaEventRecord(c->ev_up, stream));
+    const int64_t* se = b->dev_se;
+    const uint8_t* tag = b->dev_tag;
+    if (!dev_ptrs && N) {
+        char* st = static_cast<char*>(c->stage.p);
+        TALP_CUDA(cudaMemcpyAsync(st, b->dev_se, 16 * N, cudaMemcpyHostToDevice, stream));
+        TALP_CUDA(cudaMemcpyAsync(st + align_up(16 * N, 256), b->dev_tag, N, cudaMemcpyHostToDevice, stream));
+        se = reinterpret_cast<const int64_t*>(st);
+        tag = reinterpret_cast<const uint8_t*>(st + align_up(16 * N, 256));
+    }
+    TALP_CUDA(cudaMemsetAsync(ws + o_out, 0, o_st + 16 - o_out, stream));
+    TALP_CUDA(launch_concurrency(se, tag, reinterpret_cast<const ConcDev*>(ws + o_dev), static_cast<uint32_t>(m),
+                                 reinterpret_cast<const ConcChunk*>(ws + o_chunk), static_cast<uint32_t>(nc),
+                                 reinterpret_cast<int64_t*>(ws + o_top), reinterpret_cast<int64_t*>(ws + o_in),
+                                 reinterpret_cast<int64_t*>(ws + o_out), reinterpret_cast<uint32_t*>(ws + o_st),
+                                 stream));
+    c->kernel_launches += nc ? 3 : 0;
+    TALP_CUDA(cudaMemcpyAsync(c->down.p, ws + o_out, down_bytes, cudaMemcpyDeviceToHost, stream));
+    TALP_CUDA(cudaEventRecord(c->ev_ws, stream));
+    c->ws_used = true;
+    TALP_CUDA(cudaStreamSynchronize(stream));
+    memcpy(out_host, c->down.p, sizeof(int64_t) * 2 * kConcLevels * m);
+    uint32_t status = 0;
+    memcpy(&status, static_cast<char*>(c->down.p) + (o_st - o_out), sizeof(status));
+    if (status & 3u) return fail(TALP_GPU_EINVAL, "concurrency: invalid record (end < start or bad kind)");
+    if (status & 4u) return fail(TALP_GPU_EINVAL, "concurrency: device records out of start order");
+    return TALP_GPU_OK;
+}
+
 talp_gpu_status talp_gpu_unit_sums(talp_gpu_ctx* c, uint64_t trace_id, uint32_t region, int64_t* host_out,
                                    int64_t* dev_out, void* stream_) {
     if (!c) return fail(TALP_GPU_EINVAL, "null context");

@@ -114,6 +114,21 @@ struct SortCtl {
 constexpr int kMaxRuns = 16;
 constexpr int kMergeRounds = 4;   // ceil(log2(kMaxRuns))
 
+// Concurrency profile: levels k = 1 .. kConcLevels of concurrently active
+// records per device; one device's window and record range, and the chunks
+// its records are cut into.
+constexpr int kConcLevels = 8;
+struct ConcDev {
+    int64_t a, b;              // region window of the device's rank
+    uint64_t rec0, n;          // its records in the record arrays
+    uint32_t chunk0, nchunk;   // its chunks
+};
+struct ConcChunk {
+    uint64_t rec0;             // first record
+    uint32_t n;                // records
+    uint32_t dev;              // device index
+};
+
 // ---------------------------------------------------------------- helpers
 
 __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
