@@ -27,64 +27,106 @@ constexpr int kItems = 8;
 constexpr int kTile = 32 * kItems;
 constexpr int kWarps = 8;
 
-// sorted-descending list of the K largest ends seen (INT64_MIN: none)
+// Sorted-descending list of the K largest ends seen.  Two widths: absolute
+// int64 (INT64_MIN: none) for the state carried between tiles and chunks,
+// and uint32 offsets from a tile's first clipped start for the tile's own
+// work (0: at or before that start, which no later record can use).
+template <typename T>
 struct TopK {
-    int64_t v[K];
+    T v[K];
 };
 
-__device__ __forceinline__ void cas_desc(int64_t& x, int64_t& y) {
-    const int64_t hi = x > y ? x : y, lo = x > y ? y : x;
-    x = hi;
-    y = lo;
+template <typename T>
+__device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
+template <typename T>
+__device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
+
+template <typename T>
+__device__ __forceinline__ T none_v();
+template <>
+__device__ __forceinline__ int64_t none_v<int64_t>() { return INT64_MIN; }
+template <>
+__device__ __forceinline__ uint32_t none_v<uint32_t>() { return 0u; }
+
+template <typename T>
+__device__ __forceinline__ void clear_top(TopK<T>& x) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) x.v[i] = none_v<T>();
 }
 
 // top-K of the union of two sorted-descending lists (result sorted)
-__device__ __forceinline__ void merge_top(TopK& x, const TopK& y) {
+template <typename T>
+__device__ __forceinline__ void merge_top(TopK<T>& x, const TopK<T>& y) {
 #pragma unroll
-    for (int i = 0; i < K; ++i) x.v[i] = max64(x.v[i], y.v[K - 1 - i]);   // bitonic
+    for (int i = 0; i < K; ++i) x.v[i] = tmax(x.v[i], y.v[K - 1 - i]);   // bitonic
 #pragma unroll
     for (int w = K / 2; w > 0; w >>= 1) {
 #pragma unroll
         for (int i = 0; i < K; ++i)
-            if ((i & w) == 0) cas_desc(x.v[i], x.v[i + w]);
+            if ((i & w) == 0) {
+                const T hi = tmax(x.v[i], x.v[i + w]), lo = tmin(x.v[i], x.v[i + w]);
+                x.v[i] = hi;
+                x.v[i + w] = lo;
+            }
     }
 }
 
-__device__ __forceinline__ void insert_top(TopK& x, int64_t e) {
+template <typename T>
+__device__ __forceinline__ void insert_top(TopK<T>& x, T e) {
 #pragma unroll
     for (int i = 0; i < K; ++i) {
-        const int64_t hi = x.v[i] > e ? x.v[i] : e;
-        e = x.v[i] > e ? e : x.v[i];
+        const T hi = tmax(x.v[i], e);
+        e = tmin(x.v[i], e);
         x.v[i] = hi;
     }
 }
 
-__device__ __forceinline__ void clear_top(TopK& x) {
-#pragma unroll
-    for (int i = 0; i < K; ++i) x.v[i] = INT64_MIN;
+__device__ __forceinline__ uint32_t shfl_up_t(uint32_t v, int d) { return __shfl_up_sync(0xFFFFFFFFu, v, d); }
+__device__ __forceinline__ int64_t shfl_up_t(int64_t v, int d) {
+    return static_cast<int64_t>(__shfl_up_sync(0xFFFFFFFFu, static_cast<long long>(v), d));
 }
+__device__ __forceinline__ uint32_t shfl_t(uint32_t v, int s) { return __shfl_sync(0xFFFFFFFFu, v, s); }
+__device__ __forceinline__ int64_t shfl_t(int64_t v, int s) { return shfl64(v, s); }
 
-__device__ __forceinline__ TopK shfl_top(const TopK& x, int src) {
-    TopK y;
+template <typename T>
+__device__ __forceinline__ TopK<T> shfl_top(const TopK<T>& x, int src) {
+    TopK<T> y;
 #pragma unroll
-    for (int i = 0; i < K; ++i) y.v[i] = shfl64(x.v[i], src);
+    for (int i = 0; i < K; ++i) y.v[i] = shfl_t(x.v[i], src);
     return y;
 }
 
-__device__ __forceinline__ TopK shfl_up_top(const TopK& x, int d) {
-    TopK y;
+template <typename T>
+__device__ __forceinline__ TopK<T> shfl_up_top(const TopK<T>& x, int d) {
+    TopK<T> y;
 #pragma unroll
-    for (int i = 0; i < K; ++i) y.v[i] = static_cast<int64_t>(__shfl_up_sync(0xFFFFFFFFu, static_cast<long long>(x.v[i]), d));
+    for (int i = 0; i < K; ++i) y.v[i] = shfl_up_t(x.v[i], d);
     return y;
 }
 
 // warp-inclusive scan of top-K lists over lanes
-__device__ __forceinline__ void scan_top(TopK& x, int lane) {
+template <typename T>
+__device__ __forceinline__ void scan_top(TopK<T>& x, int lane) {
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        const TopK y = shfl_up_top(x, d);
+        const TopK<T> y = shfl_up_top(x, d);
         if (lane >= d) merge_top(x, y);
     }
+}
+
+// absolute value -> offset from s0 (0 at or before s0), and back
+__device__ __forceinline__ uint32_t rel32(int64_t x, int64_t s0) {
+    if (x <= s0) return 0u;
+    const uint64_t d = static_cast<uint64_t>(x) - static_cast<uint64_t>(s0);   // exact: 0 < d < 2^64
+    return d > 0xFFFFFFFFull ? 0xFFFFFFFFu : static_cast<uint32_t>(d);
+}
+// x is at or before s0, or within 2^32 - 1 ns after it
+__device__ __forceinline__ bool near32(int64_t x, int64_t s0) {
+    return x <= s0 || static_cast<uint64_t>(x) - static_cast<uint64_t>(s0) < 0xFFFFFFFFull;
+}
+__device__ __forceinline__ void to_abs(TopK<int64_t>& out, const TopK<uint32_t>& x, int64_t s0) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) out.v[i] = s0 + static_cast<int64_t>(x.v[i]);
 }
 
 // One tile of a chunk staged in shared memory: rows of 16 bytes and tags.
@@ -93,8 +135,6 @@ struct Stage {
     uint8_t tag[kTile];
 };
 
-// Load the records [r0, r0 + n) of the record array into the warp's stage
-// (n <= kTile), clipped to the window.
 __device__ __forceinline__ void stage_tile(Stage& st, const int64_t* __restrict__ se, const uint8_t* __restrict__ tag,
                                            uint64_t r0, int n, int lane) {
     for (int q = lane; q < n; q += 32) {
@@ -102,6 +142,13 @@ __device__ __forceinline__ void stage_tile(Stage& st, const int64_t* __restrict_
         st.tag[q] = tag[r0 + q];
     }
     __syncwarp();
+}
+
+// clipped record q of the stage: start max(s, a), end in [start, b]
+__device__ __forceinline__ void clipped(const Stage& st, int q, const ConcDev& dv, int64_t& s, int64_t& e) {
+    const longlong2 r = st.se[q];
+    s = max64(r.x, dv.a);
+    e = max64(min64(r.y, dv.b), s);
 }
 
 // ------------------------------------------------------------- chunk top-K
@@ -116,35 +163,61 @@ __global__ void __launch_bounds__(kWarps * 32) conc_chunk_top(const int64_t* __r
     if (c >= n_chunks) return;
     const ConcChunk ch = chunks[c];
     const ConcDev dv = devs[ch.dev];
-    TopK ta, tk;
-    clear_top(ta);
-    clear_top(tk);
+    TopK<int64_t> ca, ck;   // the chunk's lists so far (warp-uniform)
+    clear_top(ca);
+    clear_top(ck);
     uint32_t bad = 0;
     for (uint32_t o = 0; o < ch.n; o += kTile) {
         const int n = static_cast<int>(min(static_cast<uint32_t>(kTile), ch.n - o));
         stage_tile(stg[wid], se, tag, ch.rec0 + o, n, lane);
+        int64_t s0, e0;
+        clipped(stg[wid], 0, dv, s0, e0);
+        TopK<uint32_t> la, lk;
+        clear_top(la);
+        clear_top(lk);
+        bool fits = true;
+#pragma unroll
         for (int i = 0; i < kItems; ++i) {
             const int q = lane * kItems + i;
             if (q < n) {
                 const longlong2 r = stg[wid].se[q];
                 const uint32_t kind = stg[wid].tag[q] >> 5;
                 bad |= (r.y < r.x ? 1u : 0u) | (kind > 4u ? 2u : 0u);
-                const int64_t e = min64(r.y, dv.b);
-                insert_top(ta, e);
-                if (kind == 0u) insert_top(tk, e);
+                int64_t s, e;
+                clipped(stg[wid], q, dv, s, e);
+                fits &= near32(e, s0);
+                const uint32_t re = rel32(e, s0);
+                insert_top(la, re);
+                if (kind == 0u) insert_top(lk, re);
             }
         }
+        if (__all_sync(0xFFFFFFFFu, fits)) {
+            scan_top(la, lane);
+            scan_top(lk, lane);
+            TopK<int64_t> xa, xk;
+            to_abs(xa, shfl_top(la, 31), s0);
+            to_abs(xk, shfl_top(lk, 31), s0);
+            merge_top(ca, xa);
+            merge_top(ck, xk);
+        } else if (lane == 0) {
+            // a tile spanning 2^32 ns or more: plain 64-bit inserts
+            for (int q = 0; q < n; ++q) {
+                int64_t s, e;
+                clipped(stg[wid], q, dv, s, e);
+                insert_top(ca, e);
+                if ((stg[wid].tag[q] >> 5) == 0u) insert_top(ck, e);
+            }
+        }
+        ca = shfl_top(ca, 0);
+        ck = shfl_top(ck, 0);
         __syncwarp();
     }
-    // reduce the lanes' lists: the last lane of an inclusive scan holds all
-    scan_top(ta, lane);
-    scan_top(tk, lane);
     bad = __reduce_or_sync(0xFFFFFFFFu, bad);
-    if (lane == 31) {
+    if (lane == 0) {
 #pragma unroll
         for (int i = 0; i < K; ++i) {
-            top[static_cast<uint64_t>(c) * 2 * K + i] = ta.v[i];
-            top[static_cast<uint64_t>(c) * 2 * K + K + i] = tk.v[i];
+            top[static_cast<uint64_t>(c) * 2 * K + i] = ca.v[i];
+            top[static_cast<uint64_t>(c) * 2 * K + K + i] = ck.v[i];
         }
         if (bad) atomicOr(status, bad);
     }
@@ -157,12 +230,12 @@ __global__ void conc_chunk_scan(const ConcDev* __restrict__ devs, uint32_t n_dev
     const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n_dev) return;
     const ConcDev dv = devs[g];
-    TopK ra, rk;
+    TopK<int64_t> ra, rk;
     clear_top(ra);
     clear_top(rk);
     for (uint32_t q = 0; q < dv.nchunk; ++q) {
         const uint64_t c = dv.chunk0 + q;
-        TopK xa, xk;
+        TopK<int64_t> xa, xk;
 #pragma unroll
         for (int i = 0; i < K; ++i) {
             in[c * 2 * K + i] = ra.v[i];
@@ -176,7 +249,7 @@ __global__ void conc_chunk_scan(const ConcDev* __restrict__ devs, uint32_t n_dev
 }
 
 // ------------------------------------------------------------- levels
-__global__ void __launch_bounds__(kWarps * 32) conc_chunk_levels(const int64_t* __restrict__ se,
+__global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_t* __restrict__ se,
                                                                 const uint8_t* __restrict__ tag,
                                                                 const ConcDev* __restrict__ devs,
                                                                 const ConcChunk* __restrict__ chunks,
@@ -189,7 +262,7 @@ __global__ void __launch_bounds__(kWarps * 32) conc_chunk_levels(const int64_t* 
     if (c >= n_chunks) return;
     const ConcChunk ch = chunks[c];
     const ConcDev dv = devs[ch.dev];
-    TopK sa, sk;   // state before the current tile
+    TopK<int64_t> sa, sk;   // state before the current tile (warp-uniform)
 #pragma unroll
     for (int i = 0; i < K; ++i) {
         sa.v[i] = in[static_cast<uint64_t>(c) * 2 * K + i];
@@ -208,62 +281,102 @@ __global__ void __launch_bounds__(kWarps * 32) conc_chunk_levels(const int64_t* 
         // start of the record after the tile (clipped), or none
         int64_t after = INT64_MAX;
         if (r0 + n < dev_end) after = max64(se[2 * (r0 + n)], dv.a);
-        // lane lists of this tile's ends, scanned across the warp
-        TopK la, lk;
+        int64_t s0, e0;
+        clipped(stg[wid], 0, dv, s0, e0);
+        // offsets from s0: the tile's records, the entering state, the bounds
+        uint32_t s[kItems], e[kItems];
+        uint32_t kmask = 0;
+        bool fits = true;
+        TopK<uint32_t> la, lk;
         clear_top(la);
         clear_top(lk);
-        int64_t s[kItems], e[kItems];
-        uint32_t kd[kItems];
 #pragma unroll
         for (int i = 0; i < kItems; ++i) {
             const int q = lane * kItems + i;
+            s[i] = e[i] = 0xFFFFFFFFu;
             if (q < n) {
-                const longlong2 r = stg[wid].se[q];
-                s[i] = max64(r.x, dv.a);
-                e[i] = max64(min64(r.y, dv.b), s[i]);
-                kd[i] = stg[wid].tag[q] >> 5;
-                if (q > 0) bad |= stg[wid].se[q - 1].x > r.x ? 4u : 0u;
+                int64_t sa64, ea64;
+                clipped(stg[wid], q, dv, sa64, ea64);
+                if (q > 0) bad |= stg[wid].se[q - 1].x > stg[wid].se[q].x ? 4u : 0u;
+                fits &= near32(ea64, s0);
+                s[i] = rel32(sa64, s0);
+                e[i] = rel32(ea64, s0);
+                const bool isK = (stg[wid].tag[q] >> 5) == 0u;
+                kmask |= isK ? 1u << i : 0u;
                 insert_top(la, e[i]);
-                if (kd[i] == 0u) insert_top(lk, e[i]);
-            } else {
-                s[i] = e[i] = INT64_MAX;
-                kd[i] = 1u;
+                if (isK) insert_top(lk, e[i]);
             }
         }
-        scan_top(la, lane);
-        scan_top(lk, lane);
-        // entering state of this lane = tile state + lanes before it
-        TopK xa = shfl_up_top(la, 1), xk = shfl_up_top(lk, 1);
-        if (lane == 0) {
-            clear_top(xa);
-            clear_top(xk);
-        }
-        merge_top(xa, sa);
-        merge_top(xk, sk);
-        // next lane's first start (the last lane: the record after the tile)
-        int64_t nxt = shfl64(s[0], (lane + 1) & 31);
-        if (lane == 31 || (lane + 1) * kItems >= n) nxt = after;
 #pragma unroll
-        for (int i = 0; i < kItems; ++i) {
-            const int q = lane * kItems + i;
-            if (q < n) {
-                insert_top(xa, e[i]);
-                if (kd[i] == 0u) insert_top(xk, e[i]);
-                const int64_t ns = (i + 1 < kItems && q + 1 < n) ? s[i + 1] : nxt;
-                const int64_t hi = min64(ns, dv.b);
+        for (int i = 0; i < K; ++i) fits &= near32(sa.v[i], s0) && near32(sk.v[i], s0);
+        if (__all_sync(0xFFFFFFFFu, fits)) {
+            TopK<uint32_t> ta, tk;   // entering state as offsets
 #pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    // E_k below s_i (or none: INT64_MIN) contributes nothing;
-                    // clamping first keeps the difference from overflowing
-                    acc_a[k] += max64(min64(hi, max64(xa.v[k], s[i])) - s[i], 0);
-                    acc_k[k] += max64(min64(hi, max64(xk.v[k], s[i])) - s[i], 0);
+            for (int i = 0; i < K; ++i) {
+                ta.v[i] = rel32(sa.v[i], s0);
+                tk.v[i] = rel32(sk.v[i], s0);
+            }
+            scan_top(la, lane);
+            scan_top(lk, lane);
+            TopK<uint32_t> xa = shfl_up_top(la, 1), xk = shfl_up_top(lk, 1);
+            if (lane == 0) {
+                clear_top(xa);
+                clear_top(xk);
+            }
+            merge_top(xa, ta);
+            merge_top(xk, tk);
+            const uint32_t bnd = rel32(dv.b, s0);
+            uint32_t nxt = shfl_t(s[0], (lane + 1) & 31);
+            if (lane == 31 || (lane + 1) * kItems >= n) nxt = rel32(after, s0);
+#pragma unroll
+            for (int i = 0; i < kItems; ++i) {
+                const int q = lane * kItems + i;
+                if (q < n) {
+                    insert_top(xa, e[i]);
+                    if (kmask & (1u << i)) insert_top(xk, e[i]);
+                    const uint32_t ns = (i + 1 < kItems && q + 1 < n) ? s[i + 1] : nxt;
+                    // the gap [s_i, min(next start, window end)) at level k
+                    // lasts until E_k: min(gap, max(E_k, s_i) - s_i)
+                    const uint32_t hi = tmin(ns, bnd);
+                    const uint32_t gap = hi > s[i] ? hi - s[i] : 0u;
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        acc_a[k] += tmin(gap, tmax(xa.v[k], s[i]) - s[i]);
+                        acc_k[k] += tmin(gap, tmax(xk.v[k], s[i]) - s[i]);
+                    }
                 }
             }
+            // state after the tile: the entering state and every record of it
+            merge_top(la, ta);
+            merge_top(lk, tk);
+            to_abs(sa, shfl_top(la, 31), s0);
+            to_abs(sk, shfl_top(lk, 31), s0);
+        } else {
+            // a tile spanning 2^32 ns or more: lane 0 walks it in 64 bits
+            if (lane == 0) {
+                for (int q = 0; q < n; ++q) {
+                    int64_t sq, eq;
+                    clipped(stg[wid], q, dv, sq, eq);
+                    insert_top(sa, eq);
+                    const bool isK = (stg[wid].tag[q] >> 5) == 0u;
+                    if (isK) insert_top(sk, eq);
+                    int64_t ns = after;
+                    if (q + 1 < n) {
+                        int64_t s1, e1;
+                        clipped(stg[wid], q + 1, dv, s1, e1);
+                        ns = s1;
+                    }
+                    const int64_t hi = min64(ns, dv.b);
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        acc_a[k] += max64(min64(hi, max64(sa.v[k], sq)) - sq, 0);
+                        acc_k[k] += max64(min64(hi, max64(sk.v[k], sq)) - sq, 0);
+                    }
+                }
+            }
+            sa = shfl_top(sa, 0);
+            sk = shfl_top(sk, 0);
         }
-        // state after the tile: everything up to the last lane
-        const TopK ta = shfl_top(la, 31), tk = shfl_top(lk, 31);
-        merge_top(sa, ta);
-        merge_top(sk, tk);
         __syncwarp();
     }
     if (ch.n > 0 && ch.rec0 > dv.rec0 && lane == 0) bad |= se[2 * (ch.rec0 - 1)] > se[2 * ch.rec0] ? 4u : 0u;
