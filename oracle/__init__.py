@@ -69,6 +69,8 @@ class Oracle:
         lib.oracle_metrics.restype = None
         lib.oracle_concurrency.argtypes = [ctypes.c_uint32, P, P, P, P, P, ctypes.c_uint32, P]
         lib.oracle_concurrency.restype = ctypes.c_int
+        lib.oracle_scalability.argtypes = [ctypes.c_uint32, P, P, P, ctypes.c_uint32, ctypes.c_int, P]
+        lib.oracle_scalability.restype = None
         self.lib = lib
 
     def validate(self, t) -> int:
@@ -110,6 +112,19 @@ class Oracle:
         if self.lib.oracle_concurrency(n, _p(dpr), _p(dse), _p(dtg), _p(doff), _p(win), K, _p(out)) != 0:
             raise MemoryError("oracle_concurrency")
         return out
+
+    def scalability(self, runs, ref: int = 0, weak: bool = False) -> list:
+        """Scaling factors of region-metrics dicts `runs` (one per run, as
+        region_metrics returns) against runs[ref]: per run a dict with
+        speedup, host_comp_scal, host_global_eff, dev_comp_scal, dev_global_eff."""
+        k = len(runs)
+        iruns = np.array([[r["elapsed_ns"], r["sum_useful"], r["sum_kernel"]] for r in runs], np.int64)
+        units = np.array([[r["n_ranks"], r["m_devices"]] for r in runs], np.uint32)
+        pe = np.array([[r["host_pe"], r["dev_pe"]] for r in runs], np.float64)
+        out = np.zeros((k, 5), np.float64)
+        self.lib.oracle_scalability(k, _p(iruns), _p(units), _p(pe), int(ref), int(bool(weak)), _p(out))
+        names = ("speedup", "host_comp_scal", "host_global_eff", "dev_comp_scal", "dev_global_eff")
+        return [{nm: float(v) for nm, v in zip(names, row)} for row in out]
 
     def metrics_from_sums(self, n_ranks, devices_per_rank, hs, du, win) -> dict:
         dpr = _c(devices_per_rank, np.uint32)
@@ -165,6 +180,10 @@ def metrics_from_sums(*a):
 
 def concurrency(t, region, K=8):
     return default().concurrency(t, region, K)
+
+
+def scalability(runs, ref=0, weak=False):
+    return default().scalability(runs, ref, weak)
 
 
 def region_metrics(t, region):

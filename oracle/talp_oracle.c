@@ -323,3 +323,39 @@ void oracle_metrics(uint32_t n_ranks, const uint32_t *devices_per_rank, const in
     }
     *flags = fl;
 }
+
+/*
+ * Scalability across runs (POP's second branch, which TALP leaves to the
+ * user across several runs, Sec. 3.3): the region metrics of n_runs runs of
+ * one application at different scales against the reference run `ref`.
+ * For run r (iruns[r] = {E, sum U, sum D_K}, units[r] = {n, m}, pe[r] =
+ * {PE_host, PE_dev} as computed above):
+ *   out[r][0] = speedup            E_ref / E_r
+ *   out[r][1] = host comp. scal.   strong: sumU_ref / sumU_r
+ *                                  weak:   (sumU_ref * n_r) / (sumU_r * n_ref)
+ *   out[r][2] = host global eff.   PE_host_r * out[r][1]
+ *   out[r][3] = device comp. scal. the same with sum D_K and m
+ *   out[r][4] = device global eff. PE_dev_r * out[r][3]
+ * FP64, round to nearest, the order as written; a zero denominator reads 1.
+ */
+static double ratio_scaled(int64_t num, int64_t k_num, int64_t den, int64_t k_den) {
+    double d = (double)den * (double)k_den;
+    if (d == 0.0) return 1.0;
+    return ((double)num * (double)k_num) / d;
+}
+
+void oracle_scalability(uint32_t n_runs, const int64_t *iruns, const uint32_t *units, const double *pe,
+                        uint32_t ref, int weak, double *out) {
+    const int64_t E0 = iruns[3 * ref], U0 = iruns[3 * ref + 1], K0 = iruns[3 * ref + 2];
+    const int64_t n0 = units[2 * ref], m0 = units[2 * ref + 1];
+    for (uint32_t r = 0; r < n_runs; ++r) {
+        const int64_t E = iruns[3 * r], U = iruns[3 * r + 1], Kd = iruns[3 * r + 2];
+        const int64_t n = units[2 * r], m = units[2 * r + 1];
+        double *o = out + 5 * r;
+        o[0] = ratio(E0, E);
+        o[1] = weak ? ratio_scaled(U0, n, U, n0) : ratio(U0, U);
+        o[2] = pe[2 * r] * o[1];
+        o[3] = weak ? ratio_scaled(K0, m, Kd, m0) : ratio(K0, Kd);
+        o[4] = pe[2 * r + 1] * o[3];
+    }
+}

@@ -43,6 +43,11 @@ MUTANTS = [
      "for (int64_t k = 1; k < c && k <= (int64_t)K; ++k)"),
     ("concurrency end not clipped", "                int64_t e = min64(dev_se[2 * j + 1], b);\n                if (e <= s) continue;\n                ea[na]",
      "                int64_t e = dev_se[2 * j + 1];\n                if (e <= s) continue;\n                ea[na]"),
+    ("strong scalability inverted", "o[1] = weak ? ratio_scaled(U0, n, U, n0) : ratio(U0, U);",
+     "o[1] = weak ? ratio_scaled(U0, n, U, n0) : ratio(U, U0);"),
+    ("weak scalability uses the reference's ranks twice", "o[3] = weak ? ratio_scaled(K0, m, Kd, m0) : ratio(K0, Kd);",
+     "o[3] = weak ? ratio_scaled(K0, m0, Kd, m0) : ratio(K0, Kd);"),
+    ("global efficiency of the reference run", "o[2] = pe[2 * r] * o[1];", "o[2] = pe[2 * ref] * o[1];"),
     ("concurrency kernels read from stream bits", "if ((dev_tag[j] >> 5) == 0) {\n                    ek[nk]",
      "if ((dev_tag[j] & 31) == 0) {\n                    ek[nk]"),
 ]

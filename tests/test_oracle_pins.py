@@ -280,10 +280,57 @@ def pin_concurrency_closed_forms(O):
     assert O.concurrency(chain, 0, 3)[0, 0].tolist() == [951, 0, 0]      # clipped at 1000
 
 
+def _runs(O, ns=(1, 2, 4, 8), gpus=(1, 2, 2, 3)):
+    return [O.region_metrics(tg.random_trace(40 + k, trace_id=k, n_ranks=n, devices_per_rank=g, dev_events=400,
+                                             host_events=300, n_regions=2), 1) for k, (n, g) in enumerate(zip(ns, gpus))]
+
+
+def pin_scalability_identities(O):
+    """Reference run: speedup and scalabilities 1, global = parallel
+    efficiency.  Strong scaling: GE_r = PE_ref * speedup_r * n_ref / n_r
+    (m for the device); weak scaling: GE_r = PE_ref * speedup_r."""
+    runs = _runs(O)
+    for ref in (0, 2):
+        for weak in (False, True):
+            sc = O.scalability(runs, ref, weak)
+            assert sc[ref]["speedup"] == 1.0 and sc[ref]["host_comp_scal"] == 1.0 and sc[ref]["dev_comp_scal"] == 1.0
+            assert sc[ref]["host_global_eff"] == runs[ref]["host_pe"]
+            assert sc[ref]["dev_global_eff"] == runs[ref]["dev_pe"]
+            for r, x in enumerate(sc):
+                fh = 1.0 if weak else runs[ref]["n_ranks"] / runs[r]["n_ranks"]
+                fd = 1.0 if weak else runs[ref]["m_devices"] / runs[r]["m_devices"]
+                assert math.isclose(x["host_global_eff"], runs[ref]["host_pe"] * x["speedup"] * fh, rel_tol=1e-13)
+                assert math.isclose(x["dev_global_eff"], runs[ref]["dev_pe"] * x["speedup"] * fd, rel_tol=1e-13)
+                assert math.isclose(x["speedup"], runs[ref]["elapsed_ns"] / runs[r]["elapsed_ns"], rel_tol=1e-15)
+
+
+def pin_scalability_closed_forms(O):
+    """A run that repeats the reference on twice the ranks (same elapsed
+    time, twice the useful and kernel time): strong scalability 1/2, weak
+    scalability 1, speedup 1."""
+    t = tg.random_trace(77, trace_id=1, n_ranks=2, devices_per_rank=[1, 3], dev_events=[300, 200, 500, 100],
+                        host_events=[200, 250], n_regions=1)
+    def twice(a, off):
+        return np.concatenate([a, a]), np.concatenate([off[:-1], off[:-1] + off[-1], [2 * off[-1]]]).astype(np.uint64)
+    hse, hoff = twice(t.host_se, t.host_off)
+    dse, doff = twice(t.dev_se, t.dev_off)
+    t2 = tg.Trace(trace_id=2, n_ranks=4, devices_per_rank=np.tile(t.devices_per_rank, 2),
+                  region_window=np.concatenate([t.region_window, t.region_window], axis=1), host_se=hse,
+                  host_state=np.concatenate([t.host_state, t.host_state]), host_off=hoff, dev_se=dse,
+                  dev_tag=np.concatenate([t.dev_tag, t.dev_tag]), dev_off=doff)
+    runs = [O.region_metrics(t, 0), O.region_metrics(t2, 0)]
+    strong = O.scalability(runs, 0, False)[1]
+    weak = O.scalability(runs, 0, True)[1]
+    assert strong["speedup"] == 1.0 and strong["host_comp_scal"] == 0.5 and strong["dev_comp_scal"] == 0.5
+    assert weak["speedup"] == 1.0 and weak["host_comp_scal"] == 1.0 and weak["dev_comp_scal"] == 1.0
+    assert weak["host_global_eff"] == runs[1]["host_pe"] == runs[0]["host_pe"]
+
+
 ALL_PINS = [pin_brute_force, pin_balanced_devices_lb_one, pin_single_unit_lb_one,
             pin_disjoint_transfers_not_hidden, pin_transfers_inside_kernels_cost_nothing, pin_covering_kernel,
             pin_union_at_most_sum, pin_tiled_host_elapsed_and_ce, pin_invariants, pin_pils_tables,
-            pin_empty_and_degenerate, pin_validation, pin_concurrency_brute_force, pin_concurrency_closed_forms]
+            pin_empty_and_degenerate, pin_validation, pin_concurrency_brute_force, pin_concurrency_closed_forms,
+            pin_scalability_identities, pin_scalability_closed_forms]
 
 
 # ----------------------------------------------------------------------------
