@@ -236,6 +236,37 @@ talp_gpu_status talp_gpu_metrics_combine(talp_gpu_ctx *ctx, const talp_gpu_metri
                                          talp_gpu_metrics *out_host, void *stream);
 
 /*
+ * Scalability across runs: POP's second branch, which needs several runs
+ * and which TALP leaves to the user (Sec. 3.3).  runs[0 .. n_runs-1] are
+ * the metrics of one region (the same region index) of runs of one
+ * application at different scales, runs[ref] the reference.  For run r:
+ *   speedup         = E_ref / E_r
+ *   host_comp_scal  strong: sumU_ref / sumU_r
+ *                   weak:   (sumU_ref * n_r) / (sumU_r * n_ref)
+ *   host_global_eff = PE_host_r * host_comp_scal
+ *   dev_comp_scal   the same with the kernel sums and m
+ *   dev_global_eff  = PE_dev_r * dev_comp_scal
+ * FP64 on the GPU, round to nearest in the order written; a zero
+ * denominator reads 1.  out_host[n_runs], host memory; synchronises stream.
+ * The hardware-counter children of computation scalability (IPC,
+ * instructions, frequency) are not covered.
+ * Errors: EINVAL (no runs, ref out of range, bad mode, mixed regions), ECUDA.
+ */
+#define TALP_GPU_SCALING_STRONG 0u
+#define TALP_GPU_SCALING_WEAK 1u
+typedef struct {
+    uint64_t trace_id;
+    uint32_t region;
+    uint32_t flags;                    /* the run's TALP_GPU_M_* flags */
+    uint32_t n_ranks, m_devices;
+    double speedup;
+    double host_comp_scal, host_global_eff;
+    double dev_comp_scal, dev_global_eff;
+} talp_gpu_scaling;
+talp_gpu_status talp_gpu_scalability(talp_gpu_ctx *ctx, const talp_gpu_metrics *runs, size_t n_runs, size_t ref,
+                                     uint32_t mode, talp_gpu_scaling *out_host, void *stream);
+
+/*
  * Raw per-unit times of one region (TALP also reports raw times so users can
  * form their own indicators): host_out [n_ranks][3] = useful, offload, MPI
  * per rank; dev_out [m][3] = kernel union D_K, memory-operation union, busy

@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEDOUT
 EXPORTED_SYMBOLS = (
     "talp_gpu_create", "talp_gpu_destroy", "talp_gpu_ingest_events", "talp_gpu_region_metrics",
     "talp_gpu_region_metrics_batch", "talp_gpu_region_metrics_device", "talp_gpu_metrics_combine",
-    "talp_gpu_concurrency",
+    "talp_gpu_concurrency", "talp_gpu_scalability",
     "talp_gpu_unit_sums",
     "talp_gpu_reset", "talp_gpu_memory", "talp_gpu_profile", "talp_gpu_profile_read", "talp_gpu_reduce_noalloc",
     "talp_gpu_plan_create", "talp_gpu_plan_launch", "talp_gpu_plan_metrics", "talp_gpu_plan_info",
@@ -90,6 +90,13 @@ class talp_gpu_server_stats(ctypes.Structure):
                 ("jobs_open", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
+class talp_gpu_scaling(ctypes.Structure):
+    _fields_ = [("trace_id", ctypes.c_uint64), ("region", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("n_ranks", ctypes.c_uint32), ("m_devices", ctypes.c_uint32), ("speedup", ctypes.c_double),
+                ("host_comp_scal", ctypes.c_double), ("host_global_eff", ctypes.c_double),
+                ("dev_comp_scal", ctypes.c_double), ("dev_global_eff", ctypes.c_double)]
+
+
 class talp_gpu_metrics(ctypes.Structure):
     _fields_ = ([("trace_id", ctypes.c_uint64), ("region", ctypes.c_uint32), ("flags", ctypes.c_uint32),
                  ("n_ranks", ctypes.c_uint32), ("m_devices", ctypes.c_uint32)]
@@ -136,6 +143,8 @@ def load_library():
                                      I32),
         "talp_gpu_unit_sums": ([P, U64, U32, P, P, P], I32),
         "talp_gpu_concurrency": ([P, ctypes.POINTER(talp_gpu_trace_batch), U32, P, P], I32),
+        "talp_gpu_scalability": ([P, ctypes.POINTER(talp_gpu_metrics), S, S, U32, ctypes.POINTER(talp_gpu_scaling),
+                                  P], I32),
         "talp_gpu_reset": ([P, U64], I32),
         "talp_gpu_memory": ([P, ctypes.POINTER(S), ctypes.POINTER(S)], I32),
         "talp_gpu_profile": ([P, I32], I32),
@@ -256,6 +265,22 @@ def talp_gpu_concurrency(ctx, batch, region, stream=None, check=True):
         _check(st)
         return out
     return st, out
+
+
+def talp_gpu_scalability(ctx, runs, ref=0, weak=False, stream=None, check=True):
+    """Scaling factors of region metrics `runs` (structs or dicts) against
+    runs[ref]; a list of dicts."""
+    arr = (talp_gpu_metrics * len(runs))()
+    for k, p in enumerate(runs):
+        arr[k] = p if isinstance(p, talp_gpu_metrics) else metrics_from_dict(p)
+    out = (talp_gpu_scaling * max(1, len(runs)))()
+    st = load_library().talp_gpu_scalability(ctx, arr, len(runs), ref, 1 if weak else 0, out, _stream(stream))
+    res = [{f: (float(getattr(o, f)) if t is ctypes.c_double else int(getattr(o, f))) for f, t in o._fields_}
+           for o in list(out)[:len(runs)]]
+    if check:
+        _check(st)
+        return res
+    return st, res
 
 
 def talp_gpu_unit_sums(ctx, trace_id, region, n_ranks, m_devices, stream=None):

@@ -946,6 +946,40 @@ talp_gpu_status talp_gpu_metrics_combine(talp_gpu_ctx* c, const talp_gpu_metrics
     return check_metrics_flags(out_host, 1);
 }
 
+talp_gpu_status talp_gpu_scalability(talp_gpu_ctx* c, const talp_gpu_metrics* runs, size_t n_runs, size_t ref,
+                                     uint32_t mode, talp_gpu_scaling* out_host, void* stream_) {
+    static_assert(sizeof(ScaleOut) == sizeof(talp_gpu_scaling), "scaling record layout");
+    if (!c) return fail(TALP_GPU_EINVAL, "null context");
+    if (!runs || !out_host || n_runs == 0) return fail(TALP_GPU_EINVAL, "null argument or no runs");
+    if (n_runs > (1u << 20)) return fail(TALP_GPU_EINVAL, "more than 2^20 runs");
+    if (ref >= n_runs) return fail(TALP_GPU_EINVAL, "reference run out of range");
+    if (mode != TALP_GPU_SCALING_STRONG && mode != TALP_GPU_SCALING_WEAK) return fail(TALP_GPU_EINVAL, "bad mode");
+    for (size_t k = 1; k < n_runs; ++k)
+        if (runs[k].region != runs[0].region) return fail(TALP_GPU_EINVAL, "runs of different regions");
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    TALP_CUDA(cudaSetDevice(c->device));
+    const size_t rb = align_up(sizeof(MetricsOut) * n_runs, 256);
+    if (c->ws_used) TALP_CUDA(cudaStreamWaitEvent(stream, c->ev_ws, 0));
+    TALP_TRY(grow(c, c->ws, rb + sizeof(ScaleOut) * n_runs));
+    MetricsOut* druns = static_cast<MetricsOut*>(c->ws.p);
+    ScaleOut* dout = reinterpret_cast<ScaleOut*>(static_cast<char*>(c->ws.p) + rb);
+    TALP_CUDA(cudaEventSynchronize(c->ev_up));
+    TALP_TRY(grow_pinned(c->up, rb));
+    memcpy(c->up.p, runs, sizeof(MetricsOut) * n_runs);
+    TALP_CUDA(cudaMemcpyAsync(druns, c->up.p, sizeof(MetricsOut) * n_runs, cudaMemcpyHostToDevice, stream));
+    TALP_CUDA(cudaEventRecord(c->ev_up, stream));
+    TALP_CUDA(launch_scalability(druns, static_cast<uint32_t>(n_runs), static_cast<uint32_t>(ref),
+                                 mode == TALP_GPU_SCALING_WEAK ? 1 : 0, dout, stream));
+    ++c->kernel_launches;
+    TALP_TRY(grow_pinned(c->down, sizeof(ScaleOut) * n_runs));
+    TALP_CUDA(cudaMemcpyAsync(c->down.p, dout, sizeof(ScaleOut) * n_runs, cudaMemcpyDeviceToHost, stream));
+    TALP_CUDA(cudaEventRecord(c->ev_ws, stream));
+    c->ws_used = true;
+    TALP_CUDA(cudaStreamSynchronize(stream));
+    memcpy(out_host, c->down.p, sizeof(ScaleOut) * n_runs);
+    return TALP_GPU_OK;
+}
+
 talp_gpu_status talp_gpu_concurrency(talp_gpu_ctx* c, const talp_gpu_trace_batch* b, uint32_t region,
                                      int64_t* out_host, void* stream_) {
     if (!c) return fail(TALP_GPU_EINVAL, "null context");

@@ -67,6 +67,13 @@ struct MetricsOut {
     double dev_pe, dev_lb, dev_ce, dev_oe;
 };
 
+// Scaling factors of one run against a reference run; mirrors talp_gpu_scaling.
+struct ScaleOut {
+    uint64_t trace_id;
+    uint32_t region, flags, n_ranks, m_devices;
+    double speedup, host_comp_scal, host_global_eff, dev_comp_scal, dev_global_eff;
+};
+
 struct FinalizeJob {
     const TraceDev* t;
     MetricsOut* out;

@@ -82,9 +82,6 @@ __device__ __forceinline__ void insert_top(TopK<T>& x, T e) {
 }
 
 __device__ __forceinline__ uint32_t shfl_up_t(uint32_t v, int d) { return __shfl_up_sync(0xFFFFFFFFu, v, d); }
-__device__ __forceinline__ int64_t shfl_up_t(int64_t v, int d) {
-    return static_cast<int64_t>(__shfl_up_sync(0xFFFFFFFFu, static_cast<long long>(v), d));
-}
 __device__ __forceinline__ uint32_t shfl_t(uint32_t v, int s) { return __shfl_sync(0xFFFFFFFFu, v, s); }
 __device__ __forceinline__ int64_t shfl_t(int64_t v, int s) { return shfl64(v, s); }
 

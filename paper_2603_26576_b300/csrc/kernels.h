@@ -41,6 +41,8 @@ cudaError_t launch_finalize(const FinalizeJob* jobs, uint32_t n_jobs, cudaStream
 cudaError_t launch_concurrency(const int64_t* se, const uint8_t* tag, const ConcDev* devs, uint32_t n_dev,
                                const ConcChunk* chunks, uint32_t n_chunks, int64_t* top, int64_t* in, int64_t* out,
                                uint32_t* status, cudaStream_t stream);
+cudaError_t launch_scalability(const MetricsOut* runs, uint32_t n_runs, uint32_t ref, int weak, ScaleOut* out,
+                               cudaStream_t stream);
 cudaError_t launch_combine(const MetricsOut* parts, uint32_t n_parts, MetricsOut* out, cudaStream_t stream);
 
 // Sort stage over the device segments flagged out of order (sortable ones),

@@ -358,6 +358,49 @@ __global__ void __launch_bounds__(256) combine_kernel(const MetricsOut* __restri
     *out = o;
 }
 
+// ------------------------------------------------------------ scalability
+//
+// POP's second branch across runs (TALP leaves it to the user, Sec. 3.3):
+// per run, against the reference run, speedup E_ref / E_r, computation
+// scalability from the useful (host) and kernel (device) sums -- strong:
+// sum_ref / sum_r; weak: (sum_ref * units_r) / (sum_r * units_ref) -- and
+// global efficiency = parallel efficiency x computation scalability.  FP64
+// in the order written, round to nearest; a zero denominator reads 1.
+__device__ __forceinline__ double ratio_scaled(int64_t num, int64_t k_num, int64_t den, int64_t k_den) {
+    const double d = __dmul_rn(__ll2double_rn(den), __ll2double_rn(k_den));
+    if (d == 0.0) return 1.0;
+    return __ddiv_rn(__dmul_rn(__ll2double_rn(num), __ll2double_rn(k_num)), d);
+}
+
+__global__ void scalability_kernel(const MetricsOut* __restrict__ runs, uint32_t n_runs, uint32_t ref, int weak,
+                                   ScaleOut* __restrict__ out) {
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_runs) return;
+    const MetricsOut& b = runs[ref];
+    const MetricsOut& x = runs[r];
+    ScaleOut o;
+    o.trace_id = x.trace_id;
+    o.region = x.region;
+    o.flags = x.flags & 0x707u;
+    o.n_ranks = x.n_ranks;
+    o.m_devices = x.m_devices;
+    o.speedup = ratio(b.elapsed_ns, x.elapsed_ns);
+    o.host_comp_scal = weak ? ratio_scaled(b.sum_useful, x.n_ranks, x.sum_useful, b.n_ranks)
+                            : ratio(b.sum_useful, x.sum_useful);
+    o.host_global_eff = __dmul_rn(x.host_pe, o.host_comp_scal);
+    o.dev_comp_scal = weak ? ratio_scaled(b.sum_kernel, x.m_devices, x.sum_kernel, b.m_devices)
+                           : ratio(b.sum_kernel, x.sum_kernel);
+    o.dev_global_eff = __dmul_rn(x.dev_pe, o.dev_comp_scal);
+    out[r] = o;
+}
+
+cudaError_t launch_scalability(const MetricsOut* runs, uint32_t n_runs, uint32_t ref, int weak, ScaleOut* out,
+                               cudaStream_t stream) {
+    if (n_runs == 0) return cudaSuccess;
+    scalability_kernel<<<(n_runs + 127) / 128, 128, 0, stream>>>(runs, n_runs, ref, weak, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_combine(const MetricsOut* parts, uint32_t n_parts, MetricsOut* out, cudaStream_t stream) {
     if (n_parts == 0) return cudaSuccess;
     combine_kernel<<<1, 256, 0, stream>>>(parts, n_parts, out);
