@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--workload", default="plain",
-                    choices=["plain", "small", "scale", "batched", "batched-full", "serving", "concurrency"])
+                    choices=["plain", "small", "scale", "batched", "batched-full", "serving", "concurrency", "raw"])
     ap.add_argument("--wave-records", type=float, default=3e9, help="batched-full: records per wave")
     ap.add_argument("--traces", type=int, default=4096, help="batched: number of traces")
     ap.add_argument("--ev-hi", type=int, default=None,
@@ -543,6 +543,98 @@ def run_concurrency(a):
     return 0 if exact else 1
 
 
+def run_raw(a):
+    """Raw activity records: the plain trace's device records as per-rank
+    delivery buffers (all devices and streams interleaved in completion
+    order), ingested through talp_gpu_ingest_raw from HBM and reduced, one
+    synchronous step per call; against the same records already in lanes
+    in start order."""
+    import torch
+    import oracle
+    import paper_2603_26576_b300 as P
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    scale = a.scale if a.scale != 1.0 else 0.25
+    t = tg.plain_large(scale=scale)
+    r = tg.to_raw(t)
+    up = lambda x: torch.from_numpy(x).to(dev)  # noqa: E731
+    arr = dict(host_se=up(t.host_se), host_state=up(t.host_state), raw_se=up(r.raw_se), raw_tag=up(r.raw_tag),
+               raw_dev=up(r.raw_dev))
+    lanes = dict(host_se=arr["host_se"], host_state=arr["host_state"], dev_se=up(t.dev_se), dev_tag=up(t.dev_tag))
+    rb, keep = P.raw_batch_from_arrays(t.trace_id, t.devices_per_rank, t.region_window, arr["host_se"],
+                                       arr["host_state"], t.host_off, arr["raw_se"], arr["raw_tag"], arr["raw_dev"],
+                                       r.raw_off)
+    lb, keep2 = P.batch_from_arrays(t.trace_id + 1, t.devices_per_rank, t.region_window, lanes["host_se"],
+                                    lanes["host_state"], t.host_off, lanes["dev_se"], lanes["dev_tag"], t.dev_off,
+                                    P.TALP_GPU_SORTED_BY_START)
+    ctx = P.Context(0)
+    stream = torch.cuda.Stream()
+    R = t.n_regions
+    out_dev = torch.empty(R * 200, dtype=torch.uint8, device=dev)
+
+    def step_raw():
+        P.talp_gpu_ingest_raw(ctx.ctx, [rb], stream)
+        P.talp_gpu_region_metrics_device(ctx.ctx, [t.trace_id], P.TALP_GPU_ALL_REGIONS, out_dev.data_ptr(), stream)
+
+    def step_lanes():
+        P.talp_gpu_ingest_events(ctx.ctx, [lb], stream)
+        P.talp_gpu_region_metrics_device(ctx.ctx, [t.trace_id + 1], P.TALP_GPU_ALL_REGIONS, out_dev.data_ptr(),
+                                         stream)
+
+    def timed(fn, k):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    for _ in range(max(a.warmup, 3)):
+        step_raw()
+        step_lanes()
+    P.talp_gpu_profile_read(ctx.ctx)
+    l0 = P.talp_gpu_profile_read(ctx.ctx)["kernel_launches"]
+    clocks = Clocks(0)
+    clocks.start()
+    time.sleep(0.3)
+    ms = timed(step_raw, a.steps)
+    ck = clocks.stop()
+    launches = P.talp_gpu_profile_read(ctx.ctx)["kernel_launches"] - l0 + a.steps
+    ms_lanes = timed(step_lanes, a.steps)
+    got = P.talp_gpu_region_metrics(ctx.ctx, t.trace_id, P.TALP_GPU_ALL_REGIONS, stream, n_regions=R)
+    lane_res = P.talp_gpu_region_metrics(ctx.ctx, t.trace_id + 1, P.TALP_GPU_ALL_REGIONS, stream, n_regions=R)
+    same = all(P.metrics_to_dict(x) == dict(P.metrics_to_dict(y), trace_id=t.trace_id) for x, y in zip(got, lane_res))
+    N = t.n_records
+    peak, peak_kind = measured_peaks()
+    achieved = BYTES_PER_RECORD * N / (ms / 1000.0) / 1e9
+    c0 = time.perf_counter()
+    oracle.region_metrics(tg.plain_large(scale=scale, n_ranks=1), 0)
+    cpu_s = time.perf_counter() - c0
+    line = {
+        "metric": METRIC, "value": N / (ms / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64", "data": "synthetic (seeded generator; the paper's traces are not available)",
+        "config": {"workload": f"plain large trace at scale {scale:g} as raw per-rank delivery buffers (4 devices x "
+                               "4 streams per rank interleaved in completion order)",
+                   "records_per_step": N, "form": "talp_gpu_ingest_raw + metrics, one synchronous call per step",
+                   "lanes_in_start_order_ms_per_step": ms_lanes, "raw_over_lanes_time": ms / ms_lanes,
+                   "bit_exact_raw_vs_lanes": same,
+                   "l2": "records (%.1f GB) larger than L2; no flush" % (BYTES_PER_RECORD * N / 1e9)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "whole step (scatter, sweep, merge sort, re-sweep, finalize)",
+                     "kernel_ms": ms, "peak_source": f"{peak_kind} hbm_gbs"},
+        "cpu_baseline": {"value": None if not cpu_s else (N / t.n_ranks) / cpu_s, "unit": UNIT, "cores": 1,
+                         "kind": "oracle", "sample": f"one rank of the workload, {cpu_s:.2f} s"},
+        "e2e": None, "gpu_launches": launches, "clocks": ck,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0 if same else 1
+
+
 # ----------------------------------------------------------------- serving
 
 
@@ -808,6 +900,8 @@ def main():
         return run_batched_full(a)
     if a.workload == "concurrency":
         return run_concurrency(a)
+    if a.workload == "raw":
+        return run_raw(a)
     if a.workload == "serving":
         return run_serving(a)
     import torch

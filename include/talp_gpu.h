@@ -189,6 +189,47 @@ talp_gpu_status talp_gpu_destroy(talp_gpu_ctx *ctx);
 talp_gpu_status talp_gpu_ingest_events(talp_gpu_ctx *ctx, const talp_gpu_trace_batch *batches,
                                        size_t n_batches, void *stream);
 
+/*
+ * Raw activity records (Sec. 4.2: device records reach the tool in buffers,
+ * delivered when full or flushed, with the records of all of a process's
+ * devices and streams interleaved in completion order).  Same as
+ * talp_gpu_trace_batch except for the device records: rank i's records are
+ * raw_se / raw_tag / raw_dev [raw_off[i] .. raw_off[i+1]), in delivery
+ * order, raw_dev being the record's device within its rank (0 ..
+ * devices_per_rank[i] - 1, at most 8 devices per rank).  Records of one
+ * stream must be delivered in start order (a stream executes in order); the
+ * streams may interleave arbitrarily.
+ */
+typedef struct {
+    uint64_t trace_id;
+    uint32_t n_ranks;
+    uint32_t n_regions;
+    uint32_t flags;                    /* TALP_GPU_DEVICE_PTRS (all record arrays), TALP_GPU_APPEND */
+    uint32_t reserved;                 /* must be 0 */
+    const uint32_t *devices_per_rank;  /* host [n_ranks], each <= 8 */
+    const int64_t *region_window;      /* host [n_regions][n_ranks][2] */
+    const int64_t *host_se;            /* [N_host][2] */
+    const uint8_t *host_state;         /* [N_host] */
+    const uint64_t *host_off;          /* host [n_ranks + 1] */
+    const int64_t *raw_se;             /* [N_raw][2] */
+    const uint8_t *raw_tag;            /* [N_raw] kind << 5 | stream */
+    const uint8_t *raw_dev;            /* [N_raw] device within the rank */
+    const uint64_t *raw_off;           /* host [n_ranks + 1], raw_off[0] == 0 */
+} talp_gpu_raw_batch;
+
+/*
+ * Ingest raw activity records: a stable scatter on the GPU groups every
+ * rank's records by (device, stream) into per-device lanes, each stream in
+ * delivery (= start) order, then the lanes go through
+ * talp_gpu_ingest_events without TALP_GPU_SORTED_BY_START (the out-of-order
+ * devices are merged by start on the GPU).  Synchronises `stream` once, to
+ * read each device's record count.  With device pointers, one batch per
+ * call.  Errors: those of talp_gpu_ingest_events, and EINVAL for a record
+ * naming a device its rank does not have or more than 8 devices in a rank.
+ */
+talp_gpu_status talp_gpu_ingest_raw(talp_gpu_ctx *ctx, const talp_gpu_raw_batch *batches, size_t n_batches,
+                                    void *stream);
+
 /* ----------------------------------------------------------------- results */
 
 /*

@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEDOUT
 EXPORTED_SYMBOLS = (
     "talp_gpu_create", "talp_gpu_destroy", "talp_gpu_ingest_events", "talp_gpu_region_metrics",
     "talp_gpu_region_metrics_batch", "talp_gpu_region_metrics_device", "talp_gpu_metrics_combine",
-    "talp_gpu_concurrency", "talp_gpu_scalability",
+    "talp_gpu_concurrency", "talp_gpu_scalability", "talp_gpu_ingest_raw",
     "talp_gpu_unit_sums",
     "talp_gpu_reset", "talp_gpu_memory", "talp_gpu_profile", "talp_gpu_profile_read", "talp_gpu_reduce_noalloc",
     "talp_gpu_plan_create", "talp_gpu_plan_launch", "talp_gpu_plan_metrics", "talp_gpu_plan_info",
@@ -90,6 +90,16 @@ class talp_gpu_server_stats(ctypes.Structure):
                 ("jobs_open", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
+class talp_gpu_raw_batch(ctypes.Structure):
+    _fields_ = [
+        ("trace_id", ctypes.c_uint64), ("n_ranks", ctypes.c_uint32), ("n_regions", ctypes.c_uint32),
+        ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("devices_per_rank", ctypes.c_void_p),
+        ("region_window", ctypes.c_void_p), ("host_se", ctypes.c_void_p), ("host_state", ctypes.c_void_p),
+        ("host_off", ctypes.c_void_p), ("raw_se", ctypes.c_void_p), ("raw_tag", ctypes.c_void_p),
+        ("raw_dev", ctypes.c_void_p), ("raw_off", ctypes.c_void_p),
+    ]
+
+
 class talp_gpu_scaling(ctypes.Structure):
     _fields_ = [("trace_id", ctypes.c_uint64), ("region", ctypes.c_uint32), ("flags", ctypes.c_uint32),
                 ("n_ranks", ctypes.c_uint32), ("m_devices", ctypes.c_uint32), ("speedup", ctypes.c_double),
@@ -145,6 +155,7 @@ def load_library():
         "talp_gpu_concurrency": ([P, ctypes.POINTER(talp_gpu_trace_batch), U32, P, P], I32),
         "talp_gpu_scalability": ([P, ctypes.POINTER(talp_gpu_metrics), S, S, U32, ctypes.POINTER(talp_gpu_scaling),
                                   P], I32),
+        "talp_gpu_ingest_raw": ([P, ctypes.POINTER(talp_gpu_raw_batch), S, P], I32),
         "talp_gpu_reset": ([P, U64], I32),
         "talp_gpu_memory": ([P, ctypes.POINTER(S), ctypes.POINTER(S)], I32),
         "talp_gpu_profile": ([P, I32], I32),
@@ -265,6 +276,42 @@ def talp_gpu_concurrency(ctx, batch, region, stream=None, check=True):
         _check(st)
         return out
     return st, out
+
+
+def raw_batch_from_arrays(trace_id, devices_per_rank, region_window, host_se, host_state, host_off, raw_se,
+                          raw_tag, raw_dev, raw_off, flags=0):
+    """Build a talp_gpu_raw_batch (record arrays: all numpy host arrays, or
+    all CUDA tensors).  Returns (batch, keepalive)."""
+    dpr = np.ascontiguousarray(devices_per_rank, dtype=np.uint32)
+    win = np.ascontiguousarray(region_window, dtype=np.int64)
+    hoff = np.ascontiguousarray(host_off, dtype=np.uint64)
+    roff = np.ascontiguousarray(raw_off, dtype=np.uint64)
+    keep = [dpr, win, hoff, roff]
+    ptrs, dev_flags = [], set()
+    for a, dt in ((host_se, np.int64), (host_state, np.uint8), (raw_se, np.int64), (raw_tag, np.uint8),
+                  (raw_dev, np.uint8)):
+        if not hasattr(a, "data_ptr"):
+            a = np.ascontiguousarray(a, dtype=dt)
+        keep.append(a)
+        p, is_dev = _ptr(a)
+        ptrs.append(p)
+        dev_flags.add(is_dev)
+    if len(dev_flags) != 1:
+        raise ValueError("record arrays must be all host or all device")
+    if dev_flags.pop():
+        flags |= TALP_GPU_DEVICE_PTRS
+    b = talp_gpu_raw_batch()
+    b.trace_id, b.n_ranks, b.n_regions, b.flags, b.reserved = int(trace_id), int(dpr.shape[0]), int(win.shape[0]), \
+        int(flags), 0
+    b.devices_per_rank, b.region_window, b.host_off, b.raw_off = dpr.ctypes.data, win.ctypes.data, hoff.ctypes.data, \
+        roff.ctypes.data
+    b.host_se, b.host_state, b.raw_se, b.raw_tag, b.raw_dev = ptrs
+    return b, keep
+
+
+def talp_gpu_ingest_raw(ctx, batches, stream=None):
+    arr = (talp_gpu_raw_batch * len(batches))(*batches)
+    _check(load_library().talp_gpu_ingest_raw(ctx, arr, len(batches), _stream(stream)))
 
 
 def talp_gpu_scalability(ctx, runs, ref=0, weak=False, stream=None, check=True):
@@ -539,6 +586,27 @@ class Context:
 
     def memory(self):
         return talp_gpu_memory(self.ctx)
+
+    def ingest_raw(self, raws, flags=0, stream=None, arrays=None):
+        """Ingest raw activity records (objects with .trace and raw_se /
+        raw_tag / raw_dev / raw_off as tracegen.to_raw makes); `arrays`
+        may hold CUDA tensors for the five record arrays of each."""
+        batches, keep = [], []
+        for k, r in enumerate(raws):
+            t = r.trace
+            rec = dict(host_se=t.host_se, host_state=t.host_state, raw_se=r.raw_se, raw_tag=r.raw_tag,
+                       raw_dev=r.raw_dev)
+            if arrays is not None:
+                rec.update(arrays[k])
+            b, kp = raw_batch_from_arrays(t.trace_id, t.devices_per_rank, t.region_window, rec["host_se"],
+                                          rec["host_state"], t.host_off, rec["raw_se"], rec["raw_tag"],
+                                          rec["raw_dev"], r.raw_off, flags)
+            batches.append(b)
+            keep.append(kp)
+            self._shapes[int(t.trace_id)] = (int(t.n_ranks), int(np.asarray(t.devices_per_rank).sum()),
+                                             int(np.asarray(t.region_window).shape[0]))
+        talp_gpu_ingest_raw(self.ctx, batches, stream)
+        self._keep = keep
 
     def concurrency(self, t, region, arrays=None, stream=None, check=True):
         """Concurrency profile of trace `t` (records in start order) in one

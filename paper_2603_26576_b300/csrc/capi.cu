@@ -135,9 +135,12 @@ struct talp_gpu_ctx {
     DevBuf ws;          // segment table, starts, jobs, payload, warp records, flags, sort control
     DevBuf stage;       // host-pointer record staging
     DevBuf sortbuf;     // ping-pong copies of the device segments being sorted
+    DevBuf raw;         // raw activity records: staging, lanes, counters
     PinBuf up, down;    // pinned upload / download scratch
     cudaEvent_t ev_up = nullptr;      // upload scratch free again
     cudaEvent_t ev_ws = nullptr;      // workspace/staging free again
+    cudaEvent_t ev_raw = nullptr;     // raw-record buffer free again
+    bool raw_used = false;
     bool ws_used = false;
     Tuning defaults;
     bool shape_forced = false;
@@ -762,6 +765,7 @@ talp_gpu_status talp_gpu_create(talp_gpu_ctx** out, int device, size_t hbm_budge
     c->budget = hbm_budget_bytes ? hbm_budget_bytes : static_cast<size_t>(fr * 0.9);
     cudaEventCreateWithFlags(&c->ev_up, cudaEventDisableTiming);
     cudaEventCreateWithFlags(&c->ev_ws, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&c->ev_raw, cudaEventDisableTiming);
     cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     // overrides of the sweep tuning (benchmarks and tests)
     if (const char* s = getenv("TALP_GPU_SWEEP_SHAPE")) {
@@ -790,10 +794,12 @@ talp_gpu_status talp_gpu_destroy(talp_gpu_ctx* c) {
     dev_free(c, c->ws.p, c->ws.cap);
     dev_free(c, c->stage.p, c->stage.cap);
     dev_free(c, c->sortbuf.p, c->sortbuf.cap);
+    dev_free(c, c->raw.p, c->raw.cap);
     if (c->up.p) cudaFreeHost(c->up.p);
     if (c->down.p) cudaFreeHost(c->down.p);
     if (c->ev_up) cudaEventDestroy(c->ev_up);
     if (c->ev_ws) cudaEventDestroy(c->ev_ws);
+    if (c->ev_raw) cudaEventDestroy(c->ev_raw);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (auto& pr : c->ev_pending) {
         cudaEventDestroy(pr.first);
@@ -944,6 +950,168 @@ talp_gpu_status talp_gpu_metrics_combine(talp_gpu_ctx* c, const talp_gpu_metrics
     TALP_CUDA(cudaStreamSynchronize(stream));
     memcpy(out_host, c->down.p, sizeof(MetricsOut));
     return check_metrics_flags(out_host, 1);
+}
+
+talp_gpu_status talp_gpu_ingest_raw(talp_gpu_ctx* c, const talp_gpu_raw_batch* rb, size_t nb, void* stream_) {
+    if (!c) return fail(TALP_GPU_EINVAL, "null context");
+    if (nb == 0) return TALP_GPU_OK;
+    if (!rb) return fail(TALP_GPU_EINVAL, "null batches");
+    const bool dev_ptrs = (rb[0].flags & TALP_GPU_DEVICE_PTRS) != 0;
+    const int tile = raw_tile_records();
+    std::vector<RawRank> ranks;
+    std::vector<RawTile> tiles;
+    std::vector<uint64_t> out_base(nb), hbase(nb), m_of(nb);
+    uint64_t nr = 0, outn = 0, nh = 0, mtot = 0;
+    for (size_t k = 0; k < nb; ++k) {
+        const talp_gpu_raw_batch& b = rb[k];
+        if ((b.flags & TALP_GPU_DEVICE_PTRS) != (rb[0].flags & TALP_GPU_DEVICE_PTRS))
+            return fail(TALP_GPU_EINVAL, "raw batches mix host and device pointers");
+        if (b.flags & ~(TALP_GPU_DEVICE_PTRS | TALP_GPU_APPEND)) return fail(TALP_GPU_EINVAL, "raw: unknown flags");
+        if (b.n_ranks == 0 || !b.devices_per_rank || !b.raw_off || !b.host_off)
+            return fail(TALP_GPU_EINVAL, "raw: bad header");
+        if (b.raw_off[0] != 0) return fail(TALP_GPU_EINVAL, "raw: raw_off[0] != 0");
+        outn = align_up(outn, 16);
+        out_base[k] = outn;
+        uint64_t m = 0;
+        for (uint32_t i = 0; i < b.n_ranks; ++i) {
+            const uint32_t D = b.devices_per_rank[i];
+            if (D > static_cast<uint32_t>(kRawMaxDevices))
+                return fail(TALP_GPU_EINVAL, "raw: more than 8 devices in a rank");
+            if (b.raw_off[i + 1] < b.raw_off[i]) return fail(TALP_GPU_EINVAL, "raw: raw_off decreases");
+            const uint64_t n = b.raw_off[i + 1] - b.raw_off[i];
+            if (n && D == 0) return fail(TALP_GPU_EINVAL, "raw: records of a rank without devices");
+            RawRank r;
+            r.rec0 = nr + b.raw_off[i];
+            r.out0 = outn + b.raw_off[i];
+            r.dev0 = static_cast<uint32_t>(mtot + m);
+            r.D = D;
+            r.tile0 = static_cast<uint32_t>(tiles.size());
+            for (uint64_t o = 0; o < n; o += tile)
+                tiles.push_back(RawTile{r.rec0 + o, static_cast<uint32_t>(std::min<uint64_t>(tile, n - o)),
+                                        static_cast<uint32_t>(ranks.size())});
+            r.ntile = static_cast<uint32_t>(tiles.size()) - r.tile0;
+            ranks.push_back(r);
+            m += D;
+        }
+        m_of[k] = m;
+        mtot += m;
+        const uint64_t n = b.raw_off[b.n_ranks];
+        if (n && (!b.raw_se || !b.raw_tag || !b.raw_dev)) return fail(TALP_GPU_EINVAL, "raw: null record arrays");
+        nr += n;
+        outn += n;
+        nh = align_up(nh, 16);
+        hbase[k] = nh;
+        nh += b.host_off[b.n_ranks];
+    }
+    if (tiles.size() > 0xFFFFFFFFull || mtot > 0xFFFFFFFFull) return fail(TALP_GPU_EINVAL, "raw: too large");
+    const size_t nt = tiles.size(), nrk = ranks.size();
+
+    // device buffer: [input staging][host staging][lanes][tables][hist][offs][counts][status]
+    size_t o = 0;
+    const size_t o_rse = o; o = align_up(o + (dev_ptrs ? 0 : 16 * nr), 256);
+    const size_t o_rtag = o; o = align_up(o + (dev_ptrs ? 0 : nr), 256);
+    const size_t o_rdev = o; o = align_up(o + (dev_ptrs ? 0 : nr), 256);
+    const size_t o_hse = o; o = align_up(o + (dev_ptrs ? 0 : 16 * nh), 256);
+    const size_t o_hst = o; o = align_up(o + (dev_ptrs ? 0 : nh + 16), 256);
+    const size_t o_lse = o; o = align_up(o + 16 * outn, 256);
+    const size_t o_ltag = o; o = align_up(o + outn + 16, 256);
+    const size_t o_ranks = o; o = align_up(o + sizeof(RawRank) * nrk, 256);
+    const size_t o_tiles = o; o = align_up(o + sizeof(RawTile) * nt, 256);
+    const size_t o_hist = o; o = align_up(o + 4ull * kRawMaxDevices * 32 * nt, 256);
+    const size_t o_offs = o; o = align_up(o + 8ull * kRawMaxDevices * 32 * nt, 256);
+    const size_t o_cnt = o; o = align_up(o + 8 * mtot, 256);
+    const size_t o_st = o; o += 256;
+    const size_t tab_bytes = o_hist - o_ranks;
+
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    TALP_CUDA(cudaSetDevice(c->device));
+    if (c->raw_used) TALP_CUDA(cudaStreamWaitEvent(stream, c->ev_raw, 0));
+    TALP_TRY(grow(c, c->raw, o));
+    char* R = static_cast<char*>(c->raw.p);
+    TALP_CUDA(cudaEventSynchronize(c->ev_up));
+    TALP_TRY(grow_pinned(c->up, tab_bytes));
+    memcpy(c->up.p, ranks.data(), sizeof(RawRank) * nrk);
+    if (nt) memcpy(static_cast<char*>(c->up.p) + (o_tiles - o_ranks), tiles.data(), sizeof(RawTile) * nt);
+    TALP_CUDA(cudaMemcpyAsync(R + o_ranks, c->up.p, tab_bytes, cudaMemcpyHostToDevice, stream));
+    TALP_CUDA(cudaEventRecord(c->ev_up, stream));
+    const int64_t* rse;
+    const uint8_t *rtag, *rdev;
+    if (dev_ptrs) {
+        if (nb != 1) return fail(TALP_GPU_EINVAL, "raw: device pointers take one batch per call");
+        rse = rb[0].raw_se;
+        rtag = rb[0].raw_tag;
+        rdev = rb[0].raw_dev;
+        if (reinterpret_cast<uintptr_t>(rse) & 15u) return fail(TALP_GPU_EINVAL, "raw: raw_se not 16-byte aligned");
+    } else {
+        uint64_t p = 0;
+        for (size_t k = 0; k < nb; ++k) {
+            const uint64_t n = rb[k].raw_off[rb[k].n_ranks];
+            if (n) {
+                TALP_CUDA(cudaMemcpyAsync(R + o_rse + 16 * p, rb[k].raw_se, 16 * n, cudaMemcpyHostToDevice, stream));
+                TALP_CUDA(cudaMemcpyAsync(R + o_rtag + p, rb[k].raw_tag, n, cudaMemcpyHostToDevice, stream));
+                TALP_CUDA(cudaMemcpyAsync(R + o_rdev + p, rb[k].raw_dev, n, cudaMemcpyHostToDevice, stream));
+            }
+            const uint64_t h = rb[k].host_off[rb[k].n_ranks];
+            if (h) {
+                if (!rb[k].host_se || !rb[k].host_state) return fail(TALP_GPU_EINVAL, "raw: null host arrays");
+                TALP_CUDA(cudaMemcpyAsync(R + o_hse + 16 * hbase[k], rb[k].host_se, 16 * h, cudaMemcpyHostToDevice,
+                                          stream));
+                TALP_CUDA(cudaMemcpyAsync(R + o_hst + hbase[k], rb[k].host_state, h, cudaMemcpyHostToDevice, stream));
+            }
+            p += n;
+        }
+        rse = reinterpret_cast<const int64_t*>(R + o_rse);
+        rtag = reinterpret_cast<const uint8_t*>(R + o_rtag);
+        rdev = reinterpret_cast<const uint8_t*>(R + o_rdev);
+    }
+    TALP_CUDA(cudaMemsetAsync(R + o_st, 0, 16, stream));
+    const int grid = static_cast<int>(std::max<size_t>(1, std::min<size_t>(nt, static_cast<size_t>(c->num_sms) * 8)));
+    TALP_CUDA(launch_raw_count(rdev, rtag, reinterpret_cast<const RawTile*>(R + o_tiles), static_cast<uint32_t>(nt),
+                               reinterpret_cast<const RawRank*>(R + o_ranks), static_cast<uint32_t>(nrk),
+                               reinterpret_cast<uint32_t*>(R + o_hist), reinterpret_cast<uint64_t*>(R + o_offs),
+                               reinterpret_cast<uint64_t*>(R + o_cnt), reinterpret_cast<uint32_t*>(R + o_st), grid,
+                               stream));
+    TALP_CUDA(launch_raw_scatter(rse, rtag, rdev, reinterpret_cast<const RawTile*>(R + o_tiles),
+                                 static_cast<uint32_t>(nt), reinterpret_cast<const RawRank*>(R + o_ranks),
+                                 reinterpret_cast<const uint64_t*>(R + o_offs), reinterpret_cast<int64_t*>(R + o_lse),
+                                 reinterpret_cast<uint8_t*>(R + o_ltag), grid, stream));
+    c->kernel_launches += nt ? 3 : 0;
+    // the ingest needs each device's record count on the host
+    TALP_TRY(grow_pinned(c->down, 8 * mtot + 16));
+    TALP_CUDA(cudaMemcpyAsync(c->down.p, R + o_cnt, 8 * mtot, cudaMemcpyDeviceToHost, stream));
+    TALP_CUDA(cudaMemcpyAsync(static_cast<char*>(c->down.p) + 8 * mtot, R + o_st, 4, cudaMemcpyDeviceToHost, stream));
+    TALP_CUDA(cudaStreamSynchronize(stream));
+    const uint64_t* cnt = static_cast<const uint64_t*>(c->down.p);
+    uint32_t status = 0;
+    memcpy(&status, static_cast<char*>(c->down.p) + 8 * mtot, 4);
+    if (status) return fail(TALP_GPU_EINVAL, "raw: a record names a device its rank does not have");
+
+    std::vector<std::vector<uint64_t>> dev_off(nb);
+    std::vector<talp_gpu_trace_batch> tb(nb);
+    uint64_t g = 0;
+    for (size_t k = 0; k < nb; ++k) {
+        const talp_gpu_raw_batch& b = rb[k];
+        dev_off[k].assign(m_of[k] + 1, 0);
+        for (uint64_t d = 0; d < m_of[k]; ++d, ++g) dev_off[k][d + 1] = dev_off[k][d] + cnt[g];
+        talp_gpu_trace_batch& t = tb[k];
+        memset(&t, 0, sizeof(t));
+        t.trace_id = b.trace_id;
+        t.n_ranks = b.n_ranks;
+        t.n_regions = b.n_regions;
+        t.flags = TALP_GPU_DEVICE_PTRS | (b.flags & TALP_GPU_APPEND);
+        t.devices_per_rank = b.devices_per_rank;
+        t.region_window = b.region_window;
+        t.host_se = dev_ptrs ? b.host_se : reinterpret_cast<const int64_t*>(R + o_hse) + 2 * hbase[k];
+        t.host_state = dev_ptrs ? b.host_state : reinterpret_cast<const uint8_t*>(R + o_hst) + hbase[k];
+        t.host_off = b.host_off;
+        t.dev_se = reinterpret_cast<const int64_t*>(R + o_lse) + 2 * out_base[k];
+        t.dev_tag = reinterpret_cast<const uint8_t*>(R + o_ltag) + out_base[k];
+        t.dev_off = dev_off[k].data();
+    }
+    const talp_gpu_status st = talp_gpu_ingest_events(c, tb.data(), nb, stream_);
+    TALP_CUDA(cudaEventRecord(c->ev_raw, stream));
+    c->raw_used = true;
+    return st;
 }
 
 talp_gpu_status talp_gpu_scalability(talp_gpu_ctx* c, const talp_gpu_metrics* runs, size_t n_runs, size_t ref,

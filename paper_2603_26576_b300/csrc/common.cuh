@@ -136,6 +136,22 @@ struct ConcChunk {
     uint32_t dev;              // device index
 };
 
+// Raw activity-record adapter: per rank its input records and output lane
+// range, per tile of input records its rank.
+constexpr int kRawMaxDevices = 8;   // local devices per rank (buckets: device x stream)
+struct RawRank {
+    uint64_t rec0;             // first input record
+    uint64_t out0;             // first output lane record (the rank's devices in order)
+    uint32_t dev0;             // global index of its first device
+    uint32_t D;                // its devices
+    uint32_t tile0, ntile;     // its input tiles
+};
+struct RawTile {
+    uint64_t rec0;             // first input record
+    uint32_t n;                // records
+    uint32_t rank;             // global rank index
+};
+
 // ---------------------------------------------------------------- helpers
 
 __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }

@@ -616,6 +616,52 @@ def split_runs(trace: Trace, k: int, seed=3) -> Trace:
     return _with_dev(trace, se, tag)
 
 
+@dataclass
+class RawTrace:
+    """A trace's device records as an activity API delivers them: per rank,
+    one buffer of all its devices' records with the device index within
+    the rank, the streams interleaved in completion order (a record is
+    delivered when it and every earlier record of its stream are done)."""
+    trace: Trace
+    raw_se: np.ndarray       # int64[N, 2]
+    raw_tag: np.ndarray      # uint8[N]
+    raw_dev: np.ndarray      # uint8[N]
+    raw_off: np.ndarray      # uint64[n + 1]
+
+
+def to_raw(trace: Trace) -> RawTrace:
+    dpr = np.asarray(trace.devices_per_rank, np.int64)
+    m = int(dpr.sum())
+    cnt = np.diff(trace.dev_off.astype(np.int64))
+    g = np.repeat(np.arange(m), cnt)                                  # global device of each record
+    rank = np.repeat(np.repeat(np.arange(trace.n_ranks), dpr), cnt)
+    local = g - np.concatenate([[0], np.cumsum(dpr)])[rank]
+    lane = g * 32 + (trace.dev_tag & 31).astype(np.int64)
+    # per (device, stream) lane in start order; delivery key: the running
+    # maximum end along the lane (a record is done when it and all before it
+    # in its stream are), computed for all lanes at once by lifting each
+    # lane above the previous ones
+    if trace.sorted_by_start:
+        small = lane.astype(np.int16) if m * 32 < (1 << 15) else lane   # 16-bit keys sort by radix
+        order = np.argsort(small, kind="stable")   # each device already in start order
+    else:
+        order = np.lexsort((trace.dev_se[:, 0], lane))
+    se, tag, lane, rank, local = trace.dev_se[order], trace.dev_tag[order], lane[order], rank[order], local[order]
+    if se.shape[0]:
+        lo = int(se[:, 1].min())
+        span = int(se[:, 1].max()) - lo + 1
+        seg = np.concatenate([[0], np.cumsum(lane[1:] != lane[:-1])])
+        key = np.maximum.accumulate((se[:, 1] - lo) + seg * span) - seg * span
+    else:
+        key = np.zeros(0, np.int64)
+    d = np.argsort((rank.astype(np.int64) << 42) | key, kind="stable") if key.size and int(key.max()) < (1 << 42) \
+        else np.lexsort((key, rank))
+    off = np.zeros(trace.n_ranks + 1, np.uint64)
+    off[1:] = np.cumsum(np.bincount(rank, minlength=trace.n_ranks))
+    return RawTrace(trace, np.ascontiguousarray(se[d]), np.ascontiguousarray(tag[d]),
+                    np.ascontiguousarray(local[d].astype(np.uint8)), off)
+
+
 def _with_dev(trace, se, tag):
     return Trace(trace_id=trace.trace_id, n_ranks=trace.n_ranks, devices_per_rank=trace.devices_per_rank,
                  region_window=trace.region_window, host_se=trace.host_se, host_state=trace.host_state,
