@@ -137,7 +137,10 @@ struct talp_gpu_ctx {
     DevBuf sortbuf;     // ping-pong copies of the device segments being sorted
     DevBuf raw;         // raw activity records: staging, lanes, counters
     PinBuf up, down;    // pinned upload / download scratch
+    PinBuf upf;         // pinned upload scratch of result calls (their own, so that an ingest
+                        // followed by a result call never waits for the ingest's upload)
     cudaEvent_t ev_up = nullptr;      // upload scratch free again
+    cudaEvent_t ev_upf = nullptr;     // result-call upload scratch free again
     cudaEvent_t ev_ws = nullptr;      // workspace/staging free again
     cudaEvent_t ev_raw = nullptr;     // raw-record buffer free again
     bool raw_used = false;
@@ -764,6 +767,7 @@ talp_gpu_status talp_gpu_create(talp_gpu_ctx** out, int device, size_t hbm_budge
     cudaMemGetInfo(&fr, &tot);
     c->budget = hbm_budget_bytes ? hbm_budget_bytes : static_cast<size_t>(fr * 0.9);
     cudaEventCreateWithFlags(&c->ev_up, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&c->ev_upf, cudaEventDisableTiming);
     cudaEventCreateWithFlags(&c->ev_ws, cudaEventDisableTiming);
     cudaEventCreateWithFlags(&c->ev_raw, cudaEventDisableTiming);
     cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
@@ -796,8 +800,10 @@ talp_gpu_status talp_gpu_destroy(talp_gpu_ctx* c) {
     dev_free(c, c->sortbuf.p, c->sortbuf.cap);
     dev_free(c, c->raw.p, c->raw.cap);
     if (c->up.p) cudaFreeHost(c->up.p);
+    if (c->upf.p) cudaFreeHost(c->upf.p);
     if (c->down.p) cudaFreeHost(c->down.p);
     if (c->ev_up) cudaEventDestroy(c->ev_up);
+    if (c->ev_upf) cudaEventDestroy(c->ev_upf);
     if (c->ev_ws) cudaEventDestroy(c->ev_ws);
     if (c->ev_raw) cudaEventDestroy(c->ev_raw);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -879,11 +885,11 @@ static talp_gpu_status finalize_common(talp_gpu_ctx* c, const uint64_t* ids, siz
     TALP_TRY(grow(c, c->ws, jb + sizeof(MetricsOut) * nj));
     MetricsOut* res = reinterpret_cast<MetricsOut*>(static_cast<char*>(c->ws.p) + jb);
     for (size_t k = 0; k < nj; ++k) jobs[k].out = out_dev_user ? out_dev_user + k : res + k;
-    TALP_CUDA(cudaEventSynchronize(c->ev_up));
-    TALP_TRY(grow_pinned(c->up, jb));
-    memcpy(c->up.p, jobs.data(), sizeof(FinalizeJob) * nj);
-    TALP_CUDA(cudaMemcpyAsync(c->ws.p, c->up.p, sizeof(FinalizeJob) * nj, cudaMemcpyHostToDevice, stream));
-    TALP_CUDA(cudaEventRecord(c->ev_up, stream));
+    TALP_CUDA(cudaEventSynchronize(c->ev_upf));
+    TALP_TRY(grow_pinned(c->upf, jb));
+    memcpy(c->upf.p, jobs.data(), sizeof(FinalizeJob) * nj);
+    TALP_CUDA(cudaMemcpyAsync(c->ws.p, c->upf.p, sizeof(FinalizeJob) * nj, cudaMemcpyHostToDevice, stream));
+    TALP_CUDA(cudaEventRecord(c->ev_upf, stream));
     TALP_CUDA(launch_finalize(static_cast<const FinalizeJob*>(c->ws.p), static_cast<uint32_t>(nj), stream));
     ++c->kernel_launches;
     if (!sync) {
