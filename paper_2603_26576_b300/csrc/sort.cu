@@ -448,47 +448,63 @@ __global__ void __launch_bounds__(256) sort_merge_split_kernel(const SegDesc* __
     }
 }
 
-__global__ void __launch_bounds__(256) sort_merge_kernel(const SegDesc* __restrict__ segs, SortCtl* ctl, int r) {
+// Each CTA takes a contiguous range of tiles, so consecutive tiles share
+// their segment's descriptor, run starts and the split at their common
+// boundary: only the split at a chunk's far end is read from memory, and it
+// is fetched one chunk ahead.
+__global__ void __launch_bounds__(256, 8) sort_merge_kernel(const SegDesc* __restrict__ segs, SortCtl* ctl, int r) {
     __shared__ longlong2 s_in[kMergeChunk];
-    __shared__ longlong2 s_out[kMergeChunk];
     __shared__ uint8_t s_tin[kMergeChunk];
-    __shared__ uint8_t s_tout[kMergeChunk];
+    __shared__ uint64_t s_runs[kMaxRuns + 1];
     if (static_cast<uint32_t>(r) >= ctl->max_rounds) return;
-    const uint32_t ntile = static_cast<uint32_t>(ctl->ntile);
-    for (uint32_t t = blockIdx.x; t < ntile; t += gridDim.x) {
-        const uint32_t k = seg_of_tile(ctl, t);
+    const uint64_t ntile = ctl->ntile;
+    const uint64_t tb0 = ntile * blockIdx.x / gridDim.x, tb1 = ntile * (blockIdx.x + 1) / gridDim.x;
+    if (tb0 >= tb1) return;
+    uint32_t k = seg_of_tile(ctl, static_cast<uint32_t>(tb0));
+    uint64_t t = tb0;
+    while (t < tb1) {
+        while (t >= ctl->tile_base[k + 1]) ++k;   // block-uniform
+        const uint64_t tb = ctl->tile_base[k], te = min(ctl->tile_base[k + 1], tb1);
         const uint32_t R = ctl->rounds[k];
-        if (R == 0 || static_cast<uint32_t>(r) >= R) {   // block-uniform
-            t = skip_segment(ctl, k, t);
+        if (R == 0 || static_cast<uint32_t>(r) >= R) {
+            t = te;
             continue;
         }
         const SegDesc& d = segs[ctl->list[k]];
+        const uint64_t n_seg = d.n;
         const int64_t* se;
         const uint8_t* tag;
         merge_src(d, ctl, k, r, se, tag);
         int64_t* dse = ctl->buf_se[r & 1] + 2 * ctl->rec_base[k];
         uint8_t* dtag = ctl->buf_tag[r & 1] + ctl->rec_base[k];
-        const uint64_t* runs = ctl->runs + static_cast<uint64_t>(k) * (kMaxRuns + 1);
         const uint32_t nr = ctl->nruns[k] + 1;
+        __syncthreads();
+        if (threadIdx.x <= nr) s_runs[threadIdx.x] = ctl->runs[static_cast<uint64_t>(k) * (kMaxRuns + 1) + threadIdx.x];
+        __syncthreads();
         const uint32_t w = 1u << r;
-        const uint64_t tb = ctl->tile_base[k];
-        const uint64_t t0 = static_cast<uint64_t>(t - tb) * kSortTile;
-        const uint64_t t1 = min(t0 + static_cast<uint64_t>(kSortTile), d.n);
-        for (uint64_t h0 = t0; h0 < t1; h0 += kMergeChunk) {
-            const uint64_t h1 = min(h0 + static_cast<uint64_t>(kMergeChunk), t1);
+        // outputs of this segment's tiles in [t, te), chunk by chunk
+        const uint64_t o_end = min((te - tb) * kSortTile, n_seg);
+        uint64_t h0 = (t - tb) * kSortTile;
+        auto split_at = [&](uint64_t h) -> uint64_t {
+            return ctl->offs[(tb + h / kSortTile) * 256 + (h % kSortTile) / kMergeChunk];
+        };
+        // split at the current chunk's far end, fetched one chunk ahead; the
+        // split at its near end is the previous chunk's far end
+        uint64_t pre = h0 + kMergeChunk < n_seg ? split_at(h0 + kMergeChunk) : 0;
+        uint64_t near = h0 > 0 && h0 < n_seg ? split_at(h0) : 0;
+        for (; h0 < o_end; h0 += kMergeChunk) {
+            const uint64_t h1 = min(h0 + static_cast<uint64_t>(kMergeChunk), n_seg);
+            const uint64_t far = pre;
+            if (h1 + kMergeChunk < n_seg) pre = split_at(h1 + kMergeChunk);
             for (uint32_t g = 0; g < nr; g += 2 * w) {
-                const uint64_t pa = runs[g];
-                const uint64_t pm = runs[min(g + w, nr)];
-                const uint64_t pb = runs[min(g + 2 * w, nr)];
+                const uint64_t pa = s_runs[g];
+                const uint64_t pm = s_runs[min(g + w, nr)];
+                const uint64_t pb = s_runs[min(g + 2 * w, nr)];
                 if (pb <= h0 || pa >= h1) continue;
                 const uint64_t lo = max(h0, pa), hi = min(h1, pb);
                 const uint64_t nA = pm - pa;
-                // splits at the chunk's ends (stored by the split kernel),
-                // or the pair's own ends when the pair starts or ends inside
-                const uint64_t i0 = pa >= h0 ? 0
-                                             : ctl->offs[(tb + h0 / kSortTile) * 256 + (h0 % kSortTile) / kMergeChunk];
-                const uint64_t i1 = pb <= h1 ? nA
-                                             : ctl->offs[(tb + h1 / kSortTile) * 256 + (h1 % kSortTile) / kMergeChunk];
+                const uint64_t i0 = pa >= h0 ? 0 : near;
+                const uint64_t i1 = pb <= h1 ? nA : far;
                 const uint64_t j0 = (lo - pa) - i0, j1 = (hi - pa) - i1;
                 const int ca = static_cast<int>(i1 - i0), cb = static_cast<int>(j1 - j0);
                 for (int q = threadIdx.x; q < ca + cb; q += blockDim.x) {
@@ -497,7 +513,8 @@ __global__ void __launch_bounds__(256) sort_merge_kernel(const SegDesc* __restri
                     s_tin[q] = tag[src];
                 }
                 __syncthreads();
-                // 4 outputs per thread: merge path inside the staged ranges
+                // 4 outputs per thread: merge path inside the staged ranges,
+                // written straight to the output
                 const int n = ca + cb;
                 const int o0 = min(static_cast<int>(threadIdx.x) * 4, n);
                 const int o1 = min(o0 + 4, n);
@@ -512,18 +529,15 @@ __global__ void __launch_bounds__(256) sort_merge_kernel(const SegDesc* __restri
                     for (int o = o0; o < o1; ++o) {
                         const bool takeA = ib >= cb || (ia < ca && s_in[ia].x <= s_in[ca + ib].x);
                         const int src = takeA ? ia++ : ca + ib++;
-                        s_out[o] = s_in[src];
-                        s_tout[o] = s_tin[src];
+                        *reinterpret_cast<longlong2*>(dse + 2 * (lo + o)) = s_in[src];
+                        dtag[lo + o] = s_tin[src];
                     }
                 }
                 __syncthreads();
-                for (int q = threadIdx.x; q < n; q += blockDim.x) {
-                    *reinterpret_cast<longlong2*>(dse + 2 * (lo + q)) = s_out[q];
-                    dtag[lo + q] = s_tout[q];
-                }
-                __syncthreads();
             }
+            near = far;
         }
+        t = te;
     }
 }
 
