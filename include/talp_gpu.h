@@ -199,12 +199,29 @@ talp_gpu_status talp_gpu_ingest_events(talp_gpu_ctx *ctx, const talp_gpu_trace_b
  * devices_per_rank[i] - 1, at most 8 devices per rank).  Records of one
  * stream must be delivered in start order (a stream executes in order); the
  * streams may interleave arbitrarily.
+ *
+ * TALP_GPU_HOLD_BACK streams a trace's buffers over several calls.  A later
+ * buffer may still bring a record that starts before records of other
+ * streams already delivered, so, per device, only the records starting at
+ * or before its watermark W = min over the device's declared streams of
+ * their last delivered start are folded; the others are held back on the
+ * GPU and delivered again, ahead of the next call's records of the trace.
+ * stream_mask[i * 8 + d] declares the streams (bit s = stream s) of device
+ * d of rank i; a declared stream that has delivered nothing yet holds its
+ * device's watermark below every record.  A call for the trace without
+ * TALP_GPU_HOLD_BACK folds every held record (a flush) and ends the hold
+ * state; so do a call without TALP_GPU_APPEND and talp_gpu_reset.  The
+ * first hold-back call of a trace may come without APPEND (it creates the
+ * trace), later ones take APPEND.
  */
+#define TALP_GPU_HOLD_BACK 0x8u   /* raw batches: hold back records a later buffer may precede */
+
 typedef struct {
     uint64_t trace_id;
     uint32_t n_ranks;
     uint32_t n_regions;
-    uint32_t flags;                    /* TALP_GPU_DEVICE_PTRS (all record arrays), TALP_GPU_APPEND */
+    uint32_t flags;                    /* TALP_GPU_DEVICE_PTRS (all record arrays), TALP_GPU_APPEND,
+                                          TALP_GPU_HOLD_BACK */
     uint32_t reserved;                 /* must be 0 */
     const uint32_t *devices_per_rank;  /* host [n_ranks], each <= 8 */
     const int64_t *region_window;      /* host [n_regions][n_ranks][2] */
@@ -215,20 +232,33 @@ typedef struct {
     const uint8_t *raw_tag;            /* [N_raw] kind << 5 | stream */
     const uint8_t *raw_dev;            /* [N_raw] device within the rank */
     const uint64_t *raw_off;           /* host [n_ranks + 1], raw_off[0] == 0 */
+    const uint32_t *stream_mask;       /* host [n_ranks][8] declared streams; needed with HOLD_BACK, else
+                                          may be NULL */
 } talp_gpu_raw_batch;
 
 /*
  * Ingest raw activity records: a stable scatter on the GPU groups every
  * rank's records by (device, stream) into per-device lanes, each stream in
- * delivery (= start) order, then the lanes go through
- * talp_gpu_ingest_events without TALP_GPU_SORTED_BY_START (the out-of-order
- * devices are merged by start on the GPU).  Synchronises `stream` once, to
- * read each device's record count.  With device pointers, one batch per
- * call.  Errors: those of talp_gpu_ingest_events, and EINVAL for a record
- * naming a device its rank does not have or more than 8 devices in a rank.
+ * delivery (= start) order, then (TALP_GPU_HOLD_BACK) splits each lane at
+ * its device's watermark, and the lanes go through talp_gpu_ingest_events
+ * without TALP_GPU_SORTED_BY_START (the out-of-order devices are merged by
+ * start on the GPU).  Synchronises `stream` once, to read each device's
+ * record count.  A trace appears at most once per call.  Errors: those of
+ * talp_gpu_ingest_events; EINVAL for a record naming a device its rank does
+ * not have, more than 8 devices in a rank, HOLD_BACK without stream masks,
+ * a shape that differs from the held records' trace, 2^32 records in one
+ * rank of a hold-back call, and a record on a stream its device does not
+ * declare (found on the GPU; the trace's held records are then dropped).
  */
 talp_gpu_status talp_gpu_ingest_raw(talp_gpu_ctx *ctx, const talp_gpu_raw_batch *batches, size_t n_batches,
                                     void *stream);
+
+/*
+ * Number of raw records of trace `trace_id` held back by TALP_GPU_HOLD_BACK
+ * calls and not folded yet (0 for a trace without hold state).  Host call,
+ * no GPU work.  Errors: EINVAL (null argument).
+ */
+talp_gpu_status talp_gpu_raw_held(talp_gpu_ctx *ctx, uint64_t trace_id, uint64_t *out_host);
 
 /* ----------------------------------------------------------------- results */
 

@@ -15,6 +15,7 @@ TALP_GPU_ALL_REGIONS = (1 << 32) - 1
 TALP_GPU_DEVICE_PTRS = 0x1
 TALP_GPU_SORTED_BY_START = 0x2
 TALP_GPU_APPEND = 0x4
+TALP_GPU_HOLD_BACK = 0x8
 
 STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEDOUT", -5: "ENOTFOUND", -6: "EBUSY"}
 
@@ -22,7 +23,7 @@ STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEDOUT
 EXPORTED_SYMBOLS = (
     "talp_gpu_create", "talp_gpu_destroy", "talp_gpu_ingest_events", "talp_gpu_region_metrics",
     "talp_gpu_region_metrics_batch", "talp_gpu_region_metrics_device", "talp_gpu_metrics_combine",
-    "talp_gpu_concurrency", "talp_gpu_scalability", "talp_gpu_ingest_raw",
+    "talp_gpu_concurrency", "talp_gpu_scalability", "talp_gpu_ingest_raw", "talp_gpu_raw_held",
     "talp_gpu_unit_sums",
     "talp_gpu_reset", "talp_gpu_memory", "talp_gpu_profile", "talp_gpu_profile_read", "talp_gpu_reduce_noalloc",
     "talp_gpu_plan_create", "talp_gpu_plan_launch", "talp_gpu_plan_metrics", "talp_gpu_plan_info",
@@ -96,7 +97,7 @@ class talp_gpu_raw_batch(ctypes.Structure):
         ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("devices_per_rank", ctypes.c_void_p),
         ("region_window", ctypes.c_void_p), ("host_se", ctypes.c_void_p), ("host_state", ctypes.c_void_p),
         ("host_off", ctypes.c_void_p), ("raw_se", ctypes.c_void_p), ("raw_tag", ctypes.c_void_p),
-        ("raw_dev", ctypes.c_void_p), ("raw_off", ctypes.c_void_p),
+        ("raw_dev", ctypes.c_void_p), ("raw_off", ctypes.c_void_p), ("stream_mask", ctypes.c_void_p),
     ]
 
 
@@ -156,6 +157,7 @@ def load_library():
         "talp_gpu_scalability": ([P, ctypes.POINTER(talp_gpu_metrics), S, S, U32, ctypes.POINTER(talp_gpu_scaling),
                                   P], I32),
         "talp_gpu_ingest_raw": ([P, ctypes.POINTER(talp_gpu_raw_batch), S, P], I32),
+        "talp_gpu_raw_held": ([P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)], I32),
         "talp_gpu_reset": ([P, U64], I32),
         "talp_gpu_memory": ([P, ctypes.POINTER(S), ctypes.POINTER(S)], I32),
         "talp_gpu_profile": ([P, I32], I32),
@@ -279,14 +281,19 @@ def talp_gpu_concurrency(ctx, batch, region, stream=None, check=True):
 
 
 def raw_batch_from_arrays(trace_id, devices_per_rank, region_window, host_se, host_state, host_off, raw_se,
-                          raw_tag, raw_dev, raw_off, flags=0):
+                          raw_tag, raw_dev, raw_off, flags=0, stream_mask=None):
     """Build a talp_gpu_raw_batch (record arrays: all numpy host arrays, or
-    all CUDA tensors).  Returns (batch, keepalive)."""
+    all CUDA tensors; stream_mask: host [n_ranks][8] or None).  Returns
+    (batch, keepalive)."""
     dpr = np.ascontiguousarray(devices_per_rank, dtype=np.uint32)
     win = np.ascontiguousarray(region_window, dtype=np.int64)
     hoff = np.ascontiguousarray(host_off, dtype=np.uint64)
     roff = np.ascontiguousarray(raw_off, dtype=np.uint64)
     keep = [dpr, win, hoff, roff]
+    smask = None
+    if stream_mask is not None:
+        smask = np.ascontiguousarray(stream_mask, dtype=np.uint32).reshape(dpr.shape[0], 8)
+        keep.append(smask)
     ptrs, dev_flags = [], set()
     for a, dt in ((host_se, np.int64), (host_state, np.uint8), (raw_se, np.int64), (raw_tag, np.uint8),
                   (raw_dev, np.uint8)):
@@ -306,12 +313,19 @@ def raw_batch_from_arrays(trace_id, devices_per_rank, region_window, host_se, ho
     b.devices_per_rank, b.region_window, b.host_off, b.raw_off = dpr.ctypes.data, win.ctypes.data, hoff.ctypes.data, \
         roff.ctypes.data
     b.host_se, b.host_state, b.raw_se, b.raw_tag, b.raw_dev = ptrs
+    b.stream_mask = smask.ctypes.data if smask is not None else None
     return b, keep
 
 
 def talp_gpu_ingest_raw(ctx, batches, stream=None):
     arr = (talp_gpu_raw_batch * len(batches))(*batches)
     _check(load_library().talp_gpu_ingest_raw(ctx, arr, len(batches), _stream(stream)))
+
+
+def talp_gpu_raw_held(ctx, trace_id):
+    out = ctypes.c_uint64(0)
+    _check(load_library().talp_gpu_raw_held(ctx, int(trace_id), ctypes.byref(out)))
+    return int(out.value)
 
 
 def talp_gpu_scalability(ctx, runs, ref=0, weak=False, stream=None, check=True):
@@ -589,9 +603,12 @@ class Context:
 
     def ingest_raw(self, raws, flags=0, stream=None, arrays=None):
         """Ingest raw activity records (objects with .trace and raw_se /
-        raw_tag / raw_dev / raw_off as tracegen.to_raw makes); `arrays`
-        may hold CUDA tensors for the five record arrays of each."""
+        raw_tag / raw_dev / raw_off as tracegen.to_raw makes, and a
+        stream_mask attribute for TALP_GPU_HOLD_BACK); `flags` is one
+        word for all or a list with one per trace; `arrays` may hold CUDA
+        tensors for the five record arrays of each."""
         batches, keep = [], []
+        fl = list(flags) if isinstance(flags, (list, tuple)) else [flags] * len(raws)
         for k, r in enumerate(raws):
             t = r.trace
             rec = dict(host_se=t.host_se, host_state=t.host_state, raw_se=r.raw_se, raw_tag=r.raw_tag,
@@ -600,13 +617,17 @@ class Context:
                 rec.update(arrays[k])
             b, kp = raw_batch_from_arrays(t.trace_id, t.devices_per_rank, t.region_window, rec["host_se"],
                                           rec["host_state"], t.host_off, rec["raw_se"], rec["raw_tag"],
-                                          rec["raw_dev"], r.raw_off, flags)
+                                          rec["raw_dev"], r.raw_off, fl[k], getattr(r, "stream_mask", None))
             batches.append(b)
             keep.append(kp)
             self._shapes[int(t.trace_id)] = (int(t.n_ranks), int(np.asarray(t.devices_per_rank).sum()),
                                              int(np.asarray(t.region_window).shape[0]))
         talp_gpu_ingest_raw(self.ctx, batches, stream)
         self._keep = keep
+
+    def raw_held(self, trace_id):
+        """Raw records of the trace held back and not folded yet."""
+        return talp_gpu_raw_held(self.ctx, trace_id)
 
     def concurrency(self, t, region, arrays=None, stream=None, check=True):
         """Concurrency profile of trace `t` (records in start order) in one

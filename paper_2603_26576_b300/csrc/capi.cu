@@ -52,6 +52,8 @@ talp_gpu_status cuda_fail(cudaError_t e, const char* what) {
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Per-trace device state: partial sums, windows, running carries.
+struct RawHold;   // held-back raw records of a trace
+
 struct TraceState {
     uint64_t id = 0;
     uint32_t n = 0, m = 0, R = 0;
@@ -157,6 +159,8 @@ struct talp_gpu_ctx {
     uint64_t kernel_launches = 0;
     int64_t wait_limit = 4000000000LL;   // cycles (~2 s at 2 GHz)
     int dependents = 0;                  // live plans and servers on this context
+    std::unordered_map<uint64_t, RawHold*> holds;   // trace id -> held-back raw records
+    bool raw_inner = false;              // ingest_events called by ingest_raw
 };
 
 const TraceDev* talp::trace_device_desc(talp_gpu_ctx* c, uint64_t trace_id, uint32_t* n_regions) {
@@ -432,6 +436,8 @@ talp_gpu_status get_traces(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches,
     ts.assign(nb, nullptr);
     for (size_t k = 0; k < nb; ++k) {
         const talp_gpu_trace_batch& b = batches[k];
+        // a new trace of this id ends the old one's held-back raw records
+        if (!(b.flags & TALP_GPU_APPEND) && !c->raw_inner) raw_hold_drop(c, b.trace_id);
         auto it = c->traces.find(b.trace_id);
         if (it != c->traces.end() && same_shape(it->second, b)) {
             ts[k] = it->second;
@@ -793,6 +799,7 @@ talp_gpu_status talp_gpu_destroy(talp_gpu_ctx* c) {
     if (c->dependents > 0) return fail(TALP_GPU_EBUSY, "plans or servers still use this context");
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
+    raw_hold_drop(c, TALP_GPU_ALL);
     for (auto& kv : c->traces) free_trace(c, kv.second);
     c->traces.clear();
     dev_free(c, c->ws.p, c->ws.cap);
@@ -958,61 +965,136 @@ talp_gpu_status talp_gpu_metrics_combine(talp_gpu_ctx* c, const talp_gpu_metrics
     return check_metrics_flags(out_host, 1);
 }
 
+}  // extern "C"
+
+namespace {
+
+// Held-back raw records of a trace: its shape, each stream's last delivered
+// start and declared-stream masks, and the held records (ping-pong buffers;
+// rank r's held records at buf[cur] + off[r], cnt[r] of them).
+struct RawHold {
+    uint32_t n = 0;
+    std::vector<uint32_t> dpr;
+    std::vector<uint32_t> smask;   // [n][kRawMaxDevices]
+    DevBuf ls;                     // int64 [n][kRawBuckets]
+    bool fresh = true;             // ls not written yet
+    DevBuf buf[2];
+    size_t o_tag[2] = {0, 0}, o_dev[2] = {0, 0};   // byte offsets of the tags and devices in buf[k]
+    int cur = 0;
+    std::vector<uint64_t> off, cnt;
+};
+
+// held-record buffer for up to cap records: rows, then tags, then devices
+size_t hold_tag_at(uint64_t cap) { return align_up(16 * cap, 256); }
+size_t hold_dev_at(uint64_t cap) { return align_up(hold_tag_at(cap) + cap, 256); }
+size_t hold_bytes(uint64_t cap) { return align_up(hold_dev_at(cap) + cap, 256) + 256; }
+
+}  // namespace
+
+void talp::raw_hold_drop(talp_gpu_ctx* c, uint64_t trace_id) {
+    auto& m = c->holds;
+    auto drop = [&](RawHold* h) {
+        dev_free(c, h->ls.p, h->ls.cap);
+        dev_free(c, h->buf[0].p, h->buf[0].cap);
+        dev_free(c, h->buf[1].p, h->buf[1].cap);
+        delete h;
+    };
+    if (trace_id == TALP_GPU_ALL) {
+        for (auto& kv : m) drop(kv.second);
+        m.clear();
+        return;
+    }
+    auto it = m.find(trace_id);
+    if (it == m.end()) return;
+    drop(it->second);
+    m.erase(it);
+}
+
+uint64_t talp::raw_held_records(talp_gpu_ctx* c, uint64_t trace_id) {
+    auto it = c->holds.find(trace_id);
+    if (it == c->holds.end()) return 0;
+    uint64_t t = 0;
+    for (uint64_t v : it->second->cnt) t += v;
+    return t;
+}
+
+extern "C" {
+
+talp_gpu_status talp_gpu_raw_held(talp_gpu_ctx* c, uint64_t trace_id, uint64_t* out_host) {
+    if (!c || !out_host) return fail(TALP_GPU_EINVAL, "null argument");
+    *out_host = raw_held_records(c, trace_id);
+    return TALP_GPU_OK;
+}
+
 talp_gpu_status talp_gpu_ingest_raw(talp_gpu_ctx* c, const talp_gpu_raw_batch* rb, size_t nb, void* stream_) {
     if (!c) return fail(TALP_GPU_EINVAL, "null context");
     if (nb == 0) return TALP_GPU_OK;
     if (!rb) return fail(TALP_GPU_EINVAL, "null batches");
     const bool dev_ptrs = (rb[0].flags & TALP_GPU_DEVICE_PTRS) != 0;
-    const int tile = raw_tile_records();
-    std::vector<RawRank> ranks;
-    std::vector<RawTile> tiles;
+    const uint64_t tile = static_cast<uint64_t>(raw_tile_records());
+    auto& holds = c->holds;
+
+    // pass 1: headers, sizes and the hold state each batch continues
+    std::vector<RawHold*> hs(nb, nullptr);      // hold state read (held records prepended)
+    std::vector<bool> hb(nb, false);            // batch holds back
     std::vector<uint64_t> out_base(nb), hbase(nb), m_of(nb);
-    uint64_t nr = 0, outn = 0, nh = 0, mtot = 0;
+    uint64_t nr = 0, outn = 0, nh = 0, mtot = 0, nt = 0, nrk = 0;
+    bool any_hold = false;
     for (size_t k = 0; k < nb; ++k) {
         const talp_gpu_raw_batch& b = rb[k];
         if ((b.flags & TALP_GPU_DEVICE_PTRS) != (rb[0].flags & TALP_GPU_DEVICE_PTRS))
             return fail(TALP_GPU_EINVAL, "raw batches mix host and device pointers");
-        if (b.flags & ~(TALP_GPU_DEVICE_PTRS | TALP_GPU_APPEND)) return fail(TALP_GPU_EINVAL, "raw: unknown flags");
+        if (b.flags & ~(TALP_GPU_DEVICE_PTRS | TALP_GPU_APPEND | TALP_GPU_HOLD_BACK))
+            return fail(TALP_GPU_EINVAL, "raw: unknown flags");
         if (b.n_ranks == 0 || !b.devices_per_rank || !b.raw_off || !b.host_off)
             return fail(TALP_GPU_EINVAL, "raw: bad header");
         if (b.raw_off[0] != 0) return fail(TALP_GPU_EINVAL, "raw: raw_off[0] != 0");
+        for (size_t j = 0; j < k; ++j)
+            if (rb[j].trace_id == b.trace_id) return fail(TALP_GPU_EINVAL, "raw: a trace twice in one call");
+        hb[k] = (b.flags & TALP_GPU_HOLD_BACK) != 0;
+        if (hb[k] && !b.stream_mask) return fail(TALP_GPU_EINVAL, "raw: hold-back needs the stream masks");
+        auto it = holds.find(b.trace_id);
+        if (it != holds.end() && (b.flags & TALP_GPU_APPEND)) {
+            RawHold* h = it->second;
+            if (h->n != b.n_ranks || !std::equal(h->dpr.begin(), h->dpr.end(), b.devices_per_rank))
+                return fail(TALP_GPU_EINVAL, "raw: shape differs from the held records' trace");
+            hs[k] = h;
+        }
         outn = align_up(outn, 16);
         out_base[k] = outn;
-        uint64_t m = 0;
+        uint64_t m = 0, n_in = 0;
         for (uint32_t i = 0; i < b.n_ranks; ++i) {
             const uint32_t D = b.devices_per_rank[i];
             if (D > static_cast<uint32_t>(kRawMaxDevices))
                 return fail(TALP_GPU_EINVAL, "raw: more than 8 devices in a rank");
             if (b.raw_off[i + 1] < b.raw_off[i]) return fail(TALP_GPU_EINVAL, "raw: raw_off decreases");
             const uint64_t n = b.raw_off[i + 1] - b.raw_off[i];
+            const uint64_t held = hs[k] ? hs[k]->cnt[i] : 0;
             if (n && D == 0) return fail(TALP_GPU_EINVAL, "raw: records of a rank without devices");
-            RawRank r;
-            r.rec0 = nr + b.raw_off[i];
-            r.out0 = outn + b.raw_off[i];
-            r.dev0 = static_cast<uint32_t>(mtot + m);
-            r.D = D;
-            r.tile0 = static_cast<uint32_t>(tiles.size());
-            for (uint64_t o = 0; o < n; o += tile)
-                tiles.push_back(RawTile{r.rec0 + o, static_cast<uint32_t>(std::min<uint64_t>(tile, n - o)),
-                                        static_cast<uint32_t>(ranks.size())});
-            r.ntile = static_cast<uint32_t>(tiles.size()) - r.tile0;
-            ranks.push_back(r);
+            if (hb[k] && n + held >= (1ull << 32)) return fail(TALP_GPU_EINVAL, "raw: 2^32 records in a held rank");
+            nt += (held + tile - 1) / tile + (n + tile - 1) / tile;
+            n_in += n + held;
             m += D;
         }
         m_of[k] = m;
         mtot += m;
+        nrk += b.n_ranks;
         const uint64_t n = b.raw_off[b.n_ranks];
         if (n && (!b.raw_se || !b.raw_tag || !b.raw_dev)) return fail(TALP_GPU_EINVAL, "raw: null record arrays");
+        if (dev_ptrs && (reinterpret_cast<uintptr_t>(b.raw_se) & 15u))
+            return fail(TALP_GPU_EINVAL, "raw: raw_se not 16-byte aligned");
         nr += n;
-        outn += n;
+        outn += n_in;
         nh = align_up(nh, 16);
         hbase[k] = nh;
         nh += b.host_off[b.n_ranks];
+        any_hold = any_hold || hb[k];
     }
-    if (tiles.size() > 0xFFFFFFFFull || mtot > 0xFFFFFFFFull) return fail(TALP_GPU_EINVAL, "raw: too large");
-    const size_t nt = tiles.size(), nrk = ranks.size();
+    if (nt > 0xFFFFFFFFull || mtot > 0xFFFFFFFFull || nrk > 0xFFFFFFFFull)
+        return fail(TALP_GPU_EINVAL, "raw: too large");
 
-    // device buffer: [input staging][host staging][lanes][tables][hist][offs][counts][status]
+    // device buffer: [input staging][host staging][lanes][fold lanes][tables][fold bases][hist][offs][moves]
+    //                [device counts][fold counts][hold counts][status]
     size_t o = 0;
     const size_t o_rse = o; o = align_up(o + (dev_ptrs ? 0 : 16 * nr), 256);
     const size_t o_rtag = o; o = align_up(o + (dev_ptrs ? 0 : nr), 256);
@@ -1021,34 +1103,121 @@ talp_gpu_status talp_gpu_ingest_raw(talp_gpu_ctx* c, const talp_gpu_raw_batch* r
     const size_t o_hst = o; o = align_up(o + (dev_ptrs ? 0 : nh + 16), 256);
     const size_t o_lse = o; o = align_up(o + 16 * outn, 256);
     const size_t o_ltag = o; o = align_up(o + outn + 16, 256);
+    const size_t o_fse = o; o = align_up(o + (any_hold ? 16 * outn : 0), 256);
+    const size_t o_ftag = o; o = align_up(o + (any_hold ? outn + 16 : 0), 256);
     const size_t o_ranks = o; o = align_up(o + sizeof(RawRank) * nrk, 256);
     const size_t o_tiles = o; o = align_up(o + sizeof(RawTile) * nt, 256);
-    const size_t o_hist = o; o = align_up(o + 4ull * kRawMaxDevices * 32 * nt, 256);
-    const size_t o_offs = o; o = align_up(o + 8ull * kRawMaxDevices * 32 * nt, 256);
+    const size_t tab_bytes = o - o_ranks;
+    const size_t o_fbase = o; o = align_up(o + 8 * nrk, 256);
+    const size_t o_hist = o; o = align_up(o + 4ull * kRawBuckets * nt, 256);
+    const size_t o_offs = o; o = align_up(o + 8ull * kRawBuckets * nt, 256);
+    const size_t o_moves = o; o = align_up(o + (any_hold ? sizeof(RawMove) * kRawBuckets * nrk : 0), 256);
     const size_t o_cnt = o; o = align_up(o + 8 * mtot, 256);
+    const size_t o_fcnt = o; o = align_up(o + 8 * mtot, 256);
+    const size_t o_hcnt = o; o = align_up(o + 8 * nrk, 256);
     const size_t o_st = o; o += 256;
-    const size_t tab_bytes = o_hist - o_ranks;
+    const size_t down_bytes = o - o_cnt;
 
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
     TALP_CUDA(cudaSetDevice(c->device));
     if (c->raw_used) TALP_CUDA(cudaStreamWaitEvent(stream, c->ev_raw, 0));
     TALP_TRY(grow(c, c->raw, o));
     char* R = static_cast<char*>(c->raw.p);
+
+    // hold states: new ones for hold-back batches without one, and the
+    // buffer the held records of this call go to
+    std::vector<RawHold*> hn(nb, nullptr);
+    for (size_t k = 0; k < nb; ++k) {
+        if (!hb[k]) continue;
+        const talp_gpu_raw_batch& b = rb[k];
+        RawHold* h = hs[k];
+        if (!h) {
+            raw_hold_drop(c, b.trace_id);
+            h = new RawHold();
+            h->n = b.n_ranks;
+            h->dpr.assign(b.devices_per_rank, b.devices_per_rank + b.n_ranks);
+            h->off.assign(b.n_ranks, 0);
+            h->cnt.assign(b.n_ranks, 0);
+            talp_gpu_status st = grow(c, h->ls, sizeof(int64_t) * kRawBuckets * b.n_ranks);
+            if (st != TALP_GPU_OK) {
+                delete h;
+                return st;
+            }
+            holds[b.trace_id] = h;
+        }
+        h->smask.assign(b.stream_mask, b.stream_mask + b.n_ranks * kRawMaxDevices);
+        uint64_t n_in = b.raw_off[b.n_ranks];
+        for (uint64_t v : h->cnt) n_in += v;
+        TALP_TRY(grow(c, h->buf[1 - h->cur], hold_bytes(n_in)));
+        h->o_tag[1 - h->cur] = hold_tag_at(n_in);
+        h->o_dev[1 - h->cur] = hold_dev_at(n_in);
+        hn[k] = h;
+    }
+
+    // pass 2: ranks and tiles (held records first, then the new ones)
+    std::vector<RawRank> ranks;
+    std::vector<RawTile> tiles;
+    ranks.reserve(nrk);
+    tiles.reserve(nt);
+    std::vector<std::vector<uint64_t>> slot(nb);   // hold-back: each rank's slot in the next held buffer
+    {
+        uint64_t p = 0, g0 = 0;
+        for (size_t k = 0; k < nb; ++k) {
+            const talp_gpu_raw_batch& b = rb[k];
+            const int64_t* se = dev_ptrs ? b.raw_se : reinterpret_cast<const int64_t*>(R + o_rse) + 2 * p;
+            const uint8_t* tg = dev_ptrs ? b.raw_tag : reinterpret_cast<const uint8_t*>(R + o_rtag) + p;
+            const uint8_t* dv = dev_ptrs ? b.raw_dev : reinterpret_cast<const uint8_t*>(R + o_rdev) + p;
+            RawHold* h = hs[k];     // held records read
+            RawHold* hx = hn[k];    // held records written
+            const char* hbuf = h ? static_cast<const char*>(h->buf[h->cur].p) : nullptr;
+            char* nbuf = hx ? static_cast<char*>(hx->buf[1 - hx->cur].p) : nullptr;
+            slot[k].assign(b.n_ranks, 0);
+            uint64_t rel = 0;
+            for (uint32_t i = 0; i < b.n_ranks; ++i) {
+                RawRank r;
+                memset(&r, 0, sizeof(r));
+                r.out0 = out_base[k] + rel;
+                r.dev0 = static_cast<uint32_t>(g0);
+                r.D = b.devices_per_rank[i];
+                r.tile0 = static_cast<uint32_t>(tiles.size());
+                const uint32_t ri = static_cast<uint32_t>(ranks.size());
+                const uint64_t held = h ? h->cnt[i] : 0;
+                for (uint64_t q = 0; q < held; q += tile)
+                    tiles.push_back(RawTile{reinterpret_cast<const int64_t*>(hbuf) + 2 * (h->off[i] + q),
+                                            reinterpret_cast<const uint8_t*>(hbuf + h->o_tag[h->cur]) + h->off[i] + q,
+                                            reinterpret_cast<const uint8_t*>(hbuf + h->o_dev[h->cur]) + h->off[i] + q,
+                                            r.out0 + q, static_cast<uint32_t>(std::min<uint64_t>(tile, held - q)),
+                                            ri});
+                const uint64_t n = b.raw_off[i + 1] - b.raw_off[i];
+                for (uint64_t q = 0; q < n; q += tile)
+                    tiles.push_back(RawTile{se + 2 * (b.raw_off[i] + q), tg + b.raw_off[i] + q, dv + b.raw_off[i] + q,
+                                            r.out0 + held + q, static_cast<uint32_t>(std::min<uint64_t>(tile, n - q)),
+                                            ri});
+                r.ntile = static_cast<uint32_t>(tiles.size()) - r.tile0;
+                if (hx) {
+                    r.last_start = static_cast<int64_t*>(hx->ls.p) + static_cast<uint64_t>(kRawBuckets) * i;
+                    r.hold_se = reinterpret_cast<int64_t*>(nbuf) + 2 * rel;
+                    r.hold_tag = reinterpret_cast<uint8_t*>(nbuf + hx->o_tag[1 - hx->cur]) + rel;
+                    r.hold_dev = reinterpret_cast<uint8_t*>(nbuf + hx->o_dev[1 - hx->cur]) + rel;
+                    for (int d = 0; d < kRawMaxDevices; ++d) r.smask[d] = hx->smask[i * kRawMaxDevices + d];
+                    r.fresh = hx->fresh ? 1u : 0u;
+                    slot[k][i] = rel;
+                }
+                ranks.push_back(r);
+                rel += held + n;
+                g0 += r.D;
+            }
+            p += b.raw_off[b.n_ranks];
+        }
+    }
+
     TALP_CUDA(cudaEventSynchronize(c->ev_up));
-    TALP_TRY(grow_pinned(c->up, tab_bytes));
+    TALP_TRY(grow_pinned(c->up, tab_bytes + 8 * nrk));
     memcpy(c->up.p, ranks.data(), sizeof(RawRank) * nrk);
     if (nt) memcpy(static_cast<char*>(c->up.p) + (o_tiles - o_ranks), tiles.data(), sizeof(RawTile) * nt);
     TALP_CUDA(cudaMemcpyAsync(R + o_ranks, c->up.p, tab_bytes, cudaMemcpyHostToDevice, stream));
     TALP_CUDA(cudaEventRecord(c->ev_up, stream));
-    const int64_t* rse;
-    const uint8_t *rtag, *rdev;
-    if (dev_ptrs) {
-        if (nb != 1) return fail(TALP_GPU_EINVAL, "raw: device pointers take one batch per call");
-        rse = rb[0].raw_se;
-        rtag = rb[0].raw_tag;
-        rdev = rb[0].raw_dev;
-        if (reinterpret_cast<uintptr_t>(rse) & 15u) return fail(TALP_GPU_EINVAL, "raw: raw_se not 16-byte aligned");
-    } else {
+    if (!dev_ptrs) {
         uint64_t p = 0;
         for (size_t k = 0; k < nb; ++k) {
             const uint64_t n = rb[k].raw_off[rb[k].n_ranks];
@@ -1066,39 +1235,57 @@ talp_gpu_status talp_gpu_ingest_raw(talp_gpu_ctx* c, const talp_gpu_raw_batch* r
             }
             p += n;
         }
-        rse = reinterpret_cast<const int64_t*>(R + o_rse);
-        rtag = reinterpret_cast<const uint8_t*>(R + o_rtag);
-        rdev = reinterpret_cast<const uint8_t*>(R + o_rdev);
     }
     TALP_CUDA(cudaMemsetAsync(R + o_st, 0, 16, stream));
-    const int grid = static_cast<int>(std::max<size_t>(1, std::min<size_t>(nt, static_cast<size_t>(c->num_sms) * 8)));
-    TALP_CUDA(launch_raw_count(rdev, rtag, reinterpret_cast<const RawTile*>(R + o_tiles), static_cast<uint32_t>(nt),
-                               reinterpret_cast<const RawRank*>(R + o_ranks), static_cast<uint32_t>(nrk),
-                               reinterpret_cast<uint32_t*>(R + o_hist), reinterpret_cast<uint64_t*>(R + o_offs),
-                               reinterpret_cast<uint64_t*>(R + o_cnt), reinterpret_cast<uint32_t*>(R + o_st), grid,
-                               stream));
-    TALP_CUDA(launch_raw_scatter(rse, rtag, rdev, reinterpret_cast<const RawTile*>(R + o_tiles),
-                                 static_cast<uint32_t>(nt), reinterpret_cast<const RawRank*>(R + o_ranks),
-                                 reinterpret_cast<const uint64_t*>(R + o_offs), reinterpret_cast<int64_t*>(R + o_lse),
-                                 reinterpret_cast<uint8_t*>(R + o_ltag), grid, stream));
-    c->kernel_launches += nt ? 3 : 0;
+    const int grid = static_cast<int>(std::max<uint64_t>(1, std::min<uint64_t>(nt, static_cast<uint64_t>(c->num_sms) * 8)));
+    const RawTile* dtiles = reinterpret_cast<const RawTile*>(R + o_tiles);
+    const RawRank* dranks = reinterpret_cast<const RawRank*>(R + o_ranks);
+    RawMove* dmoves = any_hold ? reinterpret_cast<RawMove*>(R + o_moves) : nullptr;
+    uint32_t* dst = reinterpret_cast<uint32_t*>(R + o_st);
+    TALP_CUDA(launch_raw_count(dtiles, static_cast<uint32_t>(nt), dranks, static_cast<uint32_t>(nrk),
+                               reinterpret_cast<uint32_t*>(R + o_hist), reinterpret_cast<uint64_t*>(R + o_offs), dmoves,
+                               reinterpret_cast<uint64_t*>(R + o_cnt), dst, grid, stream));
+    TALP_CUDA(launch_raw_scatter(dtiles, static_cast<uint32_t>(nt), dranks, reinterpret_cast<const uint64_t*>(R + o_offs),
+                                 reinterpret_cast<int64_t*>(R + o_lse), reinterpret_cast<uint8_t*>(R + o_ltag), grid,
+                                 stream));
+    c->kernel_launches += (nt ? 2 : 0) + (nrk ? 1 : 0);
+    if (any_hold) {
+        TALP_CUDA(launch_raw_hold(dranks, static_cast<uint32_t>(nrk), reinterpret_cast<const int64_t*>(R + o_lse), dmoves,
+                                  reinterpret_cast<uint64_t*>(R + o_fcnt), reinterpret_cast<uint64_t*>(R + o_hcnt), dst,
+                                  stream));
+        ++c->kernel_launches;
+    }
     // the ingest needs each device's record count on the host
-    TALP_TRY(grow_pinned(c->down, 8 * mtot + 16));
-    TALP_CUDA(cudaMemcpyAsync(c->down.p, R + o_cnt, 8 * mtot, cudaMemcpyDeviceToHost, stream));
-    TALP_CUDA(cudaMemcpyAsync(static_cast<char*>(c->down.p) + 8 * mtot, R + o_st, 4, cudaMemcpyDeviceToHost, stream));
+    TALP_TRY(grow_pinned(c->down, down_bytes));
+    TALP_CUDA(cudaMemcpyAsync(c->down.p, R + o_cnt, down_bytes, cudaMemcpyDeviceToHost, stream));
     TALP_CUDA(cudaStreamSynchronize(stream));
-    const uint64_t* cnt = static_cast<const uint64_t*>(c->down.p);
+    const char* D = static_cast<const char*>(c->down.p);
+    const uint64_t* cnt = reinterpret_cast<const uint64_t*>(D);
+    const uint64_t* fcnt = reinterpret_cast<const uint64_t*>(D + (o_fcnt - o_cnt));
+    const uint64_t* hcnt = reinterpret_cast<const uint64_t*>(D + (o_hcnt - o_cnt));
     uint32_t status = 0;
-    memcpy(&status, static_cast<char*>(c->down.p) + 8 * mtot, 4);
-    if (status) return fail(TALP_GPU_EINVAL, "raw: a record names a device its rank does not have");
+    memcpy(&status, D + (o_st - o_cnt), 4);
+    if (status) {
+        for (size_t k = 0; k < nb; ++k)
+            if (hb[k]) raw_hold_drop(c, rb[k].trace_id);
+        if (status & 1u) return fail(TALP_GPU_EINVAL, "raw: a record names a device its rank does not have");
+        return fail(TALP_GPU_EINVAL, "raw: a record on a stream its device's stream mask does not declare");
+    }
 
     std::vector<std::vector<uint64_t>> dev_off(nb);
     std::vector<talp_gpu_trace_batch> tb(nb);
-    uint64_t g = 0;
+    uint64_t* fbase = static_cast<uint64_t*>(c->up.p) + tab_bytes / 8;   // the table upload has completed
+    uint64_t g = 0, ri = 0;
     for (size_t k = 0; k < nb; ++k) {
         const talp_gpu_raw_batch& b = rb[k];
+        const uint64_t* cn = hb[k] ? fcnt : cnt;
         dev_off[k].assign(m_of[k] + 1, 0);
-        for (uint64_t d = 0; d < m_of[k]; ++d, ++g) dev_off[k][d + 1] = dev_off[k][d] + cnt[g];
+        for (uint64_t d = 0; d < m_of[k]; ++d, ++g) dev_off[k][d + 1] = dev_off[k][d] + cn[g];
+        uint64_t dl = 0;   // first device of rank i within the batch
+        for (uint32_t i = 0; i < b.n_ranks; ++i, ++ri) {
+            fbase[ri] = out_base[k] + dev_off[k][dl];
+            dl += b.devices_per_rank[i];
+        }
         talp_gpu_trace_batch& t = tb[k];
         memset(&t, 0, sizeof(t));
         t.trace_id = b.trace_id;
@@ -1110,11 +1297,41 @@ talp_gpu_status talp_gpu_ingest_raw(talp_gpu_ctx* c, const talp_gpu_raw_batch* r
         t.host_se = dev_ptrs ? b.host_se : reinterpret_cast<const int64_t*>(R + o_hse) + 2 * hbase[k];
         t.host_state = dev_ptrs ? b.host_state : reinterpret_cast<const uint8_t*>(R + o_hst) + hbase[k];
         t.host_off = b.host_off;
-        t.dev_se = reinterpret_cast<const int64_t*>(R + o_lse) + 2 * out_base[k];
-        t.dev_tag = reinterpret_cast<const uint8_t*>(R + o_ltag) + out_base[k];
+        const size_t lo = hb[k] ? o_fse : o_lse, lt = hb[k] ? o_ftag : o_ltag;
+        t.dev_se = reinterpret_cast<const int64_t*>(R + lo) + 2 * out_base[k];
+        t.dev_tag = reinterpret_cast<const uint8_t*>(R + lt) + out_base[k];
         t.dev_off = dev_off[k].data();
     }
+    if (any_hold) {
+        TALP_CUDA(cudaMemcpyAsync(R + o_fbase, fbase, 8 * nrk, cudaMemcpyHostToDevice, stream));
+        TALP_CUDA(cudaEventRecord(c->ev_up, stream));
+        TALP_CUDA(launch_raw_move(dtiles, static_cast<uint32_t>(nt), dranks, dmoves,
+                                  reinterpret_cast<const uint64_t*>(R + o_fbase),
+                                  reinterpret_cast<const int64_t*>(R + o_lse), reinterpret_cast<const uint8_t*>(R + o_ltag),
+                                  reinterpret_cast<int64_t*>(R + o_fse), reinterpret_cast<uint8_t*>(R + o_ftag), grid,
+                                  stream));
+        ++c->kernel_launches;
+        ri = 0;
+        for (size_t k = 0; k < nb; ++k) {
+            if (!hb[k]) {
+                ri += rb[k].n_ranks;
+                continue;
+            }
+            RawHold* h = hn[k];
+            for (uint32_t i = 0; i < rb[k].n_ranks; ++i, ++ri) {
+                h->off[i] = slot[k][i];
+                h->cnt[i] = hcnt[ri];
+            }
+            h->cur = 1 - h->cur;
+            h->fresh = false;
+        }
+    }
+    // a batch without hold-back folded every held record: its hold state ends
+    for (size_t k = 0; k < nb; ++k)
+        if (!hb[k] && holds.count(rb[k].trace_id)) raw_hold_drop(c, rb[k].trace_id);
+    c->raw_inner = true;
     const talp_gpu_status st = talp_gpu_ingest_events(c, tb.data(), nb, stream_);
+    c->raw_inner = false;
     TALP_CUDA(cudaEventRecord(c->ev_raw, stream));
     c->raw_used = true;
     return st;
@@ -1276,6 +1493,7 @@ talp_gpu_status talp_gpu_reset(talp_gpu_ctx* c, uint64_t trace_id) {
     if (trace_id == TALP_GPU_ALL) {
         for (auto& kv : c->traces)
             if (kv.second->plan_refs) return fail(TALP_GPU_EBUSY, "a plan uses one of the traces");
+        raw_hold_drop(c, TALP_GPU_ALL);
         for (auto& kv : c->traces) free_trace(c, kv.second);
         c->traces.clear();
         return TALP_GPU_OK;
@@ -1283,6 +1501,7 @@ talp_gpu_status talp_gpu_reset(talp_gpu_ctx* c, uint64_t trace_id) {
     auto it = c->traces.find(trace_id);
     if (it == c->traces.end()) return fail(TALP_GPU_ENOTFOUND, "unknown trace id");
     if (it->second->plan_refs) return fail(TALP_GPU_EBUSY, "a plan uses this trace");
+    raw_hold_drop(c, trace_id);
     free_trace(c, it->second);
     c->traces.erase(it);
     return TALP_GPU_OK;

@@ -136,20 +136,38 @@ struct ConcChunk {
     uint32_t dev;              // device index
 };
 
-// Raw activity-record adapter: per rank its input records and output lane
-// range, per tile of input records its rank.
+// Raw activity-record adapter: per rank its lane range and hold-back state,
+// per tile of input records its source arrays and rank.
 constexpr int kRawMaxDevices = 8;   // local devices per rank (buckets: device x stream)
+constexpr int kRawBuckets = kRawMaxDevices * 32;
 struct RawRank {
-    uint64_t rec0;             // first input record
-    uint64_t out0;             // first output lane record (the rank's devices in order)
+    uint64_t out0;             // first lane record (the rank's devices in order)
     uint32_t dev0;             // global index of its first device
     uint32_t D;                // its devices
     uint32_t tile0, ntile;     // its input tiles
+    int64_t* last_start;       // hold-back: [D][32] last start seen per (device, stream); null: fold all
+    int64_t* hold_se;          // hold-back: where its held records go (rows, tags, devices)
+    uint8_t* hold_tag;
+    uint8_t* hold_dev;
+    uint32_t smask[kRawMaxDevices];   // hold-back: declared streams of each device
+    uint32_t fresh;            // hold-back: last_start not written yet (every stream unseen)
+    uint32_t pad;
 };
 struct RawTile {
-    uint64_t rec0;             // first input record
+    const int64_t* se;         // the tile's records (rows, tags, device indexes)
+    const uint8_t* tag;
+    const uint8_t* dev;
+    uint64_t lpos;             // lane position of its first record (a rank's tiles cover its lanes in order)
     uint32_t n;                // records
     uint32_t rank;             // global rank index
+};
+// per (rank, bucket): its scattered records [src, src + nfold + nhold), the
+// final prefix going to fold_dst and the rest to hold_dst (both relative to
+// the rank's fold and hold bases)
+struct RawMove {
+    uint64_t src;
+    uint32_t fold_dst, hold_dst;
+    uint32_t nfold, nhold;
 };
 
 // ---------------------------------------------------------------- helpers

@@ -41,12 +41,16 @@ cudaError_t launch_finalize(const FinalizeJob* jobs, uint32_t n_jobs, cudaStream
 cudaError_t launch_concurrency(const int64_t* se, const uint8_t* tag, const ConcDev* devs, uint32_t n_dev,
                                const ConcChunk* chunks, uint32_t n_chunks, int64_t* top, int64_t* in, int64_t* out,
                                uint32_t* status, cudaStream_t stream);
-cudaError_t launch_raw_count(const uint8_t* rdev, const uint8_t* rtag, const RawTile* tiles, uint32_t n_tiles,
-                             const RawRank* ranks, uint32_t n_ranks, uint32_t* hist, uint64_t* offs,
-                             uint64_t* dev_count, uint32_t* status, int grid, cudaStream_t stream);
-cudaError_t launch_raw_scatter(const int64_t* rse, const uint8_t* rtag, const uint8_t* rdev, const RawTile* tiles,
-                               uint32_t n_tiles, const RawRank* ranks, const uint64_t* offs, int64_t* lse,
-                               uint8_t* ltag, int grid, cudaStream_t stream);
+cudaError_t launch_raw_count(const RawTile* tiles, uint32_t n_tiles, const RawRank* ranks, uint32_t n_ranks,
+                             uint32_t* hist, uint64_t* offs, RawMove* moves, uint64_t* dev_count, uint32_t* status,
+                             int grid, cudaStream_t stream);
+cudaError_t launch_raw_scatter(const RawTile* tiles, uint32_t n_tiles, const RawRank* ranks, const uint64_t* offs,
+                               int64_t* lse, uint8_t* ltag, int grid, cudaStream_t stream);
+cudaError_t launch_raw_hold(const RawRank* ranks, uint32_t n_ranks, const int64_t* lse, RawMove* moves,
+                            uint64_t* fold_count, uint64_t* hold_count, uint32_t* status, cudaStream_t stream);
+cudaError_t launch_raw_move(const RawTile* tiles, uint32_t n_tiles, const RawRank* ranks, const RawMove* moves,
+                            const uint64_t* fold_base, const int64_t* lse, const uint8_t* ltag, int64_t* fse,
+                            uint8_t* ftag, int grid, cudaStream_t stream);
 int raw_tile_records();
 cudaError_t launch_scalability(const MetricsOut* runs, uint32_t n_runs, uint32_t ref, int weak, ScaleOut* out,
                                cudaStream_t stream);

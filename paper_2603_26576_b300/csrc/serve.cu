@@ -146,6 +146,7 @@ struct talp_gpu_server {
     bool stop_done = false;
 
     std::thread th_serve, th_done;
+    bool held = false;                 // counted as a user of the context
 
     // statistics (under mu)
     uint64_t slices_submitted = 0, slices_folded = 0, records_folded = 0, waves = 0, queries_answered = 0,
@@ -511,6 +512,8 @@ talp_gpu_status talp_gpu_server_create(talp_gpu_ctx* ctx, const talp_gpu_server_
     }
     s->th_serve = std::thread(serve_loop, s);
     s->th_done = std::thread(done_loop, s);
+    ctx_hold(ctx, +1);
+    s->held = true;
     *out = s;
     return TALP_GPU_OK;
 }
@@ -736,6 +739,7 @@ talp_gpu_status talp_gpu_server_destroy(talp_gpu_server* s) {
     }
     if (s->s_fold) cudaStreamDestroy(s->s_fold);
     if (s->s_query) cudaStreamDestroy(s->s_query);
+    if (s->held) ctx_hold(s->ctx, -1);
     delete s;
     return TALP_GPU_OK;
 }

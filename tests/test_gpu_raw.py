@@ -77,3 +77,156 @@ def test_errors(ctx):
     ctx.ingest_raw([r])                  # the context is still usable
     assert_trace_equal(ctx, t, "raw-after-errors")
     ctx.reset()
+
+
+# ------------------------------------------------------------------ hold-back
+
+def _delivered(parts, upto):
+    """Per rank, the raw records of parts 0..upto in delivery order."""
+    n = parts[0].trace.n_ranks
+    out = []
+    for i in range(n):
+        se, tag, dev = [], [], []
+        for p in parts[:upto + 1]:
+            a, b = int(p.raw_off[i]), int(p.raw_off[i + 1])
+            se.append(p.raw_se[a:b])
+            tag.append(p.raw_tag[a:b])
+            dev.append(p.raw_dev[a:b])
+        out.append((np.concatenate(se), np.concatenate(tag), np.concatenate(dev)))
+    return out
+
+
+def _folded_trace(t, parts, upto, flush=False):
+    """The trace restricted to the records folded after delivery `upto`:
+    per device, the delivered records starting at or before the minimum,
+    over the device's declared streams, of each stream's last delivered
+    start (a declared stream with nothing delivered: nothing folds); with
+    flush, every delivered record."""
+    dpr = np.asarray(t.devices_per_rank, np.int64)
+    masks = parts[0].stream_mask
+    se_all, tag_all, counts = [], [], []
+    for i, (se, tag, dev) in enumerate(_delivered(parts, upto)):
+        for d in range(int(dpr[i])):
+            sel = dev == d
+            s, g = se[sel], tag[sel]
+            if not flush:
+                W = np.iinfo(np.int64).max
+                for st in range(32):
+                    if (int(masks[i, d]) >> st) & 1:
+                        on = (g & 31) == st
+                        W = min(W, int(s[on, 0].max()) if on.any() else np.iinfo(np.int64).min)
+                keep = s[:, 0] <= W
+                s, g = s[keep], g[keep]
+            o = np.lexsort((s[:, 1], s[:, 0]))
+            se_all.append(s[o])
+            tag_all.append(g[o])
+            counts.append(s.shape[0])
+    off = np.zeros(len(counts) + 1, np.uint64)
+    off[1:] = np.cumsum(counts)
+    return tg.Trace(trace_id=t.trace_id, n_ranks=t.n_ranks, devices_per_rank=t.devices_per_rank,
+                    region_window=t.region_window, host_se=t.host_se, host_state=t.host_state, host_off=t.host_off,
+                    dev_se=np.concatenate(se_all) if se_all else np.zeros((0, 2), np.int64),
+                    dev_tag=np.concatenate(tag_all) if tag_all else np.zeros(0, np.uint8), dev_off=off)
+
+
+def _hold_back_run(ctx, t, n_calls, seed, arrays=False):
+    import torch
+    import paper_2603_26576_b300 as P
+    parts = tg.raw_deliveries(tg.to_raw(t), n_calls, seed=seed)
+    for j, p in enumerate(parts):
+        arr = None
+        if arrays:
+            arr = [dict(host_se=torch.from_numpy(p.trace.host_se).cuda(),
+                        host_state=torch.from_numpy(p.trace.host_state).cuda(),
+                        raw_se=torch.from_numpy(p.raw_se).cuda(), raw_tag=torch.from_numpy(p.raw_tag).cuda(),
+                        raw_dev=torch.from_numpy(p.raw_dev).cuda())]
+        ctx.ingest_raw([p], flags=P.TALP_GPU_HOLD_BACK | (P.TALP_GPU_APPEND if j else 0), arrays=arr)
+        f = _folded_trace(t, parts, j)
+        delivered = sum(int(q.raw_off[-1]) for q in parts[:j + 1])
+        assert ctx.raw_held(t.trace_id) == delivered - int(f.dev_off[-1]), ("held", seed, j)
+        for r in range(t.n_regions):
+            h, d = ctx.unit_sums(t.trace_id, r)
+            np.testing.assert_array_equal(d, oracle.device_unions(f, r), err_msg=str(("hold", seed, j, r)))
+    # flush: a call without HOLD_BACK folds every held record
+    et = tg.Trace(trace_id=t.trace_id, n_ranks=t.n_ranks, devices_per_rank=t.devices_per_rank,
+                  region_window=t.region_window, host_se=np.zeros((0, 2), np.int64), host_state=np.zeros(0, np.uint8),
+                  host_off=np.zeros(t.n_ranks + 1, np.uint64), dev_se=np.zeros((0, 2), np.int64),
+                  dev_tag=np.zeros(0, np.uint8), dev_off=np.zeros(t.m_devices + 1, np.uint64))
+    empty = tg.RawTrace(et, np.zeros((0, 2), np.int64), np.zeros(0, np.uint8), np.zeros(0, np.uint8),
+                        np.zeros(t.n_ranks + 1, np.uint64))
+    ctx.ingest_raw([empty], flags=P.TALP_GPU_APPEND)
+    assert ctx.raw_held(t.trace_id) == 0
+    assert_trace_equal(ctx, t, ("hold-flush", seed))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_hold_back_streamed_buffers(ctx, seed):
+    law = tg.DeviceLaw("lognormal", (0, 1, 2, 3), (4, 5), occupancy=1.6)
+    t = tg.random_trace(seed, trace_id=300 + seed, n_ranks=3, devices_per_rank=[2, 1, 3],
+                        dev_events=[5000, 3000, 7000, 1, 0, 2600], host_events=[200, 30, 9], n_regions=3, law=law)
+    _hold_back_run(ctx, t, 2 + 2 * seed, seed, arrays=(seed % 2 == 1))
+    ctx.reset()
+
+
+def test_hold_back_tiny_and_many_calls(ctx):
+    for s in range(12):
+        t = tg.tiny_trace(s, trace_id=400 + s, max_ranks=3, max_devs=3, max_events=120)
+        _hold_back_run(ctx, t, 1 + s % 7, s)
+    ctx.reset()
+
+
+def test_hold_back_with_plain_trace_in_one_call(ctx):
+    """A hold-back trace and an ordinary one in the same call, then both
+    finished; the ordinary one folds at once."""
+    import paper_2603_26576_b300 as P
+    law = tg.DeviceLaw("lognormal", (0, 1, 2), (3,), occupancy=1.2)
+    a = tg.random_trace(21, trace_id=501, n_ranks=2, devices_per_rank=2, dev_events=4000, host_events=100, law=law)
+    b = tg.random_trace(22, trace_id=502, n_ranks=2, devices_per_rank=[1, 3], dev_events=2500, host_events=50)
+    pa = tg.raw_deliveries(tg.to_raw(a), 3, seed=1)
+    pb = tg.raw_deliveries(tg.to_raw(b), 2, seed=2)
+    H, A = P.TALP_GPU_HOLD_BACK, P.TALP_GPU_APPEND
+    ctx.ingest_raw([pa[0], pb[0]], flags=[H, 0])
+    assert ctx.raw_held(b.trace_id) == 0
+    ctx.ingest_raw([pb[1], pa[1]], flags=[A, H | A])
+    ctx.ingest_raw([pa[2]], flags=A)          # last buffer, folded with the held records
+    assert ctx.raw_held(a.trace_id) == 0
+    assert_trace_equal(ctx, a, "hold-mixed-a")
+    assert_trace_equal(ctx, b, "hold-mixed-b")
+    ctx.reset()
+
+
+def test_hold_back_errors(ctx):
+    import paper_2603_26576_b300 as P
+    t = tg.random_trace(5, trace_id=600, n_ranks=2, devices_per_rank=2, dev_events=2000, host_events=40)
+    parts = tg.raw_deliveries(tg.to_raw(t), 3, seed=3)
+    nomask = tg.RawTrace(parts[0].trace, parts[0].raw_se, parts[0].raw_tag, parts[0].raw_dev, parts[0].raw_off)
+    with pytest.raises(P.TalpGpuError) as e:          # hold-back needs the stream masks
+        ctx.ingest_raw([nomask], flags=P.TALP_GPU_HOLD_BACK)
+    assert e.value.status == EINVAL
+    ctx.ingest_raw([parts[0]], flags=P.TALP_GPU_HOLD_BACK)
+    held = ctx.raw_held(t.trace_id)
+    # a record on a stream its device does not declare: EINVAL, hold state dropped
+    undeclared = parts[1].stream_mask.copy()
+    i = int(np.searchsorted(parts[1].raw_off[1:], 0, side="right"))   # first rank with records
+    k0 = int(parts[1].raw_off[i])
+    undeclared[i, int(parts[1].raw_dev[k0])] &= ~np.uint32(1 << int(parts[1].raw_tag[k0] & 31))
+    bad = tg.RawTrace(parts[1].trace, parts[1].raw_se, parts[1].raw_tag, parts[1].raw_dev, parts[1].raw_off,
+                      undeclared)
+    if int(parts[1].raw_off[-1]):
+        with pytest.raises(P.TalpGpuError) as e:
+            ctx.ingest_raw([bad], flags=P.TALP_GPU_HOLD_BACK | P.TALP_GPU_APPEND)
+        assert e.value.status == EINVAL
+        assert ctx.raw_held(t.trace_id) == 0
+    assert held >= 0
+    # shape mismatch against the held records' trace
+    ctx.ingest_raw([parts[0]], flags=P.TALP_GPU_HOLD_BACK)
+    other = tg.random_trace(6, trace_id=600, n_ranks=3, devices_per_rank=1, dev_events=50, host_events=5)
+    op = tg.raw_deliveries(tg.to_raw(other), 2, seed=1)[1]
+    with pytest.raises(P.TalpGpuError) as e:
+        ctx.ingest_raw([op], flags=P.TALP_GPU_HOLD_BACK | P.TALP_GPU_APPEND)
+    assert e.value.status == EINVAL
+    # reset ends the hold state; the context stays usable
+    ctx.reset(t.trace_id)
+    assert ctx.raw_held(t.trace_id) == 0
+    _hold_back_run(ctx, t, 3, 3)
+    ctx.reset()

@@ -627,6 +627,52 @@ class RawTrace:
     raw_tag: np.ndarray      # uint8[N]
     raw_dev: np.ndarray      # uint8[N]
     raw_off: np.ndarray      # uint64[n + 1]
+    stream_mask: np.ndarray = None   # uint32[n, 8]: declared streams of each device (hold-back)
+
+
+def stream_masks(trace: Trace) -> np.ndarray:
+    """uint32[n, 8]: bit s of [i, d] set when device d of rank i has a
+    record on stream s."""
+    dpr = np.asarray(trace.devices_per_rank, np.int64)
+    cnt = np.diff(trace.dev_off.astype(np.int64))
+    g = np.repeat(np.arange(int(dpr.sum())), cnt)
+    rank = np.repeat(np.repeat(np.arange(trace.n_ranks), dpr), cnt)
+    local = g - np.concatenate([[0], np.cumsum(dpr)])[rank]
+    out = np.zeros((trace.n_ranks, 8), np.uint32)
+    np.bitwise_or.at(out, (rank, local), np.left_shift(np.uint32(1), (trace.dev_tag & 31).astype(np.uint32)))
+    return out
+
+
+def raw_deliveries(raw: RawTrace, n_calls: int, seed=7) -> list:
+    """Cut every rank's delivery sequence at random into n_calls consecutive
+    buffers; part j holds buffer j of every rank (a RawTrace whose trace
+    has the whole trace's windows, the host records in part 0 only, and no
+    device records of its own), with the trace's stream masks."""
+    t = raw.trace
+    rng = _rng(seed, t.trace_id, D_TRACE, 41)
+    masks = stream_masks(t)
+    off = raw.raw_off.astype(np.int64)
+    cuts = np.zeros((t.n_ranks, n_calls + 1), np.int64)
+    for i in range(t.n_ranks):
+        c = np.sort(rng.integers(0, off[i + 1] - off[i] + 1, size=n_calls - 1))
+        cuts[i] = np.concatenate([[0], c, [off[i + 1] - off[i]]])
+    m = int(np.asarray(t.devices_per_rank, np.int64).sum())
+    parts = []
+    for j in range(n_calls):
+        idx = np.concatenate([np.arange(off[i] + cuts[i, j], off[i] + cuts[i, j + 1]) for i in range(t.n_ranks)])
+        roff = np.zeros(t.n_ranks + 1, np.uint64)
+        roff[1:] = np.cumsum(cuts[:, j + 1] - cuts[:, j])
+        if j == 0:
+            hse, hst, hoff = t.host_se, t.host_state, t.host_off
+        else:
+            hse, hst, hoff = np.zeros((0, 2), np.int64), np.zeros(0, np.uint8), np.zeros(t.n_ranks + 1, np.uint64)
+        pt = Trace(trace_id=t.trace_id, n_ranks=t.n_ranks, devices_per_rank=t.devices_per_rank,
+                   region_window=t.region_window, host_se=hse, host_state=hst, host_off=hoff,
+                   dev_se=np.zeros((0, 2), np.int64), dev_tag=np.zeros(0, np.uint8),
+                   dev_off=np.zeros(m + 1, np.uint64), sorted_by_start=True, meta=dict(t.meta))
+        parts.append(RawTrace(pt, np.ascontiguousarray(raw.raw_se[idx]), np.ascontiguousarray(raw.raw_tag[idx]),
+                              np.ascontiguousarray(raw.raw_dev[idx]), roff, masks))
+    return parts
 
 
 def to_raw(trace: Trace) -> RawTrace:
