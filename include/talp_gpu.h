@@ -477,6 +477,16 @@ talp_gpu_status talp_gpu_server_open_job(talp_gpu_server *srv, uint64_t job_id, 
 /* Queue one time slice of a job (the batch's trace_id, n_ranks, n_regions,
  * devices_per_rank and region_window are ignored: the job's are used). */
 talp_gpu_status talp_gpu_server_submit(talp_gpu_server *srv, uint64_t job_id, const talp_gpu_trace_batch *slice);
+/* Queue one raw activity buffer of a job (talp_gpu_raw_batch; its
+ * trace_id, n_ranks, n_regions, devices_per_rank and region_window are
+ * ignored: the job's are used; at most 8 devices per rank).  Flags:
+ * TALP_GPU_HOLD_BACK only.  With it, the wave folds the records up to each
+ * device's watermark and holds the rest back on the GPU (stream_mask, [n][8],
+ * declares the streams and is kept by the job); without it, the buffer and
+ * every held record of the job are folded.  A query answers over the folded
+ * records.  Records per buffer are limited by max_slice_records; the record
+ * arrays are host memory, copied during the call. */
+talp_gpu_status talp_gpu_server_submit_raw(talp_gpu_server *srv, uint64_t job_id, const talp_gpu_raw_batch *buf);
 /* Metrics of one region (or TALP_GPU_ALL_REGIONS: out_host[n_regions]);
  * blocks until answered.  EINVAL when the job's records were invalid. */
 talp_gpu_status talp_gpu_server_query(talp_gpu_server *srv, uint64_t job_id, uint32_t region,

@@ -27,7 +27,7 @@ EXPORTED_SYMBOLS = (
     "talp_gpu_unit_sums",
     "talp_gpu_reset", "talp_gpu_memory", "talp_gpu_profile", "talp_gpu_profile_read", "talp_gpu_reduce_noalloc",
     "talp_gpu_plan_create", "talp_gpu_plan_launch", "talp_gpu_plan_metrics", "talp_gpu_plan_info",
-    "talp_gpu_plan_destroy", "talp_gpu_server_create", "talp_gpu_server_open_job", "talp_gpu_server_submit",
+    "talp_gpu_plan_destroy", "talp_gpu_server_create", "talp_gpu_server_open_job", "talp_gpu_server_submit", "talp_gpu_server_submit_raw",
     "talp_gpu_server_query", "talp_gpu_server_drain", "talp_gpu_server_close_job", "talp_gpu_server_info",
     "talp_gpu_server_destroy", "talp_gpu_last_error",
 )
@@ -173,6 +173,7 @@ def load_library():
                                    I32),
         "talp_gpu_server_open_job": ([P, U64, U32, P, U32, P], I32),
         "talp_gpu_server_submit": ([P, U64, ctypes.POINTER(talp_gpu_trace_batch)], I32),
+        "talp_gpu_server_submit_raw": ([P, U64, ctypes.POINTER(talp_gpu_raw_batch)], I32),
         "talp_gpu_server_query": ([P, U64, U32, ctypes.POINTER(talp_gpu_metrics)], I32),
         "talp_gpu_server_drain": ([P], I32),
         "talp_gpu_server_close_job": ([P, U64], I32),
@@ -438,6 +439,13 @@ def talp_gpu_server_open_job(srv, job_id, devices_per_rank, region_window, check
 
 def talp_gpu_server_submit(srv, job_id, batch, check=True):
     st = load_library().talp_gpu_server_submit(srv, int(job_id), ctypes.byref(batch))
+    if check:
+        _check(st)
+    return st
+
+
+def talp_gpu_server_submit_raw(srv, job_id, batch, check=True):
+    st = load_library().talp_gpu_server_submit_raw(srv, int(job_id), ctypes.byref(batch))
     if check:
         _check(st)
     return st
@@ -710,6 +718,22 @@ class Server:
                                     TALP_GPU_SORTED_BY_START if sorted_by_start else 0)
         st = talp_gpu_server_submit(self.handle, job_id, b, check)
         del keep
+        return st
+
+    def submit_raw(self, job_id, host_se, host_state, host_off, raw_se, raw_tag, raw_dev, raw_off,
+                   stream_mask=None, hold_back=True, check=True):
+        """Queue one raw activity buffer (host numpy arrays, copied during the
+        call); with hold_back, records a later buffer may precede are held
+        back (stream_mask declares each device's streams)."""
+        b, keep = raw_batch_from_arrays(job_id, np.zeros(0, np.uint32), np.zeros((0, 0, 2), np.int64), host_se,
+                                        host_state, host_off, raw_se, raw_tag, raw_dev, raw_off,
+                                        TALP_GPU_HOLD_BACK if hold_back else 0, None)
+        sm = None
+        if stream_mask is not None:
+            sm = np.ascontiguousarray(stream_mask, dtype=np.uint32)
+            b.stream_mask = sm.ctypes.data
+        st = talp_gpu_server_submit_raw(self.handle, job_id, b, check)
+        del keep, sm
         return st
 
     def query(self, job_id, region=TALP_GPU_ALL_REGIONS, check=True):

@@ -49,6 +49,8 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 struct Slice {
     int chunk = -1;
     uint32_t flags = 0;
+    bool raw = false;              // raw activity records (raw_dev / raw_off below), folded by the raw adapter
+    const uint8_t* raw_dev = nullptr;
     const int64_t* host_se = nullptr;
     const uint8_t* host_state = nullptr;
     const uint64_t* host_off = nullptr;
@@ -63,6 +65,7 @@ struct Job {
     uint32_t n = 0, m = 0, R = 0;
     std::vector<uint32_t> dpr;
     std::vector<int64_t> win;      // [R][n][2]
+    std::vector<uint32_t> smask;   // [n][8] declared streams of the latest raw submission
     std::deque<Slice> pending;
     uint64_t submitted = 0;        // slices accepted
     uint64_t enqueued = 0;         // slices in enqueued waves
@@ -271,35 +274,66 @@ void form_waves(talp_gpu_server* s, std::unique_lock<std::mutex>& lk) {
             ++j->enqueued;
         }
         if (take.empty()) return;
-        std::vector<talp_gpu_trace_batch> bs(take.size());
+        std::vector<talp_gpu_trace_batch> bs;
+        std::vector<talp_gpu_raw_batch> rs;
+        std::vector<std::vector<uint32_t>> masks;   // copied under the lock: submitters may replace them
+        masks.reserve(take.size());
         for (size_t k = 0; k < take.size(); ++k) {
             const Job* j = owners[k];
-            talp_gpu_trace_batch& b = bs[k];
+            const Slice& sl = take[k];
+            if (sl.raw) {
+                talp_gpu_raw_batch r;
+                memset(&r, 0, sizeof(r));
+                r.trace_id = j->id;
+                r.n_ranks = j->n;
+                r.n_regions = j->R;
+                r.flags = TALP_GPU_APPEND | (sl.flags & TALP_GPU_HOLD_BACK);
+                r.devices_per_rank = j->dpr.data();
+                r.region_window = j->win.data();
+                r.host_se = sl.host_se;
+                r.host_state = sl.host_state;
+                r.host_off = sl.host_off;
+                r.raw_se = sl.dev_se;
+                r.raw_tag = sl.dev_tag;
+                r.raw_dev = sl.raw_dev;
+                r.raw_off = sl.dev_off;
+                masks.push_back(j->smask);
+                r.stream_mask = masks.back().data();
+                rs.push_back(r);
+                continue;
+            }
+            talp_gpu_trace_batch b;
             memset(&b, 0, sizeof(b));
             b.trace_id = j->id;
             b.n_ranks = j->n;
             b.n_regions = j->R;
-            b.flags = TALP_GPU_APPEND | (take[k].flags & TALP_GPU_SORTED_BY_START);
+            b.flags = TALP_GPU_APPEND | (sl.flags & TALP_GPU_SORTED_BY_START);
             b.devices_per_rank = j->dpr.data();
             b.region_window = j->win.data();
-            b.host_se = take[k].host_se;
-            b.host_state = take[k].host_state;
-            b.host_off = take[k].host_off;
-            b.dev_se = take[k].dev_se;
-            b.dev_tag = take[k].dev_tag;
-            b.dev_off = take[k].dev_off;
+            b.host_se = sl.host_se;
+            b.host_state = sl.host_state;
+            b.host_off = sl.host_off;
+            b.dev_se = sl.dev_se;
+            b.dev_tag = sl.dev_tag;
+            b.dev_off = sl.dev_off;
+            bs.push_back(b);
         }
         lk.unlock();
         if (s->fin_to_wait) cudaStreamWaitEvent(s->s_fold, s->fin_to_wait, 0);
         s->fin_to_wait = nullptr;
-        const talp_gpu_status st = talp_gpu_ingest_events(s->ctx, bs.data(), bs.size(), s->s_fold);
+        // plain slices in one ingest; raw ones in one call of the raw adapter
+        // (hold-back state per job lives in the context, keyed by the job id)
+        talp_gpu_status st = TALP_GPU_OK, st_raw = TALP_GPU_OK;
+        if (!bs.empty()) st = talp_gpu_ingest_events(s->ctx, bs.data(), bs.size(), s->s_fold);
+        if (!rs.empty()) st_raw = talp_gpu_ingest_raw(s->ctx, rs.data(), rs.size(), s->s_fold);
         Wave w;
         record_wave(s, w);
         lk.lock();
         w.id = s->next_wave++;
         for (size_t k = 0; k < take.size(); ++k) {
             owners[k]->last_wave = w.id;
-            if (st != TALP_GPU_OK) owners[k]->error = st;   // the job's state is no longer defined
+            const talp_gpu_status sk = take[k].raw ? st_raw : st;
+            if (sk != TALP_GPU_OK) owners[k]->error = sk;   // the job's state is no longer defined
             w.chunks.push_back(take[k].chunk);
             w.records += take[k].records;
         }
@@ -485,9 +519,9 @@ talp_gpu_status talp_gpu_server_create(talp_gpu_ctx* ctx, const talp_gpu_server_
         talp_gpu_server_destroy(s);
         return fail(TALP_GPU_ECUDA, "server_create: stream creation failed");
     }
-    // pinned staging of one slice: 17 bytes per record plus the offsets of
-    // the largest job shape
-    s->chunk_bytes = align_up(17ull * s->cfg.max_slice_records + 16ull * (kMaxUnitsPerJob + 1) + 256, 4096);
+    // pinned staging of one slice: 18 bytes per record (raw buffers carry a
+    // device index) plus the offsets of the largest job shape
+    s->chunk_bytes = align_up(18ull * s->cfg.max_slice_records + 16ull * (kMaxUnitsPerJob + 1) + 256, 4096);
     for (uint32_t k = 0; k < s->cfg.staging_slices; ++k) {
         char* p = nullptr;
         if (cudaMallocHost(&p, s->chunk_bytes) != cudaSuccess) {
@@ -610,6 +644,76 @@ talp_gpu_status talp_gpu_server_submit(talp_gpu_server* s, uint64_t job_id, cons
         s->cv_chunk.notify_all();
         return fail(TALP_GPU_ENOTFOUND, "server_submit: job closed meanwhile");
     }
+    it->second->pending.push_back(sl);
+    ++it->second->submitted;
+    ++s->slices_submitted;
+    wake(s);
+    return TALP_GPU_OK;
+}
+
+talp_gpu_status talp_gpu_server_submit_raw(talp_gpu_server* s, uint64_t job_id, const talp_gpu_raw_batch* b) {
+    if (!s || !b) return fail(TALP_GPU_EINVAL, "server_submit_raw: null argument");
+    if (b->flags & ~static_cast<uint32_t>(TALP_GPU_HOLD_BACK))
+        return fail(TALP_GPU_EINVAL, "server_submit_raw: only TALP_GPU_HOLD_BACK may be set");
+    if ((b->flags & TALP_GPU_HOLD_BACK) && !b->stream_mask)
+        return fail(TALP_GPU_EINVAL, "server_submit_raw: hold-back needs the stream masks");
+    uint32_t n = 0;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->jobs.find(job_id);
+        if (it == s->jobs.end()) return fail(TALP_GPU_ENOTFOUND, "server_submit_raw: unknown job");
+        n = it->second->n;
+        for (uint32_t i = 0; i < n; ++i)
+            if (it->second->dpr[i] > static_cast<uint32_t>(kRawMaxDevices))
+                return fail(TALP_GPU_EINVAL, "server_submit_raw: more than 8 devices in a rank");
+    }
+    if (!b->host_off || !b->raw_off || b->host_off[0] != 0 || b->raw_off[0] != 0)
+        return fail(TALP_GPU_EINVAL, "server_submit_raw: offsets must start at 0");
+    for (uint32_t i = 0; i < n; ++i)
+        if (b->host_off[i + 1] < b->host_off[i] || b->raw_off[i + 1] < b->raw_off[i])
+            return fail(TALP_GPU_EINVAL, "server_submit_raw: offsets decrease");
+    const uint64_t nh = b->host_off[n], nd = b->raw_off[n];
+    if (nh + nd > s->cfg.max_slice_records)
+        return fail(TALP_GPU_EINVAL, "server_submit_raw: buffer larger than max_slice_records");
+    if ((nh && (!b->host_se || !b->host_state)) || (nd && (!b->raw_se || !b->raw_tag || !b->raw_dev)))
+        return fail(TALP_GPU_EINVAL, "server_submit_raw: null record array");
+    int ch = -1;
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        s->cv_chunk.wait(lk, [&] { return !s->free_chunks.empty() || s->stop; });
+        if (s->stop) return fail(TALP_GPU_EBUSY, "server_submit_raw: server stopping");
+        ch = s->free_chunks.back();
+        s->free_chunks.pop_back();
+    }
+    char* p = s->chunks[ch];
+    size_t o = 0;
+    auto put = [&](const void* src, size_t bytes) -> char* {
+        char* d = p + o;
+        if (bytes) memcpy(d, src, bytes);
+        o = align_up(o + bytes, 16);
+        return d;
+    };
+    Slice sl;
+    sl.chunk = ch;
+    sl.flags = b->flags;
+    sl.raw = true;
+    sl.host_se = reinterpret_cast<const int64_t*>(put(b->host_se, 16 * nh));
+    sl.dev_se = reinterpret_cast<const int64_t*>(put(b->raw_se, 16 * nd));
+    sl.host_state = reinterpret_cast<const uint8_t*>(put(b->host_state, nh));
+    sl.dev_tag = reinterpret_cast<const uint8_t*>(put(b->raw_tag, nd));
+    sl.raw_dev = reinterpret_cast<const uint8_t*>(put(b->raw_dev, nd));
+    sl.host_off = reinterpret_cast<const uint64_t*>(put(b->host_off, 8ull * (n + 1)));
+    sl.dev_off = reinterpret_cast<const uint64_t*>(put(b->raw_off, 8ull * (n + 1)));
+    sl.records = nh + nd;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->jobs.find(job_id);
+    if (it == s->jobs.end()) {
+        s->free_chunks.push_back(ch);
+        s->cv_chunk.notify_all();
+        return fail(TALP_GPU_ENOTFOUND, "server_submit_raw: job closed meanwhile");
+    }
+    if (b->stream_mask) it->second->smask.assign(b->stream_mask, b->stream_mask + 8ull * n);
+    else if (it->second->smask.empty()) it->second->smask.assign(8ull * n, 0);
     it->second->pending.push_back(sl);
     ++it->second->submitted;
     ++s->slices_submitted;

@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 import tracegen as tg
-from gpu_common import assert_trace_equal, make_ctx
+from gpu_common import assert_trace_equal, folded_trace, make_ctx
 
 pytestmark = pytest.mark.gpu
 
@@ -81,54 +81,6 @@ def test_errors(ctx):
 
 # ------------------------------------------------------------------ hold-back
 
-def _delivered(parts, upto):
-    """Per rank, the raw records of parts 0..upto in delivery order."""
-    n = parts[0].trace.n_ranks
-    out = []
-    for i in range(n):
-        se, tag, dev = [], [], []
-        for p in parts[:upto + 1]:
-            a, b = int(p.raw_off[i]), int(p.raw_off[i + 1])
-            se.append(p.raw_se[a:b])
-            tag.append(p.raw_tag[a:b])
-            dev.append(p.raw_dev[a:b])
-        out.append((np.concatenate(se), np.concatenate(tag), np.concatenate(dev)))
-    return out
-
-
-def _folded_trace(t, parts, upto, flush=False):
-    """The trace restricted to the records folded after delivery `upto`:
-    per device, the delivered records starting at or before the minimum,
-    over the device's declared streams, of each stream's last delivered
-    start (a declared stream with nothing delivered: nothing folds); with
-    flush, every delivered record."""
-    dpr = np.asarray(t.devices_per_rank, np.int64)
-    masks = parts[0].stream_mask
-    se_all, tag_all, counts = [], [], []
-    for i, (se, tag, dev) in enumerate(_delivered(parts, upto)):
-        for d in range(int(dpr[i])):
-            sel = dev == d
-            s, g = se[sel], tag[sel]
-            if not flush:
-                W = np.iinfo(np.int64).max
-                for st in range(32):
-                    if (int(masks[i, d]) >> st) & 1:
-                        on = (g & 31) == st
-                        W = min(W, int(s[on, 0].max()) if on.any() else np.iinfo(np.int64).min)
-                keep = s[:, 0] <= W
-                s, g = s[keep], g[keep]
-            o = np.lexsort((s[:, 1], s[:, 0]))
-            se_all.append(s[o])
-            tag_all.append(g[o])
-            counts.append(s.shape[0])
-    off = np.zeros(len(counts) + 1, np.uint64)
-    off[1:] = np.cumsum(counts)
-    return tg.Trace(trace_id=t.trace_id, n_ranks=t.n_ranks, devices_per_rank=t.devices_per_rank,
-                    region_window=t.region_window, host_se=t.host_se, host_state=t.host_state, host_off=t.host_off,
-                    dev_se=np.concatenate(se_all) if se_all else np.zeros((0, 2), np.int64),
-                    dev_tag=np.concatenate(tag_all) if tag_all else np.zeros(0, np.uint8), dev_off=off)
-
-
 def _hold_back_run(ctx, t, n_calls, seed, arrays=False):
     import torch
     import paper_2603_26576_b300 as P
@@ -141,7 +93,7 @@ def _hold_back_run(ctx, t, n_calls, seed, arrays=False):
                         raw_se=torch.from_numpy(p.raw_se).cuda(), raw_tag=torch.from_numpy(p.raw_tag).cuda(),
                         raw_dev=torch.from_numpy(p.raw_dev).cuda())]
         ctx.ingest_raw([p], flags=P.TALP_GPU_HOLD_BACK | (P.TALP_GPU_APPEND if j else 0), arrays=arr)
-        f = _folded_trace(t, parts, j)
+        f = folded_trace(t, parts, j)
         delivered = sum(int(q.raw_off[-1]) for q in parts[:j + 1])
         assert ctx.raw_held(t.trace_id) == delivered - int(f.dev_off[-1]), ("held", seed, j)
         for r in range(t.n_regions):

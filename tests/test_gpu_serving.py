@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 import tracegen as tg
-from gpu_common import assert_metrics_equal, make_ctx
+from gpu_common import assert_metrics_equal, folded_trace, make_ctx
 
 pytestmark = pytest.mark.gpu
 
@@ -182,4 +182,57 @@ def test_serving_errors_stay_with_their_job():
         assert st == ENOTFOUND
         st, _ = talp_gpu_server_query(srv.handle, good.trace_id, good.n_regions, check=False)
         assert st == EINVAL
+    c.close()
+
+
+# ------------------------------------------------------- raw activity buffers
+
+def _raw_client(srv, t, parts, results, errors):
+    try:
+        for p in parts:
+            srv.submit_raw(t.trace_id, p.trace.host_se, p.trace.host_state, p.trace.host_off, p.raw_se, p.raw_tag,
+                           p.raw_dev, p.raw_off, stream_mask=p.stream_mask, hold_back=True)
+            results.append(srv.query(t.trace_id))
+        z = np.zeros(t.n_ranks + 1, np.uint64)
+        srv.submit_raw(t.trace_id, np.zeros((0, 2), np.int64), np.zeros(0, np.uint8), z, np.zeros((0, 2), np.int64),
+                       np.zeros(0, np.uint8), np.zeros(0, np.uint8), z, hold_back=False)   # flush
+        results.append(srv.query(t.trace_id))
+    except Exception as e:  # pragma: no cover - reported by the test
+        errors.append((t.trace_id, repr(e)))
+
+
+def test_serving_raw_buffers_hold_back():
+    """Jobs stream raw activity buffers (streams interleaved in completion
+    order) with hold-back; every answer equals the oracle on the records
+    folded so far (per device, those at or before the watermark), and after
+    the flush on the whole trace."""
+    from paper_2603_26576_b300 import Server
+    c = make_ctx()
+    law = tg.DeviceLaw("lognormal", (0, 1, 2, 3), (4, 5), occupancy=1.5)
+    ts = [tg.random_trace(40 + k, trace_id=700 + k, n_ranks=2 + k % 3, devices_per_rank=1 + k % 4,
+                          dev_events=1500 + 700 * k, host_events=200, n_regions=3, law=law) for k in range(6)]
+    ts += [tg.tiny_trace(s, trace_id=720 + s, max_ranks=3, max_devs=3, max_events=150) for s in range(6)]
+    with Server(c, max_jobs=32, max_slice_records=1 << 17, staging_slices=8) as srv:
+        plan = []
+        for i, t in enumerate(ts):
+            parts = tg.raw_deliveries(tg.to_raw(t), 2 + i % 5, seed=i)
+            srv.open_job(t.trace_id, t.devices_per_rank, t.region_window)
+            plan.append((t, parts, [], []))
+        th = [threading.Thread(target=_raw_client, args=(srv, t, parts, res, err)) for t, parts, res, err in plan]
+        for x in th:
+            x.start()
+        for x in th:
+            x.join()
+        for t, parts, res, err in plan:
+            assert not err, err
+            assert len(res) == len(parts) + 1
+            for j in range(len(parts)):
+                f = folded_trace(t, parts, j)
+                for r in range(t.n_regions):
+                    assert_metrics_equal(res[j][r], oracle.region_metrics(f, r), ("raw-serve", t.trace_id, j, r))
+            for r in range(t.n_regions):
+                assert_metrics_equal(res[-1][r], oracle.region_metrics(t, r), ("raw-serve-flush", t.trace_id, r))
+            srv.close_job(t.trace_id)
+        st = srv.stats()
+        assert st["jobs_open"] == 0
     c.close()
