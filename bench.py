@@ -77,6 +77,8 @@ def parse():
                     help="plain/small: device records grouped by stream (each stream in start order, as per-stream "
                          "activity buffers deliver them); the library sorts them")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--hold-calls", type=int, default=1,
+                    help="raw: stream each step's records as this many delivery buffers with hold-back")
     return ap.parse_args()
 
 
@@ -571,9 +573,24 @@ def run_raw(a):
     stream = torch.cuda.Stream()
     R = t.n_regions
     out_dev = torch.empty(R * 200, dtype=torch.uint8, device=dev)
+    hold = max(1, a.hold_calls)
+    hold_batches = []
+    if hold > 1:
+        # the same records as `hold` delivery buffers: all but the last with
+        # hold-back, the last one flushes; the first one starts the trace
+        for j, p in enumerate(tg.raw_deliveries(r, hold, seed=5)):
+            pa = [up(p.trace.host_se), up(p.trace.host_state), up(p.raw_se), up(p.raw_tag), up(p.raw_dev)]
+            fl = (P.TALP_GPU_HOLD_BACK if j < hold - 1 else 0) | (P.TALP_GPU_APPEND if j else 0)
+            hold_batches.append(P.raw_batch_from_arrays(t.trace_id, t.devices_per_rank, t.region_window, pa[0],
+                                                        pa[1], p.trace.host_off, pa[2], pa[3], pa[4], p.raw_off,
+                                                        fl, p.stream_mask) + (pa,))
 
     def step_raw():
-        P.talp_gpu_ingest_raw(ctx.ctx, [rb], stream)
+        if hold > 1:
+            for hb_, _, _ in hold_batches:
+                P.talp_gpu_ingest_raw(ctx.ctx, [hb_], stream)
+        else:
+            P.talp_gpu_ingest_raw(ctx.ctx, [rb], stream)
         P.talp_gpu_region_metrics_device(ctx.ctx, [t.trace_id], P.TALP_GPU_ALL_REGIONS, out_dev.data_ptr(), stream)
 
     def step_lanes():
@@ -619,7 +636,10 @@ def run_raw(a):
         "dtype": "int64", "data": "synthetic (seeded generator; the paper's traces are not available)",
         "config": {"workload": f"plain large trace at scale {scale:g} as raw per-rank delivery buffers (4 devices x "
                                "4 streams per rank interleaved in completion order)",
-                   "records_per_step": N, "form": "talp_gpu_ingest_raw + metrics, one synchronous call per step",
+                   "records_per_step": N,
+                   "form": ("talp_gpu_ingest_raw + metrics, one synchronous call per step" if hold == 1 else
+                            f"{hold} delivery buffers per step through talp_gpu_ingest_raw with hold-back "
+                            "(the last one flushes), then metrics"),
                    "lanes_in_start_order_ms_per_step": ms_lanes, "raw_over_lanes_time": ms / ms_lanes,
                    "bit_exact_raw_vs_lanes": same,
                    "l2": "records (%.1f GB) larger than L2; no flush" % (BYTES_PER_RECORD * N / 1e9)},
