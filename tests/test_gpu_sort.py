@@ -66,6 +66,19 @@ def test_unsorted_wide_timestamps(ctx):
     ctx.reset()
 
 
+@pytest.mark.parametrize("k", [2, 4, 7, 16])
+def test_few_sorted_runs_wide_timestamps(ctx, k):
+    """k-run segments whose starts span 2^50 to 2^57 ns or sit near -2^61:
+    the merge path compares full 64-bit starts in its splits and merges."""
+    for scale, offset in [(1 << 45, -(1 << 61)), (1 << 40, 0), (1 << 38, 5)]:
+        ts = [tg.split_runs(tg.rescale_time(tg.tiny_trace(s, trace_id=s, max_events=400), scale, offset), k, seed=s)
+              for s in range(16)]
+        ctx.ingest(ts)
+        for t in ts:
+            assert_trace_equal(ctx, t, ("wide-runs", k, scale), sums=(t.trace_id % 4 == 0))
+        ctx.reset()
+
+
 def test_mixed_sorted_and_unsorted_batches(ctx):
     """One ingest call with traces that assert start order and traces that
     do not; a trace that asserts order but lies is still reported."""
