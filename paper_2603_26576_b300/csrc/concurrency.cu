@@ -84,6 +84,8 @@ __device__ __forceinline__ void insert_top(TopK<T>& x, T e) {
 __device__ __forceinline__ uint32_t shfl_up_t(uint32_t v, int d) { return __shfl_up_sync(0xFFFFFFFFu, v, d); }
 __device__ __forceinline__ uint32_t shfl_t(uint32_t v, int s) { return __shfl_sync(0xFFFFFFFFu, v, s); }
 __device__ __forceinline__ int64_t shfl_t(int64_t v, int s) { return shfl64(v, s); }
+__device__ __forceinline__ uint32_t shfl_xor_t(uint32_t v, int m) { return __shfl_xor_sync(0xFFFFFFFFu, v, m); }
+__device__ __forceinline__ int64_t shfl_xor_t(int64_t v, int m) { return shfl_xor64(v, m); }
 
 template <typename T>
 __device__ __forceinline__ TopK<T> shfl_top(const TopK<T>& x, int src) {
@@ -127,87 +129,108 @@ __device__ __forceinline__ void to_abs(TopK<int64_t>& out, const TopK<uint32_t>&
 }
 
 // One tile of a chunk staged in shared memory: rows of 16 bytes and tags.
+// Lane L works on records L * kItems .. L * kItems + kItems - 1, so record q
+// sits at (q % kItems) * 33 + q / kItems: the lanes' reads of their i-th
+// records are consecutive (no bank conflicts), and so are the staging
+// writes of 8 consecutive records.
+constexpr int kSlots = kItems * 33;
 struct Stage {
-    longlong2 se[kTile];
-    uint8_t tag[kTile];
+    longlong2 se[kSlots];
+    uint8_t tag[kSlots];
 };
+
+__device__ __forceinline__ int slot(int q) { return (q % kItems) * 33 + q / kItems; }
 
 __device__ __forceinline__ void stage_tile(Stage& st, const int64_t* __restrict__ se, const uint8_t* __restrict__ tag,
                                            uint64_t r0, int n, int lane) {
     for (int q = lane; q < n; q += 32) {
-        st.se[q] = *reinterpret_cast<const longlong2*>(se + 2 * (r0 + q));
-        st.tag[q] = tag[r0 + q];
+        st.se[slot(q)] = *reinterpret_cast<const longlong2*>(se + 2 * (r0 + q));
+        st.tag[slot(q)] = tag[r0 + q];
     }
     __syncwarp();
 }
 
+__device__ __forceinline__ longlong2 row_of(const Stage& st, int q) { return st.se[slot(q)]; }
+__device__ __forceinline__ uint32_t kind_of(const Stage& st, int q) { return st.tag[slot(q)] >> 5; }
+
 // clipped record q of the stage: start max(s, a), end in [start, b]
 __device__ __forceinline__ void clipped(const Stage& st, int q, const ConcDev& dv, int64_t& s, int64_t& e) {
-    const longlong2 r = st.se[q];
+    const longlong2 r = row_of(st, q);
+    s = max64(r.x, dv.a);
+    e = max64(min64(r.y, dv.b), s);
+}
+
+// clipped row
+__device__ __forceinline__ void clip_row(const longlong2 r, const ConcDev& dv, int64_t& s, int64_t& e) {
     s = max64(r.x, dv.a);
     e = max64(min64(r.y, dv.b), s);
 }
 
 // ------------------------------------------------------------- chunk top-K
+// The K largest ends of a chunk do not depend on the order of its records:
+// each lane takes every 32nd record straight from memory (coalesced) into
+// its own lists, as 32-bit offsets from the chunk's first clipped start
+// (every clipped start and end of the chunk is at or after it), and the
+// warp merges the 32 lists once.  A chunk whose ends reach 2^32 - 1 ns or
+// more past its first start is redone with 64-bit lists.
+template <typename T>
+__device__ __forceinline__ void warp_merge_top(TopK<T>& x) {
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) {
+        TopK<T> y;
+#pragma unroll
+        for (int i = 0; i < K; ++i) y.v[i] = shfl_xor_t(x.v[i], m);
+        merge_top(x, y);
+    }
+}
+
 __global__ void __launch_bounds__(kWarps * 32) conc_chunk_top(const int64_t* __restrict__ se,
                                                              const uint8_t* __restrict__ tag,
                                                              const ConcDev* __restrict__ devs,
                                                              const ConcChunk* __restrict__ chunks, uint32_t n_chunks,
                                                              int64_t* __restrict__ top, uint32_t* __restrict__ status) {
-    __shared__ Stage stg[kWarps];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t c = blockIdx.x * kWarps + wid;
     if (c >= n_chunks) return;
     const ConcChunk ch = chunks[c];
     const ConcDev dv = devs[ch.dev];
-    TopK<int64_t> ca, ck;   // the chunk's lists so far (warp-uniform)
+    TopK<int64_t> ca, ck;
     clear_top(ca);
     clear_top(ck);
     uint32_t bad = 0;
-    for (uint32_t o = 0; o < ch.n; o += kTile) {
-        const int n = static_cast<int>(min(static_cast<uint32_t>(kTile), ch.n - o));
-        stage_tile(stg[wid], se, tag, ch.rec0 + o, n, lane);
+    if (ch.n > 0) {
         int64_t s0, e0;
-        clipped(stg[wid], 0, dv, s0, e0);
+        clip_row(*reinterpret_cast<const longlong2*>(se + 2 * ch.rec0), dv, s0, e0);
         TopK<uint32_t> la, lk;
         clear_top(la);
         clear_top(lk);
         bool fits = true;
-#pragma unroll
-        for (int i = 0; i < kItems; ++i) {
-            const int q = lane * kItems + i;
-            if (q < n) {
-                const longlong2 r = stg[wid].se[q];
-                const uint32_t kind = stg[wid].tag[q] >> 5;
-                bad |= (r.y < r.x ? 1u : 0u) | (kind > 4u ? 2u : 0u);
-                int64_t s, e;
-                clipped(stg[wid], q, dv, s, e);
-                fits &= near32(e, s0);
-                const uint32_t re = rel32(e, s0);
-                insert_top(la, re);
-                if (kind == 0u) insert_top(lk, re);
-            }
+        for (uint32_t q = lane; q < ch.n; q += 32) {
+            const longlong2 r = *reinterpret_cast<const longlong2*>(se + 2 * (ch.rec0 + q));
+            const uint32_t kind = tag[ch.rec0 + q] >> 5;
+            bad |= (r.y < r.x ? 1u : 0u) | (kind > 4u ? 2u : 0u);
+            int64_t s, e;
+            clip_row(r, dv, s, e);
+            fits &= near32(e, s0);
+            const uint32_t re = rel32(e, s0);
+            insert_top(la, re);
+            if (kind == 0u) insert_top(lk, re);
         }
         if (__all_sync(0xFFFFFFFFu, fits)) {
-            scan_top(la, lane);
-            scan_top(lk, lane);
-            TopK<int64_t> xa, xk;
-            to_abs(xa, shfl_top(la, 31), s0);
-            to_abs(xk, shfl_top(lk, 31), s0);
-            merge_top(ca, xa);
-            merge_top(ck, xk);
-        } else if (lane == 0) {
-            // a tile spanning 2^32 ns or more: plain 64-bit inserts
-            for (int q = 0; q < n; ++q) {
+            warp_merge_top(la);
+            warp_merge_top(lk);
+            to_abs(ca, la, s0);
+            to_abs(ck, lk, s0);
+        } else {
+            for (uint32_t q = lane; q < ch.n; q += 32) {
                 int64_t s, e;
-                clipped(stg[wid], q, dv, s, e);
+                clip_row(*reinterpret_cast<const longlong2*>(se + 2 * (ch.rec0 + q)), dv, s, e);
                 insert_top(ca, e);
-                if ((stg[wid].tag[q] >> 5) == 0u) insert_top(ck, e);
+                if ((tag[ch.rec0 + q] >> 5) == 0u) insert_top(ck, e);
             }
+            warp_merge_top(ca);
+            warp_merge_top(ck);
         }
-        ca = shfl_top(ca, 0);
-        ck = shfl_top(ck, 0);
-        __syncwarp();
     }
     bad = __reduce_or_sync(0xFFFFFFFFu, bad);
     if (lane == 0) {
@@ -254,20 +277,20 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
                                                                 int64_t* __restrict__ out,
                                                                 uint32_t* __restrict__ status) {
     __shared__ Stage stg[kWarps];
+    __shared__ unsigned long long s_acc[kWarps][2 * K];   // the warp's level sums of its chunk
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t c = blockIdx.x * kWarps + wid;
     if (c >= n_chunks) return;
     const ConcChunk ch = chunks[c];
     const ConcDev dv = devs[ch.dev];
+    if (lane < 2 * K) s_acc[wid][lane] = 0;
+    __syncwarp();
     TopK<int64_t> sa, sk;   // state before the current tile (warp-uniform)
 #pragma unroll
     for (int i = 0; i < K; ++i) {
         sa.v[i] = in[static_cast<uint64_t>(c) * 2 * K + i];
         sk.v[i] = in[static_cast<uint64_t>(c) * 2 * K + K + i];
     }
-    int64_t acc_a[K], acc_k[K];
-#pragma unroll
-    for (int i = 0; i < K; ++i) acc_a[i] = acc_k[i] = 0;
     uint32_t bad = 0;
     const uint64_t dev_end = dv.rec0 + dv.n;
     for (uint32_t o = 0; o < ch.n; o += kTile) {
@@ -294,11 +317,11 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
             if (q < n) {
                 int64_t sa64, ea64;
                 clipped(stg[wid], q, dv, sa64, ea64);
-                if (q > 0) bad |= stg[wid].se[q - 1].x > stg[wid].se[q].x ? 4u : 0u;
+                if (q > 0) bad |= row_of(stg[wid], q - 1).x > row_of(stg[wid], q).x ? 4u : 0u;
                 fits &= near32(ea64, s0);
                 s[i] = rel32(sa64, s0);
                 e[i] = rel32(ea64, s0);
-                const bool isK = (stg[wid].tag[q] >> 5) == 0u;
+                const bool isK = kind_of(stg[wid], q) == 0u;
                 kmask |= isK ? 1u << i : 0u;
                 insert_top(la, e[i]);
                 if (isK) insert_top(lk, e[i]);
@@ -322,6 +345,11 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
             }
             merge_top(xa, ta);
             merge_top(xk, tk);
+            // a lane's gaps in the tile are disjoint and lie within 2^32 - 1 ns
+            // of s0, so its level sums of the tile fit 32 bits
+            uint32_t acc_a[K], acc_k[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc_a[k] = acc_k[k] = 0;
             const uint32_t bnd = rel32(dv.b, s0);
             uint32_t nxt = shfl_t(s[0], (lane + 1) & 31);
             if (lane == 31 || (lane + 1) * kItems >= n) nxt = rel32(after, s0);
@@ -343,6 +371,17 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
                     }
                 }
             }
+#pragma unroll
+            for (int k = 0; k < K; ++k) {   // warp sums in 16-bit halves (no overflow)
+                const uint32_t al = __reduce_add_sync(0xFFFFFFFFu, acc_a[k] & 0xFFFFu);
+                const uint32_t ah = __reduce_add_sync(0xFFFFFFFFu, acc_a[k] >> 16);
+                const uint32_t kl = __reduce_add_sync(0xFFFFFFFFu, acc_k[k] & 0xFFFFu);
+                const uint32_t kh = __reduce_add_sync(0xFFFFFFFFu, acc_k[k] >> 16);
+                if (lane == 0) {
+                    s_acc[wid][k] += (static_cast<unsigned long long>(ah) << 16) + al;
+                    s_acc[wid][K + k] += (static_cast<unsigned long long>(kh) << 16) + kl;
+                }
+            }
             // state after the tile: the entering state and every record of it
             merge_top(la, ta);
             merge_top(lk, tk);
@@ -355,7 +394,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
                     int64_t sq, eq;
                     clipped(stg[wid], q, dv, sq, eq);
                     insert_top(sa, eq);
-                    const bool isK = (stg[wid].tag[q] >> 5) == 0u;
+                    const bool isK = kind_of(stg[wid], q) == 0u;
                     if (isK) insert_top(sk, eq);
                     int64_t ns = after;
                     if (q + 1 < n) {
@@ -366,8 +405,9 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
                     const int64_t hi = min64(ns, dv.b);
 #pragma unroll
                     for (int k = 0; k < K; ++k) {
-                        acc_a[k] += max64(min64(hi, max64(sa.v[k], sq)) - sq, 0);
-                        acc_k[k] += max64(min64(hi, max64(sk.v[k], sq)) - sq, 0);
+                        s_acc[wid][k] += static_cast<unsigned long long>(max64(min64(hi, max64(sa.v[k], sq)) - sq, 0));
+                        s_acc[wid][K + k] +=
+                            static_cast<unsigned long long>(max64(min64(hi, max64(sk.v[k], sq)) - sq, 0));
                     }
                 }
             }
@@ -378,14 +418,10 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
     }
     if (ch.n > 0 && ch.rec0 > dv.rec0 && lane == 0) bad |= se[2 * (ch.rec0 - 1)] > se[2 * ch.rec0] ? 4u : 0u;
     bad = __reduce_or_sync(0xFFFFFFFFu, bad);
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const int64_t va = warp_sum64(acc_a[k]);
-        const int64_t vk = warp_sum64(acc_k[k]);
-        if (lane == 0) {
-            if (va) atomic_add64(&out[static_cast<uint64_t>(ch.dev) * 2 * K + k], va);
-            if (vk) atomic_add64(&out[static_cast<uint64_t>(ch.dev) * 2 * K + K + k], vk);
-        }
+    __syncwarp();
+    if (lane < 2 * K) {
+        const int64_t v = static_cast<int64_t>(s_acc[wid][lane]);
+        if (v) atomic_add64(&out[static_cast<uint64_t>(ch.dev) * 2 * K + lane], v);
     }
     if (lane == 0 && bad) atomicOr(status, bad);
 }
