@@ -182,3 +182,19 @@ def test_hold_back_errors(ctx):
     assert ctx.raw_held(t.trace_id) == 0
     _hold_back_run(ctx, t, 3, 3)
     ctx.reset()
+
+
+def test_many_streams_per_device(ctx):
+    """Devices with up to 32 streams: more than 16 runs per lane sends the
+    lanes down the sort stage's radix path; the same with hold-back, where
+    every one of the 32 declared streams bounds the watermark."""
+    import paper_2603_26576_b300 as P
+    law = tg.DeviceLaw("lognormal", tuple(range(24)), tuple(range(24, 32)), occupancy=3.0)
+    t = tg.random_trace(77, trace_id=901, n_ranks=2, devices_per_rank=[3, 2], dev_events=[6000, 9000, 1, 4000, 2049],
+                        host_events=[100, 50], n_regions=2, law=law)
+    assert int(np.bitwise_or.reduce(tg.stream_masks(t), axis=None)) == 0xFFFFFFFF
+    ctx.ingest_raw([tg.to_raw(t)])
+    assert_trace_equal(ctx, t, "raw-32-streams")
+    ctx.reset()
+    _hold_back_run(ctx, t, 5, 9)
+    ctx.reset()
