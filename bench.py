@@ -76,6 +76,9 @@ def parse():
     ap.add_argument("--unsorted", action="store_true",
                     help="plain/small: device records grouped by stream (each stream in start order, as per-stream "
                          "activity buffers deliver them); the library sorts them")
+    ap.add_argument("--runs", type=int, default=0,
+                    help="with --unsorted: deal each device's records into this many sorted runs laid end to end "
+                         "instead of grouping them by stream")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--hold-calls", type=int, default=1,
                     help="raw: stream each step's records as this many delivery buffers with hold-back")
@@ -249,7 +252,8 @@ def workload_name(a):
     else:
         base = "single trace: 4 ranks x 1 GPU x 1 stream, 10k host + 10k device intervals/rank, 1 region"
     if a.unsorted:
-        base += ", device records grouped by stream (sorted by the library)"
+        base += (f", each device's records in {a.runs} sorted runs (sorted by the library)" if getattr(a, "runs", 0)
+                 else ", device records grouped by stream (sorted by the library)")
     return base if a.scale == 1.0 else f"{base} (scale {a.scale})"
 
 
@@ -944,7 +948,7 @@ def main():
         d_arrays = dict(host_se=t.host_se, host_state=t.host_state, dev_se=t.dev_se, dev_tag=t.dev_tag)
     else:
         if a.unsorted:
-            t = tg.interleave_lanes(t)
+            t = tg.split_runs(t, a.runs, seed=1) if a.runs > 0 else tg.interleave_lanes(t)
         # device-resident copies of the records
         d_arrays = dict(host_se=torch.from_numpy(t.host_se).to(dev),
                         host_state=torch.from_numpy(t.host_state).to(dev),
@@ -1061,8 +1065,10 @@ def main():
             "dtype": "int64", "data": "synthetic (seeded generator; the paper's traces are not available)",
             "config": {"workload": workload_name(a), "records_per_step": N, "bytes_per_step": BYTES_PER_RECORD * N,
                        "regions": R, "l2": "inputs (%.1f GB) larger than L2; no flush" % (BYTES_PER_RECORD * N / 1e9),
-                       "input_order": ("device records grouped by stream, each stream in start order; the "
-                                       "library finds the out-of-order devices and sorts them (sort stage)")
+                       "input_order": ((f"each device's records dealt into {a.runs} sorted runs laid end to end"
+                                        if a.runs > 0 else "device records grouped by stream, each stream in start "
+                                        "order") + "; the library finds the out-of-order devices and sorts them "
+                                       "(sort stage)")
                        if a.unsorted else "device records in start order (caller asserts SORTED_BY_START)",
                        "hbm_gb_per_s": BYTES_PER_RECORD * N * a.steps / (ms / 1000.0) / 1e9},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": ck,
