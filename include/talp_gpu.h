@@ -482,10 +482,14 @@ talp_gpu_status talp_gpu_server_submit(talp_gpu_server *srv, uint64_t job_id, co
  * ignored: the job's are used; at most 8 devices per rank).  Flags:
  * TALP_GPU_HOLD_BACK only.  With it, the wave folds the records up to each
  * device's watermark and holds the rest back on the GPU (stream_mask, [n][8],
- * declares the streams and is kept by the job); without it, the buffer and
+ * declares the streams); without it, the buffer and
  * every held record of the job are folded.  A query answers over the folded
- * records.  Records per buffer are limited by max_slice_records; the record
- * arrays are host memory, copied during the call. */
+ * records.  The job's declared streams are the union of all masks it was
+ * given.  The buffer is checked during the call: EINVAL for a record naming
+ * a device its rank does not have or (with HOLD_BACK) a stream its device
+ * does not declare, and nothing is queued.  Records per buffer are limited
+ * by max_slice_records; the record arrays are host memory, copied during
+ * the call. */
 talp_gpu_status talp_gpu_server_submit_raw(talp_gpu_server *srv, uint64_t job_id, const talp_gpu_raw_batch *buf);
 /* Metrics of one region (or TALP_GPU_ALL_REGIONS: out_host[n_regions]);
  * blocks until answered.  EINVAL when the job's records were invalid. */

@@ -65,7 +65,7 @@ struct Job {
     uint32_t n = 0, m = 0, R = 0;
     std::vector<uint32_t> dpr;
     std::vector<int64_t> win;      // [R][n][2]
-    std::vector<uint32_t> smask;   // [n][8] declared streams of the latest raw submission
+    std::vector<uint32_t> smask;   // [n][8] declared streams: the union of every raw submission's masks
     std::deque<Slice> pending;
     uint64_t submitted = 0;        // slices accepted
     uint64_t enqueued = 0;         // slices in enqueued waves
@@ -658,13 +658,15 @@ talp_gpu_status talp_gpu_server_submit_raw(talp_gpu_server* s, uint64_t job_id, 
     if ((b->flags & TALP_GPU_HOLD_BACK) && !b->stream_mask)
         return fail(TALP_GPU_EINVAL, "server_submit_raw: hold-back needs the stream masks");
     uint32_t n = 0;
+    std::vector<uint32_t> dpr;
     {
         std::lock_guard<std::mutex> lk(s->mu);
         auto it = s->jobs.find(job_id);
         if (it == s->jobs.end()) return fail(TALP_GPU_ENOTFOUND, "server_submit_raw: unknown job");
         n = it->second->n;
+        dpr = it->second->dpr;
         for (uint32_t i = 0; i < n; ++i)
-            if (it->second->dpr[i] > static_cast<uint32_t>(kRawMaxDevices))
+            if (dpr[i] > static_cast<uint32_t>(kRawMaxDevices))
                 return fail(TALP_GPU_EINVAL, "server_submit_raw: more than 8 devices in a rank");
     }
     if (!b->host_off || !b->raw_off || b->host_off[0] != 0 || b->raw_off[0] != 0)
@@ -677,6 +679,30 @@ talp_gpu_status talp_gpu_server_submit_raw(talp_gpu_server* s, uint64_t job_id, 
         return fail(TALP_GPU_EINVAL, "server_submit_raw: buffer larger than max_slice_records");
     if ((nh && (!b->host_se || !b->host_state)) || (nd && (!b->raw_se || !b->raw_tag || !b->raw_dev)))
         return fail(TALP_GPU_EINVAL, "server_submit_raw: null record array");
+    // A wave folds the raw buffers of many jobs in one call of the raw
+    // adapter, which rejects the whole call for one bad record: check the
+    // buffer here, so that only its submitter sees the error.  The job's
+    // declared streams are the union of every mask it submitted (held
+    // records of a stream stay declared).
+    std::vector<uint32_t> mask;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->jobs.find(job_id);
+        if (it == s->jobs.end()) return fail(TALP_GPU_ENOTFOUND, "server_submit_raw: unknown job");
+        mask = it->second->smask;
+        if (dpr.empty()) dpr = it->second->dpr;
+    }
+    mask.resize(8ull * n, 0u);
+    if (b->stream_mask)
+        for (uint64_t q = 0; q < 8ull * n; ++q) mask[q] |= b->stream_mask[q];
+    const bool hold = (b->flags & TALP_GPU_HOLD_BACK) != 0;
+    for (uint32_t i = 0; i < n; ++i)
+        for (uint64_t q = b->raw_off[i]; q < b->raw_off[i + 1]; ++q) {
+            const uint32_t d = b->raw_dev[q];
+            if (d >= dpr[i]) return fail(TALP_GPU_EINVAL, "server_submit_raw: a record names a device its rank does not have");
+            if (hold && !((mask[8ull * i + d] >> (b->raw_tag[q] & 31u)) & 1u))
+                return fail(TALP_GPU_EINVAL, "server_submit_raw: a record on a stream its device does not declare");
+        }
     int ch = -1;
     {
         std::unique_lock<std::mutex> lk(s->mu);
@@ -712,8 +738,10 @@ talp_gpu_status talp_gpu_server_submit_raw(talp_gpu_server* s, uint64_t job_id, 
         s->cv_chunk.notify_all();
         return fail(TALP_GPU_ENOTFOUND, "server_submit_raw: job closed meanwhile");
     }
-    if (b->stream_mask) it->second->smask.assign(b->stream_mask, b->stream_mask + 8ull * n);
-    else if (it->second->smask.empty()) it->second->smask.assign(8ull * n, 0);
+    std::vector<uint32_t>& sm = it->second->smask;
+    sm.resize(8ull * n, 0u);
+    if (b->stream_mask)
+        for (uint64_t q = 0; q < 8ull * n; ++q) sm[q] |= b->stream_mask[q];
     it->second->pending.push_back(sl);
     ++it->second->submitted;
     ++s->slices_submitted;

@@ -236,3 +236,44 @@ def test_serving_raw_buffers_hold_back():
         st = srv.stats()
         assert st["jobs_open"] == 0
     c.close()
+
+
+def test_serving_raw_bad_buffer_stays_with_its_submitter():
+    """A raw buffer with a record on a stream its device never declared, or
+    naming a device its rank lacks, is refused at submission (EINVAL) and
+    nothing of it is queued; the jobs' other raw buffers, folded in the same
+    waves, give the oracle's metrics of their whole traces."""
+    from paper_2603_26576_b300 import Server
+    c = make_ctx()
+    law = tg.DeviceLaw("lognormal", (0, 1, 2), (3, 4), occupancy=1.2)
+    good = tg.random_trace(61, trace_id=801, n_ranks=2, devices_per_rank=2, dev_events=2000, host_events=100, law=law)
+    bad = tg.random_trace(62, trace_id=802, n_ranks=2, devices_per_rank=[1, 2], dev_events=1500, host_events=80,
+                          law=law)
+    pg = tg.raw_deliveries(tg.to_raw(good), 3, seed=4)
+    pb = tg.raw_deliveries(tg.to_raw(bad), 3, seed=5)
+    with Server(c, max_jobs=8, max_slice_records=1 << 16, staging_slices=4) as srv:
+        for t in (good, bad):
+            srv.open_job(t.trace_id, t.devices_per_rank, t.region_window)
+
+        def sub(t, p, tag=None, dev=None, hold=True, check=True):
+            return srv.submit_raw(t.trace_id, p.trace.host_se, p.trace.host_state, p.trace.host_off, p.raw_se,
+                                  p.raw_tag if tag is None else tag, p.raw_dev if dev is None else dev, p.raw_off,
+                                  stream_mask=p.stream_mask, hold_back=hold, check=check)
+        sub(good, pg[0])
+        sub(bad, pb[0])
+        assert int(pb[1].raw_off[1]) > 0, "rank 0 of the second buffer has records"
+        tag = pb[1].raw_tag.copy()
+        tag[0] = (tag[0] & 0xE0) | 31                    # stream 31: never declared
+        assert sub(bad, pb[1], tag=tag, check=False) == EINVAL
+        dev = pb[1].raw_dev.copy()
+        dev[0] = 1                                       # rank 0 has one device
+        assert sub(bad, pb[1], dev=dev, check=False) == EINVAL
+        sub(good, pg[1])
+        sub(bad, pb[1])
+        sub(good, pg[2], hold=False)
+        sub(bad, pb[2], hold=False)
+        for t in (good, bad):
+            res = srv.query(t.trace_id)
+            for r in range(t.n_regions):
+                assert_metrics_equal(res[r], oracle.region_metrics(t, r), ("raw-bad-buffer", t.trace_id, r))
+    c.close()
