@@ -115,6 +115,20 @@ def oracle_sample(name, scale):
     return tg.single_trace_small(scale=scale)
 
 
+def host_cpu():
+    """The host the CPU oracle runs on: logical cores and CPU model."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"host_nproc": os.cpu_count(), "host_cpu": model}
+
+
 def time_oracle(t):
     import oracle
     t0 = time.perf_counter()
@@ -236,7 +250,8 @@ def run_reference(a):
         "config": {"workload": workload_name(a), "sample": f"one rank of the workload: {n} records per step",
                    "l2": "inputs in host memory (CPU oracle)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"one rank ({t.m_devices} devices, {n} records) x {t.n_regions} regions"},
+                         "sample": f"one rank ({t.m_devices} devices, {n} records) x {t.n_regions} regions",
+                         **host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -983,17 +998,17 @@ def main():
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(a.steps):
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
+    ev[0].record(stream)
+    for q in range(a.steps):
         step_device()
-    e1.record(stream)
+        ev[q + 1].record(stream)
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
     ck = clocks.stop()
-    ms = e0.elapsed_time(e1)
+    ms = ev[0].elapsed_time(ev[-1])
+    per_step = sorted(ev[q].elapsed_time(ev[q + 1]) for q in range(a.steps))
     prof = P.talp_gpu_profile_read(ctx.ctx)
     P.talp_gpu_profile(ctx.ctx, False)
     launches = prof["kernel_launches"] - launches0
@@ -1056,7 +1071,7 @@ def main():
         dt = time_oracle(s)
         cpu = {"value": s.n_records / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"one rank of the workload ({s.m_devices} devices, {s.n_records} records) x "
-                         f"{s.n_regions} regions, {dt:.1f} s"}
+                         f"{s.n_regions} regions, {dt:.1f} s", **host_cpu()}
 
     if rank == 0:
         line = {
@@ -1070,7 +1085,8 @@ def main():
                                         "order") + "; the library finds the out-of-order devices and sorts them "
                                        "(sort stage)")
                        if a.unsorted else "device records in start order (caller asserts SORTED_BY_START)",
-                       "hbm_gb_per_s": BYTES_PER_RECORD * N * a.steps / (ms / 1000.0) / 1e9},
+                       "hbm_gb_per_s": BYTES_PER_RECORD * N * a.steps / (ms / 1000.0) / 1e9,
+                       "ms_per_step_best": per_step[0], "ms_per_step_median": per_step[len(per_step) // 2]},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": ck,
             "check": {"elapsed_ns_region0": res[0].elapsed_ns, "dev_pe_region0": res[0].dev_pe},
         }
