@@ -198,3 +198,19 @@ def test_many_streams_per_device(ctx):
     ctx.reset()
     _hold_back_run(ctx, t, 5, 9)
     ctx.reset()
+
+
+def test_device_pointers_several_traces_one_call(ctx):
+    """Raw buffers of several traces in device memory, one call: every
+    tile points into its own trace's arrays."""
+    import torch
+    ts = [tg.random_trace(90 + k, trace_id=950 + k, n_ranks=1 + k, devices_per_rank=1 + (k % 3), dev_events=1500 + 500 * k,
+                          host_events=60, n_regions=2) for k in range(4)]
+    rs = [tg.to_raw(t) for t in ts]
+    arrays = [dict(host_se=torch.from_numpy(t.host_se).cuda(), host_state=torch.from_numpy(t.host_state).cuda(),
+                   raw_se=torch.from_numpy(r.raw_se).cuda(), raw_tag=torch.from_numpy(r.raw_tag).cuda(),
+                   raw_dev=torch.from_numpy(r.raw_dev).cuda()) for t, r in zip(ts, rs)]
+    ctx.ingest_raw(rs, arrays=arrays)
+    for t in ts:
+        assert_trace_equal(ctx, t, "raw-device-multi")
+    ctx.reset()
