@@ -778,6 +778,9 @@ talp_gpu_status talp_gpu_create(talp_gpu_ctx** out, int device, size_t hbm_budge
     cudaEventCreateWithFlags(&c->ev_raw, cudaEventDisableTiming);
     cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     // overrides of the sweep tuning (benchmarks and tests)
+    // device-side wait limit in clock cycles; a negative value makes every
+    // sweep report a time-out at its first wait (tests of the failure path)
+    if (const char* s = getenv("TALP_GPU_WAIT_LIMIT")) c->wait_limit = strtoll(s, nullptr, 10);
     if (const char* s = getenv("TALP_GPU_SWEEP_SHAPE")) {
         c->defaults.shape = atoi(s) % kNumSweepShapes;
         c->shape_forced = true;

@@ -209,7 +209,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Bounded wait: returns false when `limit` clock cycles pass first.
+// Copies already issued must still land before a CTA exits: that drain
+// waits with its own bound, whatever the configured limit.
+constexpr int64_t kDrainWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
+// A negative limit reports a time-out at once: the failure path's test hook.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int64_t limit) {
+    if (limit < 0) return false;
     if (mbar_try_wait(bar, parity)) return true;
     const int64_t t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {

@@ -639,7 +639,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
             if (d_status) atomicOr(d_status, ST_TIMEOUT);
             // let the copies still in flight land before the CTA's shared memory goes away
             for (uint32_t t = n_consumed; t < n_issued; ++t)
-                (void)mbar_wait_bounded(&bars[t % STAGES], (t / STAGES) & 1u, wait_limit);
+                (void)mbar_wait_bounded(&bars[t % STAGES], (t / STAGES) & 1u, kDrainWaitCycles);
             wrec[gw].head_seg = NONE;
             wrec[gw].tail_seg = NONE;
         }

@@ -1,0 +1,38 @@
+"""Failure path of the device-side waits, without faulting or hanging the
+GPU: a context whose wait limit is negative makes every sweep report a
+time-out at its first wait (a wait on a flag nothing sets).  The kernel
+lets its copies in flight land, returns, and the next result call gives
+ETIMEDOUT; the GPU and a fresh context stay usable."""
+import pytest
+
+import tracegen as tg
+from gpu_common import assert_trace_equal, env, make_ctx
+
+pytestmark = pytest.mark.gpu
+
+ETIMEDOUT = -4
+
+
+def test_wait_limit_runs_out_reports_etimedout():
+    import paper_2603_26576_b300 as P
+    t = tg.random_trace(3, trace_id=41, n_ranks=3, devices_per_rank=2, dev_events=4000, host_events=500,
+                        n_regions=2)
+    with env(TALP_GPU_WAIT_LIMIT=-1):
+        c = P.Context(0)
+    try:
+        c.ingest([t], flags=P.TALP_GPU_SORTED_BY_START)
+        with pytest.raises(P.TalpGpuError) as e:
+            c.metrics(t.trace_id)
+        assert e.value.status == ETIMEDOUT
+        # the same context answers the next ingest the same way: nothing is stuck
+        c.reset()
+        c.ingest([t], flags=P.TALP_GPU_SORTED_BY_START)
+        with pytest.raises(P.TalpGpuError) as e:
+            c.metrics(t.trace_id)
+        assert e.value.status == ETIMEDOUT
+    finally:
+        c.close()
+    good = make_ctx()
+    good.ingest([t], flags=P.TALP_GPU_SORTED_BY_START)
+    assert_trace_equal(good, t, "after-timeout")
+    good.close()
