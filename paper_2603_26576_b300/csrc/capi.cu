@@ -670,8 +670,10 @@ talp_gpu_status enqueue_ingest(talp_gpu_ctx* c, const Layout& L, const char* up,
             e1 = take_event(c);
             TALP_CUDA(cudaEventRecord(e0, stream));
         }
+        // with a sort stage to follow, segments found out of order are not computed any further
         TALP_CUDA(launch_sweep(L.shape, static_cast<int>(L.rmax), L.grid, dsegs, dstart, dsend,
-                               static_cast<uint32_t>(L.n_segs), wrec, seg_flags, gstatus, c->wait_limit, stream));
+                               static_cast<uint32_t>(L.n_segs), wrec, seg_flags, gstatus, c->wait_limit, L.sorting,
+                               stream));
         if (profile) {
             TALP_CUDA(cudaEventRecord(e1, stream));
             c->ev_pending.emplace_back(e0, e1);
@@ -693,7 +695,7 @@ talp_gpu_status enqueue_ingest(talp_gpu_ctx* c, const Layout& L, const char* up,
                                         static_cast<int>(std::max<uint64_t>(gs, 1)), stream));
             TALP_CUDA(launch_sweep(L.shape, static_cast<int>(L.rmax), L.full_grid, rsegs, rstart, rrend,
                                    static_cast<uint32_t>(L.n_dev_segs), wrec, seg_flags, gstatus, c->wait_limit,
-                                   stream));
+                                   false, stream));
             TALP_CUDA(launch_fixup(rsegs, rstart, wrec, static_cast<uint32_t>(L.full_grid) * L.warps, seg_flags,
                                    false, stream));
             nl += 2 + 1 + kMergeRounds + 24 + 1 + 2;

@@ -249,7 +249,7 @@ extern "C" talp_gpu_status talp_gpu_reduce_noalloc(const talp_gpu_trace_batch* b
         e = launch_sweep(shape, static_cast<int>(R), grid, reinterpret_cast<const SegDesc*>(S + kOffSegs),
                          reinterpret_cast<const uint64_t*>(S + kOffStart),
                          reinterpret_cast<const uint64_t*>(S + kOffEnd), n_segs, wrec, flags, gstatus,
-                         4000000000LL, stream);
+                         4000000000LL, false, stream);
     if (e == cudaSuccess && nrec > 0)
         e = launch_fixup(reinterpret_cast<const SegDesc*>(S + kOffSegs),
                          reinterpret_cast<const uint64_t*>(S + kOffStart), wrec, n_wrec, flags, false, stream);

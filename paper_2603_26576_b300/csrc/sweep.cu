@@ -223,7 +223,11 @@ __device__ __forceinline__ void pieces64(const longlong2* sse, int base, const u
     }
 }
 
-template <int ITEMS, int WARPS, int STAGES, int RMAX, int MINB>
+// SKIP: the ingest sorts the device segments found out of order and sweeps
+// them again from their saved sums, so a warp that finds such a segment out
+// of order lets the rest of its part of it stream past uncomputed.  Ingests
+// that assert start order launch the instantiation without it.
+template <int ITEMS, int WARPS, int STAGES, int RMAX, int MINB, bool SKIP>
 __global__ void __launch_bounds__(WARPS * 32, MINB)
     sweep_kernel(const SegDesc* __restrict__ segs, const uint64_t* __restrict__ seg_start,
                  const uint64_t* __restrict__ seg_rend, uint32_t n_segs,
@@ -330,6 +334,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     int64_t acc = 0;          // lane j < 3R: sum of chain j % 3 in region j / 3
     int64_t carryK = NEG_INF, carryM = NEG_INF, last_s = NEG_INF;
     uint32_t pbad = 0;
+    bool d_sortable = false;  // SKIP: the segment may be sorted and swept again
+    bool skip_seg = false;    // SKIP, warp-uniform: this warp found it out of order
     bool portion_open = false;
     uint32_t n_consumed = 0;
     bool timed_out = false;
@@ -359,6 +365,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
             }
             acc = 0;
             pbad = 0;
+            if constexpr (SKIP) {
+                d_sortable = !d_host && (d.pad[0] & kSegSortable) != 0;
+                skip_seg = false;
+            }
             if (!d_host && cw.pos == cw.seg_base) {
                 carryK = d.carry_in[0];
                 carryM = d.carry_in[1];
@@ -380,6 +390,29 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
         const uint64_t off = cw.pos - cw.seg_base;
         const uint64_t rem = cw.seg_end - cw.pos;
         const int len = rem < static_cast<uint64_t>(TILE) ? static_cast<int>(rem) : TILE;
+        if constexpr (SKIP) {
+            if (skip_seg) {   // the rest of a segment that will be sorted and swept again
+                release(st);
+                ++n_consumed;
+                const bool seg_done = cw.pos + static_cast<uint64_t>(len) == cw.seg_end;
+                const uint32_t seg_now = cw.seg;
+                const bool more = walk_advance(cw, static_cast<uint32_t>(len), seg_start, seg_rend, n_segs, r1);
+                if (seg_done) {   // its flags go out; its sums and carries are restored before the re-sweep
+                    const uint32_t bits = __reduce_or_sync(0xFFFFFFFFu, pbad);
+                    if (lane == 0) {
+                        if (bits) {
+                            atomicOr(d_status, bits);
+                            atomicOr(&seg_flags[seg_now], bits);
+                        }
+                        if (!more) wrec[gw].tail_seg = seg_now;
+                    }
+                    first_portion = false;
+                    portion_open = false;
+                }
+                if (!more) break;
+                continue;
+            }
+        }
         const uintptr_t A = reinterpret_cast<uintptr_t>(d_tag + off);
         uint8_t* stag = stage + C::SE_BYTES + static_cast<int>(A & 15u);
         const int direct_from =
@@ -595,6 +628,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
             }
             release(st);
         }
+        if constexpr (SKIP) {
+            if (d_sortable && __any_sync(0xFFFFFFFFu, (bad & ST_UNSORTED) != 0u)) skip_seg = true;
+        }
         ++n_consumed;
         pbad |= bad;
         last_s = tile_last_s;
@@ -657,8 +693,11 @@ static cudaError_t ensure_smem_attr() {
     constexpr int MINB = WARPS == 8 ? 2 : 3;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<ITEMS, WARPS, STAGES, RMAX, MINB>,
+        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<ITEMS, WARPS, STAGES, RMAX, MINB, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(sweep_kernel<ITEMS, WARPS, STAGES, RMAX, MINB, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -669,10 +708,11 @@ template <int ITEMS, int WARPS, int STAGES, int RMAX>
 static cudaError_t launch_t(int grid, const SegDesc* segs, const uint64_t* seg_start, const uint64_t* seg_rend,
                             uint32_t n_segs,
                             WarpRec* wrec, uint32_t* seg_flags, uint32_t* gstatus, int64_t wait_limit,
-                            cudaStream_t stream) {
+                            bool skip_sorted_out, cudaStream_t stream) {
     using C = SweepCfg<ITEMS, WARPS, STAGES>;
     constexpr int MINB = WARPS == 8 ? 2 : 3;
-    auto k = sweep_kernel<ITEMS, WARPS, STAGES, RMAX, MINB>;
+    auto k = skip_sorted_out ? sweep_kernel<ITEMS, WARPS, STAGES, RMAX, MINB, true>
+                             : sweep_kernel<ITEMS, WARPS, STAGES, RMAX, MINB, false>;
     cudaError_t e = ensure_smem_attr<ITEMS, WARPS, STAGES, RMAX>();
     if (e != cudaSuccess) return e;
     k<<<grid, WARPS * 32, C::SMEM, stream>>>(segs, seg_start, seg_rend, n_segs, wrec, seg_flags, gstatus,
@@ -684,7 +724,7 @@ template <int ITEMS, int WARPS, int STAGES, int RMAX>
 static int occupancy_t() {
     using C = SweepCfg<ITEMS, WARPS, STAGES>;
     constexpr int MINB = WARPS == 8 ? 2 : 3;
-    auto k = sweep_kernel<ITEMS, WARPS, STAGES, RMAX, MINB>;
+    auto k = sweep_kernel<ITEMS, WARPS, STAGES, RMAX, MINB, false>;
     if (ensure_smem_attr<ITEMS, WARPS, STAGES, RMAX>() != cudaSuccess) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, WARPS * 32, C::SMEM) != cudaSuccess) return 0;
@@ -701,7 +741,8 @@ static int occupancy_t() {
     }
 
 #define TALP_LAUNCH(I, W, S, RM) \
-    launch_t<I, W, S, RM>(grid, segs, seg_start, seg_rend, n_segs, wrec, seg_flags, gstatus, wait_limit, stream)
+    launch_t<I, W, S, RM>(grid, segs, seg_start, seg_rend, n_segs, wrec, seg_flags, gstatus, wait_limit, \
+                          skip_sorted_out, stream)
 #define TALP_OCC(I, W, S, RM) occupancy_t<I, W, S, RM>()
 
 // The region count no longer shapes the kernel's registers (each lane owns
@@ -709,7 +750,7 @@ static int occupancy_t() {
 // every R <= 8.
 cudaError_t launch_sweep(int shape, int rmax, int grid, const SegDesc* segs, const uint64_t* seg_start,
                          const uint64_t* seg_rend, uint32_t n_segs, WarpRec* wrec, uint32_t* seg_flags,
-                         uint32_t* gstatus, int64_t wait_limit, cudaStream_t stream) {
+                         uint32_t* gstatus, int64_t wait_limit, bool skip_sorted_out, cudaStream_t stream) {
     (void)rmax;
     TALP_SHAPE_SWITCH(shape, 8, TALP_LAUNCH)
     return cudaErrorInvalidValue;
