@@ -129,6 +129,27 @@ def host_cpu():
     return {"host_nproc": os.cpu_count(), "host_cpu": model}
 
 
+def _oracle_worker(args):
+    """One process of the all-cores oracle run: the same bounded sample,
+    timed three times (the median), so that the processes overlap."""
+    name, scale = args
+    import oracle
+    s = oracle_sample(name, scale)
+    dts = sorted(time_oracle(s) for _ in range(3))
+    return s.n_records, dts[1]
+
+
+def oracle_all_cores(name, scale):
+    """The untuned oracle on every host core at once: one process per core
+    (started by spawn: this process holds a GPU context), each on the
+    sample; the throughput is the sum over processes."""
+    import multiprocessing as mp
+    p = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(p) as pool:
+        res = pool.map(_oracle_worker, [(name, scale)] * p)
+    return sum(n / dt for n, dt in res), p, res[0][0]
+
+
 def time_oracle(t):
     import oracle
     t0 = time.perf_counter()
@@ -1065,13 +1086,16 @@ def main():
             "kernel_ms": sweep_ms, "peak_source": f"{peak_kind} hbm_gbs"}
 
     # ---- CPU oracle on a bounded sample (rank 0, N = 1 only)
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         s = oracle_sample(a.workload, a.scale)
         dt = time_oracle(s)
         cpu = {"value": s.n_records / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"one rank of the workload ({s.m_devices} devices, {s.n_records} records) x "
                          f"{s.n_regions} regions, {dt:.1f} s", **host_cpu()}
+        v_all, p_all, n_all = oracle_all_cores(a.workload, a.scale)
+        cpu_all = {"value": v_all, "unit": UNIT, "cores": p_all, "kind": "oracle",
+                   "sample": f"the same sample ({n_all} records) in {p_all} processes at once, one per core"}
 
     if rank == 0:
         line = {
@@ -1087,7 +1111,8 @@ def main():
                        if a.unsorted else "device records in start order (caller asserts SORTED_BY_START)",
                        "hbm_gb_per_s": BYTES_PER_RECORD * N * a.steps / (ms / 1000.0) / 1e9,
                        "ms_per_step_best": per_step[0], "ms_per_step_median": per_step[len(per_step) // 2]},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": ck,
+            "roofline": roof, "cpu_baseline": cpu, "cpu_all_cores": cpu_all, "e2e": e2e, "gpu_launches": launches,
+            "clocks": ck,
             "check": {"elapsed_ns_region0": res[0].elapsed_ns, "dev_pe_region0": res[0].dev_pe},
         }
         print(json.dumps(line), flush=True)
