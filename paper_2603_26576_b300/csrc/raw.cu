@@ -43,17 +43,22 @@ __global__ void __launch_bounds__(kRawThreads) raw_hist_kernel(const RawTile* __
         for (int b = threadIdx.x; b < kBuckets; b += kRawThreads) h[b] = 0;
         __syncthreads();
         // warp-aggregated: one shared-memory add per distinct bucket of 32 records
-        for (uint32_t q0 = 0; q0 < tl.n; q0 += kRawThreads) {
-            const uint32_t q = q0 + threadIdx.x;
-            uint32_t bk = kBuckets + (threadIdx.x & 31);   // unique when unused
+        // all the tile's device and tag bytes loaded first, then one
+        // shared-memory add per record
+        uint8_t dv[kRawItems], tv[kRawItems];
+#pragma unroll
+        for (int r = 0; r < kRawItems; ++r) {
+            const uint32_t q = r * kRawThreads + threadIdx.x;
+            dv[r] = q < tl.n ? tl.dev[q] : 0xFF;
+            tv[r] = q < tl.n ? tl.tag[q] : 0;
+        }
+#pragma unroll
+        for (int r = 0; r < kRawItems; ++r) {
+            const uint32_t q = r * kRawThreads + threadIdx.x;
             if (q < tl.n) {
-                const uint8_t d = tl.dev[q];
-                if (d < D) bk = bucket_of(d, tl.tag[q]);
+                if (dv[r] < D) atomicAdd(&h[bucket_of(dv[r], tv[r])], 1u);
                 else atomicOr(status, 1u);
             }
-            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, bk);
-            if (bk < static_cast<uint32_t>(kBuckets) && (threadIdx.x & 31) == __ffs(peers) - 1)
-                atomicAdd(&h[bk], static_cast<uint32_t>(__popc(peers)));
         }
         __syncthreads();
         for (int b = threadIdx.x; b < kBuckets; b += kRawThreads) hist[static_cast<uint64_t>(t) * kBuckets + b] = h[b];
