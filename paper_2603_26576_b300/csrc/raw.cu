@@ -42,7 +42,6 @@ __global__ void __launch_bounds__(kRawThreads) raw_hist_kernel(const RawTile* __
         const uint32_t D = ranks[tl.rank].D;
         for (int b = threadIdx.x; b < kBuckets; b += kRawThreads) h[b] = 0;
         __syncthreads();
-        // warp-aggregated: one shared-memory add per distinct bucket of 32 records
         // all the tile's device and tag bytes loaded first, then one
         // shared-memory add per record
         uint8_t dv[kRawItems], tv[kRawItems];
