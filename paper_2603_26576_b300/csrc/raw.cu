@@ -137,11 +137,17 @@ __global__ void __launch_bounds__(kRawThreads) raw_scatter_kernel(const RawTile*
         const uint32_t w0 = wid * (kRawTile / (kRawThreads / 32));
         uint32_t bk[kRawItems], rnk[kRawItems];
         bool ok[kRawItems];
+        uint8_t tv[kRawItems];
+#pragma unroll
+        for (int r = 0; r < kRawItems; ++r) {   // the lane's device and tag bytes, loaded first
+            const uint32_t q = w0 + r * 32 + lane;
+            const uint8_t dv = q < tl.n ? tl.dev[q] : 0xFF;
+            tv[r] = q < tl.n ? tl.tag[q] : 0;
+            ok[r] = dv < D;
+            bk[r] = ok[r] ? bucket_of(dv, tv[r]) : kBuckets + lane;   // unique when unused
+        }
 #pragma unroll
         for (int r = 0; r < kRawItems; ++r) {
-            const uint32_t q = w0 + r * 32 + lane;
-            ok[r] = q < tl.n && tl.dev[q] < D;
-            bk[r] = ok[r] ? bucket_of(tl.dev[q], tl.tag[q]) : kBuckets + lane;   // unique when unused
             const uint32_t peers = __match_any_sync(0xFFFFFFFFu, bk[r]);
             const uint32_t below = __popc(peers & ((1u << lane) - 1u));
             uint32_t basec = 0;
@@ -168,7 +174,7 @@ __global__ void __launch_bounds__(kRawThreads) raw_scatter_kernel(const RawTile*
                 const uint32_t q = w0 + r * 32 + lane;
                 const uint64_t o = offs[static_cast<uint64_t>(t) * kBuckets + bk[r]] + cnt[wid][bk[r]] + rnk[r];
                 *reinterpret_cast<longlong2*>(lse + 2 * o) = *reinterpret_cast<const longlong2*>(tl.se + 2 * q);
-                ltag[o] = tl.tag[q];
+                ltag[o] = tv[r];
             }
         }
         __syncthreads();
