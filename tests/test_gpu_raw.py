@@ -214,3 +214,25 @@ def test_device_pointers_several_traces_one_call(ctx):
     for t in ts:
         assert_trace_equal(ctx, t, "raw-device-multi")
     ctx.reset()
+
+
+def test_hold_state_ends_with_a_new_trace_of_the_id(ctx):
+    """Held records belong to their trace: an ordinary ingest of the same id
+    without APPEND (a new trace) drops them, and so does reset; the new
+    trace's metrics are its own."""
+    import paper_2603_26576_b300 as P
+    law = tg.DeviceLaw("lognormal", (0, 1, 2), (3,), occupancy=1.3)
+    t = tg.random_trace(31, trace_id=970, n_ranks=2, devices_per_rank=2, dev_events=3000, host_events=100, law=law)
+    parts = tg.raw_deliveries(tg.to_raw(t), 3, seed=2)
+    ctx.ingest_raw([parts[0]], flags=P.TALP_GPU_HOLD_BACK)
+    assert ctx.raw_held(t.trace_id) > 0
+    other = tg.random_trace(32, trace_id=970, n_ranks=2, devices_per_rank=2, dev_events=800, host_events=60)
+    ctx.ingest([other])
+    assert ctx.raw_held(t.trace_id) == 0
+    assert_trace_equal(ctx, other, "new-trace-of-the-id")
+    ctx.ingest_raw([parts[0]], flags=P.TALP_GPU_HOLD_BACK)
+    assert ctx.raw_held(t.trace_id) > 0
+    ctx.reset(t.trace_id)
+    assert ctx.raw_held(t.trace_id) == 0
+    _hold_back_run(ctx, t, 3, 2)
+    ctx.reset()

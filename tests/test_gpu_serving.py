@@ -277,3 +277,31 @@ def test_serving_raw_bad_buffer_stays_with_its_submitter():
             for r in range(t.n_regions):
                 assert_metrics_equal(res[r], oracle.region_metrics(t, r), ("raw-bad-buffer", t.trace_id, r))
     c.close()
+
+
+def test_serving_raw_job_closed_with_held_records_reopens_clean():
+    """Closing a job drops its held raw records with its state; the same id
+    opened again starts from nothing."""
+    from paper_2603_26576_b300 import Server
+    c = make_ctx()
+    law = tg.DeviceLaw("lognormal", (0, 1, 2), (3,), occupancy=1.3)
+    t = tg.random_trace(71, trace_id=880, n_ranks=2, devices_per_rank=2, dev_events=2500, host_events=90, law=law)
+    parts = tg.raw_deliveries(tg.to_raw(t), 3, seed=6)
+    with Server(c, max_jobs=4, max_slice_records=1 << 16, staging_slices=4) as srv:
+        def sub(p, hold=True):
+            srv.submit_raw(t.trace_id, p.trace.host_se, p.trace.host_state, p.trace.host_off, p.raw_se, p.raw_tag,
+                           p.raw_dev, p.raw_off, stream_mask=p.stream_mask, hold_back=hold)
+        srv.open_job(t.trace_id, t.devices_per_rank, t.region_window)
+        sub(parts[0])
+        sub(parts[1])
+        srv.query(t.trace_id)                  # both folded (with whatever they hold back)
+        assert c.raw_held(t.trace_id) > 0
+        srv.close_job(t.trace_id)
+        assert c.raw_held(t.trace_id) == 0
+        srv.open_job(t.trace_id, t.devices_per_rank, t.region_window)
+        for j, p in enumerate(parts):
+            sub(p, hold=j < len(parts) - 1)
+        res = srv.query(t.trace_id)
+        for r in range(t.n_regions):
+            assert_metrics_equal(res[r], oracle.region_metrics(t, r), ("reopened", r))
+    c.close()
