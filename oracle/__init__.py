@@ -27,6 +27,8 @@ INT_FIELDS = ("elapsed_ns", "sum_useful", "sum_offload", "sum_mpi", "max_useful_
 RATIO_FIELDS = ("host_pe", "host_mpi_pe", "host_mpi_lb", "host_mpi_ce", "host_oe",
                 "dev_pe", "dev_lb", "dev_ce", "dev_oe")
 FLAG_EMPTY, FLAG_HOST_NOT_TILED, FLAG_NO_DEVICES = 1, 2, 4
+THREAD_INT_FIELDS = ("elapsed_ns", "sum_useful", "sum_offload", "sum_busiest", "max_busiest", "n_threads")
+THREAD_RATIO_FIELDS = ("pe", "mpi_pe", "mpi_lb", "mpi_ce", "thread_lb", "oe")
 
 
 def compile_c(src: str, out: str) -> str:
@@ -71,6 +73,8 @@ class Oracle:
         lib.oracle_concurrency.restype = ctypes.c_int
         lib.oracle_scalability.argtypes = [ctypes.c_uint32, P, P, P, ctypes.c_uint32, ctypes.c_int, P]
         lib.oracle_scalability.restype = None
+        lib.oracle_thread_metrics.argtypes = [ctypes.c_uint32, P, P, P, P, P]
+        lib.oracle_thread_metrics.restype = None
         self.lib = lib
 
     def validate(self, t) -> int:
@@ -125,6 +129,27 @@ class Oracle:
         self.lib.oracle_scalability(k, _p(iruns), _p(units), _p(pe), int(ref), int(bool(weak)), _p(out))
         names = ("speedup", "host_comp_scal", "host_global_eff", "dev_comp_scal", "dev_global_eff")
         return [{nm: float(v) for nm, v in zip(names, row)} for row in out]
+
+    def thread_metrics_from_sums(self, proc_off, hs) -> dict:
+        """Host tree with threads from per-thread sums hs int64[nT, 3] (the
+        units of process i are proc_off[i] .. proc_off[i+1]-1)."""
+        po = _c(proc_off, np.uint32)
+        hs = _c(hs, np.int64)
+        assert po[0] == 0 and po[-1] == hs.shape[0] and np.all(np.diff(po.astype(np.int64)) >= 1)
+        iout = np.zeros(6, np.int64)
+        dout = np.zeros(6, np.float64)
+        flags = np.zeros(1, np.uint32)
+        self.lib.oracle_thread_metrics(po.shape[0] - 1, _p(po), _p(hs), _p(iout), _p(dout), _p(flags))
+        res = {k: int(v) for k, v in zip(THREAD_INT_FIELDS, iout)}
+        res.update({k: float(v) for k, v in zip(THREAD_RATIO_FIELDS, dout)})
+        res["flags"] = int(flags[0])
+        res["n_procs"] = int(po.shape[0] - 1)
+        return res
+
+    def thread_metrics(self, t, region: int, proc_off) -> dict:
+        """Host tree with threads of one region: every host unit of t is a
+        thread, grouped into processes by proc_off."""
+        return self.thread_metrics_from_sums(proc_off, self.host_sums(t, region))
 
     def metrics_from_sums(self, n_ranks, devices_per_rank, hs, du, win) -> dict:
         dpr = _c(devices_per_rank, np.uint32)
@@ -188,6 +213,10 @@ def scalability(runs, ref=0, weak=False):
 
 def region_metrics(t, region):
     return default().region_metrics(t, region)
+
+
+def thread_metrics(t, region, proc_off):
+    return default().thread_metrics(t, region, proc_off)
 
 
 def trace_metrics(t):

@@ -30,6 +30,9 @@
  *   - ratio order in FP64: (double)num / ((double)k * (double)den) for the
  *     forms with n or m in the denominator, (double)num / (double)den else.
  *
+ * The host tree with threads at the end is a variant the paper does not
+ * define (one thread per process gives back the paper's tree exactly).
+ *
  * Parity is pinned (tests/test_oracle_pins.py) by brute-force per-ns tick
  * counting, closed forms, invariants, and the paper's synthetic-benchmark
  * tables; no function here is "parity unpinned".
@@ -358,4 +361,62 @@ void oracle_scalability(uint32_t n_runs, const int64_t *iruns, const uint32_t *u
         o[3] = weak ? ratio_scaled(K0, m, Kd, m0) : ratio(K0, Kd);
         o[4] = pe[2 * r + 1] * o[3];
     }
+}
+
+/*
+ * Host tree with threads.  The paper's host tree (Sec. 4.1, Eqs. 6-8) has one
+ * set of host intervals per MPI rank and no thread level; this variant gives
+ * every thread of a process its own useful / offload / MPI intervals (one
+ * host unit per thread) and adds one factor for how evenly the threads of a
+ * process are busy.  Process i owns the host units proc_off[i] ..
+ * proc_off[i+1]-1, T_i >= 1 of them.  Per thread, from host_sums (as
+ * oracle_host_sums returns them for the units): B = U + W (busy).  Then
+ *   M_i = max over the threads of process i of B   (its busiest thread)
+ *   nT  = sum_i T_i
+ *   E   = max over all threads of (U + W + MPI)     (Eq. 1 over threads)
+ *   PE        = sum U / (E nT)                      (Eq. 6 over threads)
+ *   MPI PE    = sum_i T_i M_i / (E nT)              (Eq. 7 with the busiest thread
+ *                                                    standing for its process)
+ *     MPI LB  = sum_i T_i M_i / (nT max_i M_i)
+ *     MPI CE  = max_i M_i / E
+ *   thread LB = sum B / sum_i T_i M_i               (Eq. 10's average-over-max form,
+ *                                                    inside each process)
+ *   OE        = sum U / sum B                       (Eq. 8 over threads)
+ * so PE = MPI PE x thread LB x OE and MPI PE = MPI LB x MPI CE; with one
+ * thread per process every value equals the paper's host tree (thread LB = 1).
+ * FP64 in the order written with ratio_k / ratio above; 0/0 reads 1.
+ * iout[6]: E, sum U, sum W, sum_i T_i M_i, max_i M_i, nT.
+ * dout[6]: PE, MPI PE, MPI LB, MPI CE, thread LB, OE.
+ * *flags : 1 = EMPTY (E == 0, every ratio 1).
+ */
+void oracle_thread_metrics(uint32_t n_procs, const uint32_t *proc_off, const int64_t *host_sums,
+                           int64_t *iout, double *dout, uint32_t *flags) {
+    int64_t E = 0, sU = 0, sW = 0, sTM = 0, maxM = 0, nT = 0;
+    for (uint32_t i = 0; i < n_procs; ++i) {
+        const int64_t T = (int64_t)proc_off[i + 1] - (int64_t)proc_off[i];
+        int64_t M = 0;
+        for (uint32_t u = proc_off[i]; u < proc_off[i + 1]; ++u) {
+            const int64_t U = host_sums[3 * u + 0], W = host_sums[3 * u + 1], P = host_sums[3 * u + 2];
+            E = max64(E, U + W + P);
+            sU += U;
+            sW += W;
+            M = max64(M, U + W);
+        }
+        sTM += T * M;
+        maxM = max64(maxM, M);
+        nT += T;
+    }
+    iout[0] = E; iout[1] = sU; iout[2] = sW; iout[3] = sTM; iout[4] = maxM; iout[5] = nT;
+    *flags = 0;
+    if (E == 0) {
+        *flags = 1;
+        for (int q = 0; q < 6; ++q) dout[q] = 1.0;
+        return;
+    }
+    dout[0] = ratio_k(sU, E, nT);
+    dout[1] = ratio_k(sTM, E, nT);
+    dout[2] = ratio_k(sTM, nT, maxM);
+    dout[3] = ratio(maxM, E);
+    dout[4] = ratio(sU + sW, sTM);
+    dout[5] = ratio(sU, sU + sW);
 }

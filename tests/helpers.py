@@ -129,3 +129,18 @@ def host_tiles_windows(trace, region):
         if not np.all(cov == 1):
             return False
     return True
+
+
+def host_units_trace(trace, order, trace_id=0):
+    """A device-free trace whose host unit k is unit order[k] of `trace` (its
+    intervals and windows); units may repeat."""
+    order = [int(u) for u in order]
+    segs = [trace.host_segment(u) for u in order]
+    hoff = np.zeros(len(order) + 1, np.uint64)
+    hoff[1:] = np.cumsum([s[0].shape[0] for s in segs])
+    return Trace(trace_id=trace_id, n_ranks=len(order), devices_per_rank=np.zeros(len(order), np.uint32),
+                 region_window=np.ascontiguousarray(trace.region_window[:, order, :]),
+                 host_se=np.concatenate([s[0] for s in segs]).reshape(-1, 2).astype(np.int64),
+                 host_state=np.concatenate([s[1] for s in segs]).astype(np.uint8), host_off=hoff,
+                 dev_se=np.zeros((0, 2), np.int64), dev_tag=np.zeros(0, np.uint8),
+                 dev_off=np.zeros(1, np.uint64))

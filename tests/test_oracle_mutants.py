@@ -15,7 +15,7 @@ from test_oracle_pins import ALL_PINS
 MUTANTS = [
     ("mpi_pe drops offload (Eq. 7)", "dout[1] = ratio_k(sU + sW, E,", "dout[1] = ratio_k(sU, E,"),
     ("host LB/CE use useful only", "maxUW = max64(maxUW, U + W);", "maxUW = max64(maxUW, U);"),
-    ("elapsed drops MPI (Eq. 1)", "E = max64(E, U + W + P);", "E = max64(E, U + W);"),
+    ("elapsed drops MPI (Eq. 1)", "E = max64(E, U + W + P);\n        sU += U;", "E = max64(E, U + W);\n        sU += U;"),
     ("OE_host counts MPI (Eq. 8)", "dout[4] = ratio(sU, sU + sW);", "dout[4] = ratio(sU, sU + sW + sMPI);"),
     ("transfers not reduced by kernels", "int64_t DM = B - K;", "int64_t DM = UM;"),
     ("transfer sign flipped", "int64_t DM = B - K;", "int64_t DM = K - B;"),
@@ -50,6 +50,19 @@ MUTANTS = [
     ("global efficiency of the reference run", "o[2] = pe[2 * r] * o[1];", "o[2] = pe[2 * ref] * o[1];"),
     ("concurrency kernels read from stream bits", "if ((dev_tag[j] >> 5) == 0) {\n                    ek[nk]",
      "if ((dev_tag[j] & 31) == 0) {\n                    ek[nk]"),
+    ("thread tree: processes not weighted by their threads", "sTM += T * M;", "sTM += M;"),
+    ("thread tree: the master stands for its process", "M = max64(M, U + W);",
+     "if (u == proc_off[i]) M = U + W;"),
+    ("thread tree: elapsed over masters only", "E = max64(E, U + W + P);\n            sU += U;",
+     "if (u == proc_off[i]) E = max64(E, U + W + P);\n            sU += U;"),
+    ("thread tree: OE over the busiest threads", "dout[5] = ratio(sU, sU + sW);", "dout[5] = ratio(sU, sTM);"),
+    ("thread tree: offload not busy", "M = max64(M, U + W);", "M = max64(M, U);"),
+    ("thread tree: thread LB over the largest busiest thread", "dout[4] = ratio(sU + sW, sTM);",
+     "dout[4] = ratio(sU + sW, nT * maxM);"),
+    ("thread tree: nT counts processes", "nT += T;", "nT += 1;"),
+    ("thread tree: MPI CE transposed", "dout[3] = ratio(maxM, E);", "dout[3] = ratio(E, maxM);"),
+    ("thread tree: next process starts one unit late", "for (uint32_t u = proc_off[i]; u < proc_off[i + 1]; ++u)",
+     "for (uint32_t u = proc_off[i] + (i > 0); u < proc_off[i + 1]; ++u)"),
 ]
 
 

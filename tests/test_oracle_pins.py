@@ -14,7 +14,11 @@ oracle's own formulas retyped.
     two-rank traces rebuilt from each use case's narrative reproduce every
     printed value to the printed two decimals;
   * the printed tables of Sec. 5.1 and 5.2 themselves satisfy the
-    parent = product-of-children identities within their rounding.
+    parent = product-of-children identities within their rounding;
+  * the host tree with threads (a variant the paper does not define): one
+    thread per process gives the paper's host tree bit for bit, a worked
+    example by hand, processes of identical threads, per-ns ticks for its
+    integer aggregates, bounds, identities and permutation invariance.
 
 Every pin is a function of an oracle build, so test_oracle_mutants.py can run
 the same pins against deliberately broken builds and check that each one is
@@ -29,8 +33,10 @@ import pytest
 
 import oracle
 import tracegen as tg
-from helpers import (GOLDEN, fixture_trace, host_tiles_windows, load_fixture, pils_cases, tick_device,
-                     tick_host, tick_concurrency)
+from fractions import Fraction
+
+from helpers import (GOLDEN, fixture_trace, host_tiles_windows, host_units_trace, load_fixture, pils_cases,
+                     tick_device, tick_host, tick_concurrency)
 
 pytestmark = pytest.mark.filterwarnings("ignore")
 
@@ -326,11 +332,141 @@ def pin_scalability_closed_forms(O):
     assert weak["host_global_eff"] == runs[1]["host_pe"] == runs[0]["host_pe"]
 
 
+# ----------------------------------------------------------------------------
+# host tree with threads
+
+THREAD_TREE = (("pe", "host_pe"), ("mpi_pe", "host_mpi_pe"), ("mpi_lb", "host_mpi_lb"),
+               ("mpi_ce", "host_mpi_ce"), ("oe", "host_oe"))
+
+
+def pin_threads_one_per_process(O):
+    """One thread per process is the paper's host tree, bit for bit."""
+    for seed in range(40):
+        t = tg.tiny_trace(seed)
+        po = np.arange(t.n_ranks + 1, dtype=np.uint32)
+        for r in range(t.n_regions):
+            a, b = O.region_metrics(t, r), O.thread_metrics(t, r, po)
+            assert (b["elapsed_ns"], b["sum_useful"], b["sum_offload"]) == \
+                (a["elapsed_ns"], a["sum_useful"], a["sum_offload"]), (seed, r)
+            assert b["max_busiest"] == a["max_useful_offload"] and b["n_threads"] == a["n_ranks"]
+            for x, y in THREAD_TREE:
+                assert b[x] == a[y], (seed, r, x, b[x], a[y])
+            assert b["thread_lb"] == 1.0
+
+
+def pin_threads_worked_example(O):
+    """Two processes on [0, 100): process 0 = threads {U 40, W 20, MPI 35} and
+    {U 50, W 20, MPI 28}; process 1 = {U 30, MPI 60}, {U 20}, {U 10, MPI 20}.
+    By hand: E = 98 (the second thread of process 0: 50 + 20 + 28); busiest
+    threads M = 70 (a worker, not the master's 60) and 30; sum_i T_i M_i =
+    2*70 + 3*30 = 230; sum U = 150, sum W = 40, nT = 5.  So PE = 150/490,
+    MPI PE = 230/490, MPI LB = 230/350, MPI CE = 70/98, thread LB = 190/230,
+    OE = 150/190 (every denominator exact, so each value is the correctly
+    rounded fraction)."""
+    fx = dict(n_ranks=5, devices_per_rank=[0] * 5, window=[[0, 100]] * 5,
+              host=[[[0, 40, 0], [40, 60, 1], [60, 95, 2]], [[0, 50, 0], [50, 70, 1], [70, 98, 2]],
+                    [[0, 30, 0], [30, 90, 2]], [[0, 20, 0]], [[0, 10, 0], [10, 30, 2]]], device=[])
+    res = O.thread_metrics(fixture_trace(fx), 0, [0, 2, 5])
+    got = tuple(res[k] for k in ("elapsed_ns", "sum_useful", "sum_offload", "sum_busiest", "max_busiest", "n_threads"))
+    assert got == (98, 150, 40, 230, 70, 5), got
+    want = dict(pe=Fraction(150, 490), mpi_pe=Fraction(230, 490), mpi_lb=Fraction(230, 350),
+                mpi_ce=Fraction(70, 98), thread_lb=Fraction(190, 230), oe=Fraction(150, 190))
+    for k, v in want.items():
+        assert res[k] == float(v), (k, res[k], float(v))
+    assert res["flags"] == 0
+
+
+def pin_threads_replicated(O):
+    """A process of T identical threads: thread LB = 1, and the rest equal the
+    paper's tree of the one-thread trace (every sum and nT scale by T)."""
+    for seed in range(20):
+        t = tg.tiny_trace(seed, allow_empty=False)
+        T = [1 + (seed + i) % 4 for i in range(t.n_ranks)]
+        if len(set(T)) > 1 and seed % 2:
+            T = [T[0]] * t.n_ranks          # uniform T: every factor carries over
+        order = [i for i in range(t.n_ranks) for _ in range(T[i])]
+        rep = host_units_trace(t, order)
+        po = np.zeros(t.n_ranks + 1, np.uint32)
+        po[1:] = np.cumsum(T)
+        base = host_units_trace(t, range(t.n_ranks))
+        for r in range(t.n_regions):
+            a, b = O.region_metrics(base, r), O.thread_metrics(rep, r, po)
+            assert b["thread_lb"] == 1.0 and b["elapsed_ns"] == a["elapsed_ns"]
+            assert b["sum_busiest"] == sum(Ti * m for Ti, m in zip(T, (O.host_sums(base, r)[:, :2].sum(1))))
+            if len(set(T)) == 1:
+                for x, y in THREAD_TREE:
+                    assert math.isclose(b[x], a[y], rel_tol=4e-16, abs_tol=1e-300), (seed, r, x, b[x], a[y])
+
+
+def _random_groups(rng, n):
+    cuts = np.sort(rng.choice(np.arange(1, n), size=int(rng.integers(0, n)), replace=False)) if n > 1 else []
+    return np.concatenate([[0], cuts, [n]]).astype(np.uint32)
+
+
+def pin_threads_brute_force(O):
+    """Integer aggregates of the thread tree from per-ns ticks, with the host
+    units of tiny traces cut into processes at random."""
+    for seed in range(30):
+        t = tg.tiny_trace(seed, max_ranks=6)
+        po = _random_groups(np.random.default_rng(seed), t.n_ranks)
+        for r in range(t.n_regions):
+            ticks = tick_host(t, r)
+            busy = ticks[:, 0] + ticks[:, 1]
+            M = [int(busy[a:b].max()) for a, b in zip(po[:-1], po[1:])]
+            T = np.diff(po.astype(np.int64))
+            res = O.thread_metrics(t, r, po)
+            assert res["elapsed_ns"] == int(ticks.sum(1).max(initial=0)), (seed, r)
+            assert res["sum_busiest"] == int(sum(Ti * m for Ti, m in zip(T, M))), (seed, r)
+            assert res["max_busiest"] == max(M) and res["n_threads"] == t.n_ranks and res["n_procs"] == len(M)
+            assert res["sum_useful"] == ticks[:, 0].sum() and res["sum_offload"] == ticks[:, 1].sum()
+
+
+def pin_threads_invariants(O):
+    """Every factor in [0, 1]; PE = MPI PE x thread LB x OE and MPI PE = MPI LB
+    x MPI CE within rounding; permuting the processes, or the threads inside
+    a process, changes no value."""
+    eps = 4 * np.finfo(np.float64).eps
+    for seed in range(6):
+        rng = np.random.default_rng(100 + seed)
+        base = tg.random_trace(seed, trace_id=seed, n_ranks=3, devices_per_rank=1, dev_events=50, host_events=200,
+                               n_regions=3)
+        t = tg.add_threads(base, [1 + seed % 3, 3, 5], seed=seed)
+        po = t.meta["proc_off"]
+        procs = [list(range(a, b)) for a, b in zip(po[:-1], po[1:])]
+        perm = [procs[i] for i in rng.permutation(len(procs))]
+        perm = [list(rng.permutation(p)) for p in perm]
+        pt = host_units_trace(t, [u for p in perm for u in p])
+        ppo = np.concatenate([[0], np.cumsum([len(p) for p in perm])]).astype(np.uint32)
+        for r in range(t.n_regions):
+            res = O.thread_metrics(t, r, po)
+            for k in oracle.THREAD_RATIO_FIELDS:
+                assert 0.0 <= res[k] <= 1.0, (seed, r, k, res[k])
+            for a, b in ((res["pe"], res["mpi_pe"] * res["thread_lb"] * res["oe"]),
+                         (res["mpi_pe"], res["mpi_lb"] * res["mpi_ce"])):
+                assert abs(a - b) <= eps * max(abs(a), abs(b)), (seed, r, a, b)
+            assert O.thread_metrics(pt, r, ppo) == res, (seed, r)
+            assert res["thread_lb"] < 1.0      # workers are idle part of the time
+
+
+def pin_threads_empty(O):
+    """No host time: E = 0, EMPTY, every ratio 1; a process whose threads are
+    all idle has M = 0 and counts towards nT only."""
+    fx = dict(n_ranks=3, devices_per_rank=[0] * 3, window=[[0, 10]] * 3, host=[[], [], []], device=[])
+    res = O.thread_metrics(fixture_trace(fx), 0, [0, 1, 3])
+    assert res["elapsed_ns"] == 0 and res["flags"] == 1 and all(res[k] == 1.0 for k in oracle.THREAD_RATIO_FIELDS)
+    fx["host"] = [[[0, 10, 0]], [], []]
+    res = O.thread_metrics(fixture_trace(fx), 0, [0, 1, 3])
+    assert (res["pe"], res["mpi_pe"], res["mpi_lb"], res["mpi_ce"], res["thread_lb"], res["oe"]) == \
+        (10 / 30, 10 / 30, 10 / 30, 1.0, 1.0, 1.0)
+
+
 ALL_PINS = [pin_brute_force, pin_balanced_devices_lb_one, pin_single_unit_lb_one,
             pin_disjoint_transfers_not_hidden, pin_transfers_inside_kernels_cost_nothing, pin_covering_kernel,
             pin_union_at_most_sum, pin_tiled_host_elapsed_and_ce, pin_invariants, pin_pils_tables,
             pin_empty_and_degenerate, pin_validation, pin_concurrency_brute_force, pin_concurrency_closed_forms,
-            pin_scalability_identities, pin_scalability_closed_forms]
+            pin_scalability_identities, pin_scalability_closed_forms, pin_threads_one_per_process,
+            pin_threads_worked_example, pin_threads_replicated, pin_threads_brute_force, pin_threads_invariants,
+            pin_threads_empty]
 
 
 # ----------------------------------------------------------------------------

@@ -115,7 +115,7 @@ def _rng(seed: int, trace_id: int, domain: int, index: int) -> np.random.Generat
     return np.random.Generator(np.random.Philox(key=np.array([k0, k1], dtype=np.uint64)))
 
 
-D_HOST, D_DEV, D_TRACE, D_SHAPE = 1, 2, 3, 4
+D_HOST, D_DEV, D_TRACE, D_SHAPE, D_THREAD = 1, 2, 3, 4, 5
 
 
 def _rint_pos(x):
@@ -562,6 +562,73 @@ def random_trace(seed, trace_id=0, n_ranks=3, devices_per_rank=2, dev_events=500
     host_ev = [host_events] * n_ranks if np.isscalar(host_events) else list(host_events)
     work = 0.7 + 0.3 * _rng(seed, trace_id, D_SHAPE, 3).random(n_ranks)
     return build_trace(seed, trace_id, dpr, dev_ev, host_ev, law, work=work, n_regions=n_regions, threads=1)
+
+
+# ----------------------------------------------------------------------------
+# threads: one host unit per thread, grouped into processes
+
+
+def worker_segment(rng, master_se, master_state, busy_frac):
+    """Fork-join worker of a process: inside each useful interval of its master
+    it is busy from the interval start for busy_frac x U(0.8, 1) of the
+    interval (useful; 10% of them device offloading, 2% MPI), idle elsewhere."""
+    mask = master_state == STATE_USEFUL
+    se = master_se[mask]
+    k = se.shape[0]
+    d = np.floor((se[:, 1] - se[:, 0]) * busy_frac * rng.uniform(0.8, 1.0, k)).astype(np.int64)
+    u = rng.random(k)
+    state = np.where(u < 0.02, STATE_MPI, np.where(u < 0.12, STATE_OFFLOAD, STATE_USEFUL)).astype(np.uint8)
+    keep = d > 0
+    out = np.empty((int(keep.sum()), 2), np.int64)
+    out[:, 0] = se[keep, 0]
+    out[:, 1] = se[keep, 0] + d[keep]
+    return out, state[keep]
+
+
+def add_threads(trace: Trace, threads, seed=0x7A1F + 5, imbalance=0.3, pool=None) -> Trace:
+    """Expand each rank of `trace` into a process of T_i threads: unit 0 of the
+    process is the rank itself (its master thread, owning its devices), the
+    other T_i - 1 units are fork-join workers (worker_segment) with busy
+    fraction 1 - imbalance x U(0, 1) each.  Every unit keeps its process's
+    region windows.  meta["proc_off"] = uint32[n + 1] groups the units."""
+    n = int(trace.n_ranks)
+    T = np.full(n, int(threads), np.int64) if np.isscalar(threads) else np.asarray(threads, np.int64)
+    assert T.shape == (n,) and np.all(T >= 1)
+    proc_off = np.zeros(n + 1, np.uint32)
+    proc_off[1:] = np.cumsum(T)
+    nT = int(proc_off[-1])
+
+    def proc_job(i):
+        mse, mst = trace.host_segment(i)
+        rng = _rng(seed, trace.trace_id, D_THREAD, i)
+        fr = 1.0 - imbalance * rng.random(int(T[i]) - 1)
+        parts = [(mse, mst)]
+        for w in range(int(T[i]) - 1):
+            parts.append(worker_segment(_rng(seed, trace.trace_id, D_THREAD, (i << 16) + w + 1), mse, mst, fr[w]))
+        return parts
+
+    if pool is None:
+        pool = min(32, os.cpu_count() or 1)
+    units = [u for parts in _pool_map(proc_job, list(range(n)), pool) for u in parts]
+    host_off = np.zeros(nT + 1, np.uint64)
+    host_off[1:] = np.cumsum([u[0].shape[0] for u in units])
+    dpr = np.zeros(nT, np.uint32)
+    dpr[proc_off[:-1]] = trace.devices_per_rank
+    win = np.repeat(trace.region_window, T, axis=1)
+    return Trace(trace_id=trace.trace_id, n_ranks=nT, devices_per_rank=dpr, region_window=np.ascontiguousarray(win),
+                 host_se=np.ascontiguousarray(np.concatenate([u[0] for u in units])),
+                 host_state=np.concatenate([u[1] for u in units]), host_off=host_off,
+                 dev_se=trace.dev_se, dev_tag=trace.dev_tag, dev_off=trace.dev_off,
+                 sorted_by_start=trace.sorted_by_start,
+                 meta={**trace.meta, "proc_off": proc_off, "threads": T})
+
+
+def threaded_large(seed=0x7A1F + 1, scale=1.0, trace_id=1, threads=8, pool=None):
+    """The plain large trace with 8 threads per rank: 64 processes x 8 threads
+    (one master + 7 fork-join workers) x 4 GPUs; 4 nested regions."""
+    t = add_threads(plain_large(seed, scale, trace_id, threads=pool), threads, pool=pool)
+    t.meta.update(workload=f"plain large single trace with {threads} threads per rank, 64 ranks x 4 GPUs x 4 streams")
+    return t
 
 
 # ----------------------------------------------------------------------------
