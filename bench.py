@@ -59,7 +59,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--workload", default="plain",
-                    choices=["plain", "small", "scale", "batched", "batched-full", "serving", "concurrency", "raw"])
+                    choices=["plain", "small", "scale", "batched", "batched-full", "serving", "concurrency", "raw",
+                             "threads"])
     ap.add_argument("--wave-records", type=float, default=3e9, help="batched-full: records per wave")
     ap.add_argument("--traces", type=int, default=4096, help="batched: number of traces")
     ap.add_argument("--ev-hi", type=int, default=None,
@@ -695,6 +696,97 @@ def run_raw(a):
     return 0 if same else 1
 
 
+def run_threads(a):
+    """Host tree with threads: the plain large trace with 8 threads per rank
+    (one host unit per thread; 64 processes x 8 threads x 4 GPUs), ingested
+    from HBM and reduced to the thread tree of every region, one synchronous
+    step per call; against the same step with the paper's tree."""
+    import torch
+    import oracle
+    import paper_2603_26576_b300 as P
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    t = tg.threaded_large(scale=a.scale)
+    po = t.meta["proc_off"]
+    up = lambda x: torch.from_numpy(x).to(dev)  # noqa: E731
+    arr = dict(host_se=up(t.host_se), host_state=up(t.host_state), dev_se=up(t.dev_se), dev_tag=up(t.dev_tag))
+    b, keep = P.batch_from_arrays(t.trace_id, t.devices_per_rank, t.region_window, arr["host_se"],
+                                  arr["host_state"], t.host_off, arr["dev_se"], arr["dev_tag"], t.dev_off,
+                                  P.TALP_GPU_SORTED_BY_START)
+    ctx = P.Context(0)
+    stream = torch.cuda.Stream()
+    R = t.n_regions
+    out_dev = torch.empty(R * 200, dtype=torch.uint8, device=dev)
+
+    def step_threads():
+        P.talp_gpu_ingest_events(ctx.ctx, [b], stream)
+        return P.talp_gpu_thread_metrics(ctx.ctx, t.trace_id, P.TALP_GPU_ALL_REGIONS, po, stream, n_regions=R)
+
+    def step_paper():
+        P.talp_gpu_ingest_events(ctx.ctx, [b], stream)
+        P.talp_gpu_region_metrics_device(ctx.ctx, [t.trace_id], P.TALP_GPU_ALL_REGIONS, out_dev.data_ptr(), stream)
+
+    def timed(fn, k):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    for _ in range(max(a.warmup, 3)):
+        step_threads()
+        step_paper()
+    P.talp_gpu_profile_read(ctx.ctx)
+    l0 = P.talp_gpu_profile_read(ctx.ctx)["kernel_launches"]
+    clocks = Clocks(0)
+    clocks.start()
+    time.sleep(0.3)
+    ms = timed(step_threads, a.steps)
+    ck = clocks.stop()
+    launches = P.talp_gpu_profile_read(ctx.ctx)["kernel_launches"] - l0
+    ms_paper = timed(step_paper, a.steps)
+    got = step_threads()
+    exact = all(g == dict(oracle.thread_metrics(t, r, po), trace_id=t.trace_id, region=r)
+                for r, g in enumerate(got))
+    N = t.n_records
+    peak, peak_kind = measured_peaks()
+    achieved = BYTES_PER_RECORD * N / (ms / 1000.0) / 1e9
+    one = tg.add_threads(tg.plain_large(scale=a.scale, n_ranks=1), 8)
+    c0 = time.perf_counter()
+    for r in range(R):
+        oracle.region_metrics(one, r)
+        oracle.thread_metrics(one, r, one.meta["proc_off"])
+    cpu_s = time.perf_counter() - c0
+    line = {
+        "metric": METRIC, "value": N / (ms / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64", "data": "synthetic (seeded generator; the paper's traces are not available)",
+        "config": {"workload": "plain large trace with 8 threads per rank (64 processes x 8 threads x 4 GPUs x "
+                               "4 streams; 1 master + 7 fork-join workers)"
+                               + ("" if a.scale == 1.0 else f" (scale {a.scale})"),
+                   "records_per_step": N, "host_records": t.n_host,
+                   "form": "talp_gpu_ingest_events (device records, start order) + talp_gpu_thread_metrics of "
+                           "the 4 regions, one synchronous step",
+                   "paper_tree_ms_per_step": ms_paper, "bit_exact_vs_oracle": exact,
+                   "l2": "records (%.1f GB) larger than L2; no flush" % (BYTES_PER_RECORD * N / 1e9)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "whole step (sweep, fix-up, thread tree)",
+                     "kernel_ms": ms, "peak_source": f"{peak_kind} hbm_gbs"},
+        "cpu_baseline": {"value": None if not cpu_s else one.n_records / cpu_s, "unit": UNIT, "cores": 1,
+                         "kind": "oracle", "sample": f"one process of the workload (8 threads, 4 GPUs): device "
+                                                     f"unions, host sums and both trees of the 4 regions, "
+                                                     f"{cpu_s:.2f} s"},
+        "e2e": None, "gpu_launches": launches, "clocks": ck,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0 if exact else 1
+
+
 # ----------------------------------------------------------------- serving
 
 
@@ -960,6 +1052,8 @@ def main():
         return run_batched_full(a)
     if a.workload == "concurrency":
         return run_concurrency(a)
+    if a.workload == "threads":
+        return run_threads(a)
     if a.workload == "raw":
         return run_raw(a)
     if a.workload == "serving":

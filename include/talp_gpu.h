@@ -307,6 +307,53 @@ talp_gpu_status talp_gpu_metrics_combine(talp_gpu_ctx *ctx, const talp_gpu_metri
                                          talp_gpu_metrics *out_host, void *stream);
 
 /*
+ * Host tree with threads (a variant: the paper's host tree, Sec. 4.1
+ * Eqs. 6-8, has one set of host intervals per MPI rank and no thread level).
+ * Ingest the trace with one host unit per thread -- n_ranks = the number of
+ * threads nT, each thread's useful / offload / MPI intervals as its unit's
+ * host records, each thread with its process's windows, the devices on any
+ * unit (normally the master thread's) -- and group the units into processes
+ * with proc_off (host memory, n_procs + 1 entries): process i owns units
+ * proc_off[i] .. proc_off[i+1]-1, T_i >= 1 of them.  With B = U + W per
+ * thread and M_i = the largest B of process i (its busiest thread):
+ *   E         = max over threads (U + W + MPI)            (Eq. 1 over threads)
+ *   pe        = sum U / (E nT)                            (Eq. 6 over threads)
+ *   mpi_pe    = sum_i T_i M_i / (E nT)  = mpi_lb x mpi_ce (Eq. 7, the busiest
+ *     mpi_lb  = sum_i T_i M_i / (nT max_i M_i)             thread standing for
+ *     mpi_ce  = max_i M_i / E                              its process)
+ *   thread_lb = sum B / sum_i T_i M_i                     (Eq. 10's form inside
+ *                                                          each process)
+ *   oe        = sum U / sum B                             (Eq. 8 over threads)
+ * so pe = mpi_pe x thread_lb x oe, and with one thread per process every
+ * value equals talp_gpu_region_metrics' host tree bit for bit.  E is the
+ * same as talp_gpu_region_metrics' (threads as units), so its device tree
+ * holds unchanged.  FP64 on the GPU in the order written; 0/0 reads 1; E = 0
+ * sets TALP_GPU_M_EMPTY with every ratio 1.  Sums are int64: nT x E must
+ * stay below 2^63.
+ * out_host[0] (or out_host[0 .. n_regions-1] with TALP_GPU_ALL_REGIONS),
+ * host memory; synchronises `stream`.
+ * Errors: ENOTFOUND (unknown trace), EINVAL (bad region; proc_off not
+ * starting at 0, not strictly increasing, or not ending at the trace's
+ * n_ranks; invalid records ingested: out_host is still written and its
+ * flags say why), ETIMEDOUT, ECUDA.
+ */
+typedef struct {
+    uint64_t trace_id;
+    uint32_t region;
+    uint32_t flags;                    /* TALP_GPU_M_EMPTY and the status flags */
+    uint32_t n_procs, n_threads;
+    int64_t elapsed_ns;                /* E = max over threads (U + W + MPI) */
+    int64_t sum_useful;                /* sum over threads U */
+    int64_t sum_offload;               /* sum over threads W */
+    int64_t sum_busiest;               /* sum_i T_i M_i */
+    int64_t max_busiest;               /* max_i M_i */
+    double pe, mpi_pe, mpi_lb, mpi_ce, thread_lb, oe;
+} talp_gpu_thread_tree;
+talp_gpu_status talp_gpu_thread_metrics(talp_gpu_ctx *ctx, uint64_t trace_id, uint32_t region,
+                                        const uint32_t *proc_off, uint32_t n_procs,
+                                        talp_gpu_thread_tree *out_host, void *stream);
+
+/*
  * Scalability across runs: POP's second branch, which needs several runs
  * and which TALP leaves to the user (Sec. 3.3).  runs[0 .. n_runs-1] are
  * the metrics of one region (the same region index) of runs of one

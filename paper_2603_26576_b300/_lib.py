@@ -24,7 +24,7 @@ EXPORTED_SYMBOLS = (
     "talp_gpu_create", "talp_gpu_destroy", "talp_gpu_ingest_events", "talp_gpu_region_metrics",
     "talp_gpu_region_metrics_batch", "talp_gpu_region_metrics_device", "talp_gpu_metrics_combine",
     "talp_gpu_concurrency", "talp_gpu_scalability", "talp_gpu_ingest_raw", "talp_gpu_raw_held",
-    "talp_gpu_unit_sums",
+    "talp_gpu_unit_sums", "talp_gpu_thread_metrics",
     "talp_gpu_reset", "talp_gpu_memory", "talp_gpu_profile", "talp_gpu_profile_read", "talp_gpu_reduce_noalloc",
     "talp_gpu_plan_create", "talp_gpu_plan_launch", "talp_gpu_plan_metrics", "talp_gpu_plan_info",
     "talp_gpu_plan_destroy", "talp_gpu_server_create", "talp_gpu_server_open_job", "talp_gpu_server_submit", "talp_gpu_server_submit_raw",
@@ -108,6 +108,17 @@ class talp_gpu_scaling(ctypes.Structure):
                 ("dev_comp_scal", ctypes.c_double), ("dev_global_eff", ctypes.c_double)]
 
 
+THREAD_INT_FIELDS = ("elapsed_ns", "sum_useful", "sum_offload", "sum_busiest", "max_busiest")
+THREAD_RATIO_FIELDS = ("pe", "mpi_pe", "mpi_lb", "mpi_ce", "thread_lb", "oe")
+
+
+class talp_gpu_thread_tree(ctypes.Structure):
+    _fields_ = ([("trace_id", ctypes.c_uint64), ("region", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                 ("n_procs", ctypes.c_uint32), ("n_threads", ctypes.c_uint32)]
+                + [(f, ctypes.c_int64) for f in THREAD_INT_FIELDS]
+                + [(f, ctypes.c_double) for f in THREAD_RATIO_FIELDS])
+
+
 class talp_gpu_metrics(ctypes.Structure):
     _fields_ = ([("trace_id", ctypes.c_uint64), ("region", ctypes.c_uint32), ("flags", ctypes.c_uint32),
                  ("n_ranks", ctypes.c_uint32), ("m_devices", ctypes.c_uint32)]
@@ -153,6 +164,7 @@ def load_library():
         "talp_gpu_metrics_combine": ([P, ctypes.POINTER(talp_gpu_metrics), S, ctypes.POINTER(talp_gpu_metrics), P],
                                      I32),
         "talp_gpu_unit_sums": ([P, U64, U32, P, P, P], I32),
+        "talp_gpu_thread_metrics": ([P, U64, U32, P, U32, ctypes.POINTER(talp_gpu_thread_tree), P], I32),
         "talp_gpu_concurrency": ([P, ctypes.POINTER(talp_gpu_trace_batch), U32, P, P], I32),
         "talp_gpu_scalability": ([P, ctypes.POINTER(talp_gpu_metrics), S, S, U32, ctypes.POINTER(talp_gpu_scaling),
                                   P], I32),
@@ -230,6 +242,29 @@ def talp_gpu_region_metrics(ctx, trace_id, region, stream=None, n_regions=None, 
     out = (talp_gpu_metrics * k)()
     st = load_library().talp_gpu_region_metrics(ctx, trace_id, region, out, _stream(stream))
     res = list(out) if region == TALP_GPU_ALL_REGIONS else out[0]
+    if check:
+        _check(st)
+        return res
+    return st, res
+
+
+def talp_gpu_thread_metrics(ctx, trace_id, region, proc_off, stream=None, n_regions=None, check=True):
+    """Host tree with threads of one region (a dict) or, with
+    region=TALP_GPU_ALL_REGIONS, a list of dicts over the n_regions regions;
+    proc_off (n_procs + 1 entries) groups the trace's host units into
+    processes."""
+    k = n_regions if region == TALP_GPU_ALL_REGIONS else 1
+    if k is None:
+        raise ValueError("n_regions is needed with TALP_GPU_ALL_REGIONS")
+    po = np.ascontiguousarray(proc_off, dtype=np.uint32)
+    if po.ndim != 1 or po.shape[0] < 1:
+        raise ValueError("proc_off needs n_procs + 1 entries")
+    out = (talp_gpu_thread_tree * k)()
+    st = load_library().talp_gpu_thread_metrics(ctx, trace_id, region, po.ctypes.data_as(ctypes.c_void_p),
+                                                po.shape[0] - 1, out, _stream(stream))
+    res = [{f: (float(getattr(o, f)) if t is ctypes.c_double else int(getattr(o, f))) for f, t in o._fields_}
+           for o in out]
+    res = res if region == TALP_GPU_ALL_REGIONS else res[0]
     if check:
         _check(st)
         return res
@@ -594,6 +629,12 @@ class Context:
 
     def metrics_batch(self, trace_ids, region, stream=None):
         return [metrics_to_dict(x) for x in talp_gpu_region_metrics_batch(self.ctx, trace_ids, region, stream)]
+
+    def thread_metrics(self, trace_id, proc_off, region=TALP_GPU_ALL_REGIONS, stream=None, check=True):
+        """Host tree with threads: the trace's host units are threads,
+        grouped into processes by proc_off."""
+        R = self._shapes[int(trace_id)][2]
+        return talp_gpu_thread_metrics(self.ctx, trace_id, region, proc_off, stream, n_regions=R, check=check)
 
     def unit_sums(self, trace_id, region, stream=None):
         n, m, _ = self._shapes[int(trace_id)]

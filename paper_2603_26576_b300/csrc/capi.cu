@@ -1342,6 +1342,63 @@ talp_gpu_status talp_gpu_ingest_raw(talp_gpu_ctx* c, const talp_gpu_raw_batch* r
     return st;
 }
 
+talp_gpu_status talp_gpu_thread_metrics(talp_gpu_ctx* c, uint64_t trace_id, uint32_t region,
+                                        const uint32_t* proc_off, uint32_t n_procs,
+                                        talp_gpu_thread_tree* out_host, void* stream_) {
+    static_assert(sizeof(ThreadOut) == sizeof(talp_gpu_thread_tree), "thread tree record layout");
+    if (!c) return fail(TALP_GPU_EINVAL, "null context");
+    if (!proc_off || !out_host) return fail(TALP_GPU_EINVAL, "null argument");
+    if (n_procs == 0) return fail(TALP_GPU_EINVAL, "no processes");
+    auto it = c->traces.find(trace_id);
+    if (it == c->traces.end()) return fail(TALP_GPU_ENOTFOUND, "unknown trace id " + std::to_string(trace_id));
+    TraceState* t = it->second;
+    if (proc_off[0] != 0 || proc_off[n_procs] != t->n)
+        return fail(TALP_GPU_EINVAL, "proc_off must run from 0 to the trace's n_ranks");
+    for (uint32_t i = 0; i < n_procs; ++i)
+        if (proc_off[i + 1] <= proc_off[i]) return fail(TALP_GPU_EINVAL, "a process without threads in proc_off");
+    std::vector<uint32_t> regions;
+    if (region == TALP_GPU_ALL_REGIONS) {
+        for (uint32_t r = 0; r < t->R; ++r) regions.push_back(r);
+    } else {
+        if (region >= t->R) return fail(TALP_GPU_EINVAL, "region out of range");
+        regions.push_back(region);
+    }
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    TALP_CUDA(cudaSetDevice(c->device));
+    const size_t nj = regions.size();
+    const size_t jb = align_up(sizeof(ThreadJob) * nj, 256);
+    const size_t pbytes = sizeof(uint32_t) * (static_cast<size_t>(n_procs) + 1);
+    const size_t ob = align_up(jb + pbytes, 256);
+    if (c->ws_used) TALP_CUDA(cudaStreamWaitEvent(stream, c->ev_ws, 0));
+    TALP_TRY(grow(c, c->ws, ob + sizeof(ThreadOut) * nj));
+    char* ws = static_cast<char*>(c->ws.p);
+    const uint32_t* dpo = reinterpret_cast<const uint32_t*>(ws + jb);
+    ThreadOut* dout = reinterpret_cast<ThreadOut*>(ws + ob);
+    TALP_CUDA(cudaEventSynchronize(c->ev_upf));
+    TALP_TRY(grow_pinned(c->upf, jb + pbytes));
+    char* up = static_cast<char*>(c->upf.p);
+    for (size_t k = 0; k < nj; ++k)
+        reinterpret_cast<ThreadJob*>(up)[k] = ThreadJob{t->tdev, dout + k, dpo, n_procs, regions[k]};
+    memcpy(up + jb, proc_off, pbytes);
+    TALP_CUDA(cudaMemcpyAsync(ws, up, jb + pbytes, cudaMemcpyHostToDevice, stream));
+    TALP_CUDA(cudaEventRecord(c->ev_upf, stream));
+    TALP_CUDA(launch_thread_tree(reinterpret_cast<const ThreadJob*>(ws), static_cast<uint32_t>(nj), stream));
+    ++c->kernel_launches;
+    TALP_TRY(grow_pinned(c->down, sizeof(ThreadOut) * nj));
+    TALP_CUDA(cudaMemcpyAsync(c->down.p, dout, sizeof(ThreadOut) * nj, cudaMemcpyDeviceToHost, stream));
+    TALP_CUDA(cudaEventRecord(c->ev_ws, stream));
+    c->ws_used = true;
+    TALP_CUDA(cudaStreamSynchronize(stream));
+    memcpy(out_host, c->down.p, sizeof(ThreadOut) * nj);
+    for (size_t k = 0; k < nj; ++k) {
+        const uint32_t f = out_host[k].flags;
+        if (f & TALP_GPU_M_TIMEOUT) return fail(TALP_GPU_ETIMEDOUT, "a device-side wait ran out during ingest");
+        if (f & (TALP_GPU_M_INVALID | TALP_GPU_M_UNSORTED))
+            return fail(TALP_GPU_EINVAL, "invalid or out-of-order records were ingested");
+    }
+    return TALP_GPU_OK;
+}
+
 talp_gpu_status talp_gpu_scalability(talp_gpu_ctx* c, const talp_gpu_metrics* runs, size_t n_runs, size_t ref,
                                      uint32_t mode, talp_gpu_scaling* out_host, void* stream_) {
     static_assert(sizeof(ScaleOut) == sizeof(talp_gpu_scaling), "scaling record layout");

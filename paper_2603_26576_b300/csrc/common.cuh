@@ -74,6 +74,23 @@ struct ScaleOut {
     double speedup, host_comp_scal, host_global_eff, dev_comp_scal, dev_global_eff;
 };
 
+// Host tree with threads of one region; mirrors talp_gpu_thread_metrics.
+struct ThreadOut {
+    uint64_t trace_id;
+    uint32_t region, flags, n_procs, n_threads;
+    int64_t elapsed_ns, sum_useful, sum_offload, sum_busiest, max_busiest;
+    double pe, mpi_pe, mpi_lb, mpi_ce, thread_lb, oe;
+};
+
+// One (trace, region) of the thread tree; proc_off[0 .. n_procs] (device
+// memory) groups the trace's host units into processes.
+struct ThreadJob {
+    const TraceDev* t;
+    ThreadOut* out;
+    const uint32_t* proc_off;
+    uint32_t n_procs, region;
+};
+
 struct FinalizeJob {
     const TraceDev* t;
     MetricsOut* out;

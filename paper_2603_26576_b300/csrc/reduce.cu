@@ -290,6 +290,99 @@ __global__ void __launch_bounds__(256) finalize_kernel(const FinalizeJob* __rest
     *job.out = o;
 }
 
+// ------------------------------------------------------------- thread tree
+//
+// Host tree with threads.  The paper's host tree has one set of intervals per
+// MPI rank; here every thread is a host unit of the trace and proc_off groups
+// the units into processes.  One CTA per (trace, region).  A warp takes one
+// process at a time, its lanes over the process's threads, and reduces their
+// busy time B = U + W to its maximum M_i (the busiest thread) together with
+// the sums of U and W and the largest U + W + MPI.  The CTA then reduces
+//   E = max over threads (U + W + MPI), sum U, sum W, sum_i T_i M_i, max_i M_i
+// and forms, in FP64 in this order (0/0 reads 1, E = 0 gives EMPTY with
+// every ratio 1):
+//   PE = sum U / (E nT)          MPI PE = sum T M / (E nT)
+//   MPI LB = sum T M / (nT max M)   MPI CE = max M / E
+//   thread LB = sum B / sum T M     OE = sum U / sum B
+// With one thread per process these are the Eqs. 6-8 values of finalize.
+__global__ void __launch_bounds__(256) thread_tree_kernel(const ThreadJob* __restrict__ jobs) {
+    __shared__ long long sh[32];
+    const ThreadJob job = jobs[blockIdx.x];
+    const TraceDev t = *job.t;
+    const uint32_t r = job.region, R = t.R;
+    const int lane = threadIdx.x & 31;
+    const uint32_t nw = blockDim.x >> 5;
+    auto add = [](long long a, long long b) { return a + b; };
+    auto mx = [](long long a, long long b) { return a > b ? a : b; };
+
+    long long E = 0, sU = 0, sW = 0, sTM = 0, maxM = 0;
+    for (uint32_t i = threadIdx.x >> 5; i < job.n_procs; i += nw) {
+        const uint32_t u0 = job.proc_off[i], u1 = job.proc_off[i + 1];
+        int64_t e = 0, pu = 0, pw = 0, m = 0;
+        for (uint32_t u = u0 + lane; u < u1; u += 32) {
+            const int64_t* h = t.hsum + (static_cast<uint64_t>(u) * R + r) * 3;
+            const int64_t U = h[0], W = h[1], P = h[2];
+            e = max64(e, U + W + P);
+            pu += U;
+            pw += W;
+            m = max64(m, U + W);
+        }
+        e = warp_max64(e);
+        pu = warp_sum64(pu);
+        pw = warp_sum64(pw);
+        m = warp_max64(m);
+        if (lane == 0) {
+            E = mx(E, e);
+            sU += pu;
+            sW += pw;
+            sTM += static_cast<long long>(u1 - u0) * m;
+            maxM = mx(maxM, m);
+        }
+    }
+    E = block_reduce<long long>(E, mx, sh);
+    sU = block_reduce<long long>(sU, add, sh);
+    sW = block_reduce<long long>(sW, add, sh);
+    sTM = block_reduce<long long>(sTM, add, sh);
+    maxM = block_reduce<long long>(maxM, mx, sh);
+    if (threadIdx.x != 0) return;
+
+    const int64_t nT = job.proc_off[job.n_procs];
+    uint32_t fl = 0;
+    const uint32_t st = *t.status;
+    if (st & (ST_BAD_END | ST_BAD_KIND)) fl |= 0x100u;
+    if (st & ST_UNSORTED) fl |= 0x200u;
+    if (st & ST_TIMEOUT) fl |= 0x400u;
+    ThreadOut o;
+    o.trace_id = t.trace_id;
+    o.region = r;
+    o.n_procs = job.n_procs;
+    o.n_threads = static_cast<uint32_t>(nT);
+    o.elapsed_ns = E;
+    o.sum_useful = sU;
+    o.sum_offload = sW;
+    o.sum_busiest = sTM;
+    o.max_busiest = maxM;
+    if (E == 0) {
+        fl |= 0x1u;
+        o.pe = o.mpi_pe = o.mpi_lb = o.mpi_ce = o.thread_lb = o.oe = 1.0;
+    } else {
+        o.pe = ratio_k(sU, E, nT);
+        o.mpi_pe = ratio_k(sTM, E, nT);
+        o.mpi_lb = ratio_k(sTM, nT, maxM);
+        o.mpi_ce = ratio(maxM, E);
+        o.thread_lb = ratio(sU + sW, sTM);
+        o.oe = ratio(sU, sU + sW);
+    }
+    o.flags = fl;
+    *job.out = o;
+}
+
+cudaError_t launch_thread_tree(const ThreadJob* jobs, uint32_t n_jobs, cudaStream_t stream) {
+    if (n_jobs == 0) return cudaSuccess;
+    thread_tree_kernel<<<n_jobs, 256, 0, stream>>>(jobs);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- combine
 //
 // Aggregates of one region computed on disjoint shards of a trace (whole

@@ -1,0 +1,127 @@
+"""Host tree with threads on the GPU: every integer aggregate and ratio of
+talp_gpu_thread_metrics equals the oracle's bit for bit -- tiny traces cut into
+processes at random, fork-join threaded traces (processes of 1 to 100
+threads, more processes than the kernel has warps), one thread per process
+(equal to the GPU's own host tree of Eqs. 6-8), and the plain large trace
+with 8 threads per rank at full size -- and bad process tables are refused."""
+import numpy as np
+import pytest
+
+import oracle
+import tracegen as tg
+from gpu_common import bits, make_ctx
+
+pytestmark = pytest.mark.gpu
+
+INTS = ("elapsed_ns", "sum_useful", "sum_offload", "sum_busiest", "max_busiest", "n_threads")
+
+
+def assert_thread_equal(g, o, tag):
+    for k in INTS:
+        assert g[k] == o[k], (tag, k, g[k], o[k])
+    for k in oracle.THREAD_RATIO_FIELDS:
+        assert bits(g[k]) == bits(o[k]), (tag, k, repr(g[k]), repr(o[k]))
+    assert g["flags"] == o["flags"] and g["n_procs"] == o["n_procs"], (tag, g["flags"], o["flags"])
+
+
+def check_trace(c, t, po, tag):
+    res = c.thread_metrics(t.trace_id, po)
+    assert len(res) == t.n_regions
+    for r in range(t.n_regions):
+        assert res[r]["trace_id"] == t.trace_id and res[r]["region"] == r
+        assert_thread_equal(res[r], oracle.thread_metrics(t, r, po), (tag, r))
+        one = c.thread_metrics(t.trace_id, po, region=r)
+        assert_thread_equal(one, res[r], (tag, "single region", r))
+
+
+def _groups(rng, n):
+    cuts = np.sort(rng.choice(np.arange(1, n), size=int(rng.integers(0, n)), replace=False)) if n > 1 else []
+    return np.concatenate([[0], cuts, [n]]).astype(np.uint32)
+
+
+def test_tiny_random_processes():
+    c = make_ctx()
+    traces = [tg.tiny_trace(s, trace_id=s, max_ranks=7) for s in range(60)]
+    c.ingest(traces)
+    for s, t in enumerate(traces):
+        check_trace(c, t, _groups(np.random.default_rng(s), t.n_ranks), ("tiny", s))
+    c.close()
+
+
+def test_one_thread_per_process_is_the_host_tree():
+    c = make_ctx()
+    traces = [tg.tiny_trace(s, trace_id=s) for s in range(30)]
+    traces.append(tg.random_trace(5, trace_id=99, n_ranks=40, devices_per_rank=2, dev_events=300, host_events=300,
+                                  n_regions=4))
+    c.ingest(traces)
+    pairs = (("pe", "host_pe"), ("mpi_pe", "host_mpi_pe"), ("mpi_lb", "host_mpi_lb"), ("mpi_ce", "host_mpi_ce"),
+             ("oe", "host_oe"))
+    for t in traces:
+        th = c.thread_metrics(t.trace_id, np.arange(t.n_ranks + 1))
+        host = c.metrics(t.trace_id)
+        for r in range(t.n_regions):
+            assert th[r]["elapsed_ns"] == host[r]["elapsed_ns"] and th[r]["thread_lb"] == 1.0
+            for a, b in pairs:
+                assert bits(th[r][a]) == bits(host[r][b]), (t.trace_id, r, a)
+    c.close()
+
+
+@pytest.mark.parametrize("threads", [[1, 4, 2], [8, 8, 8, 8], [100, 3], [33, 1, 64, 2, 31, 32]])
+def test_fork_join_threads(threads):
+    c = make_ctx()
+    base = tg.random_trace(len(threads), trace_id=7, n_ranks=len(threads), devices_per_rank=2, dev_events=800,
+                           host_events=600, n_regions=4)
+    t = tg.add_threads(base, threads, seed=11)
+    c.ingest([t])
+    check_trace(c, t, t.meta["proc_off"], threads)
+    c.close()
+
+
+def test_more_processes_than_warps():
+    c = make_ctx()
+    base = tg.random_trace(3, trace_id=8, n_ranks=700, devices_per_rank=[1] + [0] * 699, dev_events=200,
+                           host_events=30, n_regions=2)
+    t = tg.add_threads(base, [1 + k % 5 for k in range(700)], seed=12)
+    c.ingest([t])
+    check_trace(c, t, t.meta["proc_off"], "700 processes")
+    c.close()
+
+
+def test_bad_process_tables():
+    import paper_2603_26576_b300 as P
+    c = make_ctx()
+    t = tg.add_threads(tg.random_trace(1, trace_id=3, n_ranks=3, dev_events=100, host_events=100, n_regions=2),
+                       [2, 1, 3])
+    c.ingest([t])
+    n = t.n_ranks
+    for po in ([1, 3, 6], [0, 3, 5], [0, 3, 3, 6], [0, 4, 2, 6], [0], [0, 6, 7]):
+        st, _ = P.talp_gpu_thread_metrics(c.ctx, t.trace_id, 0, po, check=False)
+        assert st == -1, po
+    st, _ = P.talp_gpu_thread_metrics(c.ctx, t.trace_id, 2, [0, n], check=False)
+    assert st == -1                                            # region out of range
+    st, _ = P.talp_gpu_thread_metrics(c.ctx, 12345, 0, [0, n], check=False)
+    assert st == -5                                            # unknown trace
+    good = P.talp_gpu_thread_metrics(c.ctx, t.trace_id, 1, [0, n])
+    assert_thread_equal(good, oracle.thread_metrics(t, 1, [0, n]), "one process")
+    c.close()
+
+
+def test_full_size_threaded_large():
+    """The plain large trace (64 ranks x 4 GPUs, 576M records) with 8 threads
+    per rank (213M host records more), ingested from device memory with the
+    start-order flag: every region equal to the oracle."""
+    import torch
+    import paper_2603_26576_b300 as P
+    t = tg.threaded_large()
+    dev = torch.device("cuda", 0)
+    arr = dict(host_se=torch.from_numpy(t.host_se).to(dev), host_state=torch.from_numpy(t.host_state).to(dev),
+               dev_se=torch.from_numpy(t.dev_se).to(dev), dev_tag=torch.from_numpy(t.dev_tag).to(dev))
+    c = P.Context(0)
+    c.ingest([t], flags=P.TALP_GPU_SORTED_BY_START, arrays=[arr])
+    res = c.thread_metrics(t.trace_id, t.meta["proc_off"])
+    c.close()
+    del arr
+    torch.cuda.empty_cache()
+    for r in range(t.n_regions):
+        assert_thread_equal(res[r], oracle.thread_metrics(t, r, t.meta["proc_off"]), ("full", r))
+        assert res[r]["thread_lb"] < 0.9 and res[r]["n_threads"] == 512
