@@ -26,6 +26,7 @@ constexpr int K = kConcLevels;
 constexpr int kItems = 8;
 constexpr int kTile = 32 * kItems;
 constexpr int kWarps = 8;
+static_assert(K == 8 && kItems == 8, "a lane's list is its 8 records sorted by an 8-input network");
 
 // Sorted-descending list of the K largest ends seen.  Two widths: absolute
 // int64 (INT64_MIN: none) for the state carried between tiles and chunks,
@@ -68,6 +69,19 @@ __device__ __forceinline__ void merge_top(TopK<T>& x, const TopK<T>& y) {
                 x.v[i] = hi;
                 x.v[i + w] = lo;
             }
+    }
+}
+
+// Sorts 8 values into descending order: the 19-comparator network for 8
+// inputs (Knuth, TAOCP vol. 3, 5.3.4), checked on all 2^8 0-1 inputs.
+__device__ __forceinline__ void sort8_desc(uint32_t (&v)[8]) {
+    constexpr int net[19][2] = {{0, 2}, {1, 3}, {4, 6}, {5, 7}, {0, 4}, {1, 5}, {2, 6}, {3, 7}, {0, 1}, {2, 3},
+                                {4, 5}, {6, 7}, {2, 4}, {3, 5}, {1, 4}, {3, 6}, {1, 2}, {3, 4}, {5, 6}};
+#pragma unroll
+    for (int c = 0; c < 19; ++c) {
+        const uint32_t x = v[net[c][0]], y = v[net[c][1]];
+        v[net[c][0]] = x > y ? x : y;
+        v[net[c][1]] = x > y ? y : x;
     }
 }
 
@@ -307,13 +321,13 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
         uint32_t s[kItems], e[kItems];
         uint32_t kmask = 0;
         bool fits = true;
+        // the lane's own top-K lists: its kItems == K ends sorted (0 = none)
         TopK<uint32_t> la, lk;
-        clear_top(la);
-        clear_top(lk);
 #pragma unroll
         for (int i = 0; i < kItems; ++i) {
             const int q = lane * kItems + i;
             s[i] = e[i] = 0xFFFFFFFFu;
+            la.v[i] = lk.v[i] = 0u;
             if (q < n) {
                 int64_t sa64, ea64;
                 clipped(stg[wid], q, dv, sa64, ea64);
@@ -323,10 +337,12 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
                 e[i] = rel32(ea64, s0);
                 const bool isK = kind_of(stg[wid], q) == 0u;
                 kmask |= isK ? 1u << i : 0u;
-                insert_top(la, e[i]);
-                if (isK) insert_top(lk, e[i]);
+                la.v[i] = e[i];
+                lk.v[i] = isK ? e[i] : 0u;
             }
         }
+        sort8_desc(la.v);
+        sort8_desc(lk.v);
 #pragma unroll
         for (int i = 0; i < K; ++i) fits &= near32(sa.v[i], s0) && near32(sk.v[i], s0);
         if (__all_sync(0xFFFFFFFFu, fits)) {
@@ -346,8 +362,11 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
             merge_top(xa, ta);
             merge_top(xk, tk);
             // a lane's gaps in the tile are disjoint and lie within 2^32 - 1 ns
-            // of s0, so its level sums of the tile fit 32 bits
-            uint32_t acc_a[K], acc_k[K];
+            // of s0, so its level sums of the tile fit 32 bits.  The level-k
+            // time of a gap [s, hi) is min(max(E_k, s), max(hi, s)) - s; the
+            // s terms are summed once (S) and taken off at the end, which is
+            // exact in wrapping 32-bit arithmetic because the results fit.
+            uint32_t acc_a[K], acc_k[K], S = 0;
 #pragma unroll
             for (int k = 0; k < K; ++k) acc_a[k] = acc_k[k] = 0;
             const uint32_t bnd = rel32(dv.b, s0);
@@ -361,15 +380,20 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
                     if (kmask & (1u << i)) insert_top(xk, e[i]);
                     const uint32_t ns = (i + 1 < kItems && q + 1 < n) ? s[i + 1] : nxt;
                     // the gap [s_i, min(next start, window end)) at level k
-                    // lasts until E_k: min(gap, max(E_k, s_i) - s_i)
-                    const uint32_t hi = tmin(ns, bnd);
-                    const uint32_t gap = hi > s[i] ? hi - s[i] : 0u;
+                    // lasts until E_k
+                    const uint32_t hc = tmax(tmin(ns, bnd), s[i]);
+                    S += s[i];
 #pragma unroll
                     for (int k = 0; k < K; ++k) {
-                        acc_a[k] += tmin(gap, tmax(xa.v[k], s[i]) - s[i]);
-                        acc_k[k] += tmin(gap, tmax(xk.v[k], s[i]) - s[i]);
+                        acc_a[k] += tmin(tmax(xa.v[k], s[i]), hc);
+                        acc_k[k] += tmin(tmax(xk.v[k], s[i]), hc);
                     }
                 }
+            }
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                acc_a[k] -= S;
+                acc_k[k] -= S;
             }
 #pragma unroll
             for (int k = 0; k < K; ++k) {   // warp sums in 16-bit halves (no overflow)
