@@ -352,6 +352,15 @@ typedef struct {
 talp_gpu_status talp_gpu_thread_metrics(talp_gpu_ctx *ctx, uint64_t trace_id, uint32_t region,
                                         const uint32_t *proc_off, uint32_t n_procs,
                                         talp_gpu_thread_tree *out_host, void *stream);
+/*
+ * Stream-ordered variant: writes the records to device memory out_device (one
+ * per region, 8-byte aligned) without synchronising; proc_off is still host
+ * memory, read during the call.  Record problems are reported only through
+ * the flags of the written records.
+ */
+talp_gpu_status talp_gpu_thread_metrics_device(talp_gpu_ctx *ctx, uint64_t trace_id, uint32_t region,
+                                               const uint32_t *proc_off, uint32_t n_procs,
+                                               talp_gpu_thread_tree *out_device, void *stream);
 
 /*
  * Scalability across runs: POP's second branch, which needs several runs

@@ -24,7 +24,7 @@ EXPORTED_SYMBOLS = (
     "talp_gpu_create", "talp_gpu_destroy", "talp_gpu_ingest_events", "talp_gpu_region_metrics",
     "talp_gpu_region_metrics_batch", "talp_gpu_region_metrics_device", "talp_gpu_metrics_combine",
     "talp_gpu_concurrency", "talp_gpu_scalability", "talp_gpu_ingest_raw", "talp_gpu_raw_held",
-    "talp_gpu_unit_sums", "talp_gpu_thread_metrics",
+    "talp_gpu_unit_sums", "talp_gpu_thread_metrics", "talp_gpu_thread_metrics_device",
     "talp_gpu_reset", "talp_gpu_memory", "talp_gpu_profile", "talp_gpu_profile_read", "talp_gpu_reduce_noalloc",
     "talp_gpu_plan_create", "talp_gpu_plan_launch", "talp_gpu_plan_metrics", "talp_gpu_plan_info",
     "talp_gpu_plan_destroy", "talp_gpu_server_create", "talp_gpu_server_open_job", "talp_gpu_server_submit", "talp_gpu_server_submit_raw",
@@ -165,6 +165,7 @@ def load_library():
                                      I32),
         "talp_gpu_unit_sums": ([P, U64, U32, P, P, P], I32),
         "talp_gpu_thread_metrics": ([P, U64, U32, P, U32, ctypes.POINTER(talp_gpu_thread_tree), P], I32),
+        "talp_gpu_thread_metrics_device": ([P, U64, U32, P, U32, P, P], I32),
         "talp_gpu_concurrency": ([P, ctypes.POINTER(talp_gpu_trace_batch), U32, P, P], I32),
         "talp_gpu_scalability": ([P, ctypes.POINTER(talp_gpu_metrics), S, S, U32, ctypes.POINTER(talp_gpu_scaling),
                                   P], I32),
@@ -269,6 +270,22 @@ def talp_gpu_thread_metrics(ctx, trace_id, region, proc_off, stream=None, n_regi
         _check(st)
         return res
     return st, res
+
+
+def talp_gpu_thread_metrics_device(ctx, trace_id, region, proc_off, out_device_ptr, stream=None):
+    """Stream-ordered thread tree into device memory (one talp_gpu_thread_tree
+    per region at out_device_ptr)."""
+    po = np.ascontiguousarray(proc_off, dtype=np.uint32)
+    _check(load_library().talp_gpu_thread_metrics_device(ctx, trace_id, region, po.ctypes.data_as(ctypes.c_void_p),
+                                                         po.shape[0] - 1, out_device_ptr, _stream(stream)))
+
+
+def thread_tree_from_bytes(buf) -> list:
+    """talp_gpu_thread_tree records (as dicts) from their raw bytes."""
+    n = len(buf) // ctypes.sizeof(talp_gpu_thread_tree)
+    arr = (talp_gpu_thread_tree * n).from_buffer_copy(bytes(buf[: n * ctypes.sizeof(talp_gpu_thread_tree)]))
+    return [{f: (float(getattr(o, f)) if t is ctypes.c_double else int(getattr(o, f))) for f, t in o._fields_}
+            for o in arr]
 
 
 def talp_gpu_region_metrics_batch(ctx, trace_ids, region, stream=None, check=True):

@@ -1342,12 +1342,12 @@ talp_gpu_status talp_gpu_ingest_raw(talp_gpu_ctx* c, const talp_gpu_raw_batch* r
     return st;
 }
 
-talp_gpu_status talp_gpu_thread_metrics(talp_gpu_ctx* c, uint64_t trace_id, uint32_t region,
-                                        const uint32_t* proc_off, uint32_t n_procs,
-                                        talp_gpu_thread_tree* out_host, void* stream_) {
+static talp_gpu_status thread_tree_common(talp_gpu_ctx* c, uint64_t trace_id, uint32_t region,
+                                          const uint32_t* proc_off, uint32_t n_procs, ThreadOut* out_dev_user,
+                                          talp_gpu_thread_tree* out_host, cudaStream_t stream) {
     static_assert(sizeof(ThreadOut) == sizeof(talp_gpu_thread_tree), "thread tree record layout");
     if (!c) return fail(TALP_GPU_EINVAL, "null context");
-    if (!proc_off || !out_host) return fail(TALP_GPU_EINVAL, "null argument");
+    if (!proc_off || (!out_host && !out_dev_user)) return fail(TALP_GPU_EINVAL, "null argument");
     if (n_procs == 0) return fail(TALP_GPU_EINVAL, "no processes");
     auto it = c->traces.find(trace_id);
     if (it == c->traces.end()) return fail(TALP_GPU_ENOTFOUND, "unknown trace id " + std::to_string(trace_id));
@@ -1363,7 +1363,6 @@ talp_gpu_status talp_gpu_thread_metrics(talp_gpu_ctx* c, uint64_t trace_id, uint
         if (region >= t->R) return fail(TALP_GPU_EINVAL, "region out of range");
         regions.push_back(region);
     }
-    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
     TALP_CUDA(cudaSetDevice(c->device));
     const size_t nj = regions.size();
     const size_t jb = align_up(sizeof(ThreadJob) * nj, 256);
@@ -1373,7 +1372,8 @@ talp_gpu_status talp_gpu_thread_metrics(talp_gpu_ctx* c, uint64_t trace_id, uint
     TALP_TRY(grow(c, c->ws, ob + sizeof(ThreadOut) * nj));
     char* ws = static_cast<char*>(c->ws.p);
     const uint32_t* dpo = reinterpret_cast<const uint32_t*>(ws + jb);
-    ThreadOut* dout = reinterpret_cast<ThreadOut*>(ws + ob);
+    ThreadOut* res = reinterpret_cast<ThreadOut*>(ws + ob);
+    ThreadOut* dout = out_dev_user ? out_dev_user : res;
     TALP_CUDA(cudaEventSynchronize(c->ev_upf));
     TALP_TRY(grow_pinned(c->upf, jb + pbytes));
     char* up = static_cast<char*>(c->upf.p);
@@ -1384,8 +1384,13 @@ talp_gpu_status talp_gpu_thread_metrics(talp_gpu_ctx* c, uint64_t trace_id, uint
     TALP_CUDA(cudaEventRecord(c->ev_upf, stream));
     TALP_CUDA(launch_thread_tree(reinterpret_cast<const ThreadJob*>(ws), static_cast<uint32_t>(nj), stream));
     ++c->kernel_launches;
+    if (out_dev_user) {
+        TALP_CUDA(cudaEventRecord(c->ev_ws, stream));
+        c->ws_used = true;
+        return TALP_GPU_OK;
+    }
     TALP_TRY(grow_pinned(c->down, sizeof(ThreadOut) * nj));
-    TALP_CUDA(cudaMemcpyAsync(c->down.p, dout, sizeof(ThreadOut) * nj, cudaMemcpyDeviceToHost, stream));
+    TALP_CUDA(cudaMemcpyAsync(c->down.p, res, sizeof(ThreadOut) * nj, cudaMemcpyDeviceToHost, stream));
     TALP_CUDA(cudaEventRecord(c->ev_ws, stream));
     c->ws_used = true;
     TALP_CUDA(cudaStreamSynchronize(stream));
@@ -1397,6 +1402,23 @@ talp_gpu_status talp_gpu_thread_metrics(talp_gpu_ctx* c, uint64_t trace_id, uint
             return fail(TALP_GPU_EINVAL, "invalid or out-of-order records were ingested");
     }
     return TALP_GPU_OK;
+}
+
+talp_gpu_status talp_gpu_thread_metrics(talp_gpu_ctx* c, uint64_t trace_id, uint32_t region,
+                                        const uint32_t* proc_off, uint32_t n_procs,
+                                        talp_gpu_thread_tree* out_host, void* stream) {
+    if (!out_host) return fail(TALP_GPU_EINVAL, "null out");
+    return thread_tree_common(c, trace_id, region, proc_off, n_procs, nullptr, out_host,
+                              static_cast<cudaStream_t>(stream));
+}
+
+talp_gpu_status talp_gpu_thread_metrics_device(talp_gpu_ctx* c, uint64_t trace_id, uint32_t region,
+                                               const uint32_t* proc_off, uint32_t n_procs,
+                                               talp_gpu_thread_tree* out_device, void* stream) {
+    if (!out_device) return fail(TALP_GPU_EINVAL, "null out");
+    if ((reinterpret_cast<uintptr_t>(out_device) & 7u) != 0) return fail(TALP_GPU_EINVAL, "out_device misaligned");
+    return thread_tree_common(c, trace_id, region, proc_off, n_procs, reinterpret_cast<ThreadOut*>(out_device),
+                              nullptr, static_cast<cudaStream_t>(stream));
 }
 
 talp_gpu_status talp_gpu_scalability(talp_gpu_ctx* c, const talp_gpu_metrics* runs, size_t n_runs, size_t ref,

@@ -87,6 +87,33 @@ def test_more_processes_than_warps():
     c.close()
 
 
+def test_stream_ordered_variant():
+    """talp_gpu_thread_metrics_device writes the same records to device memory
+    without synchronising (here on a side stream)."""
+    import torch
+    import paper_2603_26576_b300 as P
+    c = make_ctx()
+    t = tg.add_threads(tg.random_trace(2, trace_id=4, n_ranks=5, dev_events=300, host_events=400, n_regions=3),
+                       [3, 1, 4, 1, 5])
+    po = t.meta["proc_off"]
+    stream = torch.cuda.Stream()
+    c.ingest([t], stream=stream.cuda_stream)
+    rec = __import__("ctypes").sizeof(P.talp_gpu_thread_tree)
+    out = torch.zeros(3 * rec + 8, dtype=torch.uint8, device="cuda")
+    P.talp_gpu_thread_metrics_device(c.ctx, t.trace_id, P.TALP_GPU_ALL_REGIONS, po, out.data_ptr() + 8,
+                                     stream.cuda_stream)
+    stream.synchronize()
+    got = P.thread_tree_from_bytes(out[8:].cpu().numpy().tobytes())
+    assert got == c.thread_metrics(t.trace_id, po)
+    for r in range(3):
+        assert_thread_equal(got[r], oracle.thread_metrics(t, r, po), ("device", r))
+    st = P.load_library().talp_gpu_thread_metrics_device(c.ctx, t.trace_id, 0,
+                                                         np.ascontiguousarray(po).ctypes.data, len(po) - 1,
+                                                         out.data_ptr() + 4, None)
+    assert st == -1                                            # misaligned
+    c.close()
+
+
 def test_bad_process_tables():
     import paper_2603_26576_b300 as P
     c = make_ctx()
