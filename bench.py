@@ -172,19 +172,27 @@ class Clocks:
         self.proc = None
         self.lines = []
 
+    # The samples go to a temporary file, read at stop(): a Python thread
+    # reading a pipe from nvidia-smi slowed a host-synchronising step by ~15%.
+    def _read_file(self):
+        self.out.seek(0)
+        return [ln.strip() for ln in self.out.read().splitlines() if ln.strip()]
+
     def start(self):
+        import tempfile
         try:
+            self.out = tempfile.TemporaryFile(mode="w+")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.th = threading.Thread(target=self._read, daemon=True)
-            self.th.start()
+                                         stdout=self.out, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
-
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            return
+        # nvidia-smi's own start (NVML initialisation) stalls a process that
+        # synchronises with the GPU for a few hundred ms: time nothing before
+        # it has settled (the file is read only after nvidia-smi has exited,
+        # as the two share its offset)
+        time.sleep(1.0)
 
     def stop(self):
         if self.proc is None:
@@ -194,7 +202,9 @@ class Clocks:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        self.th.join(timeout=2)
+            self.proc.wait(timeout=5)
+        self.lines = self._read_file()
+        self.out.close()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
@@ -328,15 +338,14 @@ def run_batched(a):
     plan = ctx.plan(ts, arrays, flags=P.TALP_GPU_SORTED_BY_START, plan_flags=P.TALP_GPU_PLAN_AUTOTUNE)
     plan_s = time.time() - t1
     info = plan.info()
+    clocks = Clocks(0)
+    clocks.start()
     for _ in range(max(a.warmup, 3)):
         plan.launch(stream)
     torch.cuda.synchronize()
     batched = plan.metrics(stream)
     P.talp_gpu_profile_read(ctx.ctx)
     l0 = P.talp_gpu_profile_read(ctx.ctx)["kernel_launches"]
-    clocks = Clocks(0)
-    clocks.start()
-    time.sleep(0.3)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -535,13 +544,12 @@ def run_concurrency(a):
     ctx = P.Context(0)
     stream = torch.cuda.Stream()
     region = 0
+    clocks = Clocks(0)
+    clocks.start()
     for _ in range(max(a.warmup, 3)):
         res = P.talp_gpu_concurrency(ctx.ctx, b, region, stream)
     P.talp_gpu_profile_read(ctx.ctx)
     l0 = P.talp_gpu_profile_read(ctx.ctx)["kernel_launches"]
-    clocks = Clocks(0)
-    clocks.start()
-    time.sleep(0.3)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -650,17 +658,17 @@ def run_raw(a):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / k
 
-    for _ in range(max(a.warmup, 3)):
-        step_raw()
-        step_lanes()
-    P.talp_gpu_profile_read(ctx.ctx)
-    l0 = P.talp_gpu_profile_read(ctx.ctx)["kernel_launches"]
     clocks = Clocks(0)
     clocks.start()
-    time.sleep(0.3)
+    for _ in range(max(a.warmup, 3)):
+        step_raw()
+    P.talp_gpu_profile_read(ctx.ctx)
+    l0 = P.talp_gpu_profile_read(ctx.ctx)["kernel_launches"]
     ms = timed(step_raw, a.steps)
     ck = clocks.stop()
     launches = P.talp_gpu_profile_read(ctx.ctx)["kernel_launches"] - l0 + a.steps
+    for _ in range(max(a.warmup, 3)):
+        step_lanes()
     ms_lanes = timed(step_lanes, a.steps)
     got = P.talp_gpu_region_metrics(ctx.ctx, t.trace_id, P.TALP_GPU_ALL_REGIONS, stream, n_regions=R)
     lane_res = P.talp_gpu_region_metrics(ctx.ctx, t.trace_id + 1, P.TALP_GPU_ALL_REGIONS, stream, n_regions=R)
@@ -739,14 +747,13 @@ def run_threads(a):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / k
 
-    for _ in range(max(a.warmup, 3)):
-        step_threads()
-        step_paper()
-    P.talp_gpu_profile_read(ctx.ctx)
-    l0 = P.talp_gpu_profile_read(ctx.ctx)["kernel_launches"]
     clocks = Clocks(0)
     clocks.start()
-    time.sleep(0.3)
+    for _ in range(max(a.warmup, 3)):
+        step_paper()
+        step_threads()
+    P.talp_gpu_profile_read(ctx.ctx)
+    l0 = P.talp_gpu_profile_read(ctx.ctx)["kernel_launches"]
     ms = timed(step_threads, a.steps)
     ck = clocks.stop()
     launches = P.talp_gpu_profile_read(ctx.ctx)["kernel_launches"] - l0
@@ -1104,18 +1111,17 @@ def main():
         P.talp_gpu_ingest_events(ctx.ctx, [batch_d], stream)
         P.talp_gpu_region_metrics_device(ctx.ctx, [t.trace_id], P.TALP_GPU_ALL_REGIONS, out_dev.data_ptr(), stream)
 
+    clocks = Clocks(torch.cuda.current_device() if ws == 1 else local)
+    clocks.start()
     for _ in range(max(a.warmup, 3) if a.warmup >= 3 else 3):
         step_device()
     torch.cuda.synchronize()
     # the results of the warm-up are checked once through the host API
     res = P.talp_gpu_region_metrics(ctx.ctx, t.trace_id, P.TALP_GPU_ALL_REGIONS, stream, n_regions=R)
+    step_device()                      # one more untimed step after the host-side check
     P.talp_gpu_profile(ctx.ctx, True)
     P.talp_gpu_profile_read(ctx.ctx)
     launches0 = P.talp_gpu_profile_read(ctx.ctx)["kernel_launches"]
-
-    clocks = Clocks(torch.cuda.current_device() if ws == 1 else local)
-    clocks.start()
-    time.sleep(0.3)
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
