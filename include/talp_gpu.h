@@ -551,6 +551,16 @@ talp_gpu_status talp_gpu_server_submit_raw(talp_gpu_server *srv, uint64_t job_id
  * blocks until answered.  EINVAL when the job's records were invalid. */
 talp_gpu_status talp_gpu_server_query(talp_gpu_server *srv, uint64_t job_id, uint32_t region,
                                       talp_gpu_metrics *out_host);
+/* Host tree with threads of one region (or TALP_GPU_ALL_REGIONS:
+ * out_host[n_regions]) over the same state as talp_gpu_server_query: the
+ * job's host units are threads, grouped into processes by proc_off (host
+ * memory, n_procs + 1 entries, read while the call waits; the rules of
+ * talp_gpu_thread_metrics).  Batched with the other queries on the query
+ * stream; blocks until answered.  EINVAL for a bad process table or when
+ * the job's records were invalid; ENOMEM when no room for the table. */
+talp_gpu_status talp_gpu_server_query_threads(talp_gpu_server *srv, uint64_t job_id, uint32_t region,
+                                              const uint32_t *proc_off, uint32_t n_procs,
+                                              talp_gpu_thread_tree *out_host);
 /* Wait until everything submitted so far is folded. */
 talp_gpu_status talp_gpu_server_drain(talp_gpu_server *srv);
 talp_gpu_status talp_gpu_server_close_job(talp_gpu_server *srv, uint64_t job_id);

@@ -15,6 +15,6 @@ from ._lib import (  # noqa: F401
     talp_gpu_reset, talp_gpu_unit_sums, talp_gpu_profile, talp_gpu_profile_read, talp_gpu_reduce_noalloc,
     TALP_GPU_NOALLOC_MAX_UNITS, TALP_GPU_PLAN_AUTOTUNE, Plan, talp_gpu_plan_create, talp_gpu_plan_launch,
     talp_gpu_plan_metrics, talp_gpu_plan_info, talp_gpu_plan_destroy, talp_gpu_metrics, talp_gpu_trace_batch, EXPORTED_SYMBOLS,
-    Server, talp_gpu_server_create, talp_gpu_server_open_job, talp_gpu_server_submit, talp_gpu_server_submit_raw, talp_gpu_server_query,
+    Server, talp_gpu_server_create, talp_gpu_server_open_job, talp_gpu_server_submit, talp_gpu_server_submit_raw, talp_gpu_server_query, talp_gpu_server_query_threads,
     talp_gpu_server_drain, talp_gpu_server_close_job, talp_gpu_server_info, talp_gpu_server_destroy,
 )

@@ -28,7 +28,7 @@ EXPORTED_SYMBOLS = (
     "talp_gpu_reset", "talp_gpu_memory", "talp_gpu_profile", "talp_gpu_profile_read", "talp_gpu_reduce_noalloc",
     "talp_gpu_plan_create", "talp_gpu_plan_launch", "talp_gpu_plan_metrics", "talp_gpu_plan_info",
     "talp_gpu_plan_destroy", "talp_gpu_server_create", "talp_gpu_server_open_job", "talp_gpu_server_submit", "talp_gpu_server_submit_raw",
-    "talp_gpu_server_query", "talp_gpu_server_drain", "talp_gpu_server_close_job", "talp_gpu_server_info",
+    "talp_gpu_server_query", "talp_gpu_server_query_threads", "talp_gpu_server_drain", "talp_gpu_server_close_job", "talp_gpu_server_info",
     "talp_gpu_server_destroy", "talp_gpu_last_error",
 )
 TALP_GPU_PLAN_AUTOTUNE = 0x1
@@ -188,6 +188,7 @@ def load_library():
         "talp_gpu_server_submit": ([P, U64, ctypes.POINTER(talp_gpu_trace_batch)], I32),
         "talp_gpu_server_submit_raw": ([P, U64, ctypes.POINTER(talp_gpu_raw_batch)], I32),
         "talp_gpu_server_query": ([P, U64, U32, ctypes.POINTER(talp_gpu_metrics)], I32),
+        "talp_gpu_server_query_threads": ([P, U64, U32, P, U32, ctypes.POINTER(talp_gpu_thread_tree)], I32),
         "talp_gpu_server_drain": ([P], I32),
         "talp_gpu_server_close_job": ([P, U64], I32),
         "talp_gpu_server_info": ([P, ctypes.POINTER(talp_gpu_server_stats)], I32),
@@ -516,6 +517,27 @@ def talp_gpu_server_query(srv, job_id, region, n_regions=None, check=True):
     return st, res
 
 
+def talp_gpu_server_query_threads(srv, job_id, region, proc_off, n_regions=None, check=True):
+    """Host tree with threads of a served job (a dict, or a list of dicts with
+    TALP_GPU_ALL_REGIONS)."""
+    k = n_regions if region == TALP_GPU_ALL_REGIONS else 1
+    if k is None:
+        raise ValueError("n_regions is needed with TALP_GPU_ALL_REGIONS")
+    po = np.ascontiguousarray(proc_off, dtype=np.uint32)
+    if po.ndim != 1 or po.shape[0] < 1:
+        raise ValueError("proc_off needs n_procs + 1 entries")
+    out = (talp_gpu_thread_tree * k)()
+    st = load_library().talp_gpu_server_query_threads(srv, int(job_id), region, po.ctypes.data_as(ctypes.c_void_p),
+                                                      po.shape[0] - 1, out)
+    res = [{f: (float(getattr(o, f)) if t is ctypes.c_double else int(getattr(o, f))) for f, t in o._fields_}
+           for o in out]
+    res = res if region == TALP_GPU_ALL_REGIONS else res[0]
+    if check:
+        _check(st)
+        return res
+    return st, res
+
+
 def talp_gpu_server_drain(srv):
     _check(load_library().talp_gpu_server_drain(srv))
 
@@ -800,6 +822,9 @@ class Server:
             st, r = r
             return st, ([metrics_to_dict(x) for x in r] if isinstance(r, list) else metrics_to_dict(r))
         return [metrics_to_dict(x) for x in r] if isinstance(r, list) else metrics_to_dict(r)
+
+    def query_threads(self, job_id, proc_off, region=TALP_GPU_ALL_REGIONS, check=True):
+        return talp_gpu_server_query_threads(self.handle, job_id, region, proc_off, self._R[int(job_id)], check)
 
     def drain(self):
         talp_gpu_server_drain(self.handle)

@@ -79,6 +79,11 @@ struct Query {
     uint32_t n_out = 0;
     uint64_t need = 0;             // slices that must be enqueued first
     talp_gpu_metrics* out = nullptr;
+    // a thread-tree query instead (tout set): the client's process table,
+    // valid while it waits
+    talp_gpu_thread_tree* tout = nullptr;
+    const uint32_t* proc_off = nullptr;
+    uint32_t n_procs = 0;
     talp_gpu_status st = TALP_GPU_OK;
     bool done = false;
     Clock::time_point t0;
@@ -107,6 +112,14 @@ struct QSlot {
     MetricsOut* d_out = nullptr;
     FinalizeJob* h_jobs = nullptr;
     MetricsOut* h_out = nullptr;
+    // thread-tree queries: jobs and results, and their process tables
+    ThreadJob* d_tjobs = nullptr;
+    ThreadOut* d_tout = nullptr;
+    ThreadJob* h_tjobs = nullptr;
+    ThreadOut* h_tout = nullptr;
+    uint32_t* d_po = nullptr;
+    uint32_t* h_po = nullptr;
+    size_t po_cap = 0;             // entries of d_po / h_po
     cudaEvent_t ev_fin = nullptr;  // finalize kernel done
     cudaEvent_t ev = nullptr;      // answers on the host side
     std::vector<Query*> qs;
@@ -165,12 +178,29 @@ void wake(talp_gpu_server* s) {
     s->cv_work.notify_one();
 }
 
-talp_gpu_status check_flags(const talp_gpu_metrics* out, uint32_t n) {
+template <typename T>
+talp_gpu_status check_flags(const T* out, uint32_t n) {
     for (uint32_t k = 0; k < n; ++k) {
         if (out[k].flags & TALP_GPU_M_TIMEOUT) return TALP_GPU_ETIMEDOUT;
         if (out[k].flags & (TALP_GPU_M_INVALID | TALP_GPU_M_UNSORTED)) return TALP_GPU_EINVAL;
     }
     return TALP_GPU_OK;
+}
+
+// Room for `need` process-table entries in a free query slot (server thread).
+bool grow_po(QSlot& q, size_t need) {
+    if (need <= q.po_cap) return true;
+    size_t cap = q.po_cap ? q.po_cap : 4096;
+    while (cap < need) cap *= 2;
+    if (q.d_po) cudaFree(q.d_po);
+    if (q.h_po) cudaFreeHost(q.h_po);
+    q.d_po = nullptr;
+    q.h_po = nullptr;
+    q.po_cap = 0;
+    if (cudaMalloc(&q.d_po, sizeof(uint32_t) * cap) != cudaSuccess) return false;
+    if (cudaMallocHost(&q.h_po, sizeof(uint32_t) * cap) != cudaSuccess) return false;
+    q.po_cap = cap;
+    return true;
 }
 
 cudaEvent_t take_event(talp_gpu_server* s) {
@@ -357,7 +387,23 @@ void issue_queries(talp_gpu_server* s, std::unique_lock<std::mutex>& lk) {
     QSlot& q = s->qslots[slot];
     q.qs.clear();
     int64_t need_wave = -1;
-    size_t e = 0;
+    size_t e = 0, et = 0, po_used = 0;
+    size_t po_need = 0;
+    for (const Query* r : s->queries)
+        if (r->tout) po_need += r->n_procs + 1;
+    if (po_need && !grow_po(q, po_need)) {
+        // no room for any process table now: answer the thread queries with ENOMEM
+        for (auto qi = s->queries.begin(); qi != s->queries.end();) {
+            if ((*qi)->tout) {
+                (*qi)->st = TALP_GPU_ENOMEM;
+                (*qi)->done = true;
+                qi = s->queries.erase(qi);
+            } else {
+                ++qi;
+            }
+        }
+        s->cv_done.notify_all();
+    }
     for (auto qi = s->queries.begin(); qi != s->queries.end();) {
         Query* r = *qi;
         auto it = s->jobs.find(r->job);
@@ -369,14 +415,23 @@ void issue_queries(talp_gpu_server* s, std::unique_lock<std::mutex>& lk) {
             continue;
         }
         Job* j = it->second;
-        if (j->enqueued < r->need || e + r->n_out > s->qslot_entries) {
+        const bool thr = r->tout != nullptr;
+        if (j->enqueued < r->need || (thr ? et : e) + r->n_out > s->qslot_entries ||
+            (thr && po_used + r->n_procs + 1 > q.po_cap)) {
             ++qi;
             continue;
         }
         uint32_t R = 0;
         const TraceDev* td = trace_device_desc(s->ctx, j->id, &R);
         const uint32_t r0 = r->region == TALP_GPU_ALL_REGIONS ? 0 : r->region;
-        for (uint32_t k = 0; k < r->n_out; ++k, ++e) q.h_jobs[e] = FinalizeJob{td, q.d_out + e, r0 + k, 0};
+        if (thr) {
+            memcpy(q.h_po + po_used, r->proc_off, sizeof(uint32_t) * (r->n_procs + 1));
+            for (uint32_t k = 0; k < r->n_out; ++k, ++et)
+                q.h_tjobs[et] = ThreadJob{td, q.d_tout + et, q.d_po + po_used, r->n_procs, r0 + k};
+            po_used += r->n_procs + 1;
+        } else {
+            for (uint32_t k = 0; k < r->n_out; ++k, ++e) q.h_jobs[e] = FinalizeJob{td, q.d_out + e, r0 + k, 0};
+        }
         need_wave = std::max(need_wave, j->last_wave);
         q.qs.push_back(r);
         qi = s->queries.erase(qi);
@@ -389,10 +444,18 @@ void issue_queries(talp_gpu_server* s, std::unique_lock<std::mutex>& lk) {
     ++s->query_batches;
     lk.unlock();
     if (wait_ev) cudaStreamWaitEvent(s->s_query, wait_ev, 0);
-    cudaMemcpyAsync(q.d_jobs, q.h_jobs, sizeof(FinalizeJob) * e, cudaMemcpyHostToDevice, s->s_query);
-    launch_finalize(q.d_jobs, static_cast<uint32_t>(e), s->s_query);
+    if (e) {
+        cudaMemcpyAsync(q.d_jobs, q.h_jobs, sizeof(FinalizeJob) * e, cudaMemcpyHostToDevice, s->s_query);
+        launch_finalize(q.d_jobs, static_cast<uint32_t>(e), s->s_query);
+    }
+    if (et) {
+        cudaMemcpyAsync(q.d_po, q.h_po, sizeof(uint32_t) * po_used, cudaMemcpyHostToDevice, s->s_query);
+        cudaMemcpyAsync(q.d_tjobs, q.h_tjobs, sizeof(ThreadJob) * et, cudaMemcpyHostToDevice, s->s_query);
+        launch_thread_tree(q.d_tjobs, static_cast<uint32_t>(et), s->s_query);
+    }
     cudaEventRecord(q.ev_fin, s->s_query);
-    cudaMemcpyAsync(q.h_out, q.d_out, sizeof(MetricsOut) * e, cudaMemcpyDeviceToHost, s->s_query);
+    if (e) cudaMemcpyAsync(q.h_out, q.d_out, sizeof(MetricsOut) * e, cudaMemcpyDeviceToHost, s->s_query);
+    if (et) cudaMemcpyAsync(q.h_tout, q.d_tout, sizeof(ThreadOut) * et, cudaMemcpyDeviceToHost, s->s_query);
     cudaEventRecord(q.ev, s->s_query);
     s->fin_to_wait = q.ev_fin;
     {
@@ -472,12 +535,19 @@ void done_loop(talp_gpu_server* s) {
         cudaEventSynchronize(q.ev);
         const Clock::time_point t1 = Clock::now();
         std::lock_guard<std::mutex> lk(s->mu);
-        size_t e = 0;
+        size_t e = 0, et = 0;
         for (Query* r : q.qs) {
             static_assert(sizeof(MetricsOut) == sizeof(talp_gpu_metrics), "metrics record layout");
-            memcpy(r->out, q.h_out + e, sizeof(MetricsOut) * r->n_out);
-            e += r->n_out;
-            r->st = check_flags(r->out, r->n_out);
+            static_assert(sizeof(ThreadOut) == sizeof(talp_gpu_thread_tree), "thread tree record layout");
+            if (r->tout) {
+                memcpy(r->tout, q.h_tout + et, sizeof(ThreadOut) * r->n_out);
+                et += r->n_out;
+                r->st = check_flags(r->tout, r->n_out);
+            } else {
+                memcpy(r->out, q.h_out + e, sizeof(MetricsOut) * r->n_out);
+                e += r->n_out;
+                r->st = check_flags(r->out, r->n_out);
+            }
             r->done = true;
             if (s->lat_ms.size() < (1u << 22))
                 s->lat_ms.push_back(std::chrono::duration<double, std::milli>(t1 - r->t0).count());
@@ -538,6 +608,10 @@ talp_gpu_status talp_gpu_server_create(talp_gpu_ctx* ctx, const talp_gpu_server_
             cudaMalloc(&q.d_out, sizeof(MetricsOut) * s->qslot_entries) != cudaSuccess ||
             cudaMallocHost(&q.h_jobs, sizeof(FinalizeJob) * s->qslot_entries) != cudaSuccess ||
             cudaMallocHost(&q.h_out, sizeof(MetricsOut) * s->qslot_entries) != cudaSuccess ||
+            cudaMalloc(&q.d_tjobs, sizeof(ThreadJob) * s->qslot_entries) != cudaSuccess ||
+            cudaMalloc(&q.d_tout, sizeof(ThreadOut) * s->qslot_entries) != cudaSuccess ||
+            cudaMallocHost(&q.h_tjobs, sizeof(ThreadJob) * s->qslot_entries) != cudaSuccess ||
+            cudaMallocHost(&q.h_tout, sizeof(ThreadOut) * s->qslot_entries) != cudaSuccess ||
             cudaEventCreateWithFlags(&q.ev_fin, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&q.ev, cudaEventDisableTiming) != cudaSuccess) {
             talp_gpu_server_destroy(s);
@@ -749,19 +823,29 @@ talp_gpu_status talp_gpu_server_submit_raw(talp_gpu_server* s, uint64_t job_id, 
     return TALP_GPU_OK;
 }
 
-talp_gpu_status talp_gpu_server_query(talp_gpu_server* s, uint64_t job_id, uint32_t region,
-                                      talp_gpu_metrics* out_host) {
-    if (!s || !out_host) return fail(TALP_GPU_EINVAL, "server_query: null argument");
+static talp_gpu_status server_query_common(talp_gpu_server* s, uint64_t job_id, uint32_t region,
+                                           talp_gpu_metrics* out, talp_gpu_thread_tree* tout,
+                                           const uint32_t* proc_off, uint32_t n_procs) {
     Query q;
     q.job = job_id;
     q.region = region;
-    q.out = out_host;
+    q.out = out;
+    q.tout = tout;
+    q.proc_off = proc_off;
+    q.n_procs = n_procs;
     q.t0 = Clock::now();
     std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->jobs.find(job_id);
     if (it == s->jobs.end()) return fail(TALP_GPU_ENOTFOUND, "server_query: unknown job");
     if (region != TALP_GPU_ALL_REGIONS && region >= it->second->R)
         return fail(TALP_GPU_EINVAL, "server_query: region out of range");
+    if (tout) {
+        if (n_procs == 0 || proc_off[0] != 0 || proc_off[n_procs] != it->second->n)
+            return fail(TALP_GPU_EINVAL, "server_query_threads: proc_off must run from 0 to the job's n_ranks");
+        for (uint32_t i = 0; i < n_procs; ++i)
+            if (proc_off[i + 1] <= proc_off[i])
+                return fail(TALP_GPU_EINVAL, "server_query_threads: a process without threads in proc_off");
+    }
     q.n_out = region == TALP_GPU_ALL_REGIONS ? it->second->R : 1;
     q.need = it->second->submitted;
     s->queries.push_back(&q);
@@ -771,9 +855,24 @@ talp_gpu_status talp_gpu_server_query(talp_gpu_server* s, uint64_t job_id, uint3
         set_last_error("server_query: job closed");
     else if (q.st == TALP_GPU_ETIMEDOUT)
         set_last_error("server_query: a device wait timed out");
+    else if (q.st == TALP_GPU_ENOMEM)
+        set_last_error("server_query_threads: no memory for the process table");
     else if (q.st != TALP_GPU_OK)
         set_last_error("server_query: the job holds invalid or out-of-order records");
     return q.st;
+}
+
+talp_gpu_status talp_gpu_server_query(talp_gpu_server* s, uint64_t job_id, uint32_t region,
+                                      talp_gpu_metrics* out_host) {
+    if (!s || !out_host) return fail(TALP_GPU_EINVAL, "server_query: null argument");
+    return server_query_common(s, job_id, region, out_host, nullptr, nullptr, 0);
+}
+
+talp_gpu_status talp_gpu_server_query_threads(talp_gpu_server* s, uint64_t job_id, uint32_t region,
+                                              const uint32_t* proc_off, uint32_t n_procs,
+                                              talp_gpu_thread_tree* out_host) {
+    if (!s || !out_host || !proc_off) return fail(TALP_GPU_EINVAL, "server_query_threads: null argument");
+    return server_query_common(s, job_id, region, nullptr, out_host, proc_off, n_procs);
 }
 
 talp_gpu_status talp_gpu_server_drain(talp_gpu_server* s) {
@@ -866,6 +965,12 @@ talp_gpu_status talp_gpu_server_destroy(talp_gpu_server* s) {
         if (q.d_out) cudaFree(q.d_out);
         if (q.h_jobs) cudaFreeHost(q.h_jobs);
         if (q.h_out) cudaFreeHost(q.h_out);
+        if (q.d_tjobs) cudaFree(q.d_tjobs);
+        if (q.d_tout) cudaFree(q.d_tout);
+        if (q.h_tjobs) cudaFreeHost(q.h_tjobs);
+        if (q.h_tout) cudaFreeHost(q.h_tout);
+        if (q.d_po) cudaFree(q.d_po);
+        if (q.h_po) cudaFreeHost(q.h_po);
         if (q.ev_fin) cudaEventDestroy(q.ev_fin);
         if (q.ev) cudaEventDestroy(q.ev);
     }

@@ -305,3 +305,64 @@ def test_serving_raw_job_closed_with_held_records_reopens_clean():
         for r in range(t.n_regions):
             assert_metrics_equal(res[r], oracle.region_metrics(t, r), ("reopened", r))
     c.close()
+
+
+def test_served_thread_tree_prefixes_mixed_with_metrics_queries():
+    """Jobs of threaded traces: after every slice a client asks for the host
+    tree with threads and another for the paper's metrics, concurrently; the
+    thread answers (batched with the metrics queries on the query stream)
+    equal the oracle's thread tree on the submitted prefix, bit for bit.  A
+    bad process table is refused at the call."""
+    from gpu_common import bits
+    from paper_2603_26576_b300 import Server
+    c = make_ctx()
+    jobs = []
+    for k, T in enumerate(([2, 3, 1], [4, 4], [1, 1, 1, 1], [5, 2, 7])):
+        base = tg.random_trace(60 + k, trace_id=700 + k, n_ranks=len(T), devices_per_rank=2, dev_events=1500,
+                               host_events=800, n_regions=3)
+        jobs.append(tg.add_threads(base, T, seed=k))
+    with Server(c, max_jobs=16, max_slice_records=1 << 18, staging_slices=16) as srv:
+        plan = []
+        for i, t in enumerate(jobs):
+            cuts = tg.random_cuts(t, 3 + i % 3, seed=13)
+            slices = tg.time_slices(t, cuts, shuffle_seed=(5 if i % 2 else None))
+            srv.open_job(t.trace_id, t.devices_per_rank, t.region_window)
+            plan.append((t, cuts, slices, [], []))
+        errors = []
+
+        def thread_client(t, slices, tres, mres):
+            try:
+                po = t.meta["proc_off"]
+                tres.append(srv.query_threads(t.trace_id, po))
+                for sl in slices:
+                    _submit(srv, t, sl)
+                    tres.append(srv.query_threads(t.trace_id, po))
+                    mres.append(srv.query(t.trace_id, region=1))
+            except Exception as e:  # pragma: no cover - reported by the test
+                errors.append((t.trace_id, repr(e)))
+
+        th = [threading.Thread(target=thread_client, args=(t, sl, tr, mr)) for t, _, sl, tr, mr in plan]
+        for x in th:
+            x.start()
+        for x in th:
+            x.join()
+        assert not errors, errors
+        t0 = jobs[0]
+        st, _ = srv.query_threads(t0.trace_id, [0, 2, 2, t0.n_ranks], check=False)
+        assert st == EINVAL
+        st, _ = srv.query_threads(t0.trace_id, [0, t0.n_ranks + 1], check=False)
+        assert st == EINVAL
+    for t, cuts, _, tres, mres in plan:
+        po = t.meta["proc_off"]
+        assert len(tres) == cuts.shape[0] + 2
+        for k, res in enumerate(tres):
+            p = tg.prefix_trace(t, cuts, k - 1)
+            for r in range(t.n_regions):
+                o = oracle.thread_metrics(p, r, po)
+                for f in ("elapsed_ns", "sum_useful", "sum_offload", "sum_busiest", "max_busiest", "n_threads"):
+                    assert res[r][f] == o[f], (t.trace_id, k, r, f)
+                for f in oracle.THREAD_RATIO_FIELDS:
+                    assert bits(res[r][f]) == bits(o[f]), (t.trace_id, k, r, f)
+        for k, m in enumerate(mres):
+            assert_metrics_equal(m, oracle.region_metrics(tg.prefix_trace(t, cuts, k), 1), (t.trace_id, k))
+    c.close()

@@ -114,6 +114,56 @@ def test_stream_ordered_variant():
     c.close()
 
 
+def test_threads_across_slices_sorting_and_raw_buffers():
+    """The thread tree of a trace whose device records are shuffled (the sort
+    stage runs), ingested as two APPEND time slices, and of the same trace
+    delivered as raw per-rank buffers, equals the oracle's on the whole trace."""
+    from test_gpu_parity import _split_by_time
+    c = make_ctx()
+    base = tg.random_trace(21, trace_id=31, n_ranks=4, devices_per_rank=2, dev_events=3000, host_events=1500,
+                           n_regions=3)
+    t = tg.add_threads(base, [2, 5, 1, 3], seed=4)
+    po = t.meta["proc_off"]
+    sh = tg.shuffle_segments(t, seed=9)
+    a, b = _split_by_time(sh, 0.5)
+    c.ingest([a])
+    c.ingest([b], flags=4)                                     # APPEND
+    check_trace(c, t, po, "append + sort")
+    raw = tg.to_raw(tg.add_threads(base, [2, 5, 1, 3], seed=4))
+    raw.trace.trace_id = 32
+    c.ingest_raw([raw])
+    check_trace(c, raw.trace, po, "raw buffers")
+    c.close()
+
+
+def test_invalid_records_and_empty_regions():
+    """A worker's invalid host state makes the call return EINVAL with the
+    record still written and flagged; a region whose windows are empty for
+    every thread is EMPTY with every ratio 1."""
+    import paper_2603_26576_b300 as P
+    c = make_ctx()
+    t = tg.add_threads(tg.random_trace(6, trace_id=41, n_ranks=3, dev_events=200, host_events=300, n_regions=2),
+                       [2, 2, 3])
+    po = t.meta["proc_off"]
+    bad = tg.Trace(**{**t.__dict__})
+    bad.host_state = t.host_state.copy()
+    bad.host_state[int(t.host_off[1]) + 3] = 3                 # a worker of process 0
+    c.ingest([bad])
+    st, res = P.talp_gpu_thread_metrics(c.ctx, 41, 0, po, check=False)
+    assert st == -1 and res["flags"] & 0x100 and res["n_threads"] == t.n_ranks
+    win = t.region_window.copy()
+    win[1] = 5                                                 # region 1: [5, 5) everywhere
+    empty = tg.Trace(**{**t.__dict__})
+    empty.region_window = win
+    c.ingest([empty])
+    res = c.thread_metrics(41, po)
+    assert res[1]["flags"] == 1 and res[1]["elapsed_ns"] == 0
+    assert all(res[1][k] == 1.0 for k in oracle.THREAD_RATIO_FIELDS)
+    for r in range(2):
+        assert_thread_equal(res[r], oracle.thread_metrics(empty, r, po), ("empty", r))
+    c.close()
+
+
 def test_bad_process_tables():
     import paper_2603_26576_b300 as P
     c = make_ctx()
