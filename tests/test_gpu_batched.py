@@ -133,3 +133,33 @@ def test_plan_rejects_host_pointers_and_append():
         assert ei.value.status == -1
     finally:
         c.close()
+
+
+def test_plan_of_threaded_traces_gives_thread_trees():
+    """A plan over threaded traces (one host unit per thread): after a replay
+    of the graph, talp_gpu_thread_metrics of every trace equals the oracle's
+    thread tree, and the plan's own results the paper's tree."""
+    from gpu_common import bits
+    c = make_ctx()
+    try:
+        ts = []
+        for k in range(24):
+            base = tg.random_trace(500 + k, trace_id=20_000 + k, n_ranks=1 + k % 5, devices_per_rank=1 + k % 3,
+                                   dev_events=200 + 37 * k, host_events=150, n_regions=1 + k % 4)
+            ts.append(tg.add_threads(base, [1 + (k + i) % 6 for i in range(base.n_ranks)], seed=k))
+        plan = c.plan(ts, _device_arrays(ts))
+        plan.launch()
+        plan.launch()
+        _check_plan_metrics(plan, ts, "threaded plan")
+        for t in ts:
+            po = t.meta["proc_off"]
+            got = c.thread_metrics(t.trace_id, po)
+            for r in range(t.n_regions):
+                o = oracle.thread_metrics(t, r, po)
+                for f in ("elapsed_ns", "sum_useful", "sum_offload", "sum_busiest", "max_busiest", "n_threads"):
+                    assert got[r][f] == o[f], (t.trace_id, r, f)
+                for f in oracle.THREAD_RATIO_FIELDS:
+                    assert bits(got[r][f]) == bits(o[f]), (t.trace_id, r, f)
+        plan.close()
+    finally:
+        c.close()
