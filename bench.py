@@ -188,11 +188,8 @@ class Clocks:
         except OSError:
             self.proc = None
             return
-        # nvidia-smi's own start (NVML initialisation) stalls a process that
-        # synchronises with the GPU for a few hundred ms: time nothing before
-        # it has settled (the file is read only after nvidia-smi has exited,
-        # as the two share its offset)
-        time.sleep(1.0)
+        # the file is read only after nvidia-smi has exited (the two share
+        # its offset); the warm-up that follows (warm_until) covers its start
 
     def stop(self):
         if self.proc is None:
@@ -223,6 +220,23 @@ class Clocks:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def warm_until(fn, n_min, seconds=1.0):
+    """Untimed warm-up: at least n_min steps, and steps until `seconds` of
+    wall time have passed, so that the timed steps follow continuous work.
+    After an idle spell (or nvidia-smi's start) the first ~100 ms of
+    host-synchronising round trips ran up to 3x slower on the B300 machines."""
+    import torch
+    t0 = time.perf_counter()
+    k = 0
+    while k < n_min or time.perf_counter() - t0 < seconds:
+        fn()
+        k += 1
+        if k % 4 == 0:
+            torch.cuda.synchronize()
+    torch.cuda.synchronize()
+    return k
 
 
 def measured_peaks():
@@ -340,9 +354,7 @@ def run_batched(a):
     info = plan.info()
     clocks = Clocks(0)
     clocks.start()
-    for _ in range(max(a.warmup, 3)):
-        plan.launch(stream)
-    torch.cuda.synchronize()
+    warm_until(lambda: plan.launch(stream), max(a.warmup, 3))
     batched = plan.metrics(stream)
     P.talp_gpu_profile_read(ctx.ctx)
     l0 = P.talp_gpu_profile_read(ctx.ctx)["kernel_launches"]
@@ -546,8 +558,8 @@ def run_concurrency(a):
     region = 0
     clocks = Clocks(0)
     clocks.start()
-    for _ in range(max(a.warmup, 3)):
-        res = P.talp_gpu_concurrency(ctx.ctx, b, region, stream)
+    warm_until(lambda: P.talp_gpu_concurrency(ctx.ctx, b, region, stream), max(a.warmup, 3))
+    res = P.talp_gpu_concurrency(ctx.ctx, b, region, stream)
     P.talp_gpu_profile_read(ctx.ctx)
     l0 = P.talp_gpu_profile_read(ctx.ctx)["kernel_launches"]
     e0 = torch.cuda.Event(enable_timing=True)
@@ -660,15 +672,13 @@ def run_raw(a):
 
     clocks = Clocks(0)
     clocks.start()
-    for _ in range(max(a.warmup, 3)):
-        step_raw()
+    warm_until(step_raw, max(a.warmup, 3))
     P.talp_gpu_profile_read(ctx.ctx)
     l0 = P.talp_gpu_profile_read(ctx.ctx)["kernel_launches"]
     ms = timed(step_raw, a.steps)
     ck = clocks.stop()
     launches = P.talp_gpu_profile_read(ctx.ctx)["kernel_launches"] - l0 + a.steps
-    for _ in range(max(a.warmup, 3)):
-        step_lanes()
+    warm_until(step_lanes, max(a.warmup, 3), 0.3)
     ms_lanes = timed(step_lanes, a.steps)
     got = P.talp_gpu_region_metrics(ctx.ctx, t.trace_id, P.TALP_GPU_ALL_REGIONS, stream, n_regions=R)
     lane_res = P.talp_gpu_region_metrics(ctx.ctx, t.trace_id + 1, P.TALP_GPU_ALL_REGIONS, stream, n_regions=R)
@@ -749,9 +759,8 @@ def run_threads(a):
 
     clocks = Clocks(0)
     clocks.start()
-    for _ in range(max(a.warmup, 3)):
-        step_paper()
-        step_threads()
+    warm_until(step_paper, max(a.warmup, 3), 0.3)
+    warm_until(step_threads, max(a.warmup, 3))
     P.talp_gpu_profile_read(ctx.ctx)
     l0 = P.talp_gpu_profile_read(ctx.ctx)["kernel_launches"]
     ms = timed(step_threads, a.steps)
@@ -1113,9 +1122,7 @@ def main():
 
     clocks = Clocks(torch.cuda.current_device() if ws == 1 else local)
     clocks.start()
-    for _ in range(max(a.warmup, 3) if a.warmup >= 3 else 3):
-        step_device()
-    torch.cuda.synchronize()
+    warm_until(step_device, max(a.warmup, 3))
     # the results of the warm-up are checked once through the host API
     res = P.talp_gpu_region_metrics(ctx.ctx, t.trace_id, P.TALP_GPU_ALL_REGIONS, stream, n_regions=R)
     step_device()                      # one more untimed step after the host-side check
