@@ -459,9 +459,8 @@ def run_batched_full(a):
         plan = ctx.plan(dts, arrays, flags=P.TALP_GPU_SORTED_BY_START)
         build_s += time.perf_counter() - b0
         info = plan.info()
-        for _ in range(2):                        # warm-up (and first result)
-            plan.launch(stream)
-        torch.cuda.synchronize()
+        # warm-up (and first result): the wave was just generated and planned
+        warm_until(lambda: plan.launch(stream), 2, 0.15)
         e0.record(stream)
         for _ in range(3):
             plan.launch(stream)
@@ -521,7 +520,7 @@ def run_batched_full(a):
         "config": {"workload": f"batched at full laws: {a.traces} traces, ranks log-uniform 1-512, 1-8 GPUs per rank, "
                                f"1e3-{ev_hi:g} device events per GPU log-uniform, 8 nested regions each",
                    "form": "per wave of whole traces: one CUDA-graph launch of a plan (a step = one wave; "
-                           "2 warm-up launches, the mean of 3 timed launches)",
+                           "warm-up launches for >= 150 ms, the mean of 3 timed launches)",
                    "waves": len(wv), "records": tot_rec, "bytes": BYTES_PER_RECORD * tot_rec, "segments": tot_seg,
                    "wave_records_max": int(a.wave_records), "generate_s": gen_s, "plan_build_s": build_s,
                    "plain_one_trace_per_launch_events_per_s": tot_rec / (plain_ms / 1000.0),
