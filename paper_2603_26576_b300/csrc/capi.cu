@@ -1251,8 +1251,8 @@ talp_gpu_status talp_gpu_ingest_raw(talp_gpu_ctx* c, const talp_gpu_raw_batch* r
                                reinterpret_cast<uint32_t*>(R + o_hist), reinterpret_cast<uint64_t*>(R + o_offs), dmoves,
                                reinterpret_cast<uint64_t*>(R + o_cnt), dst, grid, stream));
     TALP_CUDA(launch_raw_scatter(dtiles, static_cast<uint32_t>(nt), dranks, reinterpret_cast<const uint64_t*>(R + o_offs),
-                                 reinterpret_cast<int64_t*>(R + o_lse), reinterpret_cast<uint8_t*>(R + o_ltag), grid,
-                                 stream));
+                                 reinterpret_cast<int64_t*>(R + o_lse), reinterpret_cast<uint8_t*>(R + o_ltag), dst,
+                                 c->wait_limit, grid, stream));
     c->kernel_launches += (nt ? 2 : 0) + (nrk ? 1 : 0);
     if (any_hold) {
         TALP_CUDA(launch_raw_hold(dranks, static_cast<uint32_t>(nrk), reinterpret_cast<const int64_t*>(R + o_lse), dmoves,
@@ -1273,6 +1273,7 @@ talp_gpu_status talp_gpu_ingest_raw(talp_gpu_ctx* c, const talp_gpu_raw_batch* r
     if (status) {
         for (size_t k = 0; k < nb; ++k)
             if (hb[k]) raw_hold_drop(c, rb[k].trace_id);
+        if (status & ST_TIMEOUT) return fail(TALP_GPU_ETIMEDOUT, "raw: a device-side wait ran out");
         if (status & 1u) return fail(TALP_GPU_EINVAL, "raw: a record names a device its rank does not have");
         return fail(TALP_GPU_EINVAL, "raw: a record on a stream its device's stream mask does not declare");
     }

@@ -46,7 +46,8 @@ cudaError_t launch_raw_count(const RawTile* tiles, uint32_t n_tiles, const RawRa
                              uint32_t* hist, uint64_t* offs, RawMove* moves, uint64_t* dev_count, uint32_t* status,
                              int grid, cudaStream_t stream);
 cudaError_t launch_raw_scatter(const RawTile* tiles, uint32_t n_tiles, const RawRank* ranks, const uint64_t* offs,
-                               int64_t* lse, uint8_t* ltag, int grid, cudaStream_t stream);
+                               int64_t* lse, uint8_t* ltag, uint32_t* status, int64_t wait_limit, int grid,
+                               cudaStream_t stream);
 cudaError_t launch_raw_hold(const RawRank* ranks, uint32_t n_ranks, const int64_t* lse, RawMove* moves,
                             uint64_t* fold_count, uint64_t* hold_count, uint32_t* status, cudaStream_t stream);
 cudaError_t launch_raw_move(const RawTile* tiles, uint32_t n_tiles, const RawRank* ranks, const RawMove* moves,

@@ -126,12 +126,27 @@ __global__ void __launch_bounds__(kBuckets) raw_scan_kernel(const RawRank* __res
 __global__ void __launch_bounds__(kRawThreads) raw_scatter_kernel(const RawTile* __restrict__ tiles, uint32_t n_tiles,
                                                                   const RawRank* __restrict__ ranks,
                                                                   const uint64_t* __restrict__ offs,
-                                                                  int64_t* __restrict__ lse, uint8_t* __restrict__ ltag) {
+                                                                  int64_t* __restrict__ lse, uint8_t* __restrict__ ltag,
+                                                                  uint32_t* __restrict__ status, int64_t wait_limit) {
     __shared__ uint32_t cnt[kRawThreads / 32][kBuckets];
+    // the tile's 16-byte rows, brought in by one bulk copy while the tile is ranked
+    __shared__ __align__(16) longlong2 rows[kRawTile];
+    __shared__ __align__(8) uint64_t bar;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
     for (uint32_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         const RawTile tl = tiles[t];
         const uint32_t D = ranks[tl.rank].D;
+        if (threadIdx.x == 0 && tl.n) {
+            fence_proxy_async_smem();   // the previous tile's reads of `rows` come first
+            mbar_arrive_expect_tx(&bar, tl.n * 16u);
+            tma_load_1d(rows, tl.se, tl.n * 16u, &bar);
+        }
         for (int q = threadIdx.x; q < (kRawThreads / 32) * kBuckets; q += kRawThreads) (&cnt[0][0])[q] = 0;
         __syncthreads();
         const uint32_t w0 = wid * (kRawTile / (kRawThreads / 32));
@@ -168,12 +183,24 @@ __global__ void __launch_bounds__(kRawThreads) raw_scatter_kernel(const RawTile*
             }
         }
         __syncthreads();
+        if (tl.n) {
+            // bounded wait for the rows; past the limit the copy is still let
+            // land (and the result reports the time-out) before anything reuses
+            // the buffer, and a copy that never lands ends the CTA's work
+            bool landed = mbar_wait_bounded(&bar, phase, wait_limit);
+            if (!landed) {
+                atomicOr(status, ST_TIMEOUT);
+                landed = mbar_wait_bounded(&bar, phase, kDrainWaitCycles);
+            }
+            if (__syncthreads_or(!landed)) return;
+            phase ^= 1u;
+        }
 #pragma unroll
         for (int r = 0; r < kRawItems; ++r) {
             if (ok[r]) {
                 const uint32_t q = w0 + r * 32 + lane;
                 const uint64_t o = offs[static_cast<uint64_t>(t) * kBuckets + bk[r]] + cnt[wid][bk[r]] + rnk[r];
-                *reinterpret_cast<longlong2*>(lse + 2 * o) = *reinterpret_cast<const longlong2*>(tl.se + 2 * q);
+                *reinterpret_cast<longlong2*>(lse + 2 * o) = rows[q];
                 ltag[o] = tv[r];
             }
         }
@@ -305,8 +332,10 @@ cudaError_t launch_raw_count(const RawTile* tiles, uint32_t n_tiles, const RawRa
 }
 
 cudaError_t launch_raw_scatter(const RawTile* tiles, uint32_t n_tiles, const RawRank* ranks, const uint64_t* offs,
-                               int64_t* lse, uint8_t* ltag, int grid, cudaStream_t stream) {
-    if (n_tiles) raw_scatter_kernel<<<grid, kRawThreads, 0, stream>>>(tiles, n_tiles, ranks, offs, lse, ltag);
+                               int64_t* lse, uint8_t* ltag, uint32_t* status, int64_t wait_limit, int grid,
+                               cudaStream_t stream) {
+    if (n_tiles)
+        raw_scatter_kernel<<<grid, kRawThreads, 0, stream>>>(tiles, n_tiles, ranks, offs, lse, ltag, status, wait_limit);
     return cudaGetLastError();
 }
 

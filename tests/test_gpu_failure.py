@@ -36,3 +36,25 @@ def test_wait_limit_runs_out_reports_etimedout():
     good.ingest([t], flags=P.TALP_GPU_SORTED_BY_START)
     assert_trace_equal(good, t, "after-timeout")
     good.close()
+
+
+def test_raw_scatter_wait_runs_out_reports_etimedout():
+    """The raw adapter's bounded wait for a tile's bulk copy: with a negative
+    limit it reports a time-out (after letting the copy land) and the call
+    returns ETIMEDOUT; a fresh context then ingests the same buffers."""
+    import paper_2603_26576_b300 as P
+    t = tg.random_trace(5, trace_id=43, n_ranks=2, devices_per_rank=3, dev_events=3000, host_events=300,
+                        n_regions=2)
+    raw = tg.to_raw(t)
+    with env(TALP_GPU_WAIT_LIMIT=-1):
+        c = P.Context(0)
+    try:
+        with pytest.raises(P.TalpGpuError) as e:
+            c.ingest_raw([raw])
+        assert e.value.status == ETIMEDOUT
+    finally:
+        c.close()
+    good = make_ctx()
+    good.ingest_raw([raw])
+    assert_trace_equal(good, t, "raw-after-timeout", sums=False)
+    good.close()
