@@ -361,6 +361,19 @@ talp_gpu_status talp_gpu_thread_metrics(talp_gpu_ctx *ctx, uint64_t trace_id, ui
 talp_gpu_status talp_gpu_thread_metrics_device(talp_gpu_ctx *ctx, uint64_t trace_id, uint32_t region,
                                                const uint32_t *proc_off, uint32_t n_procs,
                                                talp_gpu_thread_tree *out_device, void *stream);
+/*
+ * Sharded thread tree (one trace split over GPUs or contexts by whole
+ * processes, each with all of its threads and their devices): parts are the
+ * records of one region computed on each shard (host memory, same trace_id
+ * and region).  E and max_busiest combine by max, the sums and the process
+ * and thread counts by addition, the status flags by or, and one kernel
+ * forms the six ratios from them, so the result equals the whole trace's
+ * bit for bit.  out_host: one record; synchronises `stream`.
+ * Errors: EINVAL (no parts, more than 2^20, mixed traces or regions, a part
+ * carrying the flag of invalid records), ETIMEDOUT, ECUDA.
+ */
+talp_gpu_status talp_gpu_thread_metrics_combine(talp_gpu_ctx *ctx, const talp_gpu_thread_tree *parts,
+                                                size_t n_parts, talp_gpu_thread_tree *out_host, void *stream);
 
 /*
  * Scalability across runs: POP's second branch, which needs several runs

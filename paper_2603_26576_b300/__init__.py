@@ -12,6 +12,7 @@ from ._lib import (  # noqa: F401
     raw_batch_from_arrays, talp_gpu_raw_batch, talp_gpu_create, talp_gpu_destroy, talp_gpu_ingest_events, talp_gpu_last_error,
     talp_gpu_memory, talp_gpu_region_metrics, talp_gpu_region_metrics_batch, talp_gpu_region_metrics_device,
     talp_gpu_thread_metrics, talp_gpu_thread_metrics_device, talp_gpu_thread_tree, thread_tree_from_bytes,
+    talp_gpu_thread_metrics_combine,
     talp_gpu_reset, talp_gpu_unit_sums, talp_gpu_profile, talp_gpu_profile_read, talp_gpu_reduce_noalloc,
     TALP_GPU_NOALLOC_MAX_UNITS, TALP_GPU_PLAN_AUTOTUNE, Plan, talp_gpu_plan_create, talp_gpu_plan_launch,
     talp_gpu_plan_metrics, talp_gpu_plan_info, talp_gpu_plan_destroy, talp_gpu_metrics, talp_gpu_trace_batch, EXPORTED_SYMBOLS,

@@ -25,6 +25,7 @@ EXPORTED_SYMBOLS = (
     "talp_gpu_region_metrics_batch", "talp_gpu_region_metrics_device", "talp_gpu_metrics_combine",
     "talp_gpu_concurrency", "talp_gpu_scalability", "talp_gpu_ingest_raw", "talp_gpu_raw_held",
     "talp_gpu_unit_sums", "talp_gpu_thread_metrics", "talp_gpu_thread_metrics_device",
+    "talp_gpu_thread_metrics_combine",
     "talp_gpu_reset", "talp_gpu_memory", "talp_gpu_profile", "talp_gpu_profile_read", "talp_gpu_reduce_noalloc",
     "talp_gpu_plan_create", "talp_gpu_plan_launch", "talp_gpu_plan_metrics", "talp_gpu_plan_info",
     "talp_gpu_plan_destroy", "talp_gpu_server_create", "talp_gpu_server_open_job", "talp_gpu_server_submit", "talp_gpu_server_submit_raw",
@@ -166,6 +167,8 @@ def load_library():
         "talp_gpu_unit_sums": ([P, U64, U32, P, P, P], I32),
         "talp_gpu_thread_metrics": ([P, U64, U32, P, U32, ctypes.POINTER(talp_gpu_thread_tree), P], I32),
         "talp_gpu_thread_metrics_device": ([P, U64, U32, P, U32, P, P], I32),
+        "talp_gpu_thread_metrics_combine": ([P, ctypes.POINTER(talp_gpu_thread_tree), S,
+                                             ctypes.POINTER(talp_gpu_thread_tree), P], I32),
         "talp_gpu_concurrency": ([P, ctypes.POINTER(talp_gpu_trace_batch), U32, P, P], I32),
         "talp_gpu_scalability": ([P, ctypes.POINTER(talp_gpu_metrics), S, S, U32, ctypes.POINTER(talp_gpu_scaling),
                                   P], I32),
@@ -279,6 +282,23 @@ def talp_gpu_thread_metrics_device(ctx, trace_id, region, proc_off, out_device_p
     po = np.ascontiguousarray(proc_off, dtype=np.uint32)
     _check(load_library().talp_gpu_thread_metrics_device(ctx, trace_id, region, po.ctypes.data_as(ctypes.c_void_p),
                                                          po.shape[0] - 1, out_device_ptr, _stream(stream)))
+
+
+def talp_gpu_thread_metrics_combine(ctx, parts, stream=None, check=True):
+    """Thread-tree records (dicts as talp_gpu_thread_metrics returns) of one
+    region on disjoint shards -> the whole trace's record (a dict)."""
+    arr = (talp_gpu_thread_tree * max(1, len(parts)))()
+    for k, p in enumerate(parts):
+        for f, _ in talp_gpu_thread_tree._fields_:
+            setattr(arr[k], f, p[f])
+    out = talp_gpu_thread_tree()
+    st = load_library().talp_gpu_thread_metrics_combine(ctx, arr, len(parts), ctypes.byref(out), _stream(stream))
+    res = {f: (float(getattr(out, f)) if t is ctypes.c_double else int(getattr(out, f)))
+           for f, t in out._fields_}
+    if check:
+        _check(st)
+        return res
+    return st, res
 
 
 def thread_tree_from_bytes(buf) -> list:

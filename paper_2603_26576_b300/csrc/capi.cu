@@ -1422,6 +1422,41 @@ talp_gpu_status talp_gpu_thread_metrics_device(talp_gpu_ctx* c, uint64_t trace_i
                               nullptr, static_cast<cudaStream_t>(stream));
 }
 
+talp_gpu_status talp_gpu_thread_metrics_combine(talp_gpu_ctx* c, const talp_gpu_thread_tree* parts, size_t n_parts,
+                                                talp_gpu_thread_tree* out_host, void* stream_) {
+    if (!c) return fail(TALP_GPU_EINVAL, "null context");
+    if (!parts || !out_host || n_parts == 0) return fail(TALP_GPU_EINVAL, "null argument or no parts");
+    if (n_parts > (1u << 20)) return fail(TALP_GPU_EINVAL, "more than 2^20 parts");
+    for (size_t k = 1; k < n_parts; ++k)
+        if (parts[k].trace_id != parts[0].trace_id || parts[k].region != parts[0].region)
+            return fail(TALP_GPU_EINVAL, "parts of different traces or regions");
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    TALP_CUDA(cudaSetDevice(c->device));
+    const size_t pb = align_up(sizeof(ThreadOut) * n_parts, 256);
+    if (c->ws_used) TALP_CUDA(cudaStreamWaitEvent(stream, c->ev_ws, 0));
+    TALP_TRY(grow(c, c->ws, pb + sizeof(ThreadOut)));
+    ThreadOut* dparts = static_cast<ThreadOut*>(c->ws.p);
+    ThreadOut* dres = reinterpret_cast<ThreadOut*>(static_cast<char*>(c->ws.p) + pb);
+    TALP_CUDA(cudaEventSynchronize(c->ev_up));
+    TALP_TRY(grow_pinned(c->up, pb));
+    memcpy(c->up.p, parts, sizeof(ThreadOut) * n_parts);
+    TALP_CUDA(cudaMemcpyAsync(dparts, c->up.p, sizeof(ThreadOut) * n_parts, cudaMemcpyHostToDevice, stream));
+    TALP_CUDA(cudaEventRecord(c->ev_up, stream));
+    TALP_CUDA(launch_thread_combine(dparts, static_cast<uint32_t>(n_parts), dres, stream));
+    ++c->kernel_launches;
+    TALP_TRY(grow_pinned(c->down, sizeof(ThreadOut)));
+    TALP_CUDA(cudaMemcpyAsync(c->down.p, dres, sizeof(ThreadOut), cudaMemcpyDeviceToHost, stream));
+    TALP_CUDA(cudaEventRecord(c->ev_ws, stream));
+    c->ws_used = true;
+    TALP_CUDA(cudaStreamSynchronize(stream));
+    memcpy(out_host, c->down.p, sizeof(ThreadOut));
+    const uint32_t f = out_host->flags;
+    if (f & TALP_GPU_M_TIMEOUT) return fail(TALP_GPU_ETIMEDOUT, "a device-side wait ran out during ingest");
+    if (f & (TALP_GPU_M_INVALID | TALP_GPU_M_UNSORTED))
+        return fail(TALP_GPU_EINVAL, "invalid or out-of-order records were ingested");
+    return TALP_GPU_OK;
+}
+
 talp_gpu_status talp_gpu_scalability(talp_gpu_ctx* c, const talp_gpu_metrics* runs, size_t n_runs, size_t ref,
                                      uint32_t mode, talp_gpu_scaling* out_host, void* stream_) {
     static_assert(sizeof(ScaleOut) == sizeof(talp_gpu_scaling), "scaling record layout");

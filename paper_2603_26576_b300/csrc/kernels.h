@@ -39,6 +39,7 @@ cudaError_t launch_prep(const FillJob* jobs, uint32_t n_jobs, cudaStream_t strea
 
 cudaError_t launch_finalize(const FinalizeJob* jobs, uint32_t n_jobs, cudaStream_t stream);
 cudaError_t launch_thread_tree(const ThreadJob* jobs, uint32_t n_jobs, cudaStream_t stream);
+cudaError_t launch_thread_combine(const ThreadOut* parts, uint32_t n_parts, ThreadOut* out, cudaStream_t stream);
 cudaError_t launch_concurrency(const int64_t* se, const uint8_t* tag, const ConcDev* devs, uint32_t n_dev,
                                const ConcChunk* chunks, uint32_t n_chunks, int64_t* top, int64_t* in, int64_t* out,
                                uint32_t* status, cudaStream_t stream);

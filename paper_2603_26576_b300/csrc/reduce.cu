@@ -305,6 +305,24 @@ __global__ void __launch_bounds__(256) finalize_kernel(const FinalizeJob* __rest
 //   MPI LB = sum T M / (nT max M)   MPI CE = max M / E
 //   thread LB = sum B / sum T M     OE = sum U / sum B
 // With one thread per process these are the Eqs. 6-8 values of finalize.
+// The six ratios from a thread record's aggregates (o.flags holds the status
+// bits on entry; EMPTY is set here): nT = o.n_threads.
+__device__ __forceinline__ void form_thread_ratios(ThreadOut& o) {
+    const int64_t E = o.elapsed_ns, nT = o.n_threads;
+    const int64_t sU = o.sum_useful, sW = o.sum_offload, sTM = o.sum_busiest, maxM = o.max_busiest;
+    if (E == 0) {
+        o.flags |= 0x1u;
+        o.pe = o.mpi_pe = o.mpi_lb = o.mpi_ce = o.thread_lb = o.oe = 1.0;
+        return;
+    }
+    o.pe = ratio_k(sU, E, nT);
+    o.mpi_pe = ratio_k(sTM, E, nT);
+    o.mpi_lb = ratio_k(sTM, nT, maxM);
+    o.mpi_ce = ratio(maxM, E);
+    o.thread_lb = ratio(sU + sW, sTM);
+    o.oe = ratio(sU, sU + sW);
+}
+
 __global__ void __launch_bounds__(256) thread_tree_kernel(const ThreadJob* __restrict__ jobs) {
     __shared__ long long sh[32];
     const ThreadJob job = jobs[blockIdx.x];
@@ -362,19 +380,61 @@ __global__ void __launch_bounds__(256) thread_tree_kernel(const ThreadJob* __res
     o.sum_offload = sW;
     o.sum_busiest = sTM;
     o.max_busiest = maxM;
-    if (E == 0) {
-        fl |= 0x1u;
-        o.pe = o.mpi_pe = o.mpi_lb = o.mpi_ce = o.thread_lb = o.oe = 1.0;
-    } else {
-        o.pe = ratio_k(sU, E, nT);
-        o.mpi_pe = ratio_k(sTM, E, nT);
-        o.mpi_lb = ratio_k(sTM, nT, maxM);
-        o.mpi_ce = ratio(maxM, E);
-        o.thread_lb = ratio(sU + sW, sTM);
-        o.oe = ratio(sU, sU + sW);
-    }
     o.flags = fl;
+    form_thread_ratios(o);
     *job.out = o;
+}
+
+// Thread-tree aggregates of disjoint shards of a trace (whole processes with
+// their threads) combine exactly: E and max M by max, the sums and the
+// process and thread counts by addition, the status flags by or; the ratios
+// are then formed by the same code.
+__global__ void __launch_bounds__(256) thread_combine_kernel(const ThreadOut* __restrict__ parts, uint32_t n_parts,
+                                                             ThreadOut* __restrict__ out) {
+    __shared__ long long sh[32];
+    auto add = [](long long a, long long b) { return a + b; };
+    auto mx = [](long long a, long long b) { return a > b ? a : b; };
+    auto bor = [](long long a, long long b) { return a | b; };
+    long long E = 0, sU = 0, sW = 0, sTM = 0, maxM = 0, np = 0, nt = 0, fl = 0;
+    for (uint32_t k = threadIdx.x; k < n_parts; k += blockDim.x) {
+        const ThreadOut& p = parts[k];
+        E = mx(E, p.elapsed_ns);
+        sU += p.sum_useful;
+        sW += p.sum_offload;
+        sTM += p.sum_busiest;
+        maxM = mx(maxM, p.max_busiest);
+        np += p.n_procs;
+        nt += p.n_threads;
+        fl |= p.flags & 0x700u;   // status bits; EMPTY is recomputed
+    }
+    E = block_reduce<long long>(E, mx, sh);
+    sU = block_reduce<long long>(sU, add, sh);
+    sW = block_reduce<long long>(sW, add, sh);
+    sTM = block_reduce<long long>(sTM, add, sh);
+    maxM = block_reduce<long long>(maxM, mx, sh);
+    np = block_reduce<long long>(np, add, sh);
+    nt = block_reduce<long long>(nt, add, sh);
+    fl = block_reduce<long long>(fl, bor, sh);
+    if (threadIdx.x != 0) return;
+    ThreadOut o;
+    o.trace_id = parts[0].trace_id;
+    o.region = parts[0].region;
+    o.n_procs = static_cast<uint32_t>(np);
+    o.n_threads = static_cast<uint32_t>(nt);
+    o.elapsed_ns = E;
+    o.sum_useful = sU;
+    o.sum_offload = sW;
+    o.sum_busiest = sTM;
+    o.max_busiest = maxM;
+    o.flags = static_cast<uint32_t>(fl);
+    form_thread_ratios(o);
+    *out = o;
+}
+
+cudaError_t launch_thread_combine(const ThreadOut* parts, uint32_t n_parts, ThreadOut* out, cudaStream_t stream) {
+    if (n_parts == 0) return cudaSuccess;
+    thread_combine_kernel<<<1, 256, 0, stream>>>(parts, n_parts, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_thread_tree(const ThreadJob* jobs, uint32_t n_jobs, cudaStream_t stream) {

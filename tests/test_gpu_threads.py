@@ -164,6 +164,37 @@ def test_invalid_records_and_empty_regions():
     c.close()
 
 
+def test_shards_of_whole_processes_combine_exactly():
+    """A threaded trace split into 1-4 shards of whole processes, each reduced
+    as its own trace: talp_gpu_thread_metrics_combine of the shards' records
+    equals the whole trace's thread tree (and the oracle's) bit for bit."""
+    import paper_2603_26576_b300 as P
+    from paper_2603_26576_b300 import shard
+    c = make_ctx()
+    base = tg.random_trace(13, trace_id=50, n_ranks=6, devices_per_rank=2, dev_events=800, host_events=500,
+                           n_regions=3)
+    t = tg.add_threads(base, [3, 1, 4, 1, 5, 2], seed=6)
+    po = t.meta["proc_off"].astype(np.int64)
+    c.ingest([t])
+    whole = c.thread_metrics(t.trace_id, po)
+    for cuts in ([0, 6], [0, 2, 6], [0, 1, 4, 6], [0, 1, 2, 3, 6]):
+        parts = {r: [] for r in range(t.n_regions)}
+        for k in range(len(cuts) - 1):
+            p0, p1 = cuts[k], cuts[k + 1]
+            sh = shard.shard_of(t, np.arange(po[p0], po[p1]), trace_id=60 + k)
+            c.ingest([sh])
+            spo = po[p0:p1 + 1] - po[p0]
+            for r, rec in enumerate(c.thread_metrics(60 + k, spo)):
+                parts[r].append(dict(rec, trace_id=t.trace_id))
+        for r in range(t.n_regions):
+            got = P.talp_gpu_thread_metrics_combine(c.ctx, parts[r])
+            assert got == whole[r], (cuts, r)
+            assert_thread_equal(got, oracle.thread_metrics(t, r, po), ("combine", cuts, r))
+    st, _ = P.talp_gpu_thread_metrics_combine(c.ctx, [whole[0], whole[1]], check=False)
+    assert st == -1                                            # mixed regions
+    c.close()
+
+
 def test_bad_process_tables():
     import paper_2603_26576_b300 as P
     c = make_ctx()
