@@ -10,7 +10,9 @@ device segment and no carry crosses GPUs); each GPU reduces its shard to the
 region aggregates (one talp_gpu_metrics record per region, 184 bytes), the
 records are all-gathered, and talp_gpu_metrics_combine forms the ratios of
 the whole trace.  Independent traces (the batched form) are split by whole
-traces with no exchange at all.
+traces with no exchange at all.  The host tree with threads splits by whole
+processes (each with all of its threads and their devices) and exchanges
+talp_gpu_thread_tree records (112 bytes) the same way.
 """
 from __future__ import annotations
 
@@ -22,6 +24,7 @@ import numpy as np
 from . import _lib
 
 RECORD_BYTES = ctypes.sizeof(_lib.talp_gpu_metrics)
+THREAD_RECORD_BYTES = ctypes.sizeof(_lib.talp_gpu_thread_tree)
 
 
 def partition_ranks(records_per_rank, world: int) -> list:
@@ -45,6 +48,26 @@ def partition_ranks(records_per_rank, world: int) -> list:
     cuts.append(n)
     # ranks left over by ties go to the empty blocks at the end
     return [np.arange(cuts[k], cuts[k + 1], dtype=np.int64) for k in range(world)]
+
+
+def partition_processes(records_per_unit, proc_off, world: int) -> list:
+    """Contiguous blocks of whole processes (proc_off groups the host units),
+    balanced by record count as partition_ranks does; returns per GPU the
+    block's process indices."""
+    po = np.asarray(proc_off, np.int64)
+    w = np.asarray(records_per_unit, np.float64)
+    cum = np.concatenate([[0.0], np.cumsum(w)])
+    per_proc = cum[po[1:]] - cum[po[:-1]]
+    return partition_ranks(per_proc, world)
+
+
+def units_of(proc_off, procs) -> np.ndarray:
+    """Host units (threads) of a contiguous block of processes."""
+    po = np.asarray(proc_off, np.int64)
+    procs = np.asarray(procs, np.int64)
+    if procs.size == 0:
+        return np.zeros(0, np.int64)
+    return np.arange(po[procs[0]], po[procs[-1] + 1], dtype=np.int64)
 
 
 def partition_traces(records_per_trace, world: int) -> list:
@@ -120,19 +143,38 @@ def unpack(buf) -> list:
     return [_lib.talp_gpu_metrics.from_buffer_copy(buf[k].tobytes()) for k in range(buf.shape[0])]
 
 
-def exchange(records, group=None) -> list:
+def pack_threads(records) -> np.ndarray:
+    """talp_gpu_thread_tree records (structs or dicts) -> uint8[k, THREAD_RECORD_BYTES]."""
+    out = np.zeros((len(records), THREAD_RECORD_BYTES), np.uint8)
+    for k, r in enumerate(records):
+        if not isinstance(r, _lib.talp_gpu_thread_tree):
+            x = _lib.talp_gpu_thread_tree()
+            for f, _ in _lib.talp_gpu_thread_tree._fields_:
+                setattr(x, f, r[f])
+            r = x
+        out[k] = np.frombuffer(bytes(r), np.uint8)
+    return out
+
+
+def unpack_threads(buf) -> list:
+    """uint8[k, THREAD_RECORD_BYTES] -> thread-tree records as dicts."""
+    return _lib.thread_tree_from_bytes(np.ascontiguousarray(buf, np.uint8).tobytes())
+
+
+def exchange(records, group=None, threads=False) -> list:
     """All-gather the region records of every rank of the process group:
     returns, per region, the list of records of all ranks (rank order).
+    talp_gpu_metrics records, or thread-tree records with threads=True.
     Works on gloo (CPU tensors) and nccl (CUDA tensors)."""
     import torch
     import torch.distributed as dist
-    local = torch.from_numpy(pack(records))
+    local = torch.from_numpy(pack_threads(records) if threads else pack(records))
     if dist.get_backend(group) == "nccl":
         local = local.cuda()
     world = dist.get_world_size(group)
     bufs = [torch.empty_like(local) for _ in range(world)]
     dist.all_gather(bufs, local, group=group)
-    per_rank = [unpack(b.cpu().numpy()) for b in bufs]
+    per_rank = [(unpack_threads if threads else unpack)(b.cpu().numpy()) for b in bufs]
     return [[per_rank[w][r] for w in range(world)] for r in range(len(records))]
 
 
@@ -163,3 +205,36 @@ def sharded_metrics(ctx, t, group=None, stream=None) -> list:
     parts = exchange(mine, group)
     return [_lib.metrics_to_dict(_lib.talp_gpu_metrics_combine(ctx.ctx, parts[r], stream, check=False)[1])
             for r in range(R)]
+
+
+def sharded_thread_metrics(ctx, t, proc_off, group=None, stream=None) -> list:
+    """Host tree with threads of every region of trace `t` (host units =
+    threads, grouped by proc_off) reduced across the ranks of the process
+    group: this process ingests its block of whole processes into `ctx`,
+    exchanges the thread-tree records and combines them."""
+    import torch.distributed as dist
+    world, me = dist.get_world_size(group), dist.get_rank(group)
+    po = np.asarray(proc_off, np.int64)
+    hoff = np.asarray(t.host_off, np.int64)
+    doff = np.asarray(t.dev_off, np.int64)
+    dstart = np.concatenate([[0], np.cumsum(np.asarray(t.devices_per_rank, np.int64))])
+    rec = np.diff(hoff) + (doff[dstart[1:]] - doff[dstart[:-1]])
+    procs = partition_processes(rec, po, world)[me]
+    s = shard_of(t, units_of(po, procs))
+    R = s.n_regions
+    if procs.size:
+        ctx.ingest([s])
+        mine = _lib.talp_gpu_thread_metrics(ctx.ctx, s.trace_id, _lib.TALP_GPU_ALL_REGIONS,
+                                            po[procs[0]:procs[-1] + 2] - po[procs[0]], stream, n_regions=R,
+                                            check=False)[1]
+        ctx.reset(s.trace_id)
+    else:
+        mine = [{f: 0 for f, _ in _lib.talp_gpu_thread_tree._fields_} for _ in range(R)]
+        for r in range(R):
+            mine[r].update(trace_id=s.trace_id, region=r)
+    parts = exchange(mine, group, threads=True)
+    out = []
+    for r in range(R):
+        live = [p for p in parts[r] if p["n_threads"]]
+        out.append(_lib.talp_gpu_thread_metrics_combine(ctx.ctx, live, stream, check=False)[1])
+    return out

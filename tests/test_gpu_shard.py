@@ -80,6 +80,14 @@ def test_sharded_metrics_through_a_process_group():
         got = shard.sharded_metrics(c, t)
         for r in range(t.n_regions):
             assert_metrics_equal(got[r], oracle.region_metrics(t, r), ("process-group", r))
+        # the host tree with threads through the same group
+        tt = tg.add_threads(t, [1 + i % 4 for i in range(t.n_ranks)], seed=2)
+        po = tt.meta["proc_off"]
+        got = shard.sharded_thread_metrics(c, tt, po)
+        for r in range(tt.n_regions):
+            want = oracle.thread_metrics(tt, r, po)
+            for f in oracle.THREAD_INT_FIELDS + oracle.THREAD_RATIO_FIELDS + ("flags", "n_procs"):
+                assert got[r][f] == want[f], ("process-group threads", r, f)
         c.close()
     finally:
         dist.destroy_process_group()

@@ -130,3 +130,89 @@ def test_exchange_world2_gloo():
     assert codes == [0, 0], codes
     res = dict(q.get(timeout=5) for _ in range(2))
     assert res == {0: True, 1: True}
+
+
+# ---------------------------------------------------------------- threads
+
+THREAD_MAX = ("elapsed_ns", "max_busiest")
+THREAD_SUM = ("sum_useful", "sum_offload", "sum_busiest", "n_threads", "n_procs")
+
+
+def _threaded():
+    return tg.add_threads(_trace(5), [3, 1, 4, 1, 5, 2, 2], seed=3)
+
+
+def _combine_thread_ints(parts):
+    out = {f: max(p[f] for p in parts) for f in THREAD_MAX}
+    out.update({f: sum(p[f] for p in parts) for f in THREAD_SUM})
+    return out
+
+
+def _thread_shards(t, world):
+    po = t.meta["proc_off"].astype(np.int64)
+    rec = [int(t.host_off[i + 1] - t.host_off[i]) for i in range(t.n_ranks)]
+    out = []
+    for procs in shard.partition_processes(rec, po, world):
+        if procs.size:
+            out.append((shard.shard_of(t, shard.units_of(po, procs)), po[procs[0]:procs[-1] + 2] - po[procs[0]]))
+    return out
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 4, 7, 9])
+def test_thread_shards_of_whole_processes_combine(world):
+    t = _threaded()
+    po = t.meta["proc_off"]
+    rec = [int(t.host_off[i + 1] - t.host_off[i]) for i in range(t.n_ranks)]
+    blocks = shard.partition_processes(rec, po, world)
+    np.testing.assert_array_equal(np.concatenate(blocks), np.arange(len(po) - 1))
+    shards = _thread_shards(t, world)
+    assert sum(s.n_records for s, _ in shards) == t.n_records
+    for r in range(t.n_regions):
+        whole = oracle.thread_metrics(t, r, po)
+        got = _combine_thread_ints([oracle.thread_metrics(s, r, spo) for s, spo in shards])
+        for f in THREAD_MAX + THREAD_SUM:
+            assert got[f] == whole[f], (world, r, f)
+
+
+def test_pack_threads_round_trip():
+    t = _threaded()
+    d = dict(oracle.thread_metrics(t, 2, t.meta["proc_off"]), trace_id=t.trace_id, region=2)
+    back = shard.unpack_threads(shard.pack_threads([d, d]))
+    assert back == [d, d]
+
+
+def _thread_worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        t = _threaded()
+        s, spo = _thread_shards(t, world)[rank]
+        mine = [dict(oracle.thread_metrics(s, r, spo), trace_id=t.trace_id, region=r) for r in range(t.n_regions)]
+        gathered = shard.exchange(mine, threads=True)
+        ok = True
+        for r in range(t.n_regions):
+            assert [p["region"] for p in gathered[r]] == [r] * world
+            got = _combine_thread_ints(gathered[r])
+            whole = oracle.thread_metrics(t, r, t.meta["proc_off"])
+            ok &= all(got[f] == whole[f] for f in THREAD_MAX + THREAD_SUM)
+        q.put((rank, ok))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_thread_exchange_world2_gloo():
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_thread_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    for p in ps:
+        p.join(timeout=120)
+    codes = [p.exitcode for p in ps]
+    assert codes == [0, 0], codes
+    res = dict(q.get(timeout=5) for _ in range(2))
+    assert res == {0: True, 1: True}
