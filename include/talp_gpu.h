@@ -15,6 +15,10 @@
  *               device obtained by the flattening of Sec. 4.2.
  * All interval arithmetic is exact int64 nanoseconds on the GPU; the nine
  * ratios are formed in FP64 with a fixed expression order.
+ * Beyond the two trees: raw activity buffers in completion order
+ * (talp_gpu_ingest_raw), the per-device concurrency profile, POP scaling
+ * factors across runs, and a host tree with threads (a variant the paper
+ * does not define, equal to the host tree with one thread per process).
  *
  * Conventions shared by every call
  * --------------------------------
