@@ -161,6 +161,7 @@ struct talp_gpu_ctx {
     int dependents = 0;                  // live plans and servers on this context
     std::unordered_map<uint64_t, RawHold*> holds;   // trace id -> held-back raw records
     bool raw_inner = false;              // ingest_events called by ingest_raw
+    std::vector<uint8_t> raw_presort;    // with raw_inner: per device of the ingest, known out of order
 };
 
 const TraceDev* talp::trace_device_desc(talp_gpu_ctx* c, uint64_t trace_id, uint32_t* n_regions) {
@@ -515,6 +516,7 @@ talp_gpu_status fill_ingest(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches
     size_t pw = 0, bk_used = 0, nf = 0;
     uint32_t nj = 0;
     uint64_t si = 0, pos = 0;
+    size_t presort_at = 0;   // first device of this batch in c->raw_presort
     for (size_t k = 0; k < nb; ++k) {
         const talp_gpu_trace_batch& b = batches[k];
         TraceState* t = ts[k];
@@ -593,10 +595,16 @@ talp_gpu_status fill_ingest(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches
             s.pad[0] = sflag;
             if (L.sorting) restore[si] = bkd ? bkd + static_cast<size_t>(g) * R * 3 : nullptr;
             sstart[si] = pos;
-            send[si] = pos + s.n;
-            pos += s.n + L.seg_cost;
+            if (sflag && c->raw_inner && presort_at + g < c->raw_presort.size() && c->raw_presort[presort_at + g]) {
+                s.pad[0] |= kSegPresort;   // not in the first sweep: sorted, then swept
+                send[si] = pos;
+            } else {
+                send[si] = pos + s.n;
+                pos += s.n + L.seg_cost;
+            }
             ++si;
         }
+        presort_at += m;
         for (uint32_t i = 0; i < n; ++i) {
             SegDesc& s = sd[si];
             memset(&s, 0, sizeof(SegDesc));
@@ -1120,6 +1128,7 @@ talp_gpu_status talp_gpu_ingest_raw(talp_gpu_ctx* c, const talp_gpu_raw_batch* r
     const size_t o_cnt = o; o = align_up(o + 8 * mtot, 256);
     const size_t o_fcnt = o; o = align_up(o + 8 * mtot, 256);
     const size_t o_hcnt = o; o = align_up(o + 8 * nrk, 256);
+    const size_t o_nstr = o; o = align_up(o + 4 * mtot, 256);
     const size_t o_st = o; o += 256;
     const size_t down_bytes = o - o_cnt;
 
@@ -1249,7 +1258,8 @@ talp_gpu_status talp_gpu_ingest_raw(talp_gpu_ctx* c, const talp_gpu_raw_batch* r
     uint32_t* dst = reinterpret_cast<uint32_t*>(R + o_st);
     TALP_CUDA(launch_raw_count(dtiles, static_cast<uint32_t>(nt), dranks, static_cast<uint32_t>(nrk),
                                reinterpret_cast<uint32_t*>(R + o_hist), reinterpret_cast<uint64_t*>(R + o_offs), dmoves,
-                               reinterpret_cast<uint64_t*>(R + o_cnt), dst, grid, stream));
+                               reinterpret_cast<uint64_t*>(R + o_cnt), reinterpret_cast<uint32_t*>(R + o_nstr), dst,
+                               grid, stream));
     TALP_CUDA(launch_raw_scatter(dtiles, static_cast<uint32_t>(nt), dranks, reinterpret_cast<const uint64_t*>(R + o_offs),
                                  reinterpret_cast<int64_t*>(R + o_lse), reinterpret_cast<uint8_t*>(R + o_ltag), dst,
                                  c->wait_limit, grid, stream));
@@ -1268,6 +1278,7 @@ talp_gpu_status talp_gpu_ingest_raw(talp_gpu_ctx* c, const talp_gpu_raw_batch* r
     const uint64_t* cnt = reinterpret_cast<const uint64_t*>(D);
     const uint64_t* fcnt = reinterpret_cast<const uint64_t*>(D + (o_fcnt - o_cnt));
     const uint64_t* hcnt = reinterpret_cast<const uint64_t*>(D + (o_hcnt - o_cnt));
+    const uint32_t* nstr = reinterpret_cast<const uint32_t*>(D + (o_nstr - o_cnt));
     uint32_t status = 0;
     memcpy(&status, D + (o_st - o_cnt), 4);
     if (status) {
@@ -1282,11 +1293,18 @@ talp_gpu_status talp_gpu_ingest_raw(talp_gpu_ctx* c, const talp_gpu_raw_batch* r
     std::vector<talp_gpu_trace_batch> tb(nb);
     uint64_t* fbase = static_cast<uint64_t*>(c->up.p) + tab_bytes / 8;   // the table upload has completed
     uint64_t g = 0, ri = 0;
+    // a device whose lane is several non-empty streams is out of start order
+    // (whatever the streams' times, it is sorted): it skips the first sweep.
+    // Held-back lanes are a subset of their streams and keep the usual path.
+    c->raw_presort.assign(mtot, 0);
     for (size_t k = 0; k < nb; ++k) {
         const talp_gpu_raw_batch& b = rb[k];
         const uint64_t* cn = hb[k] ? fcnt : cnt;
         dev_off[k].assign(m_of[k] + 1, 0);
-        for (uint64_t d = 0; d < m_of[k]; ++d, ++g) dev_off[k][d + 1] = dev_off[k][d] + cn[g];
+        for (uint64_t d = 0; d < m_of[k]; ++d, ++g) {
+            dev_off[k][d + 1] = dev_off[k][d] + cn[g];
+            c->raw_presort[g] = (!hb[k] && nstr[g] > 1) ? 1 : 0;
+        }
         uint64_t dl = 0;   // first device of rank i within the batch
         for (uint32_t i = 0; i < b.n_ranks; ++i, ++ri) {
             fbase[ri] = out_base[k] + dev_off[k][dl];
@@ -1338,6 +1356,7 @@ talp_gpu_status talp_gpu_ingest_raw(talp_gpu_ctx* c, const talp_gpu_raw_batch* r
     c->raw_inner = true;
     const talp_gpu_status st = talp_gpu_ingest_events(c, tb.data(), nb, stream_);
     c->raw_inner = false;
+    c->raw_presort.clear();
     TALP_CUDA(cudaEventRecord(c->ev_raw, stream));
     c->raw_used = true;
     return st;

@@ -108,6 +108,8 @@ struct FillJob {
 
 // SegDesc.pad[0] bits
 constexpr uint8_t kSegSortable = 1;   // device segment may be sorted when found out of order
+constexpr uint8_t kSegPresort = 2;    // known out of order (several streams of a raw buffer): left out
+                                      // of the first sweep and sorted, then swept
 
 // Control block of the sort stage (device memory; pointers into scratch).
 struct SortCtl {

@@ -44,8 +44,8 @@ cudaError_t launch_concurrency(const int64_t* se, const uint8_t* tag, const Conc
                                const ConcChunk* chunks, uint32_t n_chunks, int64_t* top, int64_t* in, int64_t* out,
                                uint32_t* status, cudaStream_t stream);
 cudaError_t launch_raw_count(const RawTile* tiles, uint32_t n_tiles, const RawRank* ranks, uint32_t n_ranks,
-                             uint32_t* hist, uint64_t* offs, RawMove* moves, uint64_t* dev_count, uint32_t* status,
-                             int grid, cudaStream_t stream);
+                             uint32_t* hist, uint64_t* offs, RawMove* moves, uint64_t* dev_count,
+                             uint32_t* dev_streams, uint32_t* status, int grid, cudaStream_t stream);
 cudaError_t launch_raw_scatter(const RawTile* tiles, uint32_t n_tiles, const RawRank* ranks, const uint64_t* offs,
                                int64_t* lse, uint8_t* ltag, uint32_t* status, int64_t wait_limit, int grid,
                                cudaStream_t stream);

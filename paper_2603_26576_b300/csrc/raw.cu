@@ -69,7 +69,8 @@ __global__ void __launch_bounds__(kRawThreads) raw_hist_kernel(const RawTile* __
 // range and each device's count
 __global__ void __launch_bounds__(kBuckets) raw_scan_kernel(const RawRank* __restrict__ ranks, uint32_t n_ranks,
                                                             const uint32_t* __restrict__ hist, uint64_t* __restrict__ offs,
-                                                            RawMove* __restrict__ moves, uint64_t* __restrict__ dev_count) {
+                                                            RawMove* __restrict__ moves, uint64_t* __restrict__ dev_count,
+                                                            uint32_t* __restrict__ dev_streams) {
     __shared__ uint64_t s_tot[kBuckets];
     const uint32_t b = threadIdx.x;
     for (uint32_t r = blockIdx.x; r < n_ranks; r += gridDim.x) {
@@ -115,8 +116,13 @@ __global__ void __launch_bounds__(kBuckets) raw_scan_kernel(const RawRank* __res
         }
         if (b < rk.D) {
             uint64_t c = 0;
-            for (int s = 0; s < 32; ++s) c += s_tot[b * 32 + s];
+            uint32_t ns = 0;
+            for (int s = 0; s < 32; ++s) {
+                c += s_tot[b * 32 + s];
+                ns += s_tot[b * 32 + s] ? 1u : 0u;
+            }
             dev_count[rk.dev0 + b] = c;
+            dev_streams[rk.dev0 + b] = ns;
         }
         __syncthreads();
     }
@@ -322,12 +328,12 @@ __global__ void __launch_bounds__(kRawThreads) raw_move_kernel(const RawTile* __
 }  // namespace
 
 cudaError_t launch_raw_count(const RawTile* tiles, uint32_t n_tiles, const RawRank* ranks, uint32_t n_ranks,
-                             uint32_t* hist, uint64_t* offs, RawMove* moves, uint64_t* dev_count, uint32_t* status,
-                             int grid, cudaStream_t stream) {
+                             uint32_t* hist, uint64_t* offs, RawMove* moves, uint64_t* dev_count,
+                             uint32_t* dev_streams, uint32_t* status, int grid, cudaStream_t stream) {
     if (n_tiles) raw_hist_kernel<<<grid, kRawThreads, 0, stream>>>(tiles, n_tiles, ranks, hist, status);
     if (n_ranks)
         raw_scan_kernel<<<n_ranks < 65535u ? n_ranks : 65535u, kBuckets, 0, stream>>>(ranks, n_ranks, hist, offs,
-                                                                                     moves, dev_count);
+                                                                                     moves, dev_count, dev_streams);
     return cudaGetLastError();
 }
 

@@ -40,9 +40,14 @@ __device__ __forceinline__ int passes_for(int64_t mn, int64_t mx) {
     return (bits + 7) / 8;
 }
 
-// radix passes of flagged segment k (0 when it is merged instead)
+// nruns of a flagged segment found already in start order (a presorted
+// segment whose streams do not interleave): neither merged nor radix sorted,
+// swept again from its own records
+constexpr uint32_t kInOrder = 0xFFFFFFFFu;
+
+// radix passes of flagged segment k (0 when it is merged instead, or in order)
 __device__ __forceinline__ int radix_passes(const SortCtl* ctl, uint32_t k) {
-    return ctl->rounds[k] ? 0 : passes_for(ctl->mn[k], ctl->mx[k]);
+    return (ctl->rounds[k] || ctl->nruns[k] == kInOrder) ? 0 : passes_for(ctl->mn[k], ctl->mx[k]);
 }
 
 // segment k of the flagged list owning tile t
@@ -84,7 +89,8 @@ __global__ void __launch_bounds__(1024) sort_plan_kernel(const SegDesc* __restri
         uint64_t n = 0;
         if (s < n_segs) {
             const SegDesc& d = segs[s];
-            f = !d.is_host && (d.pad[0] & kSegSortable) && (seg_flags[s] & ST_UNSORTED);
+            f = !d.is_host && (d.pad[0] & kSegSortable) &&
+                ((seg_flags[s] & ST_UNSORTED) || (d.pad[0] & kSegPresort));
             n = f ? d.n : 0;
         }
         const uint64_t tiles = f ? (n + kSortTile - 1) / kSortTile : 0;
@@ -356,6 +362,11 @@ __global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(const SegDes
 __global__ void sort_merge_plan_kernel(const SegDesc* __restrict__ segs, SortCtl* ctl) {
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < ctl->nflag; k += gridDim.x * blockDim.x) {
         const uint32_t c = ctl->nruns[k];
+        if (c == 0 && (segs[ctl->list[k]].pad[0] & kSegPresort)) {
+            ctl->rounds[k] = 0;
+            ctl->nruns[k] = kInOrder;
+            continue;
+        }
         if (c == 0 || c + 1 > static_cast<uint32_t>(kMaxRuns)) {
             ctl->rounds[k] = 0;
             atomicMax(&ctl->max_passes, static_cast<uint32_t>(passes_for(ctl->mn[k], ctl->mx[k])));
@@ -555,11 +566,13 @@ __global__ void __launch_bounds__(256) sort_resweep_plan_kernel(const SegDesc* _
         }
         if (k < nflag) {
             SegDesc s = segs[ctl->list[k]];
-            const int P = ctl->rounds[k] ? static_cast<int>(ctl->rounds[k]) : passes_for(ctl->mn[k], ctl->mx[k]);
-            const int b = (P - 1) & 1;
-            s.se = ctl->buf_se[b] + 2 * ctl->rec_base[k];
-            s.tag = ctl->buf_tag[b] + ctl->rec_base[k];
-            s.tag_limit = ctl->buf_tag_limit[b];
+            if (ctl->nruns[k] != kInOrder) {
+                const int P = ctl->rounds[k] ? static_cast<int>(ctl->rounds[k]) : passes_for(ctl->mn[k], ctl->mx[k]);
+                const int b = (P - 1) & 1;
+                s.se = ctl->buf_se[b] + 2 * ctl->rec_base[k];
+                s.tag = ctl->buf_tag[b] + ctl->rec_base[k];
+                s.tag_limit = ctl->buf_tag_limit[b];
+            }
             out[k] = s;
             out_start[k] = ctl->rec_base[k];
             out_rend[k] = ctl->rec_base[k] + s.n;

@@ -236,3 +236,46 @@ def test_hold_state_ends_with_a_new_trace_of_the_id(ctx):
     assert ctx.raw_held(t.trace_id) == 0
     _hold_back_run(ctx, t, 3, 2)
     ctx.reset()
+
+
+def test_streams_that_do_not_interleave(ctx):
+    """Devices whose lane is several streams are sorted without a first
+    sweep; here some of them are already in start order (streams one after
+    the other in time, or every record starting at the same time) and are
+    swept from their own records, others interleave and are merged.  Every
+    unit equals the oracle."""
+    rng = np.random.default_rng(8)
+    segs = []
+    for kind in ("phases", "interleaved", "same_start", "one_stream", "phases", "empty"):
+        if kind == "empty":
+            segs.append((np.zeros((0, 2), np.int64), np.zeros(0, np.uint8)))
+            continue
+        n = 600
+        if kind == "phases":          # stream 0, then stream 1, then stream 2, in time
+            s = np.sort(rng.integers(0, 30_000, n))
+            st = np.minimum(np.arange(n) * 3 // n, 2)
+        elif kind == "interleaved":
+            s = np.sort(rng.integers(0, 30_000, n))
+            st = rng.integers(0, 3, n)
+        elif kind == "same_start":
+            s = np.full(n, 777)
+            st = rng.integers(0, 2, n)
+        else:
+            s = np.sort(rng.integers(0, 30_000, n))
+            st = np.zeros(n, np.int64)
+        d = rng.integers(1, 400, n)
+        se = np.stack([s, s + d], axis=1).astype(np.int64)
+        kd = rng.choice(np.array([0, 0, 0, 1, 2], np.uint8), n)
+        segs.append((se, tg.make_tag(kd, st.astype(np.uint8))))
+    dpr = np.array([3, 3], np.uint32)
+    dev_off = np.concatenate([[0], np.cumsum([x[0].shape[0] for x in segs])]).astype(np.uint64)
+    host = [np.array([[0, 12_000], [12_000, 31_000]], np.int64), np.array([[0, 31_000]], np.int64)]
+    t = tg.Trace(trace_id=90, n_ranks=2, devices_per_rank=dpr,
+                 region_window=np.array([[[0, 31_000], [0, 31_000]], [[5_000, 20_000], [100, 900]]], np.int64),
+                 host_se=np.concatenate(host), host_state=np.array([0, 1, 2], np.uint8),
+                 host_off=np.array([0, 2, 3], np.uint64), dev_se=np.concatenate([x[0] for x in segs]),
+                 dev_tag=np.concatenate([x[1] for x in segs]), dev_off=dev_off)
+    raw = tg.to_raw(t)
+    ctx.ingest_raw([raw])
+    assert_trace_equal(ctx, t, "streams-in-order")
+    ctx.reset()
