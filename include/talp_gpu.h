@@ -84,6 +84,10 @@ enum { TALP_DEV_KERNEL = 0, TALP_DEV_H2D = 1, TALP_DEV_D2H = 2, TALP_DEV_D2D = 3
 #define TALP_GPU_DEVICE_PTRS     0x1u  /* host_se/host_state/dev_se/dev_tag are device pointers */
 #define TALP_GPU_SORTED_BY_START 0x2u  /* caller asserts each device's records are in start order */
 #define TALP_GPU_APPEND          0x4u  /* fold into the trace's running state (later time slice) */
+#define TALP_GPU_NOT_SORTED      0x10u /* caller hint: device records are out of start order (e.g.
+                                        * grouped by stream): every device goes straight to the
+                                        * sort stage without a first sweep; one found in order is
+                                        * swept from its own records.  Not with SORTED_BY_START. */
 
 /*
  * One trace (or one later time slice of it with TALP_GPU_APPEND).

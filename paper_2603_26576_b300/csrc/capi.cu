@@ -300,8 +300,10 @@ talp_gpu_status check_batch(const talp_gpu_trace_batch& b, uint64_t* n_host, uin
     if (b.n_regions == 0 || b.n_regions > TALP_GPU_MAX_REGIONS)
         return fail(TALP_GPU_EINVAL, "n_regions must be in 1..8");
     if (b.reserved != 0) return fail(TALP_GPU_EINVAL, "reserved must be 0");
-    if (b.flags & ~(TALP_GPU_DEVICE_PTRS | TALP_GPU_SORTED_BY_START | TALP_GPU_APPEND))
+    if (b.flags & ~(TALP_GPU_DEVICE_PTRS | TALP_GPU_SORTED_BY_START | TALP_GPU_APPEND | TALP_GPU_NOT_SORTED))
         return fail(TALP_GPU_EINVAL, "unknown flag bits");
+    if ((b.flags & TALP_GPU_SORTED_BY_START) && (b.flags & TALP_GPU_NOT_SORTED))
+        return fail(TALP_GPU_EINVAL, "SORTED_BY_START and NOT_SORTED together");
     if (!b.devices_per_rank || !b.region_window || !b.host_off || !b.dev_off)
         return fail(TALP_GPU_EINVAL, "null header array");
     uint64_t m = 0;
@@ -595,7 +597,9 @@ talp_gpu_status fill_ingest(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches
             s.pad[0] = sflag;
             if (L.sorting) restore[si] = bkd ? bkd + static_cast<size_t>(g) * R * 3 : nullptr;
             sstart[si] = pos;
-            if (sflag && c->raw_inner && presort_at + g < c->raw_presort.size() && c->raw_presort[presort_at + g]) {
+            const bool presort = (b.flags & TALP_GPU_NOT_SORTED) ||
+                                 (c->raw_inner && presort_at + g < c->raw_presort.size() && c->raw_presort[presort_at + g]);
+            if (sflag && presort) {
                 s.pad[0] |= kSegPresort;   // not in the first sweep: sorted, then swept
                 send[si] = pos;
             } else {

@@ -145,3 +145,29 @@ def test_unsorted_with_many_warps_per_segment():
         assert_trace_equal(c, t, "unsorted-big")
     finally:
         c.close()
+
+
+def test_not_sorted_hint():
+    """TALP_GPU_NOT_SORTED sends every device to the sort stage without a first
+    sweep: records grouped by stream (merge path), shuffled (radix path),
+    already in start order (swept from their own records), and APPEND slices
+    all equal the oracle; the hint with SORTED_BY_START is refused."""
+    import paper_2603_26576_b300 as P
+    from test_gpu_parity import _split_by_time
+    c = make_ctx()
+    base = tg.random_trace(31, trace_id=95, n_ranks=3, devices_per_rank=[2, 1, 3], dev_events=2500,
+                           host_events=700, n_regions=3)
+    for k, t in enumerate((tg.interleave_lanes(base), tg.shuffle_segments(base, seed=4), base)):
+        t.trace_id = 95 + k
+        c.ingest([t], flags=P.TALP_GPU_NOT_SORTED)
+        assert_trace_equal(c, t, ("hint", k))
+    a, b = _split_by_time(tg.interleave_lanes(base), 0.5)
+    a.trace_id = b.trace_id = 99
+    c.ingest([a], flags=P.TALP_GPU_NOT_SORTED)
+    c.ingest([b], flags=P.TALP_GPU_NOT_SORTED | P.TALP_GPU_APPEND)
+    whole = tg.Trace(**{**base.__dict__})
+    whole.trace_id = 99
+    assert_trace_equal(c, whole, "hint-append")
+    with pytest.raises(P.TalpGpuError):
+        c.ingest([base], flags=P.TALP_GPU_NOT_SORTED | P.TALP_GPU_SORTED_BY_START)
+    c.close()
