@@ -1298,8 +1298,9 @@ talp_gpu_status talp_gpu_ingest_raw(talp_gpu_ctx* c, const talp_gpu_raw_batch* r
     uint64_t* fbase = static_cast<uint64_t*>(c->up.p) + tab_bytes / 8;   // the table upload has completed
     uint64_t g = 0, ri = 0;
     // a device whose lane is several non-empty streams is out of start order
-    // (whatever the streams' times, it is sorted): it skips the first sweep.
-    // Held-back lanes are a subset of their streams and keep the usual path.
+    // unless its streams happen not to interleave: it skips the first sweep
+    // (the sort stage finds and keeps a lane that is in order after all).
+    // With hold-back the fold lane holds a part of those streams.
     c->raw_presort.assign(mtot, 0);
     for (size_t k = 0; k < nb; ++k) {
         const talp_gpu_raw_batch& b = rb[k];
@@ -1307,7 +1308,7 @@ talp_gpu_status talp_gpu_ingest_raw(talp_gpu_ctx* c, const talp_gpu_raw_batch* r
         dev_off[k].assign(m_of[k] + 1, 0);
         for (uint64_t d = 0; d < m_of[k]; ++d, ++g) {
             dev_off[k][d + 1] = dev_off[k][d] + cn[g];
-            c->raw_presort[g] = (!hb[k] && nstr[g] > 1) ? 1 : 0;
+            c->raw_presort[g] = nstr[g] > 1 ? 1 : 0;
         }
         uint64_t dl = 0;   // first device of rank i within the batch
         for (uint32_t i = 0; i < b.n_ranks; ++i, ++ri) {
