@@ -169,14 +169,18 @@ typedef struct {
 /* ---------------------------------------------------------------- context */
 
 /*
- * Create a context on CUDA device `device`.  hbm_budget_bytes caps the device
- * memory the context may hold (traces, staging, workspace); 0 means 90% of
- * the device's free memory at creation.  *out receives the context.
+ * Create a context on CUDA device `device`.  (Library service, no passage:
+ * the context holds the per-trace running state that the at-runtime queries
+ * of Sec. 3.2 read.)  hbm_budget_bytes caps the device memory the context
+ * may hold (traces, staging, workspace); 0 means 90% of the device's free
+ * memory at creation.  *out receives the context; the caller owns it and
+ * frees it with talp_gpu_destroy.
  * Errors: EINVAL (null out, bad device), ECUDA.
  */
 talp_gpu_status talp_gpu_create(talp_gpu_ctx **out, int device, size_t hbm_budget_bytes);
 
-/* Free every device buffer and the context.  NULL is accepted.
+/* Free every device buffer and the context.  (Library service, no passage.)
+ * NULL is accepted.  Synchronises the context's device work first.
  * Errors: EBUSY (nothing freed) while a plan or a server created on the
  * context still exists: destroy those first. */
 talp_gpu_status talp_gpu_destroy(talp_gpu_ctx *ctx);
@@ -283,7 +287,9 @@ talp_gpu_status talp_gpu_region_metrics(talp_gpu_ctx *ctx, uint64_t trace_id, ui
 
 /*
  * Metrics of one region for n traces with one launch and one copy:
- * out_host[k] belongs to trace_ids[k].  Same errors as above (the first
+ * out_host[k] belongs to trace_ids[k] (the same Eqs. 1 and 6-12 per trace;
+ * batching serves many at-runtime queries at once, Sec. 3.2).  trace_ids
+ * and out_host are host memory [n].  Same errors as above (the first
  * failing trace decides the status; every entry is written).
  */
 talp_gpu_status talp_gpu_region_metrics_batch(talp_gpu_ctx *ctx, const uint64_t *trace_ids, size_t n,
@@ -589,14 +595,22 @@ talp_gpu_status talp_gpu_server_info(talp_gpu_server *srv, talp_gpu_server_stats
 /* Stop the server threads, close every job, free the server. NULL is accepted. */
 talp_gpu_status talp_gpu_server_destroy(talp_gpu_server *srv);
 
-/* Drop trace_id's state and return its HBM (TALP_GPU_ALL: every trace). */
+/* Drop trace_id's state and return its HBM (TALP_GPU_ALL: every trace).
+ * This ends a monitored run's running state: TALP keeps accumulating
+ * region times until the run ends and queries read them meanwhile
+ * (Sec. 3.2); a new trace of the same id starts from zero.  Synchronises
+ * the context's work on the trace first.  Errors: EBUSY (a plan uses the
+ * trace), ENOTFOUND (unknown id; TALP_GPU_ALL never fails this way). */
 talp_gpu_status talp_gpu_reset(talp_gpu_ctx *ctx, uint64_t trace_id);
 
-/* Device bytes the context currently holds, and its budget. */
+/* Device bytes the context currently holds, and its budget (host memory
+ * out pointers; either may be NULL).  Library service, no passage: the
+ * admission by HBM footprint that the served form applies. */
 talp_gpu_status talp_gpu_memory(talp_gpu_ctx *ctx, size_t *held_bytes, size_t *budget_bytes);
 
 /*
- * Kernel timing for benchmarks and tracing.  While enabled, every sweep
+ * Kernel timing for benchmarks and tracing (library service, no passage).
+ * While enabled, every sweep
  * launch (the pass over the records: flattening, host sums, validation) is
  * bracketed by CUDA events on the ingest stream.  talp_gpu_profile_read
  * synchronises those events, returns the totals since the last read and
@@ -624,27 +638,41 @@ talp_gpu_status talp_gpu_profile_read(talp_gpu_ctx *ctx, talp_gpu_profile_stats 
  * of it), and an allocation or free from the hook could fail or synchronise
  * the device and stall the application's streams.  No context is needed.
  * The scratch lives in one fixed-size __device__ array of the library
- * (under 6 MiB, held on every GPU that loads the library until the process
- * exits); the device used is the calling thread's current device.
+ * (under 6 MiB per device, held until the process exits); the device used is
+ * the calling thread's current device.
  *
- * b:        one trace with TALP_GPU_DEVICE_PTRS and TALP_GPU_SORTED_BY_START
- *           set and TALP_GPU_APPEND clear (records in device memory, each
+ * b:        one trace with flags exactly TALP_GPU_DEVICE_PTRS |
+ *           TALP_GPU_SORTED_BY_START (records in device memory, each
  *           device's records in start order); n_ranks + m must not exceed
  *           TALP_GPU_NOALLOC_MAX_UNITS, n_regions <= 8, else EINVAL.
  * out_host: n_regions metrics, one per region, in host memory.
- * The call synchronises `stream`.  The first call on a device looks up the
- * scratch's device address (make that first call before any stream capture).
- * Every call shares the one scratch array, which keeps the last call's
- * contents; each call clears what must start at zero.  Calls that overlap on
- * the GPU (two streams, or two host threads with different streams) race and
- * corrupt each other's results.
+ * The call synchronises `stream`.
+ *
+ * Set-up: the first call on a device looks up the scratch's device address
+ * (again after a device reset).  Under CUDA's default lazy module loading
+ * that first call also loads the array and the kernels' code, which the
+ * driver allocates (about 6 MiB plus code): make one first call -- a trace
+ * without records will do -- during set-up, before the application fills
+ * the device's memory and before any stream capture.  Later calls allocate
+ * nothing.
+ *
+ * Sharing: every call on a device uses the same array, which keeps the last
+ * call's contents; each call clears what must start at zero.  Calls whose
+ * GPU work overlapped would race on the array, so each call holds a lock of
+ * its device from its first enqueue until its stream has finished the work,
+ * also when it returns an error: calls through this library in one process
+ * are serialised per device and never overlap.
+ * TALP_GPU_WAIT_LIMIT (clock cycles, read at each call) bounds the
+ * device-side waits as for contexts.
  * Errors: EINVAL (limits, flags, invalid or out-of-order records; out_host is
  * written and its flags say why), ETIMEDOUT, ECUDA.
  */
 #define TALP_GPU_NOALLOC_MAX_UNITS 8192u
 talp_gpu_status talp_gpu_reduce_noalloc(const talp_gpu_trace_batch *b, talp_gpu_metrics *out_host, void *stream);
 
-/* Message of the last failing call on this thread ("" if none). */
+/* Message of the last failing call on this thread ("" if none; library
+ * service, no passage).  The string belongs to the library and stays valid
+ * until the thread's next failing call. */
 const char *talp_gpu_last_error(void);
 
 #ifdef __cplusplus

@@ -8,14 +8,25 @@
 // device and stall the application's own streams.  This entry point needs no
 // context and allocates nothing: its scratch (segment table, per-unit
 // partial sums, windows, running carries, warp records, metrics) lives in a
-// file-scope __device__ array of fixed size that every GPU loading the
-// library holds until the process exits.
+// file-scope __device__ array of fixed size.
 //
 // Limits: n_ranks + m <= TALP_GPU_NOALLOC_MAX_UNITS units, n_regions <= 8,
 // device record arrays already in start order (no sort scratch).
-// All calls share the one array: it keeps the last call's contents, every
-// call clears what must start at zero, and calls that overlap on the GPU
-// (different streams, or host threads racing) corrupt each other.
+//
+// Sharing: every call on a device uses that device's one copy of the array,
+// which keeps the last call's contents; every call clears what must start at
+// zero.  Two calls whose GPU work overlapped would race on it, so a call
+// holds a per-device lock from its first enqueue until its stream has
+// finished the work (on error paths too): calls made through this library in
+// one process never overlap on a device.
+//
+// Module loading: under CUDA's default lazy loading the array and the
+// kernels' code are loaded on the first call on each device, which is a
+// device allocation made by the driver.  Every call launches the same
+// kernels (also for a trace without records), so one first call during
+// set-up -- before the application fills the device's memory and before
+// any stream capture -- leaves nothing to load later.
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -64,11 +75,55 @@ static_assert(kScratchBytes <= (6u << 20), "no-alloc scratch stays within 6 MiB"
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 // Host copy of the uploaded part (pageable; cudaMemcpyAsync from pageable
-// memory has consumed the source when it returns).
+// memory has consumed the source when it returns).  One copy serves every
+// device: g_stage_mu is held while it is filled and copied.
 static unsigned char g_host_stage[kUploadBytes];
+std::mutex g_stage_mu;
 
-std::mutex g_mu;
-unsigned char* g_scratch_ptr[kMaxDevices] = {};
+// Per device: the lock held through a call's GPU work, and the scratch's
+// device address with the id of the context it was looked up in (a device
+// reset makes a new primary context, in which the array has a new address).
+struct DevSlot {
+    std::mutex mu;
+    unsigned char* scratch = nullptr;
+    unsigned long long ctx_id = 0;
+};
+DevSlot g_dev[kMaxDevices];
+
+// Driver calls reached through the runtime's entry-point query (the library
+// does not link the driver library itself).
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+
+// Id of the calling thread's current context; 0 when it cannot be had.
+unsigned long long current_ctx_id() {
+    static CtxGetCurrentFn get_cur = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_cur = reinterpret_cast<CtxGetCurrentFn>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(p);
+    });
+    if (!get_cur || !get_id) return 0;
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_cur(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
+// Device-side wait limit in clock cycles: TALP_GPU_WAIT_LIMIT as for
+// contexts (a negative value reports a time-out at once), else ~2 s.
+int64_t wait_limit_cycles() {
+    if (const char* s = getenv("TALP_GPU_WAIT_LIMIT")) return strtoll(s, nullptr, 10);
+    return 4000000000LL;
+}
 
 talp_gpu_status err(talp_gpu_status st, const char* msg) {
     set_last_error(msg);
@@ -81,8 +136,9 @@ extern "C" talp_gpu_status talp_gpu_reduce_noalloc(const talp_gpu_trace_batch* b
                                                   void* stream_) {
     if (!b || !out_host) return err(TALP_GPU_EINVAL, "null argument");
     const uint32_t need = TALP_GPU_DEVICE_PTRS | TALP_GPU_SORTED_BY_START;
-    if ((b->flags & need) != need || (b->flags & TALP_GPU_APPEND) || b->reserved)
-        return err(TALP_GPU_EINVAL, "no-alloc reduction takes device records in start order, no APPEND");
+    if (b->flags != need || b->reserved)
+        return err(TALP_GPU_EINVAL,
+                   "no-alloc reduction takes exactly DEVICE_PTRS | SORTED_BY_START (device records in start order)");
     if (b->n_ranks == 0 || b->n_regions == 0 || b->n_regions > kMaxR)
         return err(TALP_GPU_EINVAL, "n_ranks >= 1 and 1 <= n_regions <= 8");
     if (!b->devices_per_rank || !b->region_window || !b->host_off || !b->dev_off)
@@ -111,17 +167,21 @@ extern "C" talp_gpu_status talp_gpu_reduce_noalloc(const talp_gpu_trace_batch* b
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= static_cast<int>(kMaxDevices))
         return err(TALP_GPU_ECUDA, "cudaGetDevice");
 
-    std::lock_guard<std::mutex> lock(g_mu);
-    // set-up, once per device, with that device current: the scratch's
-    // device address (the first call on a device does this; make it before
-    // any stream capture)
-    if (!g_scratch_ptr[dev]) {
+    DevSlot& slot = g_dev[dev];
+    std::lock_guard<std::mutex> lock(slot.mu);
+    // set-up, once per device (again after a device reset made a new
+    // context), with that device current: the scratch's device address.  The
+    // first call on a device does this; make it before any stream capture.
+    const unsigned long long ctx_id = current_ctx_id();
+    if (!slot.scratch || ctx_id != slot.ctx_id) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) return err(TALP_GPU_ECUDA, "cudaGetSymbolAddress of the no-alloc scratch");
-        g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
+        slot.scratch = static_cast<unsigned char*>(p);
+        slot.ctx_id = ctx_id;
     }
-    unsigned char* S = g_scratch_ptr[dev];
+    unsigned char* S = slot.scratch;
+    std::unique_lock<std::mutex> stage_lock(g_stage_mu);
     unsigned char* H = g_host_stage;
 
     SegDesc* sd = reinterpret_cast<SegDesc*>(H + kOffSegs);
@@ -243,14 +303,20 @@ extern "C" talp_gpu_status talp_gpu_reduce_noalloc(const talp_gpu_trace_batch* b
     const int grid = static_cast<int>((want + warps - 1) / warps);
     const uint32_t n_wrec = static_cast<uint32_t>(grid) * warps;
 
+    // Every kernel is launched whatever the record count (the sweep and the
+    // fix-up return at once without records), so that any first call loads
+    // all of this entry point's device code.
+    const int64_t wait_limit = wait_limit_cycles();
     cudaError_t e = cudaMemcpyAsync(S, H, kUploadBytes, cudaMemcpyHostToDevice, stream);
+    stage_lock.unlock();   // a copy from pageable memory has consumed its source when it returns
+    bool enqueued = e == cudaSuccess;
     if (e == cudaSuccess) e = launch_prep(reinterpret_cast<const FillJob*>(S + kOffJobs), nj, stream);
-    if (e == cudaSuccess && nrec > 0)
+    if (e == cudaSuccess)
         e = launch_sweep(shape, static_cast<int>(R), grid, reinterpret_cast<const SegDesc*>(S + kOffSegs),
                          reinterpret_cast<const uint64_t*>(S + kOffStart),
-                         reinterpret_cast<const uint64_t*>(S + kOffEnd), n_segs, wrec, flags, gstatus,
-                         4000000000LL, false, stream);
-    if (e == cudaSuccess && nrec > 0)
+                         reinterpret_cast<const uint64_t*>(S + kOffEnd), n_segs, wrec, flags, gstatus, wait_limit,
+                         false, stream);
+    if (e == cudaSuccess)
         e = launch_fixup(reinterpret_cast<const SegDesc*>(S + kOffSegs),
                          reinterpret_cast<const uint64_t*>(S + kOffStart), wrec, n_wrec, flags, false, stream);
     if (e == cudaSuccess) e = launch_finalize(reinterpret_cast<const FinalizeJob*>(S + kOffFin), R, stream);
@@ -258,6 +324,9 @@ extern "C" talp_gpu_status talp_gpu_reduce_noalloc(const talp_gpu_trace_batch* b
         e = cudaMemcpyAsync(out_host, mout, sizeof(MetricsOut) * R, cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) {
+        // work already queued still reads the scratch: let it finish before
+        // the lock goes, so that the next call cannot overwrite it underneath
+        if (enqueued) (void)cudaStreamSynchronize(stream);
         set_last_error(std::string("no-alloc reduction: ") + cudaGetErrorString(e));
         return TALP_GPU_ECUDA;
     }
