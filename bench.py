@@ -39,6 +39,7 @@ import subprocess
 import sys
 import threading
 import time
+from types import SimpleNamespace
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -63,6 +64,8 @@ def parse():
                              "threads"])
     ap.add_argument("--wave-records", type=float, default=3e9, help="batched-full: records per wave")
     ap.add_argument("--traces", type=int, default=4096, help="batched: number of traces")
+    ap.add_argument("--check-wave", type=int, default=None,
+                    help="batched-full: the wave checked whole against the oracle (default: the smallest of >= 16 traces)")
     ap.add_argument("--ev-hi", type=int, default=None,
                     help="batched: largest events per GPU (default 5000; batched-full 1e6)")
     ap.add_argument("--scale", type=float, default=1.0)
@@ -83,6 +86,8 @@ def parse():
                     help="with --unsorted: deal each device's records into this many sorted runs laid end to end "
                          "instead of grouping them by stream")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="plain: skip the serving, plain-serving and batched sub-objects of the default line")
     ap.add_argument("--hold-calls", type=int, default=1,
                     help="raw: stream each step's records as this many delivery buffers with hold-back")
     return ap.parse_args()
@@ -321,9 +326,18 @@ def workload_name(a):
 
 
 def run_batched(a):
+    line = measure_batched(a)
+    print(json.dumps(line), flush=True)
+    return 0 if line["config"]["bit_exact_batched_vs_plain"] and line["config"]["bit_exact_sampled_vs_oracle"] else 1
+
+
+def measure_batched(a):
     """Batched form: thousands of uneven traces reduced by one CUDA-graph
-    launch of an autotuned plan, against one ingest + finalize per trace."""
+    launch of an autotuned plan, against one ingest + finalize per trace.
+    Every trace's metrics of the two forms are compared bit for bit, and 16
+    traces spread over the workload against the oracle."""
     import torch
+    import oracle
     import paper_2603_26576_b300 as P
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
@@ -397,6 +411,20 @@ def run_batched(a):
                       P.talp_gpu_region_metrics(ctx.ctx, t.trace_id, P.TALP_GPU_ALL_REGIONS, stream,
                                                 n_regions=t.n_regions)]
     agree = plain_res == batched
+    # the oracle on 16 traces spread over the workload, every region
+    firsts = np.concatenate([[0], np.cumsum([t.n_regions for t in ts])])
+    sampled = sorted(set(int(k) for k in np.linspace(0, len(ts) - 1, 16)))
+    exact = True
+    cpu_rec, cpu_s = 0, 0.0
+    for k in sampled:
+        c0 = time.perf_counter()
+        ref = oracle.trace_metrics(ts[k])
+        cpu_s += time.perf_counter() - c0
+        cpu_rec += ts[k].n_records
+        for r in range(ts[k].n_regions):
+            got = batched[int(firsts[k]) + r]
+            for f in oracle.INT_FIELDS + oracle.RATIO_FIELDS:
+                exact &= got[f] == ref[r][f]
     peak, peak_kind = measured_peaks()
     achieved = BYTES_PER_RECORD * N / (ms / 1000.0) / 1e9
     line = {
@@ -410,16 +438,20 @@ def run_batched(a):
                    "plain_one_trace_per_launch_events_per_s": N / plain_s,
                    "batched_over_plain": (N / (ms / 1000.0)) / (N / plain_s),
                    "bit_exact_batched_vs_plain": agree,
+                   "oracle_sampled_traces": sampled, "bit_exact_sampled_vs_oracle": bool(exact),
                    "l2": "inputs (%.1f GB) larger than L2; no flush" % (BYTES_PER_RECORD * N / 1e9)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "kernel": "whole graph (prep, sweep, fixup, finalize)", "kernel_ms": ms,
                      "peak_source": f"{peak_kind} hbm_gbs"},
-        "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": ck,
+        "cpu_baseline": {"value": cpu_rec / cpu_s if cpu_s else None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"the {len(sampled)} traces checked ({cpu_rec} records), {cpu_s:.2f} s"},
+        "e2e": None, "gpu_launches": launches, "clocks": ck,
     }
-    print(json.dumps(line), flush=True)
     plan.close()
     ctx.close()
-    return 0 if agree else 1
+    del arrays, hse, hst, dse, dtg, b1, b2, b3, b4, batches
+    torch.cuda.empty_cache()
+    return line
 
 
 def run_batched_full(a):
@@ -447,6 +479,12 @@ def run_batched_full(a):
     exact = True
     checked = []
     cpu_rec, cpu_s = 0, 0.0
+    # the wave checked whole against the oracle: the one with the fewest
+    # records among the waves of at least 16 traces (or the fewest overall)
+    wrec = [sum(sp.n_records for sp in w) for w in wv]
+    big = [i for i, w in enumerate(wv) if len(w) >= 16] or list(range(len(wv)))
+    check_wave = a.check_wave if a.check_wave is not None else min(big, key=lambda i: wrec[i])
+    whole_rec, whole_traces, whole_s = 0, 0, 0.0
     ctx = P.Context(0)
     clocks = Clocks(0)
     clocks.start()
@@ -487,6 +525,36 @@ def run_batched_full(a):
         e1.record(stream)
         torch.cuda.synchronize()
         plain_ms += e0.elapsed_time(e1)
+        if wi == check_wave:
+            # every trace of this wave against the oracle: the generated
+            # records (the input the plan reduced) copied out, every unit
+            # reduced by the oracle on the host cores, the metrics formed
+            # from the oracle's own sums
+            c0 = time.perf_counter()
+            q = 0
+            for d in dts:
+                first = np.concatenate([[0], np.cumsum(d.devices_per_rank.astype(np.int64))])
+
+                def fetch(r0, r1, d=d, first=first):
+                    g0, g1 = int(first[r0]), int(first[r1])
+                    x, y = int(d.dev_off[g0]), int(d.dev_off[g1])
+                    return (d.dev_se[x:y].cpu().numpy(), d.dev_tag[x:y].cpu().numpy(),
+                            np.asarray(d.dev_off[g0:g1 + 1], np.uint64) - np.uint64(x))
+
+                du = oracle.device_unions_by_rank(fetch, d.n_ranks, d.devices_per_rank, d.region_window)
+                ht = SimpleNamespace(n_ranks=d.n_ranks, region_window=d.region_window,
+                                     host_se=d.host_se.cpu().numpy(), host_state=d.host_state.cpu().numpy(),
+                                     host_off=np.asarray(d.host_off, np.uint64))
+                for r in range(d.n_regions):
+                    ref = oracle.metrics_from_sums(d.n_ranks, d.devices_per_rank, oracle.host_sums(ht, r), du[r],
+                                                   d.region_window[r])
+                    got = res[q + r]
+                    for f in oracle.INT_FIELDS + oracle.RATIO_FIELDS:
+                        exact &= got[f] == ref[f]
+                q += d.n_regions
+                whole_rec += d.n_records
+            whole_traces = len(dts)
+            whole_s = time.perf_counter() - c0
         # the smallest trace of the wave against the oracle (when it is small
         # enough for the host: waves of a few huge traces are not sampled)
         k = int(np.argmin([sp.n_records for sp in w]))
@@ -528,6 +596,9 @@ def run_batched_full(a):
                    "plain_one_trace_per_launch_events_per_s": tot_rec / (plain_ms / 1000.0),
                    "batched_over_plain": plain_ms / plan_ms,
                    "oracle_checked_traces": checked, "bit_exact_sampled_vs_oracle": bool(exact),
+                   "oracle_whole_wave": {"wave": check_wave, "traces": whole_traces, "records": whole_rec,
+                                         "oracle_s": round(whole_s, 1),
+                                         "what": "every unit and every metric field of every trace of the wave"},
                    "l2": "every wave far larger than L2; no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "kernel": "whole graph (prep, sweep, fixup, finalize), summed over waves",
@@ -895,6 +966,12 @@ def _pct(v, p):
 
 
 def run_serving(a):
+    line = measure_serving(a)
+    print(json.dumps(line), flush=True)
+    return 0 if line["bit_exact_sampled_jobs"]["exact"] and not line["errors"] else 1
+
+
+def measure_serving(a):
     """Served form: many jobs stream batches into device-resident state while
     clients query it; against the plain form (one ingest per batch, one
     synchronous metrics call per query) at the same load."""
@@ -958,9 +1035,9 @@ def run_serving(a):
     sub_slices = s2["slices_submitted"] - s0["slices_submitted"]
     # saturation: closed-loop submitters, queries still every period
     sa0 = srv.stats()
-    sat_wall = load.run(a.sat_s, closed_loop=True)
+    sat_wall = load.run(a.sat_s, closed_loop=True) if a.sat_s > 0 else 0.0
     sa1 = srv.stats()
-    lat_sat = list(load.lat)
+    lat_sat = list(load.lat) if a.sat_s > 0 else []
     srv.drain()
     # bit-exact check of sampled jobs against the oracle on what they received
     order = sorted(range(len(jobs)), key=lambda k: sum(jobs[k].batch(q).n_records for q in range(load.next_q[k])))
@@ -1011,10 +1088,26 @@ def run_serving(a):
     pload = ServeLoad(jobs, p_submit, p_query, a.rate, a.query_ms / 1000.0)
     pload.next_q = [0] * len(jobs)
     pr0 = pload.sub_records
+    clocks_p = Clocks(0)
+    clocks_p.start()
     p_wall = pload.run(a.plain_s)
     torch.cuda.synchronize()
+    ck_plain = clocks_p.stop()
     p_rec = pload.sub_records - pr0
     lat_plain = list(pload.lat)
+    # the plain form's sampled jobs against the oracle on what they received
+    p_order = sorted(range(len(jobs)), key=lambda k: sum(jobs[k].batch(q).n_records for q in range(pload.next_q[k])))
+    p_sample = p_order[:3]
+    p_exact = True
+    for k in p_sample:
+        got = [P.metrics_to_dict(x) for x in
+               P.talp_gpu_region_metrics(ctx2.ctx, k, P.TALP_GPU_ALL_REGIONS, stream, n_regions=R)]
+        pt = jobs[k].prefix(pload.next_q[k], wins[k])
+        ref = [oracle.region_metrics(pt, r) for r in range(R)]
+        for r in range(R):
+            for f in P._lib.INT_FIELDS + P._lib.RATIO_FIELDS:
+                if got[r][f] != ref[r][f]:
+                    p_exact = False
     ctx2.close()
 
     peak, peak_kind = measured_peaks()
@@ -1039,13 +1132,14 @@ def run_serving(a):
                               "measured": "inside the library, whole run"},
         "served": {"queries_per_s": n_queries / wall, "batches_per_s": sub_slices / wall,
                    "waves_per_s": waves / wall, "query_batches": s2["query_batches"] - s0["query_batches"]},
-        "saturation": {"events_per_s": (sa1["records_folded"] - sa0["records_folded"]) / sat_wall,
-                       "batches_per_s": (sa1["slices_folded"] - sa0["slices_folded"]) / sat_wall,
-                       "p50_ms": ms(_pct(lat_sat, 0.5)), "p99_ms": ms(_pct(lat_sat, 0.99)),
-                       "queries": len(lat_sat)},
+        "saturation": None if not sat_wall else {
+            "events_per_s": (sa1["records_folded"] - sa0["records_folded"]) / sat_wall,
+            "batches_per_s": (sa1["slices_folded"] - sa0["slices_folded"]) / sat_wall,
+            "p50_ms": ms(_pct(lat_sat, 0.5)), "p99_ms": ms(_pct(lat_sat, 0.99)), "queries": len(lat_sat)},
         "plain_same_load": {"events_per_s": p_rec / p_wall, "queries_per_s": len(lat_plain) / p_wall,
                             "p50_ms": ms(_pct(lat_plain, 0.5)), "p99_ms": ms(_pct(lat_plain, 0.99)),
-                            "form": "one APPEND ingest per batch + one synchronous metrics call per query"},
+                            "form": "one APPEND ingest per batch + one synchronous metrics call per query",
+                            "bit_exact_sampled_jobs": {"jobs": p_sample, "exact": p_exact}},
         "bit_exact_sampled_jobs": {"jobs": sample, "exact": exact},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if peak else None, "traffic": None, "kernel": "talp::sweep_kernel",
@@ -1059,10 +1153,9 @@ def run_serving(a):
                 "h2d_bytes_per_step": int(BYTES_PER_RECORD * folded / a.steps),
                 "d2h_bytes_per_step": int(n_queries * R * 184 / a.steps),
                 "note": "the served form takes host buffers: value is already end to end"},
-        "gpu_launches": launches, "clocks": ck, "errors": load.errors + pload.errors,
+        "gpu_launches": launches, "clocks": ck, "clocks_plain": ck_plain, "errors": load.errors + pload.errors,
     }
-    print(json.dumps(line), flush=True)
-    return 0 if exact and not line["errors"] else 1
+    return line
 
 
 def main():
@@ -1229,17 +1322,81 @@ def main():
                                                     "; the library finds the out-of-order devices and sorts them "
                                                     "(sort stage)"))
                        if a.unsorted else "device records in start order (caller asserts SORTED_BY_START)",
+                       "kernel_overlap": "each device's 4 kernel streams are independent lanes: kernels of "
+                                         "different streams overlap and are merged by the flattening",
                        "hbm_gb_per_s": BYTES_PER_RECORD * N * a.steps / (ms / 1000.0) / 1e9,
                        "ms_per_step_best": per_step[0], "ms_per_step_median": per_step[len(per_step) // 2]},
             "roofline": roof, "cpu_baseline": cpu, "cpu_all_cores": cpu_all, "e2e": e2e, "gpu_launches": launches,
             "clocks": ck,
             "check": {"elapsed_ns_region0": res[0].elapsed_ns, "dev_pe_region0": res[0].dev_pe},
         }
-        print(json.dumps(line), flush=True)
     ctx.close()
+    rc = 0
+    if rank == 0 and ws == 1 and a.workload == "plain" and not a.unsorted and a.scale == 1.0 and not a.no_extras:
+        # the metric's latency half and the spec comparisons, measured
+        # in the same run after the plain workload's buffers are released
+        del d_arrays, batch_d, keep_d
+        if e2e is not None:
+            del h_arrays, batch_h, keep_h
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        extra = default_extras(a)
+        rc = extra.pop("_rc")
+        line.update(extra)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
-    return 0
+    return rc
+
+
+def default_extras(a):
+    """Sub-objects of the default bench line: the served form and the plain
+    form at the serving load (the p50/p99 query latency of the metric), and
+    the batched form against one trace per launch."""
+    import copy
+    sv = copy.copy(a)
+    sv.warmup, sv.steps, sv.step_s, sv.sat_s, sv.plain_s = 2, 10, 1.0, 0.0, 10.0
+    sv.jobs, sv.rate, sv.query_ms = 256, 2000.0, 10.0
+    L = measure_serving(sv)
+    pl = L["plain_same_load"]
+    out = {
+        "serving": {
+            "workload": L["config"]["workload"], "seconds": sv.steps * sv.step_s, "warmup_s": sv.warmup * sv.step_s,
+            "events_per_s": L["value"], "queries_per_s": L["served"]["queries_per_s"],
+            "batches_per_s": L["served"]["batches_per_s"],
+            "client_ms": L["latency_ms"], "library_ms": L["server_latency_ms"],
+            "oracle_sampled_jobs": L["bit_exact_sampled_jobs"]["jobs"],
+            "bit_exact_sampled_vs_oracle": L["bit_exact_sampled_jobs"]["exact"],
+            "gpu_launches": L["gpu_launches"], "clocks": L["clocks"], "errors": L["errors"]},
+        "serving_plain": {
+            "workload": "the same jobs, arrivals and query period through the plain form: " + pl["form"],
+            "seconds": sv.plain_s, "events_per_s": pl["events_per_s"], "queries_per_s": pl["queries_per_s"],
+            "client_ms": {"p50": pl["p50_ms"], "p99": pl["p99_ms"]},
+            "oracle_sampled_jobs": pl["bit_exact_sampled_jobs"]["jobs"],
+            "bit_exact_sampled_vs_oracle": pl["bit_exact_sampled_jobs"]["exact"], "clocks": L["clocks_plain"]},
+    }
+    sp99, pp99 = L["latency_ms"]["p99"], pl["p99_ms"]
+    out["serving"]["vs_plain"] = {"p99_plain_over_served": (pp99 / sp99) if sp99 and pp99 else None,
+                                  "events_per_s_served_over_plain":
+                                      L["value"] / pl["events_per_s"] if pl["events_per_s"] else None}
+    bv = copy.copy(a)
+    bv.traces, bv.ev_hi, bv.steps, bv.warmup = 4096, None, 10, 3
+    B = measure_batched(bv)
+    c = B["config"]
+    out["batched"] = {
+        "workload": c["workload"], "records_per_launch": c["records_per_step"], "ms_per_launch": B["ms_per_step"],
+        "events_per_s": B["value"], "plain_one_trace_per_launch_events_per_s": c["plain_one_trace_per_launch_events_per_s"],
+        "batched_over_plain": c["batched_over_plain"], "roofline_frac": B["roofline"]["frac"],
+        "bit_exact_batched_vs_plain": c["bit_exact_batched_vs_plain"],
+        "oracle_sampled_traces": c["oracle_sampled_traces"],
+        "bit_exact_sampled_vs_oracle": c["bit_exact_sampled_vs_oracle"], "plan": c["plan"],
+        "gpu_launches": B["gpu_launches"], "clocks": B["clocks"]}
+    ok = (out["serving"]["bit_exact_sampled_vs_oracle"] and out["serving_plain"]["bit_exact_sampled_vs_oracle"]
+          and not out["serving"]["errors"] and out["batched"]["bit_exact_sampled_vs_oracle"]
+          and out["batched"]["bit_exact_batched_vs_plain"])
+    out["_rc"] = 0 if ok else 1
+    return out
 
 
 if __name__ == "__main__":

@@ -15,6 +15,8 @@ from __future__ import annotations
 import ctypes
 import os
 import subprocess
+from concurrent.futures import ThreadPoolExecutor
+from types import SimpleNamespace
 
 import numpy as np
 
@@ -221,3 +223,38 @@ def thread_metrics(t, region, proc_off):
 
 def trace_metrics(t):
     return default().trace_metrics(t)
+
+
+def device_unions_by_rank(fetch, n_ranks, devices_per_rank, region_window, block_ranks=64, threads=None):
+    """int64[R, m, 3]: oracle_device_unions of every region for every device
+    of a trace too large to hold on the host at once.  fetch(r0, r1) returns
+    (dev_se, dev_tag, dev_off) of ranks r0 .. r1-1 (dev_off from 0 over their
+    devices); blocks of ranks are fetched in turn and their ranks reduced by
+    the oracle on host threads (the C calls release the GIL).  Plumbing only:
+    every number comes from oracle_device_unions, one rank at a time."""
+    dpr = np.asarray(devices_per_rank, np.int64)
+    win = np.asarray(region_window, np.int64)
+    R, m = int(win.shape[0]), int(dpr.sum())
+    first = np.concatenate([[0], np.cumsum(dpr)])
+    out = np.zeros((R, m, 3), np.int64)
+    threads = threads or os.cpu_count() or 1
+    orc = default()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        for r0 in range(0, int(n_ranks), block_ranks):
+            r1 = min(int(n_ranks), r0 + block_ranks)
+            se, tag, off = fetch(r0, r1)
+            off = np.asarray(off, np.uint64)
+
+            def job(i, se=se, tag=tag, off=off, r0=r0):
+                g0, g1 = int(first[i] - first[r0]), int(first[i + 1] - first[r0])
+                a, b = int(off[g0]), int(off[g1])
+                one = SimpleNamespace(n_ranks=1, devices_per_rank=dpr[i:i + 1].astype(np.uint32),
+                                      dev_se=se[a:b], dev_tag=tag[a:b],
+                                      dev_off=(off[g0:g1 + 1] - off[g0]).astype(np.uint64),
+                                      region_window=win[:, i:i + 1])
+                return i, [orc.device_unions(one, r) for r in range(R)]
+
+            for i, res in ex.map(job, range(r0, r1)):
+                for r in range(R):
+                    out[r, first[i]:first[i + 1]] = res[r]
+    return out
