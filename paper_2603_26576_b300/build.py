@@ -12,8 +12,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libtalp_gpu.so")
-SOURCES = ["sweep.cu", "reduce.cu", "sort.cu", "capi.cu", "noalloc.cu", "serve.cu", "concurrency.cu", "raw.cu"]
-HEADERS = ["common.cuh", "kernels.h", "engine.h"]
+SOURCES = ["sweep.cu", "reduce.cu", "sort.cu", "fms.cu", "capi.cu", "noalloc.cu", "serve.cu", "concurrency.cu", "raw.cu"]
+HEADERS = ["common.cuh", "sweep_core.cuh", "kernels.h", "engine.h"]
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 

@@ -115,7 +115,10 @@ struct Layout {
     size_t up_bytes = 0;
     size_t off_wrec = 0, off_flags = 0, off_gst = 0, off_bk = 0, off_slist = 0, off_srb = 0, off_stb = 0;
     size_t off_smn = 0, off_smx = 0, off_hist = 0, off_offs = 0, off_rsegs = 0, off_rstart = 0, off_mout = 0;
-    size_t off_nruns = 0, off_runs = 0, off_rounds = 0;
+    size_t off_nruns = 0, off_runs = 0, off_fused = 0;
+    uint64_t fms_samples = 0, fms_chunks = 0, fms_super = 0;   // table bounds of the fused merge-sweep
+    size_t off_fS = 0, off_fsb = 0, off_fcb = 0, off_fpb = 0, off_fscb = 0, off_fsamp = 0, off_fsplit = 0,
+           off_fseg = 0, off_fchunk = 0, off_fscagg = 0, off_ffix = 0;
     size_t ws_bytes = 0, stage_bytes = 0, sortbuf_bytes = 0, new_bytes = 0;
     uint32_t nj = 0;
     std::vector<uint64_t> nh, nd;
@@ -373,13 +376,24 @@ talp_gpu_status size_ingest(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches
         if (!(b.flags & TALP_GPU_SORTED_BY_START)) {
             L.sort_slots += L.mm[k];
             L.sort_recs += L.nd[k];
-            for (uint32_t g = 0; g < L.mm[k]; ++g)
-                L.sort_tiles += (b.dev_off[g + 1] - b.dev_off[g] + sort_tile_records() - 1) / sort_tile_records();
+            for (uint32_t g = 0; g < L.mm[k]; ++g) {
+                const uint64_t nseg = b.dev_off[g + 1] - b.dev_off[g];
+                L.sort_tiles += (nseg + sort_tile_records() - 1) / sort_tile_records();
+                L.fms_samples += fms_max_samples(nseg);
+                L.fms_chunks += fms_max_chunks(nseg);
+                L.fms_super += fms_max_super(nseg);
+            }
             if ((b.flags & TALP_GPU_APPEND) && L.mm[k]) L.n_backup_words += 3ull * b.n_regions * L.mm[k];
         }
     }
     if (L.n_segs > 0xFFFFFFF0ull) return fail(TALP_GPU_EINVAL, "too many segments in one call");
     L.sorting = L.sort_slots > 0;
+    if (L.sorting) {
+        // kernel attribute and grid of the fused merge-sweep, set before any
+        // launch sequence is captured
+        const cudaError_t e = fms_prepare(c->num_sms);
+        if (e != cudaSuccess) return cuda_fail(e, "fused merge-sweep set-up");
+    }
     L.sortbuf_bytes = L.sorting ? 2 * (align_up(16 * L.sort_recs, 256) + align_up(L.sort_recs + 64, 256)) : 0;
 
     L.shape = shape;
@@ -424,8 +438,19 @@ talp_gpu_status size_ingest(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches
     L.off_offs = align_up(L.off_hist + 4 * 256 * L.sort_tiles, 256);
     L.off_nruns = align_up(L.off_offs + 8 * 256 * L.sort_tiles, 256);
     L.off_runs = align_up(L.off_nruns + 4 * L.sort_slots, 256);
-    L.off_rounds = align_up(L.off_runs + 8 * (kMaxRuns + 1) * L.sort_slots, 256);
-    L.off_rsegs = align_up(L.off_rounds + 4 * L.sort_slots, 256);
+    L.off_fused = align_up(L.off_runs + 8 * (kMaxRuns + 1) * L.sort_slots, 256);
+    L.off_fS = align_up(L.off_fused + 4 * L.sort_slots, 256);
+    L.off_fsb = align_up(L.off_fS + 4 * L.sort_slots, 256);
+    L.off_fcb = align_up(L.off_fsb + 8 * (L.sort_slots + 1), 256);
+    L.off_fpb = align_up(L.off_fcb + 8 * (L.sort_slots + 1), 256);
+    L.off_fscb = align_up(L.off_fpb + 8 * L.sort_slots, 256);
+    L.off_fsamp = align_up(L.off_fscb + 8 * (L.sort_slots + 1), 256);
+    L.off_fsplit = align_up(L.off_fsamp + 8 * L.fms_samples, 256);
+    L.off_fseg = align_up(L.off_fsplit + 8 * kMaxRuns * (L.fms_chunks + L.sort_slots), 256);
+    L.off_fchunk = align_up(L.off_fseg + 4 * L.fms_chunks, 256);
+    L.off_fscagg = align_up(L.off_fchunk + sizeof(FmsChunk) * L.fms_chunks, 256);
+    L.off_ffix = align_up(L.off_fscagg + 16 * L.fms_super, 256);
+    L.off_rsegs = align_up(L.off_ffix + sizeof(FmsFix) * L.fms_chunks, 256);
     L.off_rstart = align_up(L.off_rsegs + sizeof(SegDesc) * (L.sorting ? L.n_dev_segs : 0), 256);
     L.off_rrend = align_up(L.off_rstart + 8 * (L.sorting ? L.n_dev_segs + 1 : 0), 256);
     L.off_mout = align_up(L.off_rrend + 8 * (L.sorting ? L.n_dev_segs + 1 : 0), 256);
@@ -647,7 +672,18 @@ talp_gpu_status fill_ingest(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches
         sc.offs = reinterpret_cast<uint64_t*>(wsd + L.off_offs);
         sc.nruns = reinterpret_cast<uint32_t*>(wsd + L.off_nruns);
         sc.runs = reinterpret_cast<uint64_t*>(wsd + L.off_runs);
-        sc.rounds = reinterpret_cast<uint32_t*>(wsd + L.off_rounds);
+        sc.fused = reinterpret_cast<uint32_t*>(wsd + L.off_fused);
+        sc.fms_S = reinterpret_cast<uint32_t*>(wsd + L.off_fS);
+        sc.fms_samp_base = reinterpret_cast<uint64_t*>(wsd + L.off_fsb);
+        sc.fms_chunk_base = reinterpret_cast<uint64_t*>(wsd + L.off_fcb);
+        sc.fms_split_base = reinterpret_cast<uint64_t*>(wsd + L.off_fpb);
+        sc.fms_sc_base = reinterpret_cast<uint64_t*>(wsd + L.off_fscb);
+        sc.fms_samp = reinterpret_cast<int64_t*>(wsd + L.off_fsamp);
+        sc.fms_split = reinterpret_cast<uint64_t*>(wsd + L.off_fsplit);
+        sc.fms_chunk_seg = reinterpret_cast<uint32_t*>(wsd + L.off_fseg);
+        sc.fms_chunk = reinterpret_cast<FmsChunk*>(wsd + L.off_fchunk);
+        sc.fms_sc_agg = reinterpret_cast<int64_t*>(wsd + L.off_fscagg);
+        sc.fms_fix = reinterpret_cast<FmsFix*>(wsd + L.off_ffix);
         const size_t se_b = align_up(16 * L.sort_recs, 256), tg_b = align_up(L.sort_recs + 64, 256);
         for (int q = 0; q < 2; ++q) {
             char* base = sortbuf + q * (se_b + tg_b);
@@ -704,13 +740,13 @@ talp_gpu_status enqueue_ingest(talp_gpu_ctx* c, const Layout& L, const char* up,
             TALP_CUDA(launch_sort_stage(dsegs, static_cast<uint32_t>(L.n_segs), static_cast<uint32_t>(L.n_dev_segs),
                                         seg_flags, sctl, rsegs, rstart, rrend,
                                         static_cast<int>(std::max<uint64_t>(gt, 1)),
-                                        static_cast<int>(std::max<uint64_t>(gs, 1)), stream));
+                                        static_cast<int>(std::max<uint64_t>(gs, 1)), gstatus, c->wait_limit, stream));
             TALP_CUDA(launch_sweep(L.shape, static_cast<int>(L.rmax), L.full_grid, rsegs, rstart, rrend,
                                    static_cast<uint32_t>(L.n_dev_segs), wrec, seg_flags, gstatus, c->wait_limit,
                                    false, stream));
             TALP_CUDA(launch_fixup(rsegs, rstart, wrec, static_cast<uint32_t>(L.full_grid) * L.warps, seg_flags,
                                    false, stream));
-            nl += 2 + 1 + kMergeRounds + 24 + 1 + 2;
+            nl += 2 + 1 + 4 + 24 + 1 + 2;
         }
     }
     if (L.n_fin) {

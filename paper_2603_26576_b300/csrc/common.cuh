@@ -130,15 +130,59 @@ struct SortCtl {
     const int64_t* const* restore;  // [segments] sums a flagged segment restarts from (null: zero)
     uint32_t* nruns;           // [slots] descents found in k (runs - 1)
     uint64_t* runs;            // [slots][kMaxRuns + 1] run boundaries of k (sorted by the merge plan)
-    uint32_t* rounds;          // [slots] pairwise merge rounds for k; 0: radix sort
-    uint32_t max_rounds;       // most merge rounds any flagged segment needs
+    uint32_t* fused;           // [slots] 1: k is a few sorted runs, merged and swept in one pass
+    // fused merge-sweep (fms.cu) of the segments marked in `fused`
+    uint32_t* fms_S;           // [slots] sample step of k (0: k not fused)
+    uint64_t* fms_samp_base;   // [slots + 1] first sample of k in fms_samp
+    uint64_t* fms_chunk_base;  // [slots + 1] first chunk of k
+    uint64_t* fms_split_base;  // [slots] first entry of k's split rows in fms_split
+    uint64_t* fms_sc_base;     // [slots + 1] first super-chunk of k
+    int64_t* fms_samp;         // [samples] start of every sample record
+    uint64_t* fms_split;       // per chunk boundary c = 0 .. nch of k: the position in each run
+    uint32_t* fms_chunk_seg;   // [chunks] flagged segment of each chunk
+    struct FmsChunk* fms_chunk;// [chunks] aggregate and carry of each chunk
+    int64_t* fms_sc_agg;       // [super-chunks][2] largest kernel / memory end of each super-chunk
+    struct FmsFix* fms_fix;    // [chunks] chunks swept again with their segment's true carry
+    uint64_t fms_nsamp;        // samples over every fused segment
+    uint64_t fms_nchunk;       // chunks over every fused segment
+    uint64_t fms_nsc;          // super-chunks over every fused segment
+    uint32_t fms_ticket;       // next super-chunk to hand out
+    uint32_t fms_nfix;         // fix-up jobs
+    uint32_t fms_fix_ticket;   // next fix-up job to hand out
     uint32_t pad2;
 };
 
+// Per chunk of the fused merge-sweep: the largest kernel / memory end of its
+// records, the carry it was swept with (the largest ends of the earlier
+// chunks of its super-chunk, or the earlier ingests for a segment's first
+// super-chunk) and its smallest start.
+struct FmsChunk {
+    int64_t aggK, aggM, LK, LM, s0;
+};
+
+// A chunk swept again with its true carry T (the fix-up adds the difference
+// between the sweeps with T and with its carry L).
+struct FmsFix {
+    uint64_t g;                // global chunk index
+    int64_t TK, TM;
+};
+
 // A flagged segment made of at most this many sorted runs (records grouped
-// by stream, each stream in start order) is merged instead of radix sorted.
+// by stream, each stream in start order) is merged and swept in one pass
+// (fms.cu) instead of being radix sorted and swept again.
 constexpr int kMaxRuns = 16;
-constexpr int kMergeRounds = 4;   // ceil(log2(kMaxRuns))
+// Records per chunk of the fused merge-sweep (at most).  A segment of r runs
+// is sampled every S = kFmsChunk / ((kFmsSpread + 1) r) records of each run
+// and cut at every (kFmsSpread r)-th sample in merged order; a chunk then
+// holds at most (kFmsSpread + 1) r S <= kFmsChunk records, about
+// kFmsSpread / (kFmsSpread + 1) of that on average.  Table bounds for a
+// segment of n records: at most n / S + r samples and 4 n / kFmsChunk + 2
+// chunks.  kFmsSuper consecutive chunks of a segment form a super-chunk, the
+// unit a CTA takes.
+constexpr int kFmsChunk = 2048;
+constexpr int kFmsSpread = 3;
+constexpr int kFmsMinStep = kFmsChunk / ((kFmsSpread + 1) * kMaxRuns);
+constexpr int kFmsSuper = 16;
 
 // Concurrency profile: levels k = 1 .. kConcLevels of concurrently active
 // records per device; one device's window and record range, and the chunks
@@ -240,6 +284,26 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
         if (clock64() - t0 > limit) return false;
     }
     return true;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Flags published by one CTA and read by others (release / acquire at GPU scope).
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Barrier over a subset of a CTA's warps (named barrier `id`, `threads` a
+// multiple of 32); id 0 is __syncthreads.
+__device__ __forceinline__ void named_bar(int id, int threads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
 
 // 1-D bulk copy global -> shared through the TMA unit, completing on `bar`.

@@ -59,13 +59,27 @@ cudaError_t launch_scalability(const MetricsOut* runs, uint32_t n_runs, uint32_t
                                cudaStream_t stream);
 cudaError_t launch_combine(const MetricsOut* parts, uint32_t n_parts, MetricsOut* out, cudaStream_t stream);
 
-// Sort stage over the device segments flagged out of order (sortable ones),
-// then the segment table of their sorted copies for the re-sweep.
+// Sort stage over the device segments flagged out of order (sortable ones):
+// segments of a few sorted runs are merged and swept at once (fused
+// merge-sweep), the others radix sorted; then the segment table of the
+// sorted copies for the re-sweep.
 // n_segs: entries of `segs`; n_slots: device segments (upper bound of flagged).
-cudaError_t launch_sort_stage(const SegDesc* segs, uint32_t n_segs, uint32_t n_slots, const uint32_t* seg_flags,
+cudaError_t launch_sort_stage(const SegDesc* segs, uint32_t n_segs, uint32_t n_slots, uint32_t* seg_flags,
                               SortCtl* ctl, SegDesc* resweep_segs, uint64_t* resweep_start, uint64_t* resweep_rend,
-                              int grid_tiles, int grid_segs, cudaStream_t stream);
+                              int grid_tiles, int grid_segs, uint32_t* gstatus, int64_t wait_limit,
+                              cudaStream_t stream);
 int sort_tile_records();
+
+// Fused merge-sweep (fms.cu): set-up once per process before any launch
+// (kernel attribute and grid; not during a stream capture), the launch
+// sequence (plan, samples, splitters, merge-sweep), and the table sizes
+// for a segment of n records.
+cudaError_t fms_prepare(int num_sms);
+cudaError_t launch_fms(const SegDesc* segs, SortCtl* ctl, uint32_t* seg_flags, uint32_t* gstatus, int64_t wait_limit,
+                       int grid_samples, cudaStream_t stream);
+uint64_t fms_max_samples(uint64_t n);
+uint64_t fms_max_chunks(uint64_t n);
+uint64_t fms_max_super(uint64_t n);
 
 // Message returned by talp_gpu_last_error() on this thread.
 void set_last_error(const std::string& msg);

@@ -19,11 +19,9 @@
 //
 // A flagged segment that is only a few sorted runs laid end to end (records
 // grouped by stream, each stream in start order: the order per-stream
-// activity buffers deliver) is merged instead: the min/max kernel also
-// records where the start order descends, and when a segment has at most
-// kMaxRuns runs, ceil(log2(runs)) rounds of pairwise merge-path merges move
-// each record once per round, against once per 8-bit digit for the radix
-// sort, with coalesced reads and writes.
+// activity buffers deliver) is not sorted here: the min/max kernel records
+// where the start order descends, and a segment of at most kMaxRuns runs is
+// merged and swept in one pass by the fused merge-sweep (fms.cu).
 #include "kernels.h"
 
 namespace talp {
@@ -45,9 +43,9 @@ __device__ __forceinline__ int passes_for(int64_t mn, int64_t mx) {
 // swept again from its own records
 constexpr uint32_t kInOrder = 0xFFFFFFFFu;
 
-// radix passes of flagged segment k (0 when it is merged instead, or in order)
+// radix passes of flagged segment k (0 when it is merged and swept instead, or in order)
 __device__ __forceinline__ int radix_passes(const SortCtl* ctl, uint32_t k) {
-    return (ctl->rounds[k] || ctl->nruns[k] == kInOrder) ? 0 : passes_for(ctl->mn[k], ctl->mx[k]);
+    return (ctl->fused[k] || ctl->nruns[k] == kInOrder) ? 0 : passes_for(ctl->mn[k], ctl->mx[k]);
 }
 
 // segment k of the flagged list owning tile t
@@ -127,7 +125,7 @@ __global__ void __launch_bounds__(1024) sort_plan_kernel(const SegDesc* __restri
             ctl->mn[k] = INT64_MAX;
             ctl->mx[k] = INT64_MIN;
             ctl->nruns[k] = 0;
-            ctl->rounds[k] = 0;
+            ctl->fused[k] = 0;
             // the re-sweep recomputes this ingest's part of the segment: its
             // sums restart from their value before the ingest
             const SegDesc& d = segs[s];
@@ -148,7 +146,6 @@ __global__ void __launch_bounds__(1024) sort_plan_kernel(const SegDesc* __restri
     }
     if (tid == 0) {
         ctl->max_passes = 0;
-        ctl->max_rounds = 0;
         ctl->nflag = s_base;
         ctl->nrec = s_rbase;
         ctl->ntile = s_tbase;
@@ -357,18 +354,19 @@ __global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(const SegDes
 
 
 // --------------------------------------------------------------- merge plan
-// One thread per flagged segment: a segment of at most kMaxRuns sorted runs
-// gets its run starts in order and its number of merge rounds.
+// One thread per flagged segment: a segment of 2 .. kMaxRuns sorted runs gets
+// its run starts in order and is marked for the fused merge-sweep; any other
+// goes to the radix sort (a presorted one found in order to neither).
 __global__ void sort_merge_plan_kernel(const SegDesc* __restrict__ segs, SortCtl* ctl) {
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < ctl->nflag; k += gridDim.x * blockDim.x) {
         const uint32_t c = ctl->nruns[k];
         if (c == 0 && (segs[ctl->list[k]].pad[0] & kSegPresort)) {
-            ctl->rounds[k] = 0;
+            ctl->fused[k] = 0;
             ctl->nruns[k] = kInOrder;
             continue;
         }
         if (c == 0 || c + 1 > static_cast<uint32_t>(kMaxRuns)) {
-            ctl->rounds[k] = 0;
+            ctl->fused[k] = 0;
             atomicMax(&ctl->max_passes, static_cast<uint32_t>(passes_for(ctl->mn[k], ctl->mx[k])));
             continue;
         }
@@ -384,177 +382,14 @@ __global__ void sort_merge_plan_kernel(const SegDesc* __restrict__ segs, SortCtl
         }
         runs[0] = 0;
         runs[c + 1] = segs[ctl->list[k]].n;
-        uint32_t r = 0;
-        while ((1u << r) < c + 1) ++r;
-        ctl->rounds[k] = r;
-        atomicMax(&ctl->max_rounds, r);
-    }
-}
-
-// ------------------------------------------------------------------ merge
-// Round r merges, in every merged segment, the pairs of adjacent groups of
-// 2^r runs.  A CTA takes the outputs of one sort tile, 1024 at a time; for
-// each pair those outputs overlap it finds the merge-path split at both
-// ends (ties taken from the earlier group, so the merge is stable), stages
-// the two input ranges in shared memory, merges 4 outputs per thread and
-// writes the rows back coalesced.
-constexpr int kMergeChunk = 1024;
-
-__device__ __forceinline__ uint64_t merge_split(const int64_t* A, uint64_t nA, const int64_t* B, uint64_t nB,
-                                                uint64_t q) {
-    uint64_t lo = q > nB ? q - nB : 0, hi = q < nA ? q : nA;
-    while (lo < hi) {
-        const uint64_t mid = (lo + hi) >> 1;
-        if (A[2 * mid] <= B[2 * (q - 1 - mid)]) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
-// merge input of round r for segment k (the original records, or the
-// buffer written by the previous round)
-__device__ __forceinline__ void merge_src(const SegDesc& d, const SortCtl* ctl, uint32_t k, int r,
-                                          const int64_t*& se, const uint8_t*& tag) {
-    if (r == 0) {
-        se = d.se;
-        tag = d.tag;
-    } else {
-        se = ctl->buf_se[(r - 1) & 1] + 2 * ctl->rec_base[k];
-        tag = ctl->buf_tag[(r - 1) & 1] + ctl->rec_base[k];
-    }
-}
-
-// Merge-path split at the start of every output chunk of round r, one
-// thread per chunk (the dependent binary searches of all chunks overlap):
-// the number of the chunk's pair's first-group records among the pair's
-// outputs before the chunk.  Stored in offs[tile * 256 + half] (the radix
-// offsets of a merged segment's tiles are not used).
-__global__ void __launch_bounds__(256) sort_merge_split_kernel(const SegDesc* __restrict__ segs, SortCtl* ctl,
-                                                               int r) {
-    if (static_cast<uint32_t>(r) >= ctl->max_rounds) return;
-    const uint64_t nb = ctl->ntile * (kSortTile / kMergeChunk);
-    for (uint64_t b = blockIdx.x * 256ull + threadIdx.x; b < nb; b += gridDim.x * 256ull) {
-        const uint32_t t = static_cast<uint32_t>(b / (kSortTile / kMergeChunk));
-        const uint32_t half = static_cast<uint32_t>(b % (kSortTile / kMergeChunk));
-        const uint32_t k = seg_of_tile(ctl, t);
-        const uint32_t R = ctl->rounds[k];
-        if (R == 0 || static_cast<uint32_t>(r) >= R) continue;
-        const SegDesc& d = segs[ctl->list[k]];
-        const uint64_t h = static_cast<uint64_t>(t - ctl->tile_base[k]) * kSortTile + half * kMergeChunk;
-        if (h >= d.n) continue;
-        const int64_t* se;
-        const uint8_t* tag;
-        merge_src(d, ctl, k, r, se, tag);
-        const uint64_t* runs = ctl->runs + static_cast<uint64_t>(k) * (kMaxRuns + 1);
-        const uint32_t nr = ctl->nruns[k] + 1;
-        const uint32_t w = 1u << r;
-        for (uint32_t g = 0; g < nr; g += 2 * w) {
-            const uint64_t pa = runs[g], pm = runs[min(g + w, nr)], pb = runs[min(g + 2 * w, nr)];
-            if (h >= pa && h < pb) {
-                ctl->offs[static_cast<uint64_t>(t) * 256 + half] =
-                    merge_split(se + 2 * pa, pm - pa, se + 2 * pm, pb - pm, h - pa);
-                break;
-            }
-        }
-    }
-}
-
-// Each CTA takes a contiguous range of tiles, so consecutive tiles share
-// their segment's descriptor, run starts and the split at their common
-// boundary: only the split at a chunk's far end is read from memory, and it
-// is fetched one chunk ahead.
-__global__ void __launch_bounds__(256, 8) sort_merge_kernel(const SegDesc* __restrict__ segs, SortCtl* ctl, int r) {
-    __shared__ longlong2 s_in[kMergeChunk];
-    __shared__ uint8_t s_tin[kMergeChunk];
-    __shared__ uint64_t s_runs[kMaxRuns + 1];
-    if (static_cast<uint32_t>(r) >= ctl->max_rounds) return;
-    const uint64_t ntile = ctl->ntile;
-    const uint64_t tb0 = ntile * blockIdx.x / gridDim.x, tb1 = ntile * (blockIdx.x + 1) / gridDim.x;
-    if (tb0 >= tb1) return;
-    uint32_t k = seg_of_tile(ctl, static_cast<uint32_t>(tb0));
-    uint64_t t = tb0;
-    while (t < tb1) {
-        while (t >= ctl->tile_base[k + 1]) ++k;   // block-uniform
-        const uint64_t tb = ctl->tile_base[k], te = min(ctl->tile_base[k + 1], tb1);
-        const uint32_t R = ctl->rounds[k];
-        if (R == 0 || static_cast<uint32_t>(r) >= R) {
-            t = te;
-            continue;
-        }
-        const SegDesc& d = segs[ctl->list[k]];
-        const uint64_t n_seg = d.n;
-        const int64_t* se;
-        const uint8_t* tag;
-        merge_src(d, ctl, k, r, se, tag);
-        int64_t* dse = ctl->buf_se[r & 1] + 2 * ctl->rec_base[k];
-        uint8_t* dtag = ctl->buf_tag[r & 1] + ctl->rec_base[k];
-        const uint32_t nr = ctl->nruns[k] + 1;
-        __syncthreads();
-        if (threadIdx.x <= nr) s_runs[threadIdx.x] = ctl->runs[static_cast<uint64_t>(k) * (kMaxRuns + 1) + threadIdx.x];
-        __syncthreads();
-        const uint32_t w = 1u << r;
-        // outputs of this segment's tiles in [t, te), chunk by chunk
-        const uint64_t o_end = min((te - tb) * kSortTile, n_seg);
-        uint64_t h0 = (t - tb) * kSortTile;
-        auto split_at = [&](uint64_t h) -> uint64_t {
-            return ctl->offs[(tb + h / kSortTile) * 256 + (h % kSortTile) / kMergeChunk];
-        };
-        // split at the current chunk's far end, fetched one chunk ahead; the
-        // split at its near end is the previous chunk's far end
-        uint64_t pre = h0 + kMergeChunk < n_seg ? split_at(h0 + kMergeChunk) : 0;
-        uint64_t near = h0 > 0 && h0 < n_seg ? split_at(h0) : 0;
-        for (; h0 < o_end; h0 += kMergeChunk) {
-            const uint64_t h1 = min(h0 + static_cast<uint64_t>(kMergeChunk), n_seg);
-            const uint64_t far = pre;
-            if (h1 + kMergeChunk < n_seg) pre = split_at(h1 + kMergeChunk);
-            for (uint32_t g = 0; g < nr; g += 2 * w) {
-                const uint64_t pa = s_runs[g];
-                const uint64_t pm = s_runs[min(g + w, nr)];
-                const uint64_t pb = s_runs[min(g + 2 * w, nr)];
-                if (pb <= h0 || pa >= h1) continue;
-                const uint64_t lo = max(h0, pa), hi = min(h1, pb);
-                const uint64_t nA = pm - pa;
-                const uint64_t i0 = pa >= h0 ? 0 : near;
-                const uint64_t i1 = pb <= h1 ? nA : far;
-                const uint64_t j0 = (lo - pa) - i0, j1 = (hi - pa) - i1;
-                const int ca = static_cast<int>(i1 - i0), cb = static_cast<int>(j1 - j0);
-                for (int q = threadIdx.x; q < ca + cb; q += blockDim.x) {
-                    const uint64_t src = q < ca ? pa + i0 + q : pm + j0 + (q - ca);
-                    s_in[q] = *reinterpret_cast<const longlong2*>(se + 2 * src);
-                    s_tin[q] = tag[src];
-                }
-                __syncthreads();
-                // 4 outputs per thread: merge path inside the staged ranges,
-                // written straight to the output
-                const int n = ca + cb;
-                const int o0 = min(static_cast<int>(threadIdx.x) * 4, n);
-                const int o1 = min(o0 + 4, n);
-                if (o0 < o1) {
-                    int a = max(0, o0 - cb), b = min(o0, ca);
-                    while (a < b) {
-                        const int mid = (a + b) >> 1;
-                        if (s_in[mid].x <= s_in[ca + o0 - 1 - mid].x) a = mid + 1;
-                        else b = mid;
-                    }
-                    int ia = a, ib = o0 - a;
-                    for (int o = o0; o < o1; ++o) {
-                        const bool takeA = ib >= cb || (ia < ca && s_in[ia].x <= s_in[ca + ib].x);
-                        const int src = takeA ? ia++ : ca + ib++;
-                        *reinterpret_cast<longlong2*>(dse + 2 * (lo + o)) = s_in[src];
-                        dtag[lo + o] = s_tin[src];
-                    }
-                }
-                __syncthreads();
-            }
-            near = far;
-        }
-        t = te;
+        ctl->fused[k] = 1;
     }
 }
 
 // ------------------------------------------------------- re-sweep table
 // Flagged segment k becomes segment k of a new table whose records are the
-// sorted copy; slots nflag .. n_slots-1 are empty segments.
+// sorted copy (or its own records, when found in order); fused segments
+// (already swept) and slots nflag .. n_slots-1 are empty segments.
 __global__ void __launch_bounds__(256) sort_resweep_plan_kernel(const SegDesc* __restrict__ segs, SortCtl* ctl,
                                                                 SegDesc* out, uint64_t* out_start,
                                                                 uint64_t* out_rend, uint32_t n_slots) {
@@ -564,10 +399,10 @@ __global__ void __launch_bounds__(256) sort_resweep_plan_kernel(const SegDesc* _
             out_start[k] = ctl->nrec;
             continue;
         }
-        if (k < nflag) {
+        if (k < nflag && !ctl->fused[k]) {
             SegDesc s = segs[ctl->list[k]];
             if (ctl->nruns[k] != kInOrder) {
-                const int P = ctl->rounds[k] ? static_cast<int>(ctl->rounds[k]) : passes_for(ctl->mn[k], ctl->mx[k]);
+                const int P = passes_for(ctl->mn[k], ctl->mx[k]);
                 const int b = (P - 1) & 1;
                 s.se = ctl->buf_se[b] + 2 * ctl->rec_base[k];
                 s.tag = ctl->buf_tag[b] + ctl->rec_base[k];
@@ -577,30 +412,32 @@ __global__ void __launch_bounds__(256) sort_resweep_plan_kernel(const SegDesc* _
             out_start[k] = ctl->rec_base[k];
             out_rend[k] = ctl->rec_base[k] + s.n;
         } else {
+            // no records; the table's starts stay non-decreasing (a fused
+            // segment keeps its place, the unused slots sit at the end)
             SegDesc s = segs[0];
             s.n = 0;
             s.is_host = 1;
             s.R = 0;
             out[k] = s;
-            out_start[k] = ctl->nrec;
-            out_rend[k] = ctl->nrec;
+            const uint64_t at = k < nflag ? ctl->rec_base[k] : ctl->nrec;
+            out_start[k] = at;
+            out_rend[k] = at;
         }
     }
 }
 
 }  // namespace
 
-cudaError_t launch_sort_stage(const SegDesc* segs, uint32_t n_segs, uint32_t n_slots, const uint32_t* seg_flags,
+cudaError_t launch_sort_stage(const SegDesc* segs, uint32_t n_segs, uint32_t n_slots, uint32_t* seg_flags,
                               SortCtl* ctl, SegDesc* resweep_segs, uint64_t* resweep_start, uint64_t* resweep_rend,
-                              int grid_tiles, int grid_segs, cudaStream_t stream) {
+                              int grid_tiles, int grid_segs, uint32_t* gstatus, int64_t wait_limit,
+                              cudaStream_t stream) {
     if (n_slots == 0) return cudaSuccess;
     sort_plan_kernel<<<1, 1024, 0, stream>>>(segs, n_segs, seg_flags, ctl);
     sort_minmax_kernel<<<grid_tiles, kSortThreads, 0, stream>>>(segs, ctl);
     sort_merge_plan_kernel<<<grid_segs, 32, 0, stream>>>(segs, ctl);
-    for (int r = 0; r < kMergeRounds; ++r) {
-        sort_merge_split_kernel<<<grid_tiles, 256, 0, stream>>>(segs, ctl, r);
-        sort_merge_kernel<<<grid_tiles, 256, 0, stream>>>(segs, ctl, r);
-    }
+    cudaError_t e = launch_fms(segs, ctl, seg_flags, gstatus, wait_limit, grid_tiles, stream);
+    if (e != cudaSuccess) return e;
     for (int p = 0; p < 8; ++p) {
         sort_hist_kernel<<<grid_tiles, kSortThreads, 0, stream>>>(segs, ctl, p);
         sort_scan_kernel<<<grid_segs, 256, 0, stream>>>(ctl, p);
