@@ -78,8 +78,12 @@ struct __align__(16) FmsStage {
 struct FmsShared {
     FmsStage st[kFmsStages];
     // the chunk the consumers work on: merged order (two index buffers for
-    // the merge rounds) and every record's tag in staging order
+    // the merge rounds), and every record's tag, start and end in staging
+    // order (start and end as 32-bit offsets from the chunk's smallest start,
+    // when its span allows; the merge rounds of that case carry the keys)
     uint16_t ix[2][kFmsChunk];
+    uint32_t key[2][kFmsChunk];
+    uint32_t end32[kFmsChunk];
     uint8_t tagc[kFmsChunk];
     uint64_t full[kFmsStages], empty[kFmsStages];
     int64_t red64[kFmsConsumers][4];
@@ -380,6 +384,97 @@ __device__ __forceinline__ int merge_rounds(FmsShared& sh, const FmsStage& S, co
         ++round;
     }
     return (round - 1) & 1;
+}
+
+// The 32-bit merge of a chunk (span within 2^32 ns of its smallest start):
+// the same pairwise merge-path rounds over (key, staging index) pairs held in
+// compact arrays, key = start offset.  Round 0 reads sh.key[0] in staging
+// order (index = position); each round but the last writes key[(r + 1) & 1]
+// and ix[(r + 1) & 1]; the last round (one pair: everything) writes its
+// outputs -- thread ct's E consecutive positions of the merged order, the
+// same block the sweep gives the thread -- straight into the thread's
+// registers: start and end offsets and tag.  cnt: records of the thread.
+__device__ __forceinline__ void merge32(FmsShared& sh, const ChunkMeta& M, int ct, uint32_t E, int cnt,
+                                        uint32_t (&sr)[kFmsItems], uint32_t (&er)[kFmsItems],
+                                        uint32_t (&tg)[kFmsItems]) {
+    const uint32_t n = M.n, nr = M.nr;
+    uint32_t width = 1;   // runs per group entering the round
+    int r = 0;
+    for (; 2 * width < nr; width *= 2, ++r) {
+        const uint32_t* kin = sh.key[r & 1];
+        const uint16_t* iin = sh.ix[r & 1];
+        uint32_t* kout = sh.key[(r + 1) & 1];
+        uint16_t* iout = sh.ix[(r + 1) & 1];
+        const uint32_t o0 = static_cast<uint32_t>(ct) * E;
+        const uint32_t o1 = min(n, o0 + E);
+        uint32_t o = o0;
+        while (o < o1) {
+            uint32_t g = 0;
+            while (M.roff[min(g + 2 * width, nr)] <= o) g += 2 * width;
+            const uint32_t a0 = M.roff[g], a1 = M.roff[min(g + width, nr)], b1 = M.roff[min(g + 2 * width, nr)];
+            const uint32_t la = a1 - a0, lb = b1 - a1;
+            const uint32_t l = o - a0;
+            uint32_t lo = l > lb ? l - lb : 0u, hi = l < la ? l : la;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (kin[a0 + mid] <= kin[a1 + l - mid - 1]) lo = mid + 1; else hi = mid;
+            }
+            uint32_t i = lo, j = l - lo;
+            const uint32_t stop = min(o1, b1);
+            uint32_t ka = i < la ? kin[a0 + i] : 0xFFFFFFFFu, kb = j < lb ? kin[a1 + j] : 0xFFFFFFFFu;
+            for (; o < stop; ++o) {
+                const bool takeA = j >= lb || (i < la && ka <= kb);
+                const uint32_t at = takeA ? a0 + i : a1 + j;
+                kout[o] = takeA ? ka : kb;
+                iout[o] = r ? iin[at] : static_cast<uint16_t>(at);
+                if (takeA) {
+                    ++i;
+                    ka = i < la ? kin[a0 + i] : 0xFFFFFFFFu;
+                } else {
+                    ++j;
+                    kb = j < lb ? kin[a1 + j] : 0xFFFFFFFFu;
+                }
+            }
+        }
+        cbar();
+    }
+    // the last round: groups [0, width) and [width, nr) of runs
+    const uint32_t* kin = sh.key[r & 1];
+    const uint16_t* iin = sh.ix[r & 1];
+    const uint32_t a1 = M.roff[min(width, nr)];
+    const uint32_t la = a1, lb = n - a1;
+    const uint32_t l = static_cast<uint32_t>(ct) * E;
+    uint32_t i = 0, j = 0;
+    if (cnt > 0) {
+        uint32_t lo = l > lb ? l - lb : 0u, hi = l < la ? l : la;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (kin[mid] <= kin[a1 + l - mid - 1]) lo = mid + 1; else hi = mid;
+        }
+        i = lo;
+        j = l - lo;
+    }
+    uint32_t ka = i < la ? kin[i] : 0xFFFFFFFFu, kb = j < lb ? kin[a1 + j] : 0xFFFFFFFFu;
+#pragma unroll
+    for (int q = 0; q < kFmsItems; ++q) {
+        if (q < cnt) {
+            const bool takeA = j >= lb || (i < la && ka <= kb);
+            const uint32_t at = takeA ? i : a1 + j;
+            const uint32_t x = r ? iin[at] : at;
+            sr[q] = takeA ? ka : kb;
+            er[q] = sh.end32[x];
+            tg[q] = sh.tagc[x];
+            if (takeA) {
+                ++i;
+                ka = i < la ? kin[i] : 0xFFFFFFFFu;
+            } else {
+                ++j;
+                kb = j < lb ? kin[a1 + j] : 0xFFFFFFFFu;
+            }
+        } else {
+            sr[q] = er[q] = tg[q] = 0;
+        }
+    }
 }
 
 __device__ __forceinline__ void add_sums(int64_t* p, int64_t a, int64_t b, int64_t c) {
@@ -764,6 +859,8 @@ __global__ void __launch_bounds__(kFmsThreads, 2)
                 const int64_t de = v.y - s0;
                 hib |= static_cast<uint32_t>(static_cast<uint64_t>(de) >> 32);
                 const uint32_t r = static_cast<uint32_t>(de);
+                sh.key[0][i] = static_cast<uint32_t>(v.x - s0);   // used only when the span allows
+                sh.end32[i] = r;
                 if (tg < 32u) bK = umax(bK, r); else bM = umax(bM, r);
             }
         }
@@ -833,36 +930,28 @@ __global__ void __launch_bounds__(kFmsThreads, 2)
             }
         }
 
-        // ---- merged order (the barrier after the aggregate's reduction above
-        // also published tagc)
-        const int pb = merge_rounds(sh, S, M, ct, E);
-        const uint16_t* perm = sh.ix[pb];
-
-        // ---- the sweep of the merged order
+        // ---- merged order and the sweep (the barrier after the aggregate's
+        // reduction above also published the compact arrays)
         const int64_t spanHi = max64(aK, aM);
         const int64_t hiK = FIX ? max64(M.TK, LK) : LK, hiM = FIX ? max64(M.TM, LM) : LM;
         const bool fast = span32 && (hiK <= s0 || ((hiK - s0) >> 32) == 0) && (hiM <= s0 || ((hiM - s0) >> 32) == 0);
+        const uint16_t* perm = nullptr;
         if (fast) {
             const uint32_t p0 = static_cast<uint32_t>(ct) * E;
             const int cnt = p0 < n ? static_cast<int>(min(E, n - p0)) : 0;
             uint32_t sr[kFmsItems], er[kFmsItems], tg[kFmsItems];
-#pragma unroll
-            for (int i = 0; i < kFmsItems; ++i) {
-                if (i < cnt) {
-                    const uint32_t x = perm[p0 + i];
-                    const longlong2 v = S.rows[x];
-                    sr[i] = static_cast<uint32_t>(v.x - s0);
-                    er[i] = static_cast<uint32_t>(v.y - s0);
-                    tg[i] = sh.tagc[x];
-                } else {
-                    sr[i] = er[i] = tg[i] = 0;
-                }
-            }
+            merge32(sh, M, ct, E, cnt, sr, er, tg);
             uint32_t bK = 0, bM = 0;
             bool okE = true, okS = true, okK = true;
             dev_pass1<kFmsItems, false>(sr, er, tg, cnt, bK, bM, okE, okS, okK);
+            // order self-check of the merge, inside the thread and across lanes
+            uint32_t last = 0;
+#pragma unroll
+            for (int q = 0; q < kFmsItems; ++q)
+                if (q < cnt) last = sr[q];
+            const uint32_t prev_last = __shfl_up_sync(0xFFFFFFFFu, last, 1);
             uint32_t mybad = okS ? 0u : ST_UNSORTED;
-            if (cnt > 0 && p0 > 0 && S.rows[perm[p0 - 1]].x > S.rows[perm[p0]].x) mybad |= ST_UNSORTED;
+            if (cnt > 0 && (ct & 31) > 0 && prev_last > sr[0]) mybad |= ST_UNSORTED;
             mybad = __reduce_or_sync(0xFFFFFFFFu, mybad);
             if ((ct & 31) == 0 && mybad) atomicOr(&sh.bad, mybad);
             if (FIX) {
@@ -872,6 +961,7 @@ __global__ void __launch_bounds__(kFmsThreads, 2)
                 sweep32(sh, s0, spanHi, ct, cnt, R, sr, er, tg, bK, bM, LK, LM, d.sums, 1);
             }
         } else {
+            perm = sh.ix[merge_rounds(sh, S, M, ct, E)];
             if (FIX) {
                 sweep64(sh, S, M, perm, ct, E, R, M.TK, M.TM, d.sums, 1);
                 sweep64(sh, S, M, perm, ct, E, R, LK, LM, d.sums, -1);
