@@ -210,7 +210,8 @@ talp_gpu_status talp_gpu_ingest_events(talp_gpu_ctx *ctx, const talp_gpu_trace_b
  * order, raw_dev being the record's device within its rank (0 ..
  * devices_per_rank[i] - 1, at most 8 devices per rank).  Records of one
  * stream must be delivered in start order (a stream executes in order); the
- * streams may interleave arbitrarily.
+ * streams may interleave arbitrarily.  (A stream found out of start order
+ * makes the next result call for the trace return EINVAL.)
  *
  * TALP_GPU_HOLD_BACK streams a trace's buffers over several calls.  A later
  * buffer may still bring a record that starts before records of other

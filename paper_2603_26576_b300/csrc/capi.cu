@@ -115,7 +115,7 @@ struct Layout {
     size_t up_bytes = 0;
     size_t off_wrec = 0, off_flags = 0, off_gst = 0, off_bk = 0, off_slist = 0, off_srb = 0, off_stb = 0;
     size_t off_smn = 0, off_smx = 0, off_hist = 0, off_offs = 0, off_rsegs = 0, off_rstart = 0, off_mout = 0;
-    size_t off_nruns = 0, off_runs = 0, off_fused = 0;
+    size_t off_nruns = 0, off_runs = 0, off_fused = 0, off_known = 0, off_given = 0;
     uint64_t fms_samples = 0, fms_chunks = 0, fms_super = 0;   // table bounds of the fused merge-sweep
     size_t off_fS = 0, off_fsb = 0, off_fcb = 0, off_fpb = 0, off_fscb = 0, off_fsamp = 0, off_fsplit = 0,
            off_fseg = 0, off_fchunk = 0, off_fscagg = 0, off_ffix = 0;
@@ -165,6 +165,8 @@ struct talp_gpu_ctx {
     std::unordered_map<uint64_t, RawHold*> holds;   // trace id -> held-back raw records
     bool raw_inner = false;              // ingest_events called by ingest_raw
     std::vector<uint8_t> raw_presort;    // with raw_inner: per device of the ingest, known out of order
+    const uint64_t* raw_runs = nullptr;  // with raw_inner: per device of the ingest, its lane's known runs
+                                         // (device memory, kRunsStride entries each)
 };
 
 const TraceDev* talp::trace_device_desc(talp_gpu_ctx* c, uint64_t trace_id, uint32_t* n_regions) {
@@ -421,7 +423,8 @@ talp_gpu_status size_ingest(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches
     L.off_send = align_up(L.off_start + sizeof(uint64_t) * (L.n_segs + 1), 256);
     L.off_jobs = align_up(L.off_send + sizeof(uint64_t) * (L.n_segs + 1), 256);
     L.off_rest = align_up(L.off_jobs + sizeof(FillJob) * L.n_jobs_max, 256);
-    L.off_sctl = align_up(L.off_rest + sizeof(int64_t*) * (L.sorting ? L.n_segs : 0), 256);
+    L.off_known = align_up(L.off_rest + sizeof(int64_t*) * (L.sorting ? L.n_segs : 0), 256);
+    L.off_sctl = align_up(L.off_known + sizeof(uint64_t*) * (L.sorting ? L.n_segs : 0), 256);
     L.off_fin = align_up(L.off_sctl + sizeof(SortCtl), 256);
     L.off_pay = align_up(L.off_fin + sizeof(FinalizeJob) * L.n_fin, 256);
     L.up_bytes = align_up(L.off_pay + 8 * L.payload_words, 256);
@@ -439,7 +442,8 @@ talp_gpu_status size_ingest(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches
     L.off_nruns = align_up(L.off_offs + 8 * 256 * L.sort_tiles, 256);
     L.off_runs = align_up(L.off_nruns + 4 * L.sort_slots, 256);
     L.off_fused = align_up(L.off_runs + 8 * (kMaxRuns + 1) * L.sort_slots, 256);
-    L.off_fS = align_up(L.off_fused + 4 * L.sort_slots, 256);
+    L.off_given = align_up(L.off_fused + 4 * L.sort_slots, 256);
+    L.off_fS = align_up(L.off_given + 4 * L.sort_slots, 256);
     L.off_fsb = align_up(L.off_fS + 4 * L.sort_slots, 256);
     L.off_fcb = align_up(L.off_fsb + 8 * (L.sort_slots + 1), 256);
     L.off_fpb = align_up(L.off_fcb + 8 * (L.sort_slots + 1), 256);
@@ -534,6 +538,7 @@ talp_gpu_status fill_ingest(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches
     uint64_t* send = reinterpret_cast<uint64_t*>(up + L.off_send);
     FillJob* jobs = reinterpret_cast<FillJob*>(up + L.off_jobs);
     const int64_t** restore = reinterpret_cast<const int64_t**>(up + L.off_rest);
+    const uint64_t** known = reinterpret_cast<const uint64_t**>(up + L.off_known);
     FinalizeJob* fin = reinterpret_cast<FinalizeJob*>(up + L.off_fin);
     int64_t* pay = reinterpret_cast<int64_t*>(up + L.off_pay);
     int64_t* pay_dev = reinterpret_cast<int64_t*>(wsd + L.off_pay);
@@ -624,6 +629,10 @@ talp_gpu_status fill_ingest(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches
             sstart[si] = pos;
             const bool presort = (b.flags & TALP_GPU_NOT_SORTED) ||
                                  (c->raw_inner && presort_at + g < c->raw_presort.size() && c->raw_presort[presort_at + g]);
+            if (L.sorting)   // a raw lane's runs are its streams, known from the adapter
+                known[si] = (sflag && presort && c->raw_inner && c->raw_runs)
+                                ? c->raw_runs + static_cast<size_t>(presort_at + g) * kRunsStride
+                                : nullptr;
             if (sflag && presort) {
                 s.pad[0] |= kSegPresort;   // not in the first sweep: sorted, then swept
                 send[si] = pos;
@@ -647,7 +656,10 @@ talp_gpu_status fill_ingest(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches
             s.n = b.host_off[i + 1] - o;
             s.R = static_cast<uint16_t>(R);
             s.is_host = 1;
-            if (L.sorting) restore[si] = nullptr;
+            if (L.sorting) {
+                restore[si] = nullptr;
+                known[si] = nullptr;
+            }
             sstart[si] = pos;
             send[si] = pos + s.n;
             pos += s.n + L.seg_cost;
@@ -673,6 +685,8 @@ talp_gpu_status fill_ingest(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches
         sc.nruns = reinterpret_cast<uint32_t*>(wsd + L.off_nruns);
         sc.runs = reinterpret_cast<uint64_t*>(wsd + L.off_runs);
         sc.fused = reinterpret_cast<uint32_t*>(wsd + L.off_fused);
+        sc.given = reinterpret_cast<uint32_t*>(wsd + L.off_given);
+        sc.known = reinterpret_cast<const uint64_t* const*>(wsd + L.off_known);
         sc.fms_S = reinterpret_cast<uint32_t*>(wsd + L.off_fS);
         sc.fms_samp_base = reinterpret_cast<uint64_t*>(wsd + L.off_fsb);
         sc.fms_chunk_base = reinterpret_cast<uint64_t*>(wsd + L.off_fcb);
@@ -1165,6 +1179,7 @@ talp_gpu_status talp_gpu_ingest_raw(talp_gpu_ctx* c, const talp_gpu_raw_batch* r
     const size_t o_hist = o; o = align_up(o + 4ull * kRawBuckets * nt, 256);
     const size_t o_offs = o; o = align_up(o + 8ull * kRawBuckets * nt, 256);
     const size_t o_moves = o; o = align_up(o + (any_hold ? sizeof(RawMove) * kRawBuckets * nrk : 0), 256);
+    const size_t o_runs = o; o = align_up(o + 8ull * kRunsStride * mtot, 256);
     const size_t o_cnt = o; o = align_up(o + 8 * mtot, 256);
     const size_t o_fcnt = o; o = align_up(o + 8 * mtot, 256);
     const size_t o_hcnt = o; o = align_up(o + 8 * nrk, 256);
@@ -1298,7 +1313,8 @@ talp_gpu_status talp_gpu_ingest_raw(talp_gpu_ctx* c, const talp_gpu_raw_batch* r
     uint32_t* dst = reinterpret_cast<uint32_t*>(R + o_st);
     TALP_CUDA(launch_raw_count(dtiles, static_cast<uint32_t>(nt), dranks, static_cast<uint32_t>(nrk),
                                reinterpret_cast<uint32_t*>(R + o_hist), reinterpret_cast<uint64_t*>(R + o_offs), dmoves,
-                               reinterpret_cast<uint64_t*>(R + o_cnt), reinterpret_cast<uint32_t*>(R + o_nstr), dst,
+                               reinterpret_cast<uint64_t*>(R + o_cnt), reinterpret_cast<uint32_t*>(R + o_nstr),
+                               reinterpret_cast<uint64_t*>(R + o_runs), dst,
                                grid, stream));
     TALP_CUDA(launch_raw_scatter(dtiles, static_cast<uint32_t>(nt), dranks, reinterpret_cast<const uint64_t*>(R + o_offs),
                                  reinterpret_cast<int64_t*>(R + o_lse), reinterpret_cast<uint8_t*>(R + o_ltag), dst,
@@ -1307,6 +1323,7 @@ talp_gpu_status talp_gpu_ingest_raw(talp_gpu_ctx* c, const talp_gpu_raw_batch* r
     if (any_hold) {
         TALP_CUDA(launch_raw_hold(dranks, static_cast<uint32_t>(nrk), reinterpret_cast<const int64_t*>(R + o_lse), dmoves,
                                   reinterpret_cast<uint64_t*>(R + o_fcnt), reinterpret_cast<uint64_t*>(R + o_hcnt), dst,
+                                  reinterpret_cast<uint64_t*>(R + o_runs),
                                   stream));
         ++c->kernel_launches;
     }
@@ -1395,8 +1412,10 @@ talp_gpu_status talp_gpu_ingest_raw(talp_gpu_ctx* c, const talp_gpu_raw_batch* r
     for (size_t k = 0; k < nb; ++k)
         if (!hb[k] && holds.count(rb[k].trace_id)) raw_hold_drop(c, rb[k].trace_id);
     c->raw_inner = true;
+    c->raw_runs = reinterpret_cast<const uint64_t*>(R + o_runs);
     const talp_gpu_status st = talp_gpu_ingest_events(c, tb.data(), nb, stream_);
     c->raw_inner = false;
+    c->raw_runs = nullptr;
     c->raw_presort.clear();
     TALP_CUDA(cudaEventRecord(c->ev_raw, stream));
     c->raw_used = true;

@@ -128,6 +128,9 @@ struct SortCtl {
     uint8_t* buf_tag[2];
     const uint8_t* buf_tag_limit[2];
     const int64_t* const* restore;  // [segments] sums a flagged segment restarts from (null: zero)
+    const uint64_t* const* known;   // [segments] runs already known (null: none): count r, then the
+                                    // r + 1 run boundaries (kRunsStride entries; r < 2: unknown)
+    uint32_t* given;           // [slots] 1: k's runs came from `known` (the min/max pass skips k)
     uint32_t* nruns;           // [slots] descents found in k (runs - 1)
     uint64_t* runs;            // [slots][kMaxRuns + 1] run boundaries of k (sorted by the merge plan)
     uint32_t* fused;           // [slots] 1: k is a few sorted runs, merged and swept in one pass
@@ -171,6 +174,7 @@ struct FmsFix {
 // by stream, each stream in start order) is merged and swept in one pass
 // (fms.cu) instead of being radix sorted and swept again.
 constexpr int kMaxRuns = 16;
+constexpr int kRunsStride = kMaxRuns + 2;   // entries of a known-runs record
 // Records per chunk of the fused merge-sweep (at most).  A segment of r runs
 // is sampled every S = kFmsChunk / ((kFmsSpread + 1) r) records of each run
 // and cut at every (kFmsSpread r)-th sample in merged order; a chunk then

@@ -45,12 +45,14 @@ cudaError_t launch_concurrency(const int64_t* se, const uint8_t* tag, const Conc
                                uint32_t* status, cudaStream_t stream);
 cudaError_t launch_raw_count(const RawTile* tiles, uint32_t n_tiles, const RawRank* ranks, uint32_t n_ranks,
                              uint32_t* hist, uint64_t* offs, RawMove* moves, uint64_t* dev_count,
-                             uint32_t* dev_streams, uint32_t* status, int grid, cudaStream_t stream);
+                             uint32_t* dev_streams, uint64_t* dev_runs, uint32_t* status, int grid,
+                             cudaStream_t stream);
 cudaError_t launch_raw_scatter(const RawTile* tiles, uint32_t n_tiles, const RawRank* ranks, const uint64_t* offs,
                                int64_t* lse, uint8_t* ltag, uint32_t* status, int64_t wait_limit, int grid,
                                cudaStream_t stream);
 cudaError_t launch_raw_hold(const RawRank* ranks, uint32_t n_ranks, const int64_t* lse, RawMove* moves,
-                            uint64_t* fold_count, uint64_t* hold_count, uint32_t* status, cudaStream_t stream);
+                            uint64_t* fold_count, uint64_t* hold_count, uint32_t* status, uint64_t* dev_runs,
+                            cudaStream_t stream);
 cudaError_t launch_raw_move(const RawTile* tiles, uint32_t n_tiles, const RawRank* ranks, const RawMove* moves,
                             const uint64_t* fold_base, const int64_t* lse, const uint8_t* ltag, int64_t* fse,
                             uint8_t* ftag, int grid, cudaStream_t stream);

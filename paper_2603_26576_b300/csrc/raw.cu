@@ -67,10 +67,38 @@ __global__ void __launch_bounds__(kRawThreads) raw_hist_kernel(const RawTile* __
 
 // per rank: output position of every (tile, bucket), each bucket's lane
 // range and each device's count
+// The runs of a device lane made of its streams one after another (each
+// stream in start order): the boundaries between its non-empty streams.
+// Written as a known-runs record (count r, then the r + 1 boundaries), or
+// count 0 when the lane has fewer than 2 or more than kMaxRuns non-empty
+// streams (the sort stage then finds the runs itself).  cnt(s): records of
+// stream s in the lane.
+template <typename F>
+__device__ __forceinline__ void write_runs(uint64_t* rec, F cnt) {
+    uint32_t r = 0;
+    for (int s = 0; s < 32; ++s) r += cnt(s) ? 1u : 0u;
+    if (r < 2 || r > static_cast<uint32_t>(kMaxRuns)) {
+        rec[0] = 0;
+        return;
+    }
+    rec[0] = r;
+    uint64_t at = 0;
+    uint32_t j = 0;
+    rec[1] = 0;
+    for (int s = 0; s < 32; ++s) {
+        const uint64_t c = cnt(s);
+        if (c) {
+            at += c;
+            rec[2 + j++] = at;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kBuckets) raw_scan_kernel(const RawRank* __restrict__ ranks, uint32_t n_ranks,
                                                             const uint32_t* __restrict__ hist, uint64_t* __restrict__ offs,
                                                             RawMove* __restrict__ moves, uint64_t* __restrict__ dev_count,
-                                                            uint32_t* __restrict__ dev_streams) {
+                                                            uint32_t* __restrict__ dev_streams,
+                                                            uint64_t* __restrict__ dev_runs) {
     __shared__ uint64_t s_tot[kBuckets];
     const uint32_t b = threadIdx.x;
     for (uint32_t r = blockIdx.x; r < n_ranks; r += gridDim.x) {
@@ -123,6 +151,9 @@ __global__ void __launch_bounds__(kBuckets) raw_scan_kernel(const RawRank* __res
             }
             dev_count[rk.dev0 + b] = c;
             dev_streams[rk.dev0 + b] = ns;
+            if (dev_runs)
+                write_runs(dev_runs + static_cast<uint64_t>(rk.dev0 + b) * kRunsStride,
+                           [&](int q) { return s_tot[b * 32 + q]; });
         }
         __syncthreads();
     }
@@ -224,7 +255,8 @@ __global__ void __launch_bounds__(kBuckets) raw_hold_kernel(const RawRank* __res
                                                             RawMove* __restrict__ moves,
                                                             uint64_t* __restrict__ fold_count,
                                                             uint64_t* __restrict__ hold_count,
-                                                            uint32_t* __restrict__ status) {
+                                                            uint32_t* __restrict__ status,
+                                                            uint64_t* __restrict__ dev_runs) {
     __shared__ uint32_t s_f[kBuckets], s_h[kBuckets];
     const uint32_t b = threadIdx.x;
     const uint32_t d = b >> 5, sidx = b & 31;
@@ -268,7 +300,13 @@ __global__ void __launch_bounds__(kBuckets) raw_hold_kernel(const RawRank* __res
         mv.nfold = lo;
         mv.nhold = n - lo;
         moves[static_cast<uint64_t>(r) * kBuckets + b] = mv;
-        if (sidx == 0 && d < rk.D) fold_count[rk.dev0 + d] = df;
+        if (sidx == 0 && d < rk.D) {
+            fold_count[rk.dev0 + d] = df;
+            // the fold lane is each stream's final part, stream after stream
+            if (dev_runs)
+                write_runs(dev_runs + static_cast<uint64_t>(rk.dev0 + d) * kRunsStride,
+                           [&](int q) { return static_cast<uint64_t>(s_f[d * 32 + q]); });
+        }
         if (b == 0) hold_count[r] = rh;
         __syncthreads();
     }
@@ -329,11 +367,13 @@ __global__ void __launch_bounds__(kRawThreads) raw_move_kernel(const RawTile* __
 
 cudaError_t launch_raw_count(const RawTile* tiles, uint32_t n_tiles, const RawRank* ranks, uint32_t n_ranks,
                              uint32_t* hist, uint64_t* offs, RawMove* moves, uint64_t* dev_count,
-                             uint32_t* dev_streams, uint32_t* status, int grid, cudaStream_t stream) {
+                             uint32_t* dev_streams, uint64_t* dev_runs, uint32_t* status, int grid,
+                             cudaStream_t stream) {
     if (n_tiles) raw_hist_kernel<<<grid, kRawThreads, 0, stream>>>(tiles, n_tiles, ranks, hist, status);
     if (n_ranks)
         raw_scan_kernel<<<n_ranks < 65535u ? n_ranks : 65535u, kBuckets, 0, stream>>>(ranks, n_ranks, hist, offs,
-                                                                                     moves, dev_count, dev_streams);
+                                                                                     moves, dev_count, dev_streams,
+                                                                                     dev_runs);
     return cudaGetLastError();
 }
 
@@ -346,10 +386,12 @@ cudaError_t launch_raw_scatter(const RawTile* tiles, uint32_t n_tiles, const Raw
 }
 
 cudaError_t launch_raw_hold(const RawRank* ranks, uint32_t n_ranks, const int64_t* lse, RawMove* moves,
-                            uint64_t* fold_count, uint64_t* hold_count, uint32_t* status, cudaStream_t stream) {
+                            uint64_t* fold_count, uint64_t* hold_count, uint32_t* status, uint64_t* dev_runs,
+                            cudaStream_t stream) {
     if (n_ranks)
         raw_hold_kernel<<<n_ranks < 65535u ? n_ranks : 65535u, kBuckets, 0, stream>>>(ranks, n_ranks, lse, moves,
-                                                                                     fold_count, hold_count, status);
+                                                                                     fold_count, hold_count, status,
+                                                                                     dev_runs);
     return cudaGetLastError();
 }
 

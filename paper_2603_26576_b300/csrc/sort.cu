@@ -126,9 +126,20 @@ __global__ void __launch_bounds__(1024) sort_plan_kernel(const SegDesc* __restri
             ctl->mx[k] = INT64_MIN;
             ctl->nruns[k] = 0;
             ctl->fused[k] = 0;
+            ctl->given[k] = 0;
+            const SegDesc& d = segs[s];
+            // runs already known (a raw lane: its streams, one after another):
+            // taken as they are, and the min/max pass leaves the segment alone
+            const uint64_t* kr = ctl->known ? ctl->known[s] : nullptr;
+            if (kr && kr[0] >= 2 && kr[0] <= static_cast<uint64_t>(kMaxRuns) && kr[1 + kr[0]] == d.n) {
+                const uint32_t r = static_cast<uint32_t>(kr[0]);
+                uint64_t* runs = ctl->runs + static_cast<uint64_t>(k) * (kMaxRuns + 1);
+                for (uint32_t q = 0; q <= r; ++q) runs[q] = kr[1 + q];
+                ctl->nruns[k] = r - 1;
+                ctl->given[k] = 1;
+            }
             // the re-sweep recomputes this ingest's part of the segment: its
             // sums restart from their value before the ingest
-            const SegDesc& d = segs[s];
             const int64_t* src = ctl->restore[s];
             for (int q = 0; q < 3 * d.R; ++q) d.sums[q] = src ? src[q] : 0;
             d.carry_out[0] = d.carry_in[0];
@@ -159,6 +170,10 @@ __global__ void __launch_bounds__(kSortThreads) sort_minmax_kernel(const SegDesc
     const uint32_t ntile = static_cast<uint32_t>(ctl->ntile);
     for (uint32_t t = blockIdx.x; t < ntile; t += gridDim.x) {
         const uint32_t k = seg_of_tile(ctl, t);
+        if (ctl->given[k]) {   // runs known already (block-uniform)
+            t = skip_segment(ctl, k, t);
+            continue;
+        }
         const SegDesc& d = segs[ctl->list[k]];
         const uint64_t r0 = static_cast<uint64_t>(t - ctl->tile_base[k]) * kSortTile;
         int64_t mn = INT64_MAX, mx = INT64_MIN;
