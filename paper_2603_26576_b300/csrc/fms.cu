@@ -61,6 +61,7 @@ struct ChunkMeta {
     uint64_t sc;                   // its super-chunk (main pass)
     uint32_t k, c, nr, n, valid;
     uint32_t first, last, seg_first;   // first / last chunk of its super-chunk; super-chunk 0 of its segment
+    uint32_t given;                // the segment's runs were given (not found by the min/max pass)
     int64_t LK, LM;                // fix-up: the carry it was swept with
     int64_t TK, TM;                // fix-up: the true carry
     uint32_t roff[kMaxRuns + 1];   // staging row offset of each run's range (prefix)
@@ -639,6 +640,7 @@ __global__ void __launch_bounds__(kFmsThreads, 2)
         const uint8_t* dtag = nullptr;
         uintptr_t lim = 0;
         uint64_t dn = 0;
+        uint32_t given = 0;
         bool first = false;
         for (uint32_t it = 0;; ++it) {
             const int s = static_cast<int>(it % kFmsStages);
@@ -704,6 +706,7 @@ __global__ void __launch_bounds__(kFmsThreads, 2)
                 nr = ctl->nruns[k] + 1;
                 split0 = ctl->fms_split_base[k];
                 cb = ctl->fms_chunk_base[k];
+                given = ctl->given[k];
             }
             const uint32_t c = static_cast<uint32_t>(g - cb);
             const uint64_t* row = ctl->fms_split + split0 + static_cast<uint64_t>(c) * nr;
@@ -745,11 +748,15 @@ __global__ void __launch_bounds__(kFmsThreads, 2)
                                                               hi > dn));
             if (rng_bad || n_tot == 0 || n_tot > static_cast<uint32_t>(kFmsChunk) ||
                 t_tot > static_cast<uint32_t>(kFmsTagBytes)) {
-                // cannot happen (a chunk holds 1 .. kFmsChunk records): the
-                // copies are not issued and the sweep reports a time-out
+                // cannot happen for runs in start order (a chunk holds 1 ..
+                // kFmsChunk records): the copies are not issued, and the sweep
+                // reports a time-out -- or, when the runs were given, records
+                // out of start order (a given run that is not in order can
+                // split unevenly)
                 if (lane == 0) {
-                    atomicOr(gstatus, ST_TIMEOUT);
-                    atomicOr(segs[ctl->list[k]].status, ST_TIMEOUT);
+                    const uint32_t why = given ? ST_UNSORTED : ST_TIMEOUT;
+                    if (!given) atomicOr(gstatus, ST_TIMEOUT);
+                    atomicOr(segs[ctl->list[k]].status, why);
                     S.meta.valid = 0;
                     mbar_arrive(&sh.full[s]);
                 }
@@ -773,6 +780,7 @@ __global__ void __launch_bounds__(kFmsThreads, 2)
                 S.meta.first = FIX ? 0u : (first ? 1u : 0u);
                 S.meta.last = FIX ? 0u : (g + 1 == g_end ? 1u : 0u);
                 S.meta.seg_first = FIX ? 0u : (sc == scb ? 1u : 0u);
+                S.meta.given = given;
                 S.meta.LK = LK;
                 S.meta.LM = LM;
                 S.meta.TK = TK;
@@ -861,9 +869,15 @@ __global__ void __launch_bounds__(kFmsThreads, 2)
                 const uint32_t r = static_cast<uint32_t>(de);
                 sh.key[0][i] = static_cast<uint32_t>(v.x - s0);   // used only when the span allows
                 sh.end32[i] = r;
+                // given runs: each must be in start order (found ones are by construction)
+                if (M.given && i > M.roff[q] && S.rows[i - 1].x > v.x) bad |= ST_UNSORTED;
                 if (tg < 32u) bK = umax(bK, r); else bM = umax(bM, r);
             }
         }
+        if (M.given && ct < static_cast<int>(nr) && M.roff[ct + 1] > M.roff[ct] &&
+            M.lo[ct] > ctl->runs[static_cast<uint64_t>(M.k) * (kMaxRuns + 1) + ct] &&
+            d.se[2 * (M.lo[ct] - 1)] > S.rows[M.roff[ct]].x)
+            bad |= ST_UNSORTED;   // a given run out of order across the chunk's boundary
         bK = __reduce_max_sync(0xFFFFFFFFu, bK);
         bM = __reduce_max_sync(0xFFFFFFFFu, bM);
         hib = __reduce_or_sync(0xFFFFFFFFu, hib);

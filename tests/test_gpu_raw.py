@@ -279,3 +279,37 @@ def test_streams_that_do_not_interleave(ctx):
     ctx.ingest_raw([raw])
     assert_trace_equal(ctx, t, "streams-in-order")
     ctx.reset()
+
+
+@pytest.mark.parametrize("n_events", [300, 40_000])
+def test_stream_out_of_start_order_is_reported(ctx, n_events):
+    """A raw buffer must deliver each stream in start order (a stream
+    executes in order).  The adapter takes each device lane's streams as its
+    sorted runs, so a stream delivered out of order is reported by the next
+    result call (EINVAL), whether the descent falls inside a chunk of the
+    merge or across two; the same buffer in order is exact."""
+    import paper_2603_26576_b300 as P
+    t = tg.random_trace(12, trace_id=77, n_ranks=1, devices_per_rank=1, dev_events=n_events, host_events=50)
+    # three streams on the one device, interleaved in time
+    tag = (t.dev_tag & 0xE0) | (np.arange(t.n_dev) % 3).astype(np.uint8)
+    t = tg.Trace(trace_id=77, n_ranks=1, devices_per_rank=t.devices_per_rank, region_window=t.region_window,
+                 host_se=t.host_se, host_state=t.host_state, host_off=t.host_off, dev_se=t.dev_se, dev_tag=tag,
+                 dev_off=t.dev_off)
+    r = tg.to_raw(t)
+    ctx.ingest_raw([r])
+    assert_trace_equal(ctx, t, "raw-in-order", sums=False)
+    ctx.reset()
+    # swap two records of one stream with different starts: the stream's
+    # delivery is no longer in start order
+    se = r.raw_se.copy()
+    st = r.raw_tag & 31
+    idx = np.flatnonzero(st == 1)
+    a, b = int(idx[len(idx) // 3]), int(idx[len(idx) // 3 + 1])
+    assert se[a, 0] < se[b, 0]
+    se[[a, b]] = se[[b, a]]
+    bad = tg.RawTrace(t, se, r.raw_tag, r.raw_dev, r.raw_off)
+    ctx.ingest_raw([bad])
+    with pytest.raises(P.TalpGpuError) as e:
+        ctx.metrics(77)
+    assert e.value.status == EINVAL
+    ctx.reset()
