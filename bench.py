@@ -20,7 +20,8 @@ e2e     : the same metric through the C ABI from pinned HOST buffers, the
           copy of its metrics inside the timed region;
 roofline: the sweep kernel (the dominant kernel) against the measured HBM
           copy bandwidth: 17 algorithmic bytes per record / its CUDA-event
-          duration;
+          duration (with --unsorted: the sort stage, 17 bytes per device
+          record / its CUDA-event duration);
 cpu_baseline: the CPU oracle on a bounded one-rank sample of the workload.
 
 --impl reference times the CPU oracle itself (the slow, plain statement of
@@ -1283,14 +1284,26 @@ def main():
         e2e = {"value": N * k * ws / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d + meta),
                "d2h_bytes_per_step": int(R * 200), "steps": k}
 
-    # ---- roofline of the sweep kernel
+    # ---- roofline of the sweep kernel (records in start order), or of the
+    # sort stage (device records out of order: the fused merge-sweep reads
+    # every device record once, 17 B each)
     peak, peak_kind = measured_peaks()
     sweep_ms = prof["sweep_ms"] / max(1, prof["sweep_launches"])
-    achieved = BYTES_PER_RECORD * N / (sweep_ms / 1000.0) / 1e9
-    tpr = sweep_traffic_per_record() if a.workload == "plain" and not a.unsorted else None
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": (tpr * N) if tpr is not None else None, "kernel": "talp::sweep_kernel",
-            "kernel_ms": sweep_ms, "peak_source": f"{peak_kind} hbm_gbs"}
+    if a.unsorted:
+        n_dev = int(t.dev_off[-1])
+        sort_ms = prof["sort_ms"] / max(1, prof["sort_launches"])
+        achieved = BYTES_PER_RECORD * n_dev / (sort_ms / 1000.0) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None,
+                "kernel": "sort stage (run finding, talp::fms_kernel and its plan and fix-up kernels)",
+                "kernel_ms": sort_ms, "records_per_launch": n_dev,
+                "first_sweep_ms": sweep_ms, "peak_source": f"{peak_kind} hbm_gbs"}
+    else:
+        achieved = BYTES_PER_RECORD * N / (sweep_ms / 1000.0) / 1e9
+        tpr = sweep_traffic_per_record() if a.workload == "plain" else None
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": (tpr * N) if tpr is not None else None, "kernel": "talp::sweep_kernel",
+                "kernel_ms": sweep_ms, "peak_source": f"{peak_kind} hbm_gbs"}
 
     # ---- CPU oracle on a bounded sample (rank 0, N = 1 only)
     cpu = cpu_all = None

@@ -613,16 +613,20 @@ talp_gpu_status talp_gpu_memory(talp_gpu_ctx *ctx, size_t *held_bytes, size_t *b
  * Kernel timing for benchmarks and tracing (library service, no passage).
  * While enabled, every sweep
  * launch (the pass over the records: flattening, host sums, validation) is
- * bracketed by CUDA events on the ingest stream.  talp_gpu_profile_read
- * synchronises those events, returns the totals since the last read and
- * clears them.  kernel_launches counts every kernel the context launched
- * (enabled or not).
+ * bracketed by CUDA events on the ingest stream, and so is every sort stage
+ * (the kernels between the first sweep's fix-up and the re-sweep of an
+ * ingest without TALP_GPU_SORTED_BY_START: run finding, the fused
+ * merge-sweep, the radix passes).  talp_gpu_profile_read synchronises those
+ * events, returns the totals since the last read and clears them.
+ * kernel_launches counts every kernel the context launched (enabled or not).
  */
 typedef struct {
     uint64_t sweep_launches;
     uint64_t sweep_records;            /* records covered by those launches */
     double sweep_ms;                   /* summed event time of those launches */
     uint64_t kernel_launches;
+    uint64_t sort_launches;            /* sort stages timed */
+    double sort_ms;                    /* summed event time of those stages */
 } talp_gpu_profile_stats;
 
 talp_gpu_status talp_gpu_profile(talp_gpu_ctx *ctx, int enable);

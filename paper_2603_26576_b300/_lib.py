@@ -70,7 +70,8 @@ RATIO_FIELDS = ("host_pe", "host_mpi_pe", "host_mpi_lb", "host_mpi_ce", "host_oe
 
 class talp_gpu_profile_stats(ctypes.Structure):
     _fields_ = [("sweep_launches", ctypes.c_uint64), ("sweep_records", ctypes.c_uint64),
-                ("sweep_ms", ctypes.c_double), ("kernel_launches", ctypes.c_uint64)]
+                ("sweep_ms", ctypes.c_double), ("kernel_launches", ctypes.c_uint64),
+                ("sort_launches", ctypes.c_uint64), ("sort_ms", ctypes.c_double)]
 
 
 class talp_gpu_plan_stats(ctypes.Structure):
@@ -445,7 +446,8 @@ def talp_gpu_profile_read(ctx) -> dict:
     st = talp_gpu_profile_stats()
     _check(load_library().talp_gpu_profile_read(ctx, ctypes.byref(st)))
     return dict(sweep_launches=int(st.sweep_launches), sweep_records=int(st.sweep_records),
-                sweep_ms=float(st.sweep_ms), kernel_launches=int(st.kernel_launches))
+                sweep_ms=float(st.sweep_ms), kernel_launches=int(st.kernel_launches),
+                sort_launches=int(st.sort_launches), sort_ms=float(st.sort_ms))
 
 
 def talp_gpu_plan_create(ctx, batches, plan_flags=0):

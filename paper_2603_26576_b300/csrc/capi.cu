@@ -115,7 +115,7 @@ struct Layout {
     size_t up_bytes = 0;
     size_t off_wrec = 0, off_flags = 0, off_gst = 0, off_bk = 0, off_slist = 0, off_srb = 0, off_stb = 0;
     size_t off_smn = 0, off_smx = 0, off_hist = 0, off_offs = 0, off_rsegs = 0, off_rstart = 0, off_mout = 0;
-    size_t off_nruns = 0, off_runs = 0, off_fused = 0, off_known = 0, off_given = 0;
+    size_t off_nruns = 0, off_runs = 0, off_fused = 0, off_known = 0, off_given = 0, off_seen_n = 0, off_seen_pos = 0;
     uint64_t fms_samples = 0, fms_chunks = 0, fms_super = 0;   // table bounds of the fused merge-sweep
     size_t off_fS = 0, off_fsb = 0, off_fcb = 0, off_fpb = 0, off_fscb = 0, off_fsamp = 0, off_fsplit = 0,
            off_fseg = 0, off_fchunk = 0, off_fscagg = 0, off_ffix = 0;
@@ -159,6 +159,7 @@ struct talp_gpu_ctx {
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
     std::vector<uint64_t> ev_records;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> sort_ev_pending;
     uint64_t kernel_launches = 0;
     int64_t wait_limit = 4000000000LL;   // cycles (~2 s at 2 GHz)
     int dependents = 0;                  // live plans and servers on this context
@@ -417,7 +418,7 @@ talp_gpu_status size_ingest(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches
 
     for (size_t k = 0; k < nb; ++k)
         L.payload_words += 2ull * batches[k].n_ranks * batches[k].n_regions + L.mm[k] + sizeof(TraceDev) / 8;
-    L.n_jobs_max = 8 * nb + 2;   // <= 8 per trace + seg flags + status
+    L.n_jobs_max = 8 * nb + 3;   // <= 8 per trace + seg flags + status + run log
     L.off_segs = 0;
     L.off_start = align_up(L.off_segs + sizeof(SegDesc) * L.n_segs, 256);
     L.off_send = align_up(L.off_start + sizeof(uint64_t) * (L.n_segs + 1), 256);
@@ -454,7 +455,9 @@ talp_gpu_status size_ingest(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches
     L.off_fchunk = align_up(L.off_fseg + 4 * L.fms_chunks, 256);
     L.off_fscagg = align_up(L.off_fchunk + sizeof(FmsChunk) * L.fms_chunks, 256);
     L.off_ffix = align_up(L.off_fscagg + 16 * L.fms_super, 256);
-    L.off_rsegs = align_up(L.off_ffix + sizeof(FmsFix) * L.fms_chunks, 256);
+    L.off_seen_n = align_up(L.off_ffix + sizeof(FmsFix) * L.fms_chunks, 256);
+    L.off_seen_pos = align_up(L.off_seen_n + 4 * (L.sorting ? L.n_segs + 2 : 0), 256);
+    L.off_rsegs = align_up(L.off_seen_pos + 8 * kMaxRuns * (L.sorting ? L.n_segs : 0), 256);
     L.off_rstart = align_up(L.off_rsegs + sizeof(SegDesc) * (L.sorting ? L.n_dev_segs : 0), 256);
     L.off_rrend = align_up(L.off_rstart + 8 * (L.sorting ? L.n_dev_segs + 1 : 0), 256);
     L.off_mout = align_up(L.off_rrend + 8 * (L.sorting ? L.n_dev_segs + 1 : 0), 256);
@@ -670,6 +673,7 @@ talp_gpu_status fill_ingest(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches
     send[si] = pos;
     jobs[nj++] = FillJob{reinterpret_cast<int64_t*>(seg_flags), (L.n_segs + 2) / 2, 0, nullptr};
     jobs[nj++] = FillJob{reinterpret_cast<int64_t*>(gstatus), 1, 0, nullptr};
+    if (L.sorting) jobs[nj++] = FillJob{reinterpret_cast<int64_t*>(wsd + L.off_seen_n), (L.n_segs + 2) / 2, 0, nullptr};
     if (nj > L.n_jobs_max || pw > L.payload_words || si != L.n_segs || bk_used > L.n_backup_words || nf != L.n_fin)
         return fail(TALP_GPU_ECUDA, "internal: upload table overflow");
     L.nj = nj;
@@ -687,6 +691,8 @@ talp_gpu_status fill_ingest(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches
         sc.fused = reinterpret_cast<uint32_t*>(wsd + L.off_fused);
         sc.given = reinterpret_cast<uint32_t*>(wsd + L.off_given);
         sc.known = reinterpret_cast<const uint64_t* const*>(wsd + L.off_known);
+        sc.seen_n = reinterpret_cast<const uint32_t*>(wsd + L.off_seen_n);
+        sc.seen_pos = reinterpret_cast<const uint64_t*>(wsd + L.off_seen_pos);
         sc.fms_S = reinterpret_cast<uint32_t*>(wsd + L.off_fS);
         sc.fms_samp_base = reinterpret_cast<uint64_t*>(wsd + L.off_fsb);
         sc.fms_chunk_base = reinterpret_cast<uint64_t*>(wsd + L.off_fcb);
@@ -732,16 +738,20 @@ talp_gpu_status enqueue_ingest(talp_gpu_ctx* c, const Layout& L, const char* up,
             e1 = take_event(c);
             TALP_CUDA(cudaEventRecord(e0, stream));
         }
-        // with a sort stage to follow, segments found out of order are not computed any further
+        // with a sort stage to follow, segments found out of order are not
+        // computed any further, only scanned for where their order descends
+        const RunLog rl = L.sorting ? RunLog{reinterpret_cast<uint32_t*>(wsd + L.off_seen_n),
+                                             reinterpret_cast<uint64_t*>(wsd + L.off_seen_pos)}
+                                    : RunLog{nullptr, nullptr};
         TALP_CUDA(launch_sweep(L.shape, static_cast<int>(L.rmax), L.grid, dsegs, dstart, dsend,
                                static_cast<uint32_t>(L.n_segs), wrec, seg_flags, gstatus, c->wait_limit, L.sorting,
-                               stream));
+                               rl, stream));
         if (profile) {
             TALP_CUDA(cudaEventRecord(e1, stream));
             c->ev_pending.emplace_back(e0, e1);
             c->ev_records.push_back(L.n_records);
         }
-        TALP_CUDA(launch_fixup(dsegs, dstart, wrec, L.n_wrec, seg_flags, L.sorting, stream));
+        TALP_CUDA(launch_fixup(dsegs, dstart, wrec, L.n_wrec, seg_flags, L.sorting, rl, stream));
         nl += 2;
         if (L.sorting) {
             // a2: sort the device segments found out of order, re-sweep them
@@ -751,15 +761,25 @@ talp_gpu_status enqueue_ingest(talp_gpu_ctx* c, const Layout& L, const char* up,
             uint64_t* rrend = reinterpret_cast<uint64_t*>(wsd + L.off_rrend);
             const uint64_t gt = std::min<uint64_t>(L.sort_tiles, static_cast<uint64_t>(c->num_sms) * 8);
             const uint64_t gs = std::min<uint64_t>(L.sort_slots, static_cast<uint64_t>(c->num_sms) * 4);
+            cudaEvent_t s0 = nullptr, s1 = nullptr;
+            if (profile) {
+                s0 = take_event(c);
+                s1 = take_event(c);
+                TALP_CUDA(cudaEventRecord(s0, stream));
+            }
             TALP_CUDA(launch_sort_stage(dsegs, static_cast<uint32_t>(L.n_segs), static_cast<uint32_t>(L.n_dev_segs),
                                         seg_flags, sctl, rsegs, rstart, rrend,
                                         static_cast<int>(std::max<uint64_t>(gt, 1)),
                                         static_cast<int>(std::max<uint64_t>(gs, 1)), gstatus, c->wait_limit, stream));
+            if (profile) {
+                TALP_CUDA(cudaEventRecord(s1, stream));
+                c->sort_ev_pending.emplace_back(s0, s1);
+            }
             TALP_CUDA(launch_sweep(L.shape, static_cast<int>(L.rmax), L.full_grid, rsegs, rstart, rrend,
                                    static_cast<uint32_t>(L.n_dev_segs), wrec, seg_flags, gstatus, c->wait_limit,
-                                   false, stream));
+                                   false, RunLog{nullptr, nullptr}, stream));
             TALP_CUDA(launch_fixup(rsegs, rstart, wrec, static_cast<uint32_t>(L.full_grid) * L.warps, seg_flags,
-                                   false, stream));
+                                   false, RunLog{nullptr, nullptr}, stream));
             nl += 2 + 1 + 4 + 24 + 1 + 2;
         }
     }
@@ -882,6 +902,10 @@ talp_gpu_status talp_gpu_destroy(talp_gpu_ctx* c) {
     if (c->ev_raw) cudaEventDestroy(c->ev_raw);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (auto& pr : c->ev_pending) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    for (auto& pr : c->sort_ev_pending) {
         cudaEventDestroy(pr.first);
         cudaEventDestroy(pr.second);
     }
@@ -1730,6 +1754,17 @@ talp_gpu_status talp_gpu_profile_read(talp_gpu_ctx* c, talp_gpu_profile_stats* o
     }
     c->ev_pending.clear();
     c->ev_records.clear();
+    out->sort_launches = c->sort_ev_pending.size();
+    out->sort_ms = 0.0;
+    for (auto& pr : c->sort_ev_pending) {
+        TALP_CUDA(cudaEventSynchronize(pr.second));
+        float ms = 0.f;
+        TALP_CUDA(cudaEventElapsedTime(&ms, pr.first, pr.second));
+        out->sort_ms += ms;
+        c->ev_pool.push_back(pr.first);
+        c->ev_pool.push_back(pr.second);
+    }
+    c->sort_ev_pending.clear();
     out->kernel_launches = c->kernel_launches;
     return TALP_GPU_OK;
 }

@@ -130,7 +130,10 @@ struct SortCtl {
     const int64_t* const* restore;  // [segments] sums a flagged segment restarts from (null: zero)
     const uint64_t* const* known;   // [segments] runs already known (null: none): count r, then the
                                     // r + 1 run boundaries (kRunsStride entries; r < 2: unknown)
-    uint32_t* given;           // [slots] 1: k's runs came from `known` (the min/max pass skips k)
+    const uint32_t* seen_n;    // [segments] the first sweep's run log (null: none; see RunLog)
+    const uint64_t* seen_pos;  // [segments][kMaxRuns]
+    uint32_t* given;           // [slots] where k's runs came from (kRunsFound / kRunsKnown / kRunsSeen;
+                               // the min/max pass skips k unless kRunsFound)
     uint32_t* nruns;           // [slots] descents found in k (runs - 1)
     uint64_t* runs;            // [slots][kMaxRuns + 1] run boundaries of k (sorted by the merge plan)
     uint32_t* fused;           // [slots] 1: k is a few sorted runs, merged and swept in one pass
@@ -175,6 +178,39 @@ struct FmsFix {
 // (fms.cu) instead of being radix sorted and swept again.
 constexpr int kMaxRuns = 16;
 constexpr int kRunsStride = kMaxRuns + 2;   // entries of a known-runs record
+
+// Where each device segment's start order descends, as the first sweep (and
+// its fix-up, at slice boundaries) finds it: every position j >= 1 of the
+// ingest's records of the segment with s_j < s_(j-1).  At most kMaxRuns - 1
+// positions are kept (a segment of kMaxRuns runs); the count goes past that
+// only to tell the segment is more runs than that.
+struct RunLog {
+    uint32_t* n;     // [segments] descents counted (null: nothing logged)
+    uint64_t* pos;   // [segments][kMaxRuns] their positions, in no order
+};
+
+// SortCtl.given values: where a flagged segment's runs came from
+constexpr uint32_t kRunsFound = 0;   // the min/max pass of the sort stage
+constexpr uint32_t kRunsKnown = 1;   // the caller (a raw lane's streams): unchecked
+constexpr uint32_t kRunsSeen = 2;    // the first sweep's run log (every pair of records checked)
+
+// One warp (all lanes, any divergence resolved): log the descents flagged in
+// `desc` at positions j of segment seg.
+__device__ __forceinline__ void runlog_note(const RunLog& rl, uint32_t seg, bool desc, uint64_t j) {
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, desc);
+    if (!bal) return;
+    const int lane = threadIdx.x & 31;
+    uint32_t base = kMaxRuns;
+    if (lane == 0) {
+        const uint32_t seen = *static_cast<volatile uint32_t*>(&rl.n[seg]);
+        if (seen < static_cast<uint32_t>(kMaxRuns)) base = atomicAdd(&rl.n[seg], static_cast<uint32_t>(__popc(bal)));
+    }
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if (desc) {
+        const uint32_t slot = base + __popc(bal & ((1u << lane) - 1u));
+        if (slot < static_cast<uint32_t>(kMaxRuns - 1)) rl.pos[static_cast<uint64_t>(seg) * kMaxRuns + slot] = j;
+    }
+}
 // Records per chunk of the fused merge-sweep (at most).  A segment of r runs
 // is sampled every S = kFmsChunk / ((kFmsSpread + 1) r) records of each run
 // and cut at every (kFmsSpread r)-th sample in merged order; a chunk then

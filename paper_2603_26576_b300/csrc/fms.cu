@@ -61,7 +61,7 @@ struct ChunkMeta {
     uint64_t sc;                   // its super-chunk (main pass)
     uint32_t k, c, nr, n, valid;
     uint32_t first, last, seg_first;   // first / last chunk of its super-chunk; super-chunk 0 of its segment
-    uint32_t given;                // the segment's runs were given (not found by the min/max pass)
+    uint32_t given;                // the segment's runs came from the caller, unchecked (kRunsKnown)
     int64_t LK, LM;                // fix-up: the carry it was swept with
     int64_t TK, TM;                // fix-up: the true carry
     uint32_t roff[kMaxRuns + 1];   // staging row offset of each run's range (prefix)
@@ -706,7 +706,7 @@ __global__ void __launch_bounds__(kFmsThreads, 2)
                 nr = ctl->nruns[k] + 1;
                 split0 = ctl->fms_split_base[k];
                 cb = ctl->fms_chunk_base[k];
-                given = ctl->given[k];
+                given = ctl->given[k] == kRunsKnown;
             }
             const uint32_t c = static_cast<uint32_t>(g - cb);
             const uint64_t* row = ctl->fms_split + split0 + static_cast<uint64_t>(c) * nr;
@@ -869,7 +869,8 @@ __global__ void __launch_bounds__(kFmsThreads, 2)
                 const uint32_t r = static_cast<uint32_t>(de);
                 sh.key[0][i] = static_cast<uint32_t>(v.x - s0);   // used only when the span allows
                 sh.end32[i] = r;
-                // given runs: each must be in start order (found ones are by construction)
+                // runs from the caller: each must be in start order (runs found
+                // by the min/max pass or the sweep's run log are)
                 if (M.given && i > M.roff[q] && S.rows[i - 1].x > v.x) bad |= ST_UNSORTED;
                 if (tg < 32u) bK = umax(bK, r); else bM = umax(bM, r);
             }

@@ -30,10 +30,12 @@ int sweep_tile(int shape);
 // gap up to seg_start[s + 1] is the segment's share of fixed cost.
 cudaError_t launch_sweep(int shape, int rmax, int grid, const SegDesc* segs, const uint64_t* seg_start,
                          const uint64_t* seg_rend, uint32_t n_segs, WarpRec* wrec, uint32_t* seg_flags,
-                         uint32_t* gstatus, int64_t wait_limit, bool skip_sorted_out, cudaStream_t stream);
+                         uint32_t* gstatus, int64_t wait_limit, bool skip_sorted_out, RunLog rl,
+                         cudaStream_t stream);
 
+// rl: the run log the first sweep (skip_sorted_out) fills, or {null, null}
 cudaError_t launch_fixup(const SegDesc* segs, const uint64_t* seg_start, const WarpRec* wrec, uint32_t n_wrec,
-                         uint32_t* seg_flags, bool skip_resorted, cudaStream_t stream);
+                         uint32_t* seg_flags, bool skip_resorted, RunLog rl, cudaStream_t stream);
 
 cudaError_t launch_prep(const FillJob* jobs, uint32_t n_jobs, cudaStream_t stream);
 

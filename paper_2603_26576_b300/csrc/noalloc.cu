@@ -315,10 +315,11 @@ extern "C" talp_gpu_status talp_gpu_reduce_noalloc(const talp_gpu_trace_batch* b
         e = launch_sweep(shape, static_cast<int>(R), grid, reinterpret_cast<const SegDesc*>(S + kOffSegs),
                          reinterpret_cast<const uint64_t*>(S + kOffStart),
                          reinterpret_cast<const uint64_t*>(S + kOffEnd), n_segs, wrec, flags, gstatus, wait_limit,
-                         false, stream);
+                         false, RunLog{nullptr, nullptr}, stream);
     if (e == cudaSuccess)
         e = launch_fixup(reinterpret_cast<const SegDesc*>(S + kOffSegs),
-                         reinterpret_cast<const uint64_t*>(S + kOffStart), wrec, n_wrec, flags, false, stream);
+                         reinterpret_cast<const uint64_t*>(S + kOffStart), wrec, n_wrec, flags, false,
+                         RunLog{nullptr, nullptr}, stream);
     if (e == cudaSuccess) e = launch_finalize(reinterpret_cast<const FinalizeJob*>(S + kOffFin), R, stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out_host, mout, sizeof(MetricsOut) * R, cudaMemcpyDeviceToHost, stream);

@@ -18,7 +18,8 @@ namespace talp {
 __global__ void __launch_bounds__(256) fixup_kernel(const SegDesc* __restrict__ segs,
                                                     const uint64_t* __restrict__ seg_start,
                                                     const WarpRec* __restrict__ wrec, uint32_t n_wrec,
-                                                    uint32_t* __restrict__ seg_flags, bool skip_resorted) {
+                                                    uint32_t* __restrict__ seg_flags, bool skip_resorted,
+                                                    RunLog rl) {
     constexpr int RM = 8;
     const int lane = threadIdx.x & 31;
     const uint32_t w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -35,6 +36,11 @@ __global__ void __launch_bounds__(256) fixup_kernel(const SegDesc* __restrict__ 
     if (lane == 0 && d.se[2 * off0] < d.se[2 * (off0 - 1)]) {
         atomicOr(d.status, ST_UNSORTED);
         atomicOr(&seg_flags[seg], ST_UNSORTED);
+        // the one pair of records the sweep did not compare: into the run log
+        if (rl.n && (d.pad[0] & kSegSortable)) {
+            const uint32_t slot = atomicAdd(&rl.n[seg], 1u);
+            if (slot < static_cast<uint32_t>(kMaxRuns - 1)) rl.pos[static_cast<uint64_t>(seg) * kMaxRuns + slot] = off0;
+        }
     }
     // a segment already found out of order and allowed to sort is sorted and
     // swept again from its saved sums: correcting this pass is wasted work
@@ -131,11 +137,11 @@ __global__ void __launch_bounds__(256) fixup_kernel(const SegDesc* __restrict__ 
 }
 
 cudaError_t launch_fixup(const SegDesc* segs, const uint64_t* seg_start, const WarpRec* wrec, uint32_t n_wrec,
-                         uint32_t* seg_flags, bool skip_resorted, cudaStream_t stream) {
+                         uint32_t* seg_flags, bool skip_resorted, RunLog rl, cudaStream_t stream) {
     if (n_wrec == 0) return cudaSuccess;
     const int wpb = 8;
     const int grid = static_cast<int>((n_wrec + wpb - 1) / wpb);
-    fixup_kernel<<<grid, wpb * 32, 0, stream>>>(segs, seg_start, wrec, n_wrec, seg_flags, skip_resorted);
+    fixup_kernel<<<grid, wpb * 32, 0, stream>>>(segs, seg_start, wrec, n_wrec, seg_flags, skip_resorted, rl);
     return cudaGetLastError();
 }
 

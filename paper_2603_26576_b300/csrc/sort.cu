@@ -19,9 +19,11 @@
 //
 // A flagged segment that is only a few sorted runs laid end to end (records
 // grouped by stream, each stream in start order: the order per-stream
-// activity buffers deliver) is not sorted here: the min/max kernel records
-// where the start order descends, and a segment of at most kMaxRuns runs is
-// merged and swept in one pass by the fused merge-sweep (fms.cu).
+// activity buffers deliver) is not sorted here: a segment of at most
+// kMaxRuns runs is merged and swept in one pass by the fused merge-sweep
+// (fms.cu).  Where the start order descends comes from the first sweep's run
+// log (it compares every pair of neighbouring records anyway), from the
+// caller (a raw lane's streams), or else from the min/max kernel.
 #include "kernels.h"
 
 namespace talp {
@@ -126,7 +128,7 @@ __global__ void __launch_bounds__(1024) sort_plan_kernel(const SegDesc* __restri
             ctl->mx[k] = INT64_MIN;
             ctl->nruns[k] = 0;
             ctl->fused[k] = 0;
-            ctl->given[k] = 0;
+            ctl->given[k] = kRunsFound;
             const SegDesc& d = segs[s];
             // runs already known (a raw lane: its streams, one after another):
             // taken as they are, and the min/max pass leaves the segment alone
@@ -136,7 +138,18 @@ __global__ void __launch_bounds__(1024) sort_plan_kernel(const SegDesc* __restri
                 uint64_t* runs = ctl->runs + static_cast<uint64_t>(k) * (kMaxRuns + 1);
                 for (uint32_t q = 0; q <= r; ++q) runs[q] = kr[1 + q];
                 ctl->nruns[k] = r - 1;
-                ctl->given[k] = 1;
+                ctl->given[k] = kRunsKnown;
+            } else if (ctl->seen_n && !(d.pad[0] & kSegPresort)) {
+                // swept once already: its descents are in the run log, complete
+                // when there are few enough (the merge plan puts them in order)
+                const uint32_t c = ctl->seen_n[s];
+                if (c >= 1 && c <= static_cast<uint32_t>(kMaxRuns - 1)) {
+                    uint64_t* runs = ctl->runs + static_cast<uint64_t>(k) * (kMaxRuns + 1);
+                    const uint64_t* sp = ctl->seen_pos + static_cast<uint64_t>(s) * kMaxRuns;
+                    for (uint32_t q = 0; q < c; ++q) runs[1 + q] = sp[q];
+                    ctl->nruns[k] = c;
+                    ctl->given[k] = kRunsSeen;
+                }
             }
             // the re-sweep recomputes this ingest's part of the segment: its
             // sums restart from their value before the ingest
@@ -170,7 +183,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_minmax_kernel(const SegDesc
     const uint32_t ntile = static_cast<uint32_t>(ctl->ntile);
     for (uint32_t t = blockIdx.x; t < ntile; t += gridDim.x) {
         const uint32_t k = seg_of_tile(ctl, t);
-        if (ctl->given[k]) {   // runs known already (block-uniform)
+        if (ctl->given[k] != kRunsFound) {   // runs known already (block-uniform)
             t = skip_segment(ctl, k, t);
             continue;
         }

@@ -111,12 +111,42 @@ __device__ __forceinline__ bool walk_advance(Walk& w, uint32_t len, const uint64
 // them again from their saved sums, so a warp that finds such a segment out
 // of order lets the rest of its part of it stream past uncomputed.  Ingests
 // that assert start order launch the instantiation without it.
+// Run log of a tile with a descent (first sweep only): j0 = the segment
+// position of the lane's first record; last_s = the start before the tile.
+// From the lane's 32-bit offsets (the tile's fast path, its buffer already
+// handed back to the copy engine) ...
+template <int ITEMS>
+__device__ __forceinline__ void note_tile_regs(const RunLog& rl, uint32_t seg, uint64_t j0,
+                                               const uint32_t (&sr)[ITEMS], int cnt, int64_t s0, int64_t last_s) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t before = __shfl_up_sync(0xFFFFFFFFu, sr[ITEMS - 1], 1);
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        bool desc = false;
+        if (i < cnt) desc = i > 0 ? sr[i] < sr[i - 1] : (lane > 0 ? sr[0] < before : s0 < last_s);
+        runlog_note(rl, seg, desc && j0 + i > 0, j0 + i);
+    }
+}
+
+// ... or from the tile in shared memory
+template <int ITEMS>
+__device__ __forceinline__ void note_tile_smem(const RunLog& rl, uint32_t seg, uint64_t j0, const longlong2* sse,
+                                               int base, int cnt, int64_t last_s) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        bool desc = false;
+        if (i < cnt) desc = sse[base + i].x < ((i > 0 || lane > 0) ? sse[base + i - 1].x : last_s);
+        runlog_note(rl, seg, desc && j0 + i > 0, j0 + i);
+    }
+}
+
 template <int ITEMS, int WARPS, int STAGES, int RMAX, int MINB, bool SKIP>
 __global__ void __launch_bounds__(WARPS * 32, MINB)
     sweep_kernel(const SegDesc* __restrict__ segs, const uint64_t* __restrict__ seg_start,
                  const uint64_t* __restrict__ seg_rend, uint32_t n_segs,
                  WarpRec* __restrict__ wrec, uint32_t* __restrict__ seg_flags, uint32_t* __restrict__ gstatus,
-                 int64_t wait_limit) {
+                 int64_t wait_limit, RunLog rl) {
     using C = SweepCfg<ITEMS, WARPS, STAGES>;
     constexpr int TILE = C::TILE;
     extern __shared__ __align__(128) uint8_t smem[];
@@ -276,6 +306,17 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
         const int len = rem < static_cast<uint64_t>(TILE) ? static_cast<int>(rem) : TILE;
         if constexpr (SKIP) {
             if (skip_seg) {   // the rest of a segment that will be sorted and swept again
+                if (rl.n) {
+                    // only scanned for the run log, unless the segment has
+                    // too many runs for it already
+                    uint32_t many = 0;
+                    if (lane == 0) many = *static_cast<volatile uint32_t*>(&rl.n[cw.seg]) >= kMaxRuns;
+                    if (!__shfl_sync(0xFFFFFFFFu, many, 0)) {
+                        const int b0 = lane * ITEMS;
+                        note_tile_smem<ITEMS>(rl, cw.seg, off + b0, sse, b0, max(0, min(ITEMS, len - b0)), last_s);
+                    }
+                    last_s = sse[len - 1].x;
+                }
                 release(st);
                 ++n_consumed;
                 const bool seg_done = cw.pos + static_cast<uint64_t>(len) == cw.seg_end;
@@ -354,6 +395,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
                 if (full) dev_pass1<ITEMS, true>(sr, er, tg, cnt, aK, aM, okE, okS, okK);
                 else dev_pass1<ITEMS, false>(sr, er, tg, cnt, aK, aM, okE, okS, okK);
                 bad |= (okE ? 0u : ST_BAD_END) | (okK ? 0u : ST_BAD_KIND) | (okS ? 0u : ST_UNSORTED);
+                if constexpr (SKIP) {
+                    if (rl.n && d_sortable && __any_sync(0xFFFFFFFFu, (bad & ST_UNSORTED) != 0u))
+                        note_tile_regs<ITEMS>(rl, cw.seg, off + base, sr, cnt, s0, last_s);
+                }
                 uint32_t iK = aK, iM = aM;
 #pragma unroll
                 for (int dd = 1; dd < 32; dd <<= 1) {
@@ -510,6 +555,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
                 c2 = warp_sum64(c2);
                 if (lane / 3 == src / 3 && mine) acc += lchain == 0 ? c0 : (lchain == 1 ? c1 : c2);
             }
+            if constexpr (SKIP) {
+                if (rl.n && d_sortable && !d_host && __any_sync(0xFFFFFFFFu, (bad & ST_UNSORTED) != 0u))
+                    note_tile_smem<ITEMS>(rl, cw.seg, off + base, sse, base, cnt, last_s);
+            }
             release(st);
         }
         if constexpr (SKIP) {
@@ -592,7 +641,7 @@ template <int ITEMS, int WARPS, int STAGES, int RMAX>
 static cudaError_t launch_t(int grid, const SegDesc* segs, const uint64_t* seg_start, const uint64_t* seg_rend,
                             uint32_t n_segs,
                             WarpRec* wrec, uint32_t* seg_flags, uint32_t* gstatus, int64_t wait_limit,
-                            bool skip_sorted_out, cudaStream_t stream) {
+                            bool skip_sorted_out, RunLog rl, cudaStream_t stream) {
     using C = SweepCfg<ITEMS, WARPS, STAGES>;
     constexpr int MINB = WARPS == 8 ? 2 : 3;
     auto k = skip_sorted_out ? sweep_kernel<ITEMS, WARPS, STAGES, RMAX, MINB, true>
@@ -600,7 +649,7 @@ static cudaError_t launch_t(int grid, const SegDesc* segs, const uint64_t* seg_s
     cudaError_t e = ensure_smem_attr<ITEMS, WARPS, STAGES, RMAX>();
     if (e != cudaSuccess) return e;
     k<<<grid, WARPS * 32, C::SMEM, stream>>>(segs, seg_start, seg_rend, n_segs, wrec, seg_flags, gstatus,
-                                              wait_limit);
+                                              wait_limit, rl);
     return cudaGetLastError();
 }
 
@@ -626,7 +675,7 @@ static int occupancy_t() {
 
 #define TALP_LAUNCH(I, W, S, RM) \
     launch_t<I, W, S, RM>(grid, segs, seg_start, seg_rend, n_segs, wrec, seg_flags, gstatus, wait_limit, \
-                          skip_sorted_out, stream)
+                          skip_sorted_out, rl, stream)
 #define TALP_OCC(I, W, S, RM) occupancy_t<I, W, S, RM>()
 
 // The region count no longer shapes the kernel's registers (each lane owns
@@ -634,7 +683,8 @@ static int occupancy_t() {
 // every R <= 8.
 cudaError_t launch_sweep(int shape, int rmax, int grid, const SegDesc* segs, const uint64_t* seg_start,
                          const uint64_t* seg_rend, uint32_t n_segs, WarpRec* wrec, uint32_t* seg_flags,
-                         uint32_t* gstatus, int64_t wait_limit, bool skip_sorted_out, cudaStream_t stream) {
+                         uint32_t* gstatus, int64_t wait_limit, bool skip_sorted_out, RunLog rl,
+                         cudaStream_t stream) {
     (void)rmax;
     TALP_SHAPE_SWITCH(shape, 8, TALP_LAUNCH)
     return cudaErrorInvalidValue;

@@ -147,6 +147,51 @@ def test_unsorted_with_many_warps_per_segment():
         c.close()
 
 
+def _runs_of_sizes(trace, sizes, seed):
+    """The trace's one device segment dealt into sorted runs of the given
+    sizes (records drawn at random for each run, each run in start order),
+    laid end to end: the start order descends only where a run begins."""
+    rng = np.random.default_rng(seed)
+    n = int(trace.dev_off[1])
+    assert sum(sizes) == n
+    grp = rng.permutation(np.repeat(np.arange(len(sizes)), sizes))
+    order = np.argsort(grp, kind="stable")
+    se, tag = trace.dev_se.copy(), trace.dev_tag.copy()
+    se[:n], tag[:n] = se[:n][order], tag[:n][order]
+    return tg._with_dev(trace, se, tag)
+
+
+@pytest.mark.parametrize("shape", [0, 1, 2, 3])
+def test_run_boundaries_at_tile_and_slice_edges(shape):
+    """The first sweep logs where each device's start order descends (inside
+    a tile, at a tile's first record, at a warp slice's first record through
+    the fix-up, in tiles it only scans after the segment is found out of
+    order); with one tile per warp every tile edge is a slice edge.  Runs
+    that begin exactly there, one-record runs, and 15 / 16 / 17 descents
+    (16 runs is the most the fused merge-sweep takes) all equal the oracle."""
+    tile = 32 * (9, 7, 11, 13)[shape]     # records per tile of each sweep shape
+    c = make_ctx(shape=shape, tiles_per_warp=1)
+    try:
+        for k in (2, 15, 16, 17):
+            for variant in range(3):
+                if variant == 0:     # every run a whole number of tiles
+                    sizes = [tile * (1 + (i % 3)) for i in range(k)]
+                elif variant == 1:   # runs one record off a tile edge, and one-record runs
+                    sizes = [tile + (1 if i % 2 else -1) if i % 4 else 1 for i in range(k)]
+                else:                # runs of random lengths
+                    sizes = list(np.random.default_rng(k).integers(1, 3 * tile, k))
+                n = int(sum(sizes))
+                base = tg.random_trace(100 * k + variant, trace_id=k * 10 + variant, n_ranks=1, devices_per_rank=1,
+                                       dev_events=n, host_events=50, n_regions=3)
+                assert int(base.dev_off[1]) == n
+                t = _runs_of_sizes(base, sizes, seed=k + variant)
+                c.ingest([t])
+                assert_trace_equal(c, t, ("run edges", shape, k, variant))
+        c.reset()
+    finally:
+        c.close()
+
+
 def test_not_sorted_hint():
     """TALP_GPU_NOT_SORTED sends every device to the sort stage without a first
     sweep: records grouped by stream (merge path), shuffled (radix path),
