@@ -469,10 +469,11 @@ talp_gpu_status talp_gpu_concurrency(talp_gpu_ctx *ctx, const talp_gpu_trace_bat
  *             device addresses for the plan's lifetime; their contents may
  *             change between launches (shapes and offsets may not).
  * plan_flags: TALP_GPU_PLAN_AUTOTUNE times every sweep shape (records per
- *             lane, warps, pipeline stages) and tiles-per-warp setting on
- *             these traces and keeps the fastest; the choice is also
- *             remembered by the context for later ingests of the same size
- *             class.
+ *             lane, warps, pipeline stages) x per-segment cost x work split
+ *             (one fixed slice of the records per warp, or 16 slices per
+ *             warp handed to the warps as they come free) on these traces
+ *             and keeps the fastest; the choice is also remembered by the
+ *             context for later ingests of the same size class.
  * Errors: EINVAL, ENOMEM (admission: plan workspace + new traces), EBUSY
  * (a trace id in use by a plan with another shape), ECUDA.
  * A trace used by a plan cannot be reset or re-shaped (EBUSY) until the plan
@@ -492,7 +493,8 @@ typedef struct {
     uint32_t sweep_stages;             /*   TMA pipeline stages per warp */
     uint32_t tiles_per_warp;           /*   minimum tiles per warp (grid sizing) */
     uint32_t sweep_grid;               /*   CTAs of the sweep launch */
-    uint32_t reserved;
+    uint32_t slices_per_warp;          /*   0: one fixed slice of the records per warp; k: k slices per
+                                        *   warp handed to the warps as they come free */
 } talp_gpu_plan_stats;
 
 talp_gpu_status talp_gpu_plan_create(talp_gpu_ctx *ctx, const talp_gpu_trace_batch *batches, size_t n,

@@ -78,7 +78,7 @@ class talp_gpu_plan_stats(ctypes.Structure):
     _fields_ = [("n_metrics", ctypes.c_uint64), ("records", ctypes.c_uint64), ("segments", ctypes.c_uint64),
                 ("kernels_per_launch", ctypes.c_uint32), ("sweep_items", ctypes.c_uint32),
                 ("sweep_warps", ctypes.c_uint32), ("sweep_stages", ctypes.c_uint32),
-                ("tiles_per_warp", ctypes.c_uint32), ("sweep_grid", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("tiles_per_warp", ctypes.c_uint32), ("sweep_grid", ctypes.c_uint32), ("slices_per_warp", ctypes.c_uint32)]
 
 
 class talp_gpu_server_config(ctypes.Structure):

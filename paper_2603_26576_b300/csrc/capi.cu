@@ -99,10 +99,11 @@ struct Tuning {
     int shape = kDefaultSweepShape;
     int tpw = 4;              // minimum tiles per warp (grid sizing of small ingests)
     uint64_t seg_cost = 0;    // phantom records per segment (balances segment switches)
+    int spw = 0;              // slices per warp handed out by a ticket (0: one fixed slice per warp)
 };
 
 struct Layout {
-    int shape = 0, warps = 0, tile = 0, grid = 0, full_grid = 0, tpw = 4;
+    int shape = 0, warps = 0, tile = 0, grid = 0, full_grid = 0, tpw = 4, spw = 0;
     uint64_t seg_cost = 0;
     uint32_t rmax = 1, n_wrec = 0, n_wrec_cap = 0;
     uint64_t n_segs = 0, n_records = 0, n_dev_segs = 0;
@@ -413,8 +414,9 @@ talp_gpu_status size_ingest(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches
     want = std::min(std::max<uint64_t>(want, 1), max_warps);
     L.grid = static_cast<int>((want + L.warps - 1) / L.warps);
     L.full_grid = static_cast<int>(max_warps / L.warps);
-    L.n_wrec = static_cast<uint32_t>(L.grid) * L.warps;
-    L.n_wrec_cap = static_cast<uint32_t>(L.sorting ? std::max(L.grid, L.full_grid) : L.grid) * L.warps;
+    L.spw = tu.spw;
+    L.n_wrec = static_cast<uint32_t>(L.grid) * L.warps * static_cast<uint32_t>(L.spw > 0 ? L.spw : 1);
+    L.n_wrec_cap = std::max<uint32_t>(L.n_wrec, L.sorting ? static_cast<uint32_t>(L.full_grid) * L.warps : 0u);
 
     for (size_t k = 0; k < nb; ++k)
         L.payload_words += 2ull * batches[k].n_ranks * batches[k].n_regions + L.mm[k] + sizeof(TraceDev) / 8;
@@ -672,7 +674,7 @@ talp_gpu_status fill_ingest(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches
     sstart[si] = pos;
     send[si] = pos;
     jobs[nj++] = FillJob{reinterpret_cast<int64_t*>(seg_flags), (L.n_segs + 2) / 2, 0, nullptr};
-    jobs[nj++] = FillJob{reinterpret_cast<int64_t*>(gstatus), 1, 0, nullptr};
+    jobs[nj++] = FillJob{reinterpret_cast<int64_t*>(gstatus), 2, 0, nullptr};   // status, pad, slice ticket
     if (L.sorting) jobs[nj++] = FillJob{reinterpret_cast<int64_t*>(wsd + L.off_seen_n), (L.n_segs + 2) / 2, 0, nullptr};
     if (nj > L.n_jobs_max || pw > L.payload_words || si != L.n_segs || bk_used > L.n_backup_words || nf != L.n_fin)
         return fail(TALP_GPU_ECUDA, "internal: upload table overflow");
@@ -745,7 +747,7 @@ talp_gpu_status enqueue_ingest(talp_gpu_ctx* c, const Layout& L, const char* up,
                                     : RunLog{nullptr, nullptr};
         TALP_CUDA(launch_sweep(L.shape, static_cast<int>(L.rmax), L.grid, dsegs, dstart, dsend,
                                static_cast<uint32_t>(L.n_segs), wrec, seg_flags, gstatus, c->wait_limit, L.sorting,
-                               rl, stream));
+                               rl, L.spw > 0 ? L.n_wrec : 0u, L.spw > 0 ? gstatus + 2 : nullptr, stream));
         if (profile) {
             TALP_CUDA(cudaEventRecord(e1, stream));
             c->ev_pending.emplace_back(e0, e1);
@@ -777,7 +779,7 @@ talp_gpu_status enqueue_ingest(talp_gpu_ctx* c, const Layout& L, const char* up,
             }
             TALP_CUDA(launch_sweep(L.shape, static_cast<int>(L.rmax), L.full_grid, rsegs, rstart, rrend,
                                    static_cast<uint32_t>(L.n_dev_segs), wrec, seg_flags, gstatus, c->wait_limit,
-                                   false, RunLog{nullptr, nullptr}, stream));
+                                   false, RunLog{nullptr, nullptr}, 0u, nullptr, stream));
             TALP_CUDA(launch_fixup(rsegs, rstart, wrec, static_cast<uint32_t>(L.full_grid) * L.warps, seg_flags,
                                    false, RunLog{nullptr, nullptr}, stream));
             nl += 2 + 1 + 4 + 24 + 1 + 2;
@@ -875,6 +877,10 @@ talp_gpu_status talp_gpu_create(talp_gpu_ctx** out, int device, size_t hbm_budge
     }
     if (const char* s = getenv("TALP_GPU_SEG_COST")) {
         c->defaults.seg_cost = strtoull(s, nullptr, 10);
+        c->shape_forced = true;
+    }
+    if (const char* s = getenv("TALP_GPU_SLICES_PER_WARP")) {
+        c->defaults.spw = atoi(s) > 0 ? atoi(s) : 0;
         c->shape_forced = true;
     }
     *out = c;
@@ -1806,17 +1812,20 @@ talp_gpu_status talp_gpu_plan_create(talp_gpu_ctx* c, const talp_gpu_trace_batch
     cudaStream_t s = c->cap_stream;
 
     // candidate tunings (all sized first, so admission sees the largest):
-    // every sweep shape x segment costs {1/4, 1, 4} of the default
+    // every sweep shape x segment costs {1/4, 1, 4} of the default x fixed
+    // slices or 16 slices per warp handed out as warps come free
     std::vector<Tuning> cand;
     const Tuning base = pick_tuning(c, batches, nb);
     if ((plan_flags & TALP_GPU_PLAN_AUTOTUNE) && !c->shape_forced) {
         for (int sh = 0; sh < kNumSweepShapes; ++sh)
-            for (uint64_t mul : {1ull, 4ull, 16ull}) {
-                Tuning t = base;
-                t.shape = sh;
-                t.seg_cost = base.seg_cost * mul / 4;
-                cand.push_back(t);
-            }
+            for (uint64_t mul : {1ull, 4ull, 16ull})
+                for (int spw : {0, 16}) {
+                    Tuning t = base;
+                    t.shape = sh;
+                    t.seg_cost = base.seg_cost * mul / 4;
+                    t.spw = spw;
+                    cand.push_back(t);
+                }
     } else {
         cand.push_back(base);
     }
@@ -1950,7 +1959,7 @@ talp_gpu_status talp_gpu_plan_info(talp_gpu_plan* p, talp_gpu_plan_stats* out) {
     out->sweep_stages = kSweepShapes[p->L.shape].stages;
     out->tiles_per_warp = static_cast<uint32_t>(p->L.tpw);
     out->sweep_grid = static_cast<uint32_t>(p->L.grid);
-    out->reserved = 0;
+    out->slices_per_warp = static_cast<uint32_t>(p->L.spw);
     return TALP_GPU_OK;
 }
 

@@ -28,10 +28,13 @@ int sweep_tile(int shape);
 // seg_start[s]: virtual start of segment s (n_segs + 1 entries, the last the
 // total); seg_rend[s]: virtual end of its records (start + records).  The
 // gap up to seg_start[s + 1] is the segment's share of fixed cost.
+// ticket null: one slice of the virtual array per warp (wrec: grid * warps
+// records); else n_slices slices handed out through *ticket, which must be
+// 0 at launch (wrec: n_slices records).
 cudaError_t launch_sweep(int shape, int rmax, int grid, const SegDesc* segs, const uint64_t* seg_start,
                          const uint64_t* seg_rend, uint32_t n_segs, WarpRec* wrec, uint32_t* seg_flags,
                          uint32_t* gstatus, int64_t wait_limit, bool skip_sorted_out, RunLog rl,
-                         cudaStream_t stream);
+                         uint32_t n_slices, uint32_t* ticket, cudaStream_t stream);
 
 // rl: the run log the first sweep (skip_sorted_out) fills, or {null, null}
 cudaError_t launch_fixup(const SegDesc* segs, const uint64_t* seg_start, const WarpRec* wrec, uint32_t n_wrec,

@@ -315,7 +315,7 @@ extern "C" talp_gpu_status talp_gpu_reduce_noalloc(const talp_gpu_trace_batch* b
         e = launch_sweep(shape, static_cast<int>(R), grid, reinterpret_cast<const SegDesc*>(S + kOffSegs),
                          reinterpret_cast<const uint64_t*>(S + kOffStart),
                          reinterpret_cast<const uint64_t*>(S + kOffEnd), n_segs, wrec, flags, gstatus, wait_limit,
-                         false, RunLog{nullptr, nullptr}, stream);
+                         false, RunLog{nullptr, nullptr}, 0u, nullptr, stream);
     if (e == cudaSuccess)
         e = launch_fixup(reinterpret_cast<const SegDesc*>(S + kOffSegs),
                          reinterpret_cast<const uint64_t*>(S + kOffStart), wrec, n_wrec, flags, false,

@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     sweep_kernel(const SegDesc* __restrict__ segs, const uint64_t* __restrict__ seg_start,
                  const uint64_t* __restrict__ seg_rend, uint32_t n_segs,
                  WarpRec* __restrict__ wrec, uint32_t* __restrict__ seg_flags, uint32_t* __restrict__ gstatus,
-                 int64_t wait_limit, RunLog rl) {
+                 int64_t wait_limit, RunLog rl, uint32_t n_chunks, uint32_t* __restrict__ ticket) {
     using C = SweepCfg<ITEMS, WARPS, STAGES>;
     constexpr int TILE = C::TILE;
     extern __shared__ __align__(128) uint8_t smem[];
@@ -158,8 +158,44 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     const uint64_t GW = static_cast<uint64_t>(gridDim.x) * WARPS;
     const uint64_t gw = static_cast<uint64_t>(blockIdx.x) * WARPS + wid;
     const uint64_t N = seg_start[n_segs];
-    const uint64_t r0 = (N * gw) / GW;
-    const uint64_t r1 = (N * (gw + 1)) / GW;
+    // Slices of the virtual array: with a ticket, n_chunks equal slices
+    // handed to the warps as they come free (so that warps whose slices run
+    // slow, e.g. many short segments cut by window boundaries, take fewer);
+    // without, one slice per warp.  wrec has one record per slice.
+    const uint64_t NCH = ticket ? n_chunks : GW;
+    auto next_slice = [&]() -> uint64_t {
+        uint32_t t = 0;
+        if (lane == 0) t = atomicAdd(ticket, 1u);
+        return __shfl_sync(0xFFFFFFFFu, t, 0);
+    };
+    auto empty_rec = [&](uint64_t c) {
+        if (lane == 0) {
+            WarpRec rec;
+            rec.head_pos = (N * c) / NCH;
+            rec.head_end = rec.head_pos;
+            rec.head_seg = NONE;
+            rec.tail_seg = NONE;
+            rec.head_K = rec.head_M = rec.tail_K = rec.tail_M = NEG_INF;
+            wrec[c] = rec;
+        }
+    };
+
+    if (lane == 0) {
+#pragma unroll
+        for (int st = 0; st < STAGES; ++st) mbar_init(&bars[st], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+
+    // copies issued and tiles consumed over all of the warp's slices (the
+    // ring's stage and phase follow from them)
+    uint32_t n_issued = 0, n_consumed = 0;
+    bool timed_out = false;
+    uint32_t* d_status = nullptr;
+    uint64_t chunk = ticket ? next_slice() : gw;
+    for (; chunk < NCH; chunk = ticket ? next_slice() : NCH) {
+    const uint64_t r0 = (N * chunk) / NCH;
+    const uint64_t r1 = (N * (chunk + 1)) / NCH;
 
     // segment containing r0: the last index whose start is <= r0
     uint32_t lo = 0, hi = n_segs;
@@ -171,29 +207,12 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     cw.pos = r0;
     cw.seg = lo;
     if (r0 >= r1 || !walk_enter(cw, seg_start, seg_rend, n_segs, r1)) {
-        // the slice holds no record (empty or phantom positions only)
-        if (lane == 0) {
-            WarpRec rec;
-            rec.head_pos = r0;
-            rec.head_end = r0;
-            rec.head_seg = NONE;
-            rec.tail_seg = NONE;
-            rec.head_K = rec.head_M = rec.tail_K = rec.tail_M = NEG_INF;
-            wrec[gw] = rec;
-        }
-        return;
+        empty_rec(chunk);   // the slice holds no record (empty or phantom positions only)
+        continue;
     }
-
-    if (lane == 0) {
-#pragma unroll
-        for (int st = 0; st < STAGES; ++st) mbar_init(&bars[st], 1);
-        fence_mbar_init();
-    }
-    __syncwarp();
 
     // ---- producer (lane 0): its own walk over the same tile sequence
     Walk iw = cw;
-    uint32_t n_issued = 0;
     bool iw_done = false;
     uint32_t iw_cached = NONE;
     const int64_t* iw_se = nullptr;
@@ -225,14 +244,14 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     };
 
     if (lane == 0) {
-        for (int st = 0; st < STAGES && !iw_done; ++st) issue(st);
+        for (int st = 0; st < STAGES && !iw_done; ++st) issue(static_cast<int>(n_issued % STAGES));
     }
 
     // ---- consumers (all lanes): the same walk
     if (lane == 0) {
-        wrec[gw].head_pos = cw.pos;
-        wrec[gw].head_seg = cw.seg;
-        wrec[gw].head_end = cw.seg_end;
+        wrec[chunk].head_pos = cw.pos;
+        wrec[chunk].head_seg = cw.seg;
+        wrec[chunk].head_end = cw.seg_end;
     }
     bool first_portion = true;
 
@@ -240,7 +259,6 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     const uint8_t* d_tag = nullptr;
     uintptr_t d_lim = 0;
     int64_t* d_sums = nullptr;
-    uint32_t* d_status = nullptr;
     int64_t* d_cout = nullptr;
     int d_R = 0;
     bool d_host = false;
@@ -251,8 +269,6 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     bool d_sortable = false;  // SKIP: the segment may be sorted and swept again
     bool skip_seg = false;    // SKIP, warp-uniform: this warp found it out of order
     bool portion_open = false;
-    uint32_t n_consumed = 0;
-    bool timed_out = false;
     const int lchain = lane % 3;
 
     auto release = [&](int st) {
@@ -329,7 +345,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
                             atomicOr(d_status, bits);
                             atomicOr(&seg_flags[seg_now], bits);
                         }
-                        if (!more) wrec[gw].tail_seg = seg_now;
+                        if (!more) wrec[chunk].tail_seg = seg_now;
                     }
                     first_portion = false;
                     portion_open = false;
@@ -587,13 +603,13 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
                     atomic_max64(&d_cout[2], last_s);
                 }
                 if (first_portion) {
-                    wrec[gw].head_K = carryK;
-                    wrec[gw].head_M = carryM;
+                    wrec[chunk].head_K = carryK;
+                    wrec[chunk].head_M = carryM;
                 }
                 if (slice_done) {
-                    wrec[gw].tail_seg = seg_now;
-                    wrec[gw].tail_K = carryK;
-                    wrec[gw].tail_M = carryM;
+                    wrec[chunk].tail_seg = seg_now;
+                    wrec[chunk].tail_K = carryK;
+                    wrec[chunk].tail_M = carryM;
                 }
             }
             first_portion = false;
@@ -601,6 +617,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
         }
         if (slice_done) break;
     }
+    if (timed_out) break;
+    }   // slices
 
     if (timed_out) {
         if (lane == 0) {
@@ -609,9 +627,12 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
             // let the copies still in flight land before the CTA's shared memory goes away
             for (uint32_t t = n_consumed; t < n_issued; ++t)
                 (void)mbar_wait_bounded(&bars[t % STAGES], (t / STAGES) & 1u, kDrainWaitCycles);
-            wrec[gw].head_seg = NONE;
-            wrec[gw].tail_seg = NONE;
+            wrec[chunk].head_seg = NONE;
+            wrec[chunk].tail_seg = NONE;
         }
+        // every slice's record is written, swept or not (the fix-up reads them all)
+        if (ticket)
+            for (chunk = next_slice(); chunk < NCH; chunk = next_slice()) empty_rec(chunk);
     }
 }
 
@@ -641,7 +662,8 @@ template <int ITEMS, int WARPS, int STAGES, int RMAX>
 static cudaError_t launch_t(int grid, const SegDesc* segs, const uint64_t* seg_start, const uint64_t* seg_rend,
                             uint32_t n_segs,
                             WarpRec* wrec, uint32_t* seg_flags, uint32_t* gstatus, int64_t wait_limit,
-                            bool skip_sorted_out, RunLog rl, cudaStream_t stream) {
+                            bool skip_sorted_out, RunLog rl, uint32_t n_slices, uint32_t* ticket,
+                            cudaStream_t stream) {
     using C = SweepCfg<ITEMS, WARPS, STAGES>;
     constexpr int MINB = WARPS == 8 ? 2 : 3;
     auto k = skip_sorted_out ? sweep_kernel<ITEMS, WARPS, STAGES, RMAX, MINB, true>
@@ -649,7 +671,7 @@ static cudaError_t launch_t(int grid, const SegDesc* segs, const uint64_t* seg_s
     cudaError_t e = ensure_smem_attr<ITEMS, WARPS, STAGES, RMAX>();
     if (e != cudaSuccess) return e;
     k<<<grid, WARPS * 32, C::SMEM, stream>>>(segs, seg_start, seg_rend, n_segs, wrec, seg_flags, gstatus,
-                                              wait_limit, rl);
+                                              wait_limit, rl, n_slices, ticket);
     return cudaGetLastError();
 }
 
@@ -675,7 +697,7 @@ static int occupancy_t() {
 
 #define TALP_LAUNCH(I, W, S, RM) \
     launch_t<I, W, S, RM>(grid, segs, seg_start, seg_rend, n_segs, wrec, seg_flags, gstatus, wait_limit, \
-                          skip_sorted_out, rl, stream)
+                          skip_sorted_out, rl, n_slices, ticket, stream)
 #define TALP_OCC(I, W, S, RM) occupancy_t<I, W, S, RM>()
 
 // The region count no longer shapes the kernel's registers (each lane owns
@@ -684,7 +706,7 @@ static int occupancy_t() {
 cudaError_t launch_sweep(int shape, int rmax, int grid, const SegDesc* segs, const uint64_t* seg_start,
                          const uint64_t* seg_rend, uint32_t n_segs, WarpRec* wrec, uint32_t* seg_flags,
                          uint32_t* gstatus, int64_t wait_limit, bool skip_sorted_out, RunLog rl,
-                         cudaStream_t stream) {
+                         uint32_t n_slices, uint32_t* ticket, cudaStream_t stream) {
     (void)rmax;
     TALP_SHAPE_SWITCH(shape, 8, TALP_LAUNCH)
     return cudaErrorInvalidValue;
