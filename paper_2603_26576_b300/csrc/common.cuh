@@ -155,7 +155,7 @@ struct SortCtl {
     uint32_t fms_ticket;       // next super-chunk to hand out
     uint32_t fms_nfix;         // fix-up jobs
     uint32_t fms_fix_ticket;   // next fix-up job to hand out
-    uint32_t pad2;
+    uint32_t n_find;           // flagged segments whose runs the min/max pass must find
 };
 
 // Per chunk of the fused merge-sweep: the largest kernel / memory end of its

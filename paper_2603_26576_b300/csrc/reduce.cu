@@ -157,14 +157,17 @@ __global__ void __launch_bounds__(256) prep_kernel(const FillJob* __restrict__ j
 
 cudaError_t launch_prep(const FillJob* jobs, uint32_t n_jobs, cudaStream_t stream) {
     if (n_jobs == 0) return cudaSuccess;
-    dim3 grid(8, n_jobs < 65535 ? n_jobs : 65535);
+    // a few large jobs (one trace) get 8 CTAs each; many small ones (a
+    // batch of traces) one, so that the launch is not thousands of CTAs with
+    // nothing to do
+    dim3 grid(n_jobs >= 1024 ? 1 : 8, n_jobs < 65535 ? n_jobs : 65535);
     prep_kernel<<<grid, 256, 0, stream>>>(jobs, n_jobs);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- finalize
 //
-// One CTA per (trace, region): reduce the per-rank host sums and per-device
+// One warp per (trace, region): reduce the per-rank host sums and per-device
 // unions into E and the sums/maxima, then form the nine ratios in FP64 with
 // the fixed order num / (k * den) (forms with n or m) or num / den, round to
 // nearest, no contraction: Eqs. 6-8 (host tree) and 9-12 (device tree).
@@ -220,18 +223,24 @@ __device__ __forceinline__ T block_reduce(T v, Op op, T* sh) {
     return r;
 }
 
-__global__ void __launch_bounds__(256) finalize_kernel(const FinalizeJob* __restrict__ jobs) {
-    __shared__ long long sh[32];
-    const FinalizeJob job = jobs[blockIdx.x];
+// One warp per (trace, region) job, 8 jobs per CTA: the unit sums of the
+// job are read once and reduced by warp shuffles (integer sums and maxima,
+// so the order of the reduction does not matter).
+constexpr int kFinWarps = 8;
+__global__ void __launch_bounds__(32 * kFinWarps) finalize_kernel(const FinalizeJob* __restrict__ jobs,
+                                                                  uint32_t n_jobs) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t jx = blockIdx.x * kFinWarps + (threadIdx.x >> 5);
+    if (jx >= n_jobs) return;
+    const FinalizeJob job = jobs[jx];
     const TraceDev t = *job.t;
     const uint32_t r = job.region;
     const uint32_t R = t.R;
-    auto add = [](long long a, long long b) { return a + b; };
     auto mx = [](long long a, long long b) { return a > b ? a : b; };
-    auto bor = [](long long a, long long b) { return a | b; };
 
-    long long E = 0, sU = 0, sW = 0, sP = 0, maxUW = 0, not_tiled = 0;
-    for (uint32_t i = threadIdx.x; i < t.n; i += blockDim.x) {
+    long long E = 0, sU = 0, sW = 0, sP = 0, maxUW = 0;
+    uint32_t not_tiled = 0;
+    for (uint32_t i = lane; i < t.n; i += 32) {
         const int64_t* h = t.hsum + (static_cast<uint64_t>(i) * R + r) * 3;
         const int64_t U = h[0], W = h[1], P = h[2];
         const int64_t* wv = t.hwin + (static_cast<uint64_t>(i) * R + r) * 2;
@@ -243,7 +252,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(const FinalizeJob* __rest
         if (U + W + P != wv[1] - wv[0]) not_tiled = 1;
     }
     long long sK = 0, maxK = 0, maxB = 0, sM = 0, sIdle = 0, sHid = 0;
-    for (uint32_t g = threadIdx.x; g < t.m; g += blockDim.x) {
+    for (uint32_t g = lane; g < t.m; g += 32) {
         const int64_t* u = t.dsum + (static_cast<uint64_t>(g) * R + r) * 3;
         const int64_t K = u[0], UM = u[1], B = u[2];
         const int64_t DM = B - K;
@@ -255,19 +264,19 @@ __global__ void __launch_bounds__(256) finalize_kernel(const FinalizeJob* __rest
         sIdle += (wv[1] - wv[0]) - B;
         sHid += K + UM - B;
     }
-    E = block_reduce<long long>(E, mx, sh);
-    sU = block_reduce<long long>(sU, add, sh);
-    sW = block_reduce<long long>(sW, add, sh);
-    sP = block_reduce<long long>(sP, add, sh);
-    maxUW = block_reduce<long long>(maxUW, mx, sh);
-    not_tiled = block_reduce<long long>(not_tiled, bor, sh);
-    sK = block_reduce<long long>(sK, add, sh);
-    maxK = block_reduce<long long>(maxK, mx, sh);
-    maxB = block_reduce<long long>(maxB, mx, sh);
-    sM = block_reduce<long long>(sM, add, sh);
-    sIdle = block_reduce<long long>(sIdle, add, sh);
-    sHid = block_reduce<long long>(sHid, add, sh);
-    if (threadIdx.x != 0) return;
+    E = warp_max64(E);
+    sU = warp_sum64(sU);
+    sW = warp_sum64(sW);
+    sP = warp_sum64(sP);
+    maxUW = warp_max64(maxUW);
+    not_tiled = __reduce_or_sync(0xFFFFFFFFu, not_tiled);
+    sK = warp_sum64(sK);
+    maxK = warp_max64(maxK);
+    maxB = warp_max64(maxB);
+    sM = warp_sum64(sM);
+    sIdle = warp_sum64(sIdle);
+    sHid = warp_sum64(sHid);
+    if (lane != 0) return;
 
     uint32_t fl = 0;
     if (not_tiled) fl |= 0x2u;
@@ -568,7 +577,7 @@ cudaError_t launch_combine(const MetricsOut* parts, uint32_t n_parts, MetricsOut
 
 cudaError_t launch_finalize(const FinalizeJob* jobs, uint32_t n_jobs, cudaStream_t stream) {
     if (n_jobs == 0) return cudaSuccess;
-    finalize_kernel<<<n_jobs, 256, 0, stream>>>(jobs);
+    finalize_kernel<<<(n_jobs + kFinWarps - 1) / kFinWarps, 32 * kFinWarps, 0, stream>>>(jobs, n_jobs);
     return cudaGetLastError();
 }
 

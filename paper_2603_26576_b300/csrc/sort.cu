@@ -74,11 +74,12 @@ __global__ void __launch_bounds__(1024) sort_plan_kernel(const SegDesc* __restri
                                                          const uint32_t* __restrict__ seg_flags, SortCtl* ctl) {
     __shared__ uint32_t s_cnt[32];
     __shared__ uint64_t s_rec[32], s_til[32];
-    __shared__ uint32_t s_base;
+    __shared__ uint32_t s_base, s_find;
     __shared__ uint64_t s_rbase, s_tbase;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (tid == 0) {
         s_base = 0;
+        s_find = 0;
         s_rbase = 0;
         s_tbase = 0;
     }
@@ -151,6 +152,7 @@ __global__ void __launch_bounds__(1024) sort_plan_kernel(const SegDesc* __restri
                     ctl->given[k] = kRunsSeen;
                 }
             }
+            if (ctl->given[k] == kRunsFound) atomicAdd(&s_find, 1u);
             // the re-sweep recomputes this ingest's part of the segment: its
             // sums restart from their value before the ingest
             const int64_t* src = ctl->restore[s];
@@ -170,6 +172,7 @@ __global__ void __launch_bounds__(1024) sort_plan_kernel(const SegDesc* __restri
     }
     if (tid == 0) {
         ctl->max_passes = 0;
+        ctl->n_find = s_find;
         ctl->nflag = s_base;
         ctl->nrec = s_rbase;
         ctl->ntile = s_tbase;
@@ -180,6 +183,7 @@ __global__ void __launch_bounds__(1024) sort_plan_kernel(const SegDesc* __restri
 // ------------------------------------------------------------ min / max
 __global__ void __launch_bounds__(kSortThreads) sort_minmax_kernel(const SegDesc* __restrict__ segs, SortCtl* ctl) {
     __shared__ int64_t s_mn[kSortThreads / 32], s_mx[kSortThreads / 32];
+    if (ctl->n_find == 0) return;   // every flagged segment's runs are known already
     const uint32_t ntile = static_cast<uint32_t>(ctl->ntile);
     for (uint32_t t = blockIdx.x; t < ntile; t += gridDim.x) {
         const uint32_t k = seg_of_tile(ctl, t);

@@ -460,6 +460,13 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
             const bool outside = mine && (span_hi <= wa || span_lo >= wb);
             if (inside) acc += lchain == 0 ? tot0 : (lchain == 1 ? tot1 : tot2);
             uint32_t sb = __ballot_sync(0xFFFFFFFFu, mine && lchain == 0 && !inside && !outside);
+            // windows cutting the tile: the pieces' starts do not depend on
+            // the window, so the shapes with registers to spare (the ones
+            // short segments use) work them out once (over sr, no longer
+            // needed as starts) and each window only clips
+            constexpr bool kStarts = ITEMS <= 9;
+            uint32_t pO[ITEMS];
+            if (kStarts && sb && !d_host) piece_starts<ITEMS>(sr, pO, er, tg, cnt, xK, xM);
             while (sb) {
                 const int src = __ffs(sb) - 1;
                 sb &= sb - 1;
@@ -468,7 +475,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
                 int64_t c0, c1, c2;
                 if (!d_host) {
                     uint32_t k1 = 0, k2 = 0, k3 = 0;
-                    pieces32<ITEMS, false>(sr, er, tg, cnt, xK, xM, a, b, k1, k2, k3);
+                    if (kStarts) clip_pieces<ITEMS>(sr, pO, er, tg, cnt, a, b, k1, k2, k3);
+                    else pieces32<ITEMS, false>(sr, er, tg, cnt, xK, xM, a, b, k1, k2, k3);
                     c0 = __reduce_add_sync(0xFFFFFFFFu, k1);
                     c1 = __reduce_add_sync(0xFFFFFFFFu, k2);
                     c2 = __reduce_add_sync(0xFFFFFFFFu, k3);

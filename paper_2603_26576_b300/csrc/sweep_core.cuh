@@ -75,6 +75,53 @@ __device__ __forceinline__ void pieces32(const uint32_t (&sr)[ITEMS], const uint
     sM += sO - sK;
 }
 
+// The start of each record's new piece in the all-records chain (written
+// over sr) and in its own chain (pO), with the lane's carries Kp / Mp: the
+// part of pieces32 that does not depend on the window, for tiles clipped to
+// several windows.
+template <int ITEMS>
+__device__ __forceinline__ void piece_starts(uint32_t (&sr)[ITEMS], uint32_t (&pO)[ITEMS],
+                                             const uint32_t (&er)[ITEMS], const uint32_t (&tg)[ITEMS], int cnt,
+                                             uint32_t Kp, uint32_t Mp) {
+    uint32_t Ap = umax(Kp, Mp);
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        pO[i] = 0;
+        if (i < cnt) {
+            const bool isK = tg[i] < 32u;
+            const uint32_t own = isK ? Kp : Mp;
+            pO[i] = umax(sr[i], own);
+            sr[i] = umax(sr[i], Ap);
+            const uint32_t nw = umax(own, er[i]);
+            Kp = isK ? nw : Kp;
+            Mp = isK ? Mp : nw;
+            Ap = umax(Ap, er[i]);
+        }
+    }
+}
+
+// pieces32 clipped to [a, b) from the piece starts (pA, pO) of piece_starts:
+// the same sums.
+template <int ITEMS>
+__device__ __forceinline__ void clip_pieces(const uint32_t (&pA)[ITEMS], const uint32_t (&pO)[ITEMS],
+                                            const uint32_t (&er)[ITEMS], const uint32_t (&tg)[ITEMS], int cnt,
+                                            uint32_t a, uint32_t b, uint32_t& sK, uint32_t& sM, uint32_t& sA) {
+    uint32_t sO = 0;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        if (i < cnt) {
+            const uint32_t e = umin(er[i], b);
+            const uint32_t pa = umax(pA[i], a);
+            sA += umax(e, pa) - pa;
+            const uint32_t po = umax(pO[i], a);
+            const uint32_t lO = umax(e, po) - po;
+            sO += lO;
+            sK += tg[i] < 32u ? lO : 0u;
+        }
+    }
+    sM += sO - sK;
+}
+
 // Host tile (32-bit offsets): per-state sums of lengths clipped to [a, b),
 // the lane's smallest start and largest end, and validation.
 template <int ITEMS, bool FULL>

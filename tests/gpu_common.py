@@ -55,13 +55,15 @@ def env(**kv):
                 os.environ[k] = v
 
 
-def make_ctx(shape=None, tiles_per_warp=None, budget=0):
+def make_ctx(shape=None, tiles_per_warp=None, budget=0, slices_per_warp=None):
     import paper_2603_26576_b300 as P
     kv = {}
     if shape is not None:
         kv["TALP_GPU_SWEEP_SHAPE"] = shape
     if tiles_per_warp is not None:
         kv["TALP_GPU_TILES_PER_WARP"] = tiles_per_warp
+    if slices_per_warp is not None:
+        kv["TALP_GPU_SLICES_PER_WARP"] = slices_per_warp
     with env(**kv):
         return P.Context(0, budget)
 

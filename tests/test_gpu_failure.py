@@ -38,6 +38,30 @@ def test_wait_limit_runs_out_reports_etimedout():
     good.close()
 
 
+def test_wait_limit_runs_out_with_slices_handed_out():
+    """The same with the sweep's dynamic work split: warps that gave up still
+    take the remaining slices (writing their records empty, so the fix-up
+    reads only written records); then a good context equals the oracle."""
+    import paper_2603_26576_b300 as P
+    t = tg.random_trace(4, trace_id=42, n_ranks=3, devices_per_rank=2, dev_events=6000, host_events=500,
+                        n_regions=2)
+    with env(TALP_GPU_WAIT_LIMIT=-1, TALP_GPU_SLICES_PER_WARP=16, TALP_GPU_TILES_PER_WARP=1):
+        c = P.Context(0)
+    try:
+        for flags in (P.TALP_GPU_SORTED_BY_START, 0):
+            c.ingest([t], flags=flags)
+            with pytest.raises(P.TalpGpuError) as e:
+                c.metrics(t.trace_id)
+            assert e.value.status == ETIMEDOUT
+            c.reset()
+    finally:
+        c.close()
+    good = make_ctx(slices_per_warp=16, tiles_per_warp=1)
+    good.ingest([t], flags=P.TALP_GPU_SORTED_BY_START)
+    assert_trace_equal(good, t, "after-timeout, slices")
+    good.close()
+
+
 def test_raw_scatter_wait_runs_out_reports_etimedout():
     """The raw adapter's bounded wait for a tile's bulk copy: with a negative
     limit it reports a time-out (after letting the copy land) and the call

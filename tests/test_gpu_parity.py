@@ -76,6 +76,32 @@ def test_random_traces_shapes(shape, tpw):
         c.close()
 
 
+@pytest.mark.parametrize("spw", [1, 5, 64])
+def test_slices_handed_out_by_ticket(spw):
+    """The sweep's dynamic work split (slices of the records taken by warps
+    as they come free, a record per slice for the fix-up): mid-size traces,
+    long covering intervals and records out of start order (the first
+    sweep's run log and the sort stage) equal the oracle under 1, 5 and 64
+    slices per warp and one tile per warp."""
+    c = make_ctx(tiles_per_warp=1, slices_per_warp=spw)
+    try:
+        for seed in range(2):
+            t = tg.random_trace(seed + 70, trace_id=seed, n_ranks=3, devices_per_rank=[1, 2, 3],
+                                dev_events=[2000 + 37 * seed, 5000, 1, 0, 333, 7000], host_events=[4000, 1, 2500],
+                                n_regions=5)
+            c.ingest([t])
+            assert_trace_equal(c, t, ("slices", spw, seed))
+            c.ingest([_covering_trace(seed + 20)])
+            assert_trace_equal(c, _covering_trace(seed + 20), ("slices covering", spw, seed))
+            u = tg.split_runs(tg.random_trace(seed + 80, trace_id=40 + seed, n_ranks=2, devices_per_rank=2,
+                                              dev_events=9000, host_events=300, n_regions=3), 4, seed=seed)
+            c.ingest([u])
+            assert_trace_equal(c, u, ("slices unsorted", spw, seed))
+            c.reset()
+    finally:
+        c.close()
+
+
 def _covering_trace(seed, n=20000):
     """Long kernels and copies that span many tiles and warps: the carry
     entering a slice can reach far ahead."""
