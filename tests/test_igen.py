@@ -86,3 +86,27 @@ def test_waves_group_whole_traces():
     assert [sp.trace_id for w in ws for sp in w] == list(range(40))
     for w in ws:
         assert len(w) == 1 or sum(sp.n_records for sp in w) <= 50_000
+
+
+def test_plain_large_has_concurrent_kernel_streams():
+    """The plain large trace's 4 kernel streams are independent lanes: on a
+    device, kernels of different streams overlap (up to 4 at once), so the
+    headline workload merges concurrent kernels as Sec. 4.2's first
+    flattening step requires.  Counted by a +1/-1 sweep over the events of
+    two devices of a 1% sample (same laws, fewer events)."""
+    import tracegen as tg
+    t = tg.plain_large(scale=0.01, n_ranks=2, gpus_per_rank=1)
+    for g in range(t.m_devices):
+        a, b = int(t.dev_off[g]), int(t.dev_off[g + 1])
+        se, tag = t.dev_se[a:b], t.dev_tag[a:b]
+        k = (tag >> 5) == 0
+        assert sorted(np.unique(tag[k] & 31)) == [0, 1, 2, 3]
+        pts = np.concatenate([se[k, 0], se[k, 1]])
+        step = np.concatenate([np.ones(int(k.sum()), np.int64), -np.ones(int(k.sum()), np.int64)])
+        order = np.lexsort((step, pts))                     # ends before starts at equal times
+        level = np.cumsum(step[order])
+        assert level.max() == 4
+        # time with two or more kernels running: a sizeable share of the kernel time
+        dt = np.diff(pts[order])
+        multi = int(dt[level[:-1] >= 2].sum())
+        assert multi > 0.1 * int((se[k, 1] - se[k, 0]).sum())
