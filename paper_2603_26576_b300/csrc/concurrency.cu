@@ -96,6 +96,7 @@ __device__ __forceinline__ void insert_top(TopK<T>& x, T e) {
 }
 
 __device__ __forceinline__ uint32_t shfl_up_t(uint32_t v, int d) { return __shfl_up_sync(0xFFFFFFFFu, v, d); }
+__device__ __forceinline__ int64_t shfl_up_t(int64_t v, int d) { return shfl_up64(v, d); }
 __device__ __forceinline__ uint32_t shfl_t(uint32_t v, int s) { return __shfl_sync(0xFFFFFFFFu, v, s); }
 __device__ __forceinline__ int64_t shfl_t(int64_t v, int s) { return shfl64(v, s); }
 __device__ __forceinline__ uint32_t shfl_xor_t(uint32_t v, int m) { return __shfl_xor_sync(0xFFFFFFFFu, v, m); }
@@ -127,7 +128,7 @@ __device__ __forceinline__ void scan_top(TopK<T>& x, int lane) {
     }
 }
 
-// absolute value -> offset from s0 (0 at or before s0), and back
+// absolute value -> offset from s0 (0 at or before s0)
 __device__ __forceinline__ uint32_t rel32(int64_t x, int64_t s0) {
     if (x <= s0) return 0u;
     const uint64_t d = static_cast<uint64_t>(x) - static_cast<uint64_t>(s0);   // exact: 0 < d < 2^64
@@ -137,35 +138,52 @@ __device__ __forceinline__ uint32_t rel32(int64_t x, int64_t s0) {
 __device__ __forceinline__ bool near32(int64_t x, int64_t s0) {
     return x <= s0 || static_cast<uint64_t>(x) - static_cast<uint64_t>(s0) < 0xFFFFFFFFull;
 }
-__device__ __forceinline__ void to_abs(TopK<int64_t>& out, const TopK<uint32_t>& x, int64_t s0) {
-#pragma unroll
-    for (int i = 0; i < K; ++i) out.v[i] = s0 + static_cast<int64_t>(x.v[i]);
-}
 
 // One tile of a chunk staged in shared memory: rows of 16 bytes and tags.
 // Lane L works on records L * kItems .. L * kItems + kItems - 1, so record q
 // sits at (q % kItems) * 33 + q / kItems: the lanes' reads of their i-th
 // records are consecutive (no bank conflicts), and so are the staging
-// writes of 8 consecutive records.
+// writes of 8 consecutive records.  The tags arrive as the aligned 4-byte
+// words that hold the tile's tag bytes (each word holds at least one of
+// them, so it lies in mapped memory); byte q is at toff + q.
 constexpr int kSlots = kItems * 33;
+constexpr int kTagWords = kTile / 4 + 2;
 struct Stage {
     longlong2 se[kSlots];
-    uint8_t tag[kSlots];
+    uint32_t tagw[kTagWords];
 };
 
 __device__ __forceinline__ int slot(int q) { return (q % kItems) * 33 + q / kItems; }
 
-__device__ __forceinline__ void stage_tile(Stage& st, const int64_t* __restrict__ se, const uint8_t* __restrict__ tag,
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Copies of one tile (records r0 .. r0 + n - 1) into a stage, issued by
+// every lane as one commit group; they land while the warp works on the
+// tile before.
+__device__ __forceinline__ void issue_tile(Stage& st, const int64_t* __restrict__ se, const uint8_t* __restrict__ tag,
                                            uint64_t r0, int n, int lane) {
-    for (int q = lane; q < n; q += 32) {
-        st.se[slot(q)] = *reinterpret_cast<const longlong2*>(se + 2 * (r0 + q));
-        st.tag[slot(q)] = tag[r0 + q];
-    }
-    __syncwarp();
+    for (int q = lane; q < n; q += 32) cp_async16(&st.se[slot(q)], se + 2 * (r0 + q));
+    const uintptr_t A = reinterpret_cast<uintptr_t>(tag + r0);
+    const uintptr_t w0 = A & ~static_cast<uintptr_t>(3);
+    const int nw = static_cast<int>((A + static_cast<uintptr_t>(n) + 3 - w0) >> 2);
+    for (int w = lane; w < nw; w += 32) cp_async4(&st.tagw[w], reinterpret_cast<const void*>(w0 + 4u * w));
+    cp_async_commit();
 }
 
 __device__ __forceinline__ longlong2 row_of(const Stage& st, int q) { return st.se[slot(q)]; }
-__device__ __forceinline__ uint32_t kind_of(const Stage& st, int q) { return st.tag[slot(q)] >> 5; }
+__device__ __forceinline__ uint32_t kind_of(const Stage& st, int toff, int q) {
+    return reinterpret_cast<const uint8_t*>(st.tagw)[toff + q] >> 5;
+}
 
 // clipped record q of the stage: start max(s, a), end in [start, b]
 __device__ __forceinline__ void clipped(const Stage& st, int q, const ConcDev& dv, int64_t& s, int64_t& e) {
@@ -181,12 +199,14 @@ __device__ __forceinline__ void clip_row(const longlong2 r, const ConcDev& dv, i
 }
 
 // ------------------------------------------------------------- chunk top-K
-// The K largest ends of a chunk do not depend on the order of its records:
-// each lane takes every 32nd record straight from memory (coalesced) into
-// its own lists, as 32-bit offsets from the chunk's first clipped start
-// (every clipped start and end of the chunk is at or after it), and the
-// warp merges the 32 lists once.  A chunk whose ends reach 2^32 - 1 ns or
-// more past its first start is redone with 64-bit lists.
+// Only the ends still running after the chunk's last (clipped) start matter
+// to later chunks: every later start is at or after it, so an end at or
+// before it can only ever give a zero contribution there.  Each lane takes
+// every 32nd record straight from memory (coalesced), validates it, and
+// keeps the rare ends past that start in its own lists; the warp merges the
+// 32 lists once.  The lists of the scan that follows therefore agree with
+// the full top-K lists on every entry above the next chunk's first start,
+// which is all the levels pass reads of them.
 template <typename T>
 __device__ __forceinline__ void warp_merge_top(TopK<T>& x) {
 #pragma unroll
@@ -213,38 +233,36 @@ __global__ void __launch_bounds__(kWarps * 32) conc_chunk_top(const int64_t* __r
     clear_top(ck);
     uint32_t bad = 0;
     if (ch.n > 0) {
-        int64_t s0, e0;
-        clip_row(*reinterpret_cast<const longlong2*>(se + 2 * ch.rec0), dv, s0, e0);
-        TopK<uint32_t> la, lk;
-        clear_top(la);
-        clear_top(lk);
-        bool fits = true;
-        for (uint32_t q = lane; q < ch.n; q += 32) {
-            const longlong2 r = *reinterpret_cast<const longlong2*>(se + 2 * (ch.rec0 + q));
-            const uint32_t kind = tag[ch.rec0 + q] >> 5;
-            bad |= (r.y < r.x ? 1u : 0u) | (kind > 4u ? 2u : 0u);
-            int64_t s, e;
-            clip_row(r, dv, s, e);
-            fits &= near32(e, s0);
-            const uint32_t re = rel32(e, s0);
-            insert_top(la, re);
-            if (kind == 0u) insert_top(lk, re);
-        }
-        if (__all_sync(0xFFFFFFFFu, fits)) {
-            warp_merge_top(la);
-            warp_merge_top(lk);
-            to_abs(ca, la, s0);
-            to_abs(ck, lk, s0);
-        } else {
-            for (uint32_t q = lane; q < ch.n; q += 32) {
-                int64_t s, e;
-                clip_row(*reinterpret_cast<const longlong2*>(se + 2 * (ch.rec0 + q)), dv, s, e);
-                insert_top(ca, e);
-                if ((tag[ch.rec0 + q] >> 5) == 0u) insert_top(ck, e);
+        // the chunk's last clipped start
+        const int64_t sl = max64(se[2 * (ch.rec0 + ch.n - 1)], dv.a);
+        // four records per lane in flight at a time
+        for (uint32_t q0 = 0; q0 < ch.n; q0 += 4 * 32) {
+            longlong2 r[4];
+            uint32_t kind[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t q = q0 + u * 32 + lane;
+                r[u] = make_longlong2(0, 0);
+                kind[u] = 0;
+                if (q < ch.n) {
+                    r[u] = *reinterpret_cast<const longlong2*>(se + 2 * (ch.rec0 + q));
+                    kind[u] = tag[ch.rec0 + q] >> 5;
+                }
             }
-            warp_merge_top(ca);
-            warp_merge_top(ck);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                bad |= (r[u].y < r[u].x ? 1u : 0u) | (kind[u] > 4u ? 2u : 0u);
+                // clipped end min(e, b) (at least the clipped start, which is
+                // at most sl, so the test needs no lower clip)
+                const int64_t e = min64(r[u].y, dv.b);
+                if (e > sl) {
+                    insert_top(ca, e);
+                    if (kind[u] == 0u) insert_top(ck, e);
+                }
+            }
         }
+        warp_merge_top(ca);
+        warp_merge_top(ck);
     }
     bad = __reduce_or_sync(0xFFFFFFFFu, bad);
     if (lane == 0) {
@@ -258,31 +276,77 @@ __global__ void __launch_bounds__(kWarps * 32) conc_chunk_top(const int64_t* __r
 }
 
 // --------------------------------------------------- per-device chunk scan
-// entering state of each chunk: top-K over all earlier chunks of its device
-__global__ void conc_chunk_scan(const ConcDev* __restrict__ devs, uint32_t n_dev, const int64_t* __restrict__ top,
-                                int64_t* __restrict__ in) {
-    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+// Entering state of each chunk: the top-K over all earlier chunks of its
+// device.  One warp per device, 32 chunks at a time: a warp scan of the
+// chunks' lists, merged with the carry of the chunks before.
+constexpr int kScanWarps = 4;
+
+__global__ void __launch_bounds__(kScanWarps * 32) conc_chunk_scan(const ConcDev* __restrict__ devs, uint32_t n_dev,
+                                                                  const int64_t* __restrict__ top,
+                                                                  int64_t* __restrict__ in) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t g = blockIdx.x * kScanWarps + (threadIdx.x >> 5);
     if (g >= n_dev) return;
     const ConcDev dv = devs[g];
-    TopK<int64_t> ra, rk;
-    clear_top(ra);
-    clear_top(rk);
-    for (uint32_t q = 0; q < dv.nchunk; ++q) {
-        const uint64_t c = dv.chunk0 + q;
+    TopK<int64_t> ca, ck;   // carry: every chunk before the current group
+    clear_top(ca);
+    clear_top(ck);
+    for (uint32_t q0 = 0; q0 < dv.nchunk; q0 += 32) {
+        const uint32_t q = q0 + lane;
+        const uint64_t c = static_cast<uint64_t>(dv.chunk0) + q;
         TopK<int64_t> xa, xk;
+        clear_top(xa);
+        clear_top(xk);
+        if (q < dv.nchunk) {
 #pragma unroll
-        for (int i = 0; i < K; ++i) {
-            in[c * 2 * K + i] = ra.v[i];
-            in[c * 2 * K + K + i] = rk.v[i];
-            xa.v[i] = top[c * 2 * K + i];
-            xk.v[i] = top[c * 2 * K + K + i];
+            for (int i = 0; i < K; ++i) {
+                xa.v[i] = top[c * 2 * K + i];
+                xk.v[i] = top[c * 2 * K + K + i];
+            }
         }
-        merge_top(ra, xa);
-        merge_top(rk, xk);
+        scan_top(xa, lane);
+        scan_top(xk, lane);
+        TopK<int64_t> ea = shfl_up_top(xa, 1), ek = shfl_up_top(xk, 1);
+        if (lane == 0) {
+            clear_top(ea);
+            clear_top(ek);
+        }
+        merge_top(ea, ca);
+        merge_top(ek, ck);
+        if (q < dv.nchunk) {
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                in[c * 2 * K + i] = ea.v[i];
+                in[c * 2 * K + K + i] = ek.v[i];
+            }
+        }
+        merge_top(ca, shfl_top(xa, 31));
+        merge_top(ck, shfl_top(xk, 31));
     }
 }
 
 // ------------------------------------------------------------- levels
+// The state carried from tile to tile (the top-K ends of everything before
+// the tile) is kept as 32-bit offsets from the previous tile's first start
+// and rebased on the next tile's with one max and one subtraction per entry
+// (an entry at or before the new base becomes 0: no later start can use
+// it).  Only when a tile had to take the int64 path does the state live as
+// int64 in shared memory until a tile converts it back.
+//
+// In a lane's walk the K = 8 list is split in two: the 4 largest ends (every
+// record updates them) and the next 4, which an end joins only when the top
+// 4 push it out while it is still running at the record's start (a
+// concurrency of 5 or more, rare); levels 5-8 are added only for records at
+// which some lane of the warp has such an end.
+__device__ __forceinline__ void ins4(uint32_t (&x)[4], uint32_t& e) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint32_t hi = tmax(x[i], e);
+        e = tmin(x[i], e);
+        x[i] = hi;
+    }
+}
+
 __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_t* __restrict__ se,
                                                                 const uint8_t* __restrict__ tag,
                                                                 const ConcDev* __restrict__ devs,
@@ -290,68 +354,134 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
                                                                 uint32_t n_chunks, const int64_t* __restrict__ in,
                                                                 int64_t* __restrict__ out,
                                                                 uint32_t* __restrict__ status) {
-    __shared__ Stage stg[kWarps];
-    __shared__ unsigned long long s_acc[kWarps][2 * K];   // the warp's level sums of its chunk
+    // per warp: two stages (the tile being worked on and the next one in
+    // flight), then the level sums and the int64 state of every warp
+    extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    Stage* stg = reinterpret_cast<Stage*>(smem) + 2 * wid;
+    unsigned long long* s_acc =
+        reinterpret_cast<unsigned long long*>(smem + sizeof(Stage) * 2 * kWarps) + wid * 2 * K;   // level sums
+    int64_t* s_st = reinterpret_cast<int64_t*>(smem + sizeof(Stage) * 2 * kWarps) + (kWarps + wid) * 2 * K;
     const uint32_t c = blockIdx.x * kWarps + wid;
     if (c >= n_chunks) return;
     const ConcChunk ch = chunks[c];
     const ConcDev dv = devs[ch.dev];
-    if (lane < 2 * K) s_acc[wid][lane] = 0;
-    __syncwarp();
-    TopK<int64_t> sa, sk;   // state before the current tile (warp-uniform)
-#pragma unroll
-    for (int i = 0; i < K; ++i) {
-        sa.v[i] = in[static_cast<uint64_t>(c) * 2 * K + i];
-        sk.v[i] = in[static_cast<uint64_t>(c) * 2 * K + K + i];
+    if (ch.n > 0) issue_tile(stg[0], se, tag, ch.rec0, static_cast<int>(min(static_cast<uint32_t>(kTile), ch.n)), lane);
+    if (lane < 2 * K) {
+        s_acc[lane] = 0;
+        s_st[lane] = in[static_cast<uint64_t>(c) * 2 * K + lane];   // entering state of the chunk
     }
+    __syncwarp();
+    // state before the current tile (warp-uniform): offsets from sbase when
+    // rel, else s_st
+    bool rel = false;
+    int64_t sbase = 0;
+    uint32_t ra[K], rk[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) ra[i] = rk[i] = 0u;
     uint32_t bad = 0;
+    int64_t last_x = INT64_MIN;   // the previous tile's last start (order check)
     const uint64_t dev_end = dv.rec0 + dv.n;
-    for (uint32_t o = 0; o < ch.n; o += kTile) {
+    for (uint32_t o = 0, t = 0; o < ch.n; o += kTile, ++t) {
         const int n = static_cast<int>(min(static_cast<uint32_t>(kTile), ch.n - o));
         const uint64_t r0 = ch.rec0 + o;
-        stage_tile(stg[wid], se, tag, r0, n, lane);
-        if (o > 0 && lane == 0) bad |= se[2 * (r0 - 1)] > se[2 * r0] ? 4u : 0u;
         // start of the record after the tile (clipped), or none
         int64_t after = INT64_MAX;
         if (r0 + n < dev_end) after = max64(se[2 * (r0 + n)], dv.a);
-        int64_t s0, e0;
-        clipped(stg[wid], 0, dv, s0, e0);
-        // offsets from s0: the tile's records, the entering state, the bounds
+        if (o + kTile < ch.n) {
+            issue_tile(stg[(t + 1) & 1], se, tag, r0 + kTile,
+                       static_cast<int>(min(static_cast<uint32_t>(kTile), ch.n - o - kTile)), lane);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncwarp();
+        const Stage& S = stg[t & 1];
+        const int toff = static_cast<int>(reinterpret_cast<uintptr_t>(tag + r0) & 3u);
+        const int64_t x0 = row_of(S, 0).x, xl = row_of(S, n - 1).x;
+        if (lane == 0) bad |= last_x > x0 ? 4u : 0u;
+        last_x = xl;
+        const int64_t s0 = max64(x0, dv.a);
+        // the entering state as offsets from s0
+        TopK<uint32_t> ta, tk;
+        bool fits = true;
+        if (rel) {
+            const int64_t d = s0 - sbase;
+            if (d >= 0 && d <= 0xFFFFFFFFll) {
+                const uint32_t d32 = static_cast<uint32_t>(d);
+#pragma unroll
+                for (int i = 0; i < K; ++i) {
+                    ta.v[i] = tmax(ra[i], d32) - d32;
+                    tk.v[i] = tmax(rk[i], d32) - d32;
+                }
+            } else {   // every entry at or before s0 (or records out of order, reported)
+                clear_top(ta);
+                clear_top(tk);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                const int64_t xa = s_st[i], xk = s_st[K + i];
+                fits &= near32(xa, s0) && near32(xk, s0);
+                ta.v[i] = rel32(xa, s0);
+                tk.v[i] = rel32(xk, s0);
+            }
+        }
+        // the tile's records as offsets from s0.  A tile that starts inside
+        // the window needs no start clip, and ends are clipped to b only:
+        // an end below its start (a record after b) is at or before every
+        // later start, so it only ever contributes 0 -- as the gap bound
+        // min(next start, b) already makes the gaps after b empty.
         uint32_t s[kItems], e[kItems];
         uint32_t kmask = 0;
-        bool fits = true;
-        // the lane's own top-K lists: its kItems == K ends sorted (0 = none)
-        TopK<uint32_t> la, lk;
+        TopK<uint32_t> la, lk;   // the lane's own K ends, sorted (0 = none)
+        const bool plain = x0 >= dv.a && x0 < dv.b && static_cast<uint64_t>(xl - x0) < 0xFFFFFFFFull;
+        if (plain) {
+            uint32_t hib = 0;
+            int64_t prev = lane > 0 ? row_of(S, lane * kItems - 1).x : x0;
 #pragma unroll
-        for (int i = 0; i < kItems; ++i) {
-            const int q = lane * kItems + i;
-            s[i] = e[i] = 0xFFFFFFFFu;
-            la.v[i] = lk.v[i] = 0u;
-            if (q < n) {
-                int64_t sa64, ea64;
-                clipped(stg[wid], q, dv, sa64, ea64);
-                if (q > 0) bad |= row_of(stg[wid], q - 1).x > row_of(stg[wid], q).x ? 4u : 0u;
-                fits &= near32(ea64, s0);
-                s[i] = rel32(sa64, s0);
-                e[i] = rel32(ea64, s0);
-                const bool isK = kind_of(stg[wid], q) == 0u;
-                kmask |= isK ? 1u << i : 0u;
-                la.v[i] = e[i];
-                lk.v[i] = isK ? e[i] : 0u;
+            for (int i = 0; i < kItems; ++i) {
+                const int q = lane * kItems + i;
+                s[i] = e[i] = 0xFFFFFFFFu;
+                la.v[i] = lk.v[i] = 0u;
+                if (q < n) {
+                    const longlong2 r = row_of(S, q);
+                    bad |= prev > r.x ? 4u : 0u;
+                    prev = r.x;
+                    const int64_t de = min64(r.y, dv.b) - s0;
+                    hib |= static_cast<uint32_t>(static_cast<uint64_t>(de) >> 32);
+                    s[i] = static_cast<uint32_t>(r.x) - static_cast<uint32_t>(s0);
+                    e[i] = static_cast<uint32_t>(de);
+                    const bool isK = kind_of(S, toff, q) == 0u;
+                    kmask |= isK ? 1u << i : 0u;
+                    la.v[i] = e[i];
+                    lk.v[i] = isK ? e[i] : 0u;
+                }
+            }
+            fits &= hib == 0;
+        } else {
+#pragma unroll
+            for (int i = 0; i < kItems; ++i) {
+                const int q = lane * kItems + i;
+                s[i] = e[i] = 0xFFFFFFFFu;
+                la.v[i] = lk.v[i] = 0u;
+                if (q < n) {
+                    int64_t sa64, ea64;
+                    clipped(S, q, dv, sa64, ea64);
+                    if (q > 0) bad |= row_of(S, q - 1).x > row_of(S, q).x ? 4u : 0u;
+                    fits &= near32(ea64, s0);
+                    s[i] = rel32(sa64, s0);
+                    e[i] = rel32(ea64, s0);
+                    const bool isK = kind_of(S, toff, q) == 0u;
+                    kmask |= isK ? 1u << i : 0u;
+                    la.v[i] = e[i];
+                    lk.v[i] = isK ? e[i] : 0u;
+                }
             }
         }
         sort8_desc(la.v);
         sort8_desc(lk.v);
-#pragma unroll
-        for (int i = 0; i < K; ++i) fits &= near32(sa.v[i], s0) && near32(sk.v[i], s0);
         if (__all_sync(0xFFFFFFFFu, fits)) {
-            TopK<uint32_t> ta, tk;   // entering state as offsets
-#pragma unroll
-            for (int i = 0; i < K; ++i) {
-                ta.v[i] = rel32(sa.v[i], s0);
-                tk.v[i] = rel32(sk.v[i], s0);
-            }
             scan_top(la, lane);
             scan_top(lk, lane);
             TopK<uint32_t> xa = shfl_up_top(la, 1), xk = shfl_up_top(lk, 1);
@@ -362,11 +492,21 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
             merge_top(xa, ta);
             merge_top(xk, tk);
             // a lane's gaps in the tile are disjoint and lie within 2^32 - 1 ns
-            // of s0, so its level sums of the tile fit 32 bits.  The level-k
-            // time of a gap [s, hi) is min(max(E_k, s), max(hi, s)) - s; the
-            // s terms are summed once (S) and taken off at the end, which is
-            // exact in wrapping 32-bit arithmetic because the results fit.
-            uint32_t acc_a[K], acc_k[K], S = 0;
+            // of s0, so its level sums of the tile -- and the warp's, whose
+            // gaps are disjoint too -- fit 32 bits.  The level-k time of a gap
+            // [s, hi) is min(max(E_k, s), max(hi, s)) - s; the s terms are
+            // summed once (S, and SH for the gaps where levels 5-8 are added)
+            // and taken off at the end, exact in wrapping 32-bit arithmetic
+            // because the results fit.
+            uint32_t ma[4], oa[4], mk[4], ok[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                ma[i] = xa.v[i];
+                oa[i] = xa.v[4 + i];
+                mk[i] = xk.v[i];
+                ok[i] = xk.v[4 + i];
+            }
+            uint32_t acc_a[K], acc_k[K], S = 0, SH = 0;
 #pragma unroll
             for (int k = 0; k < K; ++k) acc_a[k] = acc_k[k] = 0;
             const uint32_t bnd = rel32(dv.b, s0);
@@ -375,68 +515,100 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
 #pragma unroll
             for (int i = 0; i < kItems; ++i) {
                 const int q = lane * kItems + i;
-                if (q < n) {
-                    insert_top(xa, e[i]);
-                    if (kmask & (1u << i)) insert_top(xk, e[i]);
-                    const uint32_t ns = (i + 1 < kItems && q + 1 < n) ? s[i + 1] : nxt;
-                    // the gap [s_i, min(next start, window end)) at level k
-                    // lasts until E_k
-                    const uint32_t hc = tmax(tmin(ns, bnd), s[i]);
+                const bool v = q < n;
+                const uint32_t ns = (i + 1 < kItems && q + 1 < n) ? s[i + 1] : nxt;
+                // the gap [s_i, min(next start, window end)) at level k
+                // lasts until E_k
+                const uint32_t hc = tmax(tmin(ns, bnd), s[i]);
+                if (v) {
+                    uint32_t ev = e[i];
+                    ins4(ma, ev);
+                    if (ev > s[i]) ins4(oa, ev);   // a 5th end still running
+                    if (kmask & (1u << i)) {
+                        uint32_t ek = e[i];
+                        ins4(mk, ek);
+                        if (ek > s[i]) ins4(ok, ek);
+                    }
                     S += s[i];
 #pragma unroll
-                    for (int k = 0; k < K; ++k) {
-                        acc_a[k] += tmin(tmax(xa.v[k], s[i]), hc);
-                        acc_k[k] += tmin(tmax(xk.v[k], s[i]), hc);
+                    for (int k = 0; k < 4; ++k) {
+                        acc_a[k] += tmin(tmax(ma[k], s[i]), hc);
+                        acc_k[k] += tmin(tmax(mk[k], s[i]), hc);
+                    }
+                }
+                if (__any_sync(0xFFFFFFFFu, v && tmax(oa[0], ok[0]) > s[i])) {
+                    if (v) {
+                        SH += s[i];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            acc_a[4 + k] += tmin(tmax(oa[k], s[i]), hc);
+                            acc_k[4 + k] += tmin(tmax(ok[k], s[i]), hc);
+                        }
                     }
                 }
             }
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                acc_a[k] -= S;
-                acc_k[k] -= S;
-            }
-#pragma unroll
-            for (int k = 0; k < K; ++k) {   // warp sums in 16-bit halves (no overflow)
-                const uint32_t al = __reduce_add_sync(0xFFFFFFFFu, acc_a[k] & 0xFFFFu);
-                const uint32_t ah = __reduce_add_sync(0xFFFFFFFFu, acc_a[k] >> 16);
-                const uint32_t kl = __reduce_add_sync(0xFFFFFFFFu, acc_k[k] & 0xFFFFu);
-                const uint32_t kh = __reduce_add_sync(0xFFFFFFFFu, acc_k[k] >> 16);
+                const uint32_t sub = k < 4 ? S : SH;
+                const uint32_t wa = __reduce_add_sync(0xFFFFFFFFu, acc_a[k] - sub);
+                const uint32_t wk = __reduce_add_sync(0xFFFFFFFFu, acc_k[k] - sub);
                 if (lane == 0) {
-                    s_acc[wid][k] += (static_cast<unsigned long long>(ah) << 16) + al;
-                    s_acc[wid][K + k] += (static_cast<unsigned long long>(kh) << 16) + kl;
+                    s_acc[k] += wa;
+                    s_acc[K + k] += wk;
                 }
             }
             // state after the tile: the entering state and every record of it
             merge_top(la, ta);
             merge_top(lk, tk);
-            to_abs(sa, shfl_top(la, 31), s0);
-            to_abs(sk, shfl_top(lk, 31), s0);
+            const TopK<uint32_t> na = shfl_top(la, 31), nk = shfl_top(lk, 31);
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                ra[i] = na.v[i];
+                rk[i] = nk.v[i];
+            }
+            sbase = s0;
+            rel = true;
         } else {
             // a tile spanning 2^32 ns or more: lane 0 walks it in 64 bits
             if (lane == 0) {
+                TopK<int64_t> sa, sk;
+#pragma unroll
+                for (int i = 0; i < K; ++i) {
+                    if (rel) {
+                        sa.v[i] = ra[i] ? sbase + static_cast<int64_t>(ra[i]) : INT64_MIN;
+                        sk.v[i] = rk[i] ? sbase + static_cast<int64_t>(rk[i]) : INT64_MIN;
+                    } else {
+                        sa.v[i] = s_st[i];
+                        sk.v[i] = s_st[K + i];
+                    }
+                }
                 for (int q = 0; q < n; ++q) {
                     int64_t sq, eq;
-                    clipped(stg[wid], q, dv, sq, eq);
+                    clipped(S, q, dv, sq, eq);
                     insert_top(sa, eq);
-                    const bool isK = kind_of(stg[wid], q) == 0u;
+                    const bool isK = kind_of(S, toff, q) == 0u;
                     if (isK) insert_top(sk, eq);
                     int64_t ns = after;
                     if (q + 1 < n) {
                         int64_t s1, e1;
-                        clipped(stg[wid], q + 1, dv, s1, e1);
+                        clipped(S, q + 1, dv, s1, e1);
                         ns = s1;
                     }
                     const int64_t hi = min64(ns, dv.b);
 #pragma unroll
                     for (int k = 0; k < K; ++k) {
-                        s_acc[wid][k] += static_cast<unsigned long long>(max64(min64(hi, max64(sa.v[k], sq)) - sq, 0));
-                        s_acc[wid][K + k] +=
+                        s_acc[k] += static_cast<unsigned long long>(max64(min64(hi, max64(sa.v[k], sq)) - sq, 0));
+                        s_acc[K + k] +=
                             static_cast<unsigned long long>(max64(min64(hi, max64(sk.v[k], sq)) - sq, 0));
                     }
                 }
+#pragma unroll
+                for (int i = 0; i < K; ++i) {
+                    s_st[i] = sa.v[i];
+                    s_st[K + i] = sk.v[i];
+                }
             }
-            sa = shfl_top(sa, 0);
-            sk = shfl_top(sk, 0);
+            rel = false;
         }
         __syncwarp();
     }
@@ -444,7 +616,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
     bad = __reduce_or_sync(0xFFFFFFFFu, bad);
     __syncwarp();
     if (lane < 2 * K) {
-        const int64_t v = static_cast<int64_t>(s_acc[wid][lane]);
+        const int64_t v = static_cast<int64_t>(s_acc[lane]);
         if (v) atomic_add64(&out[static_cast<uint64_t>(ch.dev) * 2 * K + lane], v);
     }
     if (lane == 0 && bad) atomicOr(status, bad);
@@ -457,9 +629,17 @@ cudaError_t launch_concurrency(const int64_t* se, const uint8_t* tag, const Conc
                                uint32_t* status, cudaStream_t stream) {
     if (n_chunks == 0) return cudaSuccess;
     const uint32_t blocks = (n_chunks + kWarps - 1) / kWarps;
+    constexpr int kSmem = static_cast<int>(sizeof(Stage)) * 2 * kWarps + 2 * kWarps * 2 * K * 8;
+    static bool attr_set = false;   // set once per process, before the first launch
+    if (!attr_set) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(conc_chunk_levels, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
     conc_chunk_top<<<blocks, kWarps * 32, 0, stream>>>(se, tag, devs, chunks, n_chunks, top, status);
-    conc_chunk_scan<<<(n_dev + 127) / 128, 128, 0, stream>>>(devs, n_dev, top, in);
-    conc_chunk_levels<<<blocks, kWarps * 32, 0, stream>>>(se, tag, devs, chunks, n_chunks, in, out, status);
+    conc_chunk_scan<<<(n_dev + kScanWarps - 1) / kScanWarps, kScanWarps * 32, 0, stream>>>(devs, n_dev, top, in);
+    conc_chunk_levels<<<blocks, kWarps * 32, kSmem, stream>>>(se, tag, devs, chunks, n_chunks, in, out, status);
     return cudaGetLastError();
 }
 

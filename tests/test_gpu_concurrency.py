@@ -46,6 +46,22 @@ def test_mid_size_across_chunks(ctx, seed):
         np.testing.assert_array_equal(ctx.concurrency(t, r, arrays=arr), want, err_msg=str(("dev", seed, r)))
 
 
+@pytest.mark.parametrize("seed", range(2))
+def test_high_concurrency_across_tiles_and_chunks(ctx, seed):
+    """12 independent kernel streams at half occupancy each, plus copies: a
+    dozen records active at once is common, so the upper half of the top-8
+    lists and levels 5-8 are busy on most tiles; devices span several
+    chunks and the nested windows cut tiles at both ends."""
+    law = tg.DeviceLaw("lognormal", tuple(range(12)), (12, 13), occupancy=6.0)
+    t = tg.random_trace(seed, trace_id=seed, n_ranks=2, devices_per_rank=[2, 1], dev_events=[40000, 17000, 999],
+                        host_events=[10, 10], n_regions=4, law=law)
+    arr = _dev(t)
+    for r in range(t.n_regions):
+        want = oracle.concurrency(t, r, 8)
+        assert want[:2, 0, 7].min() > 0 and want[:2, 1, 7].min() > 0   # level 8 reached, kernels too
+        np.testing.assert_array_equal(ctx.concurrency(t, r, arrays=arr), want, err_msg=str((seed, r)))
+
+
 def test_level_one_is_the_union(ctx):
     t = tg.random_trace(7, trace_id=7, n_ranks=2, devices_per_rank=3, dev_events=30000, host_events=100,
                         n_regions=3)
