@@ -99,7 +99,6 @@ __device__ __forceinline__ uint32_t shfl_up_t(uint32_t v, int d) { return __shfl
 __device__ __forceinline__ int64_t shfl_up_t(int64_t v, int d) { return shfl_up64(v, d); }
 __device__ __forceinline__ uint32_t shfl_t(uint32_t v, int s) { return __shfl_sync(0xFFFFFFFFu, v, s); }
 __device__ __forceinline__ int64_t shfl_t(int64_t v, int s) { return shfl64(v, s); }
-__device__ __forceinline__ uint32_t shfl_xor_t(uint32_t v, int m) { return __shfl_xor_sync(0xFFFFFFFFu, v, m); }
 __device__ __forceinline__ int64_t shfl_xor_t(int64_t v, int m) { return shfl_xor64(v, m); }
 
 template <typename T>
@@ -192,11 +191,6 @@ __device__ __forceinline__ void clipped(const Stage& st, int q, const ConcDev& d
     e = max64(min64(r.y, dv.b), s);
 }
 
-// clipped row
-__device__ __forceinline__ void clip_row(const longlong2 r, const ConcDev& dv, int64_t& s, int64_t& e) {
-    s = max64(r.x, dv.a);
-    e = max64(min64(r.y, dv.b), s);
-}
 
 // ------------------------------------------------------------- chunk top-K
 // Only the ends still running after the chunk's last (clipped) start matter

@@ -24,8 +24,9 @@
 // Sweep (one CTA per super-chunk of kFmsSuper consecutive chunks of a
 // segment at a time; a producer warp and 8 consumer warps):
 //  - the producer stages each run's range of a chunk in shared memory with
-//    1-D bulk copies (cp.async.bulk) completing on the stage's mbarrier, two
-//    stages deep (it never waits for its copies);
+//    1-D bulk copies (cp.async.bulk) completing on the stage's mbarrier (it
+//    never waits for its copies; one stage, so that three CTAs fit on an SM
+//    and hide each other's copies and barriers);
 //  - the consumers take the chunk's largest kernel and memory ends (its
 //    aggregate) and validate its records, rank every record by merge path
 //    (its position in its run plus the number of records of every other run
@@ -51,7 +52,7 @@ constexpr int kFmsConsumers = 8;                   // consumer warps
 constexpr int kFmsThreads = 32 * (kFmsConsumers + 1);
 constexpr int kFmsCT = 32 * kFmsConsumers;         // consumer threads
 constexpr int kFmsItems = kFmsChunk / kFmsCT;      // records per consumer thread (at most)
-constexpr int kFmsStages = 2;
+constexpr int kFmsStages = 1;                     // 3 CTAs per SM: 72 KB, 72 registers
 constexpr int kFmsTagBytes = kFmsChunk + 32 * kMaxRuns;
 constexpr int kRmax = 8;                           // regions per trace (at most)
 
@@ -611,7 +612,7 @@ __device__ __forceinline__ void sweep32(FmsShared& sh, int64_t s0, int64_t spanH
 // jobs, each chunk swept with its true carry T and with its carry L, the
 // difference added.
 template <bool FIX>
-__global__ void __launch_bounds__(kFmsThreads, 2)
+__global__ void __launch_bounds__(kFmsThreads, 3)
     fms_kernel(const SegDesc* __restrict__ segs, SortCtl* ctl, uint32_t* __restrict__ seg_flags,
                uint32_t* __restrict__ gstatus, int64_t wait_limit) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
