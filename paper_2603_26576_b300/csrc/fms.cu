@@ -56,6 +56,24 @@ constexpr int kFmsStages = 1;                     // 3 CTAs per SM: 72 KB, 72 re
 constexpr int kFmsTagBytes = kFmsChunk + 32 * kMaxRuns;
 constexpr int kRmax = 8;                           // regions per trace (at most)
 
+// The fields of a chunk's segment descriptor the consumers use, copied by
+// the producer (one 8-byte word per lane) so that the consumers find them in
+// shared memory instead of behind two dependent global loads.
+struct SegCopy {
+    int64_t win[2 * kRmax];        // region windows
+    int64_t cin[3];                // carry_in: largest kernel / memory end, last start of earlier ingests
+    int64_t* sums;
+    uint32_t* status;
+    int64_t* cout;                 // carry_out
+    int64_t R;                     // regions
+    int64_t seg;                   // segment index (ctl->list[k])
+    const uint8_t* tag;
+    const int64_t* se;
+};
+constexpr int kSegCopyWords = 2 * kRmax + 10;
+static_assert(sizeof(SegCopy) == 8 * kSegCopyWords, "one 8-byte word per field");
+static_assert(kSegCopyWords <= 32, "one word per producer lane");
+
 // per-chunk description written by the producer for the consumers
 struct ChunkMeta {
     uint64_t g;                    // global chunk index
@@ -69,16 +87,21 @@ struct ChunkMeta {
     uint32_t tpos[kMaxRuns];       // tag-area index of each range's first tag
     uint32_t direct[kMaxRuns];     // first range index whose tag the bulk copy does not cover
     uint64_t lo[kMaxRuns];         // position of each range in its run's segment
+    SegCopy sd;                    // its segment's descriptor fields
 };
 
 struct __align__(16) FmsStage {
     longlong2 rows[kFmsChunk];
     uint8_t tags[kFmsTagBytes];    // per run: the 16-byte aligned superset of its tags
-    ChunkMeta meta;
 };
 
 struct FmsShared {
     FmsStage st[kFmsStages];
+    // chunk descriptions, two deep: the consumers hand the stage back as soon
+    // as they no longer read its rows and tags (after the chunk's aggregate
+    // on the 32-bit path), and the producer then fills the stage and the
+    // other description while they merge and sweep
+    ChunkMeta meta[2];
     // the chunk the consumers work on: merged order (two index buffers for
     // the merge rounds), and every record's tag, start and end in staging
     // order (start and end as 32-bit offsets from the chunk's smallest start,
@@ -643,6 +666,7 @@ __global__ void __launch_bounds__(kFmsThreads, 3)
         uint64_t dn = 0;
         uint32_t given = 0;
         bool first = false;
+        int64_t sdw = 0;   // this lane's word of the segment copy (SegCopy order)
         for (uint32_t it = 0;; ++it) {
             const int s = static_cast<int>(it % kFmsStages);
             if (it >= static_cast<uint32_t>(kFmsStages)) {
@@ -654,6 +678,7 @@ __global__ void __launch_bounds__(kFmsThreads, 3)
                 }
             }
             FmsStage& S = sh.st[s];
+            ChunkMeta& MT = sh.meta[it & 1];
             // ---- the next chunk, and its segment's descriptor when it changes
             bool more = true, fresh = false;
             int64_t TK = NEG_INF, TM = NEG_INF, LK = NEG_INF, LM = NEG_INF;
@@ -693,13 +718,23 @@ __global__ void __launch_bounds__(kFmsThreads, 3)
             }
             if (!more) {
                 if (lane == 0) {
-                    S.meta.valid = 0;
+                    MT.valid = 0;
                     mbar_arrive(&sh.full[s]);
                 }
                 break;
             }
             if (fresh) {
-                const SegDesc& d = segs[ctl->list[k]];
+                const uint32_t sid = ctl->list[k];
+                const SegDesc& d = segs[sid];
+                if (lane < 2 * kRmax) sdw = lane < 2 * static_cast<int>(d.R) ? d.win[lane] : 0;
+                else if (lane < 2 * kRmax + 3) sdw = d.carry_in[lane - 2 * kRmax];
+                else if (lane == 2 * kRmax + 3) sdw = reinterpret_cast<int64_t>(d.sums);
+                else if (lane == 2 * kRmax + 4) sdw = reinterpret_cast<int64_t>(d.status);
+                else if (lane == 2 * kRmax + 5) sdw = reinterpret_cast<int64_t>(d.carry_out);
+                else if (lane == 2 * kRmax + 6) sdw = d.R;
+                else if (lane == 2 * kRmax + 7) sdw = sid;
+                else if (lane == 2 * kRmax + 8) sdw = reinterpret_cast<int64_t>(d.tag);
+                else if (lane == 2 * kRmax + 9) sdw = reinterpret_cast<int64_t>(d.se);
                 dse = d.se;
                 dtag = d.tag;
                 lim = reinterpret_cast<uintptr_t>(d.tag_limit);
@@ -758,34 +793,35 @@ __global__ void __launch_bounds__(kFmsThreads, 3)
                     const uint32_t why = given ? ST_UNSORTED : ST_TIMEOUT;
                     if (!given) atomicOr(gstatus, ST_TIMEOUT);
                     atomicOr(segs[ctl->list[k]].status, why);
-                    S.meta.valid = 0;
+                    MT.valid = 0;
                     mbar_arrive(&sh.full[s]);
                 }
                 break;
             }
             if (lane < static_cast<int>(nr)) {
-                S.meta.roff[lane] = ro;
-                S.meta.tpos[lane] = to + static_cast<uint32_t>(A & 15u);
-                S.meta.direct[lane] = direct;
-                S.meta.lo[lane] = lo;
+                MT.roff[lane] = ro;
+                MT.tpos[lane] = to + static_cast<uint32_t>(A & 15u);
+                MT.direct[lane] = direct;
+                MT.lo[lane] = lo;
             }
+            if (lane < kSegCopyWords) reinterpret_cast<int64_t*>(&MT.sd)[lane] = sdw;
             if (lane == 0) {
-                S.meta.roff[nr] = n_tot;
-                S.meta.g = g;
-                S.meta.sc = sc;
-                S.meta.k = k;
-                S.meta.c = c;
-                S.meta.nr = nr;
-                S.meta.n = n_tot;
-                S.meta.valid = 1;
-                S.meta.first = FIX ? 0u : (first ? 1u : 0u);
-                S.meta.last = FIX ? 0u : (g + 1 == g_end ? 1u : 0u);
-                S.meta.seg_first = FIX ? 0u : (sc == scb ? 1u : 0u);
-                S.meta.given = given;
-                S.meta.LK = LK;
-                S.meta.LM = LM;
-                S.meta.TK = TK;
-                S.meta.TM = TM;
+                MT.roff[nr] = n_tot;
+                MT.g = g;
+                MT.sc = sc;
+                MT.k = k;
+                MT.c = c;
+                MT.nr = nr;
+                MT.n = n_tot;
+                MT.valid = 1;
+                MT.first = FIX ? 0u : (first ? 1u : 0u);
+                MT.last = FIX ? 0u : (g + 1 == g_end ? 1u : 0u);
+                MT.seg_first = FIX ? 0u : (sc == scb ? 1u : 0u);
+                MT.given = given;
+                MT.LK = LK;
+                MT.LM = LM;
+                MT.TK = TK;
+                MT.TM = TM;
             }
             __syncwarp();
             // lane 0's arrive releases the meta fields written by every lane
@@ -815,11 +851,11 @@ __global__ void __launch_bounds__(kFmsThreads, 3)
             if (ct == 0) atomicOr(gstatus, ST_TIMEOUT);
             break;
         }
-        const ChunkMeta& M = S.meta;
+        const ChunkMeta& M = sh.meta[it & 1];
         if (!M.valid) break;   // no more chunks
         const uint32_t n = M.n, nr = M.nr;
-        const SegDesc& d = segs[ctl->list[M.k]];
-        const int R = d.R;
+        const SegCopy& d = M.sd;
+        const int R = static_cast<int>(d.R);
         if (ct < 2 * R) sh.win[ct] = d.win[ct];
         if (ct == 0) sh.bad = 0;
         const uint32_t E = items_for(n);
@@ -829,18 +865,24 @@ __global__ void __launch_bounds__(kFmsThreads, 3)
             LK = M.LK;
             LM = M.LM;
         } else if (M.first) {
-            LK = M.seg_first ? d.carry_in[0] : NEG_INF;
-            LM = M.seg_first ? d.carry_in[1] : NEG_INF;
+            LK = M.seg_first ? d.cin[0] : NEG_INF;
+            LM = M.seg_first ? d.cin[1] : NEG_INF;
         } else {
             LK = sh.LK;
             LM = sh.LM;
         }
         const int64_t scK0 = M.first ? NEG_INF : sh.scK, scM0 = M.first ? NEG_INF : sh.scM;
         // tags the bulk copy could not fetch (past the last 16-byte boundary of the array)
+        bool wrote = false;
         for (uint32_t q = 0; q < nr; ++q) {
             const uint32_t rl = M.roff[q + 1] - M.roff[q];
-            for (uint32_t j = M.direct[q] + ct; j < rl; j += kFmsCT) S.tags[M.tpos[q] + j] = d.tag[M.lo[q] + j];
+            for (uint32_t j = M.direct[q] + ct; j < rl; j += kFmsCT) {
+                S.tags[M.tpos[q] + j] = d.tag[M.lo[q] + j];
+                wrote = true;
+            }
         }
+        // the stage's next bulk copies must land after these writes
+        if (wrote) fence_proxy_async_smem();
         cbar();
 
         // ---- aggregate, validation and span of the chunk's records.  Each
@@ -856,12 +898,16 @@ __global__ void __launch_bounds__(kFmsThreads, 3)
             }
         }
         uint32_t bK = 0, bM = 0, hib = 0, bad = 0;
-        {
-            uint32_t q = 0;
-            for (uint32_t i = ct; i < n; i += kFmsCT) {
-                while (i >= M.roff[q + 1]) ++q;
+        const bool given = M.given != 0;
+        for (uint32_t q = 0; q < nr; ++q) {
+            // this thread's records of run q: the staging indexes i == ct
+            // (mod kFmsCT) in [a, b)
+            const uint32_t a = M.roff[q], b = M.roff[q + 1];
+            const uint32_t tp = M.tpos[q] - a;
+            const uint32_t i0 = a + ((static_cast<uint32_t>(ct) + kFmsCT - a % kFmsCT) % kFmsCT);
+            for (uint32_t i = i0; i < b; i += kFmsCT) {
                 const longlong2 v = S.rows[i];
-                const uint32_t tg = S.tags[M.tpos[q] + (i - M.roff[q])];
+                const uint32_t tg = S.tags[tp + i];
                 sh.tagc[i] = static_cast<uint8_t>(tg);
                 bad |= (v.y < v.x) ? ST_BAD_END : 0u;
                 bad |= (tg >= 160u) ? ST_BAD_KIND : 0u;
@@ -872,11 +918,11 @@ __global__ void __launch_bounds__(kFmsThreads, 3)
                 sh.end32[i] = r;
                 // runs from the caller: each must be in start order (runs found
                 // by the min/max pass or the sweep's run log are)
-                if (M.given && i > M.roff[q] && S.rows[i - 1].x > v.x) bad |= ST_UNSORTED;
+                if (given && i > a && S.rows[i - 1].x > v.x) bad |= ST_UNSORTED;
                 if (tg < 32u) bK = umax(bK, r); else bM = umax(bM, r);
             }
         }
-        if (M.given && ct < static_cast<int>(nr) && M.roff[ct + 1] > M.roff[ct] &&
+        if (given && ct < static_cast<int>(nr) && M.roff[ct + 1] > M.roff[ct] &&
             M.lo[ct] > ctl->runs[static_cast<uint64_t>(M.k) * (kMaxRuns + 1) + ct] &&
             d.se[2 * (M.lo[ct] - 1)] > S.rows[M.roff[ct]].x)
             bad |= ST_UNSORTED;   // a given run out of order across the chunk's boundary
@@ -928,7 +974,7 @@ __global__ void __launch_bounds__(kFmsThreads, 3)
         }
         if (FIX) bad = 0;   // reported by the main pass
         // APPEND: the slice starts no earlier than the device's last ingested record
-        if (!FIX && M.c == 0 && s0 < d.carry_in[2]) bad |= ST_UNSORTED;
+        if (!FIX && M.c == 0 && s0 < d.cin[2]) bad |= ST_UNSORTED;
         if (!FIX && ct == 0) {
             FmsChunk& fc = ctl->fms_chunk[M.g];
             fc.aggK = aK;
@@ -951,6 +997,11 @@ __global__ void __launch_bounds__(kFmsThreads, 3)
         const int64_t spanHi = max64(aK, aM);
         const int64_t hiK = FIX ? max64(M.TK, LK) : LK, hiM = FIX ? max64(M.TM, LM) : LM;
         const bool fast = span32 && (hiK <= s0 || ((hiK - s0) >> 32) == 0) && (hiM <= s0 || ((hiM - s0) >> 32) == 0);
+        // the 32-bit path reads only the compact arrays from here on: the
+        // stage goes back to the producer now (every read of it ended at the
+        // barrier after the aggregate)
+        const bool early = fast;
+        if (early && ct == 0) mbar_arrive(&sh.empty[s]);
         const uint16_t* perm = nullptr;
         if (fast) {
             const uint32_t p0 = static_cast<uint32_t>(ct) * E;
@@ -996,14 +1047,14 @@ __global__ void __launch_bounds__(kFmsThreads, 3)
             const uint32_t bits = bad | sh.bad;
             if (bits) {
                 atomicOr(d.status, bits);
-                atomicOr(&seg_flags[ctl->list[M.k]], bits);
+                atomicOr(&seg_flags[d.seg], bits);
             }
             if (!FIX) {
-                atomic_max64(&d.carry_out[0], aK);
-                atomic_max64(&d.carry_out[1], aM);
-                atomic_max64(&d.carry_out[2], mxS);
+                atomic_max64(&d.cout[0], aK);
+                atomic_max64(&d.cout[1], aM);
+                atomic_max64(&d.cout[2], mxS);
             }
-            mbar_arrive(&sh.empty[s]);
+            if (!early) mbar_arrive(&sh.empty[s]);
         }
     }
 }
