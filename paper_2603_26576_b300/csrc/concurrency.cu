@@ -476,12 +476,33 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
         sort8_desc(la.v);
         sort8_desc(lk.v);
         if (__all_sync(0xFFFFFFFFu, fits)) {
-            scan_top(la, lane);
-            scan_top(lk, lane);
-            TopK<uint32_t> xa = shfl_up_top(la, 1), xk = shfl_up_top(lk, 1);
-            if (lane == 0) {
-                clear_top(xa);
-                clear_top(xk);
+            // A lane needs from the lanes before it only the ends still
+            // running at its first start th (a lane without records: at the
+            // next tile's first start).  With pm the largest end of lanes
+            // 0 .. L (kernel ends are among them), lane L looks back at lane
+            // L - d only while pm(L - d) > th: usually the previous lane or
+            // two.  The ends at or before th it skips contribute nothing to
+            // its records, nor to any later lane.
+            const uint32_t aft = rel32(after, s0);
+            const uint32_t th = lane * kItems < n ? s[0] : aft;
+            uint32_t pm = la.v[0];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, pm, d);
+                if (lane >= d) pm = tmax(pm, y);
+            }
+            TopK<uint32_t> xa, xk;
+            clear_top(xa);
+            clear_top(xk);
+            for (int d = 1; d < 32; ++d) {
+                const uint32_t pd = __shfl_up_sync(0xFFFFFFFFu, pm, d);
+                const bool need = lane >= d && pd > th;
+                if (!__any_sync(0xFFFFFFFFu, need)) break;
+                const TopK<uint32_t> ya = shfl_up_top(la, d), yk = shfl_up_top(lk, d);
+                if (need) {
+                    merge_top(xa, ya);
+                    merge_top(xk, yk);
+                }
             }
             merge_top(xa, ta);
             merge_top(xk, tk);
@@ -505,7 +526,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
             for (int k = 0; k < K; ++k) acc_a[k] = acc_k[k] = 0;
             const uint32_t bnd = rel32(dv.b, s0);
             uint32_t nxt = shfl_t(s[0], (lane + 1) & 31);
-            if (lane == 31 || (lane + 1) * kItems >= n) nxt = rel32(after, s0);
+            if (lane == 31 || (lane + 1) * kItems >= n) nxt = aft;
 #pragma unroll
             for (int i = 0; i < kItems; ++i) {
                 const int q = lane * kItems + i;
@@ -551,14 +572,16 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
                     s_acc[K + k] += wk;
                 }
             }
-            // state after the tile: the entering state and every record of it
-            merge_top(la, ta);
-            merge_top(lk, tk);
-            const TopK<uint32_t> na = shfl_top(la, 31), nk = shfl_top(lk, 31);
+            // state after the tile: lane 31's lists after its walk hold every
+            // end still running at its last start (or, without records, at
+            // the next tile's first start), which covers every end running at
+            // the next tile's first start
 #pragma unroll
-            for (int i = 0; i < K; ++i) {
-                ra[i] = na.v[i];
-                rk[i] = nk.v[i];
+            for (int i = 0; i < 4; ++i) {
+                ra[i] = shfl_t(ma[i], 31);
+                ra[4 + i] = shfl_t(oa[i], 31);
+                rk[i] = shfl_t(mk[i], 31);
+                rk[4 + i] = shfl_t(ok[i], 31);
             }
             sbase = s0;
             rel = true;
