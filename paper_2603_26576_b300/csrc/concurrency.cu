@@ -11,10 +11,13 @@
 // so c(t) >= k there iff t < E_k(i), the k-th largest end among records
 // j <= i: the time with c >= k in [s_i, s_{i+1}) is
 //   max(0, min(s_{i+1}, E_k(i)) - s_i).
-// A device's record list is cut into chunks; the top-K ends of each chunk
-// are merged into every later chunk's entering state by a per-device scan,
-// and each chunk then walks its records with a warp-wide scan of top-K
-// lists per tile.  Top-K merges are bitonic (elementwise max against the
+// A device's record list is cut into chunks, each walked tile by tile by one
+// warp.  A main pass walks every chunk as if nothing ran into it and leaves
+// the chunk's exit state (its largest ends still running after its last
+// start); a per-device scan of those gives each chunk its true entering
+// state; a fix-up pass walks again, with both entering states, the leading
+// tiles of the chunks into which earlier ends still run, and adds the
+// difference.  Top-K merges are bitonic (elementwise max against the
 // reversed list, then a bitonic half-cleaner cascade).
 #include "kernels.h"
 
@@ -99,7 +102,6 @@ __device__ __forceinline__ uint32_t shfl_up_t(uint32_t v, int d) { return __shfl
 __device__ __forceinline__ int64_t shfl_up_t(int64_t v, int d) { return shfl_up64(v, d); }
 __device__ __forceinline__ uint32_t shfl_t(uint32_t v, int s) { return __shfl_sync(0xFFFFFFFFu, v, s); }
 __device__ __forceinline__ int64_t shfl_t(int64_t v, int s) { return shfl64(v, s); }
-__device__ __forceinline__ int64_t shfl_xor_t(int64_t v, int m) { return shfl_xor64(v, m); }
 
 template <typename T>
 __device__ __forceinline__ TopK<T> shfl_top(const TopK<T>& x, int src) {
@@ -192,83 +194,6 @@ __device__ __forceinline__ void clipped(const Stage& st, int q, const ConcDev& d
 }
 
 
-// ------------------------------------------------------------- chunk top-K
-// Only the ends still running after the chunk's last (clipped) start matter
-// to later chunks: every later start is at or after it, so an end at or
-// before it can only ever give a zero contribution there.  Each lane takes
-// every 32nd record straight from memory (coalesced), validates it, and
-// keeps the rare ends past that start in its own lists; the warp merges the
-// 32 lists once.  The lists of the scan that follows therefore agree with
-// the full top-K lists on every entry above the next chunk's first start,
-// which is all the levels pass reads of them.
-template <typename T>
-__device__ __forceinline__ void warp_merge_top(TopK<T>& x) {
-#pragma unroll
-    for (int m = 16; m > 0; m >>= 1) {
-        TopK<T> y;
-#pragma unroll
-        for (int i = 0; i < K; ++i) y.v[i] = shfl_xor_t(x.v[i], m);
-        merge_top(x, y);
-    }
-}
-
-__global__ void __launch_bounds__(kWarps * 32) conc_chunk_top(const int64_t* __restrict__ se,
-                                                             const uint8_t* __restrict__ tag,
-                                                             const ConcDev* __restrict__ devs,
-                                                             const ConcChunk* __restrict__ chunks, uint32_t n_chunks,
-                                                             int64_t* __restrict__ top, uint32_t* __restrict__ status) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const uint32_t c = blockIdx.x * kWarps + wid;
-    if (c >= n_chunks) return;
-    const ConcChunk ch = chunks[c];
-    const ConcDev dv = devs[ch.dev];
-    TopK<int64_t> ca, ck;
-    clear_top(ca);
-    clear_top(ck);
-    uint32_t bad = 0;
-    if (ch.n > 0) {
-        // the chunk's last clipped start
-        const int64_t sl = max64(se[2 * (ch.rec0 + ch.n - 1)], dv.a);
-        // four records per lane in flight at a time
-        for (uint32_t q0 = 0; q0 < ch.n; q0 += 4 * 32) {
-            longlong2 r[4];
-            uint32_t kind[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const uint32_t q = q0 + u * 32 + lane;
-                r[u] = make_longlong2(0, 0);
-                kind[u] = 0;
-                if (q < ch.n) {
-                    r[u] = *reinterpret_cast<const longlong2*>(se + 2 * (ch.rec0 + q));
-                    kind[u] = tag[ch.rec0 + q] >> 5;
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                bad |= (r[u].y < r[u].x ? 1u : 0u) | (kind[u] > 4u ? 2u : 0u);
-                // clipped end min(e, b) (at least the clipped start, which is
-                // at most sl, so the test needs no lower clip)
-                const int64_t e = min64(r[u].y, dv.b);
-                if (e > sl) {
-                    insert_top(ca, e);
-                    if (kind[u] == 0u) insert_top(ck, e);
-                }
-            }
-        }
-        warp_merge_top(ca);
-        warp_merge_top(ck);
-    }
-    bad = __reduce_or_sync(0xFFFFFFFFu, bad);
-    if (lane == 0) {
-#pragma unroll
-        for (int i = 0; i < K; ++i) {
-            top[static_cast<uint64_t>(c) * 2 * K + i] = ca.v[i];
-            top[static_cast<uint64_t>(c) * 2 * K + K + i] = ck.v[i];
-        }
-        if (bad) atomicOr(status, bad);
-    }
-}
-
 // --------------------------------------------------- per-device chunk scan
 // Entering state of each chunk: the top-K over all earlier chunks of its
 // device.  One warp per device, 32 chunks at a time: a warp scan of the
@@ -341,12 +266,13 @@ __device__ __forceinline__ void ins4(uint32_t (&x)[4], uint32_t& e) {
     }
 }
 
+template <bool FIX>
 __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_t* __restrict__ se,
                                                                 const uint8_t* __restrict__ tag,
                                                                 const ConcDev* __restrict__ devs,
                                                                 const ConcChunk* __restrict__ chunks,
                                                                 uint32_t n_chunks, const int64_t* __restrict__ in,
-                                                                int64_t* __restrict__ out,
+                                                                int64_t* __restrict__ top, int64_t* __restrict__ out,
                                                                 uint32_t* __restrict__ status) {
     // per warp: two stages (the tile being worked on and the next one in
     // flight), then the level sums and the int64 state of every warp
@@ -356,26 +282,37 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
     unsigned long long* s_acc =
         reinterpret_cast<unsigned long long*>(smem + sizeof(Stage) * 2 * kWarps) + wid * 2 * K;   // level sums
     int64_t* s_st = reinterpret_cast<int64_t*>(smem + sizeof(Stage) * 2 * kWarps) + (kWarps + wid) * 2 * K;
+    unsigned long long* s_acc2 =
+        reinterpret_cast<unsigned long long*>(smem + sizeof(Stage) * 2 * kWarps) + (2 * kWarps + wid) * 2 * K;
     const uint32_t c = blockIdx.x * kWarps + wid;
     if (c >= n_chunks) return;
     const ConcChunk ch = chunks[c];
     const ConcDev dv = devs[ch.dev];
-    if (ch.n > 0) issue_tile(stg[0], se, tag, ch.rec0, static_cast<int>(min(static_cast<uint32_t>(kTile), ch.n)), lane);
-    if (lane < 2 * K) {
-        s_acc[lane] = 0;
-        s_st[lane] = in[static_cast<uint64_t>(c) * 2 * K + lane];   // entering state of the chunk
-    }
-    __syncwarp();
+    // FIX: the largest end running into the chunk (its true entering state is
+    // sorted); a chunk it does not reach past its first start needs nothing
+    const int64_t E1 = FIX ? in[static_cast<uint64_t>(c) * 2 * K] : INT64_MIN;
+    if (FIX && (ch.n == 0 || E1 <= max64(se[2 * ch.rec0], dv.a))) return;
+    uint32_t bad = 0;
     // state before the current tile (warp-uniform): offsets from sbase when
     // rel, else s_st
     bool rel = false;
     int64_t sbase = 0;
     uint32_t ra[K], rk[K];
+    const uint64_t dev_end = dv.rec0 + dv.n;
+    for (int pass = 0; pass < (FIX ? 2 : 1); ++pass) {
+    unsigned long long* acc = pass ? s_acc2 : s_acc;
+    if (ch.n > 0) issue_tile(stg[0], se, tag, ch.rec0, static_cast<int>(min(static_cast<uint32_t>(kTile), ch.n)), lane);
+    if (lane < 2 * K) {
+        acc[lane] = 0;
+        // entering state: none (main pass), the true one (fix-up, pass 0)
+        s_st[lane] = FIX && pass == 0 ? in[static_cast<uint64_t>(c) * 2 * K + lane] : INT64_MIN;
+    }
+    __syncwarp();
+    rel = false;
+    sbase = 0;
 #pragma unroll
     for (int i = 0; i < K; ++i) ra[i] = rk[i] = 0u;
-    uint32_t bad = 0;
     int64_t last_x = INT64_MIN;   // the previous tile's last start (order check)
-    const uint64_t dev_end = dv.rec0 + dv.n;
     for (uint32_t o = 0, t = 0; o < ch.n; o += kTile, ++t) {
         const int n = static_cast<int>(min(static_cast<uint32_t>(kTile), ch.n - o));
         const uint64_t r0 = ch.rec0 + o;
@@ -396,6 +333,11 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
         if (lane == 0) bad |= last_x > x0 ? 4u : 0u;
         last_x = xl;
         const int64_t s0 = max64(x0, dv.a);
+        if (FIX && s0 >= E1) {   // both entering states agree on every end running from here on
+            cp_async_wait<0>();
+            __syncwarp();
+            break;
+        }
         // the entering state as offsets from s0
         TopK<uint32_t> ta, tk;
         bool fits = true;
@@ -440,13 +382,15 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
                 la.v[i] = lk.v[i] = 0u;
                 if (q < n) {
                     const longlong2 r = row_of(S, q);
-                    bad |= prev > r.x ? 4u : 0u;
+                    bad |= (prev > r.x ? 4u : 0u) | (r.y < r.x ? 1u : 0u);
                     prev = r.x;
                     const int64_t de = min64(r.y, dv.b) - s0;
                     hib |= static_cast<uint32_t>(static_cast<uint64_t>(de) >> 32);
                     s[i] = static_cast<uint32_t>(r.x) - static_cast<uint32_t>(s0);
                     e[i] = static_cast<uint32_t>(de);
-                    const bool isK = kind_of(S, toff, q) == 0u;
+                    const uint32_t kd = kind_of(S, toff, q);
+                    bad |= kd > 4u ? 2u : 0u;
+                    const bool isK = kd == 0u;
                     kmask |= isK ? 1u << i : 0u;
                     la.v[i] = e[i];
                     lk.v[i] = isK ? e[i] : 0u;
@@ -462,11 +406,15 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
                 if (q < n) {
                     int64_t sa64, ea64;
                     clipped(S, q, dv, sa64, ea64);
-                    if (q > 0) bad |= row_of(S, q - 1).x > row_of(S, q).x ? 4u : 0u;
+                    const longlong2 r = row_of(S, q);
+                    if (q > 0) bad |= row_of(S, q - 1).x > r.x ? 4u : 0u;
+                    bad |= r.y < r.x ? 1u : 0u;
                     fits &= near32(ea64, s0);
                     s[i] = rel32(sa64, s0);
                     e[i] = rel32(ea64, s0);
-                    const bool isK = kind_of(S, toff, q) == 0u;
+                    const uint32_t kd = kind_of(S, toff, q);
+                    bad |= kd > 4u ? 2u : 0u;
+                    const bool isK = kd == 0u;
                     kmask |= isK ? 1u << i : 0u;
                     la.v[i] = e[i];
                     lk.v[i] = isK ? e[i] : 0u;
@@ -568,8 +516,8 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
                 const uint32_t wa = __reduce_add_sync(0xFFFFFFFFu, acc_a[k] - sub);
                 const uint32_t wk = __reduce_add_sync(0xFFFFFFFFu, acc_k[k] - sub);
                 if (lane == 0) {
-                    s_acc[k] += wa;
-                    s_acc[K + k] += wk;
+                    acc[k] += wa;
+                    acc[K + k] += wk;
                 }
             }
             // state after the tile: lane 31's lists after its walk hold every
@@ -614,8 +562,8 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
                     const int64_t hi = min64(ns, dv.b);
 #pragma unroll
                     for (int k = 0; k < K; ++k) {
-                        s_acc[k] += static_cast<unsigned long long>(max64(min64(hi, max64(sa.v[k], sq)) - sq, 0));
-                        s_acc[K + k] +=
+                        acc[k] += static_cast<unsigned long long>(max64(min64(hi, max64(sa.v[k], sq)) - sq, 0));
+                        acc[K + k] +=
                             static_cast<unsigned long long>(max64(min64(hi, max64(sk.v[k], sq)) - sq, 0));
                     }
                 }
@@ -629,12 +577,29 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
         }
         __syncwarp();
     }
-    if (ch.n > 0 && ch.rec0 > dv.rec0 && lane == 0) bad |= se[2 * (ch.rec0 - 1)] > se[2 * ch.rec0] ? 4u : 0u;
+    }   // passes
+    if (!FIX && ch.n > 0 && ch.rec0 > dv.rec0 && lane == 0) bad |= se[2 * (ch.rec0 - 1)] > se[2 * ch.rec0] ? 4u : 0u;
     bad = __reduce_or_sync(0xFFFFFFFFu, bad);
     __syncwarp();
     if (lane < 2 * K) {
-        const int64_t v = static_cast<int64_t>(s_acc[lane]);
+        // main pass: the level sums with no entering state, and the state
+        // after the chunk for the per-device scan; fix-up: the difference the
+        // true entering state makes
+        const int64_t v = FIX ? static_cast<int64_t>(s_acc[lane] - s_acc2[lane]) : static_cast<int64_t>(s_acc[lane]);
         if (v) atomic_add64(&out[static_cast<uint64_t>(ch.dev) * 2 * K + lane], v);
+        if (!FIX) {
+            int64_t x = s_st[lane];
+            if (rel) {
+                uint32_t r = 0;
+#pragma unroll
+                for (int i = 0; i < K; ++i) {
+                    r = lane == i ? ra[i] : r;
+                    r = lane == K + i ? rk[i] : r;
+                }
+                x = r ? sbase + static_cast<int64_t>(r) : INT64_MIN;
+            }
+            top[static_cast<uint64_t>(c) * 2 * K + lane] = x;
+        }
     }
     if (lane == 0 && bad) atomicOr(status, bad);
 }
@@ -646,17 +611,23 @@ cudaError_t launch_concurrency(const int64_t* se, const uint8_t* tag, const Conc
                                uint32_t* status, cudaStream_t stream) {
     if (n_chunks == 0) return cudaSuccess;
     const uint32_t blocks = (n_chunks + kWarps - 1) / kWarps;
-    constexpr int kSmem = static_cast<int>(sizeof(Stage)) * 2 * kWarps + 2 * kWarps * 2 * K * 8;
+    constexpr int kSmem = static_cast<int>(sizeof(Stage)) * 2 * kWarps + 3 * kWarps * 2 * K * 8;
     static bool attr_set = false;   // set once per process, before the first launch
     if (!attr_set) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(conc_chunk_levels, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        cudaError_t e = cudaFuncSetAttribute(conc_chunk_levels<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(conc_chunk_levels<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    conc_chunk_top<<<blocks, kWarps * 32, 0, stream>>>(se, tag, devs, chunks, n_chunks, top, status);
+    // main pass (no entering state; each chunk's state after it into top),
+    // per-device scan (top -> in), fix-up of the chunks' leading tiles
+    conc_chunk_levels<false><<<blocks, kWarps * 32, kSmem, stream>>>(se, tag, devs, chunks, n_chunks, nullptr, top,
+                                                                     out, status);
     conc_chunk_scan<<<(n_dev + kScanWarps - 1) / kScanWarps, kScanWarps * 32, 0, stream>>>(devs, n_dev, top, in);
-    conc_chunk_levels<<<blocks, kWarps * 32, kSmem, stream>>>(se, tag, devs, chunks, n_chunks, in, out, status);
+    conc_chunk_levels<true><<<blocks, kWarps * 32, kSmem, stream>>>(se, tag, devs, chunks, n_chunks, in, nullptr,
+                                                                    out, status);
     return cudaGetLastError();
 }
 

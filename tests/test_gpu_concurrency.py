@@ -62,6 +62,31 @@ def test_high_concurrency_across_tiles_and_chunks(ctx, seed):
         np.testing.assert_array_equal(ctx.concurrency(t, r, arrays=arr), want, err_msg=str((seed, r)))
 
 
+def test_long_records_running_into_later_chunks(ctx):
+    """Records that start just before a chunk boundary (every 16384 records)
+    or at the very start and run over many tiles of the chunks after it: the
+    chunks' leading tiles are walked again with their true entering state."""
+    rng = np.random.default_rng(11)
+    n = 50000
+    gaps = rng.integers(1, 40, n)
+    s = np.cumsum(gaps).astype(np.int64)
+    e = s + rng.integers(1, 60, n)
+    for p, length in [(0, 10 ** 9), (16380, 300000), (16383, 50000), (32760, 200), (32767, 5_000_000),
+                      (40000, 700000)]:
+        e[p] = s[p] + length
+    kind = rng.integers(0, 2, n).astype(np.uint8)
+    kind[[16380, 32767]] = 0
+    kind[16383] = 1
+    base = dict(trace_id=4, n_ranks=1, devices_per_rank=np.array([1], np.uint32),
+                region_window=np.array([[[0, int(e.max()) + 5]], [[int(s[20000]), int(s[45000])]]], np.int64),
+                host_se=np.zeros((0, 2), np.int64), host_state=np.zeros(0, np.uint8),
+                host_off=np.array([0, 0], np.uint64))
+    t = tg.Trace(dev_se=np.stack([s, e], 1), dev_tag=(kind << 5).astype(np.uint8),
+                 dev_off=np.array([0, n], np.uint64), **base)
+    for r in range(2):
+        np.testing.assert_array_equal(ctx.concurrency(t, r), oracle.concurrency(t, r, 8), err_msg=str(r))
+
+
 def test_level_one_is_the_union(ctx):
     t = tg.random_trace(7, trace_id=7, n_ranks=2, devices_per_rank=3, dev_events=30000, host_events=100,
                         n_regions=3)
