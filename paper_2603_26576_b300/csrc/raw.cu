@@ -166,6 +166,7 @@ __global__ void __launch_bounds__(kRawThreads) raw_scatter_kernel(const RawTile*
                                                                   int64_t* __restrict__ lse, uint8_t* __restrict__ ltag,
                                                                   uint32_t* __restrict__ status, int64_t wait_limit) {
     __shared__ uint32_t cnt[kRawThreads / 32][kBuckets];
+    __shared__ uint64_t s_offs[kBuckets];   // the tile's lane offset of every bucket
     // the tile's 16-byte rows, brought in by one bulk copy while the tile is ranked
     __shared__ __align__(16) longlong2 rows[kRawTile];
     __shared__ __align__(8) uint64_t bar;
@@ -185,6 +186,7 @@ __global__ void __launch_bounds__(kRawThreads) raw_scatter_kernel(const RawTile*
             tma_load_1d(rows, tl.se, tl.n * 16u, &bar);
         }
         for (int q = threadIdx.x; q < (kRawThreads / 32) * kBuckets; q += kRawThreads) (&cnt[0][0])[q] = 0;
+        for (int q = threadIdx.x; q < kBuckets; q += kRawThreads) s_offs[q] = offs[static_cast<uint64_t>(t) * kBuckets + q];
         __syncthreads();
         const uint32_t w0 = wid * (kRawTile / (kRawThreads / 32));
         uint32_t bk[kRawItems], rnk[kRawItems];
@@ -236,7 +238,7 @@ __global__ void __launch_bounds__(kRawThreads) raw_scatter_kernel(const RawTile*
         for (int r = 0; r < kRawItems; ++r) {
             if (ok[r]) {
                 const uint32_t q = w0 + r * 32 + lane;
-                const uint64_t o = offs[static_cast<uint64_t>(t) * kBuckets + bk[r]] + cnt[wid][bk[r]] + rnk[r];
+                const uint64_t o = s_offs[bk[r]] + cnt[wid][bk[r]] + rnk[r];
                 *reinterpret_cast<longlong2*>(lse + 2 * o) = rows[q];
                 ltag[o] = tv[r];
             }
