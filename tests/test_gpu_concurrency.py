@@ -87,6 +87,21 @@ def test_long_records_running_into_later_chunks(ctx):
         np.testing.assert_array_equal(ctx.concurrency(t, r), oracle.concurrency(t, r, 8), err_msg=str(r))
 
 
+@pytest.mark.parametrize("scale,offset", [(1 << 9, 0), (1 << 16, 0), (7, 1 << 61)])
+def test_multi_chunk_wide_timestamps(ctx, scale, offset):
+    """Devices of several chunks with timestamps stretched so that tiles span
+    2^32 ns or more (the int64 walk, and the state kept in int64 between
+    tiles), or shifted near 2^61: the main pass, the chunk scan and the
+    fix-up of the chunks' leading tiles against the oracle."""
+    t = tg.random_trace(5, trace_id=5, n_ranks=2, devices_per_rank=[1, 2], dev_events=[40000, 17000, 33000],
+                        host_events=[10, 10], n_regions=3)
+    t = tg.rescale_time(t, scale, offset)
+    arr = _dev(t)
+    for r in range(t.n_regions):
+        np.testing.assert_array_equal(ctx.concurrency(t, r, arrays=arr), oracle.concurrency(t, r, 8),
+                                      err_msg=str((scale, r)))
+
+
 def test_level_one_is_the_union(ctx):
     t = tg.random_trace(7, trace_id=7, n_ranks=2, devices_per_rank=3, dev_events=30000, host_events=100,
                         n_regions=3)
