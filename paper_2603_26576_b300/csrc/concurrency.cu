@@ -313,12 +313,21 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
 #pragma unroll
     for (int i = 0; i < K; ++i) ra[i] = rk[i] = 0u;
     int64_t last_x = INT64_MIN;   // the previous tile's last start (order check)
+    // start of the record after a tile (clipped), or none: loaded one tile
+    // ahead, so that its latency hides behind a tile's work
+    int64_t after_nx = INT64_MAX;
+    {
+        const uint64_t p = ch.rec0 + min(static_cast<uint32_t>(kTile), ch.n);
+        if (p < dev_end) after_nx = max64(se[2 * p], dv.a);
+    }
     for (uint32_t o = 0, t = 0; o < ch.n; o += kTile, ++t) {
         const int n = static_cast<int>(min(static_cast<uint32_t>(kTile), ch.n - o));
         const uint64_t r0 = ch.rec0 + o;
-        // start of the record after the tile (clipped), or none
-        int64_t after = INT64_MAX;
-        if (r0 + n < dev_end) after = max64(se[2 * (r0 + n)], dv.a);
+        const int64_t after = after_nx;
+        if (o + kTile < ch.n) {
+            const uint64_t p = r0 + kTile + min(static_cast<uint32_t>(kTile), ch.n - o - kTile);
+            after_nx = p < dev_end ? max64(se[2 * p], dv.a) : INT64_MAX;
+        }
         if (o + kTile < ch.n) {
             issue_tile(stg[(t + 1) & 1], se, tag, r0 + kTile,
                        static_cast<int>(min(static_cast<uint32_t>(kTile), ch.n - o - kTile)), lane);
@@ -375,26 +384,28 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
         if (plain) {
             uint32_t hib = 0;
             int64_t prev = lane > 0 ? row_of(S, lane * kItems - 1).x : x0;
+            // record i of the lane (q = its tile index)
+            auto item = [&](int i, int q) {
+                const longlong2 r = row_of(S, q);
+                bad |= (prev > r.x ? 4u : 0u) | (r.y < r.x ? 1u : 0u);
+                prev = r.x;
+                const int64_t de = min64(r.y, dv.b) - s0;
+                hib |= static_cast<uint32_t>(static_cast<uint64_t>(de) >> 32);
+                s[i] = static_cast<uint32_t>(r.x) - static_cast<uint32_t>(s0);
+                e[i] = static_cast<uint32_t>(de);
+                const uint32_t kd = kind_of(S, toff, q);
+                bad |= kd > 4u ? 2u : 0u;
+                const bool isK = kd == 0u;
+                kmask |= isK ? 1u << i : 0u;
+                la.v[i] = e[i];
+                lk.v[i] = isK ? e[i] : 0u;
+            };
 #pragma unroll
             for (int i = 0; i < kItems; ++i) {
                 const int q = lane * kItems + i;
                 s[i] = e[i] = 0xFFFFFFFFu;
                 la.v[i] = lk.v[i] = 0u;
-                if (q < n) {
-                    const longlong2 r = row_of(S, q);
-                    bad |= (prev > r.x ? 4u : 0u) | (r.y < r.x ? 1u : 0u);
-                    prev = r.x;
-                    const int64_t de = min64(r.y, dv.b) - s0;
-                    hib |= static_cast<uint32_t>(static_cast<uint64_t>(de) >> 32);
-                    s[i] = static_cast<uint32_t>(r.x) - static_cast<uint32_t>(s0);
-                    e[i] = static_cast<uint32_t>(de);
-                    const uint32_t kd = kind_of(S, toff, q);
-                    bad |= kd > 4u ? 2u : 0u;
-                    const bool isK = kd == 0u;
-                    kmask |= isK ? 1u << i : 0u;
-                    la.v[i] = e[i];
-                    lk.v[i] = isK ? e[i] : 0u;
-                }
+                if (q < n) item(i, q);
             }
             fits &= hib == 0;
         } else {
@@ -510,16 +521,18 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
                     }
                 }
             }
+            // lane k < 2K adds level sum k (one shared-memory update per lane,
+            // side by side)
+            uint32_t mine = 0;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 const uint32_t sub = k < 4 ? S : SH;
                 const uint32_t wa = __reduce_add_sync(0xFFFFFFFFu, acc_a[k] - sub);
                 const uint32_t wk = __reduce_add_sync(0xFFFFFFFFu, acc_k[k] - sub);
-                if (lane == 0) {
-                    acc[k] += wa;
-                    acc[K + k] += wk;
-                }
+                mine = lane == k ? wa : mine;
+                mine = lane == K + k ? wk : mine;
             }
+            if (lane < 2 * K) acc[lane] += mine;
             // state after the tile: lane 31's lists after its walk hold every
             // end still running at its last start (or, without records, at
             // the next tile's first start), which covers every end running at
