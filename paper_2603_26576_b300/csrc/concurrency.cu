@@ -257,13 +257,17 @@ __global__ void __launch_bounds__(kScanWarps * 32) conc_chunk_scan(const ConcDev
 // 4 push it out while it is still running at the record's start (a
 // concurrency of 5 or more, rare); levels 5-8 are added only for records at
 // which some lane of the warp has such an end.
+// Insertion of e into a sorted-descending list of 4, e left as the value
+// pushed out.  Entry k of the result is max(x[k], min(x[k-1], e)) -- x[k]
+// above e's place, e at it, x[k-1] below it -- so all four come out in two
+// dependent steps instead of a chain through the list.
 __device__ __forceinline__ void ins4(uint32_t (&x)[4], uint32_t& e) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const uint32_t hi = tmax(x[i], e);
-        e = tmin(x[i], e);
-        x[i] = hi;
-    }
+    const uint32_t out = tmin(x[3], e);
+    x[3] = tmax(x[3], tmin(x[2], e));
+    x[2] = tmax(x[2], tmin(x[1], e));
+    x[1] = tmax(x[1], tmin(x[0], e));
+    x[0] = tmax(x[0], e);
+    e = out;
 }
 
 template <bool FIX>
