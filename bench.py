@@ -24,6 +24,14 @@ roofline: the sweep kernel (the dominant kernel) against the measured HBM
           record / its CUDA-event duration);
 cpu_baseline: the CPU oracle on a bounded one-rank sample of the workload.
 
+The default command's line also carries sub-objects measured in the same
+run: `serving` and `serving_plain` (the served form and the plain form at
+the serving load: p50/p99 query latency), `batched` (the small-trace batched
+form against one trace per launch), `sort_stage` (the same trace with each
+device's records grouped by stream, sorted by the library), `concurrency`
+(the concurrency profile of its devices) and `raw` (the trace at 25% as raw
+activity-record buffers), each with its own exactness check and clocks.
+
 --impl reference times the CPU oracle itself (the slow, plain statement of
 the method) on a bounded sample per step; it is the reference arm.
 
@@ -613,15 +621,23 @@ def run_batched_full(a):
 
 
 def run_concurrency(a):
+    line = measure_concurrency(a)
+    print(json.dumps(line), flush=True)
+    return 0 if line["config"]["bit_exact_rank0_vs_oracle"] else 1
+
+
+def measure_concurrency(a, t=None):
     """Concurrency profile (time with >= k active records per device, k =
     1..8, all kinds and kernels only) of the plain large trace's devices, one
-    call per step through the C ABI with the records resident in HBM."""
+    call per step through the C ABI with the records resident in HBM (`t`:
+    the trace, when the caller has generated it already)."""
     import torch
     import oracle
     import paper_2603_26576_b300 as P
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    t = tg.plain_large(scale=a.scale)
+    if t is None:
+        t = tg.plain_large(scale=a.scale)
     arr = dict(host_se=torch.from_numpy(t.host_se).to(dev), host_state=torch.from_numpy(t.host_state).to(dev),
                dev_se=torch.from_numpy(t.dev_se).to(dev), dev_tag=torch.from_numpy(t.dev_tag).to(dev))
     b, keep = P.batch_from_arrays(t.trace_id, t.devices_per_rank, t.region_window, arr["host_se"],
@@ -667,19 +683,28 @@ def run_concurrency(a):
                    "l2": "records (%.1f GB) larger than L2; no flush" % (BYTES_PER_RECORD * N / 1e9),
                    "bit_exact_rank0_vs_oracle": exact},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "chunk top-K + per-device scan + levels (the records are read twice)",
+                     "traffic": None,
+                     "kernel": "main levels pass + per-device chunk scan + fix-up of chunks' leading tiles (every "
+                               "record read once; the fix-up rereads a few tiles)",
                      "kernel_ms": ms, "peak_source": f"{peak_kind} hbm_gbs"},
         "cpu_baseline": {"value": s0.n_records / cpu_s if cpu_s else None, "unit": UNIT, "cores": 1,
                          "kind": "oracle", "sample": f"rank 0's 4 devices ({int(s0.dev_se.shape[0])} records), "
                                                      f"{cpu_s:.2f} s"},
         "e2e": None, "gpu_launches": launches, "clocks": ck,
     }
-    print(json.dumps(line), flush=True)
     ctx.close()
-    return 0 if exact else 1
+    del arr, b, keep
+    torch.cuda.empty_cache()
+    return line
 
 
 def run_raw(a):
+    line = measure_raw(a)
+    print(json.dumps(line), flush=True)
+    return 0 if line["config"]["bit_exact_raw_vs_lanes"] else 1
+
+
+def measure_raw(a):
     """Raw activity records: the plain trace's device records as per-rank
     delivery buffers (all devices and streams interleaved in completion
     order), ingested through talp_gpu_ingest_raw from HBM and reduced, one
@@ -782,9 +807,10 @@ def run_raw(a):
                          "kind": "oracle", "sample": f"one rank of the workload, {cpu_s:.2f} s"},
         "e2e": None, "gpu_launches": launches, "clocks": ck,
     }
-    print(json.dumps(line), flush=True)
     ctx.close()
-    return 0 if same else 1
+    del arr, lanes, rb, keep, lb, keep2, hold_batches
+    torch.cuda.empty_cache()
+    return line
 
 
 def run_threads(a):
@@ -1353,7 +1379,7 @@ def main():
             del h_arrays, batch_h, keep_h
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
-        extra = default_extras(a)
+        extra = default_extras(a, t, res)
         rc = extra.pop("_rc")
         line.update(extra)
     if rank == 0:
@@ -1363,10 +1389,79 @@ def main():
     return rc
 
 
-def default_extras(a):
+def measure_sort_stage(a, t, want):
+    """The plain large trace `t` with each device's records grouped by stream
+    (each stream in start order, as per-stream activity buffers deliver them):
+    the library finds the devices out of order and sorts them (the sort
+    stage: runs found by the first sweep, merged and swept in one pass by the
+    fused merge-sweep).  Same step as the plain leg (ingest + metrics of every
+    region); the results must equal `want`, the start-ordered run's."""
+    import torch
+    import paper_2603_26576_b300 as P
+    dev = torch.device("cuda", 0)
+    u = tg.interleave_lanes(t)
+    arr = {k: torch.from_numpy(getattr(u, k)).to(dev) for k in ("host_se", "host_state", "dev_se", "dev_tag")}
+    b, keep = P.batch_from_arrays(u.trace_id, u.devices_per_rank, u.region_window, arr["host_se"], arr["host_state"],
+                                  u.host_off, arr["dev_se"], arr["dev_tag"], u.dev_off, 0)
+    R = u.n_regions
+    ctx = P.Context(0)
+    stream = torch.cuda.Stream()
+    out_dev = torch.empty(R * 200, dtype=torch.uint8, device=dev)
+
+    def step():
+        P.talp_gpu_ingest_events(ctx.ctx, [b], stream)
+        P.talp_gpu_region_metrics_device(ctx.ctx, [u.trace_id], P.TALP_GPU_ALL_REGIONS, out_dev.data_ptr(), stream)
+
+    clocks = Clocks(0)
+    clocks.start()
+    warm_until(step, 3)
+    got = P.talp_gpu_region_metrics(ctx.ctx, u.trace_id, P.TALP_GPU_ALL_REGIONS, stream, n_regions=R)
+    same = all(P.metrics_to_dict(x) == P.metrics_to_dict(y) for x, y in zip(got, want))
+    step()
+    P.talp_gpu_profile(ctx.ctx, True)
+    P.talp_gpu_profile_read(ctx.ctx)
+    l0 = P.talp_gpu_profile_read(ctx.ctx)["kernel_launches"]
+    k = 10
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(k):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1) / k
+    prof = P.talp_gpu_profile_read(ctx.ctx)
+    P.talp_gpu_profile(ctx.ctx, False)
+    sort_ms = prof["sort_ms"] / max(1, prof["sort_launches"])
+    sweep_ms = prof["sweep_ms"] / max(1, prof["sweep_launches"])
+    n_dev = int(u.dev_off[-1])
+    N = u.n_records
+    peak, peak_kind = measured_peaks()
+    achieved = BYTES_PER_RECORD * n_dev / (sort_ms / 1000.0) / 1e9
+    ctx.close()
+    del arr, b, keep
+    torch.cuda.empty_cache()
+    return {
+        "workload": "the plain large trace with each device's records grouped by stream (each stream in start "
+                    "order), sorted by the library", "records_per_step": N, "steps": k, "ms_per_step": ms,
+        "events_per_s": N / (ms / 1000.0),
+        "sort_stage": {"ms": sort_ms, "device_records": n_dev, "first_sweep_ms": sweep_ms,
+                       "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                    "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
+                                    "kernel": "sort stage (run finding, talp::fms_kernel and its plan and fix-up "
+                                              "kernels), 17 B per device record"}},
+        "bit_exact_vs_start_ordered": same,
+        "gpu_launches": prof["kernel_launches"] - l0, "clocks": ck}
+
+
+def default_extras(a, t=None, want=None):
     """Sub-objects of the default bench line: the served form and the plain
-    form at the serving load (the p50/p99 query latency of the metric), and
-    the batched form against one trace per launch."""
+    form at the serving load (the p50/p99 query latency of the metric), the
+    batched form against one trace per launch, and, on the plain trace `t`
+    (results `want`), the sort stage, the concurrency profile and (at 25%)
+    the raw activity-record adapter."""
     import copy
     sv = copy.copy(a)
     sv.warmup, sv.steps, sv.step_s, sv.sat_s, sv.plain_s = 2, 10, 1.0, 0.0, 10.0
@@ -1408,6 +1503,27 @@ def default_extras(a):
     ok = (out["serving"]["bit_exact_sampled_vs_oracle"] and out["serving_plain"]["bit_exact_sampled_vs_oracle"]
           and not out["serving"]["errors"] and out["batched"]["bit_exact_sampled_vs_oracle"]
           and out["batched"]["bit_exact_batched_vs_plain"])
+    if t is not None:
+        out["sort_stage"] = measure_sort_stage(a, t, want)
+        cv = copy.copy(a)
+        cv.steps, cv.warmup, cv.scale = 5, 3, 1.0
+        C = measure_concurrency(cv, t)
+        out["concurrency"] = {
+            "workload": C["config"]["workload"], "records_per_call": C["config"]["records_per_step"],
+            "ms_per_call": C["ms_per_step"], "records_per_s": C["value"], "roofline_frac": C["roofline"]["frac"],
+            "bit_exact_rank0_vs_oracle": C["config"]["bit_exact_rank0_vs_oracle"],
+            "gpu_launches": C["gpu_launches"], "clocks": C["clocks"]}
+        rv = copy.copy(a)
+        rv.steps, rv.warmup, rv.scale, rv.hold_calls = 10, 3, 0.25, 1
+        W = measure_raw(rv)
+        out["raw"] = {
+            "workload": W["config"]["workload"], "records_per_step": W["config"]["records_per_step"],
+            "ms_per_step": W["ms_per_step"], "events_per_s": W["value"],
+            "lanes_in_start_order_ms_per_step": W["config"]["lanes_in_start_order_ms_per_step"],
+            "roofline_frac": W["roofline"]["frac"], "bit_exact_raw_vs_lanes": W["config"]["bit_exact_raw_vs_lanes"],
+            "gpu_launches": W["gpu_launches"], "clocks": W["clocks"]}
+        ok = (ok and out["sort_stage"]["bit_exact_vs_start_ordered"]
+              and out["concurrency"]["bit_exact_rank0_vs_oracle"] and out["raw"]["bit_exact_raw_vs_lanes"])
     out["_rc"] = 0 if ok else 1
     return out
 
