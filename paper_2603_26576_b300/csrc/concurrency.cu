@@ -245,8 +245,10 @@ __global__ void __launch_bounds__(kScanWarps * 32) conc_chunk_scan(const ConcDev
 }
 
 // ------------------------------------------------------------- levels
-// The state carried from tile to tile (the top-K ends of everything before
-// the tile) is kept as 32-bit offsets from the previous tile's first start
+// The state carried from tile to tile (the K largest ends before the tile
+// that may still be running at its start; ends known to have finished may
+// be missing, as they add nothing) is kept as 32-bit offsets from the
+// previous tile's first start
 // and rebased on the next tile's with one max and one subtraction per entry
 // (an entry at or before the new base becomes 0: no later start can use
 // it).  Only when a tile had to take the int64 path does the state live as
