@@ -86,6 +86,9 @@ def parse():
     ap.add_argument("--plain-s", type=float, default=3.0, help="serving: seconds of the plain-form phase")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grouped-hint", action="store_true",
+                    help="with --unsorted: pass TALP_GPU_GROUPED_BY_STREAM (the caller states its device records come "
+                         "grouped by stream, each group in start order)")
     ap.add_argument("--not-sorted-hint", action="store_true",
                     help="with --unsorted: pass TALP_GPU_NOT_SORTED (the caller knows its records are out of order)")
     ap.add_argument("--unsorted", action="store_true",
@@ -1231,7 +1234,10 @@ def main():
     torch.cuda.synchronize()
     ctx = P.Context(local)
     stream = torch.cuda.Stream(device=dev)
-    flags = (P.TALP_GPU_NOT_SORTED if a.not_sorted_hint else 0) if a.unsorted else P.TALP_GPU_SORTED_BY_START
+    if a.unsorted:
+        flags = P.TALP_GPU_GROUPED_BY_STREAM if a.grouped_hint else (P.TALP_GPU_NOT_SORTED if a.not_sorted_hint else 0)
+    else:
+        flags = P.TALP_GPU_SORTED_BY_START
     batch_d, keep_d = P.batch_from_arrays(t.trace_id, t.devices_per_rank, t.region_window, d_arrays["host_se"],
                                           d_arrays["host_state"], t.host_off, d_arrays["dev_se"],
                                           d_arrays["dev_tag"], t.dev_off, flags)
@@ -1356,7 +1362,10 @@ def main():
                        "regions": R, "l2": "inputs (%.1f GB) larger than L2; no flush" % (BYTES_PER_RECORD * N / 1e9),
                        "input_order": ((f"each device's records dealt into {a.runs} sorted runs laid end to end"
                                         if a.runs > 0 else "device records grouped by stream, each stream in start "
-                                        "order") + ("; caller hint TALP_GPU_NOT_SORTED: every device is sorted "
+                                        "order") + ("; caller flag TALP_GPU_GROUPED_BY_STREAM: each device's runs "
+                                                    "found from its stream ids, merged without a first sweep"
+                                                    if a.grouped_hint else
+                                                    "; caller hint TALP_GPU_NOT_SORTED: every device is sorted "
                                                     "without a first sweep" if a.not_sorted_hint else
                                                     "; the library finds the out-of-order devices and sorts them "
                                                     "(sort stage)"))

@@ -88,6 +88,16 @@ enum { TALP_DEV_KERNEL = 0, TALP_DEV_H2D = 1, TALP_DEV_D2H = 2, TALP_DEV_D2D = 3
                                         * grouped by stream): every device goes straight to the
                                         * sort stage without a first sweep; one found in order is
                                         * swept from its own records.  Not with SORTED_BY_START. */
+#define TALP_GPU_GROUPED_BY_STREAM 0x20u /* caller asserts that, on every device, each stretch of
+                                        * consecutive records on one stream is in start order (the
+                                        * order per-stream activity buffers deliver when handed over
+                                        * one stream after another, Sec. 4.2): the stretches are the
+                                        * device's sorted runs, found from the stream ids of its tags,
+                                        * and the device goes straight to the sort stage.  A stretch
+                                        * out of start order makes the next result call return
+                                        * TALP_GPU_EINVAL.  A device of one stretch, or of more than
+                                        * 16, is handled as under NOT_SORTED.  Not with
+                                        * SORTED_BY_START or NOT_SORTED. */
 
 /*
  * One trace (or one later time slice of it with TALP_GPU_APPEND).

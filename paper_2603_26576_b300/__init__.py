@@ -6,7 +6,7 @@ library; this module only marshals arguments.  There is no CPU fallback: if
 the library is missing, importing the binding's functions raises.
 """
 from ._lib import (  # noqa: F401
-    TALP_GPU_ALL, TALP_GPU_ALL_REGIONS, TALP_GPU_APPEND, TALP_GPU_HOLD_BACK, TALP_GPU_NOT_SORTED, TALP_GPU_DEVICE_PTRS, TALP_GPU_MAX_REGIONS,
+    TALP_GPU_ALL, TALP_GPU_ALL_REGIONS, TALP_GPU_APPEND, TALP_GPU_HOLD_BACK, TALP_GPU_NOT_SORTED, TALP_GPU_GROUPED_BY_STREAM, TALP_GPU_DEVICE_PTRS, TALP_GPU_MAX_REGIONS,
     TALP_GPU_SORTED_BY_START, TalpGpuError, LIB_PATH, Context, batch_from_arrays, load_library,
     metrics_to_dict, metrics_from_dict, talp_gpu_metrics_combine, talp_gpu_concurrency, TALP_GPU_CONC_LEVELS, talp_gpu_scalability, talp_gpu_ingest_raw, talp_gpu_raw_held,
     raw_batch_from_arrays, talp_gpu_raw_batch, talp_gpu_create, talp_gpu_destroy, talp_gpu_ingest_events, talp_gpu_last_error,

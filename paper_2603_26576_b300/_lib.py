@@ -17,6 +17,7 @@ TALP_GPU_SORTED_BY_START = 0x2
 TALP_GPU_APPEND = 0x4
 TALP_GPU_HOLD_BACK = 0x8
 TALP_GPU_NOT_SORTED = 0x10
+TALP_GPU_GROUPED_BY_STREAM = 0x20
 
 STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEDOUT", -5: "ENOTFOUND", -6: "EBUSY"}
 

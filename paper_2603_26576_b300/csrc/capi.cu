@@ -107,11 +107,12 @@ struct Layout {
     uint64_t seg_cost = 0;
     uint32_t rmax = 1, n_wrec = 0, n_wrec_cap = 0;
     uint64_t n_segs = 0, n_records = 0, n_dev_segs = 0;
+    uint64_t n_grouped = 0;   // device segments whose runs come from their stream ids
     uint64_t sort_slots = 0, sort_recs = 0, sort_tiles = 0;
     size_t n_backup_words = 0, payload_words = 0, n_jobs_max = 0, n_fin = 0;
     bool sorting = false;
     size_t off_segs = 0, off_start = 0, off_send = 0, off_jobs = 0, off_rest = 0, off_sctl = 0, off_fin = 0,
-           off_pay = 0, off_rrend = 0;
+           off_pay = 0, off_rrend = 0, off_grp = 0;
     uint64_t virt = 0;        // virtual positions (records + phantoms)
     size_t up_bytes = 0;
     size_t off_wrec = 0, off_flags = 0, off_gst = 0, off_bk = 0, off_slist = 0, off_srb = 0, off_stb = 0;
@@ -307,10 +308,13 @@ talp_gpu_status check_batch(const talp_gpu_trace_batch& b, uint64_t* n_host, uin
     if (b.n_regions == 0 || b.n_regions > TALP_GPU_MAX_REGIONS)
         return fail(TALP_GPU_EINVAL, "n_regions must be in 1..8");
     if (b.reserved != 0) return fail(TALP_GPU_EINVAL, "reserved must be 0");
-    if (b.flags & ~(TALP_GPU_DEVICE_PTRS | TALP_GPU_SORTED_BY_START | TALP_GPU_APPEND | TALP_GPU_NOT_SORTED))
+    if (b.flags & ~(TALP_GPU_DEVICE_PTRS | TALP_GPU_SORTED_BY_START | TALP_GPU_APPEND | TALP_GPU_NOT_SORTED |
+                    TALP_GPU_GROUPED_BY_STREAM))
         return fail(TALP_GPU_EINVAL, "unknown flag bits");
     if ((b.flags & TALP_GPU_SORTED_BY_START) && (b.flags & TALP_GPU_NOT_SORTED))
         return fail(TALP_GPU_EINVAL, "SORTED_BY_START and NOT_SORTED together");
+    if ((b.flags & TALP_GPU_GROUPED_BY_STREAM) && (b.flags & (TALP_GPU_SORTED_BY_START | TALP_GPU_NOT_SORTED)))
+        return fail(TALP_GPU_EINVAL, "GROUPED_BY_STREAM with SORTED_BY_START or NOT_SORTED");
     if (!b.devices_per_rank || !b.region_window || !b.host_off || !b.dev_off)
         return fail(TALP_GPU_EINVAL, "null header array");
     uint64_t m = 0;
@@ -388,6 +392,7 @@ talp_gpu_status size_ingest(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches
                 L.fms_super += fms_max_super(nseg);
             }
             if ((b.flags & TALP_GPU_APPEND) && L.mm[k]) L.n_backup_words += 3ull * b.n_regions * L.mm[k];
+            if (b.flags & TALP_GPU_GROUPED_BY_STREAM) L.n_grouped += L.mm[k];
         }
     }
     if (L.n_segs > 0xFFFFFFF0ull) return fail(TALP_GPU_EINVAL, "too many segments in one call");
@@ -462,7 +467,8 @@ talp_gpu_status size_ingest(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches
     L.off_rsegs = align_up(L.off_seen_pos + 8 * kMaxRuns * (L.sorting ? L.n_segs : 0), 256);
     L.off_rstart = align_up(L.off_rsegs + sizeof(SegDesc) * (L.sorting ? L.n_dev_segs : 0), 256);
     L.off_rrend = align_up(L.off_rstart + 8 * (L.sorting ? L.n_dev_segs + 1 : 0), 256);
-    L.off_mout = align_up(L.off_rrend + 8 * (L.sorting ? L.n_dev_segs + 1 : 0), 256);
+    L.off_grp = align_up(L.off_rrend + 8 * (L.sorting ? L.n_dev_segs + 1 : 0), 256);
+    L.off_mout = align_up(L.off_grp + 8 * kRunsStride * L.n_grouped, 256);
     L.ws_bytes = align_up(L.off_mout + sizeof(MetricsOut) * L.n_fin, 256);
     return TALP_GPU_OK;
 }
@@ -552,7 +558,7 @@ talp_gpu_status fill_ingest(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches
     MetricsOut* mout = reinterpret_cast<MetricsOut*>(wsd + L.off_mout);
     size_t pw = 0, bk_used = 0, nf = 0;
     uint32_t nj = 0;
-    uint64_t si = 0, pos = 0;
+    uint64_t si = 0, pos = 0, gi = 0;   // gi: grouped device segments so far
     size_t presort_at = 0;   // first device of this batch in c->raw_presort
     for (size_t k = 0; k < nb; ++k) {
         const talp_gpu_trace_batch& b = batches[k];
@@ -632,12 +638,22 @@ talp_gpu_status fill_ingest(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches
             s.pad[0] = sflag;
             if (L.sorting) restore[si] = bkd ? bkd + static_cast<size_t>(g) * R * 3 : nullptr;
             sstart[si] = pos;
-            const bool presort = (b.flags & TALP_GPU_NOT_SORTED) ||
+            const bool grouped = sflag && (b.flags & TALP_GPU_GROUPED_BY_STREAM);
+            const bool presort = (b.flags & TALP_GPU_NOT_SORTED) || grouped ||
                                  (c->raw_inner && presort_at + g < c->raw_presort.size() && c->raw_presort[presort_at + g]);
-            if (L.sorting)   // a raw lane's runs are its streams, known from the adapter
+            if (L.sorting) {
+                // a raw lane's runs are its streams, known from the adapter; a
+                // grouped device's runs are its stream groups, found on the GPU
+                // from its tags before the sort stage
                 known[si] = (sflag && presort && c->raw_inner && c->raw_runs)
                                 ? c->raw_runs + static_cast<size_t>(presort_at + g) * kRunsStride
                                 : nullptr;
+                if (grouped) {
+                    known[si] = reinterpret_cast<const uint64_t*>(wsd + L.off_grp) + gi * kRunsStride;
+                    s.pad[0] |= kSegGrouped;
+                    ++gi;
+                }
+            }
             if (sflag && presort) {
                 s.pad[0] |= kSegPresort;   // not in the first sweep: sorted, then swept
                 send[si] = pos;
@@ -676,7 +692,8 @@ talp_gpu_status fill_ingest(talp_gpu_ctx* c, const talp_gpu_trace_batch* batches
     jobs[nj++] = FillJob{reinterpret_cast<int64_t*>(seg_flags), (L.n_segs + 2) / 2, 0, nullptr};
     jobs[nj++] = FillJob{reinterpret_cast<int64_t*>(gstatus), 2, 0, nullptr};   // status, pad, slice ticket
     if (L.sorting) jobs[nj++] = FillJob{reinterpret_cast<int64_t*>(wsd + L.off_seen_n), (L.n_segs + 2) / 2, 0, nullptr};
-    if (nj > L.n_jobs_max || pw > L.payload_words || si != L.n_segs || bk_used > L.n_backup_words || nf != L.n_fin)
+    if (nj > L.n_jobs_max || pw > L.payload_words || si != L.n_segs || bk_used > L.n_backup_words || nf != L.n_fin ||
+        gi != L.n_grouped)
         return fail(TALP_GPU_ECUDA, "internal: upload table overflow");
     L.nj = nj;
     if (L.sorting) {
@@ -734,6 +751,11 @@ talp_gpu_status enqueue_ingest(talp_gpu_ctx* c, const Layout& L, const char* up,
     uint32_t* seg_flags = reinterpret_cast<uint32_t*>(wsd + L.off_flags);
     uint32_t* gstatus = reinterpret_cast<uint32_t*>(wsd + L.off_gst);
     if (L.n_records > 0) {
+        if (L.n_grouped) {   // the runs of grouped devices, from their tags
+            TALP_CUDA(launch_group_runs(dsegs, static_cast<uint32_t>(L.n_segs),
+                                        reinterpret_cast<const uint64_t* const*>(wsd + L.off_known), stream));
+            ++nl;
+        }
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (profile) {
             e0 = take_event(c);

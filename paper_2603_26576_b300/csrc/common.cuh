@@ -110,6 +110,8 @@ struct FillJob {
 constexpr uint8_t kSegSortable = 1;   // device segment may be sorted when found out of order
 constexpr uint8_t kSegPresort = 2;    // known out of order (several streams of a raw buffer): left out
                                       // of the first sweep and sorted, then swept
+constexpr uint8_t kSegGrouped = 4;    // records grouped by stream (the caller's word): its runs are
+                                      // found from the stream ids before the sort stage
 
 // Control block of the sort stage (device memory; pointers into scratch).
 struct SortCtl {

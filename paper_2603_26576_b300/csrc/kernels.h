@@ -71,6 +71,7 @@ cudaError_t launch_combine(const MetricsOut* parts, uint32_t n_parts, MetricsOut
 // merge-sweep), the others radix sorted; then the segment table of the
 // sorted copies for the re-sweep.
 // n_segs: entries of `segs`; n_slots: device segments (upper bound of flagged).
+cudaError_t launch_group_runs(const SegDesc* segs, uint32_t n_segs, const uint64_t* const* known, cudaStream_t stream);
 cudaError_t launch_sort_stage(const SegDesc* segs, uint32_t n_segs, uint32_t n_slots, uint32_t* seg_flags,
                               SortCtl* ctl, SegDesc* resweep_segs, uint64_t* resweep_start, uint64_t* resweep_rend,
                               int grid_tiles, int grid_segs, uint32_t* gstatus, int64_t wait_limit,

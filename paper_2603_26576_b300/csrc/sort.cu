@@ -458,6 +458,93 @@ __global__ void __launch_bounds__(256) sort_resweep_plan_kernel(const SegDesc* _
     }
 }
 
+// Runs of a device whose records come grouped by stream (each stretch of
+// consecutive records on one stream in start order, the caller's word): the
+// positions where the stream id changes.  One block per segment reads its
+// tags as aligned 16-byte blocks (thread t takes blocks t, t + 256, ...: the
+// loads coalesce) and compares every byte with the one before it (the block
+// before comes from the previous lane, or for lane 0 from memory).  The
+// boundaries go to a known-runs record (count r, then the r + 1 boundaries),
+// or count 0 when there is a single stretch or more than kMaxRuns (the sort
+// stage then finds the runs itself).  The merge-sweep checks every stretch
+// for start order.  Reading whole aligned blocks may touch up to 15 bytes
+// before and after the tags; each such block holds at least one tag byte, so
+// it lies in mapped memory, and those bytes are ignored.
+constexpr int kGroupThreads = 256;
+constexpr int kGroupCap = 64;   // boundaries kept (more: too many runs anyway)
+
+__global__ void __launch_bounds__(kGroupThreads) group_runs_kernel(const SegDesc* __restrict__ segs, uint32_t n_segs,
+                                                                   const uint64_t* const* __restrict__ known) {
+    __shared__ uint32_t s_n;
+    __shared__ uint64_t s_pos[kGroupCap];
+    const uint32_t s = blockIdx.x;
+    if (s >= n_segs) return;
+    const SegDesc& d = segs[s];
+    if (!(d.pad[0] & kSegGrouped)) return;   // uniform over the block
+    uint64_t* rec = const_cast<uint64_t*>(known[s]);
+    const uint64_t n = d.n;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    if (n > 1) {
+        const uintptr_t A = reinterpret_cast<uintptr_t>(d.tag);
+        const uintptr_t B0 = A & ~static_cast<uintptr_t>(15);
+        const uint64_t nblk = (A + n - B0 + 15) / 16;
+        // rounds of 256 consecutive blocks; every thread takes part in every
+        // round (the shuffles need the whole warp)
+        for (uint64_t r0 = 0; r0 < nblk; r0 += kGroupThreads) {
+            const uint64_t blk = r0 + threadIdx.x;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (blk < nblk) v = *reinterpret_cast<const uint4*>(B0 + 16 * blk);
+            // the byte before the block: the last byte of the previous lane's
+            // block, or (lane 0) read from memory
+            uint32_t p = __shfl_up_sync(0xFFFFFFFFu, v.w >> 24, 1);
+            if (lane == 0 && blk > 0 && blk < nblk) p = *reinterpret_cast<const uint8_t*>(B0 + 16 * blk - 1);
+            const uint32_t m = 0x1F1F1F1Fu;
+            const uint32_t d0 = (v.x ^ ((v.x << 8) | p)) & m;
+            const uint32_t d1 = (v.y ^ ((v.y << 8) | (v.x >> 24))) & m;
+            const uint32_t d2 = (v.z ^ ((v.z << 8) | (v.y >> 24))) & m;
+            const uint32_t d3 = (v.w ^ ((v.w << 8) | (v.z >> 24))) & m;
+            if ((d0 | d1 | d2 | d3) && blk < nblk) {   // rare: a stream changes somewhere in the block
+                const uint32_t dw[4] = {d0, d1, d2, d3};
+                for (int j = 0; j < 16; ++j) {
+                    if ((dw[j >> 2] >> (8 * (j & 3))) & 0xFFu) {
+                        // tag index of byte j; a boundary needs it and the byte
+                        // before to be tags of the segment
+                        const int64_t q = static_cast<int64_t>(B0 + 16 * blk + j) - static_cast<int64_t>(A);
+                        if (q >= 1 && q < static_cast<int64_t>(n)) {
+                            const uint32_t k = atomicAdd(&s_n, 1u);
+                            if (k < static_cast<uint32_t>(kGroupCap)) s_pos[k] = static_cast<uint64_t>(q);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t c = s_n;   // boundaries: c + 1 runs
+        if (c == 0 || c + 1 > static_cast<uint32_t>(kMaxRuns)) {
+            rec[0] = 0;
+        } else {
+            // the boundaries in ascending order (at most kMaxRuns - 1 of them)
+            for (uint32_t a = 1; a < c; ++a) {
+                const uint64_t v = s_pos[a];
+                uint32_t b = a;
+                while (b > 0 && s_pos[b - 1] > v) {
+                    s_pos[b] = s_pos[b - 1];
+                    --b;
+                }
+                s_pos[b] = v;
+            }
+            rec[0] = c + 1;
+            rec[1] = 0;
+            for (uint32_t a = 0; a < c; ++a) rec[2 + a] = s_pos[a];
+            rec[2 + c] = n;
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_sort_stage(const SegDesc* segs, uint32_t n_segs, uint32_t n_slots, uint32_t* seg_flags,
@@ -478,6 +565,11 @@ cudaError_t launch_sort_stage(const SegDesc* segs, uint32_t n_segs, uint32_t n_s
     const int g = static_cast<int>((n_slots + 1 + 255) / 256);
     sort_resweep_plan_kernel<<<g < 1024 ? g : 1024, 256, 0, stream>>>(segs, ctl, resweep_segs, resweep_start,
                                                                        resweep_rend, n_slots);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_group_runs(const SegDesc* segs, uint32_t n_segs, const uint64_t* const* known, cudaStream_t stream) {
+    if (n_segs) group_runs_kernel<<<n_segs, kGroupThreads, 0, stream>>>(segs, n_segs, known);
     return cudaGetLastError();
 }
 

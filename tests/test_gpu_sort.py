@@ -216,3 +216,71 @@ def test_not_sorted_hint():
     with pytest.raises(P.TalpGpuError):
         c.ingest([base], flags=P.TALP_GPU_NOT_SORTED | P.TALP_GPU_SORTED_BY_START)
     c.close()
+
+
+def test_grouped_by_stream():
+    """TALP_GPU_GROUPED_BY_STREAM: each device's records grouped by stream, the
+    groups found from the stream ids and merged without a first sweep: device
+    and host record arrays, devices of one stream (in order already), of
+    20 streams (more runs than the merge takes: the library finds them), of
+    no records, a stream split into two separate stretches, and APPEND slices
+    all equal the oracle; a stretch out of start order, and the flag with
+    SORTED_BY_START or NOT_SORTED, are refused."""
+    import torch
+    import paper_2603_26576_b300 as P
+    from test_gpu_parity import _split_by_time
+    c = make_ctx()
+    base = tg.random_trace(33, trace_id=101, n_ranks=3, devices_per_rank=[2, 1, 3], dev_events=[3000, 1, 0, 4000,
+                           2500, 40000], host_events=700, n_regions=3)
+    g = tg.interleave_lanes(base)
+    c.ingest([g], flags=P.TALP_GPU_GROUPED_BY_STREAM)
+    assert_trace_equal(c, g, "grouped, host arrays")
+    dev = torch.device("cuda", 0)
+    arr = {k: torch.from_numpy(getattr(g, k)).to(dev) for k in ("host_se", "host_state", "dev_se", "dev_tag")}
+    g.trace_id = 102
+    c.ingest([g], flags=P.TALP_GPU_GROUPED_BY_STREAM, arrays=[arr])
+    assert_trace_equal(c, g, "grouped, device arrays")
+    # one device of 20 streams (tags rewritten), the rest as before
+    w = tg.Trace(**{**base.__dict__})
+    w.dev_tag = w.dev_tag.copy()
+    a0, a1 = int(w.dev_off[5]), int(w.dev_off[6])
+    w.dev_tag[a0:a1] = (w.dev_tag[a0:a1] & 0xE0) | (np.arange(a1 - a0) % 20).astype(np.uint8)
+    w = tg.interleave_lanes(w)
+    w.trace_id = 103
+    c.ingest([w], flags=P.TALP_GPU_GROUPED_BY_STREAM)
+    assert_trace_equal(c, w, "grouped, 20 streams")
+    # a stream in two separate stretches: still each stretch in order
+    sp = tg.Trace(**{**g.__dict__})
+    sp.dev_se, sp.dev_tag = g.dev_se.copy(), g.dev_tag.copy()
+    b0, b1 = int(sp.dev_off[3]), int(sp.dev_off[4])
+    seg_se, seg_tag = sp.dev_se[b0:b1].copy(), sp.dev_tag[b0:b1].copy()
+    first = seg_tag[0] & 31
+    run = np.flatnonzero((seg_tag & 31) == first)
+    half = run[: len(run) // 2]
+    rest = np.setdiff1d(np.arange(b1 - b0), half)
+    order = np.concatenate([half, rest[(seg_tag[rest] & 31) != first], rest[(seg_tag[rest] & 31) == first]])
+    sp.dev_se[b0:b1], sp.dev_tag[b0:b1] = seg_se[order], seg_tag[order]
+    sp.trace_id = 104
+    c.ingest([sp], flags=P.TALP_GPU_GROUPED_BY_STREAM)
+    assert_trace_equal(c, sp, "grouped, a stream in two stretches")
+    # APPEND slices
+    a, b = _split_by_time(g, 0.5)
+    a.trace_id = b.trace_id = 105
+    c.ingest([a], flags=P.TALP_GPU_GROUPED_BY_STREAM)
+    c.ingest([b], flags=P.TALP_GPU_GROUPED_BY_STREAM | P.TALP_GPU_APPEND)
+    whole = tg.Trace(**{**base.__dict__})
+    whole.trace_id = 105
+    assert_trace_equal(c, whole, "grouped-append")
+    # a stretch out of start order
+    bad = tg.Trace(**{**g.__dict__})
+    bad.dev_se = g.dev_se.copy()
+    q = int(bad.dev_off[3]) + 5
+    bad.dev_se[[q, q + 1]] = bad.dev_se[[q + 1, q]]
+    bad.trace_id = 106
+    c.ingest([bad], flags=P.TALP_GPU_GROUPED_BY_STREAM)
+    st, _ = c.metrics(bad.trace_id, check=False)
+    assert st == -1
+    for f in (P.TALP_GPU_SORTED_BY_START, P.TALP_GPU_NOT_SORTED):
+        with pytest.raises(P.TalpGpuError):
+            c.ingest([g], flags=P.TALP_GPU_GROUPED_BY_STREAM | f)
+    c.close()
