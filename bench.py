@@ -1439,18 +1439,38 @@ def measure_sort_stage(a, t, want):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
-    ck = clocks.stop()
     ms = e0.elapsed_time(e1) / k
     prof = P.talp_gpu_profile_read(ctx.ctx)
     P.talp_gpu_profile(ctx.ctx, False)
     sort_ms = prof["sort_ms"] / max(1, prof["sort_launches"])
     sweep_ms = prof["sweep_ms"] / max(1, prof["sweep_launches"])
+    # the same records with TALP_GPU_GROUPED_BY_STREAM: the caller states the
+    # grouping, each device's runs come from its stream ids, no first sweep
+    bg, keep_g = P.batch_from_arrays(u.trace_id, u.devices_per_rank, u.region_window, arr["host_se"],
+                                     arr["host_state"], u.host_off, arr["dev_se"], arr["dev_tag"], u.dev_off,
+                                     P.TALP_GPU_GROUPED_BY_STREAM)
+
+    def step_g():
+        P.talp_gpu_ingest_events(ctx.ctx, [bg], stream)
+        P.talp_gpu_region_metrics_device(ctx.ctx, [u.trace_id], P.TALP_GPU_ALL_REGIONS, out_dev.data_ptr(), stream)
+
+    warm_until(step_g, 3, 0.5)
+    got_g = P.talp_gpu_region_metrics(ctx.ctx, u.trace_id, P.TALP_GPU_ALL_REGIONS, stream, n_regions=R)
+    same_g = all(P.metrics_to_dict(x) == P.metrics_to_dict(y) for x, y in zip(got_g, want))
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(k):
+        step_g()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_g = e0.elapsed_time(e1) / k
+    ck = clocks.stop()
     n_dev = int(u.dev_off[-1])
     N = u.n_records
     peak, peak_kind = measured_peaks()
     achieved = BYTES_PER_RECORD * n_dev / (sort_ms / 1000.0) / 1e9
     ctx.close()
-    del arr, b, keep
+    del arr, b, keep, bg, keep_g
     torch.cuda.empty_cache()
     return {
         "workload": "the plain large trace with each device's records grouped by stream (each stream in start "
@@ -1462,6 +1482,9 @@ def measure_sort_stage(a, t, want):
                                     "kernel": "sort stage (run finding, talp::fms_kernel and its plan and fix-up "
                                               "kernels), 17 B per device record"}},
         "bit_exact_vs_start_ordered": same,
+        "grouped_by_stream_flag": {"ms_per_step": ms_g, "events_per_s": N / (ms_g / 1000.0),
+                                   "bit_exact_vs_start_ordered": same_g,
+                                   "form": "the same records ingested with TALP_GPU_GROUPED_BY_STREAM"},
         "gpu_launches": prof["kernel_launches"] - l0, "clocks": ck}
 
 
@@ -1532,6 +1555,7 @@ def default_extras(a, t=None, want=None):
             "roofline_frac": W["roofline"]["frac"], "bit_exact_raw_vs_lanes": W["config"]["bit_exact_raw_vs_lanes"],
             "gpu_launches": W["gpu_launches"], "clocks": W["clocks"]}
         ok = (ok and out["sort_stage"]["bit_exact_vs_start_ordered"]
+              and out["sort_stage"]["grouped_by_stream_flag"]["bit_exact_vs_start_ordered"]
               and out["concurrency"]["bit_exact_rank0_vs_oracle"] and out["raw"]["bit_exact_raw_vs_lanes"])
     out["_rc"] = 0 if ok else 1
     return out
