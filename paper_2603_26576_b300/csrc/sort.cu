@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(256) sort_resweep_plan_kernel(const SegDesc* _
 // Runs of a device whose records come grouped by stream (each stretch of
 // consecutive records on one stream in start order, the caller's word): the
 // positions where the stream id changes.  One block per segment reads its
-// tags as aligned 16-byte blocks (thread t takes blocks t, t + 256, ...: the
+// tags as aligned 16-byte blocks (thread t takes blocks t, t + 1024, ...: the
 // loads coalesce) and compares every byte with the one before it (the block
 // before comes from the previous lane, or for lane 0 from memory).  The
 // boundaries go to a known-runs record (count r, then the r + 1 boundaries),
@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(256) sort_resweep_plan_kernel(const SegDesc* _
 // for start order.  Reading whole aligned blocks may touch up to 15 bytes
 // before and after the tags; each such block holds at least one tag byte, so
 // it lies in mapped memory, and those bytes are ignored.
-constexpr int kGroupThreads = 256;
+constexpr int kGroupThreads = 1024;
 constexpr int kGroupCap = 64;   // boundaries kept (more: too many runs anyway)
 
 __global__ void __launch_bounds__(kGroupThreads) group_runs_kernel(const SegDesc* __restrict__ segs, uint32_t n_segs,
@@ -490,7 +490,7 @@ __global__ void __launch_bounds__(kGroupThreads) group_runs_kernel(const SegDesc
         const uintptr_t A = reinterpret_cast<uintptr_t>(d.tag);
         const uintptr_t B0 = A & ~static_cast<uintptr_t>(15);
         const uint64_t nblk = (A + n - B0 + 15) / 16;
-        // rounds of 256 consecutive blocks; every thread takes part in every
+        // rounds of 1024 consecutive blocks; every thread takes part in every
         // round (the shuffles need the whole warp)
         for (uint64_t r0 = 0; r0 < nblk; r0 += kGroupThreads) {
             const uint64_t blk = r0 + threadIdx.x;
