@@ -306,296 +306,297 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
     uint32_t ra[K], rk[K];
     const uint64_t dev_end = dv.rec0 + dv.n;
     for (int pass = 0; pass < (FIX ? 2 : 1); ++pass) {
-    unsigned long long* acc = pass ? s_acc2 : s_acc;
-    if (ch.n > 0) issue_tile(stg[0], se, tag, ch.rec0, static_cast<int>(min(static_cast<uint32_t>(kTile), ch.n)), lane);
-    if (lane < 2 * K) {
-        acc[lane] = 0;
-        // entering state: none (main pass), the true one (fix-up, pass 0)
-        s_st[lane] = FIX && pass == 0 ? in[static_cast<uint64_t>(c) * 2 * K + lane] : INT64_MIN;
-    }
-    __syncwarp();
-    rel = false;
-    sbase = 0;
-#pragma unroll
-    for (int i = 0; i < K; ++i) ra[i] = rk[i] = 0u;
-    int64_t last_x = INT64_MIN;   // the previous tile's last start (order check)
-    // start of the record after a tile (clipped), or none: loaded one tile
-    // ahead, so that its latency hides behind a tile's work
-    int64_t after_nx = INT64_MAX;
-    {
-        const uint64_t p = ch.rec0 + min(static_cast<uint32_t>(kTile), ch.n);
-        if (p < dev_end) after_nx = max64(se[2 * p], dv.a);
-    }
-    for (uint32_t o = 0, t = 0; o < ch.n; o += kTile, ++t) {
-        const int n = static_cast<int>(min(static_cast<uint32_t>(kTile), ch.n - o));
-        const uint64_t r0 = ch.rec0 + o;
-        const int64_t after = after_nx;
-        if (o + kTile < ch.n) {
-            const uint64_t p = r0 + kTile + min(static_cast<uint32_t>(kTile), ch.n - o - kTile);
-            after_nx = p < dev_end ? max64(se[2 * p], dv.a) : INT64_MAX;
-        }
-        if (o + kTile < ch.n) {
-            issue_tile(stg[(t + 1) & 1], se, tag, r0 + kTile,
-                       static_cast<int>(min(static_cast<uint32_t>(kTile), ch.n - o - kTile)), lane);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
+        unsigned long long* acc = pass ? s_acc2 : s_acc;
+        if (ch.n > 0)
+            issue_tile(stg[0], se, tag, ch.rec0, static_cast<int>(min(static_cast<uint32_t>(kTile), ch.n)), lane);
+        if (lane < 2 * K) {
+            acc[lane] = 0;
+            // entering state: none (main pass), the true one (fix-up, pass 0)
+            s_st[lane] = FIX && pass == 0 ? in[static_cast<uint64_t>(c) * 2 * K + lane] : INT64_MIN;
         }
         __syncwarp();
-        const Stage& S = stg[t & 1];
-        const int toff = static_cast<int>(reinterpret_cast<uintptr_t>(tag + r0) & 3u);
-        const int64_t x0 = row_of(S, 0).x, xl = row_of(S, n - 1).x;
-        if (lane == 0) bad |= last_x > x0 ? 4u : 0u;
-        last_x = xl;
-        const int64_t s0 = max64(x0, dv.a);
-        if (FIX && s0 >= E1) {   // both entering states agree on every end running from here on
-            cp_async_wait<0>();
-            __syncwarp();
-            break;
+        rel = false;
+        sbase = 0;
+#pragma unroll
+        for (int i = 0; i < K; ++i) ra[i] = rk[i] = 0u;
+        int64_t last_x = INT64_MIN;   // the previous tile's last start (order check)
+        // start of the record after a tile (clipped), or none: loaded one tile
+        // ahead, so that its latency hides behind a tile's work
+        int64_t after_nx = INT64_MAX;
+        {
+            const uint64_t p = ch.rec0 + min(static_cast<uint32_t>(kTile), ch.n);
+            if (p < dev_end) after_nx = max64(se[2 * p], dv.a);
         }
-        // the entering state as offsets from s0
-        TopK<uint32_t> ta, tk;
-        bool fits = true;
-        if (rel) {
-            const int64_t d = s0 - sbase;
-            if (d >= 0 && d <= 0xFFFFFFFFll) {
-                const uint32_t d32 = static_cast<uint32_t>(d);
+        for (uint32_t o = 0, t = 0; o < ch.n; o += kTile, ++t) {
+            const int n = static_cast<int>(min(static_cast<uint32_t>(kTile), ch.n - o));
+            const uint64_t r0 = ch.rec0 + o;
+            const int64_t after = after_nx;
+            if (o + kTile < ch.n) {
+                const uint64_t p = r0 + kTile + min(static_cast<uint32_t>(kTile), ch.n - o - kTile);
+                after_nx = p < dev_end ? max64(se[2 * p], dv.a) : INT64_MAX;
+            }
+            if (o + kTile < ch.n) {
+                issue_tile(stg[(t + 1) & 1], se, tag, r0 + kTile,
+                           static_cast<int>(min(static_cast<uint32_t>(kTile), ch.n - o - kTile)), lane);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncwarp();
+            const Stage& S = stg[t & 1];
+            const int toff = static_cast<int>(reinterpret_cast<uintptr_t>(tag + r0) & 3u);
+            const int64_t x0 = row_of(S, 0).x, xl = row_of(S, n - 1).x;
+            if (lane == 0) bad |= last_x > x0 ? 4u : 0u;
+            last_x = xl;
+            const int64_t s0 = max64(x0, dv.a);
+            if (FIX && s0 >= E1) {   // both entering states agree on every end running from here on
+                cp_async_wait<0>();
+                __syncwarp();
+                break;
+            }
+            // the entering state as offsets from s0
+            TopK<uint32_t> ta, tk;
+            bool fits = true;
+            if (rel) {
+                const int64_t d = s0 - sbase;
+                if (d >= 0 && d <= 0xFFFFFFFFll) {
+                    const uint32_t d32 = static_cast<uint32_t>(d);
+#pragma unroll
+                    for (int i = 0; i < K; ++i) {
+                        ta.v[i] = tmax(ra[i], d32) - d32;
+                        tk.v[i] = tmax(rk[i], d32) - d32;
+                    }
+                } else {   // every entry at or before s0 (or records out of order, reported)
+                    clear_top(ta);
+                    clear_top(tk);
+                }
+            } else {
 #pragma unroll
                 for (int i = 0; i < K; ++i) {
-                    ta.v[i] = tmax(ra[i], d32) - d32;
-                    tk.v[i] = tmax(rk[i], d32) - d32;
+                    const int64_t xa = s_st[i], xk = s_st[K + i];
+                    fits &= near32(xa, s0) && near32(xk, s0);
+                    ta.v[i] = rel32(xa, s0);
+                    tk.v[i] = rel32(xk, s0);
                 }
-            } else {   // every entry at or before s0 (or records out of order, reported)
-                clear_top(ta);
-                clear_top(tk);
             }
-        } else {
-#pragma unroll
-            for (int i = 0; i < K; ++i) {
-                const int64_t xa = s_st[i], xk = s_st[K + i];
-                fits &= near32(xa, s0) && near32(xk, s0);
-                ta.v[i] = rel32(xa, s0);
-                tk.v[i] = rel32(xk, s0);
-            }
-        }
-        // the tile's records as offsets from s0.  A tile that starts inside
-        // the window needs no start clip, and ends are clipped to b only:
-        // an end below its start (a record after b) is at or before every
-        // later start, so it only ever contributes 0 -- as the gap bound
-        // min(next start, b) already makes the gaps after b empty.
-        uint32_t s[kItems], e[kItems];
-        uint32_t kmask = 0;
-        TopK<uint32_t> la, lk;   // the lane's own K ends, sorted (0 = none)
-        const bool plain = x0 >= dv.a && x0 < dv.b && static_cast<uint64_t>(xl - x0) < 0xFFFFFFFFull;
-        if (plain) {
-            uint32_t hib = 0;
-            int64_t prev = lane > 0 ? row_of(S, lane * kItems - 1).x : x0;
-            // record i of the lane (q = its tile index)
-            auto item = [&](int i, int q) {
-                const longlong2 r = row_of(S, q);
-                bad |= (prev > r.x ? 4u : 0u) | (r.y < r.x ? 1u : 0u);
-                prev = r.x;
-                const int64_t de = min64(r.y, dv.b) - s0;
-                hib |= static_cast<uint32_t>(static_cast<uint64_t>(de) >> 32);
-                s[i] = static_cast<uint32_t>(r.x) - static_cast<uint32_t>(s0);
-                e[i] = static_cast<uint32_t>(de);
-                const uint32_t kd = kind_of(S, toff, q);
-                bad |= kd > 4u ? 2u : 0u;
-                const bool isK = kd == 0u;
-                kmask |= isK ? 1u << i : 0u;
-                la.v[i] = e[i];
-                lk.v[i] = isK ? e[i] : 0u;
-            };
-#pragma unroll
-            for (int i = 0; i < kItems; ++i) {
-                const int q = lane * kItems + i;
-                s[i] = e[i] = 0xFFFFFFFFu;
-                la.v[i] = lk.v[i] = 0u;
-                if (q < n) item(i, q);
-            }
-            fits &= hib == 0;
-        } else {
-#pragma unroll
-            for (int i = 0; i < kItems; ++i) {
-                const int q = lane * kItems + i;
-                s[i] = e[i] = 0xFFFFFFFFu;
-                la.v[i] = lk.v[i] = 0u;
-                if (q < n) {
-                    int64_t sa64, ea64;
-                    clipped(S, q, dv, sa64, ea64);
+            // the tile's records as offsets from s0.  A tile that starts inside
+            // the window needs no start clip, and ends are clipped to b only:
+            // an end below its start (a record after b) is at or before every
+            // later start, so it only ever contributes 0 -- as the gap bound
+            // min(next start, b) already makes the gaps after b empty.
+            uint32_t s[kItems], e[kItems];
+            uint32_t kmask = 0;
+            TopK<uint32_t> la, lk;   // the lane's own K ends, sorted (0 = none)
+            const bool plain = x0 >= dv.a && x0 < dv.b && static_cast<uint64_t>(xl - x0) < 0xFFFFFFFFull;
+            if (plain) {
+                uint32_t hib = 0;
+                int64_t prev = lane > 0 ? row_of(S, lane * kItems - 1).x : x0;
+                // record i of the lane (q = its tile index)
+                auto item = [&](int i, int q) {
                     const longlong2 r = row_of(S, q);
-                    if (q > 0) bad |= row_of(S, q - 1).x > r.x ? 4u : 0u;
-                    bad |= r.y < r.x ? 1u : 0u;
-                    fits &= near32(ea64, s0);
-                    s[i] = rel32(sa64, s0);
-                    e[i] = rel32(ea64, s0);
+                    bad |= (prev > r.x ? 4u : 0u) | (r.y < r.x ? 1u : 0u);
+                    prev = r.x;
+                    const int64_t de = min64(r.y, dv.b) - s0;
+                    hib |= static_cast<uint32_t>(static_cast<uint64_t>(de) >> 32);
+                    s[i] = static_cast<uint32_t>(r.x) - static_cast<uint32_t>(s0);
+                    e[i] = static_cast<uint32_t>(de);
                     const uint32_t kd = kind_of(S, toff, q);
                     bad |= kd > 4u ? 2u : 0u;
                     const bool isK = kd == 0u;
                     kmask |= isK ? 1u << i : 0u;
                     la.v[i] = e[i];
                     lk.v[i] = isK ? e[i] : 0u;
+                };
+#pragma unroll
+                for (int i = 0; i < kItems; ++i) {
+                    const int q = lane * kItems + i;
+                    s[i] = e[i] = 0xFFFFFFFFu;
+                    la.v[i] = lk.v[i] = 0u;
+                    if (q < n) item(i, q);
                 }
-            }
-        }
-        sort8_desc(la.v);
-        sort8_desc(lk.v);
-        if (__all_sync(0xFFFFFFFFu, fits)) {
-            // A lane needs from the lanes before it only the ends still
-            // running at its first start th (a lane without records: at the
-            // next tile's first start).  With pm the largest end of lanes
-            // 0 .. L (kernel ends are among them), lane L looks back at lane
-            // L - d only while pm(L - d) > th: usually the previous lane or
-            // two.  The ends at or before th it skips contribute nothing to
-            // its records, nor to any later lane.
-            const uint32_t aft = rel32(after, s0);
-            const uint32_t th = lane * kItems < n ? s[0] : aft;
-            uint32_t pm = la.v[0];
+                fits &= hib == 0;
+            } else {
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, pm, d);
-                if (lane >= d) pm = tmax(pm, y);
-            }
-            TopK<uint32_t> xa, xk;
-            clear_top(xa);
-            clear_top(xk);
-            for (int d = 1; d < 32; ++d) {
-                const uint32_t pd = __shfl_up_sync(0xFFFFFFFFu, pm, d);
-                const bool need = lane >= d && pd > th;
-                if (!__any_sync(0xFFFFFFFFu, need)) break;
-                const TopK<uint32_t> ya = shfl_up_top(la, d), yk = shfl_up_top(lk, d);
-                if (need) {
-                    merge_top(xa, ya);
-                    merge_top(xk, yk);
-                }
-            }
-            merge_top(xa, ta);
-            merge_top(xk, tk);
-            // a lane's gaps in the tile are disjoint and lie within 2^32 - 1 ns
-            // of s0, so its level sums of the tile -- and the warp's, whose
-            // gaps are disjoint too -- fit 32 bits.  The level-k time of a gap
-            // [s, hi) is min(max(E_k, s), max(hi, s)) - s; the s terms are
-            // summed once (S, and SH for the gaps where levels 5-8 are added)
-            // and taken off at the end, exact in wrapping 32-bit arithmetic
-            // because the results fit.
-            uint32_t ma[4], oa[4], mk[4], ok[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                ma[i] = xa.v[i];
-                oa[i] = xa.v[4 + i];
-                mk[i] = xk.v[i];
-                ok[i] = xk.v[4 + i];
-            }
-            uint32_t acc_a[K], acc_k[K], S = 0, SH = 0;
-#pragma unroll
-            for (int k = 0; k < K; ++k) acc_a[k] = acc_k[k] = 0;
-            const uint32_t bnd = rel32(dv.b, s0);
-            uint32_t nxt = shfl_t(s[0], (lane + 1) & 31);
-            if (lane == 31 || (lane + 1) * kItems >= n) nxt = aft;
-#pragma unroll
-            for (int i = 0; i < kItems; ++i) {
-                const int q = lane * kItems + i;
-                const bool v = q < n;
-                const uint32_t ns = (i + 1 < kItems && q + 1 < n) ? s[i + 1] : nxt;
-                // the gap [s_i, min(next start, window end)) at level k
-                // lasts until E_k
-                const uint32_t hc = tmax(tmin(ns, bnd), s[i]);
-                if (v) {
-                    uint32_t ev = e[i];
-                    ins4(ma, ev);
-                    if (ev > s[i]) ins4(oa, ev);   // a 5th end still running
-                    if (kmask & (1u << i)) {
-                        uint32_t ek = e[i];
-                        ins4(mk, ek);
-                        if (ek > s[i]) ins4(ok, ek);
-                    }
-                    S += s[i];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        acc_a[k] += tmin(tmax(ma[k], s[i]), hc);
-                        acc_k[k] += tmin(tmax(mk[k], s[i]), hc);
+                for (int i = 0; i < kItems; ++i) {
+                    const int q = lane * kItems + i;
+                    s[i] = e[i] = 0xFFFFFFFFu;
+                    la.v[i] = lk.v[i] = 0u;
+                    if (q < n) {
+                        int64_t sa64, ea64;
+                        clipped(S, q, dv, sa64, ea64);
+                        const longlong2 r = row_of(S, q);
+                        if (q > 0) bad |= row_of(S, q - 1).x > r.x ? 4u : 0u;
+                        bad |= r.y < r.x ? 1u : 0u;
+                        fits &= near32(ea64, s0);
+                        s[i] = rel32(sa64, s0);
+                        e[i] = rel32(ea64, s0);
+                        const uint32_t kd = kind_of(S, toff, q);
+                        bad |= kd > 4u ? 2u : 0u;
+                        const bool isK = kd == 0u;
+                        kmask |= isK ? 1u << i : 0u;
+                        la.v[i] = e[i];
+                        lk.v[i] = isK ? e[i] : 0u;
                     }
                 }
-                if (__any_sync(0xFFFFFFFFu, v && tmax(oa[0], ok[0]) > s[i])) {
+            }
+            sort8_desc(la.v);
+            sort8_desc(lk.v);
+            if (__all_sync(0xFFFFFFFFu, fits)) {
+                // A lane needs from the lanes before it only the ends still
+                // running at its first start th (a lane without records: at the
+                // next tile's first start).  With pm the largest end of lanes
+                // 0 .. L (kernel ends are among them), lane L looks back at lane
+                // L - d only while pm(L - d) > th: usually the previous lane or
+                // two.  The ends at or before th it skips contribute nothing to
+                // its records, nor to any later lane.
+                const uint32_t aft = rel32(after, s0);
+                const uint32_t th = lane * kItems < n ? s[0] : aft;
+                uint32_t pm = la.v[0];
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, pm, d);
+                    if (lane >= d) pm = tmax(pm, y);
+                }
+                TopK<uint32_t> xa, xk;
+                clear_top(xa);
+                clear_top(xk);
+                for (int d = 1; d < 32; ++d) {
+                    const uint32_t pd = __shfl_up_sync(0xFFFFFFFFu, pm, d);
+                    const bool need = lane >= d && pd > th;
+                    if (!__any_sync(0xFFFFFFFFu, need)) break;
+                    const TopK<uint32_t> ya = shfl_up_top(la, d), yk = shfl_up_top(lk, d);
+                    if (need) {
+                        merge_top(xa, ya);
+                        merge_top(xk, yk);
+                    }
+                }
+                merge_top(xa, ta);
+                merge_top(xk, tk);
+                // a lane's gaps in the tile are disjoint and lie within 2^32 - 1 ns
+                // of s0, so its level sums of the tile -- and the warp's, whose
+                // gaps are disjoint too -- fit 32 bits.  The level-k time of a gap
+                // [s, hi) is min(max(E_k, s), max(hi, s)) - s; the s terms are
+                // summed once (S, and SH for the gaps where levels 5-8 are added)
+                // and taken off at the end, exact in wrapping 32-bit arithmetic
+                // because the results fit.
+                uint32_t ma[4], oa[4], mk[4], ok[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    ma[i] = xa.v[i];
+                    oa[i] = xa.v[4 + i];
+                    mk[i] = xk.v[i];
+                    ok[i] = xk.v[4 + i];
+                }
+                uint32_t acc_a[K], acc_k[K], S = 0, SH = 0;
+#pragma unroll
+                for (int k = 0; k < K; ++k) acc_a[k] = acc_k[k] = 0;
+                const uint32_t bnd = rel32(dv.b, s0);
+                uint32_t nxt = shfl_t(s[0], (lane + 1) & 31);
+                if (lane == 31 || (lane + 1) * kItems >= n) nxt = aft;
+#pragma unroll
+                for (int i = 0; i < kItems; ++i) {
+                    const int q = lane * kItems + i;
+                    const bool v = q < n;
+                    const uint32_t ns = (i + 1 < kItems && q + 1 < n) ? s[i + 1] : nxt;
+                    // the gap [s_i, min(next start, window end)) at level k
+                    // lasts until E_k
+                    const uint32_t hc = tmax(tmin(ns, bnd), s[i]);
                     if (v) {
-                        SH += s[i];
+                        uint32_t ev = e[i];
+                        ins4(ma, ev);
+                        if (ev > s[i]) ins4(oa, ev);   // a 5th end still running
+                        if (kmask & (1u << i)) {
+                            uint32_t ek = e[i];
+                            ins4(mk, ek);
+                            if (ek > s[i]) ins4(ok, ek);
+                        }
+                        S += s[i];
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
-                            acc_a[4 + k] += tmin(tmax(oa[k], s[i]), hc);
-                            acc_k[4 + k] += tmin(tmax(ok[k], s[i]), hc);
+                            acc_a[k] += tmin(tmax(ma[k], s[i]), hc);
+                            acc_k[k] += tmin(tmax(mk[k], s[i]), hc);
+                        }
+                    }
+                    if (__any_sync(0xFFFFFFFFu, v && tmax(oa[0], ok[0]) > s[i])) {
+                        if (v) {
+                            SH += s[i];
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                acc_a[4 + k] += tmin(tmax(oa[k], s[i]), hc);
+                                acc_k[4 + k] += tmin(tmax(ok[k], s[i]), hc);
+                            }
                         }
                     }
                 }
-            }
-            // lane k < 2K adds level sum k (one shared-memory update per lane,
-            // side by side)
-            uint32_t mine = 0;
+                // lane k < 2K adds level sum k (one shared-memory update per lane,
+                // side by side)
+                uint32_t mine = 0;
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const uint32_t sub = k < 4 ? S : SH;
-                const uint32_t wa = __reduce_add_sync(0xFFFFFFFFu, acc_a[k] - sub);
-                const uint32_t wk = __reduce_add_sync(0xFFFFFFFFu, acc_k[k] - sub);
-                mine = lane == k ? wa : mine;
-                mine = lane == K + k ? wk : mine;
-            }
-            if (lane < 2 * K) acc[lane] += mine;
-            // state after the tile: lane 31's lists after its walk hold every
-            // end still running at its last start (or, without records, at
-            // the next tile's first start), which covers every end running at
-            // the next tile's first start
+                for (int k = 0; k < K; ++k) {
+                    const uint32_t sub = k < 4 ? S : SH;
+                    const uint32_t wa = __reduce_add_sync(0xFFFFFFFFu, acc_a[k] - sub);
+                    const uint32_t wk = __reduce_add_sync(0xFFFFFFFFu, acc_k[k] - sub);
+                    mine = lane == k ? wa : mine;
+                    mine = lane == K + k ? wk : mine;
+                }
+                if (lane < 2 * K) acc[lane] += mine;
+                // state after the tile: lane 31's lists after its walk hold every
+                // end still running at its last start (or, without records, at
+                // the next tile's first start), which covers every end running at
+                // the next tile's first start
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                ra[i] = shfl_t(ma[i], 31);
-                ra[4 + i] = shfl_t(oa[i], 31);
-                rk[i] = shfl_t(mk[i], 31);
-                rk[4 + i] = shfl_t(ok[i], 31);
-            }
-            sbase = s0;
-            rel = true;
-        } else {
-            // a tile spanning 2^32 ns or more: lane 0 walks it in 64 bits
-            if (lane == 0) {
-                TopK<int64_t> sa, sk;
+                for (int i = 0; i < 4; ++i) {
+                    ra[i] = shfl_t(ma[i], 31);
+                    ra[4 + i] = shfl_t(oa[i], 31);
+                    rk[i] = shfl_t(mk[i], 31);
+                    rk[4 + i] = shfl_t(ok[i], 31);
+                }
+                sbase = s0;
+                rel = true;
+            } else {
+                // a tile spanning 2^32 ns or more: lane 0 walks it in 64 bits
+                if (lane == 0) {
+                    TopK<int64_t> sa, sk;
 #pragma unroll
-                for (int i = 0; i < K; ++i) {
-                    if (rel) {
-                        sa.v[i] = ra[i] ? sbase + static_cast<int64_t>(ra[i]) : INT64_MIN;
-                        sk.v[i] = rk[i] ? sbase + static_cast<int64_t>(rk[i]) : INT64_MIN;
-                    } else {
-                        sa.v[i] = s_st[i];
-                        sk.v[i] = s_st[K + i];
+                    for (int i = 0; i < K; ++i) {
+                        if (rel) {
+                            sa.v[i] = ra[i] ? sbase + static_cast<int64_t>(ra[i]) : INT64_MIN;
+                            sk.v[i] = rk[i] ? sbase + static_cast<int64_t>(rk[i]) : INT64_MIN;
+                        } else {
+                            sa.v[i] = s_st[i];
+                            sk.v[i] = s_st[K + i];
+                        }
+                    }
+                    for (int q = 0; q < n; ++q) {
+                        int64_t sq, eq;
+                        clipped(S, q, dv, sq, eq);
+                        insert_top(sa, eq);
+                        const bool isK = kind_of(S, toff, q) == 0u;
+                        if (isK) insert_top(sk, eq);
+                        int64_t ns = after;
+                        if (q + 1 < n) {
+                            int64_t s1, e1;
+                            clipped(S, q + 1, dv, s1, e1);
+                            ns = s1;
+                        }
+                        const int64_t hi = min64(ns, dv.b);
+#pragma unroll
+                        for (int k = 0; k < K; ++k) {
+                            acc[k] += static_cast<unsigned long long>(max64(min64(hi, max64(sa.v[k], sq)) - sq, 0));
+                            acc[K + k] +=
+                                static_cast<unsigned long long>(max64(min64(hi, max64(sk.v[k], sq)) - sq, 0));
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < K; ++i) {
+                        s_st[i] = sa.v[i];
+                        s_st[K + i] = sk.v[i];
                     }
                 }
-                for (int q = 0; q < n; ++q) {
-                    int64_t sq, eq;
-                    clipped(S, q, dv, sq, eq);
-                    insert_top(sa, eq);
-                    const bool isK = kind_of(S, toff, q) == 0u;
-                    if (isK) insert_top(sk, eq);
-                    int64_t ns = after;
-                    if (q + 1 < n) {
-                        int64_t s1, e1;
-                        clipped(S, q + 1, dv, s1, e1);
-                        ns = s1;
-                    }
-                    const int64_t hi = min64(ns, dv.b);
-#pragma unroll
-                    for (int k = 0; k < K; ++k) {
-                        acc[k] += static_cast<unsigned long long>(max64(min64(hi, max64(sa.v[k], sq)) - sq, 0));
-                        acc[K + k] +=
-                            static_cast<unsigned long long>(max64(min64(hi, max64(sk.v[k], sq)) - sq, 0));
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < K; ++i) {
-                    s_st[i] = sa.v[i];
-                    s_st[K + i] = sk.v[i];
-                }
+                rel = false;
             }
-            rel = false;
+            __syncwarp();
         }
-        __syncwarp();
-    }
     }   // passes
     if (!FIX && ch.n > 0 && ch.rec0 > dv.rec0 && lane == 0) bad |= se[2 * (ch.rec0 - 1)] > se[2 * ch.rec0] ? 4u : 0u;
     bad = __reduce_or_sync(0xFFFFFFFFu, bad);
