@@ -173,7 +173,12 @@ __device__ __forceinline__ void cp_async_wait() {
 // tile before.
 __device__ __forceinline__ void issue_tile(Stage& st, const int64_t* __restrict__ se, const uint8_t* __restrict__ tag,
                                            uint64_t r0, int n, int lane) {
-    for (int q = lane; q < n; q += 32) cp_async16(&st.se[slot(q)], se + 2 * (r0 + q));
+    // record lane + 32 j sits at slot (lane % 8) * 33 + lane / 8 + 4 j
+    longlong2* dst = &st.se[slot(lane)];
+    const int64_t* src = se + 2 * (r0 + lane);
+#pragma unroll
+    for (int j = 0; j < kItems; ++j)
+        if (lane + 32 * j < n) cp_async16(dst + 4 * j, src + 64 * j);
     const uintptr_t A = reinterpret_cast<uintptr_t>(tag + r0);
     const uintptr_t w0 = A & ~static_cast<uintptr_t>(3);
     const int nw = static_cast<int>((A + static_cast<uintptr_t>(n) + 3 - w0) >> 2);
