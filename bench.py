@@ -40,6 +40,7 @@ the same shape (weak scaling, no collective on the data path); the timing is
 the max over ranks.
 """
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -84,6 +85,8 @@ def parse():
     ap.add_argument("--step-s", type=float, default=1.0, help="serving: seconds of served load per step")
     ap.add_argument("--sat-s", type=float, default=3.0, help="serving: seconds of the saturation phase")
     ap.add_argument("--plain-s", type=float, default=3.0, help="serving: seconds of the plain-form phase")
+    ap.add_argument("--native-s", type=float, default=5.0,
+                    help="serving: seconds of the same load from native client threads (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grouped-hint", action="store_true",
@@ -1017,7 +1020,7 @@ def measure_serving(a):
     step_s = a.step_s
     paced_s = (a.warmup + a.steps) * step_s
     # region windows cover what the paced phases deliver (later batches are clipped)
-    horizon = int(a.rate / a.jobs * (paced_s + a.plain_s) * 2 + 64)
+    horizon = int(a.rate / a.jobs * (paced_s + a.plain_s + a.native_s) * 2 + 64)
     wins = [j.windows(horizon) for j in jobs]
     max_rec = max(b.n_records for j in jobs for b in j.batches)
 
@@ -1063,6 +1066,40 @@ def measure_serving(a):
     waves = s2["waves"] - s0["waves"]
     n_queries = s2["queries"] - s0["queries"]
     sub_slices = s2["slices_submitted"] - s0["slices_submitted"]
+    # the same paced load from native client threads: the query latency an
+    # application sees when it calls the library from its own threads
+    native = None
+    if a.native_s > 0:
+        from tracegen import serve_load
+        keep_nat, njobs = [], []
+        for k, j in enumerate(jobs):
+            assert j.job_id == k
+            arr = (P.talp_gpu_trace_batch * len(j.batches))()
+            for i, sb in enumerate(j.batches):
+                b, kp = P.batch_from_arrays(j.job_id, np.zeros(0, np.uint32), np.zeros((0, 0, 2), np.int64),
+                                            sb.host_se, sb.host_state, sb.host_off, sb.dev_se, sb.dev_tag,
+                                            sb.dev_off, P.TALP_GPU_SORTED_BY_START if sb.sorted_by_start else 0)
+                arr[i] = b
+                keep_nat.append(kp)
+            keep_nat.append(arr)
+            njobs.append(dict(job_id=j.job_id, n_ranks=int(j.trace.n_ranks), n_devices=int(j.trace.m_devices),
+                              n_slices=len(j.batches), n_regions=R, span=int(j.span),
+                              slices=ctypes.addressof(arr)))
+        fn = lambda f: ctypes.cast(f, ctypes.c_void_p).value  # noqa: E731
+        na0 = srv.stats()
+        nr = serve_load.run(srv.handle, fn(lib.talp_gpu_server_submit), fn(lib.talp_gpu_server_query), njobs,
+                            load.next_q, a.rate, a.query_ms / 1000.0, a.native_s)
+        na1 = srv.stats()
+        del keep_nat
+        native = {"p50": 1000.0 * _pct(nr["lat"], 0.5) if nr["lat"] else None,
+                  "p99": 1000.0 * _pct(nr["lat"], 0.99) if nr["lat"] else None,
+                  "max": 1000.0 * max(nr["lat"]) if nr["lat"] else None, "queries": nr["queries"],
+                  "queries_per_s": nr["queries"] / nr["wall_s"],
+                  "batches_per_s": nr["slices"] / nr["wall_s"],
+                  "events_per_s": (na1["records_folded"] - na0["records_folded"]) / nr["wall_s"],
+                  "seconds": nr["wall_s"], "errors": nr["errors"], "first_error": nr["first_error"],
+                  "measured": "native client threads (8 submitters, 16 queriers) calling the C ABI; "
+                              "around each talp_gpu_server_query call"}
     # saturation: closed-loop submitters, queries still every period
     sa0 = srv.stats()
     sat_wall = load.run(a.sat_s, closed_loop=True) if a.sat_s > 0 else 0.0
@@ -1157,6 +1194,7 @@ def measure_serving(a):
         "latency_ms": {"p50": ms(_pct(lat_paced, 0.5)), "p99": ms(_pct(lat_paced, 0.99)),
                        "max": ms(max(lat_paced) if lat_paced else None), "queries": len(lat_paced),
                        "measured": "client side, around each query call"},
+        "native_client_latency_ms": native,
         "server_latency_ms": {"p50": st_native["query_p50_ms"], "p99": st_native["query_p99_ms"],
                               "max": st_native["query_max_ms"],
                               "measured": "inside the library, whole run"},
@@ -1183,7 +1221,9 @@ def measure_serving(a):
                 "h2d_bytes_per_step": int(BYTES_PER_RECORD * folded / a.steps),
                 "d2h_bytes_per_step": int(n_queries * R * 184 / a.steps),
                 "note": "the served form takes host buffers: value is already end to end"},
-        "gpu_launches": launches, "clocks": ck, "clocks_plain": ck_plain, "errors": load.errors + pload.errors,
+        "gpu_launches": launches, "clocks": ck, "clocks_plain": ck_plain, "errors": load.errors + pload.errors + (
+            [f"native client: {native['errors']} failed calls, first status {native['first_error']}"]
+            if native and native["errors"] else []),
     }
     return line
 
@@ -1496,7 +1536,7 @@ def default_extras(a, t=None, want=None):
     the raw activity-record adapter."""
     import copy
     sv = copy.copy(a)
-    sv.warmup, sv.steps, sv.step_s, sv.sat_s, sv.plain_s = 2, 10, 1.0, 0.0, 10.0
+    sv.warmup, sv.steps, sv.step_s, sv.sat_s, sv.plain_s, sv.native_s = 2, 10, 1.0, 0.0, 10.0, 5.0
     sv.jobs, sv.rate, sv.query_ms = 256, 2000.0, 10.0
     L = measure_serving(sv)
     pl = L["plain_same_load"]
@@ -1505,7 +1545,8 @@ def default_extras(a, t=None, want=None):
             "workload": L["config"]["workload"], "seconds": sv.steps * sv.step_s, "warmup_s": sv.warmup * sv.step_s,
             "events_per_s": L["value"], "queries_per_s": L["served"]["queries_per_s"],
             "batches_per_s": L["served"]["batches_per_s"],
-            "client_ms": L["latency_ms"], "library_ms": L["server_latency_ms"],
+            "client_ms": L["latency_ms"], "native_client": L["native_client_latency_ms"],
+            "library_ms": L["server_latency_ms"],
             "oracle_sampled_jobs": L["bit_exact_sampled_jobs"]["jobs"],
             "bit_exact_sampled_vs_oracle": L["bit_exact_sampled_jobs"]["exact"],
             "gpu_launches": L["gpu_launches"], "clocks": L["clocks"], "errors": L["errors"]},
