@@ -1668,7 +1668,8 @@ talp_gpu_status talp_gpu_concurrency(talp_gpu_ctx* c, const talp_gpu_trace_batch
     const size_t o_chunk = align_up(o_dev + sizeof(ConcDev) * m, 256);
     const size_t o_top = align_up(o_chunk + sizeof(ConcChunk) * nc, 256);
     const size_t o_in = align_up(o_top + sizeof(int64_t) * 2 * kConcLevels * nc, 256);
-    const size_t o_out = align_up(o_in + sizeof(int64_t) * 2 * kConcLevels * nc, 256);
+    const size_t o_snap = align_up(o_in + sizeof(int64_t) * 2 * kConcLevels * nc, 256);
+    const size_t o_out = align_up(o_snap + sizeof(int64_t) * 2 * 2 * kConcLevels * nc, 256);
     const size_t o_st = align_up(o_out + sizeof(int64_t) * 2 * kConcLevels * m, 256);
     const size_t ws_bytes = o_st + 256;
     const size_t up_bytes = o_top;
@@ -1702,6 +1703,7 @@ talp_gpu_status talp_gpu_concurrency(talp_gpu_ctx* c, const talp_gpu_trace_batch
     TALP_CUDA(launch_concurrency(se, tag, reinterpret_cast<const ConcDev*>(ws + o_dev), static_cast<uint32_t>(m),
                                  reinterpret_cast<const ConcChunk*>(ws + o_chunk), static_cast<uint32_t>(nc),
                                  reinterpret_cast<int64_t*>(ws + o_top), reinterpret_cast<int64_t*>(ws + o_in),
+                                 reinterpret_cast<int64_t*>(ws + o_snap),
                                  reinterpret_cast<int64_t*>(ws + o_out), reinterpret_cast<uint32_t*>(ws + o_st),
                                  stream));
     c->kernel_launches += nc ? 3 : 0;

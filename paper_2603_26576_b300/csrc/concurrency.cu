@@ -283,7 +283,8 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
                                                                 const ConcDev* __restrict__ devs,
                                                                 const ConcChunk* __restrict__ chunks,
                                                                 uint32_t n_chunks, const int64_t* __restrict__ in,
-                                                                int64_t* __restrict__ top, int64_t* __restrict__ out,
+                                                                int64_t* __restrict__ top, int64_t* __restrict__ snap,
+                                                                int64_t* __restrict__ out,
                                                                 uint32_t* __restrict__ status) {
     // per warp: two stages (the tile being worked on and the next one in
     // flight), then the level sums and the int64 state of every warp
@@ -310,7 +311,14 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
     int64_t sbase = 0;
     uint32_t ra[K], rk[K];
     const uint64_t dev_end = dv.rec0 + dv.n;
+    // The main pass keeps its level sums after a chunk's first and second
+    // tiles (snap[c][0..1]).  When the fix-up's walk with the true state ends
+    // within those tiles, the same walk with no entering state is the main
+    // pass's and its sums are taken from snap instead of a second walk.
+    uint32_t walked = 0;   // tiles the current pass has walked
+    bool use_snap = false;
     for (int pass = 0; pass < (FIX ? 2 : 1); ++pass) {
+        walked = 0;
         unsigned long long* acc = pass ? s_acc2 : s_acc;
         if (ch.n > 0)
             issue_tile(stg[0], se, tag, ch.rec0, static_cast<int>(min(static_cast<uint32_t>(kTile), ch.n)), lane);
@@ -601,6 +609,13 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
                 rel = false;
             }
             __syncwarp();
+            if (!FIX && t < 2 && lane < 2 * K)
+                snap[(static_cast<uint64_t>(c) * 2 + t) * 2 * K + lane] = static_cast<int64_t>(acc[lane]);
+            ++walked;
+        }
+        if (FIX && pass == 0 && walked >= 1 && walked <= 2) {
+            use_snap = true;
+            break;
         }
     }   // passes
     if (!FIX && ch.n > 0 && ch.rec0 > dv.rec0 && lane == 0) bad |= se[2 * (ch.rec0 - 1)] > se[2 * ch.rec0] ? 4u : 0u;
@@ -610,7 +625,10 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
         // main pass: the level sums with no entering state, and the state
         // after the chunk for the per-device scan; fix-up: the difference the
         // true entering state makes
-        const int64_t v = FIX ? static_cast<int64_t>(s_acc[lane] - s_acc2[lane]) : static_cast<int64_t>(s_acc[lane]);
+        int64_t v = static_cast<int64_t>(s_acc[lane]);
+        if (FIX)
+            v -= use_snap ? snap[(static_cast<uint64_t>(c) * 2 + walked - 1) * 2 * K + lane]
+                          : static_cast<int64_t>(s_acc2[lane]);
         if (v) atomic_add64(&out[static_cast<uint64_t>(ch.dev) * 2 * K + lane], v);
         if (!FIX) {
             int64_t x = s_st[lane];
@@ -632,8 +650,8 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
 }  // namespace
 
 cudaError_t launch_concurrency(const int64_t* se, const uint8_t* tag, const ConcDev* devs, uint32_t n_dev,
-                               const ConcChunk* chunks, uint32_t n_chunks, int64_t* top, int64_t* in, int64_t* out,
-                               uint32_t* status, cudaStream_t stream) {
+                               const ConcChunk* chunks, uint32_t n_chunks, int64_t* top, int64_t* in, int64_t* snap,
+                               int64_t* out, uint32_t* status, cudaStream_t stream) {
     if (n_chunks == 0) return cudaSuccess;
     const uint32_t blocks = (n_chunks + kWarps - 1) / kWarps;
     constexpr int kSmem = static_cast<int>(sizeof(Stage)) * 2 * kWarps + 3 * kWarps * 2 * K * 8;
@@ -649,10 +667,10 @@ cudaError_t launch_concurrency(const int64_t* se, const uint8_t* tag, const Conc
     // main pass (no entering state; each chunk's state after it into top),
     // per-device scan (top -> in), fix-up of the chunks' leading tiles
     conc_chunk_levels<false><<<blocks, kWarps * 32, kSmem, stream>>>(se, tag, devs, chunks, n_chunks, nullptr, top,
-                                                                     out, status);
+                                                                     snap, out, status);
     conc_chunk_scan<<<(n_dev + kScanWarps - 1) / kScanWarps, kScanWarps * 32, 0, stream>>>(devs, n_dev, top, in);
     conc_chunk_levels<true><<<blocks, kWarps * 32, kSmem, stream>>>(se, tag, devs, chunks, n_chunks, in, nullptr,
-                                                                    out, status);
+                                                                    snap, out, status);
     return cudaGetLastError();
 }
 

@@ -46,8 +46,8 @@ cudaError_t launch_finalize(const FinalizeJob* jobs, uint32_t n_jobs, cudaStream
 cudaError_t launch_thread_tree(const ThreadJob* jobs, uint32_t n_jobs, cudaStream_t stream);
 cudaError_t launch_thread_combine(const ThreadOut* parts, uint32_t n_parts, ThreadOut* out, cudaStream_t stream);
 cudaError_t launch_concurrency(const int64_t* se, const uint8_t* tag, const ConcDev* devs, uint32_t n_dev,
-                               const ConcChunk* chunks, uint32_t n_chunks, int64_t* top, int64_t* in, int64_t* out,
-                               uint32_t* status, cudaStream_t stream);
+                               const ConcChunk* chunks, uint32_t n_chunks, int64_t* top, int64_t* in, int64_t* snap,
+                               int64_t* out, uint32_t* status, cudaStream_t stream);
 cudaError_t launch_raw_count(const RawTile* tiles, uint32_t n_tiles, const RawRank* ranks, uint32_t n_ranks,
                              uint32_t* hist, uint64_t* offs, RawMove* moves, uint64_t* dev_count,
                              uint32_t* dev_streams, uint64_t* dev_runs, uint32_t* status, int grid,
