@@ -264,6 +264,24 @@ __global__ void __launch_bounds__(kScanWarps * 32) conc_chunk_scan(const ConcDev
 // 4 push it out while it is still running at the record's start (a
 // concurrency of 5 or more, rare); levels 5-8 are added only for records at
 // which some lane of the warp has such an end.
+// Top 4 of two sorted-descending lists of 4, into the first 4 entries of x:
+// elementwise max against the reversed list, then a bitonic half-cleaner
+// cascade.
+__device__ __forceinline__ void merge4(uint32_t* x, const uint32_t (&y)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) x[i] = tmax(x[i], y[3 - i]);
+#pragma unroll
+    for (int w = 2; w > 0; w >>= 1) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if ((i & w) == 0) {
+                const uint32_t hi = tmax(x[i], x[i + w]), lo = tmin(x[i], x[i + w]);
+                x[i] = hi;
+                x[i + w] = lo;
+            }
+    }
+}
+
 // Insertion of e into a sorted-descending list of 4, e left as the value
 // pushed out.  Entry k of the result is max(x[k], min(x[k-1], e)) -- x[k]
 // above e's place, e at it, x[k-1] below it -- so all four come out in two
@@ -470,17 +488,47 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
                     const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, pm, d);
                     if (lane >= d) pm = tmax(pm, y);
                 }
+                // The lanes looked back at usually hold at most 4 ends still
+                // running at th between them; then their top 4 lists carry all
+                // of those (a kernel end running at th is one of them), and
+                // ends at or before th add nothing to this lane's gaps nor to
+                // the exit state.  Only when 5 or more run does the warp merge
+                // the lanes' full lists.
                 TopK<uint32_t> xa, xk;
                 clear_top(xa);
                 clear_top(xk);
+                uint32_t run = 0;   // ends of the looked-back lanes running at th
                 for (int d = 1; d < 32; ++d) {
                     const uint32_t pd = __shfl_up_sync(0xFFFFFFFFu, pm, d);
                     const bool need = lane >= d && pd > th;
                     if (!__any_sync(0xFFFFFFFFu, need)) break;
-                    const TopK<uint32_t> ya = shfl_up_top(la, d), yk = shfl_up_top(lk, d);
+                    uint32_t ya[4], yk[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        ya[i] = __shfl_up_sync(0xFFFFFFFFu, la.v[i], d);
+                        yk[i] = __shfl_up_sync(0xFFFFFFFFu, lk.v[i], d);
+                    }
+                    const uint32_t y4 = __shfl_up_sync(0xFFFFFFFFu, la.v[4], d);
                     if (need) {
-                        merge_top(xa, ya);
-                        merge_top(xk, yk);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) run += ya[i] > th ? 1u : 0u;
+                        run += y4 > th ? 1u : 0u;
+                        merge4(xa.v, ya);
+                        merge4(xk.v, yk);
+                    }
+                }
+                if (__any_sync(0xFFFFFFFFu, run > 4)) {
+                    clear_top(xa);
+                    clear_top(xk);
+                    for (int d = 1; d < 32; ++d) {
+                        const uint32_t pd = __shfl_up_sync(0xFFFFFFFFu, pm, d);
+                        const bool need = lane >= d && pd > th;
+                        if (!__any_sync(0xFFFFFFFFu, need)) break;
+                        const TopK<uint32_t> ya = shfl_up_top(la, d), yk = shfl_up_top(lk, d);
+                        if (need) {
+                            merge_top(xa, ya);
+                            merge_top(xk, yk);
+                        }
                     }
                 }
                 merge_top(xa, ta);
