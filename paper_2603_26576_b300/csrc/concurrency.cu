@@ -488,16 +488,20 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
                     const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, pm, d);
                     if (lane >= d) pm = tmax(pm, y);
                 }
-                // The lanes looked back at usually hold at most 4 ends still
-                // running at th between them; then their top 4 lists carry all
-                // of those (a kernel end running at th is one of them), and
-                // ends at or before th add nothing to this lane's gaps nor to
-                // the exit state.  Only when 5 or more run does the warp merge
-                // the lanes' full lists.
+                // The lanes looked back at and the entering state usually hold
+                // at most 4 ends still running at th between them; then their
+                // top 4 lists carry all of those (a kernel end running at th is
+                // one of them), and ends at or before th add nothing to this
+                // lane's gaps nor to the exit state.  Only when 5 or more run
+                // does the warp merge the full lists.
                 TopK<uint32_t> xa, xk;
                 clear_top(xa);
                 clear_top(xk);
-                uint32_t run = 0;   // ends of the looked-back lanes running at th
+                // ends of the entering state and of the looked-back lanes
+                // running at th (the first 5 of each list counted)
+                uint32_t run = 0;
+#pragma unroll
+                for (int i = 0; i < 5; ++i) run += ta.v[i] > th ? 1u : 0u;
                 for (int d = 1; d < 32; ++d) {
                     const uint32_t pd = __shfl_up_sync(0xFFFFFFFFu, pm, d);
                     const bool need = lane >= d && pd > th;
@@ -530,9 +534,18 @@ __global__ void __launch_bounds__(kWarps * 32, 2) conc_chunk_levels(const int64_
                             merge_top(xk, yk);
                         }
                     }
+                    merge_top(xa, ta);
+                    merge_top(xk, tk);
+                } else {
+                    uint32_t t4a[4], t4k[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        t4a[i] = ta.v[i];
+                        t4k[i] = tk.v[i];
+                    }
+                    merge4(xa.v, t4a);
+                    merge4(xk.v, t4k);
                 }
-                merge_top(xa, ta);
-                merge_top(xk, tk);
                 // a lane's gaps in the tile are disjoint and lie within 2^32 - 1 ns
                 // of s0, so its level sums of the tile -- and the warp's, whose
                 // gaps are disjoint too -- fit 32 bits.  The level-k time of a gap
