@@ -448,7 +448,7 @@ __device__ __forceinline__ void merge32(FmsShared& sh, const ChunkMeta& M, int c
             const uint32_t stop = min(o1, b1);
             uint32_t ka = i < la ? kin[a0 + i] : 0xFFFFFFFFu, kb = j < lb ? kin[a1 + j] : 0xFFFFFFFFu;
             for (; o < stop; ++o) {
-                const bool takeA = j >= lb || (i < la && ka <= kb);
+                const bool takeA = ka <= kb;   // an exhausted run reads as the sentinel
                 const uint32_t at = takeA ? a0 + i : a1 + j;
                 kout[o] = takeA ? ka : kb;
                 iout[o] = r ? iin[at] : static_cast<uint16_t>(at);
@@ -483,7 +483,7 @@ __device__ __forceinline__ void merge32(FmsShared& sh, const ChunkMeta& M, int c
 #pragma unroll
     for (int q = 0; q < kFmsItems; ++q) {
         if (q < cnt) {
-            const bool takeA = j >= lb || (i < la && ka <= kb);
+            const bool takeA = ka <= kb;   // an exhausted run reads as the sentinel
             const uint32_t at = takeA ? i : a1 + j;
             const uint32_t x = r ? iin[at] : at;
             sr[q] = takeA ? ka : kb;
@@ -945,7 +945,9 @@ __global__ void __launch_bounds__(kFmsThreads, 3)
             hib |= sh.red32[q][2];
             bad |= sh.red32[q][3];
         }
-        const bool span32 = hib == 0 && ((mxS - s0) >> 32) == 0;
+        // starts within 2^32 - 2 ns of s0: a 32-bit key never equals the
+        // merge's end-of-run sentinel 0xFFFFFFFF
+        const bool span32 = hib == 0 && static_cast<uint64_t>(mxS - s0) < 0xFFFFFFFFull;
         // 0 stands for "no record" (an end equal to s0 reads as none: it cannot
         // reach past any later start, so carries and sums are unchanged)
         int64_t aK = bK ? s0 + bK : NEG_INF, aM = bM ? s0 + bM : NEG_INF;
