@@ -2,7 +2,8 @@
 """Benchmark of the efficiency-metric reducer on synthetic traces.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
-                  [--workload plain|small|batched|serving] [--scale S]
+                  [--workload plain|small|scale|batched|batched-full|serving|concurrency|raw|threads]
+                  [--scale S]
 
 One step = one pass of the whole hot path over one trace resident in HBM:
 record validation, the device flattening (kernel / transfer / busy unions per
@@ -26,7 +27,9 @@ cpu_baseline: the CPU oracle on a bounded one-rank sample of the workload.
 
 The default command's line also carries sub-objects measured in the same
 run: `serving` and `serving_plain` (the served form and the plain form at
-the serving load: p50/p99 query latency), `batched` (the small-trace batched
+the serving load: p50/p99 query latency, the served form's both from Python
+client threads and from native client threads that call the C ABI, and
+inside the library), `batched` (the small-trace batched
 form against one trace per launch), `sort_stage` (the same trace with each
 device's records grouped by stream, sorted by the library), `concurrency`
 (the concurrency profile of its devices) and `raw` (the trace at 25% as raw
