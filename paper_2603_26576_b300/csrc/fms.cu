@@ -452,13 +452,13 @@ __device__ __forceinline__ void merge32(FmsShared& sh, const ChunkMeta& M, int c
                 const uint32_t at = takeA ? a0 + i : a1 + j;
                 kout[o] = takeA ? ka : kb;
                 iout[o] = r ? iin[at] : static_cast<uint16_t>(at);
-                if (takeA) {
-                    ++i;
-                    ka = i < la ? kin[a0 + i] : 0xFFFFFFFFu;
-                } else {
-                    ++j;
-                    kb = j < lb ? kin[a1 + j] : 0xFFFFFFFFu;
-                }
+                // the taken run's next key, at + 1, unless that run is used up:
+                // one predicated load, no divergent branch
+                i += takeA ? 1u : 0u;
+                j += takeA ? 0u : 1u;
+                const uint32_t nx = at + 1 < (takeA ? a1 : b1) ? kin[at + 1] : 0xFFFFFFFFu;
+                ka = takeA ? nx : ka;
+                kb = takeA ? kb : nx;
             }
         }
         cbar();
@@ -489,13 +489,11 @@ __device__ __forceinline__ void merge32(FmsShared& sh, const ChunkMeta& M, int c
             sr[q] = takeA ? ka : kb;
             er[q] = sh.end32[x];
             tg[q] = sh.tagc[x];
-            if (takeA) {
-                ++i;
-                ka = i < la ? kin[i] : 0xFFFFFFFFu;
-            } else {
-                ++j;
-                kb = j < lb ? kin[a1 + j] : 0xFFFFFFFFu;
-            }
+            i += takeA ? 1u : 0u;
+            j += takeA ? 0u : 1u;
+            const uint32_t nx = at + 1 < (takeA ? a1 : n) ? kin[at + 1] : 0xFFFFFFFFu;
+            ka = takeA ? nx : ka;
+            kb = takeA ? kb : nx;
         } else {
             sr[q] = er[q] = tg[q] = 0;
         }
